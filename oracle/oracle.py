@@ -1,0 +1,306 @@
+"""ctypes marshalling and step composition for the C oracle.
+
+TEST INFRASTRUCTURE: see the package docstring.  Every function here either
+calls one C routine of ``sam_oracle.c`` or composes them in the order of
+Sec. II of the paper (edge extraction -> pyramid -> top-level exhaustive
+search -> refinement down the pyramid -> best poses).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sam_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libsam_oracle.so")
+_lib = None
+
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_c_int = ctypes.c_int
+_c_dbl = ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile sam_oracle.c into a shared library (gcc, -O2, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        lib.or_pyramid_down.argtypes = [_u8p, _c_int, _c_int, _u8p]
+        lib.or_sobel.argtypes = [_u8p, _c_int, _c_int, _i32p, _i32p]
+        lib.or_search_mask.argtypes = [_i32p, _i32p, _c_int, _c_int, _u8p]
+        lib.or_hysteresis.argtypes = [_i32p, _i32p, _c_int, _c_int, _c_int, _c_int, _u8p]
+        lib.or_unit_field.argtypes = [_i32p, _i32p, _u8p, _c_int, _f64p]
+        lib.or_model_points.argtypes = [_u8p, _c_int, _c_int, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p]
+        lib.or_model_points.restype = _c_int
+        lib.or_rotate_points.argtypes = [_i32p, _i32p, _i32p, _i32p, _c_int, _c_int, _c_dbl,
+                                         _i32p, _i32p, _f64p, _f64p]
+        lib.or_score_pose.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _f64p, _f64p, _c_int,
+                                      _c_int, _c_int, _c_int, _c_int]
+        lib.or_score_pose.restype = _c_dbl
+        lib.or_score_map.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
+                                     _c_dbl, _c_int, _c_int, _c_int, _c_int, _f64p]
+        lib.or_candidates.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_dbl, _c_int, _i32p, _i32p, _i32p, _f64p]
+        lib.or_candidates.restype = _c_int
+        lib.or_child_shift.argtypes = [_c_int, _c_dbl, _c_dbl, _c_dbl, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]
+        lib.or_refine_level.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
+                                        _c_dbl, _c_dbl, _c_dbl, _c_int, _c_int, _c_dbl, _c_int,
+                                        _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p]
+        lib.or_nms.argtypes = [_c_int, _i32p, _i32p, _i32p, _f64p, _c_int, _c_int, _c_int, _c_int, _i32p]
+        lib.or_nms.restype = _c_int
+        _lib = lib
+    return _lib
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# edge extraction and pyramid (Sec. II)
+# ---------------------------------------------------------------------------
+
+def pyramid_down(img):
+    img = _u8(img)
+    h, w = img.shape
+    out = np.empty((h // 2, w // 2), dtype=np.uint8)
+    _L().or_pyramid_down(img, w, h, out)
+    return out
+
+
+def pyramid(img, levels):
+    out = [_u8(img)]
+    for _ in range(1, levels):
+        out.append(pyramid_down(out[-1]))
+    return out
+
+
+def sobel(img):
+    img = _u8(img)
+    h, w = img.shape
+    gx = np.empty((h, w), dtype=np.int32)
+    gy = np.empty((h, w), dtype=np.int32)
+    _L().or_sobel(img, w, h, gx, gy)
+    return gx, gy
+
+
+def search_mask(gx, gy, low):
+    gx, gy = _i32(gx), _i32(gy)
+    m = np.empty(gx.shape, dtype=np.uint8)
+    _L().or_search_mask(gx, gy, gx.size, int(low), m)
+    return m
+
+
+def hysteresis(gx, gy, low, high):
+    gx, gy = _i32(gx), _i32(gy)
+    h, w = gx.shape
+    m = np.empty(gx.shape, dtype=np.uint8)
+    _L().or_hysteresis(gx, gy, w, h, int(low), int(high), m)
+    return m
+
+
+def unit_field(gx, gy, mask):
+    gx, gy, mask = _i32(gx), _i32(gy), _u8(mask)
+    f = np.empty(gx.shape + (2,), dtype=np.float64)
+    _L().or_unit_field(gx, gy, mask, gx.size, f)
+    return f
+
+
+def model_points(tmpl, low, high):
+    """(tx, ty, gx, gy) int32 arrays of one template level's edge points."""
+    tmpl = _u8(tmpl)
+    h, w = tmpl.shape
+    tx, ty, gx, gy = (np.empty(w * h, dtype=np.int32) for _ in range(4))
+    n = _L().or_model_points(tmpl, w, h, int(low), int(high), tx, ty, gx, gy)
+    return tx[:n].copy(), ty[:n].copy(), gx[:n].copy(), gy[:n].copy()
+
+
+@dataclass
+class OracleModel:
+    """Template pyramid and per-level edge points (Sec. II inputs)."""
+
+    levels: int
+    angle_step_deg: float           # at level 0
+    low: int
+    high: int
+    polarity: int
+    sizes: list = field(default_factory=list)     # (w, h) per level
+    points: list = field(default_factory=list)    # (tx, ty, gx, gy) per level
+
+    def ntheta(self, level):
+        return int(round(360.0 / self.angle_step_deg)) >> level
+
+    def dtheta(self, level):
+        return self.angle_step_deg * (2 ** level)
+
+
+def create_model(tmpl, low, high, levels, angle_step_deg, polarity=0):
+    n0 = int(round(360.0 / angle_step_deg))
+    if abs(n0 * angle_step_deg - 360.0) > 1e-9 or n0 % (1 << (levels - 1)) != 0:
+        raise ValueError("360 / angle_step must be an integer divisible by 2^(levels-1)")
+    m = OracleModel(levels=levels, angle_step_deg=float(angle_step_deg), low=low, high=high, polarity=polarity)
+    for lvl, img in enumerate(pyramid(tmpl, levels)):
+        m.sizes.append((img.shape[1], img.shape[0]))
+        pts = model_points(img, low, high)
+        if len(pts[0]) == 0:
+            raise ValueError(f"template level {lvl} has no edge points")
+        m.points.append(pts)
+    return m
+
+
+def search_fields(img, levels, low):
+    """Per-level FP64 unit gradient fields of the search image (H x W x 2)."""
+    out = []
+    for lvl_img in pyramid(img, levels):
+        gx, gy = sobel(lvl_img)
+        out.append(unit_field(gx, gy, search_mask(gx, gy, low)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# scoring (Eq. (1), Eq. (2), neighbouring search)
+# ---------------------------------------------------------------------------
+
+def rotate_points(pts, k, dtheta_deg):
+    tx, ty, gx, gy = pts
+    n = len(tx)
+    ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
+    px, py = np.empty(n, np.float64), np.empty(n, np.float64)
+    _L().or_rotate_points(tx, ty, gx, gy, n, int(k), float(dtheta_deg), ox, oy, px, py)
+    return ox, oy, px, py
+
+
+def score_pose(field, rot, ux, uy, nbhd=3, polarity=0):
+    field = _f64(field)
+    h, w = field.shape[:2]
+    ox, oy, px, py = rot
+    return _L().or_score_pose(field, w, h, ox, oy, px, py, len(ox), int(ux), int(uy), int(nbhd), int(polarity))
+
+
+def score_map(field, pts, ntheta, dtheta_deg, step_x=1, step_y=1, nbhd=3, polarity=0):
+    """Exhaustive map M[k, gy, gx] over all poses of the step grid."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    gw, gh = (w + step_x - 1) // step_x, (h + step_y - 1) // step_y
+    out = np.empty((ntheta, gh, gw), dtype=np.float64)
+    _L().or_score_map(field, w, h, tx, ty, gx, gy, len(tx), int(ntheta), float(dtheta_deg), int(step_x),
+                      int(step_y), int(nbhd), int(polarity), out)
+    return out
+
+
+def candidates(smap, min_score, K):
+    """Top-K strict 3x3x3 local maxima (theta circular) with M >= min_score.
+
+    Returns arrays (k, gy, gx, score) sorted best first.
+    """
+    smap = _f64(smap)
+    nth, gh, gw = smap.shape
+    ck, cy, cx = (np.empty(K, np.int32) for _ in range(3))
+    cs = np.empty(K, np.float64)
+    n = _L().or_candidates(smap, nth, gh, gw, float(min_score), int(K), ck, cy, cx, cs)
+    return ck[:n].copy(), cy[:n].copy(), cx[:n].copy(), cs[:n].copy()
+
+
+def _ref_shift_d(model, level):
+    """d = 2 c_{l+1} + 1/2 - c_l per axis for the step from level+1 to level."""
+    (w0, h0), (w1, h1) = model.sizes[level], model.sizes[level + 1]
+    return 2 * (w1 // 2) + 0.5 - (w0 // 2), 2 * (h1 // 2) + 0.5 - (h0 // 2)
+
+
+def child_shift(model, level, k_parent):
+    dx, dy = _ref_shift_d(model, level)
+    sx, sy = ctypes.c_int32(), ctypes.c_int32()
+    _L().or_child_shift(int(k_parent), float(model.dtheta(level + 1)), dx, dy, ctypes.byref(sx), ctypes.byref(sy))
+    return sx.value, sy.value
+
+
+def refine_level(model, level, field, xs, ys, ks, nbhd, polarity, min_score):
+    """Best of the 27 level-`level` poses around each level+1 parent pose."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = model.points[level]
+    n = len(xs)
+    ox, oy, ok = (np.empty(n, np.int32) for _ in range(3))
+    os_ = np.empty(n, np.float64)
+    dx, dy = _ref_shift_d(model, level)
+    _L().or_refine_level(field, w, h, tx, ty, gx, gy, len(tx), model.ntheta(level), float(model.dtheta(level)),
+                         dx, dy, int(nbhd), int(polarity), float(min_score), n,
+                         _i32(xs), _i32(ys), _i32(ks), ox, oy, ok, os_)
+    return ox, oy, ok, os_
+
+
+def nms(xs, ys, ks, ss, w, h, min_side, max_out):
+    n = len(xs)
+    keep = np.empty(max(n, 1), np.int32)
+    nk = _L().or_nms(n, _i32(xs), _i32(ys), _i32(ks), _f64(ss), int(w), int(h), int(min_side), int(max_out), keep)
+    return keep[:nk].copy()
+
+
+@dataclass
+class DetectParams:
+    step_x: int = 1
+    step_y: int = 1
+    nbhd: int = 3
+    min_score: float = 0.7
+    max_detections: int = 16
+    top_k: int = 64
+
+
+def detect(model: OracleModel, img, params: DetectParams, trace=None):
+    """Full detection, Sec. II order.
+
+    Returns a list of (x, y, theta_deg, score, k) at level 0, best first.
+    If `trace` is a dict it receives the intermediate results per level.
+    """
+    L = model.levels
+    fields = search_fields(img, L, model.low)
+    top = L - 1
+    smap = score_map(fields[top], model.points[top], model.ntheta(top), model.dtheta(top),
+                     params.step_x, params.step_y, params.nbhd, model.polarity)
+    ck, cy, cx, cs = candidates(smap, params.min_score, params.top_k)
+    xs, ys, ks, ss = cx * params.step_x, cy * params.step_y, ck, cs
+    if trace is not None:
+        trace["fields"] = fields
+        trace["map"] = smap
+        trace["cand"] = (xs.copy(), ys.copy(), ks.copy(), ss.copy())
+        trace["levels"] = {}
+    for lvl in range(top - 1, -1, -1):
+        alive = np.isfinite(ss)
+        xs, ys, ks, ss = xs[alive], ys[alive], ks[alive], ss[alive]
+        xs, ys, ks, ss = refine_level(model, lvl, fields[lvl], xs, ys, ks, params.nbhd, model.polarity,
+                                      params.min_score)
+        if trace is not None:
+            trace["levels"][lvl] = (xs.copy(), ys.copy(), ks.copy(), ss.copy())
+    w0, h0 = model.sizes[0]
+    H, W = img.shape
+    keep = nms(xs, ys, ks, ss, W, H, min(w0, h0), params.max_detections)
+    return [(int(xs[i]), int(ys[i]), float(ks[i]) * model.angle_step_deg, float(ss[i]), int(ks[i])) for i in keep]

@@ -1,0 +1,470 @@
+/*
+ * Plain FP64 CPU oracle of the shape-based alignment detector of
+ * T.-S. Le and C.-Y. Lin, "GPU-accelerated image alignment for object
+ * detection in industrial applications" (arXiv 2112.05576).
+ *
+ * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load this code.  It shares
+ * no source, header, table or helper with the CUDA library; it is written
+ * for a reader checking it against the paper, one plain loop per step:
+ * single-threaded, FP64, no blocking, no vectorisation.
+ *
+ * Readings of the paper where it is silent (the paper names no gradient
+ * operator, pyramid filter, threshold units, rounding, border rule or
+ * coarse-to-fine rule); every one is listed with its justification in the
+ * project's design notes:
+ *   - gradients: 3x3 Sobel, x to the right, y downwards, integer; the
+ *     1-pixel image border has zero gradient (never an edge);
+ *   - magnitude unit: |g| / 4 (a step of height h has magnitude h), an edge
+ *     is gx^2 + gy^2 >= 16 T^2 (exact integer compare);
+ *   - search image: single threshold T_low; model: hysteresis (>= T_high
+ *     seeds, grown 8-connected through >= T_low);
+ *   - pyramid of intensities, 2x2 mean rounded half up, odd row/col dropped;
+ *   - template reference point (floor(W/2), floor(H/2)) at every level;
+ *   - projected points rounded to nearest, floor(v + 1/2), in FP64;
+ *   - samples outside the image or on non-edge pixels contribute 0.
+ *
+ * Build: gcc -O2 -fPIC -shared -ffp-contract=off (no -ffast-math, no FMA
+ * contraction, so the rounding of projected points is the plain IEEE one).
+ */
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Sec. II: "Edge extraction is followed by an image pyramid construction."  */
+/* One pyramid step: 2x2 block mean, rounded half up; odd trailing row/col   */
+/* dropped.  dst is (w/2) x (h/2), row-major, stride w/2.                    */
+/* ------------------------------------------------------------------------ */
+void or_pyramid_down(const uint8_t *src, int w, int h, uint8_t *dst)
+{
+    int w2 = w / 2, h2 = h / 2;
+    for (int y = 0; y < h2; ++y) {
+        for (int x = 0; x < w2; ++x) {
+            int s = src[(2 * y) * w + 2 * x] + src[(2 * y) * w + 2 * x + 1] +
+                    src[(2 * y + 1) * w + 2 * x] + src[(2 * y + 1) * w + 2 * x + 1];
+            dst[y * w2 + x] = (uint8_t)((s + 2) / 4);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. II: "The generating x-gradients, y-gradients and gradient            */
+/* magnitudes of edge points are recorded."  3x3 Sobel, integer:             */
+/*   gx = sum_{r=-1..1} w_r (I[y+r][x+1] - I[y+r][x-1]),  w = (1, 2, 1)      */
+/*   gy = sum_{c=-1..1} w_c (I[y+1][x+c] - I[y-1][x+c])                      */
+/* Border pixels (first/last row and column) get gx = gy = 0.                */
+/* ------------------------------------------------------------------------ */
+void or_sobel(const uint8_t *img, int w, int h, int32_t *gx, int32_t *gy)
+{
+    static const int wt[3] = {1, 2, 1};
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            int32_t sx = 0, sy = 0;
+            if (x > 0 && y > 0 && x < w - 1 && y < h - 1) {
+                for (int r = -1; r <= 1; ++r)
+                    sx += wt[r + 1] * ((int)img[(y + r) * w + x + 1] - (int)img[(y + r) * w + x - 1]);
+                for (int c = -1; c <= 1; ++c)
+                    sy += wt[c + 1] * ((int)img[(y + 1) * w + x + c] - (int)img[(y - 1) * w + x + c]);
+            }
+            gx[y * w + x] = sx;
+            gy[y * w + x] = sy;
+        }
+    }
+}
+
+/* Edge test of one pixel: magnitude |g|/4 >= T, i.e. gx^2 + gy^2 >= 16 T^2. */
+static int or_is_edge(int32_t gx, int32_t gy, int T)
+{
+    int64_t m2 = (int64_t)gx * gx + (int64_t)gy * gy;
+    return m2 >= (int64_t)16 * T * T;
+}
+
+/* Sec. II "edge detection thresholds", search image: one threshold T_low.  */
+void or_search_mask(const int32_t *gx, const int32_t *gy, int npx, int low, uint8_t *mask)
+{
+    for (int i = 0; i < npx; ++i)
+        mask[i] = (uint8_t)or_is_edge(gx[i], gy[i], low);
+}
+
+/* Sec. II "edge detection thresholds", model image: hysteresis.  A pixel is
+ * an edge if it is >= T_low and 8-connected through >= T_low pixels to a
+ * pixel >= T_high.  Plain flood fill with an explicit stack.               */
+void or_hysteresis(const int32_t *gx, const int32_t *gy, int w, int h, int low, int high, uint8_t *mask)
+{
+    int npx = w * h;
+    int *stack = (int *)malloc(sizeof(int) * (size_t)(npx > 0 ? npx : 1));
+    int top = 0;
+    for (int i = 0; i < npx; ++i)
+        mask[i] = 0;
+    for (int i = 0; i < npx; ++i) {
+        if (mask[i] || !or_is_edge(gx[i], gy[i], high))
+            continue;
+        mask[i] = 1;
+        stack[top++] = i;
+        while (top > 0) {
+            int p = stack[--top];
+            int py = p / w, px = p % w;
+            for (int dy = -1; dy <= 1; ++dy) {
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int qx = px + dx, qy = py + dy;
+                    if (qx < 0 || qy < 0 || qx >= w || qy >= h)
+                        continue;
+                    int q = qy * w + qx;
+                    if (!mask[q] && or_is_edge(gx[q], gy[q], low)) {
+                        mask[q] = 1;
+                        stack[top++] = q;
+                    }
+                }
+            }
+        }
+    }
+    free(stack);
+}
+
+/* Eq. (1) normalisation of the search image: w_hat = (gx, gy) / |g| on edge
+ * pixels, (0, 0) elsewhere.  field is interleaved (wx, wy) per pixel.     */
+void or_unit_field(const int32_t *gx, const int32_t *gy, const uint8_t *mask, int npx, double *field)
+{
+    for (int i = 0; i < npx; ++i) {
+        if (mask[i]) {
+            double m = sqrt((double)gx[i] * gx[i] + (double)gy[i] * gy[i]);
+            field[2 * i] = gx[i] / m;
+            field[2 * i + 1] = gy[i] / m;
+        } else {
+            field[2 * i] = 0.0;
+            field[2 * i + 1] = 0.0;
+        }
+    }
+}
+
+/* Model edge points of one template level (Sec. II): Sobel, hysteresis, then
+ * every edge pixel in raster order with t = (col - floor(w/2), row -
+ * floor(h/2)) and its integer gradient.  Returns the number of points; the
+ * output arrays must hold w*h entries.                                     */
+int or_model_points(const uint8_t *tmpl, int w, int h, int low, int high,
+                    int32_t *tx, int32_t *ty, int32_t *pgx, int32_t *pgy)
+{
+    int npx = w * h;
+    int32_t *gx = (int32_t *)malloc(sizeof(int32_t) * (size_t)npx);
+    int32_t *gy = (int32_t *)malloc(sizeof(int32_t) * (size_t)npx);
+    uint8_t *mask = (uint8_t *)malloc((size_t)npx);
+    or_sobel(tmpl, w, h, gx, gy);
+    or_hysteresis(gx, gy, w, h, low, high, mask);
+    int n = 0;
+    for (int row = 0; row < h; ++row) {
+        for (int col = 0; col < w; ++col) {
+            int i = row * w + col;
+            if (!mask[i])
+                continue;
+            tx[n] = col - w / 2;
+            ty[n] = row - h / 2;
+            pgx[n] = gx[i];
+            pgy[n] = gy[i];
+            ++n;
+        }
+    }
+    free(gx);
+    free(gy);
+    free(mask);
+    return n;
+}
+
+/* Eq. (2): p = R(theta) t + u.  For angle index k at a level whose angle step
+ * is dtheta_deg, theta = (k * dtheta_deg) * pi / 180 (FP64).  Offsets are
+ * rounded to the nearest pixel, floor(v + 1/2); the model gradient is turned
+ * by the same rotation and normalised to a unit vector p_hat.              */
+void or_rotate_points(const int32_t *tx, const int32_t *ty, const int32_t *gx, const int32_t *gy, int n,
+                      int k, double dtheta_deg, int32_t *ox, int32_t *oy, double *px, double *py)
+{
+    double th = ((double)k * dtheta_deg) * OR_PI / 180.0;
+    double c = cos(th), s = sin(th);
+    for (int i = 0; i < n; ++i) {
+        double x = (double)tx[i], y = (double)ty[i];
+        ox[i] = (int32_t)floor(c * x - s * y + 0.5);
+        oy[i] = (int32_t)floor(s * x + c * y + 0.5);
+        double m = sqrt((double)gx[i] * gx[i] + (double)gy[i] * gy[i]);
+        double ux = gx[i] / m, uy = gy[i] / m;
+        px[i] = c * ux - s * uy;
+        py[i] = s * ux + c * uy;
+    }
+}
+
+/* One point's vote (Sec. II neighbouring search + Eq. (1) term): the maximum,
+ * over the nbhd x nbhd window around the projected point, of
+ * p_hat . w_hat (polarity 0) or |p_hat . w_hat| (polarity 1).  Samples
+ * outside the image count as w_hat = 0.                                    */
+static double or_vote(const double *field, int w, int h, int x0, int y0, double px, double py,
+                      int nbhd, int polarity)
+{
+    int r = nbhd / 2;
+    double best = -INFINITY;
+    for (int b = -r; b <= r; ++b) {
+        for (int a = -r; a <= r; ++a) {
+            int x = x0 + a, y = y0 + b;
+            double v = 0.0;
+            if (x >= 0 && y >= 0 && x < w && y < h) {
+                const double *wv = field + 2 * ((size_t)y * w + x);
+                v = px * wv[0] + py * wv[1];
+                if (polarity)
+                    v = fabs(v);
+            }
+            if (v > best)
+                best = v;
+        }
+    }
+    return best;
+}
+
+/* Eq. (1): M(u, theta) = (1/n) sum_i vote_i, the points already rotated for
+ * theta (offsets ox, oy and unit directions px, py).                       */
+double or_score_pose(const double *field, int w, int h, const int32_t *ox, const int32_t *oy,
+                     const double *px, const double *py, int n, int ux, int uy, int nbhd, int polarity)
+{
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i)
+        sum += or_vote(field, w, h, ux + ox[i], uy + oy[i], px[i], py[i], nbhd, polarity);
+    return sum / n;
+}
+
+/* Sec. II CPU design: exhaustive search with three nested loops over
+ * x-translation, y-translation and rotation; every pose scored by Eq. (1).
+ * Poses are u = (gxi * step_x, gyi * step_y) for the grid gxi < ceil(w /
+ * step_x), gyi < ceil(h / step_y), and theta_k for k < ntheta.  The map is
+ * written out[(k * gh + gyi) * gw + gxi].  Eq. (2) depends on theta only, so
+ * each angle's rotated points are computed once up front.                  */
+void or_score_map(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                  const int32_t *gx, const int32_t *gy, int n, int ntheta, double dtheta_deg,
+                  int step_x, int step_y, int nbhd, int polarity, double *out)
+{
+    int gw = (w + step_x - 1) / step_x, gh = (h + step_y - 1) / step_y;
+    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * ntheta);
+    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * ntheta);
+    double *px = (double *)malloc(sizeof(double) * (size_t)n * ntheta);
+    double *py = (double *)malloc(sizeof(double) * (size_t)n * ntheta);
+    for (int k = 0; k < ntheta; ++k)
+        or_rotate_points(tx, ty, gx, gy, n, k, dtheta_deg, ox + (size_t)k * n, oy + (size_t)k * n,
+                         px + (size_t)k * n, py + (size_t)k * n);
+    for (int gxi = 0; gxi < gw; ++gxi) {
+        for (int gyi = 0; gyi < gh; ++gyi) {
+            for (int k = 0; k < ntheta; ++k) {
+                size_t o = (size_t)k * n;
+                out[((size_t)k * gh + gyi) * gw + gxi] =
+                    or_score_pose(field, w, h, ox + o, oy + o, px + o, py + o, n, gxi * step_x, gyi * step_y,
+                                  nbhd, polarity);
+            }
+        }
+    }
+    free(ox);
+    free(oy);
+    free(px);
+    free(py);
+}
+
+/* Total order used for every selection: higher score first, then the
+ * smaller key (angle index, y, x) -- the key is the row-major index.       */
+static int or_beats(double sa, long ka, double sb, long kb)
+{
+    return sa > sb || (sa == sb && ka < kb);
+}
+
+/* Candidate extraction at the top level (Sec. II keeps the maximum-score
+ * pose; several instances need several): poses with M >= min_score that
+ * beat each of their up to 26 neighbours in (theta, y, x), theta circular,
+ * translations clipped at the grid border; the K best by the order above.
+ * Returns the number written (<= K).                                       */
+static double *or_sort_scores;
+static long *or_sort_keys;
+static int or_cmp_idx(const void *a, const void *b)
+{
+    int i = *(const int *)a, j = *(const int *)b;
+    if (or_beats(or_sort_scores[i], or_sort_keys[i], or_sort_scores[j], or_sort_keys[j]))
+        return -1;
+    if (or_beats(or_sort_scores[j], or_sort_keys[j], or_sort_scores[i], or_sort_keys[i]))
+        return 1;
+    return 0;
+}
+
+int or_candidates(const double *map, int nth, int gh, int gw, double min_score, int K,
+                  int32_t *ck, int32_t *cy, int32_t *cx, double *cs)
+{
+    size_t total = (size_t)nth * gh * gw;
+    int cap = 1024, cnt = 0;
+    double *sc = (double *)malloc(sizeof(double) * cap);
+    long *key = (long *)malloc(sizeof(long) * cap);
+    for (int k = 0; k < nth; ++k) {
+        for (int y = 0; y < gh; ++y) {
+            for (int x = 0; x < gw; ++x) {
+                long kp = ((long)k * gh + y) * gw + x;
+                double s = map[kp];
+                if (!(s >= min_score))
+                    continue;
+                int ok = 1;
+                for (int dk = -1; dk <= 1 && ok; ++dk) {
+                    if (dk != 0 && nth == 1)
+                        continue;
+                    int k2 = ((k + dk) % nth + nth) % nth;
+                    for (int dy = -1; dy <= 1 && ok; ++dy) {
+                        for (int dx = -1; dx <= 1 && ok; ++dx) {
+                            if (dk == 0 && dy == 0 && dx == 0)
+                                continue;
+                            int y2 = y + dy, x2 = x + dx;
+                            if (y2 < 0 || x2 < 0 || y2 >= gh || x2 >= gw)
+                                continue;
+                            long kq = ((long)k2 * gh + y2) * gw + x2;
+                            if (kq == kp)
+                                continue;
+                            if (!or_beats(s, kp, map[kq], kq))
+                                ok = 0;
+                        }
+                    }
+                }
+                if (!ok)
+                    continue;
+                if (cnt == cap) {
+                    cap *= 2;
+                    sc = (double *)realloc(sc, sizeof(double) * cap);
+                    key = (long *)realloc(key, sizeof(long) * cap);
+                }
+                sc[cnt] = s;
+                key[cnt] = kp;
+                ++cnt;
+            }
+        }
+    }
+    (void)total;
+    int *idx = (int *)malloc(sizeof(int) * (size_t)(cnt > 0 ? cnt : 1));
+    for (int i = 0; i < cnt; ++i)
+        idx[i] = i;
+    or_sort_scores = sc;
+    or_sort_keys = key;
+    qsort(idx, (size_t)cnt, sizeof(int), or_cmp_idx);
+    int nout = cnt < K ? cnt : K;
+    for (int i = 0; i < nout; ++i) {
+        long kp = key[idx[i]];
+        cx[i] = (int32_t)(kp % gw);
+        cy[i] = (int32_t)((kp / gw) % gh);
+        ck[i] = (int32_t)(kp / ((long)gw * gh));
+        cs[i] = sc[idx[i]];
+    }
+    free(idx);
+    free(sc);
+    free(key);
+    return nout;
+}
+
+/* Coarse-to-fine shift (the paper only says scoring starts at the top
+ * level).  A level-(l+1) pixel X covers level-l pixels 2X and 2X+1, so its
+ * centre is 2X + 1/2; a level-(l+1) template point t' has its centre at the
+ * level-l template point 2t' + d with d = 2 c_{l+1} + 1/2 - c_l per axis
+ * (c = reference point).  A level-(l+1) pose u' therefore maps to the level-l
+ * pose 2u' + (1/2, 1/2) - R(theta) d, whose nearest pixel is 2u' + shift.
+ * theta is the parent's angle, (k_parent * dtheta_parent_deg) * pi / 180.  */
+void or_child_shift(int k_parent, double dtheta_parent_deg, double dx, double dy, int32_t *sx, int32_t *sy)
+{
+    double th = ((double)k_parent * dtheta_parent_deg) * OR_PI / 180.0;
+    double c = cos(th), s = sin(th);
+    *sx = (int32_t)floor(0.5 - (c * dx - s * dy) + 0.5);
+    *sy = (int32_t)floor(0.5 - (s * dx + c * dy) + 0.5);
+}
+
+/* One refinement level (neighbouring-search size 3 in x, y and theta): for
+ * each parent pose (x', y', k') at level l+1, evaluate the 27 level-l poses
+ * x in cx + {-1,0,1}, y in cy + {-1,0,1}, k in 2k' + {-1,0,1} (mod ntheta),
+ * with (cx, cy) = 2 (x', y') + shift(k'), skipping poses outside the image,
+ * and keep the best by the total order above.  Writes the refined pose and
+ * score; a parent whose best score is below min_score (or that has no pose
+ * inside the image) gets score -inf.                                       */
+void or_refine_level(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                     const int32_t *gx, const int32_t *gy, int n, int ntheta, double dtheta_deg,
+                     double dx, double dy, int nbhd, int polarity, double min_score, int ncand,
+                     const int32_t *in_x, const int32_t *in_y, const int32_t *in_k,
+                     int32_t *out_x, int32_t *out_y, int32_t *out_k, double *out_s)
+{
+    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *px = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *py = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int c = 0; c < ncand; ++c) {
+        int32_t sx, sy;
+        or_child_shift(in_k[c], 2.0 * dtheta_deg, dx, dy, &sx, &sy);
+        int cxp = 2 * in_x[c] + sx, cyp = 2 * in_y[c] + sy;
+        double best = -INFINITY;
+        long bkey = 0;
+        int bx = 0, by = 0, bk = 0;
+        for (int dk = -1; dk <= 1; ++dk) {
+            int k = ((2 * in_k[c] + dk) % ntheta + ntheta) % ntheta;
+            or_rotate_points(tx, ty, gx, gy, n, k, dtheta_deg, ox, oy, px, py);
+            for (int ddy = -1; ddy <= 1; ++ddy) {
+                for (int ddx = -1; ddx <= 1; ++ddx) {
+                    int x = cxp + ddx, y = cyp + ddy;
+                    if (x < 0 || y < 0 || x >= w || y >= h)
+                        continue;
+                    double s = or_score_pose(field, w, h, ox, oy, px, py, n, x, y, nbhd, polarity);
+                    long key = ((long)k * h + y) * w + x;
+                    if (best == -INFINITY || or_beats(s, key, best, bkey)) {
+                        best = s;
+                        bkey = key;
+                        bx = x;
+                        by = y;
+                        bk = k;
+                    }
+                }
+            }
+        }
+        out_x[c] = bx;
+        out_y[c] = by;
+        out_k[c] = bk;
+        out_s[c] = (best >= min_score) ? best : -INFINITY;
+    }
+    free(ox);
+    free(oy);
+    free(px);
+    free(py);
+}
+
+/* Final non-maximum suppression over level-0 detections: visit by the total
+ * order (score, then key (k, y, x) with the level-0 image width w and height
+ * h); keep a detection unless a kept one lies closer than half the smaller
+ * template side, compared exactly as 4 (dx^2 + dy^2) < min_side^2.  Entries
+ * with score -inf are skipped.  Writes indices of kept entries in order and
+ * returns how many (at most max_out).                                      */
+int or_nms(int n, const int32_t *x, const int32_t *y, const int32_t *k, const double *s, int w, int h,
+           int min_side, int max_out, int32_t *keep)
+{
+    int *idx = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    long *key = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    double *sc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        idx[i] = i;
+        key[i] = ((long)k[i] * h + y[i]) * w + x[i];
+        sc[i] = s[i];
+    }
+    or_sort_scores = sc;
+    or_sort_keys = key;
+    qsort(idx, (size_t)n, sizeof(int), or_cmp_idx);
+    int nk = 0;
+    for (int a = 0; a < n && nk < max_out; ++a) {
+        int i = idx[a];
+        if (s[i] == -INFINITY)
+            continue;
+        int ok = 1;
+        for (int b = 0; b < nk; ++b) {
+            long ddx = x[i] - x[keep[b]], ddy = y[i] - y[keep[b]];
+            if (4 * (ddx * ddx + ddy * ddy) < (long)min_side * min_side) {
+                ok = 0;
+                break;
+            }
+        }
+        if (ok)
+            keep[nk++] = i;
+    }
+    free(idx);
+    free(key);
+    free(sc);
+    return nk;
+}
