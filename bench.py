@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the shape-based alignment detector on GB300.
+
+Workload: the paper-shaped single detection at 1280x1024 -- a 200x200
+texture-less part (about 1500 edge points at level 0), 1-4 instances per
+scene with occlusion, an illumination ramp, clutter and noise; 4 pyramid
+levels, 1 degree angle step at level 0 (8 degrees, 45 angles at the top),
+neighbourhood 3, min_score 0.6.  One step = detection of one batch of
+`--batch` such scenes resident in HBM (all pipeline stages: pyramid,
+gradients, top-level exhaustive search, candidates, refinement to level 0,
+NMS, result readback).
+
+Metric: pose-point evals/s = (top-level poses x model points at the top
+level) per second, summed over the batch (refinement work is not counted).
+
+Arms: the default arm runs the CUDA library; --impl reference times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+LEVELS, STEP, LOW, HIGH, MIN_SCORE = 4, 1.0, 30, 60, 0.6
+W, H, SIDE = 1280, 1024, 200
+METRIC = "pose-point evals/s (1280x1024 detection, top-level exhaustive)"
+UNIT = "pose-point/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _scenes(n, seed0, spec=None):
+    tm, imgs, truth = None, [], []
+    for i in range(n):
+        t, sc, gt, spec = synth.config2_scene(seed=seed0 + i, W=W, H=H, side=SIDE, spec=spec)
+        tm = t if tm is None else tm
+        imgs.append(sc)
+        truth.append(gt)
+    return tm, imgs, truth, spec
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def top_pose_points(model, batch):
+    top = LEVELS - 1
+    tw, th = W >> top, H >> top
+    return batch * model.num_angles(top) * tw * th * model.num_points(top)
+
+
+# ---------------------------------------------------------------------------
+# roofline of the exhaustive scoring kernel
+# ---------------------------------------------------------------------------
+# Algorithmic work per pose-point with full reuse of the per-pixel dot
+# products across the 3x3 window (every pixel's dot with a point's
+# direction is computed once and shared by the 9 poses whose window holds
+# it): 1 dot (FMUL + FFMA), the separable 3x3 maximum (2 + 2 two-input max,
+# amortised) and 1 accumulate: 7 lane-instructions, of which 4 on the ALU
+# pipe (64 lanes/clk/SM) and 3 on the FMA pipe (128 lanes/clk/SM).  The ALU
+# pipe binds: 16 pose-points/clk/SM.
+OPS_PER_PP = 7
+PP_PER_CLK_SM = 16.0
+
+
+def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
+    achieved = pp_per_launch * OPS_PER_PP / (ms_per_launch * 1e-3) / 1e12
+    peak = PP_PER_CLK_SM * OPS_PER_PP * sm_count * sm_mhz_peak * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TOP/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": "score_map (exhaustive top level)"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_sample(budget_s=20.0, seed=9000):
+    import oracle
+    tm, imgs, _, _ = _scenes(1, seed)
+    om = oracle.create_model(tm, LOW, HIGH, LEVELS, STEP)
+    top = LEVELS - 1
+    pp_one = om.ntheta(top) * (W >> top) * (H >> top) * len(om.points[top][0])
+    params = oracle.DetectParams(min_score=MIN_SCORE, nbhd=3)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.detect(om, imgs[0], params)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s * 0.5 or n >= 8:
+            break
+    return pp_one * n / el, el, n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    tm, imgs, _, _ = _scenes(1, 9000)
+    om = oracle.create_model(tm, LOW, HIGH, LEVELS, STEP)
+    top = LEVELS - 1
+    nth = om.ntheta(top)
+    tw, th = W >> top, H >> top
+    n_top = len(om.points[top][0])
+    field = oracle.search_fields(imgs[0], LEVELS, LOW)[top]
+    # A step scores a slice of m top-level angles over every translation (the
+    # oracle's exhaustive search is >95 % of its detection time); m is sized
+    # so warm-up + timed steps take about two minutes.
+    t0 = time.perf_counter()
+    oracle.score_map_range(field, om.points[top], 0, 1, om.dtheta(top), nbhd=3)
+    t_angle = time.perf_counter() - t0
+    m = int(max(1, min(nth, 120.0 / max(1e-6, (args.steps + args.warmup) * t_angle))))
+    for i in range(args.warmup):
+        oracle.score_map_range(field, om.points[top], (i * m) % (nth - m + 1), m, om.dtheta(top), nbhd=3)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.score_map_range(field, om.points[top], (i * m) % (nth - m + 1), m, om.dtheta(top), nbhd=3)
+    el = time.perf_counter() - t0
+    val = m * tw * th * n_top * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "config2: 1280x1024 scene, 200x200 part, 4 levels, dtheta 1 deg, nbhd 3, "
+                               "min_score 0.6", "batch": 1,
+                   "sample": f"top-level exhaustive scoring of {m} of {nth} angles per step"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {m} top-level angles x {tw}x{th} translations x "
+                                   f"{n_top} points, FP64 oracle, single thread"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    import paper_2112_05576_gb300 as sam
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sam.lib()
+    B = args.batch
+    pools = max(2, args.pools)
+    tm, imgs, truth, spec = _scenes(B, 3000 + 7919 * rank)
+    # further batches: circular shifts of the same scenes (distinct buffers,
+    # so no batch is still in L2 when it is scored again)
+    rng = np.random.default_rng(11 + rank)
+    for _ in range(pools - 1):
+        for i in range(B):
+            imgs.append(np.roll(imgs[i], (int(rng.integers(0, H)), int(rng.integers(0, W))), axis=(0, 1)))
+    model = sam.Model(tm, LOW, HIGH, LEVELS, STEP)
+    params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
+                                       precision={"fp32": 0, "bf16": 1, "fp16": 2}[args.precision],
+                                       early_termination=1 if args.early else 0)
+    host = np.stack(imgs).reshape(pools, B, H, W)
+    batches = [torch.from_numpy(host[i]).to(dev) for i in range(pools)]
+    pinned = torch.from_numpy(host).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        return sam.detect_batch(model, batches[i % pools], params)
+
+    # ---- device-resident timed region ----
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    sam.profile_enable(True)
+    sam.profile_read()
+    launches0 = sam.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            res = step(i)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    launches = sam.kernel_launches() - launches0
+    prof = sam.profile_read()
+    sam.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pp_step = top_pose_points(model, B)
+    value = pp_step * args.steps * world / (ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    h2d = B * H * W
+    d2h = B * (params.max_detections * 32 + 4)
+    for i in range(2):
+        x = pinned[i % pools].to(dev, non_blocking=True)
+        sam.detect_batch(model, x, params)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        x = pinned[i % pools].to(dev, non_blocking=True)
+        sam.detect_batch(model, x, params)     # ends with the device-to-host read of the poses
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = pp_step * args.steps * world / (e2e_ms * 1e-3)
+
+    # ---- single-image latency (one detection, device-resident) ----
+    one = batches[0][0].contiguous()
+    for _ in range(3):
+        sam.detect(model, one, params)
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    n_single = 20
+    for _ in range(n_single):
+        sam.detect(model, one, params)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    single_ms = s0.elapsed_time(s1) / n_single
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    score_ms, score_calls = prof["score_map"]
+    rl = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
+                  float(peaks.get("sm_max_mhz", 2070.0)), traffic=args.traffic)
+    rl["peak_source"] = f"{peak_kind}: SMs x 16 pose-points/clk x 7 ops at sm_max_mhz"
+    clocks = clk.summary()
+    if clocks.get("sm_mhz"):
+        rl["frac_at_observed_clock"] = round(rl["frac"] * float(peaks.get("sm_max_mhz", 2070.0)) / clocks["sm_mhz"], 4)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        v, el, n = oracle_sample(args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} full config-2 detection(s) of one 1280x1024 scene, FP64 oracle, "
+                         f"single thread, {el:.1f} s"}
+    stages = {k: {"ms_per_step": round(v[0] / max(1, args.steps), 4), "calls": v[1]} for k, v in prof.items()}
+    ndet = [len(r) for r in res]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision if args.precision != "fp32" else "f32",
+        "data": "synthetic",
+        "config": {"workload": "config2: 1280x1024 scenes, 200x200 part (~1500 edge pts), 4 levels, "
+                               "dtheta 1 deg (45 top angles), nbhd 3, min_score 0.6",
+                   "batch": B, "early_termination": bool(args.early), "precision": args.precision,
+                   "l2": f"inputs larger than L2: {pools} rotating batches, per-step working set "
+                         f"~{B * (H * W * 11 // 1048576)} MB"},
+        "ms_per_detection": ms / args.steps / B,
+        "single_image_ms": single_ms,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": int(launches),
+        "stages": stages,
+        "roofline": rl,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "detections_per_image": ndet[:8],
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--pools", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--early", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

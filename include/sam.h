@@ -1,0 +1,234 @@
+/*
+ * sam.h -- C ABI of the GB300 shape-based alignment detector.
+ *
+ * The detector follows T.-S. Le and C.-Y. Lin, "GPU-accelerated image
+ * alignment for object detection in industrial applications" (arXiv
+ * 2112.05576), Sec. II: edge extraction (x/y gradients and magnitudes,
+ * thresholded), an image pyramid, an exhaustive (x, y, theta) search at the
+ * pyramid's top level scored by the normalised gradient-direction similarity
+ * of Eq. (1) over model points projected by the rigid transform of Eq. (2),
+ * each point taking the best vote in its neighbouring-search window, and
+ * refinement down the pyramid.
+ *
+ * Conventions shared by every entry point
+ *   - Images are 8-bit grey, row-major, `stride` bytes between rows
+ *     (stride >= width).  x grows to the right, y downwards.
+ *   - "device" pointers are CUDA global-memory pointers of the current
+ *     device; "host" pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is ordered on that stream; calls that return
+ *     results to host memory synchronise it before returning.
+ *   - No entry point aborts: errors are returned as sam_status, and outputs
+ *     are left unspecified on error.  sam_status_str() names each code.
+ *   - Thresholds are in units of |g| / 4 where g is the 3x3 Sobel gradient,
+ *     so a step edge of height h has magnitude h.  A pixel is an edge iff
+ *     gx^2 + gy^2 >= 16 T^2 (exact integer compare).
+ *   - Angles: theta_k = k * dtheta_l, dtheta_l = angle_step_deg * 2^l at
+ *     pyramid level l, k = 0 .. 360 / dtheta_l - 1 (full circle).
+ *   - The template reference point is (floor(W_t/2), floor(H_t/2)) at every
+ *     level; a pose (x, y, theta) puts that point at pixel (x, y).
+ */
+#ifndef SAM_H
+#define SAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SAM_OK = 0,
+    SAM_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad parameter) */
+    SAM_ERR_NOMEM = 2,        /* host or device allocation failed */
+    SAM_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SAM_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    SAM_ERR_EMPTY_MODEL = 5,  /* a template level has no edge point */
+    SAM_ERR_CAPACITY = 6      /* a fixed-capacity device buffer would overflow */
+} sam_status;
+
+/* Field precisions of the normalised search gradients w_hat. */
+enum { SAM_FP32 = 0, SAM_BF16 = 1, SAM_FP16 = 2 };
+
+typedef struct sam_model sam_model;
+
+/* Model parameters (Sec. II inputs: edge thresholds, number of pyramid
+ * levels, rotation step).
+ *   low, high       hysteresis thresholds for the template; `low` is also the
+ *                   single threshold of the search image.  1 <= low <= high.
+ *   levels          pyramid levels, 1..8; every template level must keep at
+ *                   least one edge point.
+ *   angle_step_deg  rotation step at level 0; 360/angle_step_deg must be an
+ *                   integer divisible by 2^(levels-1).
+ *   polarity        0: Eq. (1) as printed (signed cosine);
+ *                   1: ignore local polarity (|cosine| per neighbour). */
+typedef struct {
+    int low, high;
+    int levels;
+    double angle_step_deg;
+    int polarity;
+} sam_model_params;
+
+/* Detection parameters (Sec. II inputs: step sizes, neighbouring-search size).
+ *   step_x, step_y     translation steps of the top-level exhaustive search
+ *                      (>= 1; refinement below the top always uses 1 px).
+ *   neighbourhood      neighbouring-search window side, 1 or 3.
+ *   min_score          poses below this score are discarded at every level.
+ *   max_detections     at most this many poses are returned.
+ *   top_k              top-level candidates refined down the pyramid (1..1024).
+ *   precision          SAM_FP32, SAM_BF16 or SAM_FP16 storage of the top-level
+ *                      w_hat field; refinement and final scores are FP32.
+ *   early_termination  1: stop scoring a top-level pose once the partial sum
+ *                      proves M < min_score (exact-safe bound, every
+ *                      remaining term is at most 1); such poses are written
+ *                      as -inf in score maps. */
+typedef struct {
+    int step_x, step_y;
+    int neighbourhood;
+    float min_score;
+    int max_detections;
+    int top_k;
+    int precision;
+    int early_termination;
+} sam_detect_params;
+
+/* One detection at level 0: reference point (x, y) in pixels, rotation in
+ * degrees, score M of Eq. (1) (FP32).  angle_index is k at level 0. */
+typedef struct {
+    float x, y, theta_deg, score;
+    int angle_index;
+    int level0_x, level0_y;
+    int reserved;
+} sam_pose;
+
+const char *sam_status_str(sam_status s);
+
+/* Library version and the CUDA architecture it was compiled for (e.g. 1030). */
+int sam_version(void);
+int sam_compiled_arch(void);
+
+/* Fill `p` with defaults: low 30, high 60, levels 3, angle_step 1.0, polarity 0. */
+void sam_default_model_params(sam_model_params *p);
+/* Fill `p` with defaults: steps 1, neighbourhood 3, min_score 0.7,
+ * max_detections 16, top_k 64, FP32, early termination on. */
+void sam_default_detect_params(sam_detect_params *p);
+
+/* ---------------------------------------------------------------------------
+ * Model (Sec. II: the model image's edge points at every pyramid level, and
+ * per level l and angle index k the Eq. (2) projection of every point:
+ * integer offset round(R(theta_k) t) and unit direction R(theta_k) g/|g|).
+ * Built on the host in FP64; device tables are uploaded on first use.
+ *   tmpl     host pointer, w x h bytes with row pitch `stride`.
+ *   out      receives the new model; free it with sam_free_model.
+ * Errors: SAM_ERR_ARG (bad sizes or params), SAM_ERR_EMPTY_MODEL,
+ *         SAM_ERR_NOMEM.
+ * ------------------------------------------------------------------------- */
+sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params *params,
+                            sam_model **out);
+void sam_free_model(sam_model *m);
+
+/* Model inspection (host only, no device work). */
+int sam_model_levels(const sam_model *m);
+int sam_model_num_points(const sam_model *m, int level);
+int sam_model_num_angles(const sam_model *m, int level);
+int sam_model_template_size(const sam_model *m, int level, int *w, int *h);
+/* Copy the Eq. (2) table of (level, k) to host arrays of num_points entries:
+ * integer offsets ox, oy and FP32 unit directions px, py. */
+sam_status sam_model_rotated_points(const sam_model *m, int level, int k, int32_t *ox, int32_t *oy, float *px,
+                                    float *py);
+/* Copy the model's level points (template coordinates t relative to the
+ * reference point and integer Sobel gradient), in the model's point order. */
+sam_status sam_model_points(const sam_model *m, int level, int32_t *tx, int32_t *ty, int32_t *gx, int32_t *gy);
+/* Coarse-to-fine child shift for a parent at level+1 with angle index k:
+ * the level-`level` search centre is 2 (x, y) + (sx, sy). */
+sam_status sam_model_child_shift(const sam_model *m, int level, int k_parent, int32_t *sx, int32_t *sy);
+
+/* ---------------------------------------------------------------------------
+ * Full detection (Sec. II): pyramid, gradients, top-level exhaustive search,
+ * candidates, refinement to level 0, non-maximum suppression.
+ *   img            w x h image, row pitch `stride`; a device pointer if
+ *                  img_on_device != 0, else a host pointer.
+ *   out            host array of `capacity` poses, best first.
+ *   n_out          host int, receives the number of poses written.
+ * The model keeps an internal device workspace that grows to the largest
+ * image seen: calls on one model must not overlap (serialise them on one
+ * stream or host thread).  Synchronises `stream` before returning.
+ * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride, int img_on_device,
+                      const sam_detect_params *params, void *stream, sam_pose *out, int capacity, int *n_out);
+
+/* Detection of `count` images of equal size stored back to back on the
+ * device (image i at img + i * image_bytes), all steps batched into one
+ * launch per stage.  Poses of image i go to out[i * capacity ...], their
+ * count to n_out[i] (host arrays).  Synchronises `stream`. */
+sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h,
+                            int stride, const sam_detect_params *params, void *stream, sam_pose *out,
+                            int capacity, int *n_out);
+
+/* ---------------------------------------------------------------------------
+ * Individual steps on caller-owned device buffers (stream-ordered, no
+ * synchronisation, no allocation).
+ * ------------------------------------------------------------------------- */
+
+/* Pyramid step (Sec. II, "image pyramid construction"): dst(x, y) =
+ * (src(2x,2y) + src(2x+1,2y) + src(2x,2y+1) + src(2x+1,2y+1) + 2) >> 2 for
+ * x < w/2, y < h/2.  src, dst device; dst pitch dst_stride >= w/2. */
+sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, uint8_t *dst, int dst_stride,
+                            void *stream);
+
+/* Edge extraction (Sec. II) of a device image: 3x3 Sobel gx, gy (zero on the
+ * 1-pixel border), edge iff gx^2+gy^2 >= 16 low^2, and the unit field
+ * w_hat = g/|g| on edges, (0,0) elsewhere.
+ *   field   device, w*h pixel pairs (wx, wy), dense row-major: float pairs
+ *           (8 B/px) for SAM_FP32, bf16 or fp16 pairs (4 B/px) otherwise.
+ *   gx, gy  optional device int16 outputs (w*h, dense), NULL to skip. */
+sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, void *field,
+                        int16_t *gx, int16_t *gy, void *stream);
+
+/* Exhaustive score map of one model level (Eq. (1) with the neighbouring
+ * search, Eq. (2) projection, Sec. II three nested loops):
+ *   map[(k * gh + gyi) * gw + gxi] = M(gxi * step_x, gyi * step_y, theta_k)
+ * for k < num_angles(level), gh = ceil(h/step_y), gw = ceil(w/step_x).
+ *   field   device w_hat field of the search image at that level (layout and
+ *           precision as produced by sam_gradient).
+ *   map     device float array of num_angles * gh * gw.
+ * With early_termination, poses proved below min_score are written -inf. */
+sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int step_x,
+                         int step_y, int neighbourhood, float min_score, int early_termination, float *map,
+                         void *stream);
+
+/* Candidate extraction from a score map [nth][gh][gw]: poses with score >=
+ * min_score that beat all 26 neighbours in (theta circular, y, x) under the
+ * order (higher score, then smaller (k, y, x)), the best K of them.
+ *   out_kyx  device int32 array of 3*K: (k, y, x) per candidate, best first.
+ *   out_s    device float array of K.
+ *   count    device int, receives min(K, number of local maxima).
+ *   scratch  device buffer of sam_candidates_scratch_bytes(nth, gh, gw). */
+size_t sam_candidates_scratch_bytes(int nth, int gh, int gw);
+sam_status sam_candidates(const float *map, int nth, int gh, int gw, float min_score, int K, int32_t *out_kyx,
+                          float *out_s, int *count, void *scratch, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Stage timing (tracing).  When enabled, sam_detect / sam_detect_batch record
+ * CUDA events on the caller's stream before and after the launches of each
+ * stage and, at the synchronisation that ends the call, add the elapsed
+ * device time to per-stage totals.  Stages: 0 pyramid, 1 gradient,
+ * 2 exhaustive score map, 3 candidates, 4 refinement, 5 NMS.
+ * sam_profile_read copies up to n totals (milliseconds) and call counts and
+ * resets them.  Process-wide; not thread-safe.
+ * ------------------------------------------------------------------------- */
+#define SAM_NUM_STAGES 6
+void sam_profile_enable(int on);
+int sam_profile_read(float *ms, int *calls, int n);
+
+/* Number of CUDA kernels this library has launched in this process
+ * (all entry points, all devices).  Monotonic; for accounting only. */
+long long sam_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAM_H */

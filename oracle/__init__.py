@@ -23,6 +23,7 @@ from .oracle import (  # noqa: F401
     rotate_points,
     score_pose,
     score_map,
+    score_map_range,
     candidates,
     child_shift,
     refine_level,

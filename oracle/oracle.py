@@ -59,6 +59,8 @@ def _L():
         lib.or_score_pose.restype = _c_dbl
         lib.or_score_map.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
                                      _c_dbl, _c_int, _c_int, _c_int, _c_int, _f64p]
+        lib.or_score_map_range.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
+                                           _c_int, _c_dbl, _c_int, _c_int, _c_int, _c_int, _f64p]
         lib.or_candidates.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_dbl, _c_int, _i32p, _i32p, _i32p, _f64p]
         lib.or_candidates.restype = _c_int
         lib.or_child_shift.argtypes = [_c_int, _c_dbl, _c_dbl, _c_dbl, ctypes.POINTER(ctypes.c_int32),
@@ -214,6 +216,18 @@ def score_map(field, pts, ntheta, dtheta_deg, step_x=1, step_y=1, nbhd=3, polari
     out = np.empty((ntheta, gh, gw), dtype=np.float64)
     _L().or_score_map(field, w, h, tx, ty, gx, gy, len(tx), int(ntheta), float(dtheta_deg), int(step_x),
                       int(step_y), int(nbhd), int(polarity), out)
+    return out
+
+
+def score_map_range(field, pts, k_begin, k_count, dtheta_deg, step_x=1, step_y=1, nbhd=3, polarity=0):
+    """Slice [k_begin, k_begin + k_count) of the exhaustive map."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    gw, gh = (w + step_x - 1) // step_x, (h + step_y - 1) // step_y
+    out = np.empty((k_count, gh, gw), dtype=np.float64)
+    _L().or_score_map_range(field, w, h, tx, ty, gx, gy, len(tx), int(k_begin), int(k_count), float(dtheta_deg),
+                            int(step_x), int(step_y), int(nbhd), int(polarity), out)
     return out
 
 

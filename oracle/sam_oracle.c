@@ -236,24 +236,26 @@ double or_score_pose(const double *field, int w, int h, const int32_t *ox, const
  * Poses are u = (gxi * step_x, gyi * step_y) for the grid gxi < ceil(w /
  * step_x), gyi < ceil(h / step_y), and theta_k for k < ntheta.  The map is
  * written out[(k * gh + gyi) * gw + gxi].  Eq. (2) depends on theta only, so
- * each angle's rotated points are computed once up front.                  */
-void or_score_map(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
-                  const int32_t *gx, const int32_t *gy, int n, int ntheta, double dtheta_deg,
-                  int step_x, int step_y, int nbhd, int polarity, double *out)
+ * each angle's rotated points are computed once up front.  The _range form
+ * scores the angles k_begin .. k_begin + k_count - 1 only (a slice of the
+ * same map, written from out[0]).                                          */
+void or_score_map_range(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                        const int32_t *gx, const int32_t *gy, int n, int k_begin, int k_count, double dtheta_deg,
+                        int step_x, int step_y, int nbhd, int polarity, double *out)
 {
     int gw = (w + step_x - 1) / step_x, gh = (h + step_y - 1) / step_y;
-    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * ntheta);
-    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * ntheta);
-    double *px = (double *)malloc(sizeof(double) * (size_t)n * ntheta);
-    double *py = (double *)malloc(sizeof(double) * (size_t)n * ntheta);
-    for (int k = 0; k < ntheta; ++k)
-        or_rotate_points(tx, ty, gx, gy, n, k, dtheta_deg, ox + (size_t)k * n, oy + (size_t)k * n,
-                         px + (size_t)k * n, py + (size_t)k * n);
+    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * k_count);
+    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * k_count);
+    double *px = (double *)malloc(sizeof(double) * (size_t)n * k_count);
+    double *py = (double *)malloc(sizeof(double) * (size_t)n * k_count);
+    for (int j = 0; j < k_count; ++j)
+        or_rotate_points(tx, ty, gx, gy, n, k_begin + j, dtheta_deg, ox + (size_t)j * n, oy + (size_t)j * n,
+                         px + (size_t)j * n, py + (size_t)j * n);
     for (int gxi = 0; gxi < gw; ++gxi) {
         for (int gyi = 0; gyi < gh; ++gyi) {
-            for (int k = 0; k < ntheta; ++k) {
-                size_t o = (size_t)k * n;
-                out[((size_t)k * gh + gyi) * gw + gxi] =
+            for (int j = 0; j < k_count; ++j) {
+                size_t o = (size_t)j * n;
+                out[((size_t)j * gh + gyi) * gw + gxi] =
                     or_score_pose(field, w, h, ox + o, oy + o, px + o, py + o, n, gxi * step_x, gyi * step_y,
                                   nbhd, polarity);
             }
@@ -263,6 +265,14 @@ void or_score_map(const double *field, int w, int h, const int32_t *tx, const in
     free(oy);
     free(px);
     free(py);
+}
+
+/* The full map: all angles k = 0 .. ntheta-1. */
+void or_score_map(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                  const int32_t *gx, const int32_t *gy, int n, int ntheta, double dtheta_deg,
+                  int step_x, int step_y, int nbhd, int polarity, double *out)
+{
+    or_score_map_range(field, w, h, tx, ty, gx, gy, n, 0, ntheta, dtheta_deg, step_x, step_y, nbhd, polarity, out);
 }
 
 /* Total order used for every selection: higher score first, then the

@@ -1,0 +1,32 @@
+"""GB300 (sm_103a) shape-based alignment detector after Le & Lin, arXiv 2112.05576.
+
+The compute path is the CUDA library built from csrc/ (libsam.so, C ABI in
+include/sam.h); this package is its thin Python binding.
+"""
+
+from .sam import (  # noqa: F401
+    BF16,
+    FP16,
+    FP32,
+    SIGNATURES,
+    STAGES,
+    DetectParams,
+    Model,
+    ModelParams,
+    Pose,
+    SamError,
+    candidates,
+    candidates_scratch_bytes,
+    default_detect_params,
+    detect,
+    detect_batch,
+    gradient,
+    kernel_launches,
+    lib,
+    profile_enable,
+    profile_read,
+    pyramid_down,
+    score_map,
+    status_str,
+)
+from .build import build  # noqa: F401

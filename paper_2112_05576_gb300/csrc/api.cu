@@ -1,0 +1,577 @@
+// C ABI of the detector: model lifetime, the full detection pipeline and the
+// individual steps.  Every step of the pipeline runs in this library's CUDA
+// kernels; host code only validates arguments, plans device buffers and
+// orders launches on the caller's stream.
+
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+
+#include "sam_internal.h"
+
+#ifndef SAM_ARCH
+#define SAM_ARCH 0
+#endif
+
+namespace sam {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ---- stage timing ----
+struct Profiler {
+    bool on = false;
+    cudaEvent_t ev[SAM_NUM_STAGES][2] = {};
+    bool pending[SAM_NUM_STAGES] = {};
+    double ms[SAM_NUM_STAGES] = {};
+    int calls[SAM_NUM_STAGES] = {};
+};
+Profiler g_prof;
+
+void prof_begin(int stage, cudaStream_t st) {
+    if (!g_prof.on)
+        return;
+    if (!g_prof.ev[stage][0]) {
+        cudaEventCreate(&g_prof.ev[stage][0]);
+        cudaEventCreate(&g_prof.ev[stage][1]);
+    }
+    cudaEventRecord(g_prof.ev[stage][0], st);
+}
+
+void prof_end(int stage, cudaStream_t st) {
+    if (!g_prof.on)
+        return;
+    cudaEventRecord(g_prof.ev[stage][1], st);
+    g_prof.pending[stage] = true;
+}
+
+// after the stream has been synchronised
+void prof_collect() {
+    if (!g_prof.on)
+        return;
+    for (int s = 0; s < SAM_NUM_STAGES; ++s) {
+        if (!g_prof.pending[s])
+            continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g_prof.ev[s][0], g_prof.ev[s][1]) == cudaSuccess) {
+            g_prof.ms[s] += t;
+            g_prof.calls[s] += 1;
+        }
+        g_prof.pending[s] = false;
+    }
+}
+
+// Device buffers of one detection call (all images of a batch).
+struct Plan {
+    int L = 0, count = 0;
+    int w[kMaxLevels], h[kMaxLevels];
+    int pitch[kMaxLevels];           // level image row pitch (bytes)
+    size_t img_bytes[kMaxLevels];    // bytes per image per level (level 0: only if copied)
+    size_t off_img[kMaxLevels];
+    size_t off_field[kMaxLevels];    // FP32 fields
+    size_t field_px[kMaxLevels];
+    size_t off_half = 0;             // top-level bf16/fp16 field (precision != FP32)
+    int gw = 0, gh = 0, nth = 0;
+    size_t map_img = 0, off_map = 0;
+    size_t off_scratch = 0;
+    size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
+    size_t total = 0;
+};
+
+sam_status check_detect_params(const sam_model *m, const sam_detect_params *p) {
+    if (!p || p->step_x < 1 || p->step_y < 1 || (p->neighbourhood != 1 && p->neighbourhood != 3) ||
+        p->max_detections < 1 || p->max_detections > kMaxTopK || p->top_k < 1 || p->top_k > kMaxTopK ||
+        p->precision < SAM_FP32 || p->precision > SAM_FP16 || !(p->min_score >= -1.0f && p->min_score <= 1.0f))
+        return SAM_ERR_ARG;
+    (void)m;
+    return SAM_OK;
+}
+
+Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, const sam_detect_params &p) {
+    Plan P;
+    P.L = m->levels;
+    P.count = count;
+    size_t off = 0;
+    for (int l = 0; l < P.L; ++l) {
+        P.w[l] = l == 0 ? w : P.w[l - 1] / 2;
+        P.h[l] = l == 0 ? h : P.h[l - 1] / 2;
+        P.pitch[l] = (int)((P.w[l] + 15) & ~15);
+        P.img_bytes[l] = al((size_t)P.pitch[l] * P.h[l]);
+        // a multiple of 8 pixels keeps every image's field 16-byte aligned
+        P.field_px[l] = ((size_t)P.w[l] * P.h[l] + 7) & ~(size_t)7;
+    }
+    for (int l = 0; l < P.L; ++l) {
+        P.off_img[l] = off;
+        if (l > 0 || copy_level0)
+            off += al(P.img_bytes[l] * count);
+    }
+    for (int l = 0; l < P.L; ++l) {
+        P.off_field[l] = off;
+        off += al(P.field_px[l] * 8 * count);
+    }
+    const int top = P.L - 1;
+    if (p.precision != SAM_FP32) {
+        P.off_half = off;
+        off += al(P.field_px[top] * 4 * count);
+    }
+    P.nth = m->lv[top].ntheta;
+    P.gw = (P.w[top] + p.step_x - 1) / p.step_x;
+    P.gh = (P.h[top] + p.step_y - 1) / p.step_y;
+    P.map_img = (size_t)P.nth * P.gw * P.gh;
+    P.off_map = off;
+    off += al(P.map_img * 4 * count);
+    P.off_scratch = off;
+    off += al(candidates_scratch_bytes_batch(P.nth, P.gh, P.gw, count));
+    const int K = p.top_k;
+    P.off_kyx = off;
+    off += al((size_t)3 * K * 4 * count);
+    P.off_cs = off;
+    off += al((size_t)K * 4 * count);
+    P.off_ccount = off;
+    off += al((size_t)4 * count);
+    P.off_refined = off;
+    off += al((size_t)K * 16 * count);
+    P.off_out = off;
+    off += al((size_t)p.max_detections * sizeof(sam_pose) * count);
+    P.off_nout = off;
+    off += al((size_t)4 * count);
+    P.total = off;
+    return P;
+}
+
+sam_status ensure_workspace(sam_model *m, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (m->ws.base && m->ws.bytes >= bytes && m->ws.device == dev)
+        return SAM_OK;
+    if (m->ws.base) {
+        cudaFree(m->ws.base);
+        m->ws.base = nullptr;
+        m->ws.bytes = 0;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SAM_ERR_NOMEM;
+    }
+    m->ws.base = p;
+    m->ws.bytes = bytes;
+    m->ws.device = dev;
+    return SAM_OK;
+}
+
+#define SAM_CU(x)                          \
+    do {                                   \
+        if ((x) != cudaSuccess)            \
+            return SAM_ERR_CUDA;           \
+    } while (0)
+
+// Launch the whole pipeline for `count` images whose level-0 copies start at
+// img0 (row pitch pitch0, image i at img0 + i * img0_bytes).
+sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
+                        const sam_detect_params &p, cudaStream_t st) {
+    char *ws = (char *)m->ws.base;
+    const int count = P.count, top = P.L - 1;
+    const uint8_t *lvl_img[kMaxLevels];
+    int lvl_pitch[kMaxLevels];
+    size_t lvl_bytes[kMaxLevels];
+    lvl_img[0] = img0;
+    lvl_pitch[0] = pitch0;
+    lvl_bytes[0] = img0_bytes;
+    // (b) pyramid
+    prof_begin(0, st);
+    for (int l = 1; l < P.L; ++l) {
+        uint8_t *dst = (uint8_t *)(ws + P.off_img[l]);
+        SAM_CU(launch_pyramid_down(lvl_img[l - 1], P.w[l - 1], P.h[l - 1], lvl_pitch[l - 1], lvl_bytes[l - 1], dst,
+                                   P.pitch[l], P.img_bytes[l], count, st));
+        lvl_img[l] = dst;
+        lvl_pitch[l] = P.pitch[l];
+        lvl_bytes[l] = P.img_bytes[l];
+    }
+    prof_end(0, st);
+    // (a) gradients: FP32 fields on every level, plus the top level's
+    // low-precision copy for the exhaustive search
+    prof_begin(1, st);
+    for (int l = 0; l < P.L; ++l)
+        SAM_CU(launch_gradient(lvl_img[l], P.w[l], P.h[l], lvl_pitch[l], lvl_bytes[l], m->p.low, SAM_FP32,
+                               ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
+    const void *top_field = ws + P.off_field[top];
+    if (p.precision != SAM_FP32) {
+        SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low,
+                               p.precision, ws + P.off_half, P.field_px[top], nullptr, nullptr, count, st));
+        top_field = ws + P.off_half;
+    }
+    prof_end(1, st);
+    // (c) exhaustive top-level score map
+    ScoreArgs sa;
+    sa.field = top_field;
+    sa.field_img_px = P.field_px[top];
+    sa.w = P.w[top];
+    sa.h = P.h[top];
+    sa.precision = p.precision;
+    sa.step_x = p.step_x;
+    sa.step_y = p.step_y;
+    sa.nbhd = p.neighbourhood;
+    sa.polarity = m->p.polarity;
+    sa.min_score = p.min_score;
+    sa.early = p.early_termination;
+    sa.map = (float *)(ws + P.off_map);
+    sa.map_img = P.map_img;
+    sa.count = count;
+    prof_begin(2, st);
+    SAM_CU(launch_score_map(m->dev[top], sa, st));
+    prof_end(2, st);
+    // (d) candidates, refinement, NMS
+    const int K = p.top_k;
+    int32_t *kyx = (int32_t *)(ws + P.off_kyx);
+    float *cs = (float *)(ws + P.off_cs);
+    int *ccount = (int *)(ws + P.off_ccount);
+    prof_begin(3, st);
+    SAM_CU(launch_candidates(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
+                             ws + P.off_scratch, 0, count, st));
+    prof_end(3, st);
+    RefineArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    for (int l = 0; l < P.L; ++l) {
+        ra.field[l] = (const float2 *)(ws + P.off_field[l]);
+        ra.field_img_px[l] = P.field_px[l];
+        ra.w[l] = P.w[l];
+        ra.h[l] = P.h[l];
+    }
+    ra.top = top;
+    ra.step_x = p.step_x;
+    ra.step_y = p.step_y;
+    ra.nbhd = p.neighbourhood;
+    ra.polarity = m->p.polarity;
+    ra.min_score = p.min_score;
+    ra.K = K;
+    ra.cand_kyx = kyx;
+    ra.cand_s = cs;
+    ra.cand_count = ccount;
+    ra.refined = (float4 *)(ws + P.off_refined);
+    ra.count = count;
+    prof_begin(4, st);
+    SAM_CU(launch_refine(m, ra, st));
+    prof_end(4, st);
+    NmsArgs na;
+    na.refined = ra.refined;
+    na.cand_count = ccount;
+    na.K = K;
+    na.w0 = P.w[0];
+    na.h0 = P.h[0];
+    na.min_side = std::min(m->lv[0].tw, m->lv[0].th);
+    na.max_out = p.max_detections;
+    na.angle_step = m->p.angle_step_deg;
+    na.out = (sam_pose *)(ws + P.off_out);
+    na.n_out = (int *)(ws + P.off_nout);
+    na.count = count;
+    prof_begin(5, st);
+    SAM_CU(launch_nms(na, st));
+    prof_end(5, st);
+    return SAM_OK;
+}
+
+sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st, sam_pose *out,
+                        int capacity, int *n_out) {
+    char *ws = (char *)m->ws.base;
+    const int count = P.count;
+    std::vector<sam_pose> poses((size_t)p.max_detections * count);
+    std::vector<int> nout(count);
+    SAM_CU(cudaMemcpyAsync(poses.data(), ws + P.off_out, poses.size() * sizeof(sam_pose), cudaMemcpyDeviceToHost,
+                           st));
+    SAM_CU(cudaMemcpyAsync(nout.data(), ws + P.off_nout, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SAM_CU(cudaStreamSynchronize(st));
+    prof_collect();
+    for (int i = 0; i < count; ++i) {
+        const int n = std::min(nout[i], capacity);
+        memcpy(out + (size_t)i * capacity, poses.data() + (size_t)i * p.max_detections, (size_t)n * sizeof(sam_pose));
+        n_out[i] = n;
+    }
+    return SAM_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_score_map(const LevelDev &L, const ScoreArgs &a, cudaStream_t st) {
+    return launch_score_map_generic(L, a, st);
+}
+
+}  // namespace sam
+
+using namespace sam;
+
+extern "C" {
+
+const char *sam_status_str(sam_status s) {
+    switch (s) {
+    case SAM_OK:
+        return "ok";
+    case SAM_ERR_ARG:
+        return "invalid argument";
+    case SAM_ERR_NOMEM:
+        return "out of memory";
+    case SAM_ERR_CUDA:
+        return "CUDA error";
+    case SAM_ERR_TIMEOUT:
+        return "device wait timed out";
+    case SAM_ERR_EMPTY_MODEL:
+        return "template level without edge points";
+    case SAM_ERR_CAPACITY:
+        return "device buffer capacity exceeded";
+    }
+    return "unknown status";
+}
+
+int sam_version(void) { return 100; }
+int sam_compiled_arch(void) { return SAM_ARCH; }
+
+void sam_default_model_params(sam_model_params *p) {
+    if (!p)
+        return;
+    p->low = 30;
+    p->high = 60;
+    p->levels = 3;
+    p->angle_step_deg = 1.0;
+    p->polarity = 0;
+}
+
+void sam_default_detect_params(sam_detect_params *p) {
+    if (!p)
+        return;
+    p->step_x = p->step_y = 1;
+    p->neighbourhood = 3;
+    p->min_score = 0.7f;
+    p->max_detections = 16;
+    p->top_k = 64;
+    p->precision = SAM_FP32;
+    p->early_termination = 1;
+}
+
+sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params *params,
+                            sam_model **out) {
+    if (!out || !params)
+        return SAM_ERR_ARG;
+    *out = nullptr;
+    if (params->low > 1024 || params->high > 1024)
+        return SAM_ERR_ARG;
+    sam_model *m = new (std::nothrow) sam_model();
+    if (!m)
+        return SAM_ERR_NOMEM;
+    const sam_status s = build_model(tmpl, w, h, stride, *params, m);
+    if (s != SAM_OK) {
+        delete m;
+        return s;
+    }
+    *out = m;
+    return SAM_OK;
+}
+
+void sam_free_model(sam_model *m) {
+    if (!m)
+        return;
+    if (m->d_tables)
+        cudaFree(m->d_tables);
+    if (m->ws.base)
+        cudaFree(m->ws.base);
+    delete m;
+}
+
+int sam_model_levels(const sam_model *m) { return m ? m->levels : 0; }
+
+int sam_model_num_points(const sam_model *m, int level) {
+    return (m && level >= 0 && level < m->levels) ? m->lv[level].n : 0;
+}
+
+int sam_model_num_angles(const sam_model *m, int level) {
+    return (m && level >= 0 && level < m->levels) ? m->lv[level].ntheta : 0;
+}
+
+int sam_model_template_size(const sam_model *m, int level, int *w, int *h) {
+    if (!m || level < 0 || level >= m->levels)
+        return 0;
+    if (w)
+        *w = m->lv[level].tw;
+    if (h)
+        *h = m->lv[level].th;
+    return 1;
+}
+
+sam_status sam_model_rotated_points(const sam_model *m, int level, int k, int32_t *ox, int32_t *oy, float *px,
+                                    float *py) {
+    if (!m || level < 0 || level >= m->levels || k < 0 || k >= m->lv[level].ntheta || !ox || !oy || !px || !py)
+        return SAM_ERR_ARG;
+    const LevelHost &L = m->lv[level];
+    const RotPt *r = L.rot.data() + (size_t)k * L.n;
+    for (int i = 0; i < L.n; ++i) {
+        ox[i] = r[i].ox;
+        oy[i] = r[i].oy;
+        px[i] = r[i].px;
+        py[i] = r[i].py;
+    }
+    return SAM_OK;
+}
+
+sam_status sam_model_points(const sam_model *m, int level, int32_t *tx, int32_t *ty, int32_t *gx, int32_t *gy) {
+    if (!m || level < 0 || level >= m->levels || !tx || !ty || !gx || !gy)
+        return SAM_ERR_ARG;
+    const LevelHost &L = m->lv[level];
+    std::copy(L.tx.begin(), L.tx.end(), tx);
+    std::copy(L.ty.begin(), L.ty.end(), ty);
+    std::copy(L.gx.begin(), L.gx.end(), gx);
+    std::copy(L.gy.begin(), L.gy.end(), gy);
+    return SAM_OK;
+}
+
+sam_status sam_model_child_shift(const sam_model *m, int level, int k_parent, int32_t *sx, int32_t *sy) {
+    if (!m || level < 0 || level + 1 >= m->levels || k_parent < 0 || k_parent >= m->lv[level + 1].ntheta || !sx ||
+        !sy)
+        return SAM_ERR_ARG;
+    *sx = m->lv[level + 1].shift[k_parent].x;
+    *sy = m->lv[level + 1].shift[k_parent].y;
+    return SAM_OK;
+}
+
+sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride, int img_on_device,
+                      const sam_detect_params *params, void *stream, sam_pose *out, int capacity, int *n_out) {
+    if (!m || !img || !out || !n_out || capacity < 0 || stride < w)
+        return SAM_ERR_ARG;
+    *n_out = 0;
+    sam_status s = check_detect_params(m, params);
+    if (s != SAM_OK)
+        return s;
+    if ((w >> (m->levels - 1)) < 1 || (h >> (m->levels - 1)) < 1)
+        return SAM_ERR_ARG;
+    s = upload_model(m);
+    if (s != SAM_OK)
+        return s;
+    const Plan P = make_plan(m, w, h, 1, !img_on_device, *params);
+    s = ensure_workspace(m, P.total);
+    if (s != SAM_OK)
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t *img0 = img;
+    int pitch0 = stride;
+    size_t bytes0 = 0;
+    if (!img_on_device) {
+        uint8_t *dst = (uint8_t *)m->ws.base + P.off_img[0];
+        SAM_CU(cudaMemcpy2DAsync(dst, P.pitch[0], img, stride, w, h, cudaMemcpyHostToDevice, st));
+        img0 = dst;
+        pitch0 = P.pitch[0];
+    }
+    s = run_pipeline(m, P, img0, pitch0, bytes0, *params, st);
+    if (s != SAM_OK)
+        return s;
+    return read_results(m, P, *params, st, out, capacity, n_out);
+}
+
+sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h,
+                            int stride, const sam_detect_params *params, void *stream, sam_pose *out,
+                            int capacity, int *n_out) {
+    if (!m || !img || !out || !n_out || count < 1 || capacity < 0 || stride < w ||
+        image_bytes < (size_t)stride * (h - 1) + w)
+        return SAM_ERR_ARG;
+    sam_status s = check_detect_params(m, params);
+    if (s != SAM_OK)
+        return s;
+    if ((w >> (m->levels - 1)) < 1 || (h >> (m->levels - 1)) < 1)
+        return SAM_ERR_ARG;
+    s = upload_model(m);
+    if (s != SAM_OK)
+        return s;
+    const Plan P = make_plan(m, w, h, count, false, *params);
+    s = ensure_workspace(m, P.total);
+    if (s != SAM_OK)
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = run_pipeline(m, P, img, stride, image_bytes, *params, st);
+    if (s != SAM_OK)
+        return s;
+    return read_results(m, P, *params, st, out, capacity, n_out);
+}
+
+sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, uint8_t *dst, int dst_stride,
+                            void *stream) {
+    if (!src || !dst || w < 0 || h < 0 || src_stride < w || dst_stride < w / 2)
+        return SAM_ERR_ARG;
+    return launch_pyramid_down(src, w, h, src_stride, 0, dst, dst_stride, 0, 1, (cudaStream_t)stream) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
+}
+
+sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, void *field,
+                        int16_t *gx, int16_t *gy, void *stream) {
+    if (!img || !field || w < 1 || h < 1 || stride < w || low < 1 || low > 1024 || precision < SAM_FP32 ||
+        precision > SAM_FP16 || ((gx == nullptr) != (gy == nullptr)))
+        return SAM_ERR_ARG;
+    return launch_gradient(img, w, h, stride, 0, low, precision, field, (size_t)w * h, gx, gy, 1,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
+}
+
+sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int step_x,
+                         int step_y, int neighbourhood, float min_score, int early_termination, float *map,
+                         void *stream) {
+    if (!m || level < 0 || level >= m->levels || !field || !map || w < 1 || h < 1 || step_x < 1 || step_y < 1 ||
+        (neighbourhood != 1 && neighbourhood != 3) || precision < SAM_FP32 || precision > SAM_FP16)
+        return SAM_ERR_ARG;
+    sam_status s = upload_model(m);
+    if (s != SAM_OK)
+        return s;
+    ScoreArgs sa;
+    sa.field = field;
+    sa.field_img_px = (size_t)w * h;
+    sa.w = w;
+    sa.h = h;
+    sa.precision = precision;
+    sa.step_x = step_x;
+    sa.step_y = step_y;
+    sa.nbhd = neighbourhood;
+    sa.polarity = m->p.polarity;
+    sa.min_score = min_score;
+    sa.early = early_termination;
+    sa.map = map;
+    sa.map_img = 0;
+    sa.count = 1;
+    return launch_score_map(m->dev[level], sa, (cudaStream_t)stream) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+size_t sam_candidates_scratch_bytes(int nth, int gh, int gw) { return candidates_scratch_bytes(nth, gh, gw); }
+
+void sam_profile_enable(int on) { g_prof.on = on != 0; }
+
+long long sam_kernel_launches(void) { return g_launches.load(); }
+
+int sam_profile_read(float *ms, int *calls, int n) {
+    const int m = n < SAM_NUM_STAGES ? n : SAM_NUM_STAGES;
+    for (int s = 0; s < m; ++s) {
+        if (ms)
+            ms[s] = (float)g_prof.ms[s];
+        if (calls)
+            calls[s] = g_prof.calls[s];
+    }
+    for (int s = 0; s < SAM_NUM_STAGES; ++s) {
+        g_prof.ms[s] = 0.0;
+        g_prof.calls[s] = 0;
+    }
+    return m;
+}
+
+sam_status sam_candidates(const float *map, int nth, int gh, int gw, float min_score, int K, int32_t *out_kyx,
+                          float *out_s, int *count, void *scratch, void *stream) {
+    if (!map || !out_kyx || !out_s || !count || !scratch || nth < 1 || gh < 1 || gw < 1 || K < 1 || K > kMaxTopK)
+        return SAM_ERR_ARG;
+    return launch_candidates(map, 0, nth, gh, gw, min_score, K, out_kyx, out_s, count, scratch, 0, 1,
+                             (cudaStream_t)stream) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Kernels (a) and (b): edge extraction and the image pyramid (Sec. II).
+//
+// (b) pyramid step: each thread produces 16 output bytes from two 32-byte
+//     input row segments, 128-bit loads and stores on the aligned fast path;
+//     the 2x2 rounded mean is computed two bytes at a time in 16-bit lanes.
+// (a) gradient: one CTA stages an (TY+2) x (TX+2) byte tile of the image in
+//     shared memory (128-bit global loads on the aligned path), every thread
+//     computes 8 consecutive pixels of one row: integer Sobel gx, gy, the
+//     exact edge test gx^2+gy^2 >= 16 low^2 and the unit vector g/|g| (FP32,
+//     rsqrt), written as FP32 pairs (8 B/px) or bf16/fp16 pairs (4 B/px).
+// Both are HBM-bound: (b) moves 5 B per output pixel, (a) 1 B in + 8 (or 4)
+// B out per pixel.
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "sam_internal.h"
+
+namespace sam {
+namespace {
+
+// ---------------------------------------------------------------------------
+// (b) pyramid step
+// ---------------------------------------------------------------------------
+
+// Four input bytes of row 0 (p) and row 1 (q) -> two output bytes in byte
+// lanes 0 and 2 of the result: (p0+p1+q0+q1+2)>>2, (p2+p3+q2+q3+2)>>2.
+__device__ __forceinline__ uint32_t mean2x2_pair(uint32_t p, uint32_t q) {
+    const uint32_t m = 0x00FF00FFu;
+    const uint32_t s = (p & m) + ((p >> 8) & m) + (q & m) + ((q >> 8) & m) + 0x00020002u;
+    return (s >> 2) & m;
+}
+
+// 8 input bytes per row -> 4 output bytes.
+__device__ __forceinline__ uint32_t mean2x2_quad(uint32_t p0, uint32_t p1, uint32_t q0, uint32_t q1) {
+    const uint32_t lo = mean2x2_pair(p0, q0);   // outputs 0, 1 in bytes 0, 2
+    const uint32_t hi = mean2x2_pair(p1, q1);   // outputs 2, 3 in bytes 0, 2
+    return __byte_perm(lo, hi, 0x6420);
+}
+
+__global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int h, int ss, size_t src_img,
+                                    uint8_t *__restrict__ dst, int ds, size_t dst_img, int vec) {
+    const int img = blockIdx.z;
+    src += (size_t)img * src_img;
+    dst += (size_t)img * dst_img;
+    const int w2 = w >> 1, h2 = h >> 1;
+    const int y = blockIdx.y;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (y >= h2 || x0 >= w2)
+        return;
+    const uint8_t *r0 = src + (size_t)(2 * y) * ss;
+    const uint8_t *r1 = r0 + ss;
+    uint8_t *o = dst + (size_t)y * ds;
+    if (vec && x0 + 16 <= w2) {
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(r0 + 2 * x0));
+        const uint4 a1 = __ldg(reinterpret_cast<const uint4 *>(r0 + 2 * x0 + 16));
+        const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(r1 + 2 * x0));
+        const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(r1 + 2 * x0 + 16));
+        uint4 r;
+        r.x = mean2x2_quad(a0.x, a0.y, b0.x, b0.y);
+        r.y = mean2x2_quad(a0.z, a0.w, b0.z, b0.w);
+        r.z = mean2x2_quad(a1.x, a1.y, b1.x, b1.y);
+        r.w = mean2x2_quad(a1.z, a1.w, b1.z, b1.w);
+        *reinterpret_cast<uint4 *>(o + x0) = r;
+    } else {
+        const int xe = min(x0 + 16, w2);
+        for (int x = x0; x < xe; ++x)
+            o[x] = (uint8_t)((r0[2 * x] + r0[2 * x + 1] + r1[2 * x] + r1[2 * x + 1] + 2) >> 2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// (a) gradient / threshold / normalise
+// ---------------------------------------------------------------------------
+
+constexpr int GTX = 128;   // tile width (pixels)
+constexpr int GTY = 16;    // tile height
+constexpr int GPT = 8;     // pixels per thread (one row segment)
+constexpr int GTHREADS = GTX / GPT * GTY;   // 256
+constexpr int GSW = GTX + 32;               // smem row pitch: 16-byte halo on each side
+
+template <int PREC>
+struct FieldStore;
+
+template <>
+struct FieldStore<SAM_FP32> {
+    // 8 pixels -> 64 bytes
+    static __device__ __forceinline__ void store8(void *field, size_t idx, const float *wx, const float *wy) {
+        float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(field) + idx);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            p[j] = make_float4(wx[2 * j], wy[2 * j], wx[2 * j + 1], wy[2 * j + 1]);
+    }
+    static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
+        reinterpret_cast<float2 *>(field)[idx] = make_float2(wx, wy);
+    }
+};
+
+template <>
+struct FieldStore<SAM_BF16> {
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+    static __device__ __forceinline__ void store8(void *field, size_t idx, const float *wx, const float *wy) {
+        uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(field) + idx);
+        p[0] = make_uint4(pack(wx[0], wy[0]), pack(wx[1], wy[1]), pack(wx[2], wy[2]), pack(wx[3], wy[3]));
+        p[1] = make_uint4(pack(wx[4], wy[4]), pack(wx[5], wy[5]), pack(wx[6], wy[6]), pack(wx[7], wy[7]));
+    }
+    static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
+        reinterpret_cast<uint32_t *>(field)[idx] = pack(wx, wy);
+    }
+};
+
+template <>
+struct FieldStore<SAM_FP16> {
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+    static __device__ __forceinline__ void store8(void *field, size_t idx, const float *wx, const float *wy) {
+        uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(field) + idx);
+        p[0] = make_uint4(pack(wx[0], wy[0]), pack(wx[1], wy[1]), pack(wx[2], wy[2]), pack(wx[3], wy[3]));
+        p[1] = make_uint4(pack(wx[4], wy[4]), pack(wx[5], wy[5]), pack(wx[6], wy[6]), pack(wx[7], wy[7]));
+    }
+    static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
+        reinterpret_cast<uint32_t *>(field)[idx] = pack(wx, wy);
+    }
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__restrict__ img, int w, int h, int ss,
+                                                            size_t img_bytes, int low, void *__restrict__ field,
+                                                            size_t field_img_px, int16_t *__restrict__ ogx,
+                                                            int16_t *__restrict__ ogy, int vec) {
+    __shared__ __align__(16) uint8_t tile[GTY + 2][GSW];
+    const int im = blockIdx.z;
+    img += (size_t)im * img_bytes;
+    const int x0 = blockIdx.x * GTX, y0 = blockIdx.y * GTY;
+    const int tid = threadIdx.x;
+
+    // Stage rows y0-1 .. y0+GTY, columns x0-16 .. x0+GTX+15 (zero outside).
+    // tile[r][c] holds image pixel (x0 - 16 + c, y0 - 1 + r).
+    if (vec) {
+        constexpr int CH = GSW / 16;   // 16-byte chunks per row
+        for (int e = tid; e < (GTY + 2) * CH; e += GTHREADS) {
+            const int r = e / CH, c = e - r * CH;
+            const int y = y0 - 1 + r, x = x0 - 16 + 16 * c;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (y >= 0 && y < h) {
+                const uint8_t *row = img + (size_t)y * ss;
+                if (x >= 0 && x + 16 <= w) {
+                    v = __ldg(reinterpret_cast<const uint4 *>(row + x));
+                } else {
+                    uint32_t wd[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (x + j >= 0 && x + j < w)
+                            wd[j >> 2] |= (uint32_t)row[x + j] << (8 * (j & 3));
+                    v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                }
+            }
+            *reinterpret_cast<uint4 *>(&tile[r][16 * c]) = v;
+        }
+    } else {
+        for (int e = tid; e < (GTY + 2) * GSW; e += GTHREADS) {
+            const int r = e / GSW, c = e - r * GSW;
+            const int y = y0 - 1 + r, x = x0 - 16 + c;
+            tile[r][c] = (y >= 0 && y < h && x >= 0 && x < w) ? img[(size_t)y * ss + x] : 0;
+        }
+    }
+    __syncthreads();
+
+    const int ty = tid / (GTX / GPT);
+    const int tx = (tid - ty * (GTX / GPT)) * GPT;
+    const int y = y0 + ty;
+    const int xb = x0 + tx;
+    if (y >= h || xb >= w)
+        return;
+    const int r = ty + 1;      // centre row in tile
+    const int cb = tx + 16;    // column of pixel xb in tile
+    int a[GPT + 2], b[GPT + 2], c[GPT + 2];
+#pragma unroll
+    for (int j = 0; j < GPT + 2; ++j) {
+        a[j] = tile[r - 1][cb - 1 + j];
+        b[j] = tile[r][cb - 1 + j];
+        c[j] = tile[r + 1][cb - 1 + j];
+    }
+    const int thr = 16 * low * low;
+    float wx[GPT], wy[GPT];
+    int gxs[GPT], gys[GPT];
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+        const int x = xb + j;
+        int gx = 0, gy = 0;
+        if (x > 0 && x < w - 1 && y > 0 && y < h - 1) {
+            gx = (a[j + 2] + 2 * b[j + 2] + c[j + 2]) - (a[j] + 2 * b[j] + c[j]);
+            gy = (c[j] + 2 * c[j + 1] + c[j + 2]) - (a[j] + 2 * a[j + 1] + a[j + 2]);
+        }
+        const int m2 = gx * gx + gy * gy;
+        float fx = 0.f, fy = 0.f;
+        if (m2 >= thr && m2 > 0) {
+            const float inv = rsqrtf((float)m2);
+            fx = (float)gx * inv;
+            fy = (float)gy * inv;
+        }
+        wx[j] = fx;
+        wy[j] = fy;
+        gxs[j] = gx;
+        gys[j] = gy;
+    }
+    const size_t base = (size_t)im * field_img_px + (size_t)y * w + xb;
+    const bool full = (xb + GPT <= w) && vec && ((w & 7) == 0);
+    if (full) {
+        FieldStore<PREC>::store8(field, base, wx, wy);
+        if (ogx) {
+            uint4 vx, vy;
+            vx.x = (gxs[0] & 0xFFFF) | (gxs[1] << 16);
+            vx.y = (gxs[2] & 0xFFFF) | (gxs[3] << 16);
+            vx.z = (gxs[4] & 0xFFFF) | (gxs[5] << 16);
+            vx.w = (gxs[6] & 0xFFFF) | (gxs[7] << 16);
+            vy.x = (gys[0] & 0xFFFF) | (gys[1] << 16);
+            vy.y = (gys[2] & 0xFFFF) | (gys[3] << 16);
+            vy.z = (gys[4] & 0xFFFF) | (gys[5] << 16);
+            vy.w = (gys[6] & 0xFFFF) | (gys[7] << 16);
+            *reinterpret_cast<uint4 *>(ogx + base) = vx;
+            *reinterpret_cast<uint4 *>(ogy + base) = vy;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+            if (xb + j >= w)
+                break;
+            FieldStore<PREC>::store1(field, base + j, wx[j], wy[j]);
+            if (ogx) {
+                ogx[base + j] = (int16_t)gxs[j];
+                ogy[base + j] = (int16_t)gys[j];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
+                                int dst_stride, size_t dst_img, int count, cudaStream_t st) {
+    const int w2 = w / 2, h2 = h / 2;
+    if (w2 <= 0 || h2 <= 0 || count <= 0)
+        return cudaSuccess;
+    const int vec = ((uintptr_t)src % 16 == 0) && (src_stride % 16 == 0) && (count == 1 || src_img % 16 == 0) &&
+                    ((uintptr_t)dst % 16 == 0) && (dst_stride % 16 == 0) && (count == 1 || dst_img % 16 == 0);
+    const int threads = 128;
+    dim3 grid((unsigned)((w2 + 16 * threads - 1) / (16 * threads)), (unsigned)h2, (unsigned)count);
+    pyramid_down_kernel<<<grid, threads, 0, st>>>(src, w, h, src_stride, src_img, dst, dst_stride, dst_img, vec);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t img_bytes, int low, int precision,
+                            void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
+                            cudaStream_t st) {
+    if (w <= 0 || h <= 0 || count <= 0)
+        return cudaSuccess;
+    const size_t esz = precision == SAM_FP32 ? 8 : 4;
+    const int vec = ((uintptr_t)img % 16 == 0) && (stride % 16 == 0) && (count == 1 || img_bytes % 16 == 0) &&
+                    ((uintptr_t)field % 16 == 0) && (count == 1 || (field_img_px * esz) % 16 == 0) &&
+                    (!gx || (((uintptr_t)gx % 16 == 0) && ((uintptr_t)gy % 16 == 0) &&
+                             (count == 1 || field_img_px % 8 == 0)));
+    dim3 grid((unsigned)((w + GTX - 1) / GTX), (unsigned)((h + GTY - 1) / GTY), (unsigned)count);
+    switch (precision) {
+    case SAM_FP32:
+        gradient_kernel<SAM_FP32><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
+                                                             gx, gy, vec);
+        break;
+    case SAM_BF16:
+        gradient_kernel<SAM_BF16><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
+                                                             gx, gy, vec);
+        break;
+    default:
+        gradient_kernel<SAM_FP16><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
+                                                             gx, gy, vec);
+        break;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace sam

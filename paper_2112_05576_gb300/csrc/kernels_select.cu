@@ -1,0 +1,415 @@
+// Kernel (d): candidate extraction, top-K, coarse-to-fine refinement and
+// non-maximum suppression.  The paper's search keeps the maximum-score pose
+// (Sec. II); several instances need local maxima, refined level by level
+// down the pyramid with the size-3 neighbouring search in x, y and theta.
+//
+// Every selection uses one total order: higher score first, then the
+// smaller key (k * H + y) * W + x.  Ties therefore resolve identically on
+// every run, independent of atomic ordering.
+
+#include <float.h>
+
+#include <algorithm>
+
+#include "sam_internal.h"
+
+namespace sam {
+namespace {
+
+constexpr int kSortCap = 2048;   // shared-memory sort buffer (entries)
+
+__device__ __forceinline__ bool beats(float sa, unsigned long long ka, float sb, unsigned long long kb) {
+    return sa > sb || (sa == sb && ka < kb);
+}
+
+// ---------------------------------------------------------------------------
+// local maxima
+// ---------------------------------------------------------------------------
+
+__global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
+                                 float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt) {
+    const int img = blockIdx.y;
+    map += (size_t)img * map_img;
+    const size_t total = (size_t)nth * gh * gw;
+    const size_t plane = (size_t)gh * gw;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const float s = map[idx];
+        if (!(s >= min_score))
+            continue;
+        const int k = (int)(idx / plane);
+        const int r = (int)(idx - (size_t)k * plane);
+        const int y = r / gw, x = r - y * gw;
+        bool ok = true;
+        for (int dk = -1; dk <= 1 && ok; ++dk) {
+            if (dk != 0 && nth == 1)
+                continue;
+            const int k2 = (k + dk + nth) % nth;
+            for (int dy = -1; dy <= 1 && ok; ++dy) {
+                const int y2 = y + dy;
+                if (y2 < 0 || y2 >= gh)
+                    continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x2 = x + dx;
+                    if (x2 < 0 || x2 >= gw)
+                        continue;
+                    const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
+                    if (j == idx)
+                        continue;
+                    if (!beats(s, idx, map[j], j)) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        if (ok) {
+            const int pos = atomicAdd(cnt + img, 1);
+            if ((size_t)pos < cap) {
+                Cand c;
+                c.s = s;
+                c.pad = 0;
+                c.key = idx;
+                cand[(size_t)img * cap + pos] = c;
+            }
+        }
+    }
+}
+
+// Bitonic sort of n (power of two) entries in shared memory, best first.
+__device__ void bitonic_sort(float *s, unsigned long long *key, int n) {
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = ((lo & size) == 0);   // ascending block = best first
+                const bool swap = up ? beats(s[hi], key[hi], s[lo], key[lo]) : beats(s[lo], key[lo], s[hi], key[hi]);
+                if (swap) {
+                    const float ts = s[lo];
+                    s[lo] = s[hi];
+                    s[hi] = ts;
+                    const unsigned long long tk = key[lo];
+                    key[lo] = key[hi];
+                    key[hi] = tk;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ cand, size_t cap, const int *__restrict__ cnt,
+                                                    int K, int gh, int gw, int32_t *__restrict__ out_kyx,
+                                                    float *__restrict__ out_s, int *__restrict__ out_count) {
+    __shared__ float s[kSortCap];
+    __shared__ unsigned long long key[kSortCap];
+    const int img = blockIdx.x;
+    cand += (size_t)img * cap;
+    const int total = (int)min((size_t)cnt[img], cap);
+    const int chunk = kSortCap - K;
+    int have = 0;   // valid entries at the front of the buffer (sorted)
+    for (int start = 0; start < total || (start == 0 && total == 0); start += chunk) {
+        const int take = min(chunk, total - start);
+        const int used = have + max(take, 0);
+        int n2 = 1;
+        while (n2 < used)
+            n2 <<= 1;
+        for (int i = threadIdx.x; i < n2 - have; i += blockDim.x) {
+            const int d = have + i;
+            if (i < take) {
+                const Cand c = cand[start + i];
+                s[d] = c.s;
+                key[d] = c.key;
+            } else {
+                s[d] = -INFINITY;
+                key[d] = ~0ull;
+            }
+        }
+        __syncthreads();
+        if (n2 > 1)
+            bitonic_sort(s, key, n2);
+        have = min(K, used);
+        __syncthreads();
+        if (total == 0)
+            break;
+    }
+    const size_t plane = (size_t)gh * gw;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        if (i < have) {
+            const unsigned long long kk = key[i];
+            const int k = (int)(kk / plane);
+            const int r = (int)(kk - (unsigned long long)k * plane);
+            out_kyx[(size_t)img * 3 * K + 3 * i] = k;
+            out_kyx[(size_t)img * 3 * K + 3 * i + 1] = r / gw;
+            out_kyx[(size_t)img * 3 * K + 3 * i + 2] = r % gw;
+            out_s[(size_t)img * K + i] = s[i];
+        }
+    }
+    if (threadIdx.x == 0)
+        out_count[img] = have;
+}
+
+// ---------------------------------------------------------------------------
+// refinement: one CTA per (image, candidate), all levels top-1 .. 0
+// ---------------------------------------------------------------------------
+
+struct RefineLevels {
+    LevelDev L[kMaxLevels];
+};
+
+constexpr int RTHREADS = 256;
+
+template <int NB>
+__global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, RefineArgs a) {
+    const int img = blockIdx.y, c = blockIdx.x;
+    __shared__ float red[RTHREADS / 32][27];
+    __shared__ int state[4];   // x, y, k, alive
+    __shared__ float sbest;
+    const int ncand = a.cand_count[img];
+    float4 *outp = a.refined + (size_t)img * a.K + c;
+    if (c >= ncand) {
+        if (threadIdx.x == 0)
+            *outp = make_float4(__int_as_float(0), __int_as_float(0), __int_as_float(0), -INFINITY);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        const int32_t *kyx = a.cand_kyx + (size_t)img * 3 * a.K + 3 * c;
+        state[0] = kyx[2] * a.step_x;
+        state[1] = kyx[1] * a.step_y;
+        state[2] = kyx[0];
+        state[3] = 1;
+        sbest = a.cand_s[(size_t)img * a.K + c];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = a.top - 1; l >= 0; --l) {
+        const LevelDev &L = lv.L[l];
+        const int2 sh = lv.L[l + 1].shift[state[2]];
+        const int cx = 2 * state[0] + sh.x, cy = 2 * state[1] + sh.y;
+        const int kp = state[2];
+        const int W = a.w[l], H = a.h[l];
+        const float2 *F = a.field[l] + (size_t)img * a.field_img_px[l];
+        float acc[27];
+#pragma unroll
+        for (int j = 0; j < 27; ++j)
+            acc[j] = 0.f;
+#pragma unroll
+        for (int dk = 0; dk < 3; ++dk) {
+            const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
+            const RotPt *P = L.rot + (size_t)kk * L.n;
+            for (int i = threadIdx.x; i < L.n; i += RTHREADS) {
+                const RotPt p = P[i];
+                const int bx = cx + p.ox, by = cy + p.oy;
+                constexpr int D = NB + 2;   // window of dot products
+                float d[D][D];
+#pragma unroll
+                for (int yy = 0; yy < D; ++yy) {
+#pragma unroll
+                    for (int xx = 0; xx < D; ++xx) {
+                        const int X = bx + xx - D / 2, Y = by + yy - D / 2;
+                        float v = 0.f;
+                        if (X >= 0 && Y >= 0 && X < W && Y < H) {
+                            const float2 f = __ldg(F + (size_t)Y * W + X);
+                            v = fmaf(p.px, f.x, p.py * f.y);
+                            if (a.polarity)
+                                v = fabsf(v);
+                        }
+                        d[yy][xx] = v;
+                    }
+                }
+#pragma unroll
+                for (int ty = 0; ty < 3; ++ty) {
+#pragma unroll
+                    for (int tx = 0; tx < 3; ++tx) {
+                        float m = -INFINITY;
+#pragma unroll
+                        for (int b = 0; b < NB; ++b)
+#pragma unroll
+                            for (int aa = 0; aa < NB; ++aa)
+                                m = fmaxf(m, d[ty + b][tx + aa]);
+                        acc[dk * 9 + ty * 3 + tx] += m;
+                    }
+                }
+            }
+        }
+        // block reduction of the 27 sums
+#pragma unroll
+        for (int j = 0; j < 27; ++j) {
+            float v = acc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                red[warp][j] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float bs = -INFINITY;
+            unsigned long long bk = ~0ull;
+            int bx = 0, by = 0, bkk = 0;
+            bool any = false;
+            for (int dk = 0; dk < 3; ++dk) {
+                const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
+                for (int ty = 0; ty < 3; ++ty) {
+                    for (int tx = 0; tx < 3; ++tx) {
+                        const int X = cx + tx - 1, Y = cy + ty - 1;
+                        if (X < 0 || Y < 0 || X >= W || Y >= H)
+                            continue;
+                        float sum = 0.f;
+                        for (int wv = 0; wv < RTHREADS / 32; ++wv)
+                            sum += red[wv][dk * 9 + ty * 3 + tx];
+                        const float M = sum / (float)L.n;
+                        const unsigned long long key = ((unsigned long long)kk * H + Y) * W + X;
+                        if (!any || beats(M, key, bs, bk)) {
+                            any = true;
+                            bs = M;
+                            bk = key;
+                            bx = X;
+                            by = Y;
+                            bkk = kk;
+                        }
+                    }
+                }
+            }
+            state[0] = bx;
+            state[1] = by;
+            state[2] = bkk;
+            state[3] = any && bs >= a.min_score;
+            sbest = bs;
+        }
+        __syncthreads();
+        if (!state[3])
+            break;
+    }
+    if (threadIdx.x == 0)
+        *outp = make_float4(__int_as_float(state[0]), __int_as_float(state[1]), __int_as_float(state[2]),
+                            state[3] ? sbest : -INFINITY);
+}
+
+// ---------------------------------------------------------------------------
+// NMS: one CTA per image
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
+    __shared__ float s[kMaxTopK];
+    __shared__ unsigned long long key[kMaxTopK];
+    __shared__ int px[kMaxTopK], py[kMaxTopK], pk[kMaxTopK];
+    const int img = blockIdx.x;
+    const float4 *R = a.refined + (size_t)img * a.K;
+    const int nc = min(a.cand_count[img], a.K);
+    int n2 = 1;
+    while (n2 < nc)
+        n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        if (i < nc) {
+            const float4 r = R[i];
+            const int x = __float_as_int(r.x), y = __float_as_int(r.y), k = __float_as_int(r.z);
+            s[i] = r.w;
+            key[i] = ((unsigned long long)k * a.h0 + y) * a.w0 + x;
+        } else {
+            s[i] = -INFINITY;
+            key[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    if (n2 > 1)
+        bitonic_sort(s, key, n2);
+    const unsigned long long plane = (unsigned long long)a.h0 * a.w0;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const unsigned long long kk = key[i];
+        if (kk == ~0ull)
+            continue;
+        pk[i] = (int)(kk / plane);
+        const int r = (int)(kk - (unsigned long long)pk[i] * plane);
+        py[i] = r / a.w0;
+        px[i] = r - py[i] * a.w0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sam_pose *out = a.out + (size_t)img * a.max_out;
+        int kept = 0;
+        const long long ms2 = (long long)a.min_side * a.min_side;
+        for (int i = 0; i < nc && kept < a.max_out; ++i) {
+            if (s[i] == -INFINITY)
+                break;   // sorted: the rest are dead too
+            bool ok = true;
+            for (int j = 0; j < kept; ++j) {
+                const long long dx = px[i] - out[j].level0_x, dy = py[i] - out[j].level0_y;
+                if (4 * (dx * dx + dy * dy) < ms2) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok)
+                continue;
+            sam_pose p;
+            p.x = (float)px[i];
+            p.y = (float)py[i];
+            p.theta_deg = (float)(pk[i] * a.angle_step);
+            p.score = s[i];
+            p.angle_index = pk[i];
+            p.level0_x = px[i];
+            p.level0_y = py[i];
+            p.reserved = 0;
+            out[kept++] = p;
+        }
+        a.n_out[img] = kept;
+    }
+}
+
+}  // namespace
+
+size_t candidates_scratch_bytes(int nth, int gh, int gw) {
+    // At most one strict local maximum per 2x2x2 block of (theta, y, x).
+    const size_t cap = (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2);
+    return 256 + cap * sizeof(Cand);
+}
+
+static size_t cand_cap(int nth, int gh, int gw) { return (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2); }
+
+cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
+                              int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
+                              int n_img, cudaStream_t st) {
+    // scratch layout per image: [int counter, padded to 256 B][Cand cap]
+    // counters for all images live at the start of the first image's slot
+    const size_t cap = cand_cap(nth, gh, gw);
+    int *cnt = reinterpret_cast<int *>(scratch);
+    Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
+    (void)scratch_img;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n_img, st);
+    if (e != cudaSuccess)
+        return e;
+    const size_t total = (size_t)nth * gh * gw;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    dim3 grid((unsigned)blocks, (unsigned)n_img);
+    local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt);
+    topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img) {
+    return 256 * ((n_img * sizeof(int) + 255) / 256) + (size_t)n_img * cand_cap(nth, gh, gw) * sizeof(Cand);
+}
+
+cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t st) {
+    RefineLevels lv;
+    for (int l = 0; l < kMaxLevels; ++l)
+        lv.L[l] = m->dev[l];
+    dim3 grid((unsigned)a.K, (unsigned)a.count);
+    if (a.nbhd == 3)
+        refine_kernel<3><<<grid, RTHREADS, 0, st>>>(lv, a);
+    else
+        refine_kernel<1><<<grid, RTHREADS, 0, st>>>(lv, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st) {
+    nms_kernel<<<a.count, 256, 0, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace sam

@@ -1,0 +1,142 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/sam.h"
+
+namespace sam {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxTopK = 1024;
+
+// One rotated model point in device tables: integer offset (ox, oy) of
+// Eq. (2) stored as int bits in x/y, unit direction (px, py) in z/w.
+struct RotPt {
+    int ox, oy;
+    float px, py;
+};
+
+// Host-side description of one model level.
+struct LevelHost {
+    int tw = 0, th = 0;              // template size at this level
+    int n = 0;                       // edge points
+    int ntheta = 0;                  // angles at this level
+    double dtheta = 0.0;             // angle step (deg)
+    std::vector<int32_t> tx, ty, gx, gy;
+    std::vector<RotPt> rot;          // [ntheta][n]
+    std::vector<int4> bbox;          // [ntheta] (oxmin, oxmax, oymin, oymax)
+    std::vector<int2> shift;         // [ntheta] child shift to level-1 (empty at level 0)
+};
+
+// Device copy of one level's tables.
+struct LevelDev {
+    int tw, th, n, ntheta;
+    const RotPt *rot;
+    const int4 *bbox;
+    const int2 *shift;
+};
+
+struct Workspace {
+    void *base = nullptr;
+    size_t bytes = 0;
+    int device = -1;
+};
+
+}  // namespace sam
+
+struct sam_model {
+    sam_model_params p;
+    int levels = 0;
+    int ntheta0 = 0;
+    std::vector<sam::LevelHost> lv;
+    // device state (uploaded on first use)
+    int device = -1;
+    void *d_tables = nullptr;
+    sam::LevelDev dev[sam::kMaxLevels];
+    sam::Workspace ws;
+};
+
+namespace sam {
+
+// ---- accounting: every kernel launch of the library calls this ----
+void count_launches(int n);
+
+// ---- host model builder (model.cpp) ----
+sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m);
+sam_status upload_model(sam_model *m);
+
+// ---- kernels (launchers return cudaGetLastError()) ----
+// (b) pyramid step; `count` images, image i at src + i*src_img / dst + i*dst_img
+cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
+                                int dst_stride, size_t dst_img, int count, cudaStream_t st);
+// (a) gradient / threshold / normalise; field image i at field + i*field_img_px pixels
+cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t img_bytes, int low, int precision,
+                            void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
+                            cudaStream_t st);
+// (c) exhaustive score map of one level for `count` fields
+struct ScoreArgs {
+    const void *field;
+    size_t field_img_px;
+    int w, h;
+    int precision;
+    int step_x, step_y;
+    int nbhd;
+    int polarity;
+    float min_score;
+    int early;
+    float *map;
+    size_t map_img;   // floats per image
+    int count;
+};
+cudaError_t launch_score_map(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
+cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
+
+// (d) candidates: local maxima + top-K per image
+struct Cand {
+    float s;
+    uint32_t pad;
+    unsigned long long key;   // (k * gh + y) * gw + x
+};
+size_t candidates_scratch_bytes(int nth, int gh, int gw);
+size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img);
+cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
+                              int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
+                              int n_img, cudaStream_t st);
+
+// (d) refinement down the pyramid + NMS
+struct RefineArgs {
+    const float2 *field[kMaxLevels];   // FP32 fields per level, image 0
+    size_t field_img_px[kMaxLevels];   // pixels per image per level
+    int w[kMaxLevels], h[kMaxLevels];
+    int top;                           // top level index (levels-1)
+    int step_x, step_y;
+    int nbhd, polarity;
+    float min_score;
+    int K;
+    const int32_t *cand_kyx;           // per image: 3*K
+    const float *cand_s;               // per image: K
+    const int *cand_count;             // per image
+    float4 *refined;                   // per image: K (x, y, k, score) level 0
+    int count;
+};
+cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t st);
+
+struct NmsArgs {
+    const float4 *refined;   // per image K
+    const int *cand_count;
+    int K;
+    int w0, h0;
+    int min_side;
+    int max_out;
+    double angle_step;
+    sam_pose *out;           // per image max_out
+    int *n_out;              // per image
+    int count;
+};
+cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
+
+}  // namespace sam

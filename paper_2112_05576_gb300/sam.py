@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libsam.so (include/sam.h).
+
+Argument marshalling only: every step of the detector runs in the CUDA
+library.  Device buffers are torch CUDA tensors (passed by data pointer) and
+the stream is torch's current stream; host buffers are numpy arrays.  If
+the library is missing the import of a compute entry point raises: there is
+no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional
+
+import numpy as np
+
+from . import build as _build
+
+SAM_OK, SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT, SAM_ERR_EMPTY_MODEL, SAM_ERR_CAPACITY = range(7)
+FP32, BF16, FP16 = 0, 1, 2
+
+_c_int, _c_float, _c_double, _vp = ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+class ModelParams(ctypes.Structure):
+    _fields_ = [("low", _c_int), ("high", _c_int), ("levels", _c_int), ("angle_step_deg", _c_double),
+                ("polarity", _c_int)]
+
+
+class DetectParams(ctypes.Structure):
+    _fields_ = [("step_x", _c_int), ("step_y", _c_int), ("neighbourhood", _c_int), ("min_score", _c_float),
+                ("max_detections", _c_int), ("top_k", _c_int), ("precision", _c_int),
+                ("early_termination", _c_int)]
+
+
+class Pose(ctypes.Structure):
+    _fields_ = [("x", _c_float), ("y", _c_float), ("theta_deg", _c_float), ("score", _c_float),
+                ("angle_index", _c_int), ("level0_x", _c_int), ("level0_y", _c_int), ("reserved", _c_int)]
+
+
+# name -> (restype, argtypes); every symbol include/sam.h declares
+SIGNATURES = {
+    "sam_status_str": (ctypes.c_char_p, [_c_int]),
+    "sam_version": (_c_int, []),
+    "sam_compiled_arch": (_c_int, []),
+    "sam_default_model_params": (None, [ctypes.POINTER(ModelParams)]),
+    "sam_default_detect_params": (None, [ctypes.POINTER(DetectParams)]),
+    "sam_create_model": (_c_int, [_vp, _c_int, _c_int, _c_int, ctypes.POINTER(ModelParams), ctypes.POINTER(_vp)]),
+    "sam_free_model": (None, [_vp]),
+    "sam_model_levels": (_c_int, [_vp]),
+    "sam_model_num_points": (_c_int, [_vp, _c_int]),
+    "sam_model_num_angles": (_c_int, [_vp, _c_int]),
+    "sam_model_template_size": (_c_int, [_vp, _c_int, _i32p, _i32p]),
+    "sam_model_rotated_points": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p, _f32p, _f32p]),
+    "sam_model_points": (_c_int, [_vp, _c_int, _i32p, _i32p, _i32p, _i32p]),
+    "sam_model_child_shift": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p]),
+    "sam_detect": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams), _vp,
+                            ctypes.POINTER(Pose), _c_int, ctypes.POINTER(_c_int)]),
+    "sam_detect_batch": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int,
+                                  ctypes.POINTER(DetectParams), _vp, ctypes.POINTER(Pose), _c_int,
+                                  ctypes.POINTER(_c_int)]),
+    "sam_pyramid_down": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
+    "sam_gradient": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp]),
+    "sam_score_map": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_float, _c_int,
+                               _vp, _vp]),
+    "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
+    "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "sam_profile_enable": (None, [_c_int]),
+    "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
+    "sam_kernel_launches": (ctypes.c_longlong, []),
+}
+
+STAGES = ("pyramid", "gradient", "score_map", "candidates", "refine", "nms")
+
+_lib = None
+
+
+class SamError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsam.so (building it first if sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(s):
+    return lib().sam_status_str(int(s)).decode()
+
+
+def _check(s, where):
+    if s != SAM_OK:
+        raise SamError(s, where)
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def default_detect_params(**kw) -> DetectParams:
+    p = DetectParams()
+    lib().sam_default_detect_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Model:
+    """A template model (edge points per level and Eq. (2) tables)."""
+
+    def __init__(self, template: np.ndarray, low=30, high=60, levels=3, angle_step_deg=1.0, polarity=0):
+        t = np.ascontiguousarray(template, dtype=np.uint8)
+        if t.ndim != 2:
+            raise ValueError("template must be a 2-D uint8 array")
+        self.params = ModelParams(int(low), int(high), int(levels), float(angle_step_deg), int(polarity))
+        h = ctypes.c_void_p()
+        _check(lib().sam_create_model(t.ctypes.data_as(_vp), t.shape[1], t.shape[0], t.shape[1],
+                                      ctypes.byref(self.params), ctypes.byref(h)), "sam_create_model")
+        self._h = h
+        self.levels = lib().sam_model_levels(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().sam_free_model(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_points(self, level):
+        return lib().sam_model_num_points(self._h, level)
+
+    def num_angles(self, level):
+        return lib().sam_model_num_angles(self._h, level)
+
+    def template_size(self, level):
+        w, h = ctypes.c_int32(), ctypes.c_int32()
+        lib().sam_model_template_size(self._h, level, ctypes.byref(w), ctypes.byref(h))
+        return w.value, h.value
+
+    def rotated_points(self, level, k):
+        n = self.num_points(level)
+        ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
+        px, py = np.empty(n, np.float32), np.empty(n, np.float32)
+        _check(lib().sam_model_rotated_points(self._h, level, k, ox.ctypes.data_as(_i32p), oy.ctypes.data_as(_i32p),
+                                              px.ctypes.data_as(_f32p), py.ctypes.data_as(_f32p)),
+               "sam_model_rotated_points")
+        return ox, oy, px, py
+
+    def points(self, level):
+        n = self.num_points(level)
+        a = [np.empty(n, np.int32) for _ in range(4)]
+        _check(lib().sam_model_points(self._h, level, *[x.ctypes.data_as(_i32p) for x in a]), "sam_model_points")
+        return tuple(a)
+
+    def child_shift(self, level, k_parent):
+        sx, sy = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sam_model_child_shift(self._h, level, k_parent, ctypes.byref(sx), ctypes.byref(sy)),
+               "sam_model_child_shift")
+        return sx.value, sy.value
+
+
+def _poses(arr, n) -> List[dict]:
+    return [dict(x=arr[i].level0_x, y=arr[i].level0_y, theta_deg=arr[i].theta_deg, score=arr[i].score,
+                 k=arr[i].angle_index) for i in range(n)]
+
+
+def detect(model: Model, image, params: Optional[DetectParams] = None, stream=None, capacity=None):
+    """Detect the model in one image (numpy host array or torch CUDA uint8 tensor)."""
+    params = params or default_detect_params()
+    cap = capacity or params.max_detections
+    out = (Pose * cap)()
+    n = ctypes.c_int()
+    if isinstance(image, np.ndarray):
+        img = np.ascontiguousarray(image, dtype=np.uint8)
+        ptr, on_dev, h, w, stride = img.ctypes.data_as(_vp), 0, img.shape[0], img.shape[1], img.shape[1]
+        keep = img
+    else:
+        if not image.is_cuda or image.dtype.__str__() != "torch.uint8" or image.dim() != 2:
+            raise ValueError("device images must be 2-D torch.uint8 CUDA tensors")
+        if image.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+        ptr, on_dev, h, w, stride = _ptr(image), 1, image.shape[0], image.shape[1], image.stride(0)
+        keep = image
+    _check(lib().sam_detect(model.handle, ptr, w, h, stride, on_dev, ctypes.byref(params),
+                            _stream(stream) if on_dev or _has_cuda() else None, out, cap, ctypes.byref(n)),
+           "sam_detect")
+    del keep
+    return _poses(out, n.value)
+
+
+def _has_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def detect_batch(model: Model, images, params: Optional[DetectParams] = None, stream=None, capacity=None):
+    """Detect in a (N, H, W) torch.uint8 CUDA tensor; returns one pose list per image."""
+    params = params or default_detect_params()
+    cap = capacity or params.max_detections
+    N, H, W = images.shape
+    if images.stride(2) != 1 or images.stride(1) < W:
+        raise ValueError("rows must be contiguous")
+    out = (Pose * (cap * N))()
+    nout = (ctypes.c_int * N)()
+    _check(lib().sam_detect_batch(model.handle, _ptr(images), N, images.stride(0), W, H, images.stride(1),
+                                  ctypes.byref(params), _stream(stream), out, cap, nout), "sam_detect_batch")
+    return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(N)]
+
+
+# ---- individual steps on torch CUDA tensors ----
+
+def pyramid_down(src, dst, stream=None):
+    h, w = src.shape
+    _check(lib().sam_pyramid_down(_ptr(src), w, h, src.stride(0), _ptr(dst), dst.stride(0), _stream(stream)),
+           "sam_pyramid_down")
+
+
+def gradient(img, low, precision, field, gx=None, gy=None, stream=None):
+    h, w = img.shape
+    _check(lib().sam_gradient(_ptr(img), w, h, img.stride(0), int(low), int(precision), _ptr(field), _ptr(gx),
+                              _ptr(gy), _stream(stream)), "sam_gradient")
+
+
+def score_map(model: Model, level, field, w, h, precision, out, step_x=1, step_y=1, nbhd=3, min_score=0.0,
+              early=0, stream=None):
+    _check(lib().sam_score_map(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(step_x),
+                               int(step_y), int(nbhd), float(min_score), int(early), _ptr(out), _stream(stream)),
+           "sam_score_map")
+
+
+def candidates_scratch_bytes(nth, gh, gw):
+    return int(lib().sam_candidates_scratch_bytes(nth, gh, gw))
+
+
+def candidates(smap, min_score, K, out_kyx, out_s, count, scratch, stream=None):
+    nth, gh, gw = smap.shape
+    _check(lib().sam_candidates(_ptr(smap), nth, gh, gw, float(min_score), int(K), _ptr(out_kyx), _ptr(out_s),
+                                _ptr(count), _ptr(scratch), _stream(stream)), "sam_candidates")
+
+
+def profile_enable(on=True):
+    lib().sam_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """Per-stage device milliseconds and call counts since the last read."""
+    n = len(STAGES)
+    ms = (ctypes.c_float * n)()
+    calls = (ctypes.c_int32 * n)()
+    lib().sam_profile_read(ms, calls, n)
+    return {STAGES[i]: (float(ms[i]), int(calls[i])) for i in range(n)}
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(lib().sam_kernel_launches())
