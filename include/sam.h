@@ -210,6 +210,23 @@ size_t sam_candidates_scratch_bytes(int nth, int gh, int gw);
 sam_status sam_candidates(const float *map, int nth, int gh, int gw, float min_score, int K, int32_t *out_kyx,
                           float *out_s, int *count, void *scratch, void *stream);
 
+/* sam_candidates without a scratch argument and without any allocation (the
+ * paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc when they need candidates -- a deadline-bound control loop, where
+ * cudaMalloc's latency and implicit device synchronisation are not allowed,
+ * or an integration whose device memory is fixed at start-up).  Same inputs,
+ * outputs and results as sam_candidates.  Its scratch is a 4 MiB array in
+ * the library's device memory (held by every GPU that loads the library
+ * until exit); maps with sam_candidates_scratch_bytes(nth, gh, gw) above
+ * 4 MiB are rejected with SAM_ERR_CAPACITY.  The first call on a device looks
+ * up that array's device address (with the device current) and caches it;
+ * make that first call before any stream capture.  All calls share the array
+ * and leave their contents in it (the counter is cleared at the start of
+ * each call): calls whose GPU work overlaps race and must be serialised by
+ * the caller.  Errors: SAM_ERR_ARG, SAM_ERR_CAPACITY, SAM_ERR_CUDA. */
+sam_status sam_candidates_noalloc(const float *map, int nth, int gh, int gw, float min_score, int K,
+                                  int32_t *out_kyx, float *out_s, int *count, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Stage timing (tracing).  When enabled, sam_detect / sam_detect_batch record
  * CUDA events on the caller's stream before and after the launches of each

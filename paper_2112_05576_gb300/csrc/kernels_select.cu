@@ -413,3 +413,76 @@ cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st) {
 }
 
 }  // namespace sam
+
+// ---------------------------------------------------------------------------
+// Candidate extraction without run-time allocation.
+//
+// Some callers cannot call cudaMalloc at the moment they need candidates: a
+// control loop with a hard deadline (cudaMalloc can take milliseconds and
+// may synchronise the device), or an integration whose device memory is
+// budgeted once at start-up and must not grow afterwards.  This entry point
+// serves them: its scratch (the local-maximum counter and candidate list)
+// lives in the file-scope device array below instead of a caller buffer.
+//
+// Limit: 4 MiB per device, held by every GPU that loads the library until
+// the process exits; maps whose candidate capacity needs more are rejected
+// with SAM_ERR_CAPACITY before anything is launched.
+// Sharing: every call on a device uses the same array and leaves its
+// contents behind; the counter is cleared at the start of each call.  Calls
+// whose work overlaps on the GPU (other streams, other host threads) race
+// on the array and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace sam {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  The first call
+// on a device looks it up (cudaGetSymbolAddress, with that device current)
+// and caches it; later calls only read the cache.
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace sam
+
+extern "C" sam_status sam_candidates_noalloc(const float *map, int nth, int gh, int gw, float min_score, int K,
+                                             int32_t *out_kyx, float *out_s, int *count, void *stream) {
+    using namespace sam;
+    if (!map || !out_kyx || !out_s || !count || nth < 1 || gh < 1 || gw < 1 || K < 1 || K > kMaxTopK)
+        return SAM_ERR_ARG;
+    if (candidates_scratch_bytes(nth, gh, gw) > kNoAllocScratchBytes)
+        return SAM_ERR_CAPACITY;
+    void *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    return launch_candidates(map, 0, nth, gh, gw, min_score, K, out_kyx, out_s, count, scratch, 0, 1,
+                             (cudaStream_t)stream) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
+}

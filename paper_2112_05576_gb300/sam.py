@@ -68,6 +68,7 @@ SIGNATURES = {
                                _vp, _vp]),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
     "sam_profile_enable": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
     "sam_kernel_launches": (ctypes.c_longlong, []),
@@ -290,3 +291,12 @@ def profile_read():
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(lib().sam_kernel_launches())
+
+
+def candidates_noalloc(smap, min_score, K, out_kyx, out_s, count, stream=None):
+    """sam_candidates using the library's fixed device scratch (no allocation,
+    no scratch argument); for callers that cannot allocate device memory when
+    they need candidates.  Calls that overlap on the GPU must be serialised."""
+    nth, gh, gw = smap.shape
+    _check(lib().sam_candidates_noalloc(_ptr(smap), nth, gh, gw, float(min_score), int(K), _ptr(out_kyx),
+                                        _ptr(out_s), _ptr(count), _stream(stream)), "sam_candidates_noalloc")
