@@ -51,6 +51,12 @@ typedef enum {
 /* Field precisions of the normalised search gradients w_hat. */
 enum { SAM_FP32 = 0, SAM_BF16 = 1, SAM_FP16 = 2 };
 
+/* Field layouts.  SAM_LAYOUT_PIXEL: each row holds w pixels, each pixel the
+ * pair (wx, wy); row pitch w pixels.  SAM_LAYOUT_PAIRS: each row holds pixel
+ * pairs {wx_2j, wx_2j+1, wy_2j, wy_2j+1}; row pitch w rounded up to an even
+ * number of pixels, the padding pixel (odd w) zero.  Same bytes per pixel. */
+enum { SAM_LAYOUT_PIXEL = 0, SAM_LAYOUT_PAIRS = 1 };
+
 typedef struct sam_model sam_model;
 
 /* Model parameters (Sec. II inputs: edge thresholds, number of pyramid
@@ -181,11 +187,12 @@ sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, ui
 /* Edge extraction (Sec. II) of a device image: 3x3 Sobel gx, gy (zero on the
  * 1-pixel border), edge iff gx^2+gy^2 >= 16 low^2, and the unit field
  * w_hat = g/|g| on edges, (0,0) elsewhere.
- *   field   device, w*h pixel pairs (wx, wy), dense row-major: float pairs
- *           (8 B/px) for SAM_FP32, bf16 or fp16 pairs (4 B/px) otherwise.
+ *   field   device, h rows in `layout` (SAM_LAYOUT_PIXEL or SAM_LAYOUT_PAIRS),
+ *           float components (8 B/px) for SAM_FP32, bf16 or fp16 (4 B/px)
+ *           otherwise; 16-byte aligned for SAM_LAYOUT_PAIRS.
  *   gx, gy  optional device int16 outputs (w*h, dense), NULL to skip. */
-sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, void *field,
-                        int16_t *gx, int16_t *gy, void *stream);
+sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, int layout,
+                        void *field, int16_t *gx, int16_t *gy, void *stream);
 
 /* Exhaustive score map of one model level (Eq. (1) with the neighbouring
  * search, Eq. (2) projection, Sec. II three nested loops):
@@ -194,10 +201,27 @@ sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, i
  *   field   device w_hat field of the search image at that level (layout and
  *           precision as produced by sam_gradient).
  *   map     device float array of num_angles * gh * gw.
- * With early_termination, poses proved below min_score are written -inf. */
-sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int step_x,
-                         int step_y, int neighbourhood, float min_score, int early_termination, float *map,
-                         void *stream);
+ * With early_termination, poses proved below min_score are written -inf.
+ * The tiled kernel serves FP32 SAM_LAYOUT_PAIRS fields at step 1 when its
+ * shared-memory window fits; everything else uses the generic kernel.
+ * Errors: SAM_ERR_ARG, SAM_ERR_CUDA, SAM_ERR_TIMEOUT (a bounded wait for the
+ * window's TMA copy gave up; checked on the next synchronising call). */
+sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int layout,
+                         int step_x, int step_y, int neighbourhood, float min_score, int early_termination,
+                         float *map, void *stream);
+
+/* Score-kernel selection and tiling, process-wide (autotuner hook; the paper
+ * has no counterpart).  kernel: 0 automatic, 1 generic one-thread-per-pose,
+ * 2 tiled (falls back to generic when the tiled kernel cannot serve a call).
+ * sx, sy: CTA super-tile in 48x32-pose warp tiles; tg: angles per CTA;
+ * warps: 4 or 8.  Returns SAM_ERR_ARG on out-of-range values. */
+sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps);
+/* Reads back the current selection (any pointer may be NULL). */
+void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps);
+/* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
+ * clears it if any wait gave up since the last call (synchronises the
+ * device). */
+int sam_take_device_error(void);
 
 /* Candidate extraction from a score map [nth][gh][gw]: poses with score >=
  * min_score that beat all 26 neighbours in (theta circular, y, x) under the

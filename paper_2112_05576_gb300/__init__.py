@@ -8,6 +8,8 @@ from .sam import (  # noqa: F401
     BF16,
     FP16,
     FP32,
+    LAYOUT_PAIRS,
+    LAYOUT_PIXEL,
     SIGNATURES,
     STAGES,
     DetectParams,
@@ -16,10 +18,13 @@ from .sam import (  # noqa: F401
     Pose,
     SamError,
     candidates,
+    candidates_noalloc,
     candidates_scratch_bytes,
     default_detect_params,
     detect,
     detect_batch,
+    field_pitch,
+    get_score_kernel,
     gradient,
     kernel_launches,
     lib,
@@ -27,6 +32,8 @@ from .sam import (  # noqa: F401
     profile_read,
     pyramid_down,
     score_map,
+    set_score_kernel,
     status_str,
+    take_device_error,
 )
 from .build import build  # noqa: F401

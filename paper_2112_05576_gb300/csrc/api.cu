@@ -76,7 +76,8 @@ struct Plan {
     size_t off_img[kMaxLevels];
     size_t off_field[kMaxLevels];    // FP32 fields
     size_t field_px[kMaxLevels];
-    size_t off_half = 0;             // top-level bf16/fp16 field (precision != FP32)
+    size_t off_top = 0;              // top-level field, pairs layout, detection precision
+    size_t top_px = 0;               // its pixels per image (pitch (w+1)&~1, padded to 8)
     int gw = 0, gh = 0, nth = 0;
     size_t map_img = 0, off_map = 0;
     size_t off_scratch = 0;
@@ -111,15 +112,15 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
         if (l > 0 || copy_level0)
             off += al(P.img_bytes[l] * count);
     }
+    const int top = P.L - 1;
     for (int l = 0; l < P.L; ++l) {
         P.off_field[l] = off;
-        off += al(P.field_px[l] * 8 * count);
+        if (l < top)   // the top level is scored from its pairs-layout field only
+            off += al(P.field_px[l] * 8 * count);
     }
-    const int top = P.L - 1;
-    if (p.precision != SAM_FP32) {
-        P.off_half = off;
-        off += al(P.field_px[top] * 4 * count);
-    }
+    P.top_px = ((size_t)field_pitch(P.w[top], SAM_LAYOUT_PAIRS) * P.h[top] + 7) & ~(size_t)7;
+    P.off_top = off;
+    off += al(P.top_px * (p.precision == SAM_FP32 ? 8 : 4) * count);
     P.nth = m->lv[top].ntheta;
     P.gw = (P.w[top] + p.step_x - 1) / p.step_x;
     P.gh = (P.h[top] + p.step_y - 1) / p.step_y;
@@ -196,23 +197,21 @@ sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pi
         lvl_bytes[l] = P.img_bytes[l];
     }
     prof_end(0, st);
-    // (a) gradients: FP32 fields on every level, plus the top level's
-    // low-precision copy for the exhaustive search
+    // (a) gradients: FP32 pixel-layout fields for the refinement levels, the
+    // top level in the pairs layout and the detection precision
     prof_begin(1, st);
-    for (int l = 0; l < P.L; ++l)
+    for (int l = 0; l < top; ++l)
         SAM_CU(launch_gradient(lvl_img[l], P.w[l], P.h[l], lvl_pitch[l], lvl_bytes[l], m->p.low, SAM_FP32,
-                               ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
-    const void *top_field = ws + P.off_field[top];
-    if (p.precision != SAM_FP32) {
-        SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low,
-                               p.precision, ws + P.off_half, P.field_px[top], nullptr, nullptr, count, st));
-        top_field = ws + P.off_half;
-    }
+                               SAM_LAYOUT_PIXEL, ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
+    SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low, p.precision,
+                           SAM_LAYOUT_PAIRS, ws + P.off_top, P.top_px, nullptr, nullptr, count, st));
+    const void *top_field = ws + P.off_top;
     prof_end(1, st);
     // (c) exhaustive top-level score map
     ScoreArgs sa;
     sa.field = top_field;
-    sa.field_img_px = P.field_px[top];
+    sa.field_img_px = P.top_px;
+    sa.layout = SAM_LAYOUT_PAIRS;
     sa.w = P.w[top];
     sa.h = P.h[top];
     sa.precision = p.precision;
@@ -226,7 +225,7 @@ sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pi
     sa.map_img = P.map_img;
     sa.count = count;
     prof_begin(2, st);
-    SAM_CU(launch_score_map(m->dev[top], sa, st));
+    SAM_CU(launch_score_map(m, top, sa, nullptr, st));
     prof_end(2, st);
     // (d) candidates, refinement, NMS
     const int K = p.top_k;
@@ -287,8 +286,15 @@ sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p,
     SAM_CU(cudaMemcpyAsync(poses.data(), ws + P.off_out, poses.size() * sizeof(sam_pose), cudaMemcpyDeviceToHost,
                            st));
     SAM_CU(cudaMemcpyAsync(nout.data(), ws + P.off_nout, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int dev_err = 0;
+    SAM_CU(score_error_flag_async(&dev_err, st));
     SAM_CU(cudaStreamSynchronize(st));
     prof_collect();
+    if (dev_err) {
+        score_error_clear(st);
+        cudaStreamSynchronize(st);
+        return SAM_ERR_TIMEOUT;
+    }
     for (int i = 0; i < count; ++i) {
         const int n = std::min(nout[i], capacity);
         memcpy(out + (size_t)i * capacity, poses.data() + (size_t)i * p.max_detections, (size_t)n * sizeof(sam_pose));
@@ -299,8 +305,23 @@ sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p,
 
 }  // namespace
 
-cudaError_t launch_score_map(const LevelDev &L, const ScoreArgs &a, cudaStream_t st) {
-    return launch_score_map_generic(L, a, st);
+ScoreChoice &score_choice() {
+    static ScoreChoice c;
+    return c;
+}
+
+cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
+    const ScoreChoice &c = score_choice();
+    int bxw = 0, byw = 0;
+    const bool tiled = c.kernel != 1 && a.precision == SAM_FP32 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 &&
+                       a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) && ((uintptr_t)a.field % 16 == 0) &&
+                       (a.count == 1 || a.field_img_px % 2 == 0) &&
+                       tiled_plan(m->lv[level], c.cfg.sx, c.cfg.sy, c.cfg.tg, &bxw, &byw);
+    if (tiled)
+        return launch_score_tiled(m, level, a.field, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px, a.w, a.h,
+                                  a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, err, c.cfg,
+                                  st);
+    return launch_score_map_generic(m->dev[level], a, st);
 }
 
 }  // namespace sam
@@ -505,32 +526,35 @@ sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, ui
                : SAM_ERR_CUDA;
 }
 
-sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, void *field,
-                        int16_t *gx, int16_t *gy, void *stream) {
+sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, int layout,
+                        void *field, int16_t *gx, int16_t *gy, void *stream) {
     if (!img || !field || w < 1 || h < 1 || stride < w || low < 1 || low > 1024 || precision < SAM_FP32 ||
-        precision > SAM_FP16 || ((gx == nullptr) != (gy == nullptr)))
+        precision > SAM_FP16 || (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS) ||
+        ((gx == nullptr) != (gy == nullptr)) || (layout == SAM_LAYOUT_PAIRS && (gx || (uintptr_t)field % 16)))
         return SAM_ERR_ARG;
-    return launch_gradient(img, w, h, stride, 0, low, precision, field, (size_t)w * h, gx, gy, 1,
-                           (cudaStream_t)stream) == cudaSuccess
+    return launch_gradient(img, w, h, stride, 0, low, precision, layout, field,
+                           (size_t)field_pitch(w, layout) * h, gx, gy, 1, (cudaStream_t)stream) == cudaSuccess
                ? SAM_OK
                : SAM_ERR_CUDA;
 }
 
-sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int step_x,
-                         int step_y, int neighbourhood, float min_score, int early_termination, float *map,
-                         void *stream) {
+sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int layout,
+                         int step_x, int step_y, int neighbourhood, float min_score, int early_termination,
+                         float *map, void *stream) {
     if (!m || level < 0 || level >= m->levels || !field || !map || w < 1 || h < 1 || step_x < 1 || step_y < 1 ||
-        (neighbourhood != 1 && neighbourhood != 3) || precision < SAM_FP32 || precision > SAM_FP16)
+        (neighbourhood != 1 && neighbourhood != 3) || precision < SAM_FP32 || precision > SAM_FP16 ||
+        (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS))
         return SAM_ERR_ARG;
     sam_status s = upload_model(m);
     if (s != SAM_OK)
         return s;
     ScoreArgs sa;
     sa.field = field;
-    sa.field_img_px = (size_t)w * h;
+    sa.field_img_px = (size_t)field_pitch(w, layout) * h;
     sa.w = w;
     sa.h = h;
     sa.precision = precision;
+    sa.layout = layout;
     sa.step_x = step_x;
     sa.step_y = step_y;
     sa.nbhd = neighbourhood;
@@ -540,7 +564,34 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
     sa.map = map;
     sa.map_img = 0;
     sa.count = 1;
-    return launch_score_map(m->dev[level], sa, (cudaStream_t)stream) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+    return launch_score_map(m, level, sa, nullptr, (cudaStream_t)stream) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps) {
+    if (kernel < 0 || kernel > 2 || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 1 || tg > 4096 ||
+        (warps != 4 && warps != 8))
+        return SAM_ERR_ARG;
+    ScoreChoice &c = score_choice();
+    c.kernel = kernel;
+    c.cfg.sx = sx;
+    c.cfg.sy = sy;
+    c.cfg.tg = tg;
+    c.cfg.warps = warps;
+    return SAM_OK;
+}
+
+void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps) {
+    const ScoreChoice &c = score_choice();
+    if (kernel)
+        *kernel = c.kernel;
+    if (sx)
+        *sx = c.cfg.sx;
+    if (sy)
+        *sy = c.cfg.sy;
+    if (tg)
+        *tg = c.cfg.tg;
+    if (warps)
+        *warps = c.cfg.warps;
 }
 
 size_t sam_candidates_scratch_bytes(int nth, int gh, int gw) { return candidates_scratch_bytes(nth, gh, gw); }

@@ -94,6 +94,10 @@ struct FieldStore<SAM_FP32> {
     static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
         reinterpret_cast<float2 *>(field)[idx] = make_float2(wx, wy);
     }
+    // pixel pair q of a pairs-layout field: {wx0, wx1, wy0, wy1}
+    static __device__ __forceinline__ void store_pair(void *field, size_t q, float x0, float x1, float y0, float y1) {
+        reinterpret_cast<float4 *>(field)[q] = make_float4(x0, x1, y0, y1);
+    }
 };
 
 template <>
@@ -109,6 +113,9 @@ struct FieldStore<SAM_BF16> {
     }
     static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
         reinterpret_cast<uint32_t *>(field)[idx] = pack(wx, wy);
+    }
+    static __device__ __forceinline__ void store_pair(void *field, size_t q, float x0, float x1, float y0, float y1) {
+        reinterpret_cast<uint2 *>(field)[q] = make_uint2(pack(x0, x1), pack(y0, y1));
     }
 };
 
@@ -126,9 +133,12 @@ struct FieldStore<SAM_FP16> {
     static __device__ __forceinline__ void store1(void *field, size_t idx, float wx, float wy) {
         reinterpret_cast<uint32_t *>(field)[idx] = pack(wx, wy);
     }
+    static __device__ __forceinline__ void store_pair(void *field, size_t q, float x0, float x1, float y0, float y1) {
+        reinterpret_cast<uint2 *>(field)[q] = make_uint2(pack(x0, x1), pack(y0, y1));
+    }
 };
 
-template <int PREC>
+template <int PREC, int LAYOUT>
 __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__restrict__ img, int w, int h, int ss,
                                                             size_t img_bytes, int low, void *__restrict__ field,
                                                             size_t field_img_px, int16_t *__restrict__ ogx,
@@ -209,6 +219,18 @@ __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__res
         gxs[j] = gx;
         gys[j] = gy;
     }
+    if (LAYOUT == SAM_LAYOUT_PAIRS) {
+        // pixels beyond w were computed as zero, so the padding pixel of an
+        // odd-width row is written as zero too
+        const int wp = (w + 1) & ~1;
+        const size_t q0 = ((size_t)im * field_img_px + (size_t)y * wp + xb) >> 1;
+        const bool full = (xb + GPT <= wp) && vec;
+#pragma unroll
+        for (int q = 0; q < GPT / 2; ++q)
+            if (full || xb + 2 * q < wp)
+                FieldStore<PREC>::store_pair(field, q0 + q, wx[2 * q], wx[2 * q + 1], wy[2 * q], wy[2 * q + 1]);
+        return;
+    }
     const size_t base = (size_t)im * field_img_px + (size_t)y * w + xb;
     const bool full = (xb + GPT <= w) && vec && ((w & 7) == 0);
     if (full) {
@@ -256,11 +278,25 @@ cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride
     return cudaGetLastError();
 }
 
+template <int PREC>
+void gradient_dispatch(int layout, dim3 grid, cudaStream_t st, const uint8_t *img, int w, int h, int stride,
+                       size_t img_bytes, int low, void *field, size_t field_img_px, int16_t *gx, int16_t *gy,
+                       int vec) {
+    if (layout == SAM_LAYOUT_PAIRS)
+        gradient_kernel<PREC, SAM_LAYOUT_PAIRS><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field,
+                                                                          field_img_px, gx, gy, vec);
+    else
+        gradient_kernel<PREC, SAM_LAYOUT_PIXEL><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field,
+                                                                          field_img_px, gx, gy, vec);
+}
+
 cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t img_bytes, int low, int precision,
-                            void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
+                            int layout, void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
                             cudaStream_t st) {
     if (w <= 0 || h <= 0 || count <= 0)
         return cudaSuccess;
+    if (layout == SAM_LAYOUT_PAIRS && gx)
+        return cudaErrorInvalidValue;
     const size_t esz = precision == SAM_FP32 ? 8 : 4;
     const int vec = ((uintptr_t)img % 16 == 0) && (stride % 16 == 0) && (count == 1 || img_bytes % 16 == 0) &&
                     ((uintptr_t)field % 16 == 0) && (count == 1 || (field_img_px * esz) % 16 == 0) &&
@@ -269,16 +305,16 @@ cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t
     dim3 grid((unsigned)((w + GTX - 1) / GTX), (unsigned)((h + GTY - 1) / GTY), (unsigned)count);
     switch (precision) {
     case SAM_FP32:
-        gradient_kernel<SAM_FP32><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
-                                                             gx, gy, vec);
+        gradient_dispatch<SAM_FP32>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px, gx, gy,
+                                    vec);
         break;
     case SAM_BF16:
-        gradient_kernel<SAM_BF16><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
-                                                             gx, gy, vec);
+        gradient_dispatch<SAM_BF16>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px, gx, gy,
+                                    vec);
         break;
     default:
-        gradient_kernel<SAM_FP16><<<grid, GTHREADS, 0, st>>>(img, w, h, stride, img_bytes, low, field, field_img_px,
-                                                             gx, gy, vec);
+        gradient_dispatch<SAM_FP16>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px, gx, gy,
+                                    vec);
         break;
     }
     count_launches(1);

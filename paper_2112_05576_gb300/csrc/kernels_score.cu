@@ -26,16 +26,16 @@
 namespace sam {
 namespace {
 
-template <typename FT, int NB>
+template <typename E, int LAYOUT, int NB>
 __global__ void __launch_bounds__(256)
-    score_map_generic(const FT *__restrict__ field, size_t field_img_px, int w, int h,
+    score_map_generic(const E *__restrict__ field, size_t field_img_px, int pitch, int w, int h,
                       const RotPt *__restrict__ rot, int n, int step_x, int step_y, int gw, int gh, int polarity,
                       float prune_thresh, int early, float *__restrict__ map, size_t map_img) {
     const int img = blockIdx.z, k = blockIdx.y;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= gw * gh)
         return;
-    field += (size_t)img * field_img_px;
+    field += 2 * (size_t)img * field_img_px;
     const int gxi = idx % gw, gyi = idx / gw;
     const int ux = gxi * step_x, uy = gyi * step_y;
     const RotPt *P = rot + (size_t)k * n;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256)
                 const int x = x0 + a, y = y0 + b;
                 float v = 0.f;
                 if (x >= 0 && y >= 0 && x < w && y < h) {
-                    const float2 f = load_field(field, (size_t)y * w + x);
+                    const float2 f = load_field<E, LAYOUT>(field, pitch, x, y);
                     v = fmaf(p.px, f.x, p.py * f.y);
                     if (polarity)
                         v = fabsf(v);
@@ -73,22 +73,29 @@ __global__ void __launch_bounds__(256)
     map[(size_t)img * map_img + ((size_t)k * gh + gyi) * gw + gxi] = pruned ? -INFINITY : sum / (float)n;
 }
 
-template <typename FT>
+template <typename E, int LAYOUT>
 cudaError_t launch_generic_t(const LevelDev &L, const ScoreArgs &a, cudaStream_t st) {
     const int gw = (a.w + a.step_x - 1) / a.step_x, gh = (a.h + a.step_y - 1) / a.step_y;
     const float thresh = prune_threshold(L.n, a.min_score, a.precision);
     dim3 grid((unsigned)((gw * gh + 255) / 256), (unsigned)L.ntheta, (unsigned)a.count);
-    const FT *f = reinterpret_cast<const FT *>(a.field);
+    const E *f = reinterpret_cast<const E *>(a.field);
+    const int pitch = field_pitch(a.w, LAYOUT);
     if (a.nbhd == 3)
-        score_map_generic<FT, 3><<<grid, 256, 0, st>>>(f, a.field_img_px, a.w, a.h, L.rot, L.n, a.step_x,
-                                                       a.step_y, gw, gh, a.polarity, thresh, a.early, a.map,
-                                                       a.map_img);
+        score_map_generic<E, LAYOUT, 3><<<grid, 256, 0, st>>>(f, a.field_img_px, pitch, a.w, a.h, L.rot, L.n,
+                                                              a.step_x, a.step_y, gw, gh, a.polarity, thresh,
+                                                              a.early, a.map, a.map_img);
     else
-        score_map_generic<FT, 1><<<grid, 256, 0, st>>>(f, a.field_img_px, a.w, a.h, L.rot, L.n, a.step_x,
-                                                       a.step_y, gw, gh, a.polarity, thresh, a.early, a.map,
-                                                       a.map_img);
+        score_map_generic<E, LAYOUT, 1><<<grid, 256, 0, st>>>(f, a.field_img_px, pitch, a.w, a.h, L.rot, L.n,
+                                                              a.step_x, a.step_y, gw, gh, a.polarity, thresh,
+                                                              a.early, a.map, a.map_img);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t launch_generic_e(const LevelDev &L, const ScoreArgs &a, cudaStream_t st) {
+    return a.layout == SAM_LAYOUT_PAIRS ? launch_generic_t<E, SAM_LAYOUT_PAIRS>(L, a, st)
+                                        : launch_generic_t<E, SAM_LAYOUT_PIXEL>(L, a, st);
 }
 
 }  // namespace
@@ -96,11 +103,11 @@ cudaError_t launch_generic_t(const LevelDev &L, const ScoreArgs &a, cudaStream_t
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st) {
     switch (a.precision) {
     case SAM_FP32:
-        return launch_generic_t<float2>(L, a, st);
+        return launch_generic_e<float>(L, a, st);
     case SAM_BF16:
-        return launch_generic_t<__nv_bfloat162>(L, a, st);
+        return launch_generic_e<__nv_bfloat16>(L, a, st);
     default:
-        return launch_generic_t<__half2>(L, a, st);
+        return launch_generic_e<__half>(L, a, st);
     }
 }
 

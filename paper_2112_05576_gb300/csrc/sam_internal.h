@@ -75,14 +75,20 @@ cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride
                                 int dst_stride, size_t dst_img, int count, cudaStream_t st);
 // (a) gradient / threshold / normalise; field image i at field + i*field_img_px pixels
 cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t img_bytes, int low, int precision,
-                            void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
+                            int layout, void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
                             cudaStream_t st);
+// Field layouts: SAM_LAYOUT_PIXEL rows of w (wx, wy) pairs; SAM_LAYOUT_PAIRS
+// rows of (w+1)/2 pixel pairs {wx0, wx1, wy0, wy1} (row pitch w rounded up to
+// even pixels, the padding pixel zero).
+inline int field_pitch(int w, int layout) { return layout == SAM_LAYOUT_PAIRS ? ((w + 1) & ~1) : w; }
+
 // (c) exhaustive score map of one level for `count` fields
 struct ScoreArgs {
     const void *field;
     size_t field_img_px;
     int w, h;
     int precision;
+    int layout;
     int step_x, step_y;
     int nbhd;
     int polarity;
@@ -92,8 +98,31 @@ struct ScoreArgs {
     size_t map_img;   // floats per image
     int count;
 };
-cudaError_t launch_score_map(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
+
+// Tiled scorer (score_tiled.cu): FP32 paired field, step 1.
+struct TileConfig {
+    int sx = 2, sy = 1;   // super-tile in warp tiles (48 x 32 poses each)
+    int tg = 9;           // angles per CTA
+    int warps = 8;        // warps per CTA (4 or 8)
+};
+bool tiled_plan(const LevelHost &L, int sx, int sy, int tg, int *bxw, int *byw);
+cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int wp, size_t field_img_px, int W,
+                               int H, int count, int nbhd, int polarity, float min_score, int early, float *map,
+                               size_t map_img, int *err, const TileConfig &cfg, cudaStream_t st);
+
+// Score-kernel selection (process-wide; sam_set_score_kernel).
+struct ScoreChoice {
+    int kernel = 0;   // 0 automatic, 1 generic, 2 tiled
+    TileConfig cfg;
+};
+ScoreChoice &score_choice();
+// Device error flag of the tiled scorer (score_tiled.cu).
+cudaError_t score_error_flag_async(int *host, cudaStream_t st);
+cudaError_t score_error_clear(cudaStream_t st);
+// Dispatch: tiled when allowed and possible, else generic.  `err` may be
+// null (then the tiled kernel reports into a library-owned flag).
+cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {

@@ -8,11 +8,21 @@
 
 namespace sam {
 
-__device__ __forceinline__ float2 load_field(const float2 *f, size_t i) { return __ldg(f + i); }
-__device__ __forceinline__ float2 load_field(const __nv_bfloat162 *f, size_t i) {
-    return __bfloat1622float2(__ldg(f + i));
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+// (wx, wy) of pixel (x, y) of a field in either layout; E is the component
+// type (float, bf16, fp16), pitch the row pitch in pixels.
+template <typename E, int LAYOUT>
+__device__ __forceinline__ float2 load_field(const E *f, int pitch, int x, int y) {
+    if (LAYOUT == SAM_LAYOUT_PAIRS) {
+        const size_t q4 = 2 * ((size_t)y * pitch + (x & ~1));
+        return make_float2(to_f32(__ldg(f + q4 + (x & 1))), to_f32(__ldg(f + q4 + 2 + (x & 1))));
+    }
+    const size_t i = 2 * ((size_t)y * pitch + x);
+    return make_float2(to_f32(__ldg(f + i)), to_f32(__ldg(f + i + 1)));
 }
-__device__ __forceinline__ float2 load_field(const __half2 *f, size_t i) { return __half22float2(__ldg(f + i)); }
 
 // Per-term error bound of the stored unit field (component rounding).
 inline float term_eps(int precision) {

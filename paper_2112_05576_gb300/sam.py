@@ -19,6 +19,7 @@ from . import build as _build
 
 SAM_OK, SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT, SAM_ERR_EMPTY_MODEL, SAM_ERR_CAPACITY = range(7)
 FP32, BF16, FP16 = 0, 1, 2
+LAYOUT_PIXEL, LAYOUT_PAIRS = 0, 1
 
 _c_int, _c_float, _c_double, _vp = ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -63,9 +64,12 @@ SIGNATURES = {
                                   ctypes.POINTER(DetectParams), _vp, ctypes.POINTER(Pose), _c_int,
                                   ctypes.POINTER(_c_int)]),
     "sam_pyramid_down": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
-    "sam_gradient": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp]),
-    "sam_score_map": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_float, _c_int,
-                               _vp, _vp]),
+    "sam_gradient": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp]),
+    "sam_score_map": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_float,
+                               _c_int, _vp, _vp]),
+    "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
+    "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p]),
+    "sam_take_device_error": (_c_int, []),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
@@ -252,17 +256,39 @@ def pyramid_down(src, dst, stream=None):
            "sam_pyramid_down")
 
 
-def gradient(img, low, precision, field, gx=None, gy=None, stream=None):
+def field_pitch(w, layout):
+    """Row pitch in pixels of a field of width w in the given layout."""
+    return (w + 1) & ~1 if layout == LAYOUT_PAIRS else w
+
+
+def gradient(img, low, precision, field, gx=None, gy=None, stream=None, layout=None):
     h, w = img.shape
-    _check(lib().sam_gradient(_ptr(img), w, h, img.stride(0), int(low), int(precision), _ptr(field), _ptr(gx),
-                              _ptr(gy), _stream(stream)), "sam_gradient")
+    layout = LAYOUT_PIXEL if layout is None else layout
+    _check(lib().sam_gradient(_ptr(img), w, h, img.stride(0), int(low), int(precision), int(layout), _ptr(field),
+                              _ptr(gx), _ptr(gy), _stream(stream)), "sam_gradient")
 
 
 def score_map(model: Model, level, field, w, h, precision, out, step_x=1, step_y=1, nbhd=3, min_score=0.0,
-              early=0, stream=None):
-    _check(lib().sam_score_map(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(step_x),
-                               int(step_y), int(nbhd), float(min_score), int(early), _ptr(out), _stream(stream)),
-           "sam_score_map")
+              early=0, stream=None, layout=None):
+    layout = LAYOUT_PIXEL if layout is None else layout
+    _check(lib().sam_score_map(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(layout),
+                               int(step_x), int(step_y), int(nbhd), float(min_score), int(early), _ptr(out),
+                               _stream(stream)), "sam_score_map")
+
+
+def set_score_kernel(kernel=0, sx=2, sy=1, tg=9, warps=8):
+    """Select the exhaustive scorer: 0 automatic, 1 generic, 2 tiled (with its tiling)."""
+    _check(lib().sam_set_score_kernel(int(kernel), int(sx), int(sy), int(tg), int(warps)), "sam_set_score_kernel")
+
+
+def get_score_kernel():
+    v = [ctypes.c_int32() for _ in range(5)]
+    lib().sam_get_score_kernel(*[ctypes.byref(x) for x in v])
+    return dict(zip(("kernel", "sx", "sy", "tg", "warps"), (x.value for x in v)))
+
+
+def take_device_error():
+    return int(lib().sam_take_device_error())
 
 
 def candidates_scratch_bytes(nth, gh, gw):
