@@ -17,6 +17,7 @@ from .sam import (  # noqa: F401
     ModelParams,
     Pose,
     SamError,
+    autotune,
     candidates,
     candidates_noalloc,
     candidates_scratch_bytes,
@@ -28,6 +29,7 @@ from .sam import (  # noqa: F401
     gradient,
     kernel_launches,
     lib,
+    model_tiling,
     profile_enable,
     profile_read,
     pyramid_down,

@@ -174,10 +174,10 @@ sam_status ensure_workspace(sam_model *m, size_t bytes) {
             return SAM_ERR_CUDA;           \
     } while (0)
 
-// Launch the whole pipeline for `count` images whose level-0 copies start at
-// img0 (row pitch pitch0, image i at img0 + i * img0_bytes).
-sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
-                        const sam_detect_params &p, cudaStream_t st) {
+// Pyramid and gradient fields for `count` images whose level-0 copies start
+// at img0 (row pitch pitch0, image i at img0 + i * img0_bytes).
+sam_status prepare_fields(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
+                          const sam_detect_params &p, cudaStream_t st) {
     char *ws = (char *)m->ws.base;
     const int count = P.count, top = P.L - 1;
     const uint8_t *lvl_img[kMaxLevels];
@@ -205,8 +205,38 @@ sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pi
                                SAM_LAYOUT_PIXEL, ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
     SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low, p.precision,
                            SAM_LAYOUT_PAIRS, ws + P.off_top, P.top_px, nullptr, nullptr, count, st));
-    const void *top_field = ws + P.off_top;
     prof_end(1, st);
+    return SAM_OK;
+}
+
+ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_params &p) {
+    char *ws = (char *)m->ws.base;
+    const int top = P.L - 1;
+    ScoreArgs sa;
+    sa.field = ws + P.off_top;
+    sa.field_img_px = P.top_px;
+    sa.layout = SAM_LAYOUT_PAIRS;
+    sa.w = P.w[top];
+    sa.h = P.h[top];
+    sa.precision = p.precision;
+    sa.step_x = p.step_x;
+    sa.step_y = p.step_y;
+    sa.nbhd = p.neighbourhood;
+    sa.polarity = m->p.polarity;
+    sa.min_score = p.min_score;
+    sa.early = p.early_termination;
+    sa.map = (float *)(ws + P.off_map);
+    sa.map_img = P.map_img;
+    sa.count = P.count;
+    return sa;
+}
+
+// Exhaustive top-level search, candidates, refinement and NMS on the fields
+// prepared by prepare_fields.
+sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st) {
+    char *ws = (char *)m->ws.base;
+    const int count = P.count, top = P.L - 1;
+    const void *top_field = ws + P.off_top;
     // (c) exhaustive top-level score map
     ScoreArgs sa;
     sa.field = top_field;
@@ -277,6 +307,12 @@ sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pi
     return SAM_OK;
 }
 
+sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
+                        const sam_detect_params &p, cudaStream_t st) {
+    const sam_status s = prepare_fields(m, P, img0, pitch0, img0_bytes, p, st);
+    return s != SAM_OK ? s : run_search(m, P, p, st);
+}
+
 sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st, sam_pose *out,
                         int capacity, int *n_out) {
     char *ws = (char *)m->ws.base;
@@ -310,17 +346,26 @@ ScoreChoice &score_choice() {
     return c;
 }
 
+// Whether the tiled kernel can serve these arguments with this tiling.
+bool tiled_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg) {
+    int bxw = 0, byw = 0;
+    return a.precision == SAM_FP32 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 &&
+           (a.nbhd == 1 || a.nbhd == 3) && ((uintptr_t)a.field % 16 == 0) &&
+           (a.count == 1 || a.field_img_px % 2 == 0) && tiled_plan(m->lv[level], cfg.sx, cfg.sy, cfg.tg, &bxw, &byw);
+}
+
 cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
     const ScoreChoice &c = score_choice();
-    int bxw = 0, byw = 0;
-    const bool tiled = c.kernel != 1 && a.precision == SAM_FP32 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 &&
-                       a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) && ((uintptr_t)a.field % 16 == 0) &&
-                       (a.count == 1 || a.field_img_px % 2 == 0) &&
-                       tiled_plan(m->lv[level], c.cfg.sx, c.cfg.sy, c.cfg.tg, &bxw, &byw);
-    if (tiled)
+    TileConfig cfg = c.cfg;
+    if (m->tuned && c.kernel == 0) {
+        cfg.sx = m->tile_sx;
+        cfg.sy = m->tile_sy;
+        cfg.tg = m->tile_tg;
+        cfg.warps = m->tile_warps;
+    }
+    if (c.kernel != 1 && tiled_ok(m, level, a, cfg))
         return launch_score_tiled(m, level, a.field, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px, a.w, a.h,
-                                  a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, err, c.cfg,
-                                  st);
+                                  a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, err, cfg, st);
     return launch_score_map_generic(m->dev[level], a, st);
 }
 
@@ -515,6 +560,115 @@ sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t 
     if (s != SAM_OK)
         return s;
     return read_results(m, P, *params, st, out, capacity, n_out);
+}
+
+sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h, int stride,
+                        const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
+                        int *n_out) {
+    if (!m || !img || count < 1 || stride < w || image_bytes < (size_t)stride * (h - 1) + w || !n_out ||
+        max_out < 0 || (max_out > 0 && (!cfg_out || !ms_out)))
+        return SAM_ERR_ARG;
+    *n_out = 0;
+    sam_status s = check_detect_params(m, params);
+    if (s != SAM_OK)
+        return s;
+    if ((w >> (m->levels - 1)) < 1 || (h >> (m->levels - 1)) < 1)
+        return SAM_ERR_ARG;
+    s = upload_model(m);
+    if (s != SAM_OK)
+        return s;
+    const Plan P = make_plan(m, w, h, count, false, *params);
+    s = ensure_workspace(m, P.total);
+    if (s != SAM_OK)
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    s = prepare_fields(m, P, img, stride, image_bytes, *params, st);
+    if (s != SAM_OK)
+        return s;
+    const ScoreArgs sa = top_score_args(m, P, *params);
+    const int top = P.L - 1;
+    const int nth = m->lv[top].ntheta;
+    const int tgs[] = {1, 3, 5, 9, 15, nth};
+    cudaEvent_t e0, e1;
+    SAM_CU(cudaEventCreate(&e0));
+    SAM_CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    TileConfig bestc;
+    bool found = false;
+    int n = 0;
+    for (int warps : {8, 4})
+        for (int sy = 1; sy <= 2; ++sy)
+            for (int sx = 1; sx <= 3; ++sx)
+                for (int tg : tgs) {
+                    TileConfig c;
+                    c.sx = sx;
+                    c.sy = sy;
+                    c.tg = std::min(tg, nth);
+                    c.warps = warps;
+                    if (!tiled_ok(m, top, sa, c))
+                        continue;
+                    cudaError_t e = launch_score_tiled(m, top, sa.field, field_pitch(sa.w, SAM_LAYOUT_PAIRS),
+                                                       sa.field_img_px, sa.w, sa.h, sa.count, sa.nbhd, sa.polarity,
+                                                       sa.min_score, sa.early, sa.map, sa.map_img, nullptr, c, st);
+                    cudaEventRecord(e0, st);
+                    const int reps = 3;
+                    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                        e = launch_score_tiled(m, top, sa.field, field_pitch(sa.w, SAM_LAYOUT_PAIRS), sa.field_img_px,
+                                               sa.w, sa.h, sa.count, sa.nbhd, sa.polarity, sa.min_score, sa.early,
+                                               sa.map, sa.map_img, nullptr, c, st);
+                    cudaEventRecord(e1, st);
+                    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return SAM_ERR_CUDA;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= reps;
+                    if (n < max_out) {
+                        cfg_out[4 * n] = c.sx;
+                        cfg_out[4 * n + 1] = c.sy;
+                        cfg_out[4 * n + 2] = c.tg;
+                        cfg_out[4 * n + 3] = c.warps;
+                        ms_out[n] = ms;
+                    }
+                    ++n;
+                    if (ms < best) {
+                        best = ms;
+                        bestc = c;
+                        found = true;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *n_out = std::min(n, max_out);
+    if (found) {
+        m->tuned = true;
+        m->tile_sx = bestc.sx;
+        m->tile_sy = bestc.sy;
+        m->tile_tg = bestc.tg;
+        m->tile_warps = bestc.warps;
+    }
+    int dev_err = 0;
+    SAM_CU(score_error_flag_async(&dev_err, st));
+    SAM_CU(cudaStreamSynchronize(st));
+    if (dev_err) {
+        score_error_clear(st);
+        cudaStreamSynchronize(st);
+        return SAM_ERR_TIMEOUT;
+    }
+    return SAM_OK;
+}
+
+sam_status sam_model_tiling(const sam_model *m, int32_t *sx, int32_t *sy, int32_t *tg, int32_t *warps) {
+    if (!m || !sx || !sy || !tg || !warps)
+        return SAM_ERR_ARG;
+    const ScoreChoice &c = score_choice();
+    *sx = m->tuned ? m->tile_sx : c.cfg.sx;
+    *sy = m->tuned ? m->tile_sy : c.cfg.sy;
+    *tg = m->tuned ? m->tile_tg : c.cfg.tg;
+    *warps = m->tuned ? m->tile_warps : c.cfg.warps;
+    return SAM_OK;
 }
 
 sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, uint8_t *dst, int dst_stride,

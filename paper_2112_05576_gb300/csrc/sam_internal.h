@@ -58,6 +58,9 @@ struct sam_model {
     void *d_tables = nullptr;
     sam::LevelDev dev[sam::kMaxLevels];
     sam::Workspace ws;
+    // tiling chosen by sam_autotune for this model (overrides the default)
+    bool tuned = false;
+    int tile_sx = 2, tile_sy = 1, tile_tg = 9, tile_warps = 8;
 };
 
 namespace sam {

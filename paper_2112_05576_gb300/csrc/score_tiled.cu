@@ -324,6 +324,11 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
+    // prefer the largest shared-memory carve-out so window size, not the
+    // L1/shared split, limits resident CTAs
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
     kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
     count_launches(1);
     return cudaGetLastError();

@@ -70,6 +70,9 @@ SIGNATURES = {
     "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
     "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_take_device_error": (_c_int, []),
+    "sam_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams),
+                              _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
+    "sam_model_tiling": (_c_int, [_vp, _i32p, _i32p, _i32p, _i32p]),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
@@ -326,3 +329,24 @@ def candidates_noalloc(smap, min_score, K, out_kyx, out_s, count, stream=None):
     nth, gh, gw = smap.shape
     _check(lib().sam_candidates_noalloc(_ptr(smap), nth, gh, gw, float(min_score), int(K), _ptr(out_kyx),
                                         _ptr(out_s), _ptr(count), _stream(stream)), "sam_candidates_noalloc")
+
+
+def autotune(model: Model, images, params: Optional[DetectParams] = None, stream=None, max_out=256):
+    """Time every tiling of the tiled scorer on a (N, H, W) uint8 CUDA batch and keep
+    the fastest for `model`.  Returns a list of ((sx, sy, tg, warps), ms) sorted by time."""
+    params = params or default_detect_params()
+    N, H, W = images.shape
+    cfg = (ctypes.c_int32 * (4 * max_out))()
+    ms = (ctypes.c_float * max_out)()
+    n = ctypes.c_int()
+    _check(lib().sam_autotune(model.handle, _ptr(images), N, images.stride(0), W, H, images.stride(1),
+                              ctypes.byref(params), _stream(stream), cfg, ms, max_out, ctypes.byref(n)),
+           "sam_autotune")
+    res = [((cfg[4 * i], cfg[4 * i + 1], cfg[4 * i + 2], cfg[4 * i + 3]), float(ms[i])) for i in range(n.value)]
+    return sorted(res, key=lambda r: r[1])
+
+
+def model_tiling(model: Model):
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().sam_model_tiling(model.handle, *[ctypes.byref(x) for x in v]), "sam_model_tiling")
+    return tuple(x.value for x in v)

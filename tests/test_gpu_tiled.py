@@ -142,3 +142,22 @@ def test_tiled_batch_detection_matches_generic():
     for a, b in zip(tiled, generic):
         assert [(d["x"], d["y"], d["k"]) for d in a] == [(d["x"], d["y"], d["k"]) for d in b]
         assert all(abs(x["score"] - y["score"]) < TOL for x, y in zip(a, b))
+
+
+def test_autotune_picks_a_tiling_and_keeps_results():
+    imgs, tm, spec = [], None, None
+    for i in range(2):
+        t, sc, _, spec = synth.config2_scene(seed=7100 + i, spec=spec, W=640, H=512)
+        tm = t if tm is None else tm
+        imgs.append(sc)
+    m = sam.Model(tm, 30, 60, 3, 1.0)
+    p = sam.default_detect_params(min_score=0.6)
+    batch = _dev(np.stack(imgs))
+    sam.set_score_kernel(0)
+    before = sam.detect_batch(m, batch, p)
+    res = sam.autotune(m, batch, p)
+    assert len(res) >= 10 and all(ms > 0 for _, ms in res)
+    assert sam.model_tiling(m) == res[0][0]
+    after = sam.detect_batch(m, batch, p)
+    assert [[(d["x"], d["y"], d["k"]) for d in a] for a in after] == \
+        [[(d["x"], d["y"], d["k"]) for d in b] for b in before]
