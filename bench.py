@@ -248,7 +248,10 @@ def run_gpu(args):
 
     # the project's autotuner picks the scorer's tiling on this workload (setup,
     # outside every timed region)
-    tuning = sam.autotune(model, batches[0], params) if args.autotune else []
+    if args.tiling:
+        sx, sy, tg, wp = (int(v) for v in args.tiling.split(","))
+        sam.set_score_kernel(2, sx, sy, tg, wp)
+    tuning = sam.autotune(model, batches[0], params) if (args.autotune and not args.tiling) else []
 
     def step(i):
         return sam.detect_batch(model, batches[i % pools], params)
@@ -410,6 +413,7 @@ def main():
     ap.add_argument("--early", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
     args = ap.parse_args()

@@ -53,8 +53,8 @@ enum { SAM_FP32 = 0, SAM_BF16 = 1, SAM_FP16 = 2 };
 
 /* Field layouts.  SAM_LAYOUT_PIXEL: each row holds w pixels, each pixel the
  * pair (wx, wy); row pitch w pixels.  SAM_LAYOUT_PAIRS: each row holds pixel
- * pairs {wx_2j, wx_2j+1, wy_2j, wy_2j+1}; row pitch w rounded up to an even
- * number of pixels, the padding pixel (odd w) zero.  Same bytes per pixel. */
+ * pairs {wx_2j, wx_2j+1, wy_2j, wy_2j+1}; row pitch w rounded up to a
+ * multiple of 4 pixels, padding pixels zero.  Same bytes per pixel. */
 enum { SAM_LAYOUT_PIXEL = 0, SAM_LAYOUT_PAIRS = 1 };
 
 typedef struct sam_model sam_model;

@@ -77,10 +77,11 @@ struct Plan {
     size_t off_field[kMaxLevels];    // FP32 fields
     size_t field_px[kMaxLevels];
     size_t off_top = 0;              // top-level field, pairs layout, detection precision
-    size_t top_px = 0;               // its pixels per image (pitch (w+1)&~1, padded to 8)
+    size_t top_px = 0;               // its pixels per image (pairs pitch x h, padded to 8)
     int gw = 0, gh = 0, nth = 0;
     size_t map_img = 0, off_map = 0;
     size_t off_scratch = 0;
+    size_t off_rescore = 0;          // FP32 rescoring list (16-bit precisions)
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
     size_t total = 0;
 };
@@ -115,7 +116,9 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
     const int top = P.L - 1;
     for (int l = 0; l < P.L; ++l) {
         P.off_field[l] = off;
-        if (l < top)   // the top level is scored from its pairs-layout field only
+        // the top level is scored from its pairs-layout field; an FP32 pixel
+        // field is also kept there when the 16-bit map is rescored in FP32
+        if (l < top || p.precision != SAM_FP32)
             off += al(P.field_px[l] * 8 * count);
     }
     P.top_px = ((size_t)field_pitch(P.w[top], SAM_LAYOUT_PAIRS) * P.h[top] + 7) & ~(size_t)7;
@@ -129,6 +132,9 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
     off += al(P.map_img * 4 * count);
     P.off_scratch = off;
     off += al(candidates_scratch_bytes_batch(P.nth, P.gh, P.gw, count));
+    P.off_rescore = off;
+    if (p.precision != SAM_FP32)
+        off += al(rescore_scratch_bytes(P.map_img * count));
     const int K = p.top_k;
     P.off_kyx = off;
     off += al((size_t)3 * K * 4 * count);
@@ -200,7 +206,8 @@ sam_status prepare_fields(sam_model *m, const Plan &P, const uint8_t *img0, int 
     // (a) gradients: FP32 pixel-layout fields for the refinement levels, the
     // top level in the pairs layout and the detection precision
     prof_begin(1, st);
-    for (int l = 0; l < top; ++l)
+    const int nfp32 = p.precision == SAM_FP32 ? top : top + 1;
+    for (int l = 0; l < nfp32; ++l)
         SAM_CU(launch_gradient(lvl_img[l], P.w[l], P.h[l], lvl_pitch[l], lvl_bytes[l], m->p.low, SAM_FP32,
                                SAM_LAYOUT_PIXEL, ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
     SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low, p.precision,
@@ -236,26 +243,15 @@ ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_par
 sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st) {
     char *ws = (char *)m->ws.base;
     const int count = P.count, top = P.L - 1;
-    const void *top_field = ws + P.off_top;
-    // (c) exhaustive top-level score map
-    ScoreArgs sa;
-    sa.field = top_field;
-    sa.field_img_px = P.top_px;
-    sa.layout = SAM_LAYOUT_PAIRS;
-    sa.w = P.w[top];
-    sa.h = P.h[top];
-    sa.precision = p.precision;
-    sa.step_x = p.step_x;
-    sa.step_y = p.step_y;
-    sa.nbhd = p.neighbourhood;
-    sa.polarity = m->p.polarity;
-    sa.min_score = p.min_score;
-    sa.early = p.early_termination;
-    sa.map = (float *)(ws + P.off_map);
-    sa.map_img = P.map_img;
-    sa.count = count;
+    // (c) exhaustive top-level score map; a 16-bit map is rescored in FP32
+    // wherever a pose can reach min_score
+    const ScoreArgs sa = top_score_args(m, P, p);
     prof_begin(2, st);
     SAM_CU(launch_score_map(m, top, sa, nullptr, st));
+    if (p.precision != SAM_FP32)
+        SAM_CU(launch_rescore(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
+                              P.h[top], p.step_x, p.step_y, count, p.neighbourhood, m->p.polarity, p.min_score,
+                              p.precision, sa.map, P.map_img, ws + P.off_rescore, P.map_img * count, st));
     prof_end(2, st);
     // (d) candidates, refinement, NMS
     const int K = p.top_k;
@@ -349,9 +345,15 @@ ScoreChoice &score_choice() {
 // Whether the tiled kernel can serve these arguments with this tiling.
 bool tiled_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg) {
     int bxw = 0, byw = 0;
-    return a.precision == SAM_FP32 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 &&
-           (a.nbhd == 1 || a.nbhd == 3) && ((uintptr_t)a.field % 16 == 0) &&
-           (a.count == 1 || a.field_img_px % 2 == 0) && tiled_plan(m->lv[level], cfg.sx, cfg.sy, cfg.tg, &bxw, &byw);
+    return a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
+           ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) &&
+           tiled_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw);
+}
+
+cudaError_t launch_tiled_args(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg,
+                              cudaStream_t st) {
+    return launch_score_tiled(m, level, a.field, a.precision, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px, a.w,
+                              a.h, a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st);
 }
 
 cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
@@ -363,9 +365,9 @@ cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, 
         cfg.tg = m->tile_tg;
         cfg.warps = m->tile_warps;
     }
+    (void)err;
     if (c.kernel != 1 && tiled_ok(m, level, a, cfg))
-        return launch_score_tiled(m, level, a.field, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px, a.w, a.h,
-                                  a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, err, cfg, st);
+        return launch_tiled_args(m, level, a, cfg, st);
     return launch_score_map_generic(m->dev[level], a, st);
 }
 
@@ -607,15 +609,11 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                     c.warps = warps;
                     if (!tiled_ok(m, top, sa, c))
                         continue;
-                    cudaError_t e = launch_score_tiled(m, top, sa.field, field_pitch(sa.w, SAM_LAYOUT_PAIRS),
-                                                       sa.field_img_px, sa.w, sa.h, sa.count, sa.nbhd, sa.polarity,
-                                                       sa.min_score, sa.early, sa.map, sa.map_img, nullptr, c, st);
+                    cudaError_t e = launch_tiled_args(m, top, sa, c, st);
                     cudaEventRecord(e0, st);
                     const int reps = 3;
                     for (int r = 0; r < reps && e == cudaSuccess; ++r)
-                        e = launch_score_tiled(m, top, sa.field, field_pitch(sa.w, SAM_LAYOUT_PAIRS), sa.field_img_px,
-                                               sa.w, sa.h, sa.count, sa.nbhd, sa.polarity, sa.min_score, sa.early,
-                                               sa.map, sa.map_img, nullptr, c, st);
+                        e = launch_tiled_args(m, top, sa, c, st);
                     cudaEventRecord(e1, st);
                     if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                         cudaEventDestroy(e0);

@@ -220,9 +220,10 @@ __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__res
         gys[j] = gy;
     }
     if (LAYOUT == SAM_LAYOUT_PAIRS) {
-        // pixels beyond w were computed as zero, so the padding pixel of an
-        // odd-width row is written as zero too
-        const int wp = (w + 1) & ~1;
+        // pixels beyond w were computed as zero, so the padding pixels up to
+        // the row pitch (a multiple of 4, at most the thread's 8-pixel group
+        // end) are written as zero too
+        const int wp = field_pitch(w, SAM_LAYOUT_PAIRS);
         const size_t q0 = ((size_t)im * field_img_px + (size_t)y * wp + xb) >> 1;
         const bool full = (xb + GPT <= wp) && vec;
 #pragma unroll

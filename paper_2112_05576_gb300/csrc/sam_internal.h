@@ -81,9 +81,11 @@ cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t
                             int layout, void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
                             cudaStream_t st);
 // Field layouts: SAM_LAYOUT_PIXEL rows of w (wx, wy) pairs; SAM_LAYOUT_PAIRS
-// rows of (w+1)/2 pixel pairs {wx0, wx1, wy0, wy1} (row pitch w rounded up to
-// even pixels, the padding pixel zero).
-inline int field_pitch(int w, int layout) { return layout == SAM_LAYOUT_PAIRS ? ((w + 1) & ~1) : w; }
+// rows of pixel pairs {wx0, wx1, wy0, wy1}, row pitch w rounded up to a
+// multiple of 4 pixels (16-byte rows in every precision), padding pixels zero.
+__host__ __device__ inline int field_pitch(int w, int layout) {
+    return layout == SAM_LAYOUT_PAIRS ? ((w + 3) & ~3) : w;
+}
 
 // (c) exhaustive score map of one level for `count` fields
 struct ScoreArgs {
@@ -109,10 +111,10 @@ struct TileConfig {
     int tg = 9;           // angles per CTA
     int warps = 8;        // warps per CTA (4 or 8)
 };
-bool tiled_plan(const LevelHost &L, int sx, int sy, int tg, int *bxw, int *byw);
-cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int wp, size_t field_img_px, int W,
-                               int H, int count, int nbhd, int polarity, float min_score, int early, float *map,
-                               size_t map_img, int *err, const TileConfig &cfg, cudaStream_t st);
+bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *bxw, int *byw);
+cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
+                               size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
+                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st);
 
 // Score-kernel selection (process-wide; sam_set_score_kernel).
 struct ScoreChoice {
@@ -126,6 +128,15 @@ cudaError_t score_error_clear(cudaStream_t st);
 // Dispatch: tiled when allowed and possible, else generic.  `err` may be
 // null (then the tiled kernel reports into a library-owned flag).
 cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st);
+
+// FP32 rescoring of a map computed from a 16-bit field (rescore.cu): poses
+// within the storage-error bound of min_score get their FP32 score, all
+// others -inf.  scratch: rescore_scratch_bytes(poses_cap).
+float rescore_delta(int precision);
+size_t rescore_scratch_bytes(size_t poses);
+cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h, int step_x,
+                           int step_y, int count, int nbhd, int polarity, float min_score, int precision, float *map,
+                           size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {

@@ -4,32 +4,38 @@
 // window).
 //
 // Work decomposition.  A CTA owns a super-tile of translations (SX x SY warp
-// tiles of 48 x 32 poses) of one image and a group of TG consecutive angles.
-// One TMA load stages the w_hat window that every (angle, pose, point,
-// neighbour) of the CTA can touch -- the super-tile grown by the union of the
-// group's rotated offset bounding boxes and the 1-pixel search halo -- into
-// shared memory; pixels outside the image arrive as zeros, which is exactly
-// Eq. (1)'s contribution of a missing edge.  Warps then loop over (angle,
-// warp tile) items.
+// tiles) of one image and a group of TG consecutive angles.  One TMA load
+// stages the w_hat window that every (angle, pose, point, neighbour) of the
+// CTA can touch -- the super-tile grown by the union of the group's rotated
+// offset bounding boxes and the 1-pixel search halo -- into shared memory;
+// pixels outside the image arrive as zeros, which is exactly Eq. (1)'s
+// contribution of a missing edge.  Warps then loop over (angle, warp tile)
+// items.
 //
 // Register blocking.  A thread owns an R x C = 8 x 6 block of poses.  For one
 // model point the block's 3x3 windows cover (R+2) x (C+2) pixels; each pixel's
 // dot product with the point's direction is computed once (packed FP32x2 FMA
 // on a pixel pair) and shared by the up to nine poses whose windows hold it,
 // the 3x3 maximum is taken separably with 3-input max, and the result is
-// accumulated in FP32 (packed adds).  Per pose-point: ~0.9 shared loads,
+// accumulated in FP32 (packed adds).  Per pose-point: ~0.94 shared loads,
 // ~1.9 FMA-pipe instructions for the dots, 2.25 max, 0.5 add.
 //
-// Field layout (pixel pairs).  The window is FP32 with pixels 2j, 2j+1 of a
-// row stored as {wx_2j, wx_2j+1, wy_2j, wy_2j+1} (16 bytes), so one 128-bit
-// shared load feeds one packed FMA pair.  Lanes are laid out 8 along x and 4
-// along y; the 8 lanes of a quarter-warp start 3 pixel pairs apart, so their
-// 128-bit loads fall in 8 distinct 16-byte bank groups.
+// Field layout (pixel pairs).  Pixels 2j, 2j+1 of a row are stored together
+// as {wx_2j, wx_2j+1, wy_2j, wy_2j+1}: 16 bytes in FP32, 8 bytes in FP16 or
+// BF16 (converted to FP32 after the load; arithmetic and accumulation stay
+// FP32).  The shared-memory traffic is the kernel's bound (about 15 bytes per
+// pose-point in FP32, 7.5 in 16-bit storage), so lanes are laid out to keep
+// the loads conflict-free: FP32 uses 128-bit loads with 8 lanes along x, a
+// quarter-warp's lanes starting 3 pairs apart (8 distinct 16-byte slots);
+// 16-bit storage uses 64-bit loads with 16 lanes along x, a half-warp's lanes
+// starting 3 pairs apart (16 distinct 8-byte slots).
 //
 // Early termination (exact-safe, see kernels_score.cu): every 32 points a warp
 // abandons its tile when every pose's partial sum proves M < min_score.
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,11 +53,49 @@ __device__ int g_score_err;
 namespace {
 
 constexpr int TR = 8;            // rows of poses per thread
-constexpr int TC = 6;            // columns of poses per thread (TC/2 odd: bank-conflict-free 128-bit loads)
-constexpr int LX = 8, LY = 4;    // lanes along x, y
-constexpr int WTX = LX * TC;     // warp tile: 48 x 32 poses
-constexpr int WTY = LY * TR;
+constexpr int TC = 6;            // columns of poses per thread (TC/2 odd: conflict-free loads)
 constexpr int PRUNE_EVERY = 32;
+
+// Stored element type of the window: pair size, lane layout, TMA alignment.
+template <typename E>
+struct Pairs;
+
+template <>
+struct Pairs<float> {
+    using Raw = float4;
+    static constexpr int BYTES = 16;   // one pixel pair
+    static constexpr int LX = 8;       // lanes along x
+    static constexpr int XALIGN = 2;   // window start (pixels) for a 16-byte TMA start
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) { return row[q]; }
+};
+
+template <>
+struct Pairs<__half> {
+    using Raw = uint2;
+    static constexpr int BYTES = 8;
+    static constexpr int LX = 16;
+    static constexpr int XALIGN = 4;
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) {
+        const uint2 u = row[q];
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
+template <>
+struct Pairs<__nv_bfloat16> {
+    using Raw = uint2;
+    static constexpr int BYTES = 8;
+    static constexpr int LX = 16;
+    static constexpr int XALIGN = 4;
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) {
+        const uint2 u = row[q];
+        // bf16 -> fp32 is a 16-bit left shift of the bit pattern
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+    }
+};
 
 struct TiledArgs {
     const RotPt *rot;     // [nth][n]
@@ -66,10 +110,7 @@ struct TiledArgs {
     float inv_n;
     float thresh;
     int early;
-    int polarity;
 };
-
-
 
 __device__ __forceinline__ float max3(float a, float b, float c) {
     float d;
@@ -96,13 +137,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-template <int NB, bool POL>
-__device__ __forceinline__ void dots_row(const float4 *row, int pair0, float (&d)[TC + 4], int npairs,
-                                         float2 pxx, float2 pyy) {
+// Dot products of npairs pixel pairs of one window row with the point's
+// direction (px, py), packed FP32x2.
+template <typename E, bool POL>
+__device__ __forceinline__ void dots_row(const typename Pairs<E>::Raw *row, int pair0, float (&d)[TC + 4],
+                                         int npairs, float2 pxx, float2 pyy) {
 #pragma unroll
     for (int q = 0; q < (TC + 4) / 2; ++q) {
         if (q < npairs) {
-            const float4 v = row[pair0 + q];
+            const float4 v = Pairs<E>::get(row, pair0 + q);
             float2 t = __fmul2_rn(pxx, make_float2(v.x, v.y));
             t = __ffma2_rn(pyy, make_float2(v.z, v.w), t);
             d[2 * q] = POL ? fabsf(t.x) : t.x;
@@ -112,17 +155,17 @@ __device__ __forceinline__ void dots_row(const float4 *row, int pair0, float (&d
 }
 
 // One model point over the thread's R x C pose block, 3x3 neighbourhood.
-template <bool POL, bool ODD>
-__device__ __forceinline__ void point_nb3(const float4 *win, int pp, int row0, int pair0, float2 pxx, float2 pyy,
-                                          float2 (&acc)[TR][TC / 2]) {
+template <typename E, bool POL, bool ODD>
+__device__ __forceinline__ void point_nb3(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
+                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
     constexpr int NP = ODD ? (TC + 4) / 2 : (TC + 2) / 2;   // pixel pairs per row
     constexpr int OFF = ODD ? 1 : 0;
     float hp2[TC], hp1[TC];
 #pragma unroll
     for (int r = 0; r < TR + 2; ++r) {
-        const float4 *row = win + (row0 + r) * pp;
+        const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
         float d[TC + 4];
-        dots_row<3, POL>(row, pair0, d, NP, pxx, pyy);
+        dots_row<E, POL>(row, pair0, d, NP, pxx, pyy);
         float h[TC];
 #pragma unroll
         for (int c = 0; c < TC; ++c)
@@ -144,15 +187,15 @@ __device__ __forceinline__ void point_nb3(const float4 *win, int pp, int row0, i
 }
 
 // One model point, neighbourhood 1 (no search): the centre pixel only.
-template <bool POL, bool ODD>
-__device__ __forceinline__ void point_nb1(const float4 *win, int pp, int row0, int pair0, float2 pxx, float2 pyy,
-                                          float2 (&acc)[TR][TC / 2]) {
+template <typename E, bool POL, bool ODD>
+__device__ __forceinline__ void point_nb1(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
+                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
     constexpr int NP = ODD ? (TC + 2) / 2 : TC / 2;
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
-        const float4 *row = win + (row0 + r) * pp;
+        const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
         float d[TC + 4];
-        dots_row<1, POL>(row, pair0, d, NP, pxx, pyy);
+        dots_row<E, POL>(row, pair0, d, NP, pxx, pyy);
 #pragma unroll
         for (int j = 0; j < TC / 2; ++j) {
             if (ODD)
@@ -163,14 +206,17 @@ __device__ __forceinline__ void point_nb1(const float4 *win, int pp, int row0, i
     }
 }
 
-template <int NB, bool POL, int WARPS>
+template <typename E, int NB, bool POL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TiledArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: round the base up (the
     // launch adds 128 bytes of slack)
     const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
-    float4 *win = reinterpret_cast<float4 *>(smem_raw + pad);
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_org[2];   // window origin (pixel x, row y), global coords
 
@@ -191,18 +237,21 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
             xmin = min(xmin, b.x);
             ymin = min(ymin, b.z);
         }
-        const int wx0 = (stx0 + xmin - 1) & ~1;   // even: 16-byte aligned TMA start
+        // aligned start: the TMA x coordinate times the element size must be a
+        // multiple of 16 bytes
+        const int wx0 = (stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
         const int wy0 = sty0 + ymin - 1;
         s_org[0] = wx0;
         s_org[1] = wy0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * 8u;
+        const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const int xe = wx0 * Pairs<E>::BYTES / 16;   // 8-byte elements
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
             "[%5];" ::"r"(smem_addr(win)),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(wx0), "r"(wy0), "r"(img), "r"(bar)
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(img), "r"(bar)
             : "memory");
     }
     __syncthreads();
@@ -214,7 +263,7 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     const int wx0 = s_org[0], wy0 = s_org[1];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lx = lane & (LX - 1), ly = lane >> 3;
+    const int lx = lane % LX, ly = lane / LX;
     const int items = (k_end - k_begin) * a.sx * a.sy;
     float *map = a.map + (size_t)img * a.map_img;
 
@@ -245,16 +294,16 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
                 const int xs = bx + cur.ox;   // first pixel column (>= 0)
                 const int row0 = by + cur.oy;
                 if (xs & 1)
-                    point_nb3<POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    point_nb3<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
                 else
-                    point_nb3<POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                    point_nb3<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
             } else {
                 const int xs = bx + 1 + cur.ox;   // centre column
                 const int row0 = by + 1 + cur.oy;
                 if (xs & 1)
-                    point_nb1<POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    point_nb1<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
                 else
-                    point_nb1<POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                    point_nb1<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
             }
             if (a.early && ((i + 1) % PRUNE_EVERY) == 0) {
                 const float lim = a.thresh - (float)(a.n - 1 - i);
@@ -318,9 +367,19 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <int NB, bool POL, int WARPS>
+struct Geometry {
+    int wtx, wty, xalign, pair_bytes;
+};
+
+Geometry geometry(int precision) {
+    if (precision == SAM_FP32)
+        return {Pairs<float>::LX * TC, (32 / Pairs<float>::LX) * TR, Pairs<float>::XALIGN, Pairs<float>::BYTES};
+    return {Pairs<__half>::LX * TC, (32 / Pairs<__half>::LX) * TR, Pairs<__half>::XALIGN, Pairs<__half>::BYTES};
+}
+
+template <typename E, int NB, bool POL, int WARPS>
 cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
-    auto kern = score_tiled_kernel<NB, POL, WARPS>;
+    auto kern = score_tiled_kernel<E, NB, POL, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -334,12 +393,26 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
     return cudaGetLastError();
 }
 
+template <typename E>
+cudaError_t launch_e(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                     int warps, cudaStream_t st) {
+    if (warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_t<E, 3, true, 4>(tm, a, grid, smem, st) : launch_t<E, 3, false, 4>(tm, a, grid, smem, st);
+        return pol ? launch_t<E, 1, true, 4>(tm, a, grid, smem, st) : launch_t<E, 1, false, 4>(tm, a, grid, smem, st);
+    }
+    if (nbhd == 3)
+        return pol ? launch_t<E, 3, true, 8>(tm, a, grid, smem, st) : launch_t<E, 3, false, 8>(tm, a, grid, smem, st);
+    return pol ? launch_t<E, 1, true, 8>(tm, a, grid, smem, st) : launch_t<E, 1, false, 8>(tm, a, grid, smem, st);
+}
+
 }  // namespace
 
 // Window box for a tiling: the super-tile grown by the largest union of
-// rotated offset boxes over any angle group, the 1-pixel search halo, one
-// pixel of slack for the even TMA start and one for odd-start pair loads.
-bool tiled_plan(const LevelHost &L, int sx, int sy, int tg, int *bxw, int *byw) {
+// rotated offset boxes over any angle group, the 1-pixel search halo, the
+// slack of the aligned TMA start and one pixel for odd-start pair loads.
+bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *bxw, int *byw) {
+    const Geometry g = geometry(precision);
     int spx = 0, spy = 0;
     for (int k0 = 0; k0 < L.ntheta; k0 += tg) {
         int x0 = 1 << 30, x1 = -(1 << 30), y0 = 1 << 30, y1 = -(1 << 30);
@@ -352,30 +425,34 @@ bool tiled_plan(const LevelHost &L, int sx, int sy, int tg, int *bxw, int *byw) 
         spx = std::max(spx, x1 - x0);
         spy = std::max(spy, y1 - y0);
     }
-    int bx = sx * WTX + spx + 4;
-    bx = (bx + 1) & ~1;
-    const int by = sy * WTY + spy + 2;
+    int bx = sx * g.wtx + spx + 2 + (g.xalign - 1) + 1;
+    bx = (bx + g.xalign - 1) / g.xalign * g.xalign;
+    const int by = sy * g.wty + spy + 2;
     *bxw = bx;
     *byw = by;
-    return bx <= 256 && by <= 256 && (size_t)bx * by * 8 <= 200 * 1024;
+    const size_t bytes = (size_t)bx * by * g.pair_bytes / 2;
+    return bx * g.pair_bytes / 16 <= 256 && by <= 256 && bytes <= 200 * 1024;
 }
 
-// Launch over `count` images whose paired FP32 fields start at `field`
-// (row pitch wp pixels, image stride field_img_px pixels).
-cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int wp, size_t field_img_px, int W,
-                               int H, int count, int nbhd, int polarity, float min_score, int early, float *map,
-                               size_t map_img, int *err, const TileConfig &cfg, cudaStream_t st) {
+// Launch over `count` images whose pairs-layout fields start at `field`
+// (row pitch wp pixels, a multiple of 4; image stride field_img_px pixels).
+cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
+                               size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
+                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st) {
     const LevelHost &L = m->lv[level];
     int bxw = 0, byw = 0;
-    if (!tiled_plan(L, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw))
+    if (!tiled_plan(L, precision, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw))
         return cudaErrorInvalidValue;
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return cudaErrorNotSupported;
+    const Geometry g = geometry(precision);
+    // the field as a 3-D tensor of 8-byte elements: a pixel pair is 2 (FP32)
+    // or 1 (16-bit) element(s)
     CUtensorMap tm;
-    const cuuint64_t dims[3] = {(cuuint64_t)wp, (cuuint64_t)H, (cuuint64_t)count};
-    const cuuint64_t strides[2] = {(cuuint64_t)wp * 8, (cuuint64_t)field_img_px * 8};
-    const cuuint32_t box[3] = {(cuuint32_t)bxw, (cuuint32_t)byw, 1};
+    const cuuint64_t dims[3] = {(cuuint64_t)wp * g.pair_bytes / 16, (cuuint64_t)H, (cuuint64_t)count};
+    const cuuint64_t strides[2] = {(cuuint64_t)wp * g.pair_bytes / 2, (cuuint64_t)field_img_px * g.pair_bytes / 2};
+    const cuuint32_t box[3] = {(cuuint32_t)(bxw * g.pair_bytes / 16), (cuuint32_t)byw, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(field), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -393,28 +470,24 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.sx = cfg.sx;
     a.sy = cfg.sy;
     a.tg = cfg.tg;
-    a.tiles_x = (W + cfg.sx * WTX - 1) / (cfg.sx * WTX);
-    const int tiles_y = (H + cfg.sy * WTY - 1) / (cfg.sy * WTY);
+    a.tiles_x = (W + cfg.sx * g.wtx - 1) / (cfg.sx * g.wtx);
+    const int tiles_y = (H + cfg.sy * g.wty - 1) / (cfg.sy * g.wty);
     a.bxw = bxw;
     a.byw = byw;
     a.inv_n = 1.0f / (float)L.n;
-    a.thresh = prune_threshold(L.n, min_score, SAM_FP32);
+    a.thresh = prune_threshold(L.n, min_score, precision);
     a.early = early;
-    a.polarity = polarity;
-    (void)err;
     const int groups = (L.ntheta + cfg.tg - 1) / cfg.tg;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)groups, (unsigned)count);
-    const size_t smem = (size_t)bxw * byw * 8 + 128;
+    const size_t smem = (size_t)bxw * byw * g.pair_bytes / 2 + 128;
     const bool pol = polarity != 0;
-    switch (cfg.warps) {
-    case 4:
-        if (nbhd == 3)
-            return pol ? launch_t<3, true, 4>(tm, a, grid, smem, st) : launch_t<3, false, 4>(tm, a, grid, smem, st);
-        return pol ? launch_t<1, true, 4>(tm, a, grid, smem, st) : launch_t<1, false, 4>(tm, a, grid, smem, st);
+    switch (precision) {
+    case SAM_FP32:
+        return launch_e<float>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    case SAM_FP16:
+        return launch_e<__half>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
     default:
-        if (nbhd == 3)
-            return pol ? launch_t<3, true, 8>(tm, a, grid, smem, st) : launch_t<3, false, 8>(tm, a, grid, smem, st);
-        return pol ? launch_t<1, true, 8>(tm, a, grid, smem, st) : launch_t<1, false, 8>(tm, a, grid, smem, st);
+        return launch_e<__nv_bfloat16>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
     }
 }
 

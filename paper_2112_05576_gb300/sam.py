@@ -261,7 +261,7 @@ def pyramid_down(src, dst, stream=None):
 
 def field_pitch(w, layout):
     """Row pitch in pixels of a field of width w in the given layout."""
-    return (w + 1) & ~1 if layout == LAYOUT_PAIRS else w
+    return (w + 3) & ~3 if layout == LAYOUT_PAIRS else w
 
 
 def gradient(img, low, precision, field, gx=None, gy=None, stream=None, layout=None):
