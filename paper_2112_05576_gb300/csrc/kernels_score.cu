@@ -54,7 +54,11 @@ __global__ void __launch_bounds__(256)
                 float v = 0.f;
                 if (x >= 0 && y >= 0 && x < w && y < h) {
                     const float2 f = load_field<E, LAYOUT>(field, pitch, x, y);
-                    v = fmaf(p.px, f.x, p.py * f.y);
+                    // FP16 fields: the direction is rounded to FP16 too and
+                    // the product px*wx is exact, matching the tiled kernel's
+                    // mixed-precision FMA bit for bit
+                    const float px = dir_round<E>(p.px), py = dir_round<E>(p.py);
+                    v = fmaf(py, f.y, px * f.x);
                     if (polarity)
                         v = fabsf(v);
                 }

@@ -1,9 +1,11 @@
 // FP32 rescoring of a score map computed from a 16-bit stored field.
 //
 // A unit vector stored in FP16 (BF16) moves each component by at most 2^-12
-// (2^-9), so each Eq. (1) term moves by at most sqrt(2) times that and the
-// score M -- a mean of per-point maxima of such terms -- by at most
-// delta = 3.5e-4 (2.8e-3), plus FP32 rounding.  After the exhaustive 16-bit
+// (2^-9), so each Eq. (1) term moves by at most sqrt(2) times that; FP16
+// scoring also rounds the point direction to FP16, doubling its bound.  The
+// score M -- a mean of per-point maxima of such terms -- therefore moves by at
+// most delta = 6.9e-4 (FP16) or 2.8e-3 (BF16), plus FP32 rounding.  After the
+// exhaustive 16-bit
 // search, every pose with M16 >= min_score - delta is therefore rescored from
 // the FP32 field, and every other pose (including poses the 16-bit kernel
 // pruned) is provably below min_score in FP32 and is written -inf.  Candidate
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float2 *__restrict__
 
 float rescore_delta(int precision) {
     // storage error bound of M plus FP32 rounding slack
-    return precision == SAM_FP16 ? 4e-4f : (precision == SAM_BF16 ? 3e-3f : 0.f);
+    return precision == SAM_FP16 ? 8e-4f : (precision == SAM_BF16 ? 3e-3f : 0.f);
 }
 
 size_t rescore_scratch_bytes(size_t poses) { return 256 + poses * 8; }

@@ -24,7 +24,19 @@ __device__ __forceinline__ float2 load_field(const E *f, int pitch, int x, int y
     return make_float2(to_f32(__ldg(f + i)), to_f32(__ldg(f + i + 1)));
 }
 
-// Per-term error bound of the stored unit field (component rounding).
+// The point direction as the scoring arithmetic sees it: FP16 fields are
+// scored with FP16 directions (mixed-precision FMA), others in FP32.
+template <typename E>
+__device__ __forceinline__ float dir_round(float v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float dir_round<__half>(float v) {
+    return __half2float(__float2half_rn(v));
+}
+
+// Per-term error bound of the stored unit field (component rounding; FP16
+// also rounds the direction: 2 sqrt(2) 2^-12 < 7e-4; BF16: sqrt(2) 2^-9).
 inline float term_eps(int precision) {
     return precision == SAM_FP32 ? 1e-6f : (precision == SAM_FP16 ? 1e-3f : 4e-3f);
 }

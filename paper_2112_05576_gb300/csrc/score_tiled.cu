@@ -139,17 +139,49 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Dot products of npairs pixel pairs of one window row with the point's
 // direction (px, py), packed FP32x2.
+// Dot products of one pixel pair with the point direction.  FP32 and BF16
+// storage: FP32 components (BF16 widened exactly), packed FP32x2 FMA.  FP16
+// storage: mixed-precision FMA, the FP16 products formed exactly and
+// accumulated in FP32, with the direction rounded to FP16 as well (per-term
+// error at most 2 sqrt(2) 2^-12 < 7e-4 against exact arithmetic), which saves
+// the two conversions per half-pair.
+template <typename E>
+struct PairDot {
+    static __device__ __forceinline__ void run(const typename Pairs<E>::Raw *row, int q, float2 pxx, float2 pyy,
+                                               float &d0, float &d1) {
+        const float4 v = Pairs<E>::get(row, q);
+        float2 t = __fmul2_rn(pxx, make_float2(v.x, v.y));
+        t = __ffma2_rn(pyy, make_float2(v.z, v.w), t);
+        d0 = t.x;
+        d1 = t.y;
+    }
+};
+
+template <>
+struct PairDot<__half> {
+    static __device__ __forceinline__ void run(const uint2 *row, int q, float2 pxx, float2 pyy, float &d0,
+                                               float &d1) {
+        const uint2 u = row[q];
+        const unsigned short ph = __half_as_ushort(__float2half_rn(pxx.x));
+        const unsigned short qh = __half_as_ushort(__float2half_rn(pyy.x));
+        asm("{\n .reg .b16 x0, x1, y0, y1;\n .reg .f32 t0, t1;\n mov.b32 {x0, x1}, %2;\n mov.b32 {y0, y1}, %3;\n"
+            " fma.rn.f32.f16 t0, %4, x0, 0f00000000;\n fma.rn.f32.f16 t1, %4, x1, 0f00000000;\n"
+            " fma.rn.f32.f16 %0, %5, y0, t0;\n fma.rn.f32.f16 %1, %5, y1, t1;\n}"
+            : "=f"(d0), "=f"(d1)
+            : "r"(u.x), "r"(u.y), "h"(ph), "h"(qh));
+    }
+};
+
 template <typename E, bool POL>
 __device__ __forceinline__ void dots_row(const typename Pairs<E>::Raw *row, int pair0, float (&d)[TC + 4],
                                          int npairs, float2 pxx, float2 pyy) {
 #pragma unroll
     for (int q = 0; q < (TC + 4) / 2; ++q) {
         if (q < npairs) {
-            const float4 v = Pairs<E>::get(row, pair0 + q);
-            float2 t = __fmul2_rn(pxx, make_float2(v.x, v.y));
-            t = __ffma2_rn(pyy, make_float2(v.z, v.w), t);
-            d[2 * q] = POL ? fabsf(t.x) : t.x;
-            d[2 * q + 1] = POL ? fabsf(t.y) : t.y;
+            float d0, d1;
+            PairDot<E>::run(row, pair0 + q, pxx, pyy, d0, d1);
+            d[2 * q] = POL ? fabsf(d0) : d0;
+            d[2 * q + 1] = POL ? fabsf(d1) : d1;
         }
     }
 }
