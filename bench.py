@@ -323,6 +323,39 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     single_ms = s0.elapsed_time(s1) / n_single
 
+    # ---- the 16-bit stored forms on the same batches (own tiling, FP32 rescoring) ----
+    forms = {}
+    if args.precision == "fp32" and args.forms:
+        ref_dets = {i: step(i) for i in range(pools)}
+        for name, code in (("fp16", 2), ("bf16", 1)):
+            fp = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
+                                           precision=code, early_termination=1 if args.early else 0)
+            if args.autotune and not args.tiling:
+                sam.autotune(model, batches[0], fp)
+            same = all([(d["x"], d["y"], d["k"]) for d in a] == [(d["x"], d["y"], d["k"]) for d in b]
+                       for i in range(pools)
+                       for a, b in zip(sam.detect_batch(model, batches[i], fp), ref_dets[i]))
+            n_form = max(10, min(50, args.steps))
+            for i in range(3):
+                sam.detect_batch(model, batches[i % pools], fp)
+            sam.profile_enable(True)
+            sam.profile_read()
+            torch.cuda.synchronize(dev)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for i in range(n_form):
+                sam.detect_batch(model, batches[i % pools], fp)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            pf = sam.profile_read()
+            sam.profile_enable(False)
+            fms = f0.elapsed_time(f1) / n_form
+            forms[name] = {"value": top_pose_points(model, B) / (fms * 1e-3), "ms_per_step": round(fms, 4),
+                           "ms_per_detection": round(fms / B, 5),
+                           "score_map_ms": round(pf["score_map"][0] / max(1, pf["score_map"][1]), 4),
+                           "same_detections_as_fp32": bool(same), "steps": n_form,
+                           "tiling": dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model, code)))}
+
     # ---- the scorer with every pose fully evaluated (no early termination) ----
     full_params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
                                             precision=params.precision, early_termination=0)
@@ -357,7 +390,7 @@ def run_gpu(args):
     rl["no_early_termination"] = {"ms_per_launch": round(fms / max(1, fcalls), 4), "achieved": rl_full["achieved"],
                                   "frac": rl_full["frac"]}
     rl["ms_per_launch"] = round(score_ms / max(1, score_calls), 4)
-    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model)))
+    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model, params.precision)))
     rl["tiling"]["autotuned"] = bool(tuning)
     if tuning:
         rl["tiling"]["candidates"] = len(tuning)
@@ -393,6 +426,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "detections_per_image": ndet[:8],
+        "forms": forms,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -413,6 +447,7 @@ def main():
     ap.add_argument("--early", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--forms", type=int, default=1, help="also time the FP16/BF16 stored forms")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")

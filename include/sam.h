@@ -225,16 +225,19 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps);
  * every tiling of its candidate set (super-tile 1..3 x 1..2 warp tiles,
  * angles per CTA 1, 3, 5, 9, 15 or all, 4 or 8 warps; tilings whose window
  * does not fit are skipped) using CUDA events on `stream`, and keeps the
- * fastest for this model (used by later calls while sam_set_score_kernel
- * selects 0, automatic).  Optional outputs: cfg_out[4 i ..] = (sx, sy, tg,
+ * fastest for this model and this field precision (used by later calls with
+ * that precision while sam_set_score_kernel selects 0, automatic).  Optional
+ * outputs: cfg_out[4 i ..] = (sx, sy, tg,
  * warps) and ms_out[i] of up to max_out candidates; *n_out = how many were
  * written.  Uses the model's workspace; synchronises `stream`.
  * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT. */
 sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h, int stride,
                         const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
                         int *n_out);
-/* The tiling the model's next calls will use (tuned, else the default). */
-sam_status sam_model_tiling(const sam_model *m, int32_t *sx, int32_t *sy, int32_t *tg, int32_t *warps);
+/* The tiling the model's next calls with field `precision` will use (tuned,
+ * else the default). */
+sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
+                            int32_t *warps);
 /* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
  * clears it if any wait gave up since the last call (synchronises the
  * device). */

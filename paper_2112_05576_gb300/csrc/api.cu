@@ -359,11 +359,12 @@ cudaError_t launch_tiled_args(const sam_model *m, int level, const ScoreArgs &a,
 cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
     const ScoreChoice &c = score_choice();
     TileConfig cfg = c.cfg;
-    if (m->tuned && c.kernel == 0) {
-        cfg.sx = m->tile_sx;
-        cfg.sy = m->tile_sy;
-        cfg.tg = m->tile_tg;
-        cfg.warps = m->tile_warps;
+    const int pr = a.precision;
+    if (m->tuned[pr] && c.kernel == 0) {
+        cfg.sx = m->tile_sx[pr];
+        cfg.sy = m->tile_sy[pr];
+        cfg.tg = m->tile_tg[pr];
+        cfg.warps = m->tile_warps[pr];
     }
     (void)err;
     if (c.kernel != 1 && tiled_ok(m, level, a, cfg))
@@ -641,11 +642,12 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     cudaEventDestroy(e1);
     *n_out = std::min(n, max_out);
     if (found) {
-        m->tuned = true;
-        m->tile_sx = bestc.sx;
-        m->tile_sy = bestc.sy;
-        m->tile_tg = bestc.tg;
-        m->tile_warps = bestc.warps;
+        const int pr = params->precision;
+        m->tuned[pr] = true;
+        m->tile_sx[pr] = bestc.sx;
+        m->tile_sy[pr] = bestc.sy;
+        m->tile_tg[pr] = bestc.tg;
+        m->tile_warps[pr] = bestc.warps;
     }
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
@@ -658,14 +660,16 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     return SAM_OK;
 }
 
-sam_status sam_model_tiling(const sam_model *m, int32_t *sx, int32_t *sy, int32_t *tg, int32_t *warps) {
-    if (!m || !sx || !sy || !tg || !warps)
+sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
+                            int32_t *warps) {
+    if (!m || !sx || !sy || !tg || !warps || precision < SAM_FP32 || precision > SAM_FP16)
         return SAM_ERR_ARG;
     const ScoreChoice &c = score_choice();
-    *sx = m->tuned ? m->tile_sx : c.cfg.sx;
-    *sy = m->tuned ? m->tile_sy : c.cfg.sy;
-    *tg = m->tuned ? m->tile_tg : c.cfg.tg;
-    *warps = m->tuned ? m->tile_warps : c.cfg.warps;
+    const bool t = m->tuned[precision];
+    *sx = t ? m->tile_sx[precision] : c.cfg.sx;
+    *sy = t ? m->tile_sy[precision] : c.cfg.sy;
+    *tg = t ? m->tile_tg[precision] : c.cfg.tg;
+    *warps = t ? m->tile_warps[precision] : c.cfg.warps;
     return SAM_OK;
 }
 

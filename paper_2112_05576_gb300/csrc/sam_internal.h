@@ -58,9 +58,10 @@ struct sam_model {
     void *d_tables = nullptr;
     sam::LevelDev dev[sam::kMaxLevels];
     sam::Workspace ws;
-    // tiling chosen by sam_autotune for this model (overrides the default)
-    bool tuned = false;
-    int tile_sx = 2, tile_sy = 1, tile_tg = 9, tile_warps = 8;
+    // tiling chosen by sam_autotune for this model, per field precision
+    // (overrides the default)
+    bool tuned[3] = {false, false, false};
+    int tile_sx[3] = {2, 2, 2}, tile_sy[3] = {1, 1, 1}, tile_tg[3] = {9, 9, 9}, tile_warps[3] = {8, 8, 8};
 };
 
 namespace sam {
