@@ -174,6 +174,52 @@ sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t 
                             int capacity, int *n_out);
 
 /* ---------------------------------------------------------------------------
+ * Batched detection of uneven workloads (Sec. II detection applied to many
+ * (image, model) pairs; the batching itself has no counterpart in the
+ * paper).  A plan is built once for a batch shape -- image sizes, models and
+ * pairs -- and owns every device buffer.  Each run is a fixed sequence of
+ * launches over all images and pairs: pyramid steps and gradients as job
+ * lists, one persistent exhaustive scorer that takes (pair, super-tile,
+ * angle group) units from an atomic counter, FP32 rescoring for 16-bit
+ * fields, candidates, refinement and NMS; the plan captures the sequence once
+ * into a CUDA graph and replays it.
+ *   models       the plan keeps the pointers; the models must outlive it and
+ *                share one edge threshold and polarity.
+ *   image_sizes  2 * n_images ints (w, h).
+ *   pairs        n_pairs (image, model) index pairs; a model with L levels
+ *                needs images of at least 2^(L-1) pixels a side.
+ *   params       as for sam_detect, with step_x = step_y = 1.
+ * Images are written by the caller into the plan's device buffers
+ * (sam_multi_image: device pointer and row pitch of image i) before a run.
+ * sam_multi_run replays the graph on `stream`, then copies every pair's poses
+ * to out[i * capacity ...] and their count to n_out[i] (host, caller order)
+ * and synchronises the stream.  Plans are not thread-safe; runs of one plan
+ * must not overlap.  sam_multi_autotune times the scorer of the current batch
+ * (images already written) over its tiling candidates (super-tile 1..2 x
+ * 1..2, angles per unit 1, 3, 5, 9, 15, 4 or 8 warps) and keeps the fastest;
+ * sam_multi_set_tiling sets one.  sam_multi_stats: top-level pose-points per
+ * run (nominal), kernels per graph replay, device bytes held.
+ * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------- */
+typedef struct sam_multi sam_multi;
+typedef struct {
+    int image, model;
+} sam_pair;
+sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_t *image_sizes, int n_images,
+                            const sam_pair *pairs, int n_pairs, const sam_detect_params *params, sam_multi **out);
+void sam_multi_free(sam_multi *mp);
+uint8_t *sam_multi_image(sam_multi *mp, int i, int *pitch);
+/* Copy image i (w x h as declared, row pitch `stride`; device pointer if
+ * on_device, else host) into the plan, ordered on `stream`. */
+sam_status sam_multi_set_image(sam_multi *mp, int i, const uint8_t *src, int stride, int on_device, void *stream);
+sam_status sam_multi_run(sam_multi *mp, void *stream, sam_pose *out, int capacity, int *n_out);
+sam_status sam_multi_set_tiling(sam_multi *mp, int sx, int sy, int tg, int warps);
+sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
+                              int *n_out);
+sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long long *graph_kernels,
+                           size_t *device_bytes);
+
+/* ---------------------------------------------------------------------------
  * Individual steps on caller-owned device buffers (stream-ordered, no
  * synchronisation, no allocation).
  * ------------------------------------------------------------------------- */

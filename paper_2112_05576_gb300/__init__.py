@@ -15,6 +15,7 @@ from .sam import (  # noqa: F401
     DetectParams,
     Model,
     ModelParams,
+    MultiPlan,
     Pose,
     SamError,
     autotune,

@@ -38,14 +38,10 @@ __device__ __forceinline__ uint32_t mean2x2_quad(uint32_t p0, uint32_t p1, uint3
     return __byte_perm(lo, hi, 0x6420);
 }
 
-__global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int h, int ss, size_t src_img,
-                                    uint8_t *__restrict__ dst, int ds, size_t dst_img, int vec) {
-    const int img = blockIdx.z;
-    src += (size_t)img * src_img;
-    dst += (size_t)img * dst_img;
+// 16 output pixels of output row y starting at column x0.
+__device__ __forceinline__ void pyramid_16(const uint8_t *__restrict__ src, int w, int h, int ss,
+                                           uint8_t *__restrict__ dst, int ds, int vec, int y, int x0) {
     const int w2 = w >> 1, h2 = h >> 1;
-    const int y = blockIdx.y;
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
     if (y >= h2 || x0 >= w2)
         return;
     const uint8_t *r0 = src + (size_t)(2 * y) * ss;
@@ -67,6 +63,22 @@ __global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int 
         for (int x = x0; x < xe; ++x)
             o[x] = (uint8_t)((r0[2 * x] + r0[2 * x + 1] + r1[2 * x] + r1[2 * x + 1] + 2) >> 2);
     }
+}
+
+__global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int h, int ss, size_t src_img,
+                                    uint8_t *__restrict__ dst, int ds, size_t dst_img, int vec) {
+    const int img = blockIdx.z;
+    pyramid_16(src + (size_t)img * src_img, w, h, ss, dst + (size_t)img * dst_img, ds, vec, blockIdx.y,
+               (blockIdx.x * blockDim.x + threadIdx.x) * 16);
+}
+
+// One pyramid step of many images of different sizes: job blockIdx.z,
+// rows strided over gridDim.y.
+__global__ void pyramid_jobs_kernel(const ImageJob *__restrict__ jobs) {
+    const ImageJob j = jobs[blockIdx.z];
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    for (int y = blockIdx.y; y < (j.h >> 1); y += gridDim.y)
+        pyramid_16(j.src, j.w, j.h, j.src_stride, static_cast<uint8_t *>(j.dst), j.dst_stride, j.vec, y, x0);
 }
 
 // ---------------------------------------------------------------------------
@@ -138,15 +150,13 @@ struct FieldStore<SAM_FP16> {
     }
 };
 
+// One GTX x GTY tile of one image whose field starts fbase pixels into
+// `field` (the caller returns early, block-uniformly, for tiles outside).
 template <int PREC, int LAYOUT>
-__global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__restrict__ img, int w, int h, int ss,
-                                                            size_t img_bytes, int low, void *__restrict__ field,
-                                                            size_t field_img_px, int16_t *__restrict__ ogx,
-                                                            int16_t *__restrict__ ogy, int vec) {
+__device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, int w, int h, int ss, int low,
+                                              void *__restrict__ field, size_t fbase, int16_t *__restrict__ ogx,
+                                              int16_t *__restrict__ ogy, int vec, int x0, int y0) {
     __shared__ __align__(16) uint8_t tile[GTY + 2][GSW];
-    const int im = blockIdx.z;
-    img += (size_t)im * img_bytes;
-    const int x0 = blockIdx.x * GTX, y0 = blockIdx.y * GTY;
     const int tid = threadIdx.x;
 
     // Stage rows y0-1 .. y0+GTY, columns x0-16 .. x0+GTX+15 (zero outside).
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__res
         // the row pitch (a multiple of 4, at most the thread's 8-pixel group
         // end) are written as zero too
         const int wp = field_pitch(w, SAM_LAYOUT_PAIRS);
-        const size_t q0 = ((size_t)im * field_img_px + (size_t)y * wp + xb) >> 1;
+        const size_t q0 = (fbase + (size_t)y * wp + xb) >> 1;
         const bool full = (xb + GPT <= wp) && vec;
 #pragma unroll
         for (int q = 0; q < GPT / 2; ++q)
@@ -232,7 +242,7 @@ __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__res
                 FieldStore<PREC>::store_pair(field, q0 + q, wx[2 * q], wx[2 * q + 1], wy[2 * q], wy[2 * q + 1]);
         return;
     }
-    const size_t base = (size_t)im * field_img_px + (size_t)y * w + xb;
+    const size_t base = fbase + (size_t)y * w + xb;
     const bool full = (xb + GPT <= w) && vec && ((w & 7) == 0);
     if (full) {
         FieldStore<PREC>::store8(field, base, wx, wy);
@@ -263,7 +273,72 @@ __global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__res
     }
 }
 
+// `count` images of equal size, image blockIdx.z.
+template <int PREC, int LAYOUT>
+__global__ void __launch_bounds__(GTHREADS) gradient_kernel(const uint8_t *__restrict__ img, int w, int h, int ss,
+                                                            size_t img_bytes, int low, void *__restrict__ field,
+                                                            size_t field_img_px, int16_t *__restrict__ ogx,
+                                                            int16_t *__restrict__ ogy, int vec) {
+    const int im = blockIdx.z;
+    gradient_tile<PREC, LAYOUT>(img + (size_t)im * img_bytes, w, h, ss, low, field, (size_t)im * field_img_px, ogx,
+                                ogy, vec, blockIdx.x * GTX, blockIdx.y * GTY);
+}
+
+// Images of different sizes: job blockIdx.z, tiles strided over the grid.
+template <int PREC, int LAYOUT>
+__global__ void __launch_bounds__(GTHREADS) gradient_jobs_kernel(const ImageJob *__restrict__ jobs, int low) {
+    const ImageJob j = jobs[blockIdx.z];
+    for (int y0 = blockIdx.y * GTY; y0 < j.h; y0 += gridDim.y * GTY)
+        for (int x0 = blockIdx.x * GTX; x0 < j.w; x0 += gridDim.x * GTX) {
+            gradient_tile<PREC, LAYOUT>(j.src, j.w, j.h, j.src_stride, low, j.dst, 0, nullptr, nullptr, j.vec, x0,
+                                        y0);
+            __syncthreads();   // the tile buffer is reused by the next iteration
+        }
+}
+
 }  // namespace
+
+cudaError_t launch_pyramid_jobs(const ImageJob *jobs, int n_jobs, int max_w, int max_h, cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    const int threads = 128;
+    dim3 grid((unsigned)std::max(1, (max_w / 2 + 16 * threads - 1) / (16 * threads)),
+              (unsigned)std::min(std::max(1, max_h / 2), 512), (unsigned)n_jobs);
+    pyramid_jobs_kernel<<<grid, threads, 0, st>>>(jobs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_jobs(const ImageJob *jobs, int n_jobs, int max_w, int max_h, int low, int precision,
+                                 int layout, cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)std::min((max_w + GTX - 1) / GTX, 32), (unsigned)std::min((max_h + GTY - 1) / GTY, 64),
+              (unsigned)n_jobs);
+    const bool pairs = layout == SAM_LAYOUT_PAIRS;
+    switch (precision) {
+    case SAM_FP32:
+        if (pairs)
+            gradient_jobs_kernel<SAM_FP32, SAM_LAYOUT_PAIRS><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        else
+            gradient_jobs_kernel<SAM_FP32, SAM_LAYOUT_PIXEL><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        break;
+    case SAM_BF16:
+        if (pairs)
+            gradient_jobs_kernel<SAM_BF16, SAM_LAYOUT_PAIRS><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        else
+            gradient_jobs_kernel<SAM_BF16, SAM_LAYOUT_PIXEL><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        break;
+    default:
+        if (pairs)
+            gradient_jobs_kernel<SAM_FP16, SAM_LAYOUT_PAIRS><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        else
+            gradient_jobs_kernel<SAM_FP16, SAM_LAYOUT_PIXEL><<<grid, GTHREADS, 0, st>>>(jobs, low);
+        break;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
                                 int dst_stride, size_t dst_img, int count, cudaStream_t st) {

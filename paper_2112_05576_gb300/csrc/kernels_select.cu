@@ -6,6 +6,10 @@
 // Every selection uses one total order: higher score first, then the
 // smaller key (k * H + y) * W + x.  Ties therefore resolve identically on
 // every run, independent of atomic ordering.
+//
+// Each stage has a device body shared by two entry points: a uniform batch
+// (images of one size, one model) and a job list (per-image or per-pair
+// descriptors in device memory, for batches of different sizes and models).
 
 #include <float.h>
 
@@ -17,6 +21,7 @@ namespace sam {
 namespace {
 
 constexpr int kSortCap = 2048;   // shared-memory sort buffer (entries)
+constexpr int RTHREADS = 256;
 
 __device__ __forceinline__ bool beats(float sa, unsigned long long ka, float sb, unsigned long long kb) {
     return sa > sb || (sa == sb && ka < kb);
@@ -26,54 +31,69 @@ __device__ __forceinline__ bool beats(float sa, unsigned long long ka, float sb,
 // local maxima
 // ---------------------------------------------------------------------------
 
+// Whether map entry idx is a strict local maximum >= min_score over its up to
+// 26 neighbours in (theta circular, y, x).
+__device__ __forceinline__ bool is_candidate(const float *__restrict__ map, int nth, int gh, int gw, float min_score,
+                                             size_t idx) {
+    const float s = map[idx];
+    if (!(s >= min_score))
+        return false;
+    const size_t plane = (size_t)gh * gw;
+    const int k = (int)(idx / plane);
+    const int r = (int)(idx - (size_t)k * plane);
+    const int y = r / gw, x = r - y * gw;
+    for (int dk = -1; dk <= 1; ++dk) {
+        if (dk != 0 && nth == 1)
+            continue;
+        const int k2 = (k + dk + nth) % nth;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y2 = y + dy;
+            if (y2 < 0 || y2 >= gh)
+                continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x2 = x + dx;
+                if (x2 < 0 || x2 >= gw)
+                    continue;
+                const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
+                if (j == idx)
+                    continue;
+                if (!beats(s, idx, map[j], j))
+                    return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void push_candidate(const float *map, size_t idx, Cand *cand, size_t cap, int *cnt) {
+    const int pos = atomicAdd(cnt, 1);
+    if ((size_t)pos < cap) {
+        Cand c;
+        c.s = map[idx];
+        c.pad = 0;
+        c.key = idx;
+        cand[pos] = c;
+    }
+}
+
 __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
                                  float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt) {
     const int img = blockIdx.y;
     map += (size_t)img * map_img;
     const size_t total = (size_t)nth * gh * gw;
-    const size_t plane = (size_t)gh * gw;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const float s = map[idx];
-        if (!(s >= min_score))
-            continue;
-        const int k = (int)(idx / plane);
-        const int r = (int)(idx - (size_t)k * plane);
-        const int y = r / gw, x = r - y * gw;
-        bool ok = true;
-        for (int dk = -1; dk <= 1 && ok; ++dk) {
-            if (dk != 0 && nth == 1)
-                continue;
-            const int k2 = (k + dk + nth) % nth;
-            for (int dy = -1; dy <= 1 && ok; ++dy) {
-                const int y2 = y + dy;
-                if (y2 < 0 || y2 >= gh)
-                    continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int x2 = x + dx;
-                    if (x2 < 0 || x2 >= gw)
-                        continue;
-                    const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
-                    if (j == idx)
-                        continue;
-                    if (!beats(s, idx, map[j], j)) {
-                        ok = false;
-                        break;
-                    }
-                }
-            }
-        }
-        if (ok) {
-            const int pos = atomicAdd(cnt + img, 1);
-            if ((size_t)pos < cap) {
-                Cand c;
-                c.s = s;
-                c.pad = 0;
-                c.key = idx;
-                cand[(size_t)img * cap + pos] = c;
-            }
-        }
-    }
+         idx += (size_t)gridDim.x * blockDim.x)
+        if (is_candidate(map, nth, gh, gw, min_score, idx))
+            push_candidate(map, idx, cand + (size_t)img * cap, cap, cnt + img);
+}
+
+__global__ void local_max_jobs_kernel(const CandJob *__restrict__ jobs, float min_score) {
+    const CandJob j = jobs[blockIdx.y];
+    const size_t total = (size_t)j.nth * j.gh * j.gw;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x)
+        if (is_candidate(j.map, j.nth, j.gh, j.gw, min_score, idx))
+            push_candidate(j.map, idx, j.cand, j.cap, j.cnt);
 }
 
 // Bitonic sort of n (power of two) entries in shared memory, best first.
@@ -99,14 +119,12 @@ __device__ void bitonic_sort(float *s, unsigned long long *key, int n) {
     }
 }
 
-__global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ cand, size_t cap, const int *__restrict__ cnt,
-                                                    int K, int gh, int gw, int32_t *__restrict__ out_kyx,
-                                                    float *__restrict__ out_s, int *__restrict__ out_count) {
+// The best K of `total` candidates, by repeated sorts of the running top K
+// plus the next chunk in shared memory.
+__device__ void topk_body(const Cand *__restrict__ cand, int total, int K, int gh, int gw,
+                          int32_t *__restrict__ out_kyx, float *__restrict__ out_s, int *__restrict__ out_count) {
     __shared__ float s[kSortCap];
     __shared__ unsigned long long key[kSortCap];
-    const int img = blockIdx.x;
-    cand += (size_t)img * cap;
-    const int total = (int)min((size_t)cnt[img], cap);
     const int chunk = kSortCap - K;
     int have = 0;   // valid entries at the front of the buffer (sorted)
     for (int start = 0; start < total || (start == 0 && total == 0); start += chunk) {
@@ -140,60 +158,71 @@ __global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ can
             const unsigned long long kk = key[i];
             const int k = (int)(kk / plane);
             const int r = (int)(kk - (unsigned long long)k * plane);
-            out_kyx[(size_t)img * 3 * K + 3 * i] = k;
-            out_kyx[(size_t)img * 3 * K + 3 * i + 1] = r / gw;
-            out_kyx[(size_t)img * 3 * K + 3 * i + 2] = r % gw;
-            out_s[(size_t)img * K + i] = s[i];
+            out_kyx[3 * i] = k;
+            out_kyx[3 * i + 1] = r / gw;
+            out_kyx[3 * i + 2] = r % gw;
+            out_s[i] = s[i];
         }
     }
     if (threadIdx.x == 0)
-        out_count[img] = have;
+        *out_count = have;
+}
+
+__global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ cand, size_t cap,
+                                                    const int *__restrict__ cnt, int K, int gh, int gw,
+                                                    int32_t *__restrict__ out_kyx, float *__restrict__ out_s,
+                                                    int *__restrict__ out_count) {
+    const int img = blockIdx.x;
+    topk_body(cand + (size_t)img * cap, (int)min((size_t)cnt[img], cap), K, gh, gw, out_kyx + (size_t)img * 3 * K,
+              out_s + (size_t)img * K, out_count + img);
+}
+
+__global__ void __launch_bounds__(1024) topk_jobs_kernel(const CandJob *__restrict__ jobs, int K) {
+    const CandJob j = jobs[blockIdx.x];
+    topk_body(j.cand, (int)min((size_t)*j.cnt, j.cap), K, j.gh, j.gw, j.out_kyx, j.out_s, j.out_count);
 }
 
 // ---------------------------------------------------------------------------
-// refinement: one CTA per (image, candidate), all levels top-1 .. 0
+// refinement: one CTA per (image or pair, candidate), all levels top-1 .. 0
 // ---------------------------------------------------------------------------
 
 struct RefineLevels {
     LevelDev L[kMaxLevels];
 };
 
-constexpr int RTHREADS = 256;
-
 template <int NB>
-__global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, RefineArgs a) {
-    const int img = blockIdx.y, c = blockIdx.x;
+__device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
     __shared__ float red[RTHREADS / 32][27];
     __shared__ int state[4];   // x, y, k, alive
     __shared__ float sbest;
-    const int ncand = a.cand_count[img];
-    float4 *outp = a.refined + (size_t)img * a.K + c;
+    const int ncand = *j.count;
+    float4 *outp = j.refined + c;
     if (c >= ncand) {
         if (threadIdx.x == 0)
             *outp = make_float4(__int_as_float(0), __int_as_float(0), __int_as_float(0), -INFINITY);
         return;
     }
     if (threadIdx.x == 0) {
-        const int32_t *kyx = a.cand_kyx + (size_t)img * 3 * a.K + 3 * c;
-        state[0] = kyx[2] * a.step_x;
-        state[1] = kyx[1] * a.step_y;
+        const int32_t *kyx = j.kyx + 3 * c;
+        state[0] = kyx[2] * j.step_x;
+        state[1] = kyx[1] * j.step_y;
         state[2] = kyx[0];
         state[3] = 1;
-        sbest = a.cand_s[(size_t)img * a.K + c];
+        sbest = j.cs[c];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int l = a.top - 1; l >= 0; --l) {
-        const LevelDev &L = lv.L[l];
-        const int2 sh = lv.L[l + 1].shift[state[2]];
+    for (int l = j.top - 1; l >= 0; --l) {
+        const LevelDev &L = lv[l];
+        const int2 sh = lv[l + 1].shift[state[2]];
         const int cx = 2 * state[0] + sh.x, cy = 2 * state[1] + sh.y;
         const int kp = state[2];
-        const int W = a.w[l], H = a.h[l];
-        const float2 *F = a.field[l] + (size_t)img * a.field_img_px[l];
+        const int W = j.w[l], H = j.h[l];
+        const float2 *F = j.field[l];
         float acc[27];
 #pragma unroll
-        for (int j = 0; j < 27; ++j)
-            acc[j] = 0.f;
+        for (int q = 0; q < 27; ++q)
+            acc[q] = 0.f;
 #pragma unroll
         for (int dk = 0; dk < 3; ++dk) {
             const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
@@ -212,7 +241,7 @@ __global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, Refin
                         if (X >= 0 && Y >= 0 && X < W && Y < H) {
                             const float2 f = __ldg(F + (size_t)Y * W + X);
                             v = fmaf(p.px, f.x, p.py * f.y);
-                            if (a.polarity)
+                            if (j.polarity)
                                 v = fabsf(v);
                         }
                         d[yy][xx] = v;
@@ -235,13 +264,13 @@ __global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, Refin
         }
         // block reduction of the 27 sums
 #pragma unroll
-        for (int j = 0; j < 27; ++j) {
-            float v = acc[j];
+        for (int q = 0; q < 27; ++q) {
+            float v = acc[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0)
-                red[warp][j] = v;
+                red[warp][q] = v;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -275,7 +304,7 @@ __global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, Refin
             state[0] = bx;
             state[1] = by;
             state[2] = bkk;
-            state[3] = any && bs >= a.min_score;
+            state[3] = any && bs >= j.min_score;
             sbest = bs;
         }
         __syncthreads();
@@ -287,17 +316,43 @@ __global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, Refin
                             state[3] ? sbest : -INFINITY);
 }
 
+template <int NB>
+__global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, RefineArgs a) {
+    const int img = blockIdx.y;
+    RefineJob j;
+    j.L = nullptr;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        j.field[l] = a.field[l] + (size_t)img * a.field_img_px[l];
+        j.w[l] = a.w[l];
+        j.h[l] = a.h[l];
+    }
+    j.top = a.top;
+    j.step_x = a.step_x;
+    j.step_y = a.step_y;
+    j.polarity = a.polarity;
+    j.min_score = a.min_score;
+    j.kyx = a.cand_kyx + (size_t)img * 3 * a.K;
+    j.cs = a.cand_s + (size_t)img * a.K;
+    j.count = a.cand_count + img;
+    j.refined = a.refined + (size_t)img * a.K;
+    refine_body<NB>(j, lv.L, blockIdx.x);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(RTHREADS) refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
+    const RefineJob &j = jobs[blockIdx.y];
+    refine_body<NB>(j, j.L, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
-// NMS: one CTA per image
+// NMS: one CTA per image or pair
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
+__device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, int min_side, int max_out,
+                         double angle_step, sam_pose *__restrict__ out, int *__restrict__ n_out) {
     __shared__ float s[kMaxTopK];
     __shared__ unsigned long long key[kMaxTopK];
     __shared__ int px[kMaxTopK], py[kMaxTopK], pk[kMaxTopK];
-    const int img = blockIdx.x;
-    const float4 *R = a.refined + (size_t)img * a.K;
-    const int nc = min(a.cand_count[img], a.K);
     int n2 = 1;
     while (n2 < nc)
         n2 <<= 1;
@@ -306,7 +361,7 @@ __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
             const float4 r = R[i];
             const int x = __float_as_int(r.x), y = __float_as_int(r.y), k = __float_as_int(r.z);
             s[i] = r.w;
-            key[i] = ((unsigned long long)k * a.h0 + y) * a.w0 + x;
+            key[i] = ((unsigned long long)k * h0 + y) * w0 + x;
         } else {
             s[i] = -INFINITY;
             key[i] = ~0ull;
@@ -315,27 +370,26 @@ __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
     __syncthreads();
     if (n2 > 1)
         bitonic_sort(s, key, n2);
-    const unsigned long long plane = (unsigned long long)a.h0 * a.w0;
+    const unsigned long long plane = (unsigned long long)h0 * w0;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) {
         const unsigned long long kk = key[i];
         if (kk == ~0ull)
             continue;
         pk[i] = (int)(kk / plane);
         const int r = (int)(kk - (unsigned long long)pk[i] * plane);
-        py[i] = r / a.w0;
-        px[i] = r - py[i] * a.w0;
+        py[i] = r / w0;
+        px[i] = r - py[i] * w0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        sam_pose *out = a.out + (size_t)img * a.max_out;
         int kept = 0;
-        const long long ms2 = (long long)a.min_side * a.min_side;
-        for (int i = 0; i < nc && kept < a.max_out; ++i) {
+        const long long ms2 = (long long)min_side * min_side;
+        for (int i = 0; i < nc && kept < max_out; ++i) {
             if (s[i] == -INFINITY)
                 break;   // sorted: the rest are dead too
             bool ok = true;
-            for (int j = 0; j < kept; ++j) {
-                const long long dx = px[i] - out[j].level0_x, dy = py[i] - out[j].level0_y;
+            for (int q = 0; q < kept; ++q) {
+                const long long dx = px[i] - out[q].level0_x, dy = py[i] - out[q].level0_y;
                 if (4 * (dx * dx + dy * dy) < ms2) {
                     ok = false;
                     break;
@@ -346,7 +400,7 @@ __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
             sam_pose p;
             p.x = (float)px[i];
             p.y = (float)py[i];
-            p.theta_deg = (float)(pk[i] * a.angle_step);
+            p.theta_deg = (float)(pk[i] * angle_step);
             p.score = s[i];
             p.angle_index = pk[i];
             p.level0_x = px[i];
@@ -354,8 +408,19 @@ __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
             p.reserved = 0;
             out[kept++] = p;
         }
-        a.n_out[img] = kept;
+        *n_out = kept;
     }
+}
+
+__global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
+    const int img = blockIdx.x;
+    nms_body(a.refined + (size_t)img * a.K, min(a.cand_count[img], a.K), a.w0, a.h0, a.min_side, a.max_out,
+             a.angle_step, a.out + (size_t)img * a.max_out, a.n_out + img);
+}
+
+__global__ void __launch_bounds__(256) nms_jobs_kernel(const NmsJob *__restrict__ jobs, int K) {
+    const NmsJob j = jobs[blockIdx.x];
+    nms_body(j.refined, min(*j.count, K), j.w0, j.h0, j.min_side, j.max_out, j.angle_step, j.out, j.n_out);
 }
 
 }  // namespace
@@ -366,13 +431,12 @@ size_t candidates_scratch_bytes(int nth, int gh, int gw) {
     return 256 + cap * sizeof(Cand);
 }
 
-static size_t cand_cap(int nth, int gh, int gw) { return (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2); }
+size_t cand_cap(int nth, int gh, int gw) { return (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2); }
 
 cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
                               int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
                               int n_img, cudaStream_t st) {
-    // scratch layout per image: [int counter, padded to 256 B][Cand cap]
-    // counters for all images live at the start of the first image's slot
+    // scratch layout: [n_img int counters, padded to 256 B][n_img x Cand cap]
     const size_t cap = cand_cap(nth, gh, gw);
     int *cnt = reinterpret_cast<int *>(scratch);
     Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
@@ -393,6 +457,17 @@ size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img) {
     return 256 * ((n_img * sizeof(int) + 255) / 256) + (size_t)n_img * cand_cap(nth, gh, gw) * sizeof(Cand);
 }
 
+cudaError_t launch_candidates_jobs(const CandJob *jobs, int n_jobs, size_t max_total, float min_score, int K,
+                                   cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((max_total + 255) / 256, 64));
+    local_max_jobs_kernel<<<dim3((unsigned)blocks, (unsigned)n_jobs), 256, 0, st>>>(jobs, min_score);
+    topk_jobs_kernel<<<n_jobs, 1024, 0, st>>>(jobs, K);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t st) {
     RefineLevels lv;
     for (int l = 0; l < kMaxLevels; ++l)
@@ -406,13 +481,34 @@ cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_refine_jobs(const RefineJob *jobs, int n_jobs, int K, int nbhd, cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)K, (unsigned)n_jobs);
+    if (nbhd == 3)
+        refine_jobs_kernel<3><<<grid, RTHREADS, 0, st>>>(jobs);
+    else
+        refine_jobs_kernel<1><<<grid, RTHREADS, 0, st>>>(jobs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st) {
     nms_kernel<<<a.count, 256, 0, st>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+cudaError_t launch_nms_jobs(const NmsJob *jobs, int n_jobs, int K, cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    nms_jobs_kernel<<<n_jobs, 256, 0, st>>>(jobs, K);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace sam
+
 
 // ---------------------------------------------------------------------------
 // Candidate extraction without run-time allocation.

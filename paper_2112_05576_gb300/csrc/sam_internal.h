@@ -74,6 +74,20 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
 sam_status upload_model(sam_model *m);
 
 // ---- kernels (launchers return cudaGetLastError()) ----
+// One image of a job list (images of different sizes in one launch): the
+// source level and its destination (next pyramid level, or a field).
+struct ImageJob {
+    const uint8_t *src;
+    int w, h, src_stride;
+    int dst_stride;   // pyramid jobs: destination row pitch (bytes)
+    void *dst;
+    int vec;          // 1 when every pointer and pitch allows 128-bit access
+    int pad;
+};
+cudaError_t launch_pyramid_jobs(const ImageJob *jobs, int n_jobs, int max_w, int max_h, cudaStream_t st);
+cudaError_t launch_gradient_jobs(const ImageJob *jobs, int n_jobs, int max_w, int max_h, int low, int precision,
+                                 int layout, cudaStream_t st);
+
 // (b) pyramid step; `count` images, image i at src + i*src_img / dst + i*dst_img
 cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
                                 int dst_stride, size_t dst_img, int count, cudaStream_t st);
@@ -116,6 +130,25 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
                                int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st);
+
+// Persistent tiled scorer over many (image, model) pairs (score_tiled.cu).
+struct PairScore {
+    const void *tmap;   // the pair's 2-D CUtensorMap in device memory (64-byte aligned)
+    const RotPt *rot;   // the model's top-level tables
+    const int4 *bbox;
+    float *map;         // the pair's map [nth][H][W]
+    int n, nth, W, H;
+    int tiles_x, tiles; // super-tiles along x, in total
+    int bxw, byw;       // the pair's window box
+    float inv_n, thresh;
+    int item_begin;     // first work unit of this pair (units: tiles x angle groups)
+    int pad;
+};
+bool encode_pair_tmap(void *out, const void *field, int precision, int wp, int H, int bxw, int byw);
+int tiled_warp_tile(int precision, int *wty);
+cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_items, int precision, int nbhd,
+                               int polarity, int early, const TileConfig &cfg, size_t window_bytes, unsigned *counter,
+                               cudaStream_t st);
 
 // Score-kernel selection (process-wide; sam_set_score_kernel).
 struct ScoreChoice {
@@ -182,5 +215,41 @@ struct NmsArgs {
     int count;
 };
 cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
+
+// ---- job lists (batches of different sizes and models; device arrays) ----
+struct CandJob {
+    const float *map;
+    int nth, gh, gw;
+    Cand *cand;
+    size_t cap;
+    int *cnt;          // zeroed before the launch
+    int32_t *out_kyx;  // 3*K
+    float *out_s;      // K
+    int *out_count;
+};
+struct RefineJob {
+    const LevelDev *L;                 // the model's level tables (device)
+    const float2 *field[kMaxLevels];   // this image's FP32 pixel-layout fields
+    int w[kMaxLevels], h[kMaxLevels];
+    int top, step_x, step_y, polarity;
+    float min_score;
+    const int32_t *kyx;                // candidates (3*K), scores (K), count
+    const float *cs;
+    const int *count;
+    float4 *refined;                   // K
+};
+struct NmsJob {
+    const float4 *refined;
+    const int *count;
+    int w0, h0, min_side, max_out;
+    double angle_step;
+    sam_pose *out;
+    int *n_out;
+};
+size_t cand_cap(int nth, int gh, int gw);
+cudaError_t launch_candidates_jobs(const CandJob *jobs, int n_jobs, size_t max_total, float min_score, int K,
+                                   cudaStream_t st);
+cudaError_t launch_refine_jobs(const RefineJob *jobs, int n_jobs, int K, int nbhd, cudaStream_t st);
+cudaError_t launch_nms_jobs(const NmsJob *jobs, int n_jobs, int K, cudaStream_t st);
 
 }  // namespace sam

@@ -238,6 +238,19 @@ __device__ __forceinline__ void point_nb1(const typename Pairs<E>::Raw *win, int
     }
 }
 
+// What a CTA work unit needs besides its window.
+struct TileWork {
+    const RotPt *rot;
+    int n, W, H;
+    float *map;   // the image's (or pair's) map [nth][H][W]
+    float inv_n, thresh;
+    int early, sx, sy;
+};
+
+template <typename E, int NB, bool POL, int WARPS>
+__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int k_end, const TileWork &a);
+
 template <typename E, int NB, bool POL, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TiledArgs a) {
@@ -292,12 +305,31 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
             atomicExch(&g_score_err, 1);
         return;
     }
-    const int wx0 = s_org[0], wy0 = s_org[1];
+    TileWork t;
+    t.rot = a.rot;
+    t.n = a.n;
+    t.W = a.W;
+    t.H = a.H;
+    t.map = a.map + (size_t)img * a.map_img;
+    t.inv_n = a.inv_n;
+    t.thresh = a.thresh;
+    t.early = a.early;
+    t.sx = a.sx;
+    t.sy = a.sy;
+    score_items<E, NB, POL, WARPS>(win, pp, s_org[0], s_org[1], stx0, sty0, k_begin, k_end, t);
+}
 
+// The (angle, warp tile) items of one CTA work unit over its staged window
+// (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
+template <typename E, int NB, bool POL, int WARPS>
+__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int k_end, const TileWork &a) {
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane % LX, ly = lane / LX;
     const int items = (k_end - k_begin) * a.sx * a.sy;
-    float *map = a.map + (size_t)img * a.map_img;
+    float *map = a.map;
 
     for (int it = warp; it < items; it += WARPS) {
         const int k = k_begin + it / (a.sx * a.sy);
@@ -374,6 +406,107 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
                 }
             }
         }
+    }
+}
+
+// Persistent form for batches of uneven (image, model) pairs: every CTA
+// pulls work units (pair, super-tile, angle group) from one atomic counter,
+// stages the unit's window with that pair's own 2-D tensor map (box sized for
+// the pair), and scores it.  The window buffer and its mbarrier are reused
+// unit after unit (the barrier's phase alternates).  Pairs are laid out
+// largest first so the dynamic schedule ends with small units.
+template <typename E, int NB, bool POL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore *__restrict__ pairs, int n_pairs,
+                                                                  int total, int sx, int sy, int tg, int early,
+                                                                  unsigned *__restrict__ counter) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_unit[6];   // item, pair, super-tile x0, y0, window x0, y0
+    const uint32_t bar = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(counter, 1u);
+            s_unit[0] = item;
+            if (item < total) {
+                int lo = 0, hi = n_pairs - 1;   // last pair whose first item <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pairs[mid].item_begin <= item)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const PairScore &P = pairs[lo];
+                const int local = item - P.item_begin;
+                const int group = local / P.tiles, st = local - group * P.tiles;
+                const int stx0 = (st % P.tiles_x) * sx * WTX, sty0 = (st / P.tiles_x) * sy * WTY;
+                const int k_begin = group * tg, k_end = min(k_begin + tg, P.nth);
+                int xmin = 1 << 30, ymin = 1 << 30;
+                for (int k = k_begin; k < k_end; ++k) {
+                    const int4 b = P.bbox[k];
+                    xmin = min(xmin, b.x);
+                    ymin = min(ymin, b.z);
+                }
+                const int wx0 = (stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
+                const int wy0 = sty0 + ymin - 1;
+                s_unit[1] = lo;
+                s_unit[2] = stx0;
+                s_unit[3] = sty0;
+                s_unit[4] = wx0;
+                s_unit[5] = wy0;
+                const uint32_t bytes = (uint32_t)P.bxw * (uint32_t)P.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+                // the previous unit's reads of the window (generic proxy) are
+                // ordered before this unit's copy into it (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                             : "memory");
+                const int xe = wx0 * Pairs<E>::BYTES / 16;
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                    "[%4];" ::"r"(smem_addr(win)),
+                    "l"(reinterpret_cast<uint64_t>(P.tmap)), "r"(xe), "r"(wy0), "r"(bar)
+                    : "memory");
+            }
+        }
+        __syncthreads();
+        const int item = s_unit[0];
+        if (item >= total)
+            break;
+        const bool ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0)
+                atomicExch(&g_score_err, 1);
+            break;
+        }
+        const PairScore &P = pairs[s_unit[1]];
+        const int local = item - P.item_begin;
+        const int group = local / P.tiles;
+        TileWork t;
+        t.rot = P.rot;
+        t.n = P.n;
+        t.W = P.W;
+        t.H = P.H;
+        t.map = P.map;
+        t.inv_n = P.inv_n;
+        t.thresh = P.thresh;
+        t.early = early;
+        t.sx = sx;
+        t.sy = sy;
+        score_items<E, NB, POL, WARPS>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
+                                       min(group * tg + tg, P.nth), t);
+        __syncthreads();   // every warp is done with the window before the next copy
     }
 }
 
@@ -520,6 +653,86 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
         return launch_e<__half>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
     default:
         return launch_e<__nv_bfloat16>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    }
+}
+
+// 2-D tensor map of one image's pairs-layout field for the persistent kernel
+// (written to host memory; the plan copies it to device memory).
+bool encode_pair_tmap(void *out, const void *field, int precision, int wp, int H, int bxw, int byw) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return false;
+    const Geometry g = geometry(precision);
+    const cuuint64_t dims[2] = {(cuuint64_t)wp * g.pair_bytes / 16, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)wp * g.pair_bytes / 2};
+    const cuuint32_t box[2] = {(cuuint32_t)(bxw * g.pair_bytes / 16), (cuuint32_t)byw};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(field), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tiled_warp_tile(int precision, int *wty) {
+    const Geometry g = geometry(precision);
+    *wty = g.wty;
+    return g.wtx;
+}
+
+namespace {
+template <typename E, int NB, bool POL, int WARPS>
+cudaError_t launch_pairs_t(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int early,
+                           size_t smem, unsigned *counter, cudaStream_t st) {
+    auto kern = score_pairs_kernel<E, NB, POL, WARPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = std::max(1, std::min(total, sms * std::max(1, per_sm)));
+    kern<<<grid, WARPS * 32, smem, st>>>(pairs, n_pairs, total, cfg.sx, cfg.sy, cfg.tg, early, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t launch_pairs_e(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
+                           int early, size_t smem, unsigned *counter, cudaStream_t st) {
+    if (cfg.warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_pairs_t<E, 3, true, 4>(pairs, n_pairs, total, cfg, early, smem, counter, st)
+                       : launch_pairs_t<E, 3, false, 4>(pairs, n_pairs, total, cfg, early, smem, counter, st);
+        return pol ? launch_pairs_t<E, 1, true, 4>(pairs, n_pairs, total, cfg, early, smem, counter, st)
+                   : launch_pairs_t<E, 1, false, 4>(pairs, n_pairs, total, cfg, early, smem, counter, st);
+    }
+    if (nbhd == 3)
+        return pol ? launch_pairs_t<E, 3, true, 8>(pairs, n_pairs, total, cfg, early, smem, counter, st)
+                   : launch_pairs_t<E, 3, false, 8>(pairs, n_pairs, total, cfg, early, smem, counter, st);
+    return pol ? launch_pairs_t<E, 1, true, 8>(pairs, n_pairs, total, cfg, early, smem, counter, st)
+               : launch_pairs_t<E, 1, false, 8>(pairs, n_pairs, total, cfg, early, smem, counter, st);
+}
+}  // namespace
+
+cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_items, int precision, int nbhd,
+                               int polarity, int early, const TileConfig &cfg, size_t window_bytes, unsigned *counter,
+                               cudaStream_t st) {
+    if (total_items <= 0 || n_pairs <= 0)
+        return cudaSuccess;
+    const size_t smem = window_bytes + 128;
+    const bool pol = polarity != 0;
+    switch (precision) {
+    case SAM_FP32:
+        return launch_pairs_e<float>(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, st);
+    case SAM_FP16:
+        return launch_pairs_e<__half>(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, st);
+    default:
+        return launch_pairs_e<__nv_bfloat16>(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, st);
     }
 }
 

@@ -76,6 +76,16 @@ SIGNATURES = {
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
+    "sam_multi_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _i32p, _c_int, ctypes.c_void_p, _c_int,
+                                  ctypes.POINTER(DetectParams), ctypes.POINTER(_vp)]),
+    "sam_multi_free": (None, [_vp]),
+    "sam_multi_image": (ctypes.c_void_p, [_vp, _c_int, ctypes.POINTER(_c_int)]),
+    "sam_multi_set_image": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp]),
+    "sam_multi_run": (_c_int, [_vp, _vp, ctypes.POINTER(Pose), _c_int, ctypes.POINTER(_c_int)]),
+    "sam_multi_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
+    "sam_multi_autotune": (_c_int, [_vp, _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
+    "sam_multi_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_size_t)]),
     "sam_profile_enable": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
     "sam_kernel_launches": (ctypes.c_longlong, []),
@@ -350,3 +360,69 @@ def model_tiling(model: Model, precision=FP32):
     v = [ctypes.c_int32() for _ in range(4)]
     _check(lib().sam_model_tiling(model.handle, int(precision), *[ctypes.byref(x) for x in v]), "sam_model_tiling")
     return tuple(x.value for x in v)
+
+
+class MultiPlan:
+    """A batch of (image, model) pairs over images of different sizes, run as
+    one captured CUDA graph with a persistent exhaustive scorer."""
+
+    def __init__(self, models, image_sizes, pairs, params: Optional[DetectParams] = None):
+        self.params = params or default_detect_params()
+        self.models = list(models)   # keep the models alive
+        n_m = len(self.models)
+        mh = (_vp * n_m)(*[m.handle for m in self.models])
+        sizes = (ctypes.c_int32 * (2 * len(image_sizes)))(*[v for wh in image_sizes for v in wh])
+        pr = (ctypes.c_int * (2 * len(pairs)))(*[v for p in pairs for v in p])
+        h = ctypes.c_void_p()
+        _check(lib().sam_multi_create(mh, n_m, sizes, len(image_sizes), ctypes.cast(pr, ctypes.c_void_p),
+                                      len(pairs), ctypes.byref(self.params), ctypes.byref(h)), "sam_multi_create")
+        self._h = h
+        self.image_sizes = list(image_sizes)
+        self.n_pairs = len(pairs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sam_multi_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_image(self, i, image, stream=None):
+        """Copy image i (2-D uint8 numpy array or CUDA tensor) into the plan."""
+        if isinstance(image, np.ndarray):
+            img = np.ascontiguousarray(image, dtype=np.uint8)
+            _check(lib().sam_multi_set_image(self._h, i, img.ctypes.data_as(_vp), img.shape[1], 0, _stream(stream)),
+                   "sam_multi_set_image")
+            import torch
+            torch.cuda.current_stream().synchronize()
+        else:
+            _check(lib().sam_multi_set_image(self._h, i, _ptr(image), image.stride(0), 1, _stream(stream)),
+                   "sam_multi_set_image")
+
+    def run(self, stream=None, capacity=None):
+        cap = capacity or self.params.max_detections
+        out = (Pose * (cap * self.n_pairs))()
+        nout = (ctypes.c_int * self.n_pairs)()
+        _check(lib().sam_multi_run(self._h, _stream(stream), out, cap, nout), "sam_multi_run")
+        return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(self.n_pairs)]
+
+    def set_tiling(self, sx, sy, tg, warps):
+        _check(lib().sam_multi_set_tiling(self._h, sx, sy, tg, warps), "sam_multi_set_tiling")
+
+    def autotune(self, stream=None, max_out=256):
+        cfg = (ctypes.c_int32 * (4 * max_out))()
+        ms = (ctypes.c_float * max_out)()
+        n = ctypes.c_int()
+        _check(lib().sam_multi_autotune(self._h, _stream(stream), cfg, ms, max_out, ctypes.byref(n)),
+               "sam_multi_autotune")
+        res = [((cfg[4 * i], cfg[4 * i + 1], cfg[4 * i + 2], cfg[4 * i + 3]), float(ms[i])) for i in range(n.value)]
+        return sorted(res, key=lambda r: r[1])
+
+    def stats(self):
+        pp, gk, db = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
+        _check(lib().sam_multi_stats(self._h, ctypes.byref(pp), ctypes.byref(gk), ctypes.byref(db)), "sam_multi_stats")
+        return {"pose_points": pp.value, "graph_kernels": gk.value, "device_bytes": db.value}
