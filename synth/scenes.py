@@ -236,27 +236,26 @@ def render_scene(bg: np.ndarray, instances, paste_square=False) -> np.ndarray:
 
 
 def _segment_mask(H, W, ax, ay, bx, by, r):
+    """Coverage of a thick segment, as (y0, x0, local array) over its box."""
     x0, x1 = max(0, int(min(ax, bx) - r - 1)), min(W, int(max(ax, bx) + r + 2))
     y0, y1 = max(0, int(min(ay, by) - r - 1)), min(H, int(max(ay, by) + r + 2))
-    cov = np.zeros((H, W), dtype=np.float64)
     if x0 >= x1 or y0 >= y1:
-        return cov
+        return 0, 0, np.zeros((0, 0))
     ys, xs = np.mgrid[y0:y1, x0:x1].astype(np.float64)
     acc = np.zeros(xs.shape)
     for oy in _SUB:
         for ox in _SUB:
             acc += _in_prim(xs + ox, ys + oy, ("slot", ax, ay, bx + 1e-9, by, r))
-    cov[y0:y1, x0:x1] = acc / 16.0
-    return cov
+    return y0, x0, acc / 16.0
 
 
 def _rect_cover(H, W, cx, cy, hw, hh, ang):
+    """Coverage of a rotated rectangle, as (y0, x0, local array) over its box."""
     rad = math.hypot(hw, hh) + 2
     x0, x1 = max(0, int(cx - rad)), min(W, int(cx + rad) + 1)
     y0, y1 = max(0, int(cy - rad)), min(H, int(cy + rad) + 1)
-    cov = np.zeros((H, W), dtype=np.float64)
     if x0 >= x1 or y0 >= y1:
-        return cov
+        return 0, 0, np.zeros((0, 0))
     ys, xs = np.mgrid[y0:y1, x0:x1].astype(np.float64)
     c, s = math.cos(ang), math.sin(ang)
     acc = np.zeros(xs.shape)
@@ -265,8 +264,17 @@ def _rect_cover(H, W, cx, cy, hw, hh, ang):
             dx, dy = xs + ox - cx, ys + oy - cy
             lx, ly = c * dx + s * dy, -s * dx + c * dy
             acc += (np.abs(lx) < hw) & (np.abs(ly) < hh)
-    cov[y0:y1, x0:x1] = acc / 16.0
-    return cov
+    return y0, x0, acc / 16.0
+
+
+def _blend(img, cover, g):
+    """Paint grey level g over img with the given local coverage, in place."""
+    y0, x0, cov = cover
+    h, w = cov.shape
+    if h and w:
+        region = img[y0:y0 + h, x0:x0 + w]
+        img[y0:y0 + h, x0:x0 + w] = region * (1 - cov) + g * cov
+    return img
 
 
 # ----------------------------------------------------------------------------
@@ -348,7 +356,7 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None):
         a = rng.uniform(0, 2 * math.pi)
         cov = _segment_mask(H, W, ax, ay, ax + L * math.cos(a), ay + L * math.sin(a), rng.uniform(0.75, 1.5))
         g = rng.uniform(20, 240)
-        img = img * (1 - cov) + g * cov
+        img = _blend(img, cov, g)
     # occluders: rectangles covering 0-40 % of each instance
     for p in poses:
         frac = rng.uniform(0.0, 0.4)
@@ -362,7 +370,7 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None):
         a = rng.uniform(0, 2 * math.pi)
         cov = _rect_cover(H, W, p[0] + off * math.cos(a), p[1] + off * math.sin(a), hw, hh, rng.uniform(0, math.pi))
         g = rng.uniform(20, 240)
-        img = img * (1 - cov) + g * cov
+        img = _blend(img, cov, g)
     # illumination ramp: gain linear across the image along a random direction
     g0, g1 = rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5)
     off = rng.uniform(-40, 40)
