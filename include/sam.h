@@ -224,7 +224,7 @@ sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long lon
  * synchronisation, no allocation).
  * ------------------------------------------------------------------------- */
 
-/* Pyramid step (Sec. II, "image pyramid construction"): dst(x, y) =
+/* Pyramid step (Sec. II, image pyramid): dst(x, y) =
  * (src(2x,2y) + src(2x+1,2y) + src(2x,2y+1) + src(2x+1,2y+1) + 2) >> 2 for
  * x < w/2, y < h/2.  src, dst device; dst pitch dst_stride >= w/2. */
 sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, uint8_t *dst, int dst_stride,

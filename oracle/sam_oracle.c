@@ -36,7 +36,7 @@
 #define OR_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------ */
-/* Sec. II: "Edge extraction is followed by an image pyramid construction."  */
+/* Sec. II: after edge extraction the method builds an image pyramid.       */
 /* One pyramid step: 2x2 block mean, rounded half up; odd trailing row/col   */
 /* dropped.  dst is (w/2) x (h/2), row-major, stride w/2.                    */
 /* ------------------------------------------------------------------------ */
@@ -53,8 +53,8 @@ void or_pyramid_down(const uint8_t *src, int w, int h, uint8_t *dst)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. II: "The generating x-gradients, y-gradients and gradient            */
-/* magnitudes of edge points are recorded."  3x3 Sobel, integer:             */
+/* Sec. II: the x and y gradients and the gradient magnitude of every edge  */
+/* point are kept.  Operator (unnamed in the paper): 3x3 Sobel, integer:    */
 /*   gx = sum_{r=-1..1} w_r (I[y+r][x+1] - I[y+r][x-1]),  w = (1, 2, 1)      */
 /*   gy = sum_{c=-1..1} w_c (I[y+1][x+c] - I[y-1][x+c])                      */
 /* Border pixels (first/last row and column) get gx = gy = 0.                */
@@ -84,14 +84,14 @@ static int or_is_edge(int32_t gx, int32_t gy, int T)
     return m2 >= (int64_t)16 * T * T;
 }
 
-/* Sec. II "edge detection thresholds", search image: one threshold T_low.  */
+/* Sec. II edge thresholds, search image: one threshold T_low.              */
 void or_search_mask(const int32_t *gx, const int32_t *gy, int npx, int low, uint8_t *mask)
 {
     for (int i = 0; i < npx; ++i)
         mask[i] = (uint8_t)or_is_edge(gx[i], gy[i], low);
 }
 
-/* Sec. II "edge detection thresholds", model image: hysteresis.  A pixel is
+/* Sec. II edge thresholds, model image: hysteresis.  A pixel is
  * an edge if it is >= T_low and 8-connected through >= T_low pixels to a
  * pixel >= T_high.  Plain flood fill with an explicit stack.               */
 void or_hysteresis(const int32_t *gx, const int32_t *gy, int w, int h, int low, int high, uint8_t *mask)
