@@ -30,4 +30,7 @@ from .oracle import (  # noqa: F401
     nms,
     detect,
     DetectParams,
+    score_bilinear,
+    bilinear_border_mask,
+    refine_gn,
 )

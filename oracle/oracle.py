@@ -27,6 +27,7 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _c_int = ctypes.c_int
 _c_dbl = ctypes.c_double
+_vp = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +71,14 @@ def _L():
                                         _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p]
         lib.or_nms.argtypes = [_c_int, _i32p, _i32p, _i32p, _f64p, _c_int, _c_int, _c_int, _c_int, _i32p]
         lib.or_nms.restype = _c_int
+        lib.or_score_bilinear.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int,
+                                          _c_dbl, _c_dbl, _c_dbl, _c_int, _vp, _vp, _vp]
+        lib.or_score_bilinear.restype = _c_dbl
+        lib.or_bilinear_border_mask.argtypes = [_i32p, _i32p, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _u8p]
+        lib.or_bilinear_border_mask.restype = _c_int
+        lib.or_refine_gn.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
+                                     _f64p, _c_int]
+        lib.or_refine_gn.restype = _c_dbl
         _lib = lib
     return _lib
 
@@ -318,3 +327,45 @@ def detect(model: OracleModel, img, params: DetectParams, trace=None):
     H, W = img.shape
     keep = nms(xs, ys, ks, ss, W, H, min(w0, h0), params.max_detections)
     return [(int(xs[i]), int(ys[i]), float(ks[i]) * model.angle_step_deg, float(ss[i]), int(ks[i])) for i in keep]
+
+
+# ---------------------------------------------------------------------------
+# differentiable score on a continuous pose (extension of Eq. (1), Eq. (2))
+# ---------------------------------------------------------------------------
+
+def _opt_out(k):
+    a = np.zeros(k, dtype=np.float64)
+    return a, a.ctypes.data_as(_vp)
+
+
+def score_bilinear(field, pts, x, y, theta_deg, polarity=0, want=()):
+    """M_c at a continuous pose, FP64.  `want` may hold "grad", "jtj", "jtr";
+    returns the score alone, or (score, {name: array}) when `want` is set."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    outs = {k: _opt_out(n) for k, n in (("grad", 3), ("jtj", 6), ("jtr", 3)) if k in want}
+    ptr = lambda k: outs[k][1] if k in outs else None  # noqa: E731
+    s = _L().or_score_bilinear(field, w, h, tx, ty, gx, gy, len(tx), float(x), float(y), float(theta_deg),
+                               int(polarity), ptr("grad"), ptr("jtj"), ptr("jtr"))
+    if not want:
+        return s
+    return s, {k: v[0] for k, v in outs.items()}
+
+
+def bilinear_border_mask(pts, x, y, theta_deg, eps):
+    """Boolean mask of the points whose sample lies within eps of a pixel-cell border."""
+    tx, ty = _i32(pts[0]), _i32(pts[1])
+    mask = np.zeros(len(tx), dtype=np.uint8)
+    _L().or_bilinear_border_mask(tx, ty, len(tx), float(x), float(y), float(theta_deg), float(eps), mask)
+    return mask.astype(bool)
+
+
+def refine_gn(field, pts, pose, iterations=20, polarity=0):
+    """Damped Gauss-Newton refinement of a continuous pose; returns (pose, M_c)."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    p = np.array(pose, dtype=np.float64)
+    s = _L().or_refine_gn(field, w, h, tx, ty, gx, gy, len(tx), int(polarity), p, int(iterations))
+    return p, s

@@ -478,3 +478,211 @@ int or_nms(int n, const int32_t *x, const int32_t *y, const int32_t *k, const do
     free(sc);
     return nk;
 }
+
+/* ======================================================================== */
+/* Differentiable score on a continuous pose (an extension of Eq. (1); the  */
+/* paper scores integer poses only).  For a continuous pose u = (x, y) and  */
+/* angle theta in degrees, every model point is placed at                   */
+/*   p_i = R(theta) t_i + u            (Eq. (2), no rounding)               */
+/* and its unit model direction turned to d_i = R(theta) g_i / |g_i|.       */
+/* The search field w_hat is sampled by bilinear interpolation at p_i (the  */
+/* four surrounding pixels, those outside the image counting as (0, 0)):   */
+/*   w_bil(p) = (1-fx)(1-fy) w00 + fx(1-fy) w10 + (1-fx) fy w01 + fx fy w11 */
+/* with x0 = floor(px), fx = px - x0 (and the same in y).  No neighbourhood */
+/* maximum is taken (it is not differentiable).  The score is              */
+/*   M_c = (1/n) sum_i term_i,   term_i = d_i . w_bil(p_i)                  */
+/* (polarity 1: |d_i . w_bil(p_i)|).  Inside a pixel cell w_bil is          */
+/* bilinear, so its partial derivatives there are                           */
+/*   dw/dx = (1-fy)(w10 - w00) + fy(w11 - w01)                              */
+/*   dw/dy = (1-fx)(w01 - w00) + fx(w11 - w10)                              */
+/* (one-sided at cell borders, the side that floor() selects).  Chain rule: */
+/*   d term/dx = d . dw/dx,  d term/dy = d . dw/dy,                         */
+/*   d term/dtheta = (R'g/|g|) . w_bil + d . (dw/dx (R't)_x + dw/dy (R't)_y) */
+/* with R' = dR/dtheta = [[-s, -c], [c, -s]], times pi/180 per degree.      */
+/* Polarity 1 multiplies each derivative by sign(d . w_bil) (0 at 0).       */
+/* ======================================================================== */
+
+/* Field vector at integer pixel (x, y); (0, 0) outside the image. */
+static void or_field_at(const double *field, int w, int h, int x, int y, double *vx, double *vy)
+{
+    if (x >= 0 && y >= 0 && x < w && y < h) {
+        *vx = field[2 * ((size_t)y * w + x)];
+        *vy = field[2 * ((size_t)y * w + x) + 1];
+    } else {
+        *vx = 0.0;
+        *vy = 0.0;
+    }
+}
+
+/* Score M_c at (x, y, theta_deg).  Optional outputs (NULL to skip), all
+ * divided by n like the score:
+ *   grad[3] = dM_c / d(x, y, theta_deg);
+ *   jtj[6]  = (1/n) sum_i J_i J_i^T  as (xx, xy, xt, yy, yt, tt);
+ *   jtr[3]  = (1/n) sum_i J_i (1 - term_i);
+ * where J_i = d term_i / d(x, y, theta_deg): the normal equations of the
+ * Gauss-Newton fit of every term to 1.                                    */
+double or_score_bilinear(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                         const int32_t *gx, const int32_t *gy, int n, double x, double y, double theta_deg,
+                         int polarity, double *grad, double *jtj, double *jtr)
+{
+    double th = theta_deg * OR_PI / 180.0;
+    double c = cos(th), s = sin(th);
+    double sum = 0.0;
+    double g[3] = {0.0, 0.0, 0.0};
+    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i) {
+        double txi = (double)tx[i], tyi = (double)ty[i];
+        double m = sqrt((double)gx[i] * gx[i] + (double)gy[i] * gy[i]);
+        double ux = gx[i] / m, uy = gy[i] / m;
+        /* Eq. (2) and the turned direction */
+        double px = c * txi - s * tyi + x;
+        double py = s * txi + c * tyi + y;
+        double dx = c * ux - s * uy;
+        double dy = s * ux + c * uy;
+        /* bilinear sample */
+        double fx0 = floor(px), fy0 = floor(py);
+        int x0 = (int)fx0, y0 = (int)fy0;
+        double fx = px - fx0, fy = py - fy0;
+        double w00x, w00y, w10x, w10y, w01x, w01y, w11x, w11y;
+        or_field_at(field, w, h, x0, y0, &w00x, &w00y);
+        or_field_at(field, w, h, x0 + 1, y0, &w10x, &w10y);
+        or_field_at(field, w, h, x0, y0 + 1, &w01x, &w01y);
+        or_field_at(field, w, h, x0 + 1, y0 + 1, &w11x, &w11y);
+        double wx = (1 - fx) * (1 - fy) * w00x + fx * (1 - fy) * w10x + (1 - fx) * fy * w01x + fx * fy * w11x;
+        double wy = (1 - fx) * (1 - fy) * w00y + fx * (1 - fy) * w10y + (1 - fx) * fy * w01y + fx * fy * w11y;
+        double dwx_dx = (1 - fy) * (w10x - w00x) + fy * (w11x - w01x);
+        double dwy_dx = (1 - fy) * (w10y - w00y) + fy * (w11y - w01y);
+        double dwx_dy = (1 - fx) * (w01x - w00x) + fx * (w11x - w10x);
+        double dwy_dy = (1 - fx) * (w01y - w00y) + fx * (w11y - w10y);
+        double term = dx * wx + dy * wy;
+        /* derivatives of term */
+        double jx = dx * dwx_dx + dy * dwy_dx;
+        double jy = dx * dwx_dy + dy * dwy_dy;
+        double rtx = -s * txi - c * tyi;     /* (R' t)_x */
+        double rty = c * txi - s * tyi;      /* (R' t)_y */
+        double rdx = -s * ux - c * uy;       /* (R' g/|g|)_x */
+        double rdy = c * ux - s * uy;        /* (R' g/|g|)_y */
+        double jt = (rdx * wx + rdy * wy + jx * rtx + jy * rty) * (OR_PI / 180.0);
+        if (polarity) {
+            double sg = term > 0 ? 1.0 : (term < 0 ? -1.0 : 0.0);
+            term = fabs(term);
+            jx *= sg;
+            jy *= sg;
+            jt *= sg;
+        }
+        sum += term;
+        g[0] += jx;
+        g[1] += jy;
+        g[2] += jt;
+        a[0] += jx * jx;
+        a[1] += jx * jy;
+        a[2] += jx * jt;
+        a[3] += jy * jy;
+        a[4] += jy * jt;
+        a[5] += jt * jt;
+        b[0] += jx * (1.0 - term);
+        b[1] += jy * (1.0 - term);
+        b[2] += jt * (1.0 - term);
+    }
+    if (grad)
+        for (int j = 0; j < 3; ++j)
+            grad[j] = g[j] / n;
+    if (jtj)
+        for (int j = 0; j < 6; ++j)
+            jtj[j] = a[j] / n;
+    if (jtr)
+        for (int j = 0; j < 3; ++j)
+            jtr[j] = b[j] / n;
+    return sum / n;
+}
+
+/* Marks (mask[i] = 1) the model points whose sample p_i at (x, y,
+ * theta_deg) lies within eps of a pixel-cell border in x or in y, where the
+ * one-sided derivative of the bilinear sample may jump.  Returns how many.  */
+int or_bilinear_border_mask(const int32_t *tx, const int32_t *ty, int n, double x, double y, double theta_deg,
+                            double eps, uint8_t *mask)
+{
+    double th = theta_deg * OR_PI / 180.0;
+    double c = cos(th), s = sin(th);
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        double px = c * tx[i] - s * ty[i] + x;
+        double py = s * tx[i] + c * ty[i] + y;
+        double ex = px - floor(px + 0.5), ey = py - floor(py + 0.5);
+        mask[i] = (uint8_t)(fabs(ex) < eps || fabs(ey) < eps);
+        cnt += mask[i];
+    }
+    return cnt;
+}
+
+/* Solve the symmetric 3x3 system A d = b (A packed as xx, xy, xt, yy, yt,
+ * tt) by Cramer's rule.  Returns 0 if the determinant is not positive.    */
+static int or_solve3(const double *A, const double *b, double *d)
+{
+    double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[3], a12 = A[4], a22 = A[5];
+    double c00 = a11 * a22 - a12 * a12;
+    double c01 = a02 * a12 - a01 * a22;
+    double c02 = a01 * a12 - a02 * a11;
+    double det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(det > 0.0))
+        return 0;
+    double c11 = a00 * a22 - a02 * a02;
+    double c12 = a01 * a02 - a00 * a12;
+    double c22 = a00 * a11 - a01 * a01;
+    d[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) / det;
+    d[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) / det;
+    d[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) / det;
+    return 1;
+}
+
+/* Continuous pose refinement by damped Gauss-Newton (Levenberg-Marquardt)
+ * on the terms of M_c, each fitted to 1:
+ *   lambda = 1e-3; evaluate M_c, J^T J, J^T r at the pose;
+ *   repeat `iterations` times:
+ *     A = J^T J + lambda diag(J^T J) + 1e-9 I;  solve A d = J^T r;
+ *     scale d down so that max(|dx|, |dy|, |dtheta|) <= 1 (px, px, deg);
+ *     evaluate at pose + d; if M_c rose strictly, move there and set
+ *     lambda = max(lambda / 3, 1e-7); else lambda = min(4 lambda, 1e7).
+ * If the system is singular the iteration only raises lambda.  Every
+ * iteration costs exactly one evaluation of M_c and its normal equations.
+ * pose[3] = (x, y, theta_deg) in and out; returns the final M_c.           */
+double or_refine_gn(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                    const int32_t *gx, const int32_t *gy, int n, int polarity, double *pose, int iterations)
+{
+    double A[6], b[3];
+    double lambda = 1e-3;
+    double S = or_score_bilinear(field, w, h, tx, ty, gx, gy, n, pose[0], pose[1], pose[2], polarity, NULL, A, b);
+    for (int it = 0; it < iterations; ++it) {
+        double M[6] = {A[0], A[1], A[2], A[3], A[4], A[5]};
+        M[0] += lambda * A[0] + 1e-9;
+        M[3] += lambda * A[3] + 1e-9;
+        M[5] += lambda * A[5] + 1e-9;
+        double d[3];
+        if (!or_solve3(M, b, d)) {
+            lambda = fmin(4.0 * lambda, 1e7);
+            continue;
+        }
+        double big = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
+        if (big > 1.0) {
+            d[0] /= big;
+            d[1] /= big;
+            d[2] /= big;
+        }
+        double q[3] = {pose[0] + d[0], pose[1] + d[1], pose[2] + d[2]};
+        double A2[6], b2[3];
+        double S2 = or_score_bilinear(field, w, h, tx, ty, gx, gy, n, q[0], q[1], q[2], polarity, NULL, A2, b2);
+        if (S2 > S) {
+            pose[0] = q[0];
+            pose[1] = q[1];
+            pose[2] = q[2];
+            S = S2;
+            memcpy(A, A2, sizeof(A));
+            memcpy(b, b2, sizeof(b));
+            lambda = fmax(lambda / 3.0, 1e-7);
+        } else {
+            lambda = fmin(4.0 * lambda, 1e7);
+        }
+    }
+    return S;
+}
