@@ -210,6 +210,65 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched uneven form (config 3 shape)
+# ---------------------------------------------------------------------------
+
+def levels_for_side(side):
+    """Pyramid levels of a template: 3 up to 96 px, else 4 (360 one-degree
+    angles halve exactly three times: 360, 180, 90, 45)."""
+    return 3 if side <= 96 else 4
+
+
+def run_batched(args, sam, torch, dev, stream):
+    tmpls, images, pairs, _ = synth.config3_batch(n_images=args.multi)
+    models = [sam.Model(t, LOW, HIGH, levels_for_side(t.shape[0]), STEP) for t in tmpls]
+    sizes = [(im.shape[1], im.shape[0]) for im in images]
+    out = {"images": len(images), "pairs": len(pairs), "templates": [t.shape[0] for t in tmpls],
+           "workload": "config3: 64 images of 640x480..2592x1944, 8 templates 64..400 px, 2 per image"}
+    for name, code in (("fp32", 0), ("bf16", 1), ("fp16", 2)):
+        params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
+                                           precision=code, early_termination=1)
+        plan = sam.MultiPlan(models, sizes, pairs, params)
+        for i, im in enumerate(images):
+            plan.set_image(i, torch.from_numpy(im).to(dev))
+        tuning = plan.autotune()
+        for _ in range(3):
+            res = plan.run()
+        st = plan.stats()
+        n = max(5, min(20, args.steps))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            res = plan.run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / n
+        out[name] = {"value": st["pose_points"] / (ms * 1e-3), "unit": UNIT, "ms_per_batch": round(ms, 3),
+                     "ms_per_pair": round(ms / len(pairs), 4), "pose_points_per_batch": st["pose_points"],
+                     "graph_kernels": st["graph_kernels"], "runs": n,
+                     "tiling": tuning[0][0] if tuning else None,
+                     "detections": int(sum(len(r) for r in res))}
+        plan.close()
+    # the same pairs through the single-image path, one detect call per pair
+    params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
+                                       precision=0, early_termination=1)
+    dimgs = [torch.from_numpy(im).to(dev) for im in images]
+    for i, m in pairs[:8]:
+        sam.detect(models[m], dimgs[i], params)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i, m in pairs:
+        sam.detect(models[m], dimgs[i], params)
+    torch.cuda.synchronize(dev)
+    ms = (time.perf_counter() - t0) * 1e3
+    out["sequential_fp32"] = {"ms_per_batch": round(ms, 3), "ms_per_pair": round(ms / len(pairs), 4),
+                              "value": out["fp32"]["pose_points_per_batch"] / (ms * 1e-3), "unit": UNIT,
+                              "what": "one detect call per pair (single-image path), host-timed"}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -356,6 +415,9 @@ def run_gpu(args):
                            "same_detections_as_fp32": bool(same), "steps": n_form,
                            "tiling": dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model, code)))}
 
+    # ---- the batched uneven form: many image sizes and templates, one graph ----
+    batched = run_batched(args, sam, torch, dev, stream) if (args.multi > 0 and rank == 0) else None
+
     # ---- the scorer with every pose fully evaluated (no early termination) ----
     full_params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
                                             precision=params.precision, early_termination=0)
@@ -427,6 +489,7 @@ def run_gpu(args):
         "clocks": clocks,
         "detections_per_image": ndet[:8],
         "forms": forms,
+        "batched": batched,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -448,6 +511,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--forms", type=int, default=1, help="also time the FP16/BF16 stored forms")
+    ap.add_argument("--multi", type=int, default=64, help="images of the batched uneven form (0: skip)")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
