@@ -318,6 +318,67 @@ sam_status sam_candidates_noalloc(const float *map, int nth, int gh, int gw, flo
                                   int32_t *out_kyx, float *out_s, int *count, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Differentiable score on continuous poses (an extension: the paper scores
+ * integer poses only).  For pose (x, y, theta) -- x, y in pixels of the
+ * model level's image, theta in degrees -- every model point t_i of that
+ * level is placed at p_i = R(theta) t_i + (x, y) (Eq. (2) without rounding),
+ * its unit direction turned to d_i = R(theta) g_i/|g_i|, and the unit search
+ * field is sampled at p_i by bilinear interpolation of the four surrounding
+ * pixels (pixels outside the image count as (0, 0)):
+ *   M_c = (1/n) sum_i d_i . w_bil(p_i)       (polarity 1: |d_i . w_bil(p_i)|)
+ * (Eq. (1) at a continuous pose, without the neighbourhood maximum, which is
+ * not differentiable).  Its derivatives are those of the bilinear sample
+ * inside each pixel cell (one-sided at cell borders: the cell of floor(p)).
+ *
+ * Fields are FP32 unit fields in SAM_LAYOUT_PIXEL as written by sam_gradient
+ * (interleaved (wx, wy), row pitch `pitch` pixels >= w; device memory, 8-byte
+ * aligned), one per search image; a pose names its field by index
+ * (pose_field, device int32 per pose; NULL: every pose uses field 0).  At
+ * most SAM_MAX_BILINEAR_FIELDS fields per call.  Poses are device float
+ * arrays of 3 per pose (x, y, theta_deg).  A pose whose field index is out
+ * of range or whose coordinates are not finite (or exceed 2^24 in x, y)
+ * gets NaN outputs.  FP32 arithmetic with sin/cos of the pose in FP64.  All
+ * calls are stream-ordered and allocation-free; they do not synchronise.
+ * Errors: SAM_ERR_ARG (level, counts, null pointers, field sizes), SAM_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define SAM_MAX_BILINEAR_FIELDS 64
+typedef struct {
+    const float *field; /* device, FP32 (wx, wy) per pixel */
+    int w, h;           /* pixels */
+    int pitch;          /* row pitch in pixels, >= w */
+} sam_field_ref;
+
+/* Forward: score[b] = M_c at pose b.  Optional outputs (NULL to skip):
+ * grad[3b ..] = dM_c/d(x, y, theta_deg); normal[9b ..] = the normal
+ * equations of the Gauss-Newton fit of every term to 1, (1/n) sum J_i J_i^T
+ * packed (xx, xy, xt, yy, yt, tt) then (1/n) sum J_i (1 - term_i), where
+ * J_i = d term_i / d(x, y, theta_deg). */
+sam_status sam_score_bilinear(sam_model *m, int level, const sam_field_ref *fields, int n_fields,
+                              const int32_t *pose_field, const float *poses, int n_poses, float *score, float *grad,
+                              float *normal, void *stream);
+
+/* Adjoint: grad_pose[3b ..] = grad_score[b] * dM_c/d(x, y, theta_deg) at
+ * pose b (the vector-Jacobian product of the forward).  grad_score and
+ * grad_pose device float arrays of n_poses and 3 n_poses. */
+sam_status sam_score_bilinear_adjoint(sam_model *m, int level, const sam_field_ref *fields, int n_fields,
+                                      const int32_t *pose_field, const float *poses, int n_poses,
+                                      const float *grad_score, float *grad_pose, void *stream);
+
+/* Sub-pixel and sub-degree refinement of n_poses poses (in place), one
+ * launch: damped Gauss-Newton (Levenberg-Marquardt) on the terms of M_c,
+ * each fitted to 1.  Per pose, lambda = 1e-3 and M_c with its normal
+ * equations are evaluated at the start pose; then `iterations` times: solve
+ * (J^T J + lambda diag(J^T J) + 1e-9 I) d = J^T r in FP64, scale d so that
+ * max(|dx|, |dy|, |dtheta|) <= 1, evaluate at pose + d, and move there with
+ * lambda = max(lambda/3, 1e-7) if M_c rose strictly, else lambda =
+ * min(4 lambda, 1e7) (a singular system only raises lambda).  The pose is
+ * carried in FP64 and written back rounded to FP32; score (device float per
+ * pose, may be NULL) receives the final M_c.  0 <= iterations <= 10000. */
+sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields, int n_fields,
+                            const int32_t *pose_field, float *poses, int n_poses, int iterations, float *score,
+                            void *stream);
+
+/* ---------------------------------------------------------------------------
  * Stage timing (tracing).  When enabled, sam_detect / sam_detect_batch record
  * CUDA events on the caller's stream before and after the launches of each
  * stage and, at the synchronisation that ends the call, add the elapsed

@@ -13,12 +13,15 @@ from .sam import (  # noqa: F401
     SIGNATURES,
     STAGES,
     DetectParams,
+    FieldRef,
+    MAX_BILINEAR_FIELDS,
     Model,
     ModelParams,
     MultiPlan,
     Pose,
     SamError,
     autotune,
+    bilinear_score,
     candidates,
     candidates_noalloc,
     candidates_scratch_bytes,
@@ -34,9 +37,13 @@ from .sam import (  # noqa: F401
     profile_enable,
     profile_read,
     pyramid_down,
+    refine_poses,
+    score_bilinear,
+    score_bilinear_adjoint,
     score_map,
     set_score_kernel,
     status_str,
     take_device_error,
+    unit_field,
 )
 from .build import build  # noqa: F401

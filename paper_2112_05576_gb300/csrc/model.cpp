@@ -204,7 +204,7 @@ sam_status upload_model(sam_model *m) {
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     for (const LevelHost &L : m->lv)
         bytes += align(L.rot.size() * sizeof(RotPt)) + align(L.bbox.size() * sizeof(int4)) +
-                 align(std::max<size_t>(1, L.shift.size()) * sizeof(int2));
+                 align(std::max<size_t>(1, L.shift.size()) * sizeof(int2)) + align((size_t)L.n * sizeof(float4));
     void *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess)
         return SAM_ERR_NOMEM;
@@ -229,6 +229,17 @@ sam_status upload_model(sam_model *m) {
             cudaMemcpy(p, L.shift.data(), L.shift.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
             goto fail;
         p += align(std::max<size_t>(1, L.shift.size()) * sizeof(int2));
+        {
+            std::vector<float4> base((size_t)L.n);
+            for (int i = 0; i < L.n; ++i) {
+                double mg = sqrt((double)L.gx[i] * L.gx[i] + (double)L.gy[i] * L.gy[i]);
+                base[i] = make_float4((float)L.tx[i], (float)L.ty[i], (float)(L.gx[i] / mg), (float)(L.gy[i] / mg));
+            }
+            D.base = (const float4 *)p;
+            if (cudaMemcpy(p, base.data(), base.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+                goto fail;
+            p += align((size_t)L.n * sizeof(float4));
+        }
     }
     m->d_tables = base;
     m->device = dev;

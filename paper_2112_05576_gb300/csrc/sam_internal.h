@@ -38,6 +38,7 @@ struct LevelDev {
     const RotPt *rot;
     const int4 *bbox;
     const int2 *shift;
+    const float4 *base;   // [n] unrotated (tx, ty, gx/|g|, gy/|g|) for the continuous-pose score
 };
 
 struct Workspace {

@@ -42,6 +42,12 @@ class Pose(ctypes.Structure):
                 ("angle_index", _c_int), ("level0_x", _c_int), ("level0_y", _c_int), ("reserved", _c_int)]
 
 
+class FieldRef(ctypes.Structure):
+    _fields_ = [("field", _vp), ("w", _c_int), ("h", _c_int), ("pitch", _c_int)]
+
+
+MAX_BILINEAR_FIELDS = 64
+
 # name -> (restype, argtypes); every symbol include/sam.h declares
 SIGNATURES = {
     "sam_status_str": (ctypes.c_char_p, [_c_int]),
@@ -86,6 +92,11 @@ SIGNATURES = {
     "sam_multi_autotune": (_c_int, [_vp, _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
     "sam_multi_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "sam_score_bilinear": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _vp, _vp, _vp,
+                                    _vp]),
+    "sam_score_bilinear_adjoint": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _vp,
+                                            _vp, _vp]),
+    "sam_refine_poses": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
     "sam_profile_enable": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
     "sam_kernel_launches": (ctypes.c_longlong, []),
@@ -426,3 +437,129 @@ class MultiPlan:
         pp, gk, db = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
         _check(lib().sam_multi_stats(self._h, ctypes.byref(pp), ctypes.byref(gk), ctypes.byref(db)), "sam_multi_stats")
         return {"pose_points": pp.value, "graph_kernels": gk.value, "device_bytes": db.value}
+
+
+# ---------------------------------------------------------------------------
+# differentiable score on continuous poses
+# ---------------------------------------------------------------------------
+
+def unit_field(img, low, stream=None):
+    """FP32 unit gradient field (H, W, 2) of a uint8 CUDA image, pixel layout."""
+    import torch
+    h, w = img.shape
+    field = torch.empty((h, w, 2), dtype=torch.float32, device=img.device)
+    gradient(img, low, FP32, field, stream=stream, layout=LAYOUT_PIXEL)
+    return field
+
+
+def _field_refs(fields):
+    """ctypes array of FieldRef for a list of (H, W, 2) float32 CUDA tensors
+    (row pitch may exceed W: a view with strides (2 P, 2, 1))."""
+    import torch
+    if len(fields) < 1 or len(fields) > MAX_BILINEAR_FIELDS:
+        raise ValueError(f"between 1 and {MAX_BILINEAR_FIELDS} fields per call")
+    refs = (FieldRef * len(fields))()
+    for i, f in enumerate(fields):
+        if f.dtype != torch.float32 or f.dim() != 3 or f.shape[2] != 2 or not f.is_cuda \
+                or f.stride(2) != 1 or f.stride(1) != 2 or f.stride(0) % 2:
+            raise ValueError("fields are (H, W, 2) float32 CUDA tensors with unit inner strides")
+        refs[i] = FieldRef(f.data_ptr(), f.shape[1], f.shape[0], f.stride(0) // 2)
+    return refs
+
+
+def _poses_arg(poses):
+    import torch
+    if poses.dtype != torch.float32 or poses.dim() != 2 or poses.shape[1] != 3 or not poses.is_contiguous():
+        raise ValueError("poses are a contiguous (B, 3) float32 CUDA tensor of (x, y, theta_deg)")
+    return poses
+
+
+def _pose_field_arg(pose_field, B):
+    import torch
+    if pose_field is None:
+        return None
+    if pose_field.dtype != torch.int32 or pose_field.numel() != B or not pose_field.is_contiguous():
+        raise ValueError("pose_field is a contiguous int32 CUDA tensor with one entry per pose")
+    return pose_field
+
+
+def score_bilinear(model: Model, fields, poses, pose_field=None, level=0, grad=False, normal=False, stream=None):
+    """Continuous-pose score M_c of each pose (B,); with grad=True also
+    dM_c/d(x, y, theta_deg) (B, 3); with normal=True also the Gauss-Newton
+    normal equations (B, 9): J^T J packed (xx, xy, xt, yy, yt, tt), J^T r."""
+    import torch
+    poses = _poses_arg(poses)
+    B = poses.shape[0]
+    pf = _pose_field_arg(pose_field, B)
+    refs = _field_refs(fields)
+    dev = poses.device
+    score = torch.empty(B, dtype=torch.float32, device=dev)
+    g = torch.empty((B, 3), dtype=torch.float32, device=dev) if grad else None
+    nrm = torch.empty((B, 9), dtype=torch.float32, device=dev) if normal else None
+    _check(lib().sam_score_bilinear(model.handle, int(level), refs, len(fields), _ptr(pf), _ptr(poses), B,
+                                    _ptr(score), _ptr(g), _ptr(nrm), _stream(stream)), "sam_score_bilinear")
+    out = [score] + ([g] if grad else []) + ([nrm] if normal else [])
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def score_bilinear_adjoint(model: Model, fields, poses, grad_score, pose_field=None, level=0, stream=None):
+    """grad_score[b] * dM_c/d(x, y, theta_deg) at each pose, (B, 3)."""
+    import torch
+    poses = _poses_arg(poses)
+    B = poses.shape[0]
+    pf = _pose_field_arg(pose_field, B)
+    refs = _field_refs(fields)
+    gs = grad_score.to(torch.float32).contiguous()
+    gp = torch.empty((B, 3), dtype=torch.float32, device=poses.device)
+    _check(lib().sam_score_bilinear_adjoint(model.handle, int(level), refs, len(fields), _ptr(pf), _ptr(poses), B,
+                                            _ptr(gs), _ptr(gp), _stream(stream)), "sam_score_bilinear_adjoint")
+    return gp
+
+
+def refine_poses(model: Model, fields, poses, pose_field=None, iterations=20, level=0, stream=None):
+    """Damped Gauss-Newton refinement of (B, 3) poses in place (one launch);
+    returns the final M_c per pose."""
+    import torch
+    poses = _poses_arg(poses)
+    B = poses.shape[0]
+    pf = _pose_field_arg(pose_field, B)
+    refs = _field_refs(fields)
+    score = torch.empty(B, dtype=torch.float32, device=poses.device)
+    _check(lib().sam_refine_poses(model.handle, int(level), refs, len(fields), _ptr(pf), _ptr(poses), B,
+                                  int(iterations), _ptr(score), _stream(stream)), "sam_refine_poses")
+    return score
+
+
+def _autograd_function():
+    import torch
+
+    class ScoreBilinear(torch.autograd.Function):
+        """M_c(poses) with the library's adjoint kernel as backward.  The
+        pose tensor is the only differentiable input."""
+
+        @staticmethod
+        def forward(ctx, poses, model, fields, pose_field, level):
+            p = poses.detach().contiguous()
+            ctx.save_for_backward(p)
+            ctx.model, ctx.fields, ctx.pose_field, ctx.level = model, fields, pose_field, level
+            return score_bilinear(model, fields, p, pose_field, level)
+
+        @staticmethod
+        def backward(ctx, grad_score):
+            (p,) = ctx.saved_tensors
+            gp = score_bilinear_adjoint(ctx.model, ctx.fields, p, grad_score.contiguous(), ctx.pose_field, ctx.level)
+            return gp, None, None, None, None
+
+    return ScoreBilinear
+
+
+_SCORE_FN = None
+
+
+def bilinear_score(poses, model: Model, fields, pose_field=None, level=0):
+    """Differentiable M_c of (B, 3) poses (torch.autograd; backward runs the
+    adjoint kernel)."""
+    global _SCORE_FN
+    if _SCORE_FN is None:
+        _SCORE_FN = _autograd_function()
+    return _SCORE_FN.apply(poses, model, list(fields), pose_field, int(level))
