@@ -269,6 +269,79 @@ def run_batched(args, sam, torch, dev, stream):
 
 
 # ---------------------------------------------------------------------------
+# differentiable form (config 4 shape)
+# ---------------------------------------------------------------------------
+
+def _event_ms(torch, dev, stream, fn, reps):
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def run_differentiable(args, sam, torch, dev, stream, with_oracle):
+    n_tr = args.refine
+    tmpl, imgs, triples = synth.config4_triples(n=n_tr)
+    model = sam.Model(tmpl, LOW, HIGH, LEVELS, STEP)
+    fields = [sam.unit_field(torch.from_numpy(im).to(dev), LOW) for im in imgs]
+    init = torch.tensor([t[2] for t in triples], dtype=torch.float32, device=dev)
+    gt = np.array([t[1] for t in triples], dtype=np.float64)
+    pf = torch.tensor([t[0] for t in triples], dtype=torch.int32, device=dev)
+    npts = model.num_points(0)
+    reps = 20
+    out = {"workload": f"config4: {n_tr} (scene, pose) pairs, 4 scenes 1280x1024, 200x200 part "
+                       f"({npts} level-0 points), start +-1.5 px / +-1.5 deg from truth",
+           "poses": n_tr, "points": npts}
+    # forward alone, and forward + backward through the autograd Function
+    for _ in range(3):
+        sam.score_bilinear(model, fields, init, pf)
+    ms_f = _event_ms(torch, dev, stream, lambda i: sam.score_bilinear(model, fields, init, pf), reps)
+    ones = torch.ones(n_tr, device=dev)
+
+    def fb(i):
+        p = init.clone().requires_grad_(True)
+        sam.bilinear_score(p, model, fields, pf).backward(ones)
+
+    for _ in range(3):
+        fb(0)
+    ms_fb = _event_ms(torch, dev, stream, fb, reps)
+    out["forward"] = {"ms": round(ms_f, 4), "point_evals_per_s": n_tr * npts / (ms_f * 1e-3)}
+    out["forward_backward"] = {"ms": round(ms_fb, 4), "point_evals_per_s": 2 * n_tr * npts / (ms_fb * 1e-3),
+                               "kernels": 2}
+    # 20 Gauss-Newton iterations, one launch (21 evaluations per pose)
+    copies = [init.clone() for _ in range(reps + 3)]
+    for i in range(3):
+        sam.refine_poses(model, fields, copies[reps + i], pf, iterations=20)
+    ms_r = _event_ms(torch, dev, stream, lambda i: sam.refine_poses(model, fields, copies[i], pf, iterations=20), reps)
+    got = copies[0].cpu().numpy().astype(np.float64)
+    err = np.abs(got - gt)
+    ok = (err[:, 0] < 0.05) & (err[:, 1] < 0.05) & (err[:, 2] < 0.05)
+    out["refine"] = {"iterations": 20, "ms": round(ms_r, 4), "us_per_pose": round(ms_r * 1e3 / n_tr, 3),
+                     "point_evals_per_s": 21 * n_tr * npts / (ms_r * 1e-3),
+                     "within_0.05px_0.05deg": round(float(ok.mean()), 4),
+                     "median_err": [round(float(v), 4) for v in np.median(err, 0)],
+                     "p95_err": [round(float(v), 4) for v in np.percentile(err, 95, axis=0)],
+                     "start_within": round(float(((np.abs(init.cpu().numpy() - gt) < 0.05).all(1)).mean()), 4)}
+    if with_oracle:
+        import oracle
+        om = oracle.create_model(tmpl, LOW, HIGH, LEVELS, STEP)
+        ofs = [oracle.search_fields(im, 1, LOW)[0] for im in imgs]
+        t0 = time.perf_counter()
+        k = 0
+        while k < n_tr and (k < 8 or time.perf_counter() - t0 < args.cpu_budget / 4):
+            oracle.refine_gn(ofs[triples[k][0]], om.points[0], triples[k][2], iterations=20)
+            k += 1
+        el = time.perf_counter() - t0
+        out["refine"]["cpu_baseline"] = {"us_per_pose": round(el * 1e6 / k, 1), "cores": 1, "kind": "oracle",
+                                         "sample": f"{k} poses, 20 iterations, FP64 oracle, one thread"}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -418,6 +491,10 @@ def run_gpu(args):
     # ---- the batched uneven form: many image sizes and templates, one graph ----
     batched = run_batched(args, sam, torch, dev, stream) if (args.multi > 0 and rank == 0) else None
 
+    # ---- the differentiable form: continuous-pose score, adjoint, refinement ----
+    differentiable = (run_differentiable(args, sam, torch, dev, stream, world == 1 and not args.no_cpu)
+                      if (args.refine > 0 and rank == 0) else None)
+
     # ---- the scorer with every pose fully evaluated (no early termination) ----
     full_params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16,
                                             precision=params.precision, early_termination=0)
@@ -490,6 +567,7 @@ def run_gpu(args):
         "detections_per_image": ndet[:8],
         "forms": forms,
         "batched": batched,
+        "differentiable": differentiable,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -512,6 +590,7 @@ def main():
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--forms", type=int, default=1, help="also time the FP16/BF16 stored forms")
     ap.add_argument("--multi", type=int, default=64, help="images of the batched uneven form (0: skip)")
+    ap.add_argument("--refine", type=int, default=4096, help="poses of the differentiable form (0: skip)")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
