@@ -125,24 +125,41 @@ def top_pose_points(model, batch):
 # ---------------------------------------------------------------------------
 # roofline of the exhaustive scoring kernel
 # ---------------------------------------------------------------------------
-# Algorithmic work per pose-point with full reuse of the per-pixel dot
-# products across the 3x3 window (each pixel's dot with a point's direction
-# is computed once and shared by the nine poses whose window holds it): one
-# dot product (2 FP32 ops), the separable 3x3 maximum (2 + 2 comparisons,
-# amortised) and one accumulate.  The comparisons bind: they run on the ALU
-# pipe (64 lanes/clk/SM), two per lane per cycle with the 3-input max, i.e.
-# 128 comparisons/clk/SM -> 32 pose-points/clk/SM.  The FP32 ops (3 per
-# pose-point at 128/clk/SM) would allow 42.7.  Peak in comparisons/s at the
-# maximum SM clock; achieved = nominal pose-points x 4 / launch time.
+# The tiled FP32 kernel is bound by shared-memory bandwidth.  Each thread
+# scores an 8 x 6 block of translations for one angle; for every model
+# point it reads the (8 + 2) x (6 + 2) pixels under the block's 3 x 3
+# windows from the staged FP32 field, 8 bytes per pixel: 640 bytes for 48
+# pose-points, i.e. 13.33 algorithmic shared-memory bytes per pose-point.
+# Peak: 128 bytes/clk/SM x SMs x maximum SM clock.  Achieved counts nominal
+# pose-points (early termination not subtracted, as in the metric); the
+# launch without early termination is reported beside it.
+SMEM_B_PER_PP = 640.0 / 48.0
+SMEM_B_PER_CLK_SM = 128.0
+# Second bound, of the method itself with full reuse of the per-pixel dot
+# products across the 3x3 window: the separable 3x3 maximum costs 4
+# comparisons per pose-point on the ALU pipe, 128/clk/SM with the 3-input max.
 CMP_PER_PP = 4
 CMP_PER_CLK_SM = 128.0
 
 
+# DRAM bytes (read + write) of one score_tiled_kernel launch of this
+# workload, from an ncu capture at the tiling below (summary and command in
+# profiles/score_tiled_config2_batch16.md); reported only when the bench
+# runs that tiling, and to be re-taken whenever the kernel changes.
+NCU_SCORE_TRAFFIC = {"tiling": (1, 1, 3, 8), "bytes": 2834688 + 3940864}
+
+
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
-    achieved = pp_per_launch * CMP_PER_PP / (ms_per_launch * 1e-3) / 1e12
-    peak = CMP_PER_CLK_SM * sm_count * sm_mhz_peak * 1e6 / 1e12
-    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": "score_tiled_kernel (exhaustive top level)"}
+    sec = ms_per_launch * 1e-3
+    achieved = pp_per_launch * SMEM_B_PER_PP / sec / 1e12
+    peak = SMEM_B_PER_CLK_SM * sm_count * sm_mhz_peak * 1e6 / 1e12
+    alu_ach = pp_per_launch * CMP_PER_PP / sec / 1e12
+    alu_peak = CMP_PER_CLK_SM * sm_count * sm_mhz_peak * 1e6 / 1e12
+    return {"bound": "smem", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": "score_tiled_kernel (exhaustive top level)",
+            "alu": {"achieved": round(alu_ach, 3), "peak": round(alu_peak, 3), "unit": "Tcmp/s",
+                    "frac": round(alu_ach / alu_peak, 4)}}
 
 
 # ---------------------------------------------------------------------------
@@ -517,9 +534,12 @@ def run_gpu(args):
     props = torch.cuda.get_device_properties(dev)
     score_ms, score_calls = prof["score_map"]
     rl = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
-                  float(peaks.get("sm_max_mhz", 2070.0)), traffic=args.traffic)
-    rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {props.multi_processor_count} SMs x 128 comparisons/clk "
-                         f"(ALU pipe, 3-input max); 4 comparisons per pose-point")
+                  float(peaks.get("sm_max_mhz", 2070.0)),
+                  traffic=args.traffic if args.traffic is not None else (
+                      NCU_SCORE_TRAFFIC["bytes"]
+                      if tuple(sam.model_tiling(model, params.precision)) == NCU_SCORE_TRAFFIC["tiling"] else None))
+    rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {props.multi_processor_count} SMs x 128 shared-memory "
+                         f"bytes/clk; 13.33 algorithmic bytes per pose-point (8x6 translation block)")
     clocks = clk.summary()
     if clocks.get("sm_mhz"):
         rl["frac_at_observed_clock"] = round(rl["frac"] * float(peaks.get("sm_max_mhz", 2070.0)) / clocks["sm_mhz"], 4)
