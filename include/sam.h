@@ -256,6 +256,31 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
                          int step_x, int step_y, int neighbourhood, float min_score, int early_termination,
                          float *map, void *stream);
 
+/* A window of Eq. (1) scores at one level: the poses x0 <= x < x0 + gw,
+ * y0 <= y < y0 + gh (step 1, neighbourhood 1 or 3) and angle indices
+ * k0 <= k < k0 + nk, written to map[(k - k0) * gh * gw + (y - y0) * gw +
+ * (x - x0)] (device, float, 8-byte aligned).  The paper has no counterpart;
+ * it serves exhaustive searches too large for one score map (a full-
+ * resolution search of a large template over a large image is scored slice
+ * by slice) and the single-image path of the tiled scorers: `field` is the
+ * level's SAM_LAYOUT_PAIRS field in `precision` (16-byte aligned, pitch
+ * field_pitch(w)).  Templates whose rotated extent exceeds one shared-memory
+ * window are scored by the chunked kernel (points grouped by 16 x 16 offset
+ * cell, one staged window per cell).  early_termination as in
+ * sam_score_map (-inf for pruned poses).  For a 16-bit `precision` with a
+ * non-NULL field32 (the level's FP32 SAM_LAYOUT_PIXEL field, pitch w), every
+ * pose within the storage error bound of min_score is rescored in FP32 and
+ * every other pose written -inf, as in sam_detect; scratch (device, 8-byte
+ * aligned) of sam_score_window_scratch_bytes(R) bytes holds up to R such
+ * poses, and poses beyond R are written NaN.  Stream-ordered, no
+ * allocation, no synchronisation.  Errors: SAM_ERR_ARG (ranges, alignment,
+ * nk * gw * gh >= 2^32, nk > 65535, a template no scorer's window fits),
+ * SAM_ERR_CUDA. */
+size_t sam_score_window_scratch_bytes(size_t max_rescored);
+sam_status sam_score_window(sam_model *m, int level, const void *field, int w, int h, int precision, int x0, int y0,
+                            int gw, int gh, int k0, int nk, int neighbourhood, float min_score, int early_termination,
+                            const float *field32, void *scratch, size_t scratch_bytes, float *map, void *stream);
+
 /* Score-kernel selection and tiling, process-wide (autotuner hook; the paper
  * has no counterpart).  kernel: 0 automatic, 1 generic one-thread-per-pose,
  * 2 tiled (falls back to generic when the tiled kernel cannot serve a call).

@@ -356,6 +356,18 @@ cudaError_t launch_tiled_args(const sam_model *m, int level, const ScoreArgs &a,
                               a.h, a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st);
 }
 
+// The chunked scorer's CTA tile (2 x 2 warp tiles of 4 warps): a 16-pixel
+// chunk cell then needs a ~75 KB FP32 window, three CTAs per SM.
+constexpr TileConfig kChunkCfg = {2, 2, 1, 4};
+
+bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a) {
+    int bxw = 0, byw = 0;
+    return a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
+           ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) && a.count <= 65535 &&
+           m->dev[level].crot && m->lv[level].ntheta <= 65535 &&
+           chunked_plan(m->lv[level], a.precision, kChunkCfg.sx, kChunkCfg.sy, &bxw, &byw);
+}
+
 cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
     const ScoreChoice &c = score_choice();
     TileConfig cfg = c.cfg;
@@ -369,6 +381,10 @@ cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, 
     (void)err;
     if (c.kernel != 1 && tiled_ok(m, level, a, cfg))
         return launch_tiled_args(m, level, a, cfg, st);
+    if (c.kernel != 1 && chunked_ok(m, level, a))
+        return launch_score_chunked(m, level, a.field, a.precision, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px,
+                                    a.w, a.h, a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img,
+                                    kChunkCfg, st);
     return launch_score_map_generic(m->dev[level], a, st);
 }
 
@@ -721,6 +737,70 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
     sa.map_img = 0;
     sa.count = 1;
     return launch_score_map(m, level, sa, nullptr, (cudaStream_t)stream) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+size_t sam_score_window_scratch_bytes(size_t max_rescored) { return rescore_scratch_bytes(max_rescored); }
+
+sam_status sam_score_window(sam_model *m, int level, const void *field, int w, int h, int precision, int x0, int y0,
+                            int gw, int gh, int k0, int nk, int neighbourhood, float min_score, int early_termination,
+                            const float *field32, void *scratch, size_t scratch_bytes, float *map, void *stream) {
+    if (!m || level < 0 || level >= m->levels || !field || !map || w < 1 || h < 1 || precision < SAM_FP32 ||
+        precision > SAM_FP16 || (neighbourhood != 1 && neighbourhood != 3) || x0 < 0 || y0 < 0 || gw < 1 ||
+        gh < 1 || x0 > w - gw || y0 > h - gh || k0 < 0 || nk < 1 || nk > 65535 || k0 > m->lv[level].ntheta - nk ||
+        (size_t)nk * gw * gh > 0xFFFFFFFFull || (uintptr_t)field % 16 || (uintptr_t)map % 8)
+        return SAM_ERR_ARG;
+    const bool rescore = precision != SAM_FP32 && field32;
+    if (rescore && (!scratch || scratch_bytes < rescore_scratch_bytes(1) || (uintptr_t)field32 % 8 ||
+                    (uintptr_t)scratch % 8))
+        return SAM_ERR_ARG;
+    sam_status s = upload_model(m);
+    if (s != SAM_OK)
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    ScoreArgs a;
+    a.field = field;
+    a.field_img_px = (size_t)field_pitch(w, SAM_LAYOUT_PAIRS) * h;
+    a.w = w;
+    a.h = h;
+    a.precision = precision;
+    a.layout = SAM_LAYOUT_PAIRS;
+    a.step_x = 1;
+    a.step_y = 1;
+    a.nbhd = neighbourhood;
+    a.polarity = m->p.polarity;
+    a.min_score = min_score;
+    a.early = early_termination ? 1 : 0;
+    a.map = map;
+    a.map_img = (size_t)nk * gw * gh;
+    a.count = 1;
+    const PoseWindow pw{x0, y0, gw, gh, k0, nk};
+    const ScoreChoice &c = score_choice();
+    TileConfig cfg = c.cfg;
+    if (m->tuned[precision] && c.kernel == 0) {
+        cfg.sx = m->tile_sx[precision];
+        cfg.sy = m->tile_sy[precision];
+        cfg.tg = m->tile_tg[precision];
+        cfg.warps = m->tile_warps[precision];
+    }
+    cudaError_t e;
+    if (tiled_ok(m, level, a, cfg))
+        e = launch_score_tiled(m, level, field, precision, field_pitch(w, SAM_LAYOUT_PAIRS), a.field_img_px, w, h, 1,
+                               neighbourhood, m->p.polarity, min_score, a.early, map, a.map_img, cfg, st, &pw);
+    else if (chunked_ok(m, level, a))
+        e = launch_score_chunked(m, level, field, precision, field_pitch(w, SAM_LAYOUT_PAIRS), a.field_img_px, w, h,
+                                 1, neighbourhood, m->p.polarity, min_score, a.early, map, a.map_img, kChunkCfg, st,
+                                 &pw);
+    else
+        return SAM_ERR_ARG;
+    if (e != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (rescore) {
+        const size_t cap = (scratch_bytes - rescore_scratch_bytes(0)) / 8;
+        if (launch_rescore(m->dev[level], (const float2 *)field32, (size_t)w * h, w, h, 1, 1, 1, neighbourhood,
+                           m->p.polarity, min_score, precision, map, a.map_img, scratch, cap, st, &pw) != cudaSuccess)
+            return SAM_ERR_CUDA;
+    }
+    return SAM_OK;
 }
 
 sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps) {

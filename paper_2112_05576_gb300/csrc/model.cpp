@@ -114,6 +114,53 @@ void rotate_level(LevelHost &L, int k, RotPt *dst, int4 &box) {
 
 }  // namespace
 
+// Chunked tables of one level (see LevelHost): for every angle, the rotated
+// points sorted by the kChunkCell-sized cell of their offset (floor
+// division), one chunk per non-empty cell.
+static void build_chunks(LevelHost &L) {
+    const size_t n = (size_t)L.n;
+    L.crot.resize((size_t)L.ntheta * n);
+    L.cstart.assign((size_t)L.ntheta + 1, 0);
+    L.cbox.clear();
+    L.crange.clear();
+    L.cspan_x = L.cspan_y = 0;
+    std::vector<std::pair<long long, int>> key(n);
+    for (int k = 0; k < L.ntheta; ++k) {
+        const RotPt *src = L.rot.data() + (size_t)k * n;
+        RotPt *dst = L.crot.data() + (size_t)k * n;
+        for (size_t i = 0; i < n; ++i) {
+            const long long cx = (long long)floor((double)src[i].ox / kChunkCell);
+            const long long cy = (long long)floor((double)src[i].oy / kChunkCell);
+            key[i] = std::make_pair(cy * (1LL << 32) + cx, (int)i);
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) {
+                             return a.first < b.first;
+                         });
+        L.cstart[k] = (int)L.cbox.size();
+        size_t i = 0;
+        while (i < n) {
+            size_t j = i;
+            int4 b = make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30));
+            while (j < n && key[j].first == key[i].first) {
+                const RotPt &q = src[key[j].second];
+                dst[j] = q;
+                b.x = std::min(b.x, q.ox);
+                b.y = std::max(b.y, q.ox);
+                b.z = std::min(b.z, q.oy);
+                b.w = std::max(b.w, q.oy);
+                ++j;
+            }
+            L.cbox.push_back(b);
+            L.crange.push_back(make_int2((int)i, (int)j));
+            L.cspan_x = std::max(L.cspan_x, b.y - b.x);
+            L.cspan_y = std::max(L.cspan_y, b.w - b.z);
+            i = j;
+        }
+    }
+    L.cstart[L.ntheta] = (int)L.cbox.size();
+}
+
 sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m) {
     if (!tmpl || w < 3 || h < 3 || stride < w || p.levels < 1 || p.levels > kMaxLevels || p.low < 1 ||
         p.high < p.low || !(p.angle_step_deg > 0.0) || (p.polarity != 0 && p.polarity != 1))
@@ -167,6 +214,9 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
             for (int k = 0; k < L.ntheta; ++k)
                 rotate_level(L, k, L.rot.data() + (size_t)k * L.n, L.bbox[k]);
         }
+        for (int l = 0; l < p.levels; ++l)
+            if (level_needs_chunks(m->lv[l]))
+                build_chunks(m->lv[l]);
         // Coarse-to-fine shifts: a parent pose u' at level l (angle index k')
         // maps to the level-(l-1) pose 2u' + (1/2, 1/2) - R(theta) d with
         // d = 2 c_l + 1/2 - c_{l-1} per axis (c = reference point); the
@@ -204,7 +254,9 @@ sam_status upload_model(sam_model *m) {
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     for (const LevelHost &L : m->lv)
         bytes += align(L.rot.size() * sizeof(RotPt)) + align(L.bbox.size() * sizeof(int4)) +
-                 align(std::max<size_t>(1, L.shift.size()) * sizeof(int2)) + align((size_t)L.n * sizeof(float4));
+                 align(std::max<size_t>(1, L.shift.size()) * sizeof(int2)) + align((size_t)L.n * sizeof(float4)) +
+                 align(L.crot.size() * sizeof(RotPt)) + align(L.cstart.size() * sizeof(int)) +
+                 align(L.cbox.size() * sizeof(int4)) + align(L.crange.size() * sizeof(int2));
     void *base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess)
         return SAM_ERR_NOMEM;
@@ -239,6 +291,30 @@ sam_status upload_model(sam_model *m) {
             if (cudaMemcpy(p, base.data(), base.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
                 goto fail;
             p += align((size_t)L.n * sizeof(float4));
+        }
+        D.crot = nullptr;
+        D.cstart = nullptr;
+        D.cbox = nullptr;
+        D.crange = nullptr;
+        D.cspan_x = L.cspan_x;
+        D.cspan_y = L.cspan_y;
+        if (!L.crot.empty()) {
+            D.crot = (const RotPt *)p;
+            if (cudaMemcpy(p, L.crot.data(), L.crot.size() * sizeof(RotPt), cudaMemcpyHostToDevice) != cudaSuccess)
+                goto fail;
+            p += align(L.crot.size() * sizeof(RotPt));
+            D.cstart = (const int *)p;
+            if (cudaMemcpy(p, L.cstart.data(), L.cstart.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+                goto fail;
+            p += align(L.cstart.size() * sizeof(int));
+            D.cbox = (const int4 *)p;
+            if (cudaMemcpy(p, L.cbox.data(), L.cbox.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+                goto fail;
+            p += align(L.cbox.size() * sizeof(int4));
+            D.crange = (const int2 *)p;
+            if (cudaMemcpy(p, L.crange.data(), L.crange.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+                goto fail;
+            p += align(L.crange.size() * sizeof(int2));
         }
     }
     m->d_tables = base;

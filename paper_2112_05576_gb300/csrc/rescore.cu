@@ -35,6 +35,8 @@ __global__ void rescore_select_kernel(float *__restrict__ map, size_t map_img, s
             if (pos < cap) {
                 list[2 * (size_t)pos] = (unsigned)img;
                 list[2 * (size_t)pos + 1] = (unsigned)i;
+            } else {
+                m[i] = __int_as_float(0x7fc00000);   // list full: flag the pose NaN
             }
         } else {
             m[i] = -INFINITY;
@@ -44,8 +46,8 @@ __global__ void rescore_select_kernel(float *__restrict__ map, size_t map_img, s
 
 template <int NB>
 __global__ void __launch_bounds__(256) rescore_kernel(const float2 *__restrict__ field, size_t field_img_px, int w,
-                                                      int h, int gw, int gh, int step_x, int step_y,
-                                                      const RotPt *__restrict__ rot, int n, int polarity,
+                                                      int h, int gw, int gh, int step_x, int step_y, int x0, int y0,
+                                                      int k0, const RotPt *__restrict__ rot, int n, int polarity,
                                                       float *__restrict__ map, size_t map_img,
                                                       const unsigned *__restrict__ list,
                                                       const unsigned *__restrict__ count, unsigned cap) {
@@ -56,10 +58,11 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float2 *__restrict__
     for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
         const unsigned img = list[2 * (size_t)e], idx = list[2 * (size_t)e + 1];
         const unsigned plane = (unsigned)gw * (unsigned)gh;
-        const int k = (int)(idx / plane);
-        const int rem = (int)(idx - (unsigned)k * plane);
+        const int kl = (int)(idx / plane);
+        const int rem = (int)(idx - (unsigned)kl * plane);
         const int gyi = rem / gw;
-        const int ux = (rem - gyi * gw) * step_x, uy = gyi * step_y;
+        const int ux = x0 + (rem - gyi * gw) * step_x, uy = y0 + gyi * step_y;
+        const int k = k0 + kl;
         const float2 *F = field + (size_t)img * field_img_px;
         const RotPt *P = rot + (size_t)k * n;
         float sum = 0.f, comp = 0.f;
@@ -104,25 +107,28 @@ size_t rescore_scratch_bytes(size_t poses) { return 256 + poses * 8; }
 
 cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h, int step_x,
                            int step_y, int count, int nbhd, int polarity, float min_score, int precision, float *map,
-                           size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st) {
+                           size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st,
+                           const PoseWindow *window) {
     unsigned *cnt = reinterpret_cast<unsigned *>(scratch);
     unsigned *list = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(scratch) + 256);
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned), st);
     if (e != cudaSuccess)
         return e;
-    const int gw = (w + step_x - 1) / step_x, gh = (h + step_y - 1) / step_y;
-    const size_t per_img = (size_t)L.ntheta * gw * gh;
+    const PoseWindow pw =
+        window ? *window : PoseWindow{0, 0, (w + step_x - 1) / step_x, (h + step_y - 1) / step_y, 0, L.ntheta};
+    const int gw = pw.gw, gh = pw.gh;
+    const size_t per_img = (size_t)pw.nk * gw * gh;
     const float thr = min_score - rescore_delta(precision);
     const unsigned cap = (unsigned)std::min<size_t>(poses_cap, 0xFFFFFFFFu);
     dim3 g1((unsigned)std::min<size_t>((per_img + 255) / 256, 1024), (unsigned)count);
     rescore_select_kernel<<<g1, 256, 0, st>>>(map, map_img, per_img, thr, list, cnt, cap);
     const unsigned blocks = 152 * 8;
     if (nbhd == 3)
-        rescore_kernel<3><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, gw, gh, step_x, step_y, L.rot, L.n,
-                                                  polarity, map, map_img, list, cnt, cap);
+        rescore_kernel<3><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, gw, gh, step_x, step_y, pw.x0, pw.y0,
+                                                  pw.k0, L.rot, L.n, polarity, map, map_img, list, cnt, cap);
     else
-        rescore_kernel<1><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, gw, gh, step_x, step_y, L.rot, L.n,
-                                                  polarity, map, map_img, list, cnt, cap);
+        rescore_kernel<1><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, gw, gh, step_x, step_y, pw.x0, pw.y0,
+                                                  pw.k0, L.rot, L.n, polarity, map, map_img, list, cnt, cap);
     count_launches(2);
     return cudaGetLastError();
 }

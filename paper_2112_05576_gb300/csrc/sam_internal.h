@@ -30,7 +30,20 @@ struct LevelHost {
     std::vector<RotPt> rot;          // [ntheta][n]
     std::vector<int4> bbox;          // [ntheta] (oxmin, oxmax, oymin, oymax)
     std::vector<int2> shift;         // [ntheta] child shift to level-1 (empty at level 0)
+    // Chunked tables, built for levels whose rotated extent is too large for
+    // one staged window: per angle the rotated points regrouped by
+    // kChunkCell x kChunkCell cell of their offset (crot [ntheta][n], cells
+    // in (cy, cx) order); chunk c of angle k is points crange[c] of that
+    // angle's list with offset box cbox[c]; angle k owns chunks
+    // cstart[k] .. cstart[k+1] - 1.
+    std::vector<RotPt> crot;
+    std::vector<int> cstart;
+    std::vector<int4> cbox;
+    std::vector<int2> crange;
+    int cspan_x = 0, cspan_y = 0;    // largest chunk box extent (max - min)
 };
+
+constexpr int kChunkCell = 16;
 
 // Device copy of one level's tables.
 struct LevelDev {
@@ -39,6 +52,12 @@ struct LevelDev {
     const int4 *bbox;
     const int2 *shift;
     const float4 *base;   // [n] unrotated (tx, ty, gx/|g|, gy/|g|) for the continuous-pose score
+    // chunked tables (null when the level has none)
+    const RotPt *crot;
+    const int *cstart;
+    const int4 *cbox;
+    const int2 *crange;
+    int cspan_x, cspan_y;
 };
 
 struct Workspace {
@@ -128,9 +147,28 @@ struct TileConfig {
     int warps = 8;        // warps per CTA (4 or 8)
 };
 bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *bxw, int *byw);
+// Whether a level's rotated extent needs the chunked scorer (its whole-angle
+// window does not fit shared memory at the smallest tiling).
+bool level_needs_chunks(const LevelHost &L);
+// Chunked scorer window box for a CTA tile of sx x sy warp tiles.
+bool chunked_plan(const LevelHost &L, int precision, int sx, int sy, int *bxw, int *byw);
+
+// A window of the pose space: translations x0 .. x0 + gw - 1, y0 .. y0 + gh - 1
+// (step 1) and angles k0 .. k0 + nk - 1; its map is [nk][gh][gw].
+struct PoseWindow {
+    int x0, y0, gw, gh, k0, nk;
+};
+
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
-                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st);
+                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
+                               const PoseWindow *window = nullptr);
+
+// Chunked tiled scorer for levels with chunk tables (score_tiled.cu).
+cudaError_t launch_score_chunked(const sam_model *m, int level, const void *field, int precision, int wp,
+                                 size_t field_img_px, int W, int H, int count, int nbhd, int polarity,
+                                 float min_score, int early, float *map, size_t map_img, const TileConfig &cfg,
+                                 cudaStream_t st, const PoseWindow *window = nullptr);
 
 // Persistent tiled scorer over many (image, model) pairs (score_tiled.cu).
 struct PairScore {
@@ -171,7 +209,8 @@ float rescore_delta(int precision);
 size_t rescore_scratch_bytes(size_t poses);
 cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h, int step_x,
                            int step_y, int count, int nbhd, int polarity, float min_score, int precision, float *map,
-                           size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st);
+                           size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st,
+                           const PoseWindow *window = nullptr);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {

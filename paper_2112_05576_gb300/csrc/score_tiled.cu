@@ -101,7 +101,9 @@ struct TiledArgs {
     const RotPt *rot;     // [nth][n]
     const int4 *bbox;     // [nth]
     int n, nth;
-    int W, H;             // level size (poses = pixels, step 1)
+    int W, H;             // map size in poses (step 1): the pose window
+    int ox, oy;           // pose of map element (0, 0)
+    int k0, nk;           // angles k0 .. k0 + nk - 1 (map plane k - k0)
     float *map;
     size_t map_img;
     int sx, sy, tg;       // super-tile in warp tiles, angles per group
@@ -242,7 +244,8 @@ __device__ __forceinline__ void point_nb1(const typename Pairs<E>::Raw *win, int
 struct TileWork {
     const RotPt *rot;
     int n, W, H;
-    float *map;   // the image's (or pair's) map [nth][H][W]
+    int ox, oy, k0;   // pose and angle of map element (0, 0, 0)
+    float *map;   // the image's (or pair's) map [nk][H][W]
     float inv_n, thresh;
     int early, sx, sy;
 };
@@ -268,10 +271,10 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     const int img = blockIdx.z;
     const int group = blockIdx.y;
     const int st = blockIdx.x;
-    const int stx0 = (st % a.tiles_x) * a.sx * WTX;
-    const int sty0 = (st / a.tiles_x) * a.sy * WTY;
-    const int k_begin = group * a.tg;
-    const int k_end = min(k_begin + a.tg, a.nth);
+    const int stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
+    const int sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
+    const int k_begin = a.k0 + group * a.tg;
+    const int k_end = min(k_begin + a.tg, a.k0 + a.nk);
     const int pp = a.bxw / 2;   // window row pitch in pixel pairs
     const uint32_t bar = smem_addr(&mbar);
 
@@ -310,6 +313,9 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     t.n = a.n;
     t.W = a.W;
     t.H = a.H;
+    t.ox = a.ox;
+    t.oy = a.oy;
+    t.k0 = a.k0;
     t.map = a.map + (size_t)img * a.map_img;
     t.inv_n = a.inv_n;
     t.thresh = a.thresh;
@@ -383,17 +389,17 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 }
             }
         }
-        // epilogue: M = sum / n, or -inf where pruned; clip to the level
-        float *mk = map + (size_t)k * a.H * a.W;
+        // epilogue: M = sum / n, or -inf where pruned; clip to the window
+        float *mk = map + (size_t)(k - a.k0) * a.H * a.W;
 #pragma unroll
         for (int r = 0; r < TR; ++r) {
-            const int y = y0 + r;
+            const int y = y0 + r - a.oy;
             if (y >= a.H)
                 break;
             float *row = mk + (size_t)y * a.W;
 #pragma unroll
             for (int j = 0; j < TC / 2; ++j) {
-                const int x = x0 + 2 * j;
+                const int x = x0 + 2 * j - a.ox;
                 const float v0 = pruned ? -INFINITY : acc[r][j].x * a.inv_n;
                 const float v1 = pruned ? -INFINITY : acc[r][j].y * a.inv_n;
                 if (x + 1 < a.W && (a.W & 1) == 0) {
@@ -498,6 +504,9 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         t.n = P.n;
         t.W = P.W;
         t.H = P.H;
+        t.ox = 0;
+        t.oy = 0;
+        t.k0 = 0;
         t.map = P.map;
         t.inv_n = P.inv_n;
         t.thresh = P.thresh;
@@ -507,6 +516,170 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         score_items<E, NB, POL, WARPS>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
                                        min(group * tg + tg, P.nth), t);
         __syncthreads();   // every warp is done with the window before the next copy
+    }
+}
+
+
+// Chunked form for templates whose rotated extent is too large for one staged
+// window (a 512-pixel template at full resolution spans ~724 pixels).  One
+// angle per CTA and one warp tile per warp; the CTA walks the angle's point
+// chunks (points grouped by 16 x 16 cell of their offset), staging for each
+// chunk by TMA only the window its points reach from the CTA tile: CTA tile
+// + chunk box + 3x3 halo.  Accumulators stay in registers across chunks;
+// early termination is checked after every chunk, and the CTA stops when
+// every warp has pruned.  The window buffer is reused chunk after chunk
+// (mbarrier phase alternates; a proxy fence orders the previous chunk's reads
+// before the next copy).
+struct ChunkArgs {
+    const RotPt *rot;      // chunk-ordered points [nth][n]
+    const int *cstart;     // [nth + 1]
+    const int4 *cbox;      // per chunk (oxmin, oxmax, oymin, oymax)
+    const int2 *crange;    // per chunk [p0, p1) within the angle's points
+    int n;
+    int W, H, ox, oy, k0;  // map window (as TiledArgs)
+    float *map;
+    size_t map_img;
+    int sx, sy;            // CTA tile in warp tiles, sx * sy == warps
+    int tiles_x;
+    int bxw, byw;
+    float inv_n, thresh;
+    int early;
+};
+
+template <typename E, int NB, bool POL, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                    const ChunkArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_org[2];
+
+    const int img = blockIdx.z;
+    const int kl = blockIdx.y;
+    const int k = a.k0 + kl;
+    const int st = blockIdx.x;
+    const int stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
+    const int sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = lane % LX, ly = lane / LX;
+    const int x0 = stx0 + (warp % a.sx) * WTX + lx * TC;   // thread's first pose
+    const int y0 = sty0 + (warp / a.sx) * WTY + ly * TR;
+    const int pp = a.bxw / 2;
+    const uint32_t bar = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    float2 acc[TR][TC / 2];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j)
+            acc[r][j] = make_float2(0.f, 0.f);
+    const RotPt *P = a.rot + (size_t)k * a.n;
+    const int c_begin = a.cstart[k], c_end = a.cstart[k + 1];
+    bool alive = true;
+    int done = 0;
+    uint32_t parity = 0;
+    for (int c = c_begin; c < c_end; ++c) {
+        const int4 b = a.cbox[c];
+        const int2 rg = a.crange[c];
+        if (threadIdx.x == 0) {
+            const int wx0 = (stx0 + b.x - 1) & ~(Pairs<E>::XALIGN - 1);
+            const int wy0 = sty0 + b.z - 1;
+            s_org[0] = wx0;
+            s_org[1] = wy0;
+            const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+            const int xe = wx0 * Pairs<E>::BYTES / 16;
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(smem_addr(win)),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(img), "r"(bar)
+                : "memory");
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(&g_score_err, 1);
+                mbar_wait(bar, parity ^ 1u);   // let a late copy land before the CTA exits
+            }
+            return;
+        }
+        if (alive) {
+            const int bx = x0 - 1 - s_org[0];
+            const int by = y0 - 1 - s_org[1];
+            RotPt q = P[rg.x];
+            for (int i = rg.x; i < rg.y; ++i) {
+                const RotPt cur = q;
+                if (i + 1 < rg.y)
+                    q = P[i + 1];
+                const float2 pxx = make_float2(cur.px, cur.px);
+                const float2 pyy = make_float2(cur.py, cur.py);
+                if (NB == 3) {
+                    const int xs = bx + cur.ox;
+                    const int row0 = by + cur.oy;
+                    if (xs & 1)
+                        point_nb3<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    else
+                        point_nb3<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                } else {
+                    const int xs = bx + 1 + cur.ox;
+                    const int row0 = by + 1 + cur.oy;
+                    if (xs & 1)
+                        point_nb1<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    else
+                        point_nb1<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                }
+            }
+            done += rg.y - rg.x;
+            if (a.early) {
+                const float lim = a.thresh - (float)(a.n - done);
+                bool low = true;
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TC / 2; ++j)
+                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                if (__all_sync(0xffffffffu, low))
+                    alive = false;
+            }
+        }
+        // every warp is done with the window before the next copy; stop when
+        // all warps have pruned
+        if (!__syncthreads_or(alive))
+            break;
+    }
+    float *mk = a.map + (size_t)img * a.map_img + (size_t)kl * a.H * a.W;
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int y = y0 + r - a.oy;
+        if (y >= a.H)
+            break;
+        float *row = mk + (size_t)y * a.W;
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j) {
+            const int x = x0 + 2 * j - a.ox;
+            const float v0 = alive ? acc[r][j].x * a.inv_n : -INFINITY;
+            const float v1 = alive ? acc[r][j].y * a.inv_n : -INFINITY;
+            if (x + 1 < a.W && (a.W & 1) == 0) {
+                *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
+            } else {
+                if (x < a.W)
+                    row[x] = v0;
+                if (x + 1 < a.W)
+                    row[x + 1] = v1;
+            }
+        }
     }
 }
 
@@ -603,8 +776,10 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *
 // (row pitch wp pixels, a multiple of 4; image stride field_img_px pixels).
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
-                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st) {
+                               int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
+                               const PoseWindow *window) {
     const LevelHost &L = m->lv[level];
+    const PoseWindow pw = window ? *window : PoseWindow{0, 0, W, H, 0, L.ntheta};
     int bxw = 0, byw = 0;
     if (!tiled_plan(L, precision, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw))
         return cudaErrorInvalidValue;
@@ -628,21 +803,25 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.bbox = m->dev[level].bbox;
     a.n = L.n;
     a.nth = L.ntheta;
-    a.W = W;
-    a.H = H;
+    a.W = pw.gw;
+    a.H = pw.gh;
+    a.ox = pw.x0;
+    a.oy = pw.y0;
+    a.k0 = pw.k0;
+    a.nk = pw.nk;
     a.map = map;
     a.map_img = map_img;
     a.sx = cfg.sx;
     a.sy = cfg.sy;
     a.tg = cfg.tg;
-    a.tiles_x = (W + cfg.sx * g.wtx - 1) / (cfg.sx * g.wtx);
-    const int tiles_y = (H + cfg.sy * g.wty - 1) / (cfg.sy * g.wty);
+    a.tiles_x = (pw.gw + cfg.sx * g.wtx - 1) / (cfg.sx * g.wtx);
+    const int tiles_y = (pw.gh + cfg.sy * g.wty - 1) / (cfg.sy * g.wty);
     a.bxw = bxw;
     a.byw = byw;
     a.inv_n = 1.0f / (float)L.n;
     a.thresh = prune_threshold(L.n, min_score, precision);
     a.early = early;
-    const int groups = (L.ntheta + cfg.tg - 1) / cfg.tg;
+    const int groups = (pw.nk + cfg.tg - 1) / cfg.tg;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)groups, (unsigned)count);
     const size_t smem = (size_t)bxw * byw * g.pair_bytes / 2 + 128;
     const bool pol = polarity != 0;
@@ -653,6 +832,117 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
         return launch_e<__half>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
     default:
         return launch_e<__nv_bfloat16>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    }
+}
+
+namespace {
+template <typename E, int NB, bool POL, int WARPS>
+cudaError_t launch_c(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
+    auto kern = score_chunked_kernel<E, NB, POL, WARPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t launch_ce(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                      int warps, cudaStream_t st) {
+    if (warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_c<E, 3, true, 4>(tm, a, grid, smem, st) : launch_c<E, 3, false, 4>(tm, a, grid, smem, st);
+        return pol ? launch_c<E, 1, true, 4>(tm, a, grid, smem, st) : launch_c<E, 1, false, 4>(tm, a, grid, smem, st);
+    }
+    if (nbhd == 3)
+        return pol ? launch_c<E, 3, true, 8>(tm, a, grid, smem, st) : launch_c<E, 3, false, 8>(tm, a, grid, smem, st);
+    return pol ? launch_c<E, 1, true, 8>(tm, a, grid, smem, st) : launch_c<E, 1, false, 8>(tm, a, grid, smem, st);
+}
+}  // namespace
+
+bool level_needs_chunks(const LevelHost &L) {
+    int bxw = 0, byw = 0;
+    return !tiled_plan(L, SAM_FP32, 1, 1, 1, &bxw, &byw);
+}
+
+// Window box of the chunked kernel: CTA tile + largest chunk box + halo +
+// aligned-start slack + one pixel for odd-start pair loads.
+bool chunked_plan(const LevelHost &L, int precision, int sx, int sy, int *bxw, int *byw) {
+    if (L.crot.empty())
+        return false;
+    const Geometry g = geometry(precision);
+    int bx = sx * g.wtx + L.cspan_x + 2 + (g.xalign - 1) + 1;
+    bx = (bx + g.xalign - 1) / g.xalign * g.xalign;
+    const int by = sy * g.wty + L.cspan_y + 2;
+    *bxw = bx;
+    *byw = by;
+    const size_t bytes = (size_t)bx * by * g.pair_bytes / 2;
+    return bx * g.pair_bytes / 16 <= 256 && by <= 256 && bytes <= 200 * 1024;
+}
+
+// The chunked scorer over `count` images (arguments as launch_score_tiled);
+// the CTA tile is cfg.sx x cfg.sy warp tiles with cfg.sx * cfg.sy == cfg.warps.
+cudaError_t launch_score_chunked(const sam_model *m, int level, const void *field, int precision, int wp,
+                                 size_t field_img_px, int W, int H, int count, int nbhd, int polarity,
+                                 float min_score, int early, float *map, size_t map_img, const TileConfig &cfg,
+                                 cudaStream_t st, const PoseWindow *window) {
+    const LevelHost &L = m->lv[level];
+    const LevelDev &D = m->dev[level];
+    if (cfg.sx * cfg.sy != cfg.warps || (cfg.warps != 4 && cfg.warps != 8) || !D.crot)
+        return cudaErrorInvalidValue;
+    int bxw = 0, byw = 0;
+    if (!chunked_plan(L, precision, cfg.sx, cfg.sy, &bxw, &byw))
+        return cudaErrorInvalidValue;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return cudaErrorNotSupported;
+    const PoseWindow pw = window ? *window : PoseWindow{0, 0, W, H, 0, L.ntheta};
+    const Geometry g = geometry(precision);
+    CUtensorMap tm;
+    const cuuint64_t dims[3] = {(cuuint64_t)wp * g.pair_bytes / 16, (cuuint64_t)H, (cuuint64_t)count};
+    const cuuint64_t strides[2] = {(cuuint64_t)wp * g.pair_bytes / 2, (cuuint64_t)field_img_px * g.pair_bytes / 2};
+    const cuuint32_t box[3] = {(cuuint32_t)(bxw * g.pair_bytes / 16), (cuuint32_t)byw, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(field), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    ChunkArgs a;
+    a.rot = D.crot;
+    a.cstart = D.cstart;
+    a.cbox = D.cbox;
+    a.crange = D.crange;
+    a.n = L.n;
+    a.W = pw.gw;
+    a.H = pw.gh;
+    a.ox = pw.x0;
+    a.oy = pw.y0;
+    a.k0 = pw.k0;
+    a.map = map;
+    a.map_img = map_img;
+    a.sx = cfg.sx;
+    a.sy = cfg.sy;
+    a.tiles_x = (pw.gw + cfg.sx * g.wtx - 1) / (cfg.sx * g.wtx);
+    const int tiles_y = (pw.gh + cfg.sy * g.wty - 1) / (cfg.sy * g.wty);
+    a.bxw = bxw;
+    a.byw = byw;
+    a.inv_n = 1.0f / (float)L.n;
+    a.thresh = prune_threshold(L.n, min_score, precision);
+    a.early = early;
+    dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)pw.nk, (unsigned)count);
+    const size_t smem = (size_t)bxw * byw * g.pair_bytes / 2 + 128;
+    const bool pol = polarity != 0;
+    switch (precision) {
+    case SAM_FP32:
+        return launch_ce<float>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    case SAM_FP16:
+        return launch_ce<__half>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    default:
+        return launch_ce<__nv_bfloat16>(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
     }
 }
 

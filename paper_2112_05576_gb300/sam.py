@@ -73,6 +73,9 @@ SIGNATURES = {
     "sam_gradient": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp]),
     "sam_score_map": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_float,
                                _c_int, _vp, _vp]),
+    "sam_score_window_scratch_bytes": (ctypes.c_size_t, [ctypes.c_size_t]),
+    "sam_score_window": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int,
+                                  _c_int, _c_int, _c_float, _c_int, _vp, _vp, ctypes.c_size_t, _vp, _vp]),
     "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
     "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_take_device_error": (_c_int, []),
@@ -298,6 +301,21 @@ def score_map(model: Model, level, field, w, h, precision, out, step_x=1, step_y
     _check(lib().sam_score_map(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(layout),
                                int(step_x), int(step_y), int(nbhd), float(min_score), int(early), _ptr(out),
                                _stream(stream)), "sam_score_map")
+
+
+def score_window_scratch_bytes(max_rescored):
+    return int(lib().sam_score_window_scratch_bytes(int(max_rescored)))
+
+
+def score_window(model: Model, level, field, w, h, precision, x0, y0, gw, gh, k0, nk, out, nbhd=3, min_score=0.0,
+                 early=0, field32=None, scratch=None, stream=None):
+    """Scores of the pose window [x0, x0+gw) x [y0, y0+gh) x angles [k0, k0+nk)
+    into out (nk, gh, gw); field is the level's pairs-layout field."""
+    nbytes = scratch.numel() * scratch.element_size() if scratch is not None else 0
+    _check(lib().sam_score_window(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(x0),
+                                  int(y0), int(gw), int(gh), int(k0), int(nk), int(nbhd), float(min_score), int(early),
+                                  _ptr(field32), _ptr(scratch), nbytes, _ptr(out), _stream(stream)),
+           "sam_score_window")
 
 
 def set_score_kernel(kernel=0, sx=2, sy=1, tg=9, warps=8):
