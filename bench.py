@@ -359,6 +359,61 @@ def run_differentiable(args, sam, torch, dev, stream, with_oracle):
 
 
 # ---------------------------------------------------------------------------
+# large exhaustive stress slice (config 5 shape)
+# ---------------------------------------------------------------------------
+
+def run_stress(args, sam, torch, dev, stream):
+    tmpl, img, poses = synth.config5_scene()
+    H5, W5 = img.shape
+    step5 = 0.5
+    model = sam.Model(tmpl, LOW, HIGH, 1, step5)
+    n = model.num_points(0)
+    nth = model.num_angles(0)
+    dimg = torch.from_numpy(img).to(dev)
+    fields = {}
+    for prec, dt in ((0, torch.float32), (1, torch.bfloat16)):
+        wp = sam.field_pitch(W5, sam.LAYOUT_PAIRS)
+        f = torch.empty((H5, wp, 2), dtype=dt, device=dev)
+        sam.gradient(dimg, LOW, prec, f, layout=sam.LAYOUT_PAIRS)
+        fields[prec] = f
+    field32 = torch.empty((H5, W5, 2), dtype=torch.float32, device=dev)
+    sam.gradient(dimg, LOW, 0, field32, layout=sam.LAYOUT_PIXEL)
+    x, y, th = poses[0]
+    k = int(round(th / step5)) % nth
+    slices = {"angles8_full_image": (0, 0, W5, H5, min(max(0, k - 4), nth - 8), 8),
+              "all_angles_512x512": (int(x) - 256, int(y) - 256, 512, 512, 0, nth)}
+    scratch = torch.empty(sam.score_window_scratch_bytes(1 << 22), dtype=torch.uint8, device=dev)
+    out = {"workload": f"config5: {W5}x{H5} image, 512x512 part ({n} points), dtheta {step5} deg ({nth} angles), "
+                       f"level 0 only, step 1 px, nbhd 3, min_score 0.6",
+           "points": n, "full_search_pose_points": nth * W5 * H5 * n}
+    peaks, _ = _peaks()
+    smem_peak = SMEM_B_PER_CLK_SM * torch.cuda.get_device_properties(dev).multi_processor_count * \
+        float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    reps = 3
+    for name, win in slices.items():
+        x0, y0, gw, gh, k0, nk = win
+        omap = torch.empty((nk, gh, gw), dtype=torch.float32, device=dev)
+        pp = nk * gw * gh * n
+        res = {"window": list(win), "pose_points": pp}
+        for label, prec, early, f32 in (("fp32", 0, 1, None), ("fp32_no_early_termination", 0, 0, None),
+                                        ("bf16_rescored", 1, 1, field32)):
+            def call(i, prec=prec, early=early, f32=f32):
+                sam.score_window(model, 0, fields[prec], W5, H5, prec, x0, y0, gw, gh, k0, nk, omap, nbhd=3,
+                                 min_score=0.6, early=early, field32=f32, scratch=scratch if f32 is not None else None)
+            call(0)
+            ms = _event_ms(torch, dev, stream, call, reps)
+            res[label] = {"ms": round(ms, 3), "value": pp / (ms * 1e-3), "unit": UNIT,
+                          "smem_frac": round(pp * SMEM_B_PER_PP / (ms * 1e-3) / 1e12 / smem_peak, 4),
+                          "best": round(float(omap.max()), 5)}
+        out[name] = res
+    rate = out["angles8_full_image"]["fp32"]["value"]
+    out["extrapolated_full_search_s"] = {
+        "fp32": round(out["full_search_pose_points"] / rate, 1),
+        "bf16_rescored": round(out["full_search_pose_points"] / out["angles8_full_image"]["bf16_rescored"]["value"], 1)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -508,6 +563,9 @@ def run_gpu(args):
     # ---- the batched uneven form: many image sizes and templates, one graph ----
     batched = run_batched(args, sam, torch, dev, stream) if (args.multi > 0 and rank == 0) else None
 
+    # ---- the large exhaustive stress slice (chunked scorer) ----
+    stress = run_stress(args, sam, torch, dev, stream) if (args.stress and rank == 0) else None
+
     # ---- the differentiable form: continuous-pose score, adjoint, refinement ----
     differentiable = (run_differentiable(args, sam, torch, dev, stream, world == 1 and not args.no_cpu)
                       if (args.refine > 0 and rank == 0) else None)
@@ -588,6 +646,7 @@ def run_gpu(args):
         "forms": forms,
         "batched": batched,
         "differentiable": differentiable,
+        "stress": stress,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -611,6 +670,7 @@ def main():
     ap.add_argument("--forms", type=int, default=1, help="also time the FP16/BF16 stored forms")
     ap.add_argument("--multi", type=int, default=64, help="images of the batched uneven form (0: skip)")
     ap.add_argument("--refine", type=int, default=4096, help="poses of the differentiable form (0: skip)")
+    ap.add_argument("--stress", type=int, default=1, help="time the config-5 stress slices (0: skip)")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")

@@ -527,7 +527,10 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
 // chunk by TMA only the window its points reach from the CTA tile: CTA tile
 // + chunk box + 3x3 halo.  Accumulators stay in registers across chunks;
 // early termination is checked after every chunk, and the CTA stops when
-// every warp has pruned.  The window buffer is reused chunk after chunk
+// every warp has pruned.  Each chunk (at most 256 points) is summed into a
+// fresh FP32 partial that is then added to the running sum, so the running
+// sum takes one rounding per chunk rather than one per point: with ~6000
+// points per pose a plain serial FP32 sum drifts by ~1e-5 of the mean.  The window buffer is reused chunk after chunk
 // (mbarrier phase alternates; a proxy fence orders the previous chunk's reads
 // before the next copy).
 struct ChunkArgs {
@@ -618,6 +621,12 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
         if (alive) {
             const int bx = x0 - 1 - s_org[0];
             const int by = y0 - 1 - s_org[1];
+            float2 part[TR][TC / 2];
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j)
+                    part[r][j] = make_float2(0.f, 0.f);
             RotPt q = P[rg.x];
             for (int i = rg.x; i < rg.y; ++i) {
                 const RotPt cur = q;
@@ -629,18 +638,23 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
                     const int xs = bx + cur.ox;
                     const int row0 = by + cur.oy;
                     if (xs & 1)
-                        point_nb3<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                        point_nb3<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, part);
                     else
-                        point_nb3<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                        point_nb3<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, part);
                 } else {
                     const int xs = bx + 1 + cur.ox;
                     const int row0 = by + 1 + cur.oy;
                     if (xs & 1)
-                        point_nb1<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                        point_nb1<E, POL, true>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, part);
                     else
-                        point_nb1<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                        point_nb1<E, POL, false>(win, pp, row0, xs >> 1, pxx, pyy, part);
                 }
             }
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j)
+                    acc[r][j] = __fadd2_rn(acc[r][j], part[r][j]);
             done += rg.y - rg.x;
             if (a.early) {
                 const float lim = a.thresh - (float)(a.n - done);
