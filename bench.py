@@ -421,6 +421,7 @@ def run_gpu(args):
     import torch
 
     import paper_2112_05576_gb300 as sam
+    from paper_2112_05576_gb300 import shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -484,13 +485,9 @@ def run_gpu(args):
     launches = sam.kernel_launches() - launches0
     prof = sam.profile_read()
     sam.profile_enable(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
     pp_step = top_pose_points(model, B)
-    value = pp_step * args.steps * world / (ms * 1e-3)
+    value = shard.whole_job_rate(pp_step, args.steps, world, ms)
 
     # ---- end to end through the public API with host buffers ----
     h2d = B * H * W
@@ -506,12 +503,8 @@ def run_gpu(args):
         sam.detect_batch(model, x, params)     # ends with the device-to-host read of the poses
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = pp_step * args.steps * world / (e2e_ms * 1e-3)
+    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
+    e2e_value = shard.whole_job_rate(pp_step, args.steps, world, e2e_ms)
 
     # ---- single-image latency (one detection, device-resident) ----
     one = batches[0][0].contiguous()

@@ -210,3 +210,26 @@ def test_detect_with_chunked_top_level(big_case):
         assert abs(float(d["score"]) - ref) < TOL
     found = [any(abs(d["x"] - x) <= 2 and abs(d["y"] - y) <= 2 for d in dets) for x, y, _ in poses]
     assert any(found)
+
+
+def test_angle_blocks_with_library_steps_merge_to_full_search(big_case):
+    # the per-rank steps of an angle-sharded search (windowed scoring of a
+    # block with its halo angles, candidate kernels), run here block by
+    # block, merge to the candidates of the whole search
+    from paper_2112_05576_gb300 import shard
+    tmpl, img, poses, model, om = big_case
+    sub = np.ascontiguousarray(img[150:150 + 256, 300:300 + 384])
+    h, w = sub.shape
+    nth = model.num_angles(0)
+    f = _pairs_field(sub, 30, sam.FP32)
+    score_fn = shard.gpu_score_fn(model, 0, f, w, h, sam.FP32)
+    cand_fn = shard.gpu_candidates_fn()
+    K = 16
+    full = score_fn(0, nth)
+    ks, ys, xs, ss = cand_fn(full, 0.3, K)
+    want = [(int(k), int(y), int(x), float(s)) for k, y, x, s in zip(ks, ys, xs, ss)]
+    assert len(want) > 3
+    for world in (2, 5):
+        lists = [shard.block_candidates(*shard.angle_block(nth, world, r), nth, h, w, 0.3, K, score_fn, cand_fn)
+                 for r in range(world)]
+        assert shard.merge_candidates(lists, K, h, w) == want
