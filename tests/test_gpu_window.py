@@ -218,7 +218,8 @@ def test_angle_blocks_with_library_steps_merge_to_full_search(big_case):
     # block, merge to the candidates of the whole search
     from paper_2112_05576_gb300 import shard
     tmpl, img, poses, model, om = big_case
-    sub = np.ascontiguousarray(img[150:150 + 256, 300:300 + 384])
+    x, y, _ = poses[0]
+    sub = np.ascontiguousarray(img[int(y) - 200:int(y) + 200, int(x) - 200:int(x) + 200])
     h, w = sub.shape
     nth = model.num_angles(0)
     f = _pairs_field(sub, 30, sam.FP32)
@@ -226,10 +227,10 @@ def test_angle_blocks_with_library_steps_merge_to_full_search(big_case):
     cand_fn = shard.gpu_candidates_fn()
     K = 16
     full = score_fn(0, nth)
-    ks, ys, xs, ss = cand_fn(full, 0.3, K)
+    ks, ys, xs, ss = cand_fn(full, 0.05, K)
     want = [(int(k), int(y), int(x), float(s)) for k, y, x, s in zip(ks, ys, xs, ss)]
-    assert len(want) > 3
+    assert len(want) == K and abs(want[0][1] - 200) <= 1 and abs(want[0][2] - 200) <= 1
     for world in (2, 5):
-        lists = [shard.block_candidates(*shard.angle_block(nth, world, r), nth, h, w, 0.3, K, score_fn, cand_fn)
+        lists = [shard.block_candidates(*shard.angle_block(nth, world, r), nth, h, w, 0.05, K, score_fn, cand_fn)
                  for r in range(world)]
         assert shard.merge_candidates(lists, K, h, w) == want
