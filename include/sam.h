@@ -284,7 +284,9 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
 /* Score-kernel selection and tiling, process-wide (autotuner hook; the paper
  * has no counterpart).  kernel: 0 automatic, 1 generic one-thread-per-pose,
  * 2 tiled (falls back to generic when the tiled kernel cannot serve a call).
- * sx, sy: CTA super-tile in 48x32-pose warp tiles; tg: angles per CTA;
+ * sx, sy: CTA super-tile in 48x32-pose warp tiles; tg: angles per CTA, or 0
+ * for the chunked tiled kernel (one angle per CTA, points grouped by 16 x 16
+ * offset cell with one staged window per cell; requires sx * sy == warps);
  * warps: 4 or 8.  Returns SAM_ERR_ARG on out-of-range values. */
 sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps);
 /* Reads back the current selection (any pointer may be NULL). */
@@ -295,7 +297,9 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps);
  * sam_detect_batch, images on the device), then times the tiled kernel with
  * every tiling of its candidate set (super-tile 1..3 x 1..2 warp tiles,
  * angles per CTA 1, 3, 5, 9, 15 or all, 4 or 8 warps; tilings whose window
- * does not fit are skipped) using CUDA events on `stream`, and keeps the
+ * does not fit are skipped) and the chunked kernel with its CTA tiles
+ * (2x2, 4x1, 1x4 of 4 warps; 2x4, 4x2 of 8 warps; reported with tg = 0)
+ * using CUDA events on `stream`, and keeps the
  * fastest for this model and this field precision (used by later calls with
  * that precision while sam_set_score_kernel selects 0, automatic).  Optional
  * outputs: cfg_out[4 i ..] = (sx, sy, tg,

@@ -345,31 +345,43 @@ ScoreChoice &score_choice() {
 // Whether the tiled kernel can serve these arguments with this tiling.
 bool tiled_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg) {
     int bxw = 0, byw = 0;
-    return a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
+    return cfg.tg >= 1 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
            ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) &&
            tiled_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw);
 }
 
-cudaError_t launch_tiled_args(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg,
-                              cudaStream_t st) {
-    return launch_score_tiled(m, level, a.field, a.precision, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px, a.w,
-                              a.h, a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st);
-}
+// A tiling with tg == 0 selects the chunked scorer (one angle per CTA, CTA
+// tile of sx x sy warp tiles, one warp tile per warp).  Its default, 2 x 2
+// warp tiles of 4 warps, needs a ~75 KB FP32 window per 16-pixel chunk cell:
+// three CTAs per SM.
+constexpr TileConfig kChunkCfg = {2, 2, 0, 4};
 
-// The chunked scorer's CTA tile (2 x 2 warp tiles of 4 warps): a 16-pixel
-// chunk cell then needs a ~75 KB FP32 window, three CTAs per SM.
-constexpr TileConfig kChunkCfg = {2, 2, 1, 4};
-
-bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a) {
+bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg = kChunkCfg) {
     int bxw = 0, byw = 0;
-    return a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
+    return cfg.tg == 0 && cfg.sx * cfg.sy == cfg.warps && (cfg.warps == 4 || cfg.warps == 8) &&
+           a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
            ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) && a.count <= 65535 &&
            m->dev[level].crot && m->lv[level].ntheta <= 65535 &&
-           chunked_plan(m->lv[level], a.precision, kChunkCfg.sx, kChunkCfg.sy, &bxw, &byw);
+           chunked_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, &bxw, &byw);
 }
 
-cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
+// The tiled or chunked scorer for `cfg` over the map (or pose window) of `a`.
+cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg,
+                               cudaStream_t st, const PoseWindow *window = nullptr) {
+    const int wp = field_pitch(a.w, SAM_LAYOUT_PAIRS);
+    if (cfg.tg == 0)
+        return launch_score_chunked(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
+                                    a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
+    return launch_score_tiled(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
+                              a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
+}
+
+// The scorer a call uses: the model's tuned tiling (or the process-wide
+// selection), else the chunked default; false if neither serves the call.
+bool pick_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, TileConfig *out) {
     const ScoreChoice &c = score_choice();
+    if (c.kernel == 1)
+        return false;
     TileConfig cfg = c.cfg;
     const int pr = a.precision;
     if (m->tuned[pr] && c.kernel == 0) {
@@ -378,13 +390,22 @@ cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, 
         cfg.tg = m->tile_tg[pr];
         cfg.warps = m->tile_warps[pr];
     }
+    if ((cfg.tg >= 1 && tiled_ok(m, level, a, cfg)) || (cfg.tg == 0 && chunked_ok(m, level, a, cfg))) {
+        *out = cfg;
+        return true;
+    }
+    if (chunked_ok(m, level, a)) {
+        *out = kChunkCfg;
+        return true;
+    }
+    return false;
+}
+
+cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, int *err, cudaStream_t st) {
     (void)err;
-    if (c.kernel != 1 && tiled_ok(m, level, a, cfg))
-        return launch_tiled_args(m, level, a, cfg, st);
-    if (c.kernel != 1 && chunked_ok(m, level, a))
-        return launch_score_chunked(m, level, a.field, a.precision, field_pitch(a.w, SAM_LAYOUT_PAIRS), a.field_img_px,
-                                    a.w, a.h, a.count, a.nbhd, a.polarity, a.min_score, a.early, a.map, a.map_img,
-                                    kChunkCfg, st);
+    TileConfig cfg;
+    if (pick_fast_scorer(m, level, a, &cfg))
+        return launch_fast_scorer(m, level, a, cfg, st);
     return launch_score_map_generic(m->dev[level], a, st);
 }
 
@@ -615,6 +636,7 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     TileConfig bestc;
     bool found = false;
     int n = 0;
+    std::vector<TileConfig> cands;
     for (int warps : {8, 4})
         for (int sy = 1; sy <= 2; ++sy)
             for (int sx = 1; sx <= 3; ++sx)
@@ -624,13 +646,21 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                     c.sy = sy;
                     c.tg = std::min(tg, nth);
                     c.warps = warps;
-                    if (!tiled_ok(m, top, sa, c))
-                        continue;
-                    cudaError_t e = launch_tiled_args(m, top, sa, c, st);
+                    if (tiled_ok(m, top, sa, c))
+                        cands.push_back(c);
+                }
+    // chunked tilings (tg = 0): one warp tile per warp
+    for (const TileConfig &c : {TileConfig{2, 2, 0, 4}, TileConfig{4, 1, 0, 4}, TileConfig{1, 4, 0, 4},
+                                TileConfig{2, 4, 0, 8}, TileConfig{4, 2, 0, 8}})
+        if (chunked_ok(m, top, sa, c))
+            cands.push_back(c);
+    {
+        for (const TileConfig &c : cands) {
+                    cudaError_t e = launch_fast_scorer(m, top, sa, c, st);
                     cudaEventRecord(e0, st);
                     const int reps = 3;
                     for (int r = 0; r < reps && e == cudaSuccess; ++r)
-                        e = launch_tiled_args(m, top, sa, c, st);
+                        e = launch_fast_scorer(m, top, sa, c, st);
                     cudaEventRecord(e1, st);
                     if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                         cudaEventDestroy(e0);
@@ -653,7 +683,8 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                         bestc = c;
                         found = true;
                     }
-                }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *n_out = std::min(n, max_out);
@@ -774,25 +805,10 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
     a.map_img = (size_t)nk * gw * gh;
     a.count = 1;
     const PoseWindow pw{x0, y0, gw, gh, k0, nk};
-    const ScoreChoice &c = score_choice();
-    TileConfig cfg = c.cfg;
-    if (m->tuned[precision] && c.kernel == 0) {
-        cfg.sx = m->tile_sx[precision];
-        cfg.sy = m->tile_sy[precision];
-        cfg.tg = m->tile_tg[precision];
-        cfg.warps = m->tile_warps[precision];
-    }
-    cudaError_t e;
-    if (tiled_ok(m, level, a, cfg))
-        e = launch_score_tiled(m, level, field, precision, field_pitch(w, SAM_LAYOUT_PAIRS), a.field_img_px, w, h, 1,
-                               neighbourhood, m->p.polarity, min_score, a.early, map, a.map_img, cfg, st, &pw);
-    else if (chunked_ok(m, level, a))
-        e = launch_score_chunked(m, level, field, precision, field_pitch(w, SAM_LAYOUT_PAIRS), a.field_img_px, w, h,
-                                 1, neighbourhood, m->p.polarity, min_score, a.early, map, a.map_img, kChunkCfg, st,
-                                 &pw);
-    else
+    TileConfig cfg;
+    if (!pick_fast_scorer(m, level, a, &cfg))
         return SAM_ERR_ARG;
-    if (e != cudaSuccess)
+    if (launch_fast_scorer(m, level, a, cfg, st, &pw) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (rescore) {
         const size_t cap = (scratch_bytes - rescore_scratch_bytes(0)) / 8;
@@ -804,8 +820,8 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
 }
 
 sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps) {
-    if (kernel < 0 || kernel > 2 || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 1 || tg > 4096 ||
-        (warps != 4 && warps != 8))
+    if (kernel < 0 || kernel > 2 || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 0 || tg > 4096 ||
+        (warps != 4 && warps != 8) || (tg == 0 && sx * sy != warps))
         return SAM_ERR_ARG;
     ScoreChoice &c = score_choice();
     c.kernel = kernel;

@@ -14,7 +14,7 @@
 // every remaining term is at most 1, so the pose's score cannot reach
 // min_score when S_j + (n - j) < n * min_score - margin.  The margin covers
 // the FP32 rounding of S_j and the storage rounding of w_hat:
-// margin = 1e-3 + n * eps_term (eps_term 1e-6 FP32, 1e-3 FP16, 4e-3 BF16).
+// margin = 1e-3 + n * eps_term (eps_term 1e-6 FP32, 1e-3 FP16, 6e-3 BF16).
 // Pruned poses are written as -inf.
 
 #include <cuda_bf16.h>
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(256)
                 float v = 0.f;
                 if (x >= 0 && y >= 0 && x < w && y < h) {
                     const float2 f = load_field<E, LAYOUT>(field, pitch, x, y);
-                    // FP16 fields: the direction is rounded to FP16 too and
-                    // the product px*wx is exact, matching the tiled kernel's
-                    // mixed-precision FMA bit for bit
+                    // 16-bit fields: the direction is rounded to the same
+                    // type and the product px*wx is exact, matching the tiled
+                    // kernel's mixed-precision FMA bit for bit
                     const float px = dir_round<E>(p.px), py = dir_round<E>(p.py);
                     v = fmaf(py, f.y, px * f.x);
                     if (polarity)

@@ -214,9 +214,10 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
             for (int k = 0; k < L.ntheta; ++k)
                 rotate_level(L, k, L.rot.data() + (size_t)k * L.n, L.bbox[k]);
         }
+        // chunk tables for every level: required where the rotated extent
+        // exceeds one window, and a tiling choice of the autotuner elsewhere
         for (int l = 0; l < p.levels; ++l)
-            if (level_needs_chunks(m->lv[l]))
-                build_chunks(m->lv[l]);
+            build_chunks(m->lv[l]);
         // Coarse-to-fine shifts: a parent pose u' at level l (angle index k')
         // maps to the level-(l-1) pose 2u' + (1/2, 1/2) - R(theta) d with
         // d = 2 c_l + 1/2 - c_{l-1} per axis (c = reference point); the

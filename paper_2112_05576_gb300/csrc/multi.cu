@@ -59,7 +59,8 @@ struct sam_multi {
     size_t bytes = 0;
     // descriptor region
     size_t off_desc = 0, desc_bytes = 0;
-    size_t off_counters = 0;           // [work counter][cand counters x n_pairs]
+    size_t off_counters = 0;           // [work counter][cand counters, out counts, rescore counts x n_pairs]
+    size_t off_rsjobs = 0;
     size_t off_pyr = 0, off_grad = 0, off_gtop = 0, off_pairs = 0, off_tmaps = 0, off_cjobs = 0, off_rjobs = 0,
            off_njobs = 0, off_levels = 0;
     std::vector<int> pyr_count;        // jobs per pyramid step l -> l+1
@@ -217,6 +218,19 @@ sam_status upload_descriptors(sam_multi *mp) {
         c.out_count = cnt + np + i;
         put(mp->off_cjobs + (size_t)i * sizeof(CandJob), &c, sizeof(c));
         const ImgPlan &I = mp->imgs[q.img];
+        RescoreJob rs;
+        memset(&rs, 0, sizeof(rs));
+        rs.field = (const float2 *)(base + I.off_field[q.top]);
+        rs.rot = mp->models[q.model]->dev[q.top].rot;
+        rs.map = (float *)(base + q.off_map);
+        rs.list = (unsigned *)(base + q.off_rescore + rescore_scratch_bytes(0));
+        rs.count = (unsigned *)(cnt + 2 * np + i);
+        rs.w = q.W;
+        rs.h = q.H;
+        rs.n = q.n;
+        rs.nth = q.nth;
+        rs.cap = (unsigned)std::min<size_t>(q.map_img, 0xFFFFFFFFu);
+        put(mp->off_rsjobs + (size_t)i * sizeof(RescoreJob), &rs, sizeof(rs));
         RefineJob rj;
         memset(&rj, 0, sizeof(rj));
         rj.L = (const LevelDev *)(base + mp->off_levels + (size_t)q.model * sizeof(LevelDev) * kMaxLevels);
@@ -256,7 +270,7 @@ sam_status upload_descriptors(sam_multi *mp) {
 sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
     char *base = (char *)mp->base;
     const int np = (int)mp->pp.size();
-    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (1 + 2 * (size_t)np), st));
+    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (1 + 3 * (size_t)np), st));
     size_t o = mp->off_pyr;
     for (int l = 1; l < mp->Lmax; ++l) {
         const int n = mp->pyr_count[l];
@@ -276,13 +290,8 @@ sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
                              mp->p.neighbourhood, mp->models[0]->p.polarity, mp->p.early_termination, mp->cfg,
                              mp->window_bytes, (unsigned *)(base + mp->off_counters), st));
     if (mp->p.precision != SAM_FP32)
-        for (const PairPlan &q : mp->pp) {
-            const ImgPlan &I = mp->imgs[q.img];
-            MU_CU(launch_rescore(mp->models[q.model]->dev[q.top], (const float2 *)(base + I.off_field[q.top]),
-                                 I.field_px[q.top], q.W, q.H, 1, 1, 1, mp->p.neighbourhood,
-                                 mp->models[q.model]->p.polarity, mp->p.min_score, mp->p.precision,
-                                 (float *)(base + q.off_map), 0, base + q.off_rescore, q.map_img, st));
-        }
+        MU_CU(launch_rescore_jobs((const RescoreJob *)(base + mp->off_rsjobs), np, mp->max_map, mp->p.neighbourhood,
+                                  mp->models[0]->p.polarity, mp->p.min_score, mp->p.precision, st));
     MU_CU(launch_candidates_jobs((const CandJob *)(base + mp->off_cjobs), np, mp->max_map, mp->p.min_score,
                                  mp->p.top_k, st));
     MU_CU(launch_refine_jobs((const RefineJob *)(base + mp->off_rjobs), np, mp->p.top_k, mp->p.neighbourhood, st));
@@ -469,7 +478,7 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
         mp->pose_points += (long long)q.map_img * q.n;
     }
     mp->off_counters = off;
-    off += al(sizeof(int) * (1 + 2 * (size_t)n_pairs));
+    off += al(sizeof(int) * (1 + 3 * (size_t)n_pairs));
     // descriptors
     mp->off_desc = off;
     mp->pyr_count.assign(mp->Lmax, 0);
@@ -496,6 +505,7 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
     mp->off_pairs = take((size_t)n_pairs * sizeof(PairScore));
     mp->off_tmaps = take((size_t)n_pairs * 128);
     mp->off_cjobs = take((size_t)n_pairs * sizeof(CandJob));
+    mp->off_rsjobs = take((size_t)n_pairs * sizeof(RescoreJob));
     mp->off_rjobs = take((size_t)n_pairs * sizeof(RefineJob));
     mp->off_njobs = take((size_t)n_pairs * sizeof(NmsJob));
     mp->off_levels = take((size_t)n_models * sizeof(LevelDev) * kMaxLevels);

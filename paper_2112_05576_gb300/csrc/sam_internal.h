@@ -267,6 +267,19 @@ struct CandJob {
     float *out_s;      // K
     int *out_count;
 };
+// FP32 rescoring of one (image, model) pair's 16-bit map (job-list form).
+struct RescoreJob {
+    const float2 *field;   // FP32 pixel-layout field of the scored level (pitch w)
+    const RotPt *rot;      // the model level's rotated points [nth][n]
+    float *map;            // [nth][h][w]
+    unsigned *list;        // 2 x cap entries
+    unsigned *count;       // zeroed before the launch
+    int w, h, n, nth;
+    unsigned cap;
+};
+cudaError_t launch_rescore_jobs(const RescoreJob *jobs, int n_jobs, size_t max_map, int nbhd, int polarity,
+                                float min_score, int precision, cudaStream_t st);
+
 struct RefineJob {
     const LevelDev *L;                 // the model's level tables (device)
     const float2 *field[kMaxLevels];   // this image's FP32 pixel-layout fields

@@ -24,8 +24,9 @@ __device__ __forceinline__ float2 load_field(const E *f, int pitch, int x, int y
     return make_float2(to_f32(__ldg(f + i)), to_f32(__ldg(f + i + 1)));
 }
 
-// The point direction as the scoring arithmetic sees it: FP16 fields are
-// scored with FP16 directions (mixed-precision FMA), others in FP32.
+// The point direction as the scoring arithmetic sees it: 16-bit fields are
+// scored with directions rounded to the same type (mixed-precision FMA, exact
+// 16-bit products), FP32 fields in FP32.
 template <typename E>
 __device__ __forceinline__ float dir_round(float v) {
     return v;
@@ -34,11 +35,17 @@ template <>
 __device__ __forceinline__ float dir_round<__half>(float v) {
     return __half2float(__float2half_rn(v));
 }
+template <>
+__device__ __forceinline__ float dir_round<__nv_bfloat16>(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
 
-// Per-term error bound of the stored unit field (component rounding; FP16
-// also rounds the direction: 2 sqrt(2) 2^-12 < 7e-4; BF16: sqrt(2) 2^-9).
+// Per-term error bound of 16-bit storage against exact arithmetic: each
+// component of the unit field and of the direction is rounded by at most
+// 2^-12 (FP16) or 2^-9 (BF16), so a term moves by at most 2 sqrt(2) times
+// that (6.9e-4, 5.5e-3), plus FP32 rounding.
 inline float term_eps(int precision) {
-    return precision == SAM_FP32 ? 1e-6f : (precision == SAM_FP16 ? 1e-3f : 4e-3f);
+    return precision == SAM_FP32 ? 1e-6f : (precision == SAM_FP16 ? 1e-3f : 6e-3f);
 }
 
 // Early termination: prune when S_j + (n - j) < n * min_score - margin,

@@ -22,8 +22,8 @@
 //
 // Field layout (pixel pairs).  Pixels 2j, 2j+1 of a row are stored together
 // as {wx_2j, wx_2j+1, wy_2j, wy_2j+1}: 16 bytes in FP32, 8 bytes in FP16 or
-// BF16 (converted to FP32 after the load; arithmetic and accumulation stay
-// FP32).  The shared-memory traffic is the kernel's bound (about 15 bytes per
+// BF16 (multiplied by a 16-bit-rounded direction with mixed-precision FMA;
+// accumulation stays FP32).  The shared-memory traffic is the kernel's bound (about 15 bytes per
 // pose-point in FP32, 7.5 in 16-bit storage), so lanes are laid out to keep
 // the loads conflict-free: FP32 uses 128-bit loads with 8 lanes along x, a
 // quarter-warp's lanes starting 3 pairs apart (8 distinct 16-byte slots);
@@ -139,14 +139,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// Dot products of npairs pixel pairs of one window row with the point's
-// direction (px, py), packed FP32x2.
-// Dot products of one pixel pair with the point direction.  FP32 and BF16
-// storage: FP32 components (BF16 widened exactly), packed FP32x2 FMA.  FP16
-// storage: mixed-precision FMA, the FP16 products formed exactly and
-// accumulated in FP32, with the direction rounded to FP16 as well (per-term
-// error at most 2 sqrt(2) 2^-12 < 7e-4 against exact arithmetic), which saves
-// the two conversions per half-pair.
+// Dot products of one pixel pair with the point direction.  FP32 storage:
+// packed FP32x2 FMA.  FP16 and BF16 storage: mixed-precision FMA, the 16-bit
+// products formed exactly and accumulated in FP32, with the direction
+// rounded to the field's type as well (per-term error at most
+// 2 sqrt(2) 2^-12 < 7e-4 for FP16, 2 sqrt(2) 2^-9 < 5.6e-3 for BF16, against
+// exact arithmetic), which saves the conversions of the stored halves.
 template <typename E>
 struct PairDot {
     static __device__ __forceinline__ void run(const typename Pairs<E>::Raw *row, int q, float2 pxx, float2 pyy,
@@ -169,6 +167,21 @@ struct PairDot<__half> {
         asm("{\n .reg .b16 x0, x1, y0, y1;\n .reg .f32 t0, t1;\n mov.b32 {x0, x1}, %2;\n mov.b32 {y0, y1}, %3;\n"
             " fma.rn.f32.f16 t0, %4, x0, 0f00000000;\n fma.rn.f32.f16 t1, %4, x1, 0f00000000;\n"
             " fma.rn.f32.f16 %0, %5, y0, t0;\n fma.rn.f32.f16 %1, %5, y1, t1;\n}"
+            : "=f"(d0), "=f"(d1)
+            : "r"(u.x), "r"(u.y), "h"(ph), "h"(qh));
+    }
+};
+
+template <>
+struct PairDot<__nv_bfloat16> {
+    static __device__ __forceinline__ void run(const uint2 *row, int q, float2 pxx, float2 pyy, float &d0,
+                                               float &d1) {
+        const uint2 u = row[q];
+        const unsigned short ph = __bfloat16_as_ushort(__float2bfloat16_rn(pxx.x));
+        const unsigned short qh = __bfloat16_as_ushort(__float2bfloat16_rn(pyy.x));
+        asm("{\n .reg .b16 x0, x1, y0, y1;\n .reg .f32 t0, t1;\n mov.b32 {x0, x1}, %2;\n mov.b32 {y0, y1}, %3;\n"
+            " fma.rn.f32.bf16 t0, %4, x0, 0f00000000;\n fma.rn.f32.bf16 t1, %4, x1, 0f00000000;\n"
+            " fma.rn.f32.bf16 %0, %5, y0, t0;\n fma.rn.f32.bf16 %1, %5, y1, t1;\n}"
             : "=f"(d0), "=f"(d1)
             : "r"(u.x), "r"(u.y), "h"(ph), "h"(qh));
     }

@@ -1,10 +1,12 @@
-"""GPU parity of the 16-bit stored forms (FP16 / BF16 w_hat, FP32 arithmetic).
+"""GPU parity of the 16-bit stored forms (FP16 / BF16 w_hat, FP32 accumulation).
 
-The stored unit field is rounded to 16 bits; dot products, maxima and sums
+The stored unit field is rounded to 16 bits and the point direction to the
+same type; the products are exact (mixed-precision FMA) and maxima and sums
 stay FP32, so: the tiled and generic kernels agree to FP32 summation error
-on the same 16-bit field, both stay within 2e-3 of the FP64 oracle, early
-termination stays exact-safe with the widened margin, and full detections
-(refined and rescored on FP32 fields) equal the FP32 path's.
+on the same 16-bit field, both stay within the worst-case storage bound of
+the FP64 oracle (8e-4 FP16, 6e-3 BF16), early termination stays exact-safe
+with the widened margin, and full detections (refined and rescored on FP32
+fields) equal the FP32 path's.
 """
 
 import numpy as np
@@ -18,7 +20,10 @@ pytestmark = pytest.mark.gpu
 
 import paper_2112_05576_gb300 as sam  # noqa: E402
 
-LOWP = 2e-3
+# worst-case |M16 - M| against exact arithmetic: 16-bit field and direction
+# components rounded (2 sqrt(2) u per term, u = 2^-12 FP16, 2^-9 BF16) plus
+# FP32 accumulation
+LOWP = {sam.FP16: 8e-4, sam.BF16: 6e-3}
 PRECS = [(sam.FP16, torch.float16), (sam.BF16, torch.bfloat16)]
 
 
@@ -66,7 +71,7 @@ def test_tiled_lowp_matches_generic_and_oracle(cfg2, prec, dt, cfg):
     tiled = _map(m, 3, top, prec, dt, 2, cfg)
     generic = _map(m, 3, top, prec, dt, 1)
     assert np.max(np.abs(tiled - generic)) < 1e-5
-    assert np.max(np.abs(tiled - ref)) < LOWP
+    assert np.max(np.abs(tiled - ref)) < LOWP[prec]
 
 
 @pytest.mark.parametrize("prec,dt", PRECS)
@@ -81,7 +86,7 @@ def test_tiled_lowp_ragged_and_tiny(prec, dt):
         f = oracle.search_fields(img, 1, 10)[0]
         ref = oracle.score_map(f, om.points[0], 24, 15.0)
         assert np.max(np.abs(got - gen)) < 1e-5, (h, w)
-        assert np.max(np.abs(got - ref)) < LOWP, (h, w)
+        assert np.max(np.abs(got - ref)) < LOWP[prec], (h, w)
 
 
 @pytest.mark.parametrize("prec,dt", PRECS)
@@ -92,7 +97,7 @@ def test_tiled_lowp_early_termination_exact_safe(cfg2, prec, dt):
         pruned = np.isneginf(got)
         assert pruned.any()
         assert np.all(ref[pruned] < ms)
-        assert np.max(np.abs(got[~pruned] - ref[~pruned])) < LOWP
+        assert np.max(np.abs(got[~pruned] - ref[~pruned])) < LOWP[prec]
 
 
 @pytest.mark.parametrize("prec", [sam.FP16, sam.BF16])

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 import paper_2112_05576_gb300 as sam  # noqa: E402
 
 SCORE_TOL = 1e-5
-LOWP_TOL = 2e-3
+# worst-case |M16 - M|: 2 sqrt(2) u per term (u = 2^-12 FP16, 2^-9 BF16) plus FP32 rounding
+LOWP_TOL = {sam.FP16: 8e-4, sam.BF16: 6e-3}
 
 
 def _dev(a):
@@ -167,7 +168,7 @@ def test_score_map_low_precision_field(precision):
     got = _gpu_map(m, 2, top, precision=precision)
     f = oracle.search_fields(sc, 3, 30)[2]
     ref = oracle.score_map(f, om.points[2], om.ntheta(2), om.dtheta(2))
-    assert np.max(np.abs(got - ref)) < LOWP_TOL
+    assert np.max(np.abs(got - ref)) < LOWP_TOL[precision]
 
 
 # ---------------------------------------------------------------------------

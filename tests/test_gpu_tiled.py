@@ -73,8 +73,10 @@ def test_pairs_layout_gradient_matches_pixel_layout():
             assert np.all(wx[:, w:] == 0) and np.all(wy[:, w:] == 0)
 
 
-@pytest.mark.parametrize("cfg", [(2, 1, 9, 8), (1, 1, 1, 4), (3, 2, 45, 8), (1, 4, 7, 4), (2, 2, 90, 8)])
+@pytest.mark.parametrize("cfg", [(2, 1, 9, 8), (1, 1, 1, 4), (3, 2, 45, 8), (1, 4, 7, 4), (2, 2, 90, 8),
+                                 (2, 2, 0, 4), (4, 1, 0, 4), (1, 4, 0, 4), (2, 4, 0, 8), (4, 2, 0, 8)])
 def test_tiled_matches_oracle_config1_top(cfg):
+    # tg = 0: the chunked kernel
     tm, sc, _ = synth.config1_scene()
     m = sam.Model(tm, 30, 60, 3, 1.0)
     om = oracle.create_model(tm, 30, 60, 3, 1.0)
@@ -103,9 +105,11 @@ def test_tiled_ragged_sizes_match_generic_and_oracle(h, w):
     om = oracle.create_model(tm, 10, 20, 1, 15.0)
     got = _map(m, 0, img, 2, (1, 1, 5, 4))
     gen = _map(m, 0, img, 1)
+    chk = _map(m, 0, img, 2, (2, 2, 0, 4))
     ref = _oracle_map(om, 0, img)
     assert np.max(np.abs(got - ref)) < TOL
     assert np.max(np.abs(got - gen)) < TOL
+    assert np.max(np.abs(chk - ref)) < TOL
 
 
 def test_tiled_early_termination_exact_safe():
@@ -116,8 +120,9 @@ def test_tiled_early_termination_exact_safe():
     ref = _oracle_map(om, 3, top)
     full = _map(m, 3, top, 2)
     assert np.max(np.abs(full - ref)) < TOL
-    for ms in (0.5, 0.6, 0.8):
-        got = _map(m, 3, top, 2, min_score=ms, early=1)
+    for ms, cfg in ((0.5, (2, 1, 9, 8)), (0.6, (2, 1, 9, 8)), (0.8, (2, 1, 9, 8)), (0.6, (2, 2, 0, 4)),
+                    (0.8, (2, 4, 0, 8))):
+        got = _map(m, 3, top, 2, cfg, min_score=ms, early=1)
         pruned = np.isneginf(got)
         assert np.all(ref[pruned] < ms)
         assert np.max(np.abs(got[~pruned] - ref[~pruned])) < TOL

@@ -188,7 +188,7 @@ def test_chunked_16bit_with_fp32_rescoring(big_case, prec):
     # every pose left at a 16-bit value or -inf is below min_score in FP32
     assert (f32[~np.isfinite(got)] < ms).all()
     raw = _window(model, f16, img, prec, win, early=0)
-    assert np.abs(raw - f32).max() < (3e-3 if prec == sam.BF16 else 8e-4)
+    assert np.abs(raw - f32).max() < (6e-3 if prec == sam.BF16 else 8e-4)
     # a rescoring list too small for the window flags the overflow with NaN
     tiny = torch.empty(sam.score_window_scratch_bytes(4), dtype=torch.uint8, device="cuda")
     got2 = _window(model, f16, img, prec, win, early=0, min_score=0.0, field32=field32, scratch=tiny)
