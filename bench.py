@@ -130,9 +130,15 @@ def top_pose_points(model, batch):
 # point it reads the (8 + 2) x (6 + 2) pixels under the block's 3 x 3
 # windows from the staged FP32 field, 8 bytes per pixel: 640 bytes for 48
 # pose-points, i.e. 13.33 algorithmic shared-memory bytes per pose-point.
-# Peak: 128 bytes/clk/SM x SMs x maximum SM clock.  Achieved counts nominal
-# pose-points (early termination not subtracted, as in the metric); the
-# launch without early termination is reported beside it.
+# (16-bit fields: 4 bytes per pixel, half that.)  The chunked kernel uses
+# the same block; the tiled kernel's 8 x 10 block needs 10 x 12 pixels per
+# 80 poses, 12 bytes per pose-point (the figure quoted is the 8 x 6 one, so
+# the fraction is conservative for it).
+# Peak: 128 bytes/clk/SM x SMs x maximum SM clock.  Achieved counts the
+# pose-points the kernel evaluated (the library's device counter: poses
+# inside the map x points processed before early termination), so work that
+# early termination skips is not credited; the nominal-count figure and the
+# launch without early termination are reported beside it.
 SMEM_B_PER_PP = 640.0 / 48.0
 SMEM_B_PER_CLK_SM = 128.0
 # Second bound, of the method itself with full reuse of the per-pixel dot
@@ -146,7 +152,7 @@ CMP_PER_CLK_SM = 128.0
 # workload, from an ncu capture at the tiling below (summary and command in
 # profiles/score_tiled_config2_batch16.md); reported only when the bench
 # runs that tiling, and to be re-taken whenever the kernel changes.
-NCU_SCORE_TRAFFIC = {"tiling": (1, 1, 3, 8), "bytes": 2834688 + 3940864}
+NCU_SCORE_TRAFFIC = {"tiling": (1, 1, 3, 4, 10), "bytes": 2836992 + 3915264}
 
 
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
@@ -401,9 +407,13 @@ def run_stress(args, sam, torch, dev, stream):
                 sam.score_window(model, 0, fields[prec], W5, H5, prec, x0, y0, gw, gh, k0, nk, omap, nbhd=3,
                                  min_score=0.6, early=early, field32=f32, scratch=scratch if f32 is not None else None)
             call(0)
+            sam.executed_pose_points(reset=True)
             ms = _event_ms(torch, dev, stream, call, reps)
+            ex = sam.executed_pose_points(reset=True) / reps
             res[label] = {"ms": round(ms, 3), "value": pp / (ms * 1e-3), "unit": UNIT,
-                          "smem_frac": round(pp * SMEM_B_PER_PP / (ms * 1e-3) / 1e12 / smem_peak, 4),
+                          "executed_pose_points": int(ex),
+                          "smem_frac": round(ex * SMEM_B_PER_PP * (1.0 if prec == 0 else 0.5) / (ms * 1e-3) / 1e12
+                                             / smem_peak, 4),
                           "best": round(float(omap.max()), 5)}
         out[name] = res
     rate = out["angles8_full_image"]["fp32"]["value"]
@@ -454,8 +464,7 @@ def run_gpu(args):
     # the project's autotuner picks the scorer's tiling on this workload (setup,
     # outside every timed region)
     if args.tiling:
-        sx, sy, tg, wp = (int(v) for v in args.tiling.split(","))
-        sam.set_score_kernel(2, sx, sy, tg, wp)
+        sam.set_score_kernel(2, *(int(v) for v in args.tiling.split(",")))
     tuning = sam.autotune(model, batches[0], params) if (args.autotune and not args.tiling) else []
 
     def step(i):
@@ -468,6 +477,7 @@ def run_gpu(args):
     sam.profile_enable(True)
     sam.profile_read()
     launches0 = sam.kernel_launches()
+    sam.executed_pose_points(reset=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -483,6 +493,7 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     launches = sam.kernel_launches() - launches0
+    exec_pp = sam.executed_pose_points(reset=True) / max(1, args.steps)
     prof = sam.profile_read()
     sam.profile_enable(False)
     ms = shard.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
@@ -551,7 +562,7 @@ def run_gpu(args):
                            "ms_per_detection": round(fms / B, 5),
                            "score_map_ms": round(pf["score_map"][0] / max(1, pf["score_map"][1]), 4),
                            "same_detections_as_fp32": bool(same), "steps": n_form,
-                           "tiling": dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model, code)))}
+                           "tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, code)))}
 
     # ---- the batched uneven form: many image sizes and templates, one graph ----
     batched = run_batched(args, sam, torch, dev, stream) if (args.multi > 0 and rank == 0) else None
@@ -584,7 +595,7 @@ def run_gpu(args):
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(dev)
     score_ms, score_calls = prof["score_map"]
-    rl = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
+    rl = roofline(exec_pp, score_ms / max(1, score_calls), props.multi_processor_count,
                   float(peaks.get("sm_max_mhz", 2070.0)),
                   traffic=args.traffic if args.traffic is not None else (
                       NCU_SCORE_TRAFFIC["bytes"]
@@ -600,7 +611,13 @@ def run_gpu(args):
     rl["no_early_termination"] = {"ms_per_launch": round(fms / max(1, fcalls), 4), "achieved": rl_full["achieved"],
                                   "frac": rl_full["frac"]}
     rl["ms_per_launch"] = round(score_ms / max(1, score_calls), 4)
-    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps"), sam.model_tiling(model, params.precision)))
+    rl_nom = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
+                      float(peaks.get("sm_max_mhz", 2070.0)))
+    rl["executed_pose_points_per_launch"] = int(exec_pp)
+    rl["nominal_pose_points_per_launch"] = int(pp_step)
+    rl["nominal"] = {"achieved": rl_nom["achieved"], "frac": rl_nom["frac"],
+                     "what": "nominal pose-points (early termination not subtracted) x 13.33 B / launch time"}
+    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision)))
     rl["tiling"]["autotuned"] = bool(tuning)
     if tuning:
         rl["tiling"]["candidates"] = len(tuning)
@@ -664,7 +681,7 @@ def main():
     ap.add_argument("--multi", type=int, default=64, help="images of the batched uneven form (0: skip)")
     ap.add_argument("--refine", type=int, default=4096, help="poses of the differentiable form (0: skip)")
     ap.add_argument("--stress", type=int, default=1, help="time the config-5 stress slices (0: skip)")
-    ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps (no autotuning)")
+    ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps[,cols] (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
     args = ap.parse_args()

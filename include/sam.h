@@ -196,8 +196,9 @@ sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t 
  * and synchronises the stream.  Plans are not thread-safe; runs of one plan
  * must not overlap.  sam_multi_autotune times the scorer of the current batch
  * (images already written) over its tiling candidates (super-tile 1..2 x
- * 1..2, angles per unit 1, 3, 5, 9, 15, 4 or 8 warps) and keeps the fastest;
- * sam_multi_set_tiling sets one.  sam_multi_stats: top-level pose-points per
+ * 1..2, angles per unit 1, 3, 5, 9, 15, 4 or 8 warps, 6 or 10 pose columns
+ * per thread) and keeps the fastest, writing cfg_out[5 i ..] = (sx, sy, tg,
+ * warps, cols) and ms_out[i]; sam_multi_set_tiling sets one.  sam_multi_stats: top-level pose-points per
  * run (nominal), kernels per graph replay, device bytes held.
  * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT.
  * ------------------------------------------------------------------------- */
@@ -213,7 +214,7 @@ uint8_t *sam_multi_image(sam_multi *mp, int i, int *pitch);
  * on_device, else host) into the plan, ordered on `stream`. */
 sam_status sam_multi_set_image(sam_multi *mp, int i, const uint8_t *src, int stride, int on_device, void *stream);
 sam_status sam_multi_run(sam_multi *mp, void *stream, sam_pose *out, int capacity, int *n_out);
-sam_status sam_multi_set_tiling(sam_multi *mp, int sx, int sy, int tg, int warps);
+sam_status sam_multi_set_tiling(sam_multi *mp, int sx, int sy, int tg, int warps, int cols);
 sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
                               int *n_out);
 sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long long *graph_kernels,
@@ -284,27 +285,29 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
 /* Score-kernel selection and tiling, process-wide (autotuner hook; the paper
  * has no counterpart).  kernel: 0 automatic, 1 generic one-thread-per-pose,
  * 2 tiled (falls back to generic when the tiled kernel cannot serve a call).
- * sx, sy: CTA super-tile in 48x32-pose warp tiles; tg: angles per CTA, or 0
- * for the chunked tiled kernel (one angle per CTA, points grouped by 16 x 16
- * offset cell with one staged window per cell; requires sx * sy == warps);
- * warps: 4 or 8.  Returns SAM_ERR_ARG on out-of-range values. */
-sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps);
+ * A thread scores an 8 x cols block of poses of one angle (cols 6 or 10);
+ * a warp tile is (8 x cols) x 32 poses for FP32 fields, (16 x cols) x 16 for
+ * 16-bit fields.  sx, sy: CTA super-tile in warp tiles; tg: angles per CTA,
+ * or 0 for the chunked tiled kernel (one angle per CTA, points grouped by
+ * 16 x 16 offset cell with one staged window per cell; requires
+ * sx * sy == warps and cols 6); warps: 4 or 8.  Returns SAM_ERR_ARG on
+ * out-of-range values. */
+sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps, int cols);
 /* Reads back the current selection (any pointer may be NULL). */
-void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps);
+void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps, int *cols);
 
 /* Autotuner for the tiled exhaustive scorer (the paper has no counterpart).
  * Prepares the top-level field of the caller's batch (arguments as for
  * sam_detect_batch, images on the device), then times the tiled kernel with
  * every tiling of its candidate set (super-tile 1..3 x 1..2 warp tiles,
- * angles per CTA 1, 3, 5, 9, 15 or all, 4 or 8 warps; tilings whose window
- * does not fit are skipped) and the chunked kernel with its CTA tiles
- * (2x2, 4x1, 1x4 of 4 warps; 2x4, 4x2 of 8 warps; reported with tg = 0)
- * using CUDA events on `stream`, and keeps the
- * fastest for this model and this field precision (used by later calls with
- * that precision while sam_set_score_kernel selects 0, automatic).  Optional
- * outputs: cfg_out[4 i ..] = (sx, sy, tg,
- * warps) and ms_out[i] of up to max_out candidates; *n_out = how many were
- * written.  Uses the model's workspace; synchronises `stream`.
+ * angles per CTA 1, 3, 5, 9, 15 or all, 4 or 8 warps, 6 or 10 pose columns
+ * per thread; tilings whose window does not fit are skipped) and the
+ * chunked kernel with its CTA tiles (2x2, 4x1, 1x4 of 4 warps; 2x4, 4x2 of
+ * 8 warps; reported with tg = 0) using CUDA events on `stream`, and keeps
+ * the fastest for this model and this field precision (used by later calls
+ * with that precision while sam_set_score_kernel selects 0, automatic).
+ * Optional outputs: cfg_out[5 i ..] = (sx, sy, tg, warps, cols) and
+ * ms_out[i] of up to max_out candidates; *n_out = how many were written.  Uses the model's workspace; synchronises `stream`.
  * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT. */
 sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h, int stride,
                         const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
@@ -312,7 +315,7 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
 /* The tiling the model's next calls with field `precision` will use (tuned,
  * else the default). */
 sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
-                            int32_t *warps);
+                            int32_t *warps, int32_t *cols);
 /* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
  * clears it if any wait gave up since the last call (synchronises the
  * device). */
@@ -419,6 +422,15 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
 #define SAM_NUM_STAGES 6
 void sam_profile_enable(int on);
 int sam_profile_read(float *ms, int *calls, int n);
+
+/* Pose-points the tiled and chunked exhaustive scorers have evaluated on the
+ * current device since the last reset (each warp's poses inside the map
+ * times the model points it processed before finishing or being pruned by
+ * early termination; without early termination this is the nominal count,
+ * poses x points).  Synchronises
+ * the device; reset != 0 clears the counter after reading.  -1 on a CUDA
+ * error. */
+long long sam_executed_pose_points(int reset);
 
 /* Number of CUDA kernels this library has launched in this process
  * (all entry points, all devices).  Monotonic; for accounting only. */

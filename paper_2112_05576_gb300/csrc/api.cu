@@ -347,14 +347,14 @@ bool tiled_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfi
     int bxw = 0, byw = 0;
     return cfg.tg >= 1 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
            ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) &&
-           tiled_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, cfg.tg, &bxw, &byw);
+           tiled_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, cfg.tg, cfg.tc, &bxw, &byw);
 }
 
 // A tiling with tg == 0 selects the chunked scorer (one angle per CTA, CTA
 // tile of sx x sy warp tiles, one warp tile per warp).  Its default, 2 x 2
 // warp tiles of 4 warps, needs a ~75 KB FP32 window per 16-pixel chunk cell:
 // three CTAs per SM.
-constexpr TileConfig kChunkCfg = {2, 2, 0, 4};
+constexpr TileConfig kChunkCfg = {2, 2, 0, 4, kChunkCols};
 
 bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg = kChunkCfg) {
     int bxw = 0, byw = 0;
@@ -389,6 +389,7 @@ bool pick_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, TileCon
         cfg.sy = m->tile_sy[pr];
         cfg.tg = m->tile_tg[pr];
         cfg.warps = m->tile_warps[pr];
+        cfg.tc = m->tile_tc[pr];
     }
     if ((cfg.tg >= 1 && tiled_ok(m, level, a, cfg)) || (cfg.tg == 0 && chunked_ok(m, level, a, cfg))) {
         *out = cfg;
@@ -637,21 +638,24 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     bool found = false;
     int n = 0;
     std::vector<TileConfig> cands;
-    for (int warps : {8, 4})
-        for (int sy = 1; sy <= 2; ++sy)
-            for (int sx = 1; sx <= 3; ++sx)
-                for (int tg : tgs) {
-                    TileConfig c;
-                    c.sx = sx;
-                    c.sy = sy;
-                    c.tg = std::min(tg, nth);
-                    c.warps = warps;
-                    if (tiled_ok(m, top, sa, c))
-                        cands.push_back(c);
-                }
+    for (int tc : {6, 10})
+        for (int warps : {8, 4})
+            for (int sy = 1; sy <= 2; ++sy)
+                for (int sx = 1; sx <= 3; ++sx)
+                    for (int tg : tgs) {
+                        TileConfig c;
+                        c.sx = sx;
+                        c.sy = sy;
+                        c.tg = std::min(tg, nth);
+                        c.warps = warps;
+                        c.tc = tc;
+                        if (tiled_ok(m, top, sa, c))
+                            cands.push_back(c);
+                    }
     // chunked tilings (tg = 0): one warp tile per warp
-    for (const TileConfig &c : {TileConfig{2, 2, 0, 4}, TileConfig{4, 1, 0, 4}, TileConfig{1, 4, 0, 4},
-                                TileConfig{2, 4, 0, 8}, TileConfig{4, 2, 0, 8}})
+    for (const TileConfig &c : {TileConfig{2, 2, 0, 4, kChunkCols}, TileConfig{4, 1, 0, 4, kChunkCols},
+                                TileConfig{1, 4, 0, 4, kChunkCols}, TileConfig{2, 4, 0, 8, kChunkCols},
+                                TileConfig{4, 2, 0, 8, kChunkCols}})
         if (chunked_ok(m, top, sa, c))
             cands.push_back(c);
     {
@@ -671,10 +675,11 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                     cudaEventElapsedTime(&ms, e0, e1);
                     ms /= reps;
                     if (n < max_out) {
-                        cfg_out[4 * n] = c.sx;
-                        cfg_out[4 * n + 1] = c.sy;
-                        cfg_out[4 * n + 2] = c.tg;
-                        cfg_out[4 * n + 3] = c.warps;
+                        cfg_out[5 * n] = c.sx;
+                        cfg_out[5 * n + 1] = c.sy;
+                        cfg_out[5 * n + 2] = c.tg;
+                        cfg_out[5 * n + 3] = c.warps;
+                        cfg_out[5 * n + 4] = c.tc;
                         ms_out[n] = ms;
                     }
                     ++n;
@@ -695,6 +700,7 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
         m->tile_sy[pr] = bestc.sy;
         m->tile_tg[pr] = bestc.tg;
         m->tile_warps[pr] = bestc.warps;
+        m->tile_tc[pr] = bestc.tc;
     }
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
@@ -708,8 +714,8 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
 }
 
 sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
-                            int32_t *warps) {
-    if (!m || !sx || !sy || !tg || !warps || precision < SAM_FP32 || precision > SAM_FP16)
+                            int32_t *warps, int32_t *cols) {
+    if (!m || !sx || !sy || !tg || !warps || !cols || precision < SAM_FP32 || precision > SAM_FP16)
         return SAM_ERR_ARG;
     const ScoreChoice &c = score_choice();
     const bool t = m->tuned[precision];
@@ -717,6 +723,7 @@ sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int3
     *sy = t ? m->tile_sy[precision] : c.cfg.sy;
     *tg = t ? m->tile_tg[precision] : c.cfg.tg;
     *warps = t ? m->tile_warps[precision] : c.cfg.warps;
+    *cols = t ? m->tile_tc[precision] : c.cfg.tc;
     return SAM_OK;
 }
 
@@ -819,9 +826,10 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
     return SAM_OK;
 }
 
-sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps) {
+sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps, int cols) {
     if (kernel < 0 || kernel > 2 || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 0 || tg > 4096 ||
-        (warps != 4 && warps != 8) || (tg == 0 && sx * sy != warps))
+        (warps != 4 && warps != 8) || (tg == 0 && sx * sy != warps) || (cols != 6 && cols != 10) ||
+        (tg == 0 && cols != kChunkCols))
         return SAM_ERR_ARG;
     ScoreChoice &c = score_choice();
     c.kernel = kernel;
@@ -829,10 +837,11 @@ sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps) {
     c.cfg.sy = sy;
     c.cfg.tg = tg;
     c.cfg.warps = warps;
+    c.cfg.tc = cols;
     return SAM_OK;
 }
 
-void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps) {
+void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps, int *cols) {
     const ScoreChoice &c = score_choice();
     if (kernel)
         *kernel = c.kernel;
@@ -844,6 +853,8 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps) {
         *tg = c.cfg.tg;
     if (warps)
         *warps = c.cfg.warps;
+    if (cols)
+        *cols = c.cfg.tc;
 }
 
 size_t sam_candidates_scratch_bytes(int nth, int gh, int gw) { return candidates_scratch_bytes(nth, gh, gw); }

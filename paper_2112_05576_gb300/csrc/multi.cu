@@ -91,12 +91,12 @@ char *at(sam_multi *mp, size_t off) { return (char *)mp->base + off; }
 // pair's window does not fit the tiled kernel.
 bool plan_tiling(sam_multi *mp) {
     int wty = 0;
-    const int wtx = tiled_warp_tile(mp->p.precision, &wty);
+    const int wtx = tiled_warp_tile(mp->p.precision, mp->cfg.tc, &wty);
     mp->window_bytes = 0;
     const size_t pair_bytes = mp->p.precision == SAM_FP32 ? 16 : 8;
     for (PairPlan &q : mp->pp) {
         const LevelHost &L = mp->models[q.model]->lv[q.top];
-        if (!tiled_plan(L, mp->p.precision, mp->cfg.sx, mp->cfg.sy, mp->cfg.tg, &q.bxw, &q.byw))
+        if (!tiled_plan(L, mp->p.precision, mp->cfg.sx, mp->cfg.sy, mp->cfg.tg, mp->cfg.tc, &q.bxw, &q.byw))
             return false;
         q.tiles_x = (q.W + mp->cfg.sx * wtx - 1) / (mp->cfg.sx * wtx);
         const int tiles_y = (q.H + mp->cfg.sy * wty - 1) / (mp->cfg.sy * wty);
@@ -559,14 +559,16 @@ sam_status sam_multi_set_image(sam_multi *mp, int i, const uint8_t *src, int str
     return SAM_OK;
 }
 
-sam_status sam_multi_set_tiling(sam_multi *mp, int sx, int sy, int tg, int warps) {
-    if (!mp || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 1 || tg > 4096 || (warps != 4 && warps != 8))
+sam_status sam_multi_set_tiling(sam_multi *mp, int sx, int sy, int tg, int warps, int cols) {
+    if (!mp || sx < 1 || sx > 8 || sy < 1 || sy > 8 || tg < 1 || tg > 4096 || (warps != 4 && warps != 8) ||
+        (cols != 6 && cols != 10))
         return SAM_ERR_ARG;
     const TileConfig old = mp->cfg;
     mp->cfg.sx = sx;
     mp->cfg.sy = sy;
     mp->cfg.tg = tg;
     mp->cfg.warps = warps;
+    mp->cfg.tc = cols;
     const sam_status s = rebuild(mp);
     if (s != SAM_OK) {
         mp->cfg = old;
@@ -649,6 +651,7 @@ sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, flo
     float best_ms = 1e30f;
     int n = 0;
     const int tgs[] = {1, 3, 5, 9, 15};
+    for (int tc : {6, 10})
     for (int warps : {8, 4})
         for (int sy = 1; sy <= 2; ++sy)
             for (int sx = 1; sx <= 2; ++sx)
@@ -657,6 +660,7 @@ sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, flo
                     mp->cfg.sy = sy;
                     mp->cfg.tg = tg;
                     mp->cfg.warps = warps;
+                    mp->cfg.tc = tc;
                     if (rebuild(mp) != SAM_OK)
                         continue;
                     char *base = (char *)mp->base;
@@ -681,10 +685,11 @@ sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, flo
                         return SAM_ERR_CUDA;
                     }
                     if (n < max_out) {
-                        cfg_out[4 * n] = sx;
-                        cfg_out[4 * n + 1] = sy;
-                        cfg_out[4 * n + 2] = tg;
-                        cfg_out[4 * n + 3] = warps;
+                        cfg_out[5 * n] = sx;
+                        cfg_out[5 * n + 1] = sy;
+                        cfg_out[5 * n + 2] = tg;
+                        cfg_out[5 * n + 3] = warps;
+                        cfg_out[5 * n + 4] = tc;
                         ms_out[n] = ms;
                     }
                     ++n;

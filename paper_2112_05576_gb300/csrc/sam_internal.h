@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,6 +83,7 @@ struct sam_model {
     // (overrides the default)
     bool tuned[3] = {false, false, false};
     int tile_sx[3] = {2, 2, 2}, tile_sy[3] = {1, 1, 1}, tile_tg[3] = {9, 9, 9}, tile_warps[3] = {8, 8, 8};
+    int tile_tc[3] = {6, 6, 6};
 };
 
 namespace sam {
@@ -141,12 +143,21 @@ struct ScoreArgs {
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
 
 // Tiled scorer (score_tiled.cu): FP32 paired field, step 1.
+// Geometry shared by the tiled scorers: a thread owns kTileRows x cols poses
+// (cols 6 or 10); FP32 pairs put kLanesXF32 lanes along x, 16-bit pairs
+// kLanesX16; the chunked kernel uses kChunkCols columns.
+constexpr int kTileRows = 8;
+constexpr int kLanesXF32 = 8;
+constexpr int kLanesX16 = 16;
+constexpr int kChunkCols = 6;
+
 struct TileConfig {
-    int sx = 2, sy = 1;   // super-tile in warp tiles (48 x 32 poses each)
-    int tg = 9;           // angles per CTA
+    int sx = 2, sy = 1;   // super-tile in warp tiles (8 x tc lanes-along-x poses wide, 32 rows tall for FP32)
+    int tg = 9;           // angles per CTA (0: the chunked kernel)
     int warps = 8;        // warps per CTA (4 or 8)
+    int tc = 6;           // pose columns per thread (6 or 10)
 };
-bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int *bxw, int *byw);
+bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int tc, int *bxw, int *byw);
 // Whether a level's rotated extent needs the chunked scorer (its whole-angle
 // window does not fit shared memory at the smallest tiling).
 bool level_needs_chunks(const LevelHost &L);
@@ -163,6 +174,60 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
                                int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
                                const PoseWindow *window = nullptr);
+
+// Kernel arguments of the single-level tiled scorer (score_tiled_kernels.cuh).
+struct TiledArgs {
+    const RotPt *rot;     // [nth][n]
+    const int4 *bbox;     // [nth]
+    int n, nth;
+    int W, H;             // map size in poses (step 1): the pose window
+    int ox, oy;           // pose of map element (0, 0)
+    int k0, nk;           // angles k0 .. k0 + nk - 1 (map plane k - k0)
+    float *map;
+    size_t map_img;
+    int sx, sy, tg;       // super-tile in warp tiles, angles per group
+    int tiles_x;          // super-tiles along x
+    int bxw, byw;         // window box (pixels, rows)
+    float inv_n;
+    float thresh;
+    int early;
+    int *err;                   // device error flag (bounded waits)
+    unsigned long long *exec;   // executed pose-point counter
+};
+
+// Kernel arguments of the chunked scorer.
+struct ChunkArgs {
+    const RotPt *rot;      // chunk-ordered points [nth][n]
+    const int *cstart;     // [nth + 1]
+    const int4 *cbox;      // per chunk (oxmin, oxmax, oymin, oymax)
+    const int2 *crange;    // per chunk [p0, p1) within the angle's points
+    int n;
+    int W, H, ox, oy, k0;  // map window (as TiledArgs)
+    float *map;
+    size_t map_img;
+    int sx, sy;            // CTA tile in warp tiles, sx * sy == warps
+    int tiles_x;
+    int bxw, byw;
+    float inv_n, thresh;
+    int early;
+    int *err;
+    unsigned long long *exec;
+};
+
+struct PairScore;
+// Per-field-type instantiations (score_tiled_f32.cu, _f16.cu, _bf16.cu).
+#define SAM_TILED_LAUNCHERS(suf)                                                                                    \
+    cudaError_t launch_tiled_##suf(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int nbhd,     \
+                                   bool pol, int warps, int tc, cudaStream_t st);                                   \
+    cudaError_t launch_chunked_##suf(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd,   \
+                                     bool pol, int warps, cudaStream_t st);                                         \
+    cudaError_t launch_pairs_##suf(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, \
+                                   bool pol, int early, size_t smem, unsigned *counter, int *err,                   \
+                                   unsigned long long *exec, cudaStream_t st);
+SAM_TILED_LAUNCHERS(f32)
+SAM_TILED_LAUNCHERS(f16)
+SAM_TILED_LAUNCHERS(bf16)
+#undef SAM_TILED_LAUNCHERS
 
 // Chunked tiled scorer for levels with chunk tables (score_tiled.cu).
 cudaError_t launch_score_chunked(const sam_model *m, int level, const void *field, int precision, int wp,
@@ -184,7 +249,7 @@ struct PairScore {
     int pad;
 };
 bool encode_pair_tmap(void *out, const void *field, int precision, int wp, int H, int bxw, int byw);
-int tiled_warp_tile(int precision, int *wty);
+int tiled_warp_tile(int precision, int tc, int *wty);
 cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_items, int precision, int nbhd,
                                int polarity, int early, const TileConfig &cfg, size_t window_bytes, unsigned *counter,
                                cudaStream_t st);

@@ -1,0 +1,24 @@
+// Instantiation of the tiled scorers for FP16-stored fields (device code in
+// score_tiled_kernels.cuh; one translation unit per field type so the
+// variants compile in parallel).
+#include "score_tiled_kernels.cuh"
+
+namespace sam {
+
+cudaError_t launch_tiled_f16(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                           int warps, int tc, cudaStream_t st) {
+    return tiled_dispatch<__half>(tm, a, grid, smem, nbhd, pol, warps, tc, st);
+}
+
+cudaError_t launch_chunked_f16(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                             int warps, cudaStream_t st) {
+    return chunked_dispatch<__half>(tm, a, grid, smem, nbhd, pol, warps, st);
+}
+
+cudaError_t launch_pairs_f16(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
+                           int early, size_t smem, unsigned *counter, int *err, unsigned long long *exec,
+                           cudaStream_t st) {
+    return pairs_dispatch<__half>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, counter, err, exec, st);
+}
+
+}  // namespace sam

@@ -1,0 +1,784 @@
+// Device code of the tiled exhaustive scorers (kernel (c)): the
+// single-level tiled kernel, the persistent kernel over (image, model) pairs
+// and the chunked kernel for large templates.  Included by one translation
+// unit per field type (score_tiled_f32.cu, _f16.cu, _bf16.cu), which
+// instantiate the kernels for that type; the host side (tiling plans, tensor
+// maps, dispatch) is score_tiled.cu.  See score_tiled.cu for the design.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sam_internal.h"
+#include "score_common.cuh"
+
+namespace sam {
+namespace {
+
+constexpr int TR = kTileRows;        // rows of poses per thread
+constexpr int PRUNE_EVERY = 32;
+
+
+
+// Stored element type of the window: pair size, lane layout, TMA alignment.
+template <typename E>
+struct Pairs;
+
+template <>
+struct Pairs<float> {
+    using Raw = float4;
+    static constexpr int BYTES = 16;   // one pixel pair
+    static constexpr int LX = kLanesXF32;   // lanes along x
+    static constexpr int XALIGN = 2;   // window start (pixels) for a 16-byte TMA start
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) { return row[q]; }
+};
+
+template <>
+struct Pairs<__half> {
+    using Raw = uint2;
+    static constexpr int BYTES = 8;
+    static constexpr int LX = kLanesX16;
+    static constexpr int XALIGN = 4;
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) {
+        const uint2 u = row[q];
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
+template <>
+struct Pairs<__nv_bfloat16> {
+    using Raw = uint2;
+    static constexpr int BYTES = 8;
+    static constexpr int LX = kLanesX16;
+    static constexpr int XALIGN = 4;
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) {
+        const uint2 u = row[q];
+        // bf16 -> fp32 is a 16-bit left shift of the bit pattern
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+    }
+};
+
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bounded wait on an mbarrier phase; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// Dot products of one pixel pair with the point direction.  FP32 storage:
+// packed FP32x2 FMA.  FP16 and BF16 storage: mixed-precision FMA, the 16-bit
+// products formed exactly and accumulated in FP32, with the direction
+// rounded to the field's type as well (per-term error at most
+// 2 sqrt(2) 2^-12 < 7e-4 for FP16, 2 sqrt(2) 2^-9 < 5.6e-3 for BF16, against
+// exact arithmetic), which saves the conversions of the stored halves.
+template <typename E>
+struct PairDot {
+    static __device__ __forceinline__ void run(const typename Pairs<E>::Raw *row, int q, float2 pxx, float2 pyy,
+                                               float &d0, float &d1) {
+        const float4 v = Pairs<E>::get(row, q);
+        float2 t = __fmul2_rn(pxx, make_float2(v.x, v.y));
+        t = __ffma2_rn(pyy, make_float2(v.z, v.w), t);
+        d0 = t.x;
+        d1 = t.y;
+    }
+};
+
+template <>
+struct PairDot<__half> {
+    static __device__ __forceinline__ void run(const uint2 *row, int q, float2 pxx, float2 pyy, float &d0,
+                                               float &d1) {
+        const uint2 u = row[q];
+        const unsigned short ph = __half_as_ushort(__float2half_rn(pxx.x));
+        const unsigned short qh = __half_as_ushort(__float2half_rn(pyy.x));
+        asm("{\n .reg .b16 x0, x1, y0, y1;\n .reg .f32 t0, t1;\n mov.b32 {x0, x1}, %2;\n mov.b32 {y0, y1}, %3;\n"
+            " fma.rn.f32.f16 t0, %4, x0, 0f00000000;\n fma.rn.f32.f16 t1, %4, x1, 0f00000000;\n"
+            " fma.rn.f32.f16 %0, %5, y0, t0;\n fma.rn.f32.f16 %1, %5, y1, t1;\n}"
+            : "=f"(d0), "=f"(d1)
+            : "r"(u.x), "r"(u.y), "h"(ph), "h"(qh));
+    }
+};
+
+template <>
+struct PairDot<__nv_bfloat16> {
+    static __device__ __forceinline__ void run(const uint2 *row, int q, float2 pxx, float2 pyy, float &d0,
+                                               float &d1) {
+        const uint2 u = row[q];
+        const unsigned short ph = __bfloat16_as_ushort(__float2bfloat16_rn(pxx.x));
+        const unsigned short qh = __bfloat16_as_ushort(__float2bfloat16_rn(pyy.x));
+        asm("{\n .reg .b16 x0, x1, y0, y1;\n .reg .f32 t0, t1;\n mov.b32 {x0, x1}, %2;\n mov.b32 {y0, y1}, %3;\n"
+            " fma.rn.f32.bf16 t0, %4, x0, 0f00000000;\n fma.rn.f32.bf16 t1, %4, x1, 0f00000000;\n"
+            " fma.rn.f32.bf16 %0, %5, y0, t0;\n fma.rn.f32.bf16 %1, %5, y1, t1;\n}"
+            : "=f"(d0), "=f"(d1)
+            : "r"(u.x), "r"(u.y), "h"(ph), "h"(qh));
+    }
+};
+
+template <typename E, bool POL, int TC>
+__device__ __forceinline__ void dots_row(const typename Pairs<E>::Raw *row, int pair0, float (&d)[TC + 4],
+                                         int npairs, float2 pxx, float2 pyy) {
+#pragma unroll
+    for (int q = 0; q < (TC + 4) / 2; ++q) {
+        if (q < npairs) {
+            float d0, d1;
+            PairDot<E>::run(row, pair0 + q, pxx, pyy, d0, d1);
+            d[2 * q] = POL ? fabsf(d0) : d0;
+            d[2 * q + 1] = POL ? fabsf(d1) : d1;
+        }
+    }
+}
+
+// One model point over the thread's R x C pose block, 3x3 neighbourhood.
+template <typename E, bool POL, bool ODD, int TC>
+__device__ __forceinline__ void point_nb3(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
+                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
+    constexpr int NP = ODD ? (TC + 4) / 2 : (TC + 2) / 2;   // pixel pairs per row
+    constexpr int OFF = ODD ? 1 : 0;
+    float hp2[TC], hp1[TC];
+#pragma unroll
+    for (int r = 0; r < TR + 2; ++r) {
+        const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
+        float d[TC + 4];
+        dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
+        float h[TC];
+#pragma unroll
+        for (int c = 0; c < TC; ++c)
+            h[c] = max3(d[OFF + c], d[OFF + c + 1], d[OFF + c + 2]);
+        if (r >= 2) {
+#pragma unroll
+            for (int j = 0; j < TC / 2; ++j) {
+                const float v0 = max3(hp2[2 * j], hp1[2 * j], h[2 * j]);
+                const float v1 = max3(hp2[2 * j + 1], hp1[2 * j + 1], h[2 * j + 1]);
+                acc[r - 2][j] = __fadd2_rn(acc[r - 2][j], make_float2(v0, v1));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < TC; ++c) {
+            hp2[c] = hp1[c];
+            hp1[c] = h[c];
+        }
+    }
+}
+
+// One model point, neighbourhood 1 (no search): the centre pixel only.
+template <typename E, bool POL, bool ODD, int TC>
+__device__ __forceinline__ void point_nb1(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
+                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
+    constexpr int NP = ODD ? (TC + 2) / 2 : TC / 2;
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
+        float d[TC + 4];
+        dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j) {
+            if (ODD)
+                acc[r][j] = __fadd2_rn(acc[r][j], make_float2(d[2 * j + 1], d[2 * j + 2]));
+            else
+                acc[r][j] = __fadd2_rn(acc[r][j], make_float2(d[2 * j], d[2 * j + 1]));
+        }
+    }
+}
+
+// What a CTA work unit needs besides its window.
+struct TileWork {
+    const RotPt *rot;
+    int n, W, H;
+    int ox, oy, k0;   // pose and angle of map element (0, 0, 0)
+    float *map;   // the image's (or pair's) map [nk][H][W]
+    float inv_n, thresh;
+    int early, sx, sy;
+    unsigned long long *exec;   // executed pose-point counter
+};
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int k_end, const TileWork &a);
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  const TiledArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the TMA destination must be 128-byte aligned: round the base up (the
+    // launch adds 128 bytes of slack)
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_org[2];   // window origin (pixel x, row y), global coords
+
+    const int img = blockIdx.z;
+    const int group = blockIdx.y;
+    const int st = blockIdx.x;
+    const int stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
+    const int sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
+    const int k_begin = a.k0 + group * a.tg;
+    const int k_end = min(k_begin + a.tg, a.k0 + a.nk);
+    const int pp = a.bxw / 2;   // window row pitch in pixel pairs
+    const uint32_t bar = smem_addr(&mbar);
+
+    if (threadIdx.x == 0) {
+        int xmin = 1 << 30, ymin = 1 << 30;
+        for (int k = k_begin; k < k_end; ++k) {
+            const int4 b = a.bbox[k];
+            xmin = min(xmin, b.x);
+            ymin = min(ymin, b.z);
+        }
+        // aligned start: the TMA x coordinate times the element size must be a
+        // multiple of 16 bytes
+        const int wx0 = (stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
+        const int wy0 = sty0 + ymin - 1;
+        s_org[0] = wx0;
+        s_org[1] = wy0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const int xe = wx0 * Pairs<E>::BYTES / 16;   // 8-byte elements
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(smem_addr(win)),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(img), "r"(bar)
+            : "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0)) {
+        if (threadIdx.x == 0)
+            atomicExch(a.err, 1);
+        return;
+    }
+    TileWork t;
+    t.rot = a.rot;
+    t.n = a.n;
+    t.W = a.W;
+    t.H = a.H;
+    t.ox = a.ox;
+    t.oy = a.oy;
+    t.k0 = a.k0;
+    t.map = a.map + (size_t)img * a.map_img;
+    t.inv_n = a.inv_n;
+    t.thresh = a.thresh;
+    t.early = a.early;
+    t.sx = a.sx;
+    t.sy = a.sy;
+    t.exec = a.exec;
+    score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], stx0, sty0, k_begin, k_end, t);
+}
+
+// The (angle, warp tile) items of one CTA work unit over its staged window
+// (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int k_end, const TileWork &a) {
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = lane % LX, ly = lane / LX;
+    const int items = (k_end - k_begin) * a.sx * a.sy;
+    float *map = a.map;
+
+    for (int it = warp; it < items; it += WARPS) {
+        const int k = k_begin + it / (a.sx * a.sy);
+        const int wt = it % (a.sx * a.sy);
+        const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC;   // thread's first pose
+        const int y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
+        // window coordinates of the first needed pixel for offset (0, 0)
+        const int bx = x0 - 1 - wx0;
+        const int by = y0 - 1 - wy0;
+        float2 acc[TR][TC / 2];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int j = 0; j < TC / 2; ++j)
+                acc[r][j] = make_float2(0.f, 0.f);
+        const RotPt *P = a.rot + (size_t)k * a.n;
+        bool pruned = false;
+        int done = a.n;
+        RotPt p = P[0];
+        for (int i = 0; i < a.n; ++i) {
+            const RotPt cur = p;
+            if (i + 1 < a.n)
+                p = P[i + 1];
+            const float2 pxx = make_float2(cur.px, cur.px);
+            const float2 pyy = make_float2(cur.py, cur.py);
+            if (NB == 3) {
+                const int xs = bx + cur.ox;   // first pixel column (>= 0)
+                const int row0 = by + cur.oy;
+                if (xs & 1)
+                    point_nb3<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                else
+                    point_nb3<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+            } else {
+                const int xs = bx + 1 + cur.ox;   // centre column
+                const int row0 = by + 1 + cur.oy;
+                if (xs & 1)
+                    point_nb1<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                else
+                    point_nb1<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+            }
+            if (a.early && ((i + 1) % PRUNE_EVERY) == 0) {
+                const float lim = a.thresh - (float)(a.n - 1 - i);
+                bool low = true;
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TC / 2; ++j)
+                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                if (__all_sync(0xffffffffu, low)) {
+                    pruned = true;
+                    done = i + 1;
+                    break;
+                }
+            }
+        }
+        {
+            // poses of this thread's block that lie inside the map
+            const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
+            const unsigned valid = __reduce_add_sync(0xffffffffu, (unsigned)(vx * vy));
+            if (lane == 0)
+                atomicAdd(a.exec, (unsigned long long)done * valid);
+        }
+        // epilogue: M = sum / n, or -inf where pruned; clip to the window
+        float *mk = map + (size_t)(k - a.k0) * a.H * a.W;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            const int y = y0 + r - a.oy;
+            if (y >= a.H)
+                break;
+            float *row = mk + (size_t)y * a.W;
+#pragma unroll
+            for (int j = 0; j < TC / 2; ++j) {
+                const int x = x0 + 2 * j - a.ox;
+                const float v0 = pruned ? -INFINITY : acc[r][j].x * a.inv_n;
+                const float v1 = pruned ? -INFINITY : acc[r][j].y * a.inv_n;
+                if (x + 1 < a.W && (a.W & 1) == 0) {
+                    *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
+                } else {
+                    if (x < a.W)
+                        row[x] = v0;
+                    if (x + 1 < a.W)
+                        row[x + 1] = v1;
+                }
+            }
+        }
+    }
+}
+
+// Persistent form for batches of uneven (image, model) pairs: every CTA
+// pulls work units (pair, super-tile, angle group) from one atomic counter,
+// stages the unit's window with that pair's own 2-D tensor map (box sized for
+// the pair), and scores it.  The window buffer and its mbarrier are reused
+// unit after unit (the barrier's phase alternates).  Pairs are laid out
+// largest first so the dynamic schedule ends with small units.
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore *__restrict__ pairs, int n_pairs,
+                                                                  int total, int sx, int sy, int tg, int early,
+                                                                  unsigned *__restrict__ counter, int *err,
+                                                                  unsigned long long *exec) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_unit[6];   // item, pair, super-tile x0, y0, window x0, y0
+    const uint32_t bar = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(counter, 1u);
+            s_unit[0] = item;
+            if (item < total) {
+                int lo = 0, hi = n_pairs - 1;   // last pair whose first item <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pairs[mid].item_begin <= item)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const PairScore &P = pairs[lo];
+                const int local = item - P.item_begin;
+                const int group = local / P.tiles, st = local - group * P.tiles;
+                const int stx0 = (st % P.tiles_x) * sx * WTX, sty0 = (st / P.tiles_x) * sy * WTY;
+                const int k_begin = group * tg, k_end = min(k_begin + tg, P.nth);
+                int xmin = 1 << 30, ymin = 1 << 30;
+                for (int k = k_begin; k < k_end; ++k) {
+                    const int4 b = P.bbox[k];
+                    xmin = min(xmin, b.x);
+                    ymin = min(ymin, b.z);
+                }
+                const int wx0 = (stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
+                const int wy0 = sty0 + ymin - 1;
+                s_unit[1] = lo;
+                s_unit[2] = stx0;
+                s_unit[3] = sty0;
+                s_unit[4] = wx0;
+                s_unit[5] = wy0;
+                const uint32_t bytes = (uint32_t)P.bxw * (uint32_t)P.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+                // the previous unit's reads of the window (generic proxy) are
+                // ordered before this unit's copy into it (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                             : "memory");
+                const int xe = wx0 * Pairs<E>::BYTES / 16;
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                    "[%4];" ::"r"(smem_addr(win)),
+                    "l"(reinterpret_cast<uint64_t>(P.tmap)), "r"(xe), "r"(wy0), "r"(bar)
+                    : "memory");
+            }
+        }
+        __syncthreads();
+        const int item = s_unit[0];
+        if (item >= total)
+            break;
+        const bool ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0)
+                atomicExch(err, 1);
+            break;
+        }
+        const PairScore &P = pairs[s_unit[1]];
+        const int local = item - P.item_begin;
+        const int group = local / P.tiles;
+        TileWork t;
+        t.rot = P.rot;
+        t.n = P.n;
+        t.W = P.W;
+        t.H = P.H;
+        t.ox = 0;
+        t.oy = 0;
+        t.k0 = 0;
+        t.map = P.map;
+        t.inv_n = P.inv_n;
+        t.thresh = P.thresh;
+        t.early = early;
+        t.sx = sx;
+        t.sy = sy;
+        t.exec = exec;
+        score_items<E, NB, POL, WARPS, TC>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
+                                       min(group * tg + tg, P.nth), t);
+        __syncthreads();   // every warp is done with the window before the next copy
+    }
+}
+
+
+// Chunked form for templates whose rotated extent is too large for one staged
+// window (a 512-pixel template at full resolution spans ~724 pixels).  One
+// angle per CTA and one warp tile per warp; the CTA walks the angle's point
+// chunks (points grouped by 16 x 16 cell of their offset), staging for each
+// chunk by TMA only the window its points reach from the CTA tile: CTA tile
+// + chunk box + 3x3 halo.  Accumulators stay in registers across chunks;
+// early termination is checked after every chunk, and the CTA stops when
+// every warp has pruned.  Each chunk (at most 256 points) is summed into a
+// fresh FP32 partial that is then added to the running sum, so the running
+// sum takes one rounding per chunk rather than one per point: with ~6000
+// points per pose a plain serial FP32 sum drifts by ~1e-5 of the mean.  The window buffer is reused chunk after chunk
+// (mbarrier phase alternates; a proxy fence orders the previous chunk's reads
+// before the next copy).
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                    const ChunkArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_org[2];
+
+    const int img = blockIdx.z;
+    const int kl = blockIdx.y;
+    const int k = a.k0 + kl;
+    const int st = blockIdx.x;
+    const int stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
+    const int sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = lane % LX, ly = lane / LX;
+    const int x0 = stx0 + (warp % a.sx) * WTX + lx * TC;   // thread's first pose
+    const int y0 = sty0 + (warp / a.sx) * WTY + ly * TR;
+    const int pp = a.bxw / 2;
+    const uint32_t bar = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    float2 acc[TR][TC / 2];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j)
+            acc[r][j] = make_float2(0.f, 0.f);
+    const RotPt *P = a.rot + (size_t)k * a.n;
+    const int c_begin = a.cstart[k], c_end = a.cstart[k + 1];
+    bool alive = true;
+    int done = 0;
+    uint32_t parity = 0;
+    for (int c = c_begin; c < c_end; ++c) {
+        const int4 b = a.cbox[c];
+        const int2 rg = a.crange[c];
+        if (threadIdx.x == 0) {
+            const int wx0 = (stx0 + b.x - 1) & ~(Pairs<E>::XALIGN - 1);
+            const int wy0 = sty0 + b.z - 1;
+            s_org[0] = wx0;
+            s_org[1] = wy0;
+            const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+            const int xe = wx0 * Pairs<E>::BYTES / 16;
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(smem_addr(win)),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(img), "r"(bar)
+                : "memory");
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(a.err, 1);
+                mbar_wait(bar, parity ^ 1u);   // let a late copy land before the CTA exits
+            }
+            return;
+        }
+        if (alive) {
+            const int bx = x0 - 1 - s_org[0];
+            const int by = y0 - 1 - s_org[1];
+            float2 part[TR][TC / 2];
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j)
+                    part[r][j] = make_float2(0.f, 0.f);
+            RotPt q = P[rg.x];
+            for (int i = rg.x; i < rg.y; ++i) {
+                const RotPt cur = q;
+                if (i + 1 < rg.y)
+                    q = P[i + 1];
+                const float2 pxx = make_float2(cur.px, cur.px);
+                const float2 pyy = make_float2(cur.py, cur.py);
+                if (NB == 3) {
+                    const int xs = bx + cur.ox;
+                    const int row0 = by + cur.oy;
+                    if (xs & 1)
+                        point_nb3<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, part);
+                    else
+                        point_nb3<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, part);
+                } else {
+                    const int xs = bx + 1 + cur.ox;
+                    const int row0 = by + 1 + cur.oy;
+                    if (xs & 1)
+                        point_nb1<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, part);
+                    else
+                        point_nb1<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, part);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j)
+                    acc[r][j] = __fadd2_rn(acc[r][j], part[r][j]);
+            done += rg.y - rg.x;
+            if (a.early) {
+                const float lim = a.thresh - (float)(a.n - done);
+                bool low = true;
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TC / 2; ++j)
+                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                if (__all_sync(0xffffffffu, low))
+                    alive = false;
+            }
+        }
+        // every warp is done with the window before the next copy; stop when
+        // all warps have pruned
+        if (!__syncthreads_or(alive))
+            break;
+    }
+    {
+        const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
+        const unsigned valid = __reduce_add_sync(0xffffffffu, (unsigned)(vx * vy));
+        if (lane == 0)
+            atomicAdd(a.exec, (unsigned long long)done * valid);
+    }
+    float *mk = a.map + (size_t)img * a.map_img + (size_t)kl * a.H * a.W;
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int y = y0 + r - a.oy;
+        if (y >= a.H)
+            break;
+        float *row = mk + (size_t)y * a.W;
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j) {
+            const int x = x0 + 2 * j - a.ox;
+            const float v0 = alive ? acc[r][j].x * a.inv_n : -INFINITY;
+            const float v1 = alive ? acc[r][j].y * a.inv_n : -INFINITY;
+            if (x + 1 < a.W && (a.W & 1) == 0) {
+                *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
+            } else {
+                if (x < a.W)
+                    row[x] = v0;
+                if (x + 1 < a.W)
+                    row[x + 1] = v1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
+    auto kern = score_tiled_kernel<E, NB, POL, WARPS, TC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    // prefer the largest shared-memory carve-out so window size, not the
+    // L1/shared split, limits resident CTAs
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename E, int NB, bool POL, int WARPS>
+cudaError_t launch_tc(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int tc, cudaStream_t st) {
+    return tc == 10 ? launch_t<E, NB, POL, WARPS, 10>(tm, a, grid, smem, st)
+                    : launch_t<E, NB, POL, WARPS, 6>(tm, a, grid, smem, st);
+}
+
+template <typename E>
+cudaError_t tiled_dispatch(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                           int warps, int tc, cudaStream_t st) {
+    if (warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_tc<E, 3, true, 4>(tm, a, grid, smem, tc, st)
+                       : launch_tc<E, 3, false, 4>(tm, a, grid, smem, tc, st);
+        return pol ? launch_tc<E, 1, true, 4>(tm, a, grid, smem, tc, st)
+                   : launch_tc<E, 1, false, 4>(tm, a, grid, smem, tc, st);
+    }
+    if (nbhd == 3)
+        return pol ? launch_tc<E, 3, true, 8>(tm, a, grid, smem, tc, st)
+                   : launch_tc<E, 3, false, 8>(tm, a, grid, smem, tc, st);
+    return pol ? launch_tc<E, 1, true, 8>(tm, a, grid, smem, tc, st)
+               : launch_tc<E, 1, false, 8>(tm, a, grid, smem, tc, st);
+}
+
+template <typename E, int NB, bool POL, int WARPS>
+cudaError_t launch_c(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
+    auto kern = score_chunked_kernel<E, NB, POL, WARPS, kChunkCols>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t chunked_dispatch(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                             int warps, cudaStream_t st) {
+    if (warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_c<E, 3, true, 4>(tm, a, grid, smem, st) : launch_c<E, 3, false, 4>(tm, a, grid, smem, st);
+        return pol ? launch_c<E, 1, true, 4>(tm, a, grid, smem, st) : launch_c<E, 1, false, 4>(tm, a, grid, smem, st);
+    }
+    if (nbhd == 3)
+        return pol ? launch_c<E, 3, true, 8>(tm, a, grid, smem, st) : launch_c<E, 3, false, 8>(tm, a, grid, smem, st);
+    return pol ? launch_c<E, 1, true, 8>(tm, a, grid, smem, st) : launch_c<E, 1, false, 8>(tm, a, grid, smem, st);
+}
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+cudaError_t launch_pairs_t(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int early,
+                           size_t smem, unsigned *counter, int *err, unsigned long long *exec, cudaStream_t st) {
+    auto kern = score_pairs_kernel<E, NB, POL, WARPS, TC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = std::max(1, std::min(total, sms * std::max(1, per_sm)));
+    kern<<<grid, WARPS * 32, smem, st>>>(pairs, n_pairs, total, cfg.sx, cfg.sy, cfg.tg, early, counter, err, exec);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename E, int NB, bool POL, int WARPS>
+cudaError_t launch_pairs_tc(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int early,
+                            size_t smem, unsigned *counter, int *err, unsigned long long *exec, cudaStream_t st) {
+    return cfg.tc == 10
+               ? launch_pairs_t<E, NB, POL, WARPS, 10>(pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st)
+               : launch_pairs_t<E, NB, POL, WARPS, 6>(pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st);
+}
+
+template <typename E>
+cudaError_t pairs_dispatch(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
+                           int early, size_t smem, unsigned *counter, int *err, unsigned long long *exec,
+                           cudaStream_t st) {
+#define SAM_PAIRS_ARGS pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st
+    if (cfg.warps == 4) {
+        if (nbhd == 3)
+            return pol ? launch_pairs_tc<E, 3, true, 4>(SAM_PAIRS_ARGS) : launch_pairs_tc<E, 3, false, 4>(SAM_PAIRS_ARGS);
+        return pol ? launch_pairs_tc<E, 1, true, 4>(SAM_PAIRS_ARGS) : launch_pairs_tc<E, 1, false, 4>(SAM_PAIRS_ARGS);
+    }
+    if (nbhd == 3)
+        return pol ? launch_pairs_tc<E, 3, true, 8>(SAM_PAIRS_ARGS) : launch_pairs_tc<E, 3, false, 8>(SAM_PAIRS_ARGS);
+    return pol ? launch_pairs_tc<E, 1, true, 8>(SAM_PAIRS_ARGS) : launch_pairs_tc<E, 1, false, 8>(SAM_PAIRS_ARGS);
+#undef SAM_PAIRS_ARGS
+}
+
+}  // namespace
+}  // namespace sam

@@ -76,12 +76,12 @@ SIGNATURES = {
     "sam_score_window_scratch_bytes": (ctypes.c_size_t, [ctypes.c_size_t]),
     "sam_score_window": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int,
                                   _c_int, _c_int, _c_float, _c_int, _vp, _vp, ctypes.c_size_t, _vp, _vp]),
-    "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int]),
-    "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p]),
+    "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_take_device_error": (_c_int, []),
     "sam_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams),
                               _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
-    "sam_model_tiling": (_c_int, [_vp, _c_int, _i32p, _i32p, _i32p, _i32p]),
+    "sam_model_tiling": (_c_int, [_vp, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
@@ -91,7 +91,7 @@ SIGNATURES = {
     "sam_multi_image": (ctypes.c_void_p, [_vp, _c_int, ctypes.POINTER(_c_int)]),
     "sam_multi_set_image": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _vp]),
     "sam_multi_run": (_c_int, [_vp, _vp, ctypes.POINTER(Pose), _c_int, ctypes.POINTER(_c_int)]),
-    "sam_multi_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
+    "sam_multi_set_tiling": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int]),
     "sam_multi_autotune": (_c_int, [_vp, _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
     "sam_multi_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_size_t)]),
@@ -103,6 +103,7 @@ SIGNATURES = {
     "sam_profile_enable": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
     "sam_kernel_launches": (ctypes.c_longlong, []),
+    "sam_executed_pose_points": (ctypes.c_longlong, [_c_int]),
 }
 
 STAGES = ("pyramid", "gradient", "score_map", "candidates", "refine", "nms")
@@ -318,15 +319,17 @@ def score_window(model: Model, level, field, w, h, precision, x0, y0, gw, gh, k0
            "sam_score_window")
 
 
-def set_score_kernel(kernel=0, sx=2, sy=1, tg=9, warps=8):
-    """Select the exhaustive scorer: 0 automatic, 1 generic, 2 tiled (with its tiling)."""
-    _check(lib().sam_set_score_kernel(int(kernel), int(sx), int(sy), int(tg), int(warps)), "sam_set_score_kernel")
+def set_score_kernel(kernel=0, sx=2, sy=1, tg=9, warps=8, cols=6):
+    """Select the exhaustive scorer: 0 automatic, 1 generic, 2 tiled (with its
+    tiling; tg = 0 selects the chunked kernel; cols = pose columns per thread)."""
+    _check(lib().sam_set_score_kernel(int(kernel), int(sx), int(sy), int(tg), int(warps), int(cols)),
+           "sam_set_score_kernel")
 
 
 def get_score_kernel():
-    v = [ctypes.c_int32() for _ in range(5)]
+    v = [ctypes.c_int32() for _ in range(6)]
     lib().sam_get_score_kernel(*[ctypes.byref(x) for x in v])
-    return dict(zip(("kernel", "sx", "sy", "tg", "warps"), (x.value for x in v)))
+    return dict(zip(("kernel", "sx", "sy", "tg", "warps", "cols"), (x.value for x in v)))
 
 
 def take_device_error():
@@ -356,6 +359,14 @@ def profile_read():
     return {STAGES[i]: (float(ms[i]), int(calls[i])) for i in range(n)}
 
 
+def executed_pose_points(reset=False):
+    """Pose-points the tiled scorers evaluated since the last reset (synchronises)."""
+    v = int(lib().sam_executed_pose_points(1 if reset else 0))
+    if v < 0:
+        raise SamError(SAM_ERR_CUDA, "sam_executed_pose_points")
+    return v
+
+
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(lib().sam_kernel_launches())
@@ -375,18 +386,19 @@ def autotune(model: Model, images, params: Optional[DetectParams] = None, stream
     the fastest for `model`.  Returns a list of ((sx, sy, tg, warps), ms) sorted by time."""
     params = params or default_detect_params()
     N, H, W = images.shape
-    cfg = (ctypes.c_int32 * (4 * max_out))()
+    cfg = (ctypes.c_int32 * (5 * max_out))()
     ms = (ctypes.c_float * max_out)()
     n = ctypes.c_int()
     _check(lib().sam_autotune(model.handle, _ptr(images), N, images.stride(0), W, H, images.stride(1),
                               ctypes.byref(params), _stream(stream), cfg, ms, max_out, ctypes.byref(n)),
            "sam_autotune")
-    res = [((cfg[4 * i], cfg[4 * i + 1], cfg[4 * i + 2], cfg[4 * i + 3]), float(ms[i])) for i in range(n.value)]
+    res = [(tuple(cfg[5 * i:5 * i + 5]), float(ms[i])) for i in range(n.value)]
     return sorted(res, key=lambda r: r[1])
 
 
 def model_tiling(model: Model, precision=FP32):
-    v = [ctypes.c_int32() for _ in range(4)]
+    """(sx, sy, tg, warps, cols) the model's next calls with `precision` use."""
+    v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().sam_model_tiling(model.handle, int(precision), *[ctypes.byref(x) for x in v]), "sam_model_tiling")
     return tuple(x.value for x in v)
 
@@ -439,16 +451,16 @@ class MultiPlan:
         _check(lib().sam_multi_run(self._h, _stream(stream), out, cap, nout), "sam_multi_run")
         return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(self.n_pairs)]
 
-    def set_tiling(self, sx, sy, tg, warps):
-        _check(lib().sam_multi_set_tiling(self._h, sx, sy, tg, warps), "sam_multi_set_tiling")
+    def set_tiling(self, sx, sy, tg, warps, cols=6):
+        _check(lib().sam_multi_set_tiling(self._h, sx, sy, tg, warps, cols), "sam_multi_set_tiling")
 
     def autotune(self, stream=None, max_out=256):
-        cfg = (ctypes.c_int32 * (4 * max_out))()
+        cfg = (ctypes.c_int32 * (5 * max_out))()
         ms = (ctypes.c_float * max_out)()
         n = ctypes.c_int()
         _check(lib().sam_multi_autotune(self._h, _stream(stream), cfg, ms, max_out, ctypes.byref(n)),
                "sam_multi_autotune")
-        res = [((cfg[4 * i], cfg[4 * i + 1], cfg[4 * i + 2], cfg[4 * i + 3]), float(ms[i])) for i in range(n.value)]
+        res = [(tuple(cfg[5 * i:5 * i + 5]), float(ms[i])) for i in range(n.value)]
         return sorted(res, key=lambda r: r[1])
 
     def stats(self):

@@ -65,7 +65,7 @@ def cfg2():
 
 
 @pytest.mark.parametrize("prec,dt", PRECS)
-@pytest.mark.parametrize("cfg", [(1, 1, 3, 8), (2, 2, 1, 4), (1, 2, 45, 8)])
+@pytest.mark.parametrize("cfg", [(1, 1, 3, 8), (2, 2, 1, 4), (1, 2, 45, 8), (1, 1, 3, 4, 10), (2, 1, 5, 8, 10), (2, 2, 0, 4)])
 def test_tiled_lowp_matches_generic_and_oracle(cfg2, prec, dt, cfg):
     _, _, m, top, ref = cfg2
     tiled = _map(m, 3, top, prec, dt, 2, cfg)

@@ -82,7 +82,7 @@ def test_plan_autotune_and_tilings(batch):
     res = plan.autotune()
     assert len(res) >= 8 and all(ms > 0 for _, ms in res)
     assert [_key(d) for d in plan.run()] == ref
-    for t in [(2, 2, 1, 4), (1, 1, 15, 8), (2, 1, 5, 8)]:
+    for t in [(2, 2, 1, 4), (1, 1, 15, 8), (2, 1, 5, 8), (1, 1, 3, 8, 10), (2, 2, 5, 4, 10)]:
         plan.set_tiling(*t)
         assert [_key(d) for d in plan.run()] == ref
     plan.close()

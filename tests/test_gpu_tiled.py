@@ -74,9 +74,10 @@ def test_pairs_layout_gradient_matches_pixel_layout():
 
 
 @pytest.mark.parametrize("cfg", [(2, 1, 9, 8), (1, 1, 1, 4), (3, 2, 45, 8), (1, 4, 7, 4), (2, 2, 90, 8),
+                                 (2, 1, 9, 8, 10), (1, 1, 3, 4, 10), (2, 2, 5, 8, 10), (1, 2, 45, 4, 10),
                                  (2, 2, 0, 4), (4, 1, 0, 4), (1, 4, 0, 4), (2, 4, 0, 8), (4, 2, 0, 8)])
 def test_tiled_matches_oracle_config1_top(cfg):
-    # tg = 0: the chunked kernel
+    # tg = 0: the chunked kernel; a fifth value: pose columns per thread
     tm, sc, _ = synth.config1_scene()
     m = sam.Model(tm, 30, 60, 3, 1.0)
     om = oracle.create_model(tm, 30, 60, 3, 1.0)
@@ -106,10 +107,12 @@ def test_tiled_ragged_sizes_match_generic_and_oracle(h, w):
     got = _map(m, 0, img, 2, (1, 1, 5, 4))
     gen = _map(m, 0, img, 1)
     chk = _map(m, 0, img, 2, (2, 2, 0, 4))
+    wide = _map(m, 0, img, 2, (1, 2, 3, 8, 10))
     ref = _oracle_map(om, 0, img)
     assert np.max(np.abs(got - ref)) < TOL
     assert np.max(np.abs(got - gen)) < TOL
     assert np.max(np.abs(chk - ref)) < TOL
+    assert np.max(np.abs(wide - ref)) < TOL
 
 
 def test_tiled_early_termination_exact_safe():
@@ -121,7 +124,7 @@ def test_tiled_early_termination_exact_safe():
     full = _map(m, 3, top, 2)
     assert np.max(np.abs(full - ref)) < TOL
     for ms, cfg in ((0.5, (2, 1, 9, 8)), (0.6, (2, 1, 9, 8)), (0.8, (2, 1, 9, 8)), (0.6, (2, 2, 0, 4)),
-                    (0.8, (2, 4, 0, 8))):
+                    (0.8, (2, 4, 0, 8)), (0.6, (1, 1, 3, 8, 10)), (0.8, (2, 1, 5, 4, 10))):
         got = _map(m, 3, top, 2, cfg, min_score=ms, early=1)
         pruned = np.isneginf(got)
         assert np.all(ref[pruned] < ms)
@@ -166,3 +169,20 @@ def test_autotune_picks_a_tiling_and_keeps_results():
     after = sam.detect_batch(m, batch, p)
     assert [[(d["x"], d["y"], d["k"]) for d in a] for a in after] == \
         [[(d["x"], d["y"], d["k"]) for d in b] for b in before]
+
+
+@pytest.mark.parametrize("cfg", [(2, 1, 9, 8), (1, 1, 3, 8), (2, 2, 0, 4), (1, 1, 3, 4, 10)])
+def test_executed_pose_point_counter(cfg):
+    # without early termination every pose inside the map evaluates every
+    # point: the counter equals the nominal count; with it, fewer
+    tm, sc, _, _ = synth.config2_scene()
+    m = sam.Model(tm, 30, 60, 4, 1.0)
+    top = oracle.pyramid(sc, 4)[3]
+    h, w = top.shape
+    nominal = m.num_angles(3) * h * w * m.num_points(3)
+    sam.executed_pose_points(reset=True)
+    _map(m, 3, top, 2, cfg, early=0)
+    assert sam.executed_pose_points(reset=True) == nominal
+    _map(m, 3, top, 2, cfg, min_score=0.6, early=1)
+    ex = sam.executed_pose_points(reset=True)
+    assert 0 < ex < nominal
