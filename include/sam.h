@@ -316,6 +316,17 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
  * else the default). */
 sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
                             int32_t *warps, int32_t *cols);
+/* Self-test of failure detection (the paper has no counterpart): one warp
+ * waits on an mbarrier that nothing completes, with the scorers' bounded
+ * wait limited to limit_us microseconds (1 .. 10^6; the scorers use 1 s),
+ * and reports the give-up through the device error flag as the scorers do.
+ * No copy is issued, so nothing is left in flight.  Returns SAM_ERR_TIMEOUT
+ * (the expected outcome; the flag is read and cleared) with the time the
+ * wait took in *waited_ms (may be NULL); SAM_OK would mean the wait
+ * completed.  Synchronises the device.  Errors: SAM_ERR_ARG, SAM_ERR_NOMEM,
+ * SAM_ERR_CUDA. */
+sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms);
+
 /* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
  * clears it if any wait gave up since the last call (synchronises the
  * device). */

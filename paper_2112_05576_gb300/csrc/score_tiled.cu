@@ -368,6 +368,37 @@ extern "C" long long sam_executed_pose_points(int reset) {
     return (long long)v;
 }
 
+extern "C" sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms) {
+    if (limit_us < 1 || limit_us > 1000000)
+        return SAM_ERR_ARG;
+    sam::DeviceFlags fl;
+    if (!sam::device_flags(&fl))
+        return SAM_ERR_CUDA;
+    unsigned long long *d_ns = nullptr;
+    if (cudaMalloc(&d_ns, sizeof(unsigned long long)) != cudaSuccess)
+        return SAM_ERR_NOMEM;
+    sam_status s = SAM_OK;
+    unsigned long long ns = 0;
+    int flag = 0;
+    if (sam::launch_wait_selftest(fl.err, (unsigned long long)limit_us * 1000ull, d_ns, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&flag, fl.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = SAM_ERR_CUDA;
+    cudaFree(d_ns);
+    if (s != SAM_OK)
+        return s;
+    if (waited_ms)
+        *waited_ms = (double)ns * 1e-6;
+    if (flag) {
+        static const int zero = 0;
+        if (cudaMemcpy(fl.err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        return SAM_ERR_TIMEOUT;
+    }
+    return SAM_OK;
+}
+
 extern "C" int sam_take_device_error(void) {
     if (cudaDeviceSynchronize() != cudaSuccess)
         return 1;

@@ -21,4 +21,11 @@ cudaError_t launch_pairs_f32(const PairScore *pairs, int n_pairs, int total, con
     return pairs_dispatch<float>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, counter, err, exec, st);
 }
 
+cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns,
+                                 cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(err, limit_ns, waited_ns);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace sam

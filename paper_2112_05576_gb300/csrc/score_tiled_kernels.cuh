@@ -75,9 +75,20 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Bounded wait on an mbarrier phase; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
+// Bounded wait on an mbarrier phase: true when the phase completed, false
+// after `limit_ns` nanoseconds of the global timer (1 s by default; a TMA
+// window copy takes microseconds) or 2^26 polls, whichever comes first.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = kWaitLimitNs) {
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < (1 << 26); ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -86,8 +97,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "memory");
         if (done)
             return true;
+        if (global_ns() - t0 > limit_ns)
+            return false;
     }
     return false;
+}
+
+// Self-test of the bounded wait: one warp waits on a fresh mbarrier that
+// nothing arrives at (no copy is issued), gives up after limit_ns and
+// reports it through the error flag exactly as the scorers do.
+__global__ void wait_selftest_kernel(int *err, unsigned long long limit_ns, unsigned long long *waited_ns) {
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t bar = smem_addr(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait(bar, 0, limit_ns);
+    if (threadIdx.x == 0) {
+        *waited_ns = global_ns() - t0;
+        if (!ok)
+            atomicExch(err, 1);
+    }
 }
 
 // Dot products of one pixel pair with the point direction.  FP32 storage:

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sam_set_score_kernel": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
     "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_take_device_error": (_c_int, []),
+    "sam_selftest_wait_timeout": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "sam_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams),
                               _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
     "sam_model_tiling": (_c_int, [_vp, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
@@ -334,6 +335,14 @@ def get_score_kernel():
 
 def take_device_error():
     return int(lib().sam_take_device_error())
+
+
+def selftest_wait_timeout(limit_us=2000):
+    """Run the bounded-wait self-test; returns (status, milliseconds waited).
+    The expected status is SAM_ERR_TIMEOUT."""
+    ms = ctypes.c_double()
+    s = int(lib().sam_selftest_wait_timeout(int(limit_us), ctypes.byref(ms)))
+    return s, ms.value
 
 
 def candidates_scratch_bytes(nth, gh, gw):
