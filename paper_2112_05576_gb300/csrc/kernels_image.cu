@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "image_common.cuh"
 #include "sam_internal.h"
 
 namespace sam {
@@ -217,15 +218,9 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
             gx = (a[j + 2] + 2 * b[j + 2] + c[j + 2]) - (a[j] + 2 * b[j] + c[j]);
             gy = (c[j] + 2 * c[j + 1] + c[j + 2]) - (a[j] + 2 * a[j + 1] + a[j + 2]);
         }
-        const int m2 = gx * gx + gy * gy;
-        float fx = 0.f, fy = 0.f;
-        if (m2 >= thr && m2 > 0) {
-            const float inv = rsqrtf((float)m2);
-            fx = (float)gx * inv;
-            fy = (float)gy * inv;
-        }
-        wx[j] = fx;
-        wy[j] = fy;
+        const float2 u = unit_of_gradient(gx, gy, thr);
+        wx[j] = u.x;
+        wy[j] = u.y;
         gxs[j] = gx;
         gys[j] = gy;
     }
