@@ -424,8 +424,9 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
 /* ---------------------------------------------------------------------------
  * Stage timing (tracing).  When enabled, sam_detect / sam_detect_batch record
  * CUDA events on the caller's stream before and after the launches of each
- * stage and, at the synchronisation that ends the call, add the elapsed
- * device time to per-stage totals.  Stages: 0 pyramid, 1 gradient,
+ * stage; sam_profile_read waits for the recorded events and adds their
+ * elapsed device times to per-stage totals (so an enabled profiler adds no
+ * host work between calls).  Stages: 0 pyramid, 1 gradient,
  * 2 exhaustive score map, 3 candidates, 4 refinement, 5 NMS.
  * sam_profile_read copies up to n totals (milliseconds) and call counts and
  * resets them.  Process-wide; not thread-safe.

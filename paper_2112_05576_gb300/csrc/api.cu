@@ -25,46 +25,63 @@ namespace {
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // ---- stage timing ----
+// Stage events go to a pool of event pairs; their elapsed times are summed
+// only when the totals are read (or the pool is full), so an enabled profiler
+// adds two event records per stage to a call and no host work after it.
 struct Profiler {
     bool on = false;
-    cudaEvent_t ev[SAM_NUM_STAGES][2] = {};
-    bool pending[SAM_NUM_STAGES] = {};
+    static constexpr int kPool = 4096;
+    std::vector<cudaEvent_t> ev;     // 2 per slot
+    std::vector<int> stage_of;       // stage of each recorded slot
+    int used = 0;
+    int open[SAM_NUM_STAGES] = {};   // slot of each stage's begin
     double ms[SAM_NUM_STAGES] = {};
     int calls[SAM_NUM_STAGES] = {};
 };
 Profiler g_prof;
 
+// Sum every recorded pair (waits for the last one) and empty the pool.
+void prof_flush() {
+    if (g_prof.used == 0)
+        return;
+    cudaEventSynchronize(g_prof.ev[2 * (g_prof.used - 1) + 1]);
+    for (int i = 0; i < g_prof.used; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]) == cudaSuccess) {
+            g_prof.ms[g_prof.stage_of[i]] += t;
+            g_prof.calls[g_prof.stage_of[i]] += 1;
+        }
+    }
+    g_prof.used = 0;
+}
+
 void prof_begin(int stage, cudaStream_t st) {
     if (!g_prof.on)
         return;
-    if (!g_prof.ev[stage][0]) {
-        cudaEventCreate(&g_prof.ev[stage][0]);
-        cudaEventCreate(&g_prof.ev[stage][1]);
+    if (g_prof.used == Profiler::kPool)
+        prof_flush();
+    const int slot = g_prof.used;
+    if ((int)g_prof.stage_of.size() <= slot) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+            return;
+        g_prof.ev.push_back(a);
+        g_prof.ev.push_back(b);
+        g_prof.stage_of.push_back(0);
     }
-    cudaEventRecord(g_prof.ev[stage][0], st);
+    g_prof.open[stage] = slot;
+    g_prof.stage_of[slot] = stage;
+    cudaEventRecord(g_prof.ev[2 * slot], st);
 }
 
 void prof_end(int stage, cudaStream_t st) {
     if (!g_prof.on)
         return;
-    cudaEventRecord(g_prof.ev[stage][1], st);
-    g_prof.pending[stage] = true;
-}
-
-// after the stream has been synchronised
-void prof_collect() {
-    if (!g_prof.on)
+    const int slot = g_prof.open[stage];
+    if (slot != g_prof.used || (int)g_prof.stage_of.size() <= slot)
         return;
-    for (int s = 0; s < SAM_NUM_STAGES; ++s) {
-        if (!g_prof.pending[s])
-            continue;
-        float t = 0.f;
-        if (cudaEventElapsedTime(&t, g_prof.ev[s][0], g_prof.ev[s][1]) == cudaSuccess) {
-            g_prof.ms[s] += t;
-            g_prof.calls[s] += 1;
-        }
-        g_prof.pending[s] = false;
-    }
+    cudaEventRecord(g_prof.ev[2 * slot + 1], st);
+    ++g_prof.used;
 }
 
 // Device buffers of one detection call (all images of a batch).
@@ -321,7 +338,6 @@ sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p,
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
     SAM_CU(cudaStreamSynchronize(st));
-    prof_collect();
     if (dev_err) {
         score_error_clear(st);
         cudaStreamSynchronize(st);
@@ -864,6 +880,7 @@ void sam_profile_enable(int on) { g_prof.on = on != 0; }
 long long sam_kernel_launches(void) { return g_launches.load(); }
 
 int sam_profile_read(float *ms, int *calls, int n) {
+    prof_flush();
     const int m = n < SAM_NUM_STAGES ? n : SAM_NUM_STAGES;
     for (int s = 0; s < m; ++s) {
         if (ms)
