@@ -20,7 +20,7 @@ namespace sam {
 namespace {
 
 constexpr int TR = kTileRows;        // rows of poses per thread
-constexpr int PRUNE_EVERY = 16;
+constexpr int PRUNE_EVERY = 8;
 
 
 
