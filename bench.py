@@ -519,12 +519,15 @@ def run_gpu(args):
 
     # ---- single-image latency (one detection, device-resident) ----
     one = batches[0][0].contiguous()
+    # the scorer's tiling for one image per call is tuned on its own (setup)
+    if args.autotune and not args.tiling:
+        sam.autotune(model, one[None], params)
     for _ in range(3):
         sam.detect(model, one, params)
     torch.cuda.synchronize(dev)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
-    n_single = 20
+    n_single = 50
     for _ in range(n_single):
         sam.detect(model, one, params)
     s1.record(stream)
@@ -562,7 +565,7 @@ def run_gpu(args):
                            "ms_per_detection": round(fms / B, 5),
                            "score_map_ms": round(pf["score_map"][0] / max(1, pf["score_map"][1]), 4),
                            "same_detections_as_fp32": bool(same), "steps": n_form,
-                           "tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, code)))}
+                           "tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, code, B)))}
 
     # ---- the batched uneven form: many image sizes and templates, one graph ----
     batched = run_batched(args, sam, torch, dev, stream) if (args.multi > 0 and rank == 0) else None
@@ -599,7 +602,7 @@ def run_gpu(args):
                   float(peaks.get("sm_max_mhz", 2070.0)),
                   traffic=args.traffic if args.traffic is not None else (
                       NCU_SCORE_TRAFFIC["bytes"]
-                      if tuple(sam.model_tiling(model, params.precision)) == NCU_SCORE_TRAFFIC["tiling"] else None))
+                      if tuple(sam.model_tiling(model, params.precision, B)) == NCU_SCORE_TRAFFIC["tiling"] else None))
     rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {props.multi_processor_count} SMs x 128 shared-memory "
                          f"bytes/clk; 13.33 algorithmic bytes per pose-point (8x6 translation block)")
     clocks = clk.summary()
@@ -617,7 +620,7 @@ def run_gpu(args):
     rl["nominal_pose_points_per_launch"] = int(pp_step)
     rl["nominal"] = {"achieved": rl_nom["achieved"], "frac": rl_nom["frac"],
                      "what": "nominal pose-points (early termination not subtracted) x 13.33 B / launch time"}
-    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision)))
+    rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, B)))
     rl["tiling"]["autotuned"] = bool(tuning)
     if tuning:
         rl["tiling"]["candidates"] = len(tuning)
@@ -645,6 +648,7 @@ def run_gpu(args):
                          f"~{B * (H * W * 11 // 1048576)} MB"},
         "ms_per_detection": ms / args.steps / B,
         "single_image_ms": single_ms,
+        "single_image_tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, 1))),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": int(launches),

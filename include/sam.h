@@ -304,17 +304,19 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps, in
  * per thread; tilings whose window does not fit are skipped) and the
  * chunked kernel with its CTA tiles (2x2, 4x1, 1x4 of 4 warps; 2x4, 4x2 of
  * 8 warps; reported with tg = 0) using CUDA events on `stream`, and keeps
- * the fastest for this model and this field precision (used by later calls
- * with that precision while sam_set_score_kernel selects 0, automatic).
+ * the fastest for this model, this field precision and this batch class
+ * (count 1, or more than 1; used by later calls with that precision and
+ * class -- or the other class when only that one is tuned -- while
+ * sam_set_score_kernel selects 0, automatic).
  * Optional outputs: cfg_out[5 i ..] = (sx, sy, tg, warps, cols) and
  * ms_out[i] of up to max_out candidates; *n_out = how many were written.  Uses the model's workspace; synchronises `stream`.
  * Errors: SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT. */
 sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h, int stride,
                         const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
                         int *n_out);
-/* The tiling the model's next calls with field `precision` will use (tuned,
- * else the default). */
-sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
+/* The tiling the model's next calls with field `precision` over `count`
+ * images will use (tuned, else the default). */
+sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_t *sx, int32_t *sy, int32_t *tg,
                             int32_t *warps, int32_t *cols);
 /* Self-test of failure detection (the paper has no counterpart): one warp
  * waits on an mbarrier that nothing completes, with the scorers' bounded

@@ -392,6 +392,18 @@ cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a
                               a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
 }
 
+// The model's tuned tiling for field `precision` and a call over `count`
+// images: the one tuned for that batch class (one image / several), else the
+// other class's, else none.
+const TileConfig *tuned_tiling(const sam_model *m, int precision, int count) {
+    const int cls = count > 1 ? 1 : 0;
+    if (m->tuned[precision][cls])
+        return &m->tile[precision][cls];
+    if (m->tuned[precision][1 - cls])
+        return &m->tile[precision][1 - cls];
+    return nullptr;
+}
+
 // The scorer a call uses: the model's tuned tiling (or the process-wide
 // selection), else the chunked default; false if neither serves the call.
 bool pick_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, TileConfig *out) {
@@ -399,14 +411,9 @@ bool pick_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, TileCon
     if (c.kernel == 1)
         return false;
     TileConfig cfg = c.cfg;
-    const int pr = a.precision;
-    if (m->tuned[pr] && c.kernel == 0) {
-        cfg.sx = m->tile_sx[pr];
-        cfg.sy = m->tile_sy[pr];
-        cfg.tg = m->tile_tg[pr];
-        cfg.warps = m->tile_warps[pr];
-        cfg.tc = m->tile_tc[pr];
-    }
+    const TileConfig *t = tuned_tiling(m, a.precision, a.count);
+    if (t && c.kernel == 0)
+        cfg = *t;
     if ((cfg.tg >= 1 && tiled_ok(m, level, a, cfg)) || (cfg.tg == 0 && chunked_ok(m, level, a, cfg))) {
         *out = cfg;
         return true;
@@ -711,12 +718,9 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     *n_out = std::min(n, max_out);
     if (found) {
         const int pr = params->precision;
-        m->tuned[pr] = true;
-        m->tile_sx[pr] = bestc.sx;
-        m->tile_sy[pr] = bestc.sy;
-        m->tile_tg[pr] = bestc.tg;
-        m->tile_warps[pr] = bestc.warps;
-        m->tile_tc[pr] = bestc.tc;
+        const int cls = count > 1 ? 1 : 0;
+        m->tuned[pr][cls] = true;
+        m->tile[pr][cls] = bestc;
     }
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
@@ -729,17 +733,17 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     return SAM_OK;
 }
 
-sam_status sam_model_tiling(const sam_model *m, int precision, int32_t *sx, int32_t *sy, int32_t *tg,
+sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_t *sx, int32_t *sy, int32_t *tg,
                             int32_t *warps, int32_t *cols) {
-    if (!m || !sx || !sy || !tg || !warps || !cols || precision < SAM_FP32 || precision > SAM_FP16)
+    if (!m || !sx || !sy || !tg || !warps || !cols || precision < SAM_FP32 || precision > SAM_FP16 || count < 1)
         return SAM_ERR_ARG;
-    const ScoreChoice &c = score_choice();
-    const bool t = m->tuned[precision];
-    *sx = t ? m->tile_sx[precision] : c.cfg.sx;
-    *sy = t ? m->tile_sy[precision] : c.cfg.sy;
-    *tg = t ? m->tile_tg[precision] : c.cfg.tg;
-    *warps = t ? m->tile_warps[precision] : c.cfg.warps;
-    *cols = t ? m->tile_tc[precision] : c.cfg.tc;
+    const TileConfig *t = tuned_tiling(m, precision, count);
+    const TileConfig c = t ? *t : score_choice().cfg;
+    *sx = c.sx;
+    *sy = c.sy;
+    *tg = c.tg;
+    *warps = c.warps;
+    *cols = c.tc;
     return SAM_OK;
 }
 

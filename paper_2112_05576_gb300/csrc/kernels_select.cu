@@ -15,6 +15,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "sam_internal.h"
 
 namespace sam {
@@ -22,6 +24,7 @@ namespace {
 
 constexpr int kSortCap = 2048;   // shared-memory sort buffer (entries)
 constexpr int RTHREADS = 256;
+constexpr int kRefineCluster = 4;   // CTAs per refined candidate
 
 __device__ __forceinline__ bool beats(float sa, unsigned long long ka, float sb, unsigned long long kb) {
     return sa > sb || (sa == sb && ka < kb);
@@ -190,15 +193,24 @@ struct RefineLevels {
     LevelDev L[kMaxLevels];
 };
 
+// One thread-block cluster of kRefineCluster CTAs per candidate: each CTA sums
+// its share of the model points for the 27 poses, CTA 0 adds the shares in
+// rank order through distributed shared memory, picks the level's best pose
+// and the other CTAs read it back.  Every branch that skips a cluster barrier
+// is taken by the whole cluster (same candidate, same state).
 template <int NB>
 __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
     __shared__ float red[RTHREADS / 32][27];
-    __shared__ int state[4];   // x, y, k, alive
+    __shared__ float part[27];   // this CTA's sums of the 27 poses
+    __shared__ int state[4];     // x, y, k, alive
     __shared__ float sbest;
     const int ncand = *j.count;
     float4 *outp = j.refined + c;
     if (c >= ncand) {
-        if (threadIdx.x == 0)
+        if (rank == 0 && threadIdx.x == 0)
             *outp = make_float4(__int_as_float(0), __int_as_float(0), __int_as_float(0), -INFINITY);
         return;
     }
@@ -227,7 +239,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
         for (int dk = 0; dk < 3; ++dk) {
             const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
             const RotPt *P = L.rot + (size_t)kk * L.n;
-            for (int i = threadIdx.x; i < L.n; i += RTHREADS) {
+            for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
                 const RotPt p = P[i];
                 const int bx = cx + p.ox, by = cy + p.oy;
                 constexpr int D = NB + 2;   // window of dot products
@@ -262,7 +274,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                 }
             }
         }
-        // block reduction of the 27 sums
+        // block reduction of the 27 sums into this CTA's share
 #pragma unroll
         for (int q = 0; q < 27; ++q) {
             float v = acc[q];
@@ -273,7 +285,22 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                 red[warp][q] = v;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 27) {
+            float v = 0.f;
+            for (int wv = 0; wv < RTHREADS / 32; ++wv)
+                v += red[wv][threadIdx.x];
+            part[threadIdx.x] = v;
+        }
+        cluster.sync();   // every CTA's share is in its shared memory
+        if (rank == 0 && threadIdx.x == 0) {
+            float tot[27];
+            for (int q = 0; q < 27; ++q)
+                tot[q] = 0.f;
+            for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r) {
+                const float *pr = cluster.map_shared_rank(part, r);
+                for (int q = 0; q < 27; ++q)
+                    tot[q] += pr[q];
+            }
             float bs = -INFINITY;
             unsigned long long bk = ~0ull;
             int bx = 0, by = 0, bkk = 0;
@@ -285,10 +312,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                         const int X = cx + tx - 1, Y = cy + ty - 1;
                         if (X < 0 || Y < 0 || X >= W || Y >= H)
                             continue;
-                        float sum = 0.f;
-                        for (int wv = 0; wv < RTHREADS / 32; ++wv)
-                            sum += red[wv][dk * 9 + ty * 3 + tx];
-                        const float M = sum / (float)L.n;
+                        const float M = tot[dk * 9 + ty * 3 + tx] / (float)L.n;
                         const unsigned long long key = ((unsigned long long)kk * H + Y) * W + X;
                         if (!any || beats(M, key, bs, bk)) {
                             any = true;
@@ -307,17 +331,28 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
             state[3] = any && bs >= j.min_score;
             sbest = bs;
         }
+        cluster.sync();   // CTA 0's choice is in its shared memory
+        if (rank != 0 && threadIdx.x == 0) {
+            const int *s0 = cluster.map_shared_rank(state, 0u);
+            state[0] = s0[0];
+            state[1] = s0[1];
+            state[2] = s0[2];
+            state[3] = s0[3];
+            sbest = *cluster.map_shared_rank(&sbest, 0u);
+        }
         __syncthreads();
         if (!state[3])
             break;
     }
-    if (threadIdx.x == 0)
+    cluster.sync();   // CTA 0 stays until every CTA has read its state
+    if (rank == 0 && threadIdx.x == 0)
         *outp = make_float4(__int_as_float(state[0]), __int_as_float(state[1]), __int_as_float(state[2]),
                             state[3] ? sbest : -INFINITY);
 }
 
 template <int NB>
-__global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, RefineArgs a) {
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
+    refine_kernel(RefineLevels lv, RefineArgs a) {
     const int img = blockIdx.y;
     RefineJob j;
     j.L = nullptr;
@@ -335,13 +370,14 @@ __global__ void __launch_bounds__(RTHREADS) refine_kernel(RefineLevels lv, Refin
     j.cs = a.cand_s + (size_t)img * a.K;
     j.count = a.cand_count + img;
     j.refined = a.refined + (size_t)img * a.K;
-    refine_body<NB>(j, lv.L, blockIdx.x);
+    refine_body<NB>(j, lv.L, blockIdx.x / kRefineCluster);
 }
 
 template <int NB>
-__global__ void __launch_bounds__(RTHREADS) refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
+    refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
     const RefineJob &j = jobs[blockIdx.y];
-    refine_body<NB>(j, j.L, blockIdx.x);
+    refine_body<NB>(j, j.L, blockIdx.x / kRefineCluster);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,7 +508,7 @@ cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t 
     RefineLevels lv;
     for (int l = 0; l < kMaxLevels; ++l)
         lv.L[l] = m->dev[l];
-    dim3 grid((unsigned)a.K, (unsigned)a.count);
+    dim3 grid((unsigned)(a.K * kRefineCluster), (unsigned)a.count);
     if (a.nbhd == 3)
         refine_kernel<3><<<grid, RTHREADS, 0, st>>>(lv, a);
     else
@@ -484,7 +520,7 @@ cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t 
 cudaError_t launch_refine_jobs(const RefineJob *jobs, int n_jobs, int K, int nbhd, cudaStream_t st) {
     if (n_jobs <= 0)
         return cudaSuccess;
-    dim3 grid((unsigned)K, (unsigned)n_jobs);
+    dim3 grid((unsigned)(K * kRefineCluster), (unsigned)n_jobs);
     if (nbhd == 3)
         refine_jobs_kernel<3><<<grid, RTHREADS, 0, st>>>(jobs);
     else

@@ -69,6 +69,25 @@ struct Workspace {
 
 }  // namespace sam
 
+namespace sam {
+
+// Geometry shared by the tiled scorers: a thread owns kTileRows x cols poses
+// (cols 6 or 10); FP32 pairs put kLanesXF32 lanes along x, 16-bit pairs
+// kLanesX16; the chunked kernel uses kChunkCols columns.
+constexpr int kTileRows = 8;
+constexpr int kLanesXF32 = 8;
+constexpr int kLanesX16 = 16;
+constexpr int kChunkCols = 6;
+
+struct TileConfig {
+    int sx = 2, sy = 1;   // super-tile in warp tiles (8 x tc lanes-along-x poses wide, 32 rows tall for FP32)
+    int tg = 9;           // angles per CTA (0: the chunked kernel)
+    int warps = 8;        // warps per CTA (4 or 8)
+    int tc = 6;           // pose columns per thread (6 or 10)
+};
+
+}  // namespace sam
+
 struct sam_model {
     sam_model_params p;
     int levels = 0;
@@ -79,11 +98,10 @@ struct sam_model {
     void *d_tables = nullptr;
     sam::LevelDev dev[sam::kMaxLevels];
     sam::Workspace ws;
-    // tiling chosen by sam_autotune for this model, per field precision
-    // (overrides the default)
-    bool tuned[3] = {false, false, false};
-    int tile_sx[3] = {2, 2, 2}, tile_sy[3] = {1, 1, 1}, tile_tg[3] = {9, 9, 9}, tile_warps[3] = {8, 8, 8};
-    int tile_tc[3] = {6, 6, 6};
+    // tiling chosen by sam_autotune for this model, per field precision and
+    // batch class (0: one image per call, 1: several), overriding the default
+    bool tuned[3][2] = {};
+    sam::TileConfig tile[3][2];
 };
 
 namespace sam {
@@ -143,20 +161,6 @@ struct ScoreArgs {
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
 
 // Tiled scorer (score_tiled.cu): FP32 paired field, step 1.
-// Geometry shared by the tiled scorers: a thread owns kTileRows x cols poses
-// (cols 6 or 10); FP32 pairs put kLanesXF32 lanes along x, 16-bit pairs
-// kLanesX16; the chunked kernel uses kChunkCols columns.
-constexpr int kTileRows = 8;
-constexpr int kLanesXF32 = 8;
-constexpr int kLanesX16 = 16;
-constexpr int kChunkCols = 6;
-
-struct TileConfig {
-    int sx = 2, sy = 1;   // super-tile in warp tiles (8 x tc lanes-along-x poses wide, 32 rows tall for FP32)
-    int tg = 9;           // angles per CTA (0: the chunked kernel)
-    int warps = 8;        // warps per CTA (4 or 8)
-    int tc = 6;           // pose columns per thread (6 or 10)
-};
 bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int tc, int *bxw, int *byw);
 // Whether a level's rotated extent needs the chunked scorer (its whole-angle
 // window does not fit shared memory at the smallest tiling).

@@ -82,7 +82,7 @@ SIGNATURES = {
     "sam_selftest_wait_timeout": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "sam_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams),
                               _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
-    "sam_model_tiling": (_c_int, [_vp, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "sam_model_tiling": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
@@ -405,10 +405,12 @@ def autotune(model: Model, images, params: Optional[DetectParams] = None, stream
     return sorted(res, key=lambda r: r[1])
 
 
-def model_tiling(model: Model, precision=FP32):
-    """(sx, sy, tg, warps, cols) the model's next calls with `precision` use."""
+def model_tiling(model: Model, precision=FP32, count=2):
+    """(sx, sy, tg, warps, cols) the model's next calls with `precision` over
+    `count` images use (count 1: the single-image class)."""
     v = [ctypes.c_int32() for _ in range(5)]
-    _check(lib().sam_model_tiling(model.handle, int(precision), *[ctypes.byref(x) for x in v]), "sam_model_tiling")
+    _check(lib().sam_model_tiling(model.handle, int(precision), int(count), *[ctypes.byref(x) for x in v]),
+           "sam_model_tiling")
     return tuple(x.value for x in v)
 
 
