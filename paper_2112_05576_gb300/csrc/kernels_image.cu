@@ -196,6 +196,57 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
     const int tx = (tid - ty * (GTX / GPT)) * GPT;
     const int y = y0 + ty;
     const int xb = x0 + tx;
+    // FP32 pixel-layout fields of whole rows (the large fields of the lower
+    // levels) are written through a per-warp staging buffer so that every
+    // store instruction covers 512 contiguous bytes: a warp owns two rows of
+    // the tile, 1 KB of output each, whose 16-byte slots are written to
+    // shared memory in thread order and read back in address order (slot s
+    // kept at column (s mod 8) xor (s div 8 mod 8) of its 8-slot row, which
+    // keeps both accesses free of bank conflicts)
+    if (PREC == SAM_FP32 && LAYOUT == SAM_LAYOUT_PIXEL && vec && !ogx && (w & 7) == 0) {
+        const bool rows_full = __all_sync(0xffffffffu, y < h && x0 + GTX <= w);
+        if (rows_full) {
+            __shared__ __align__(16) float4 stage[GTHREADS / 32][128];
+            const int lane = tid & 31;
+            float4 *S = stage[tid >> 5];
+            const int r = ty + 1, cb = tx + 16;
+            int a[GPT + 2], b[GPT + 2], c[GPT + 2];
+#pragma unroll
+            for (int j = 0; j < GPT + 2; ++j) {
+                a[j] = tile[r - 1][cb - 1 + j];
+                b[j] = tile[r][cb - 1 + j];
+                c[j] = tile[r + 1][cb - 1 + j];
+            }
+            const int thr = 16 * low * low;
+#pragma unroll
+            for (int q = 0; q < GPT / 2; ++q) {
+                float2 u[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = 2 * q + e, x = xb + j;
+                    int gx = 0, gy = 0;
+                    if (x > 0 && x < w - 1 && y > 0 && y < h - 1) {
+                        gx = (a[j + 2] + 2 * b[j + 2] + c[j + 2]) - (a[j] + 2 * b[j] + c[j]);
+                        gy = (c[j] + 2 * c[j + 1] + c[j + 2]) - (a[j] + 2 * a[j + 1] + a[j + 2]);
+                    }
+                    u[e] = unit_of_gradient(gx, gy, thr);
+                }
+                const int sl = 4 * lane + q;
+                S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))] = make_float4(u[0].x, u[0].y, u[1].x, u[1].y);
+            }
+            __syncwarp();
+            // slots 0..63: the warp's first row, 64..127: its second row
+            const int yw = y0 + (ty & ~1);
+            float4 *out = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(field) + fbase + (size_t)yw * w + x0);
+            const size_t rowf4 = (size_t)w / 2;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int sl = 32 * i + lane;
+                out[(size_t)(sl >> 6) * rowf4 + (sl & 63)] = S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))];
+            }
+            return;
+        }
+    }
     if (y >= h || xb >= w)
         return;
     const int r = ty + 1;      // centre row in tile
