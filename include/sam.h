@@ -435,6 +435,17 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
  * ------------------------------------------------------------------------- */
 #define SAM_NUM_STAGES 6
 void sam_profile_enable(int on);
+
+/* Graph mode (process-wide, on by default; the paper has no counterpart).
+ * While it is on and stage timing is off, sam_detect and sam_detect_batch
+ * copy the call's images into the model's workspace (one device-to-device
+ * or host-to-device copy on `stream`) and replay the whole pipeline --
+ * pyramid, gradients, exhaustive score, candidates, refinement, NMS -- as
+ * one CUDA graph captured on the model's first call of that shape (image
+ * size, batch count, detection parameters), re-captured when the shape, the
+ * workspace or the scorer's tiling changes.  Results are identical to the
+ * direct path, which runs while graph mode is off or stage timing is on. */
+void sam_set_graph_mode(int on);
 int sam_profile_read(float *ms, int *calls, int n);
 
 /* Pose-points the tiled and chunked exhaustive scorers have evaluated on the

@@ -326,6 +326,82 @@ sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pi
     return s != SAM_OK ? s : run_search(m, P, p, st);
 }
 
+// ---- graph mode ----
+// Changes of the scorer's tiling (sam_set_score_kernel, sam_autotune) bump
+// the epoch, which invalidates every captured pipeline.
+std::atomic<unsigned> g_tiling_epoch{1};
+std::atomic<bool> g_graph_mode{true};
+
+void drop_graph(sam_model *m) {
+    if (m->gc.exec)
+        cudaGraphExecDestroy(m->gc.exec);
+    m->gc.exec = nullptr;
+    m->gc.valid = false;
+}
+
+bool same_params(const sam_detect_params &a, const sam_detect_params &b) {
+    return a.step_x == b.step_x && a.step_y == b.step_y && a.neighbourhood == b.neighbourhood &&
+           a.min_score == b.min_score && a.max_detections == b.max_detections && a.top_k == b.top_k &&
+           a.precision == b.precision && a.early_termination == b.early_termination;
+}
+
+// The whole pipeline of a plan whose level-0 images are in the workspace,
+// replayed from a captured graph on `st` (captured first if the cached one
+// does not match the call).
+sam_status run_graph(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st) {
+    GraphCache &g = m->gc;
+    int dev = 0;
+    SAM_CU(cudaGetDevice(&dev));
+    const unsigned epoch = g_tiling_epoch.load();
+    if (!(g.valid && g.w == P.w[0] && g.h == P.h[0] && g.count == P.count && g.device == dev && g.epoch == epoch &&
+          g.ws_base == m->ws.base && g.ws_bytes == m->ws.bytes && same_params(g.p, p))) {
+        drop_graph(m);
+        if (g.cap && g.device != dev) {
+            cudaStreamDestroy(g.cap);
+            g.cap = nullptr;
+        }
+        if (!g.cap)
+            SAM_CU(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        g.device = dev;
+        SAM_CU(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeRelaxed));
+        const char *ws = (const char *)m->ws.base;
+        const long long before = sam_kernel_launches();
+        const sam_status s = run_pipeline(m, P, (const uint8_t *)(ws + P.off_img[0]), P.pitch[0], P.img_bytes[0], p,
+                                          g.cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
+        // the capture counted its launches; replays are counted below
+        const long long kernels = sam_kernel_launches() - before;
+        count_launches(-(int)kernels);
+        if (s != SAM_OK || e != cudaSuccess || !graph) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != SAM_OK ? s : SAM_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            g.exec = nullptr;
+            return SAM_ERR_CUDA;
+        }
+        g.valid = true;
+        g.w = P.w[0];
+        g.h = P.h[0];
+        g.count = P.count;
+        g.p = p;
+        g.epoch = epoch;
+        g.ws_base = m->ws.base;
+        g.ws_bytes = m->ws.bytes;
+        g.kernels = kernels;
+    }
+    SAM_CU(cudaGraphLaunch(g.exec, st));
+    count_launches((int)g.kernels);
+    return SAM_OK;
+}
+
+bool graph_path() { return g_graph_mode.load() && !g_prof.on; }
+
 sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st, sam_pose *out,
                         int capacity, int *n_out) {
     char *ws = (char *)m->ws.base;
@@ -506,6 +582,10 @@ sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const
 void sam_free_model(sam_model *m) {
     if (!m)
         return;
+    if (m->gc.exec)
+        cudaGraphExecDestroy(m->gc.exec);
+    if (m->gc.cap)
+        cudaStreamDestroy(m->gc.cap);
     if (m->d_tables)
         cudaFree(m->d_tables);
     if (m->ws.base)
@@ -581,11 +661,21 @@ sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride
     s = upload_model(m);
     if (s != SAM_OK)
         return s;
-    const Plan P = make_plan(m, w, h, 1, !img_on_device, *params);
+    const bool graph = graph_path();
+    const Plan P = make_plan(m, w, h, 1, graph || !img_on_device, *params);
     s = ensure_workspace(m, P.total);
     if (s != SAM_OK)
         return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if (graph) {
+        uint8_t *dst = (uint8_t *)m->ws.base + P.off_img[0];
+        SAM_CU(cudaMemcpy2DAsync(dst, P.pitch[0], img, stride, w, h,
+                                 img_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        s = run_graph(m, P, *params, st);
+        if (s != SAM_OK)
+            return s;
+        return read_results(m, P, *params, st, out, capacity, n_out);
+    }
     const uint8_t *img0 = img;
     int pitch0 = stride;
     size_t bytes0 = 0;
@@ -615,11 +705,28 @@ sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t 
     s = upload_model(m);
     if (s != SAM_OK)
         return s;
-    const Plan P = make_plan(m, w, h, count, false, *params);
+    const bool graph = graph_path();
+    const Plan P = make_plan(m, w, h, count, graph, *params);
     s = ensure_workspace(m, P.total);
     if (s != SAM_OK)
         return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if (graph) {
+        // the batch into the workspace's level-0 images, then the captured pipeline
+        uint8_t *dst = (uint8_t *)m->ws.base + P.off_img[0];
+        if (image_bytes == (size_t)stride * h && P.img_bytes[0] == (size_t)P.pitch[0] * h) {
+            SAM_CU(cudaMemcpy2DAsync(dst, P.pitch[0], img, stride, w, (size_t)h * count, cudaMemcpyDeviceToDevice,
+                                     st));
+        } else {
+            for (int i = 0; i < count; ++i)
+                SAM_CU(cudaMemcpy2DAsync(dst + (size_t)i * P.img_bytes[0], P.pitch[0], img + (size_t)i * image_bytes,
+                                         stride, w, h, cudaMemcpyDeviceToDevice, st));
+        }
+        s = run_graph(m, P, *params, st);
+        if (s != SAM_OK)
+            return s;
+        return read_results(m, P, *params, st, out, capacity, n_out);
+    }
     s = run_pipeline(m, P, img, stride, image_bytes, *params, st);
     if (s != SAM_OK)
         return s;
@@ -721,6 +828,7 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
         const int cls = count > 1 ? 1 : 0;
         m->tuned[pr][cls] = true;
         m->tile[pr][cls] = bestc;
+        ++g_tiling_epoch;
     }
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
@@ -852,6 +960,7 @@ sam_status sam_set_score_kernel(int kernel, int sx, int sy, int tg, int warps, i
         (tg == 0 && cols != kChunkCols))
         return SAM_ERR_ARG;
     ScoreChoice &c = score_choice();
+    ++g_tiling_epoch;
     c.kernel = kernel;
     c.cfg.sx = sx;
     c.cfg.sy = sy;
@@ -880,6 +989,8 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps, in
 size_t sam_candidates_scratch_bytes(int nth, int gh, int gw) { return candidates_scratch_bytes(nth, gh, gw); }
 
 void sam_profile_enable(int on) { g_prof.on = on != 0; }
+
+void sam_set_graph_mode(int on) { g_graph_mode = on != 0; }
 
 long long sam_kernel_launches(void) { return g_launches.load(); }
 

@@ -88,6 +88,23 @@ struct TileConfig {
 
 }  // namespace sam
 
+namespace sam {
+// A captured detection pipeline (sam_detect / sam_detect_batch on device
+// buffers): replayed while the call's shape, parameters, workspace and
+// scorer tiling are unchanged.
+struct GraphCache {
+    bool valid = false;
+    int w = 0, h = 0, count = 0, device = -1;
+    sam_detect_params p{};
+    unsigned epoch = 0;
+    void *ws_base = nullptr;
+    size_t ws_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;   // private stream the pipeline is captured on
+    long long kernels = 0;
+};
+}  // namespace sam
+
 struct sam_model {
     sam_model_params p;
     int levels = 0;
@@ -102,6 +119,7 @@ struct sam_model {
     // batch class (0: one image per call, 1: several), overriding the default
     bool tuned[3][2] = {};
     sam::TileConfig tile[3][2];
+    sam::GraphCache gc;
 };
 
 namespace sam {

@@ -102,6 +102,7 @@ SIGNATURES = {
                                             _vp, _vp]),
     "sam_refine_poses": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
     "sam_profile_enable": (None, [_c_int]),
+    "sam_set_graph_mode": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
     "sam_kernel_launches": (ctypes.c_longlong, []),
     "sam_executed_pose_points": (ctypes.c_longlong, [_c_int]),
@@ -353,6 +354,11 @@ def candidates(smap, min_score, K, out_kyx, out_s, count, scratch, stream=None):
     nth, gh, gw = smap.shape
     _check(lib().sam_candidates(_ptr(smap), nth, gh, gw, float(min_score), int(K), _ptr(out_kyx), _ptr(out_s),
                                 _ptr(count), _ptr(scratch), _stream(stream)), "sam_candidates")
+
+
+def set_graph_mode(on=True):
+    """Replay the detection pipeline as a captured CUDA graph (default on)."""
+    lib().sam_set_graph_mode(1 if on else 0)
 
 
 def profile_enable(on=True):
