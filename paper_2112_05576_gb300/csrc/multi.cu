@@ -68,6 +68,7 @@ struct sam_multi {
     int max_w0 = 0, max_h0 = 0, Lmax = 1;
     int total_items = 0;
     size_t window_bytes = 0;
+    size_t bitmap_bytes = 0;           // edge bitmaps of the largest window
     size_t max_map = 0;
     long long pose_points = 0;
     bool dirty = true;                 // descriptors / graph must be rebuilt
@@ -93,6 +94,7 @@ bool plan_tiling(sam_multi *mp) {
     int wty = 0;
     const int wtx = tiled_warp_tile(mp->p.precision, mp->cfg.tc, &wty);
     mp->window_bytes = 0;
+    mp->bitmap_bytes = 0;
     const size_t pair_bytes = mp->p.precision == SAM_FP32 ? 16 : 8;
     for (PairPlan &q : mp->pp) {
         const LevelHost &L = mp->models[q.model]->lv[q.top];
@@ -104,6 +106,7 @@ bool plan_tiling(sam_multi *mp) {
         q.items = q.tiles * ((q.nth + mp->cfg.tg - 1) / mp->cfg.tg);
         q.cost = (double)q.items * mp->cfg.tg * mp->cfg.sx * mp->cfg.sy * q.n;
         mp->window_bytes = std::max(mp->window_bytes, (size_t)q.bxw * q.byw * pair_bytes / 2);
+        mp->bitmap_bytes = std::max(mp->bitmap_bytes, edge_bitmap_bytes(q.bxw, q.byw));
     }
     mp->order.resize(mp->pp.size());
     std::iota(mp->order.begin(), mp->order.end(), 0);
@@ -192,6 +195,7 @@ sam_status upload_descriptors(sam_multi *mp) {
         s.byw = q.byw;
         s.inv_n = 1.0f / (float)q.n;
         s.thresh = prune_threshold(q.n, mp->p.min_score, mp->p.precision);
+        s.emin = mp->p.early_termination ? edge_count_threshold(s.thresh, mp->p.precision) : 0;
         s.item_begin = item;
         item += q.items;
         put(mp->off_pairs + (size_t)r * sizeof(PairScore), &s, sizeof(s));
@@ -288,7 +292,7 @@ sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
                                mp->models[0]->p.low, mp->p.precision, SAM_LAYOUT_PAIRS, st));
     MU_CU(launch_score_pairs((const PairScore *)(base + mp->off_pairs), np, mp->total_items, mp->p.precision,
                              mp->p.neighbourhood, mp->models[0]->p.polarity, mp->p.early_termination, mp->cfg,
-                             mp->window_bytes, (unsigned *)(base + mp->off_counters), st));
+                             mp->window_bytes, mp->bitmap_bytes, (unsigned *)(base + mp->off_counters), st));
     if (mp->p.precision != SAM_FP32)
         MU_CU(launch_rescore_jobs((const RescoreJob *)(base + mp->off_rsjobs), np, mp->max_map, mp->p.neighbourhood,
                                   mp->models[0]->p.polarity, mp->p.min_score, mp->p.precision, st));
@@ -672,7 +676,7 @@ sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, flo
                         e = launch_score_pairs((const PairScore *)(base + mp->off_pairs), (int)mp->pp.size(),
                                                mp->total_items, mp->p.precision, mp->p.neighbourhood,
                                                mp->models[0]->p.polarity, mp->p.early_termination, mp->cfg,
-                                               mp->window_bytes, (unsigned *)(base + mp->off_counters), st);
+                                               mp->window_bytes, mp->bitmap_bytes, (unsigned *)(base + mp->off_counters), st);
                         cudaEventRecord(e1, st);
                         if (e == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
                             cudaEventElapsedTime(&ms, e0, e1);   // second repetition counts

@@ -213,6 +213,7 @@ struct TiledArgs {
     float inv_n;
     float thresh;
     int early;
+    int emin;                   // edge-presence bound: fewest edge windows a surviving pose needs
     int *err;                   // device error flag (bounded waits)
     unsigned long long *exec;   // executed pose-point counter
 };
@@ -244,7 +245,7 @@ struct PairScore;
     cudaError_t launch_chunked_##suf(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd,   \
                                      bool pol, int warps, cudaStream_t st);                                         \
     cudaError_t launch_pairs_##suf(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, \
-                                   bool pol, int early, size_t smem, unsigned *counter, int *err,                   \
+                                   bool pol, int early, size_t smem, size_t win_bytes, unsigned *counter, int *err, \
                                    unsigned long long *exec, cudaStream_t st);
 cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns,
                                  cudaStream_t st);
@@ -270,13 +271,18 @@ struct PairScore {
     int bxw, byw;       // the pair's window box
     float inv_n, thresh;
     int item_begin;     // first work unit of this pair (units: tiles x angle groups)
-    int pad;
+    int emin;           // edge-presence bound (as TiledArgs::emin)
 };
 bool encode_pair_tmap(void *out, const void *field, int precision, int wp, int H, int bxw, int byw);
 int tiled_warp_tile(int precision, int tc, int *wty);
 cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_items, int precision, int nbhd,
-                               int polarity, int early, const TileConfig &cfg, size_t window_bytes, unsigned *counter,
-                               cudaStream_t st);
+                               int polarity, int early, const TileConfig &cfg, size_t window_bytes,
+                               size_t bitmap_bytes, unsigned *counter, cudaStream_t st);
+// Shared memory of the edge bitmaps the tiled scorers build over a window of
+// bxw x byw pixels (edge pixels and their 3x3 dilation, one bit per pixel,
+// rows padded by 3 words for the funnel shifts of the bound pass).
+__host__ __device__ inline int edge_bitmap_words(int bxw) { return (bxw + 31) / 32 + 3; }
+__host__ __device__ inline size_t edge_bitmap_bytes(int bxw, int byw) { return 2 * (size_t)byw * edge_bitmap_words(bxw) * 4; }
 
 // Score-kernel selection (process-wide; sam_set_score_kernel).
 struct ScoreChoice {

@@ -1,6 +1,8 @@
 // Helpers shared by the scoring kernels.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -52,6 +54,17 @@ inline float term_eps(int precision) {
 // margin = 1e-3 + n * eps_term; returns the right-hand side.
 inline float prune_threshold(int n, float min_score, int precision) {
     return (float)n * min_score - (1e-3f + (float)n * term_eps(precision));
+}
+
+// Edge-presence bound: a point's vote is 0 unless its 3x3 window holds an
+// edge pixel, and at most 1 + eps_term otherwise, so a pose whose count E of
+// such points satisfies E (1 + eps_term) < thresh is below min_score.  The
+// smallest E that can survive, less one for safety (0: never prunes).
+inline int edge_count_threshold(float thresh, int precision) {
+    if (!(thresh > 0.f))
+        return 0;
+    const double t = std::ceil((double)thresh / (1.0 + (double)term_eps(precision))) - 1.0;
+    return t > 0.0 ? (int)t : 0;
 }
 
 }  // namespace sam

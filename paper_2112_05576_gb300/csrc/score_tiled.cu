@@ -142,7 +142,7 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int t
     const int by = sy * g.wty + spy + 2;
     *bxw = bx;
     *byw = by;
-    const size_t bytes = (size_t)bx * by * g.pair_bytes / 2;
+    const size_t bytes = (((size_t)bx * by * g.pair_bytes / 2 + 15) & ~(size_t)15) + edge_bitmap_bytes(bx, by);
     return bx * g.pair_bytes / 16 <= 256 && by <= 256 && bytes <= 200 * 1024;
 }
 
@@ -198,11 +198,13 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.inv_n = 1.0f / (float)L.n;
     a.thresh = prune_threshold(L.n, min_score, precision);
     a.early = early;
+    a.emin = early ? edge_count_threshold(a.thresh, precision) : 0;
     a.err = fl.err;
     a.exec = fl.exec;
     const int groups = (pw.nk + cfg.tg - 1) / cfg.tg;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)groups, (unsigned)count);
-    const size_t smem = (size_t)bxw * byw * g.pair_bytes / 2 + 128;
+    const size_t smem =
+        (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) + edge_bitmap_bytes(bxw, byw) + 128;
     const bool pol = polarity != 0;
     switch (precision) {
     case SAM_FP32:
@@ -324,23 +326,25 @@ int tiled_warp_tile(int precision, int tc, int *wty) {
 }
 
 cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_items, int precision, int nbhd,
-                               int polarity, int early, const TileConfig &cfg, size_t window_bytes, unsigned *counter,
-                               cudaStream_t st) {
+                               int polarity, int early, const TileConfig &cfg, size_t window_bytes,
+                               size_t bitmap_bytes, unsigned *counter, cudaStream_t st) {
     if (total_items <= 0 || n_pairs <= 0)
         return cudaSuccess;
-    const size_t smem = window_bytes + 128;
+    const size_t smem = ((window_bytes + 15) & ~(size_t)15) + bitmap_bytes + 128;
     const bool pol = polarity != 0;
     DeviceFlags fl;
     if (!device_flags(&fl))
         return cudaErrorUnknown;
     switch (precision) {
     case SAM_FP32:
-        return launch_pairs_f32(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, fl.err, fl.exec, st);
+        return launch_pairs_f32(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, window_bytes, counter,
+                                fl.err, fl.exec, st);
     case SAM_FP16:
-        return launch_pairs_f16(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, fl.err, fl.exec, st);
+        return launch_pairs_f16(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, window_bytes, counter,
+                                fl.err, fl.exec, st);
     default:
-        return launch_pairs_bf16(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, counter, fl.err, fl.exec,
-                                 st);
+        return launch_pairs_bf16(pairs, n_pairs, total_items, cfg, nbhd, pol, early, smem, window_bytes, counter,
+                                 fl.err, fl.exec, st);
     }
 }
 

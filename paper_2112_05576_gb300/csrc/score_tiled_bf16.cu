@@ -16,9 +16,10 @@ cudaError_t launch_chunked_bf16(const CUtensorMap &tm, const ChunkArgs &a, dim3 
 }
 
 cudaError_t launch_pairs_bf16(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
-                           int early, size_t smem, unsigned *counter, int *err, unsigned long long *exec,
-                           cudaStream_t st) {
-    return pairs_dispatch<__nv_bfloat16>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, counter, err, exec, st);
+                           int early, size_t smem, size_t win_bytes, unsigned *counter, int *err,
+                           unsigned long long *exec, cudaStream_t st) {
+    return pairs_dispatch<__nv_bfloat16>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, win_bytes, counter, err, exec,
+                             st);
 }
 
 }  // namespace sam

@@ -16,9 +16,10 @@ cudaError_t launch_chunked_f32(const CUtensorMap &tm, const ChunkArgs &a, dim3 g
 }
 
 cudaError_t launch_pairs_f32(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
-                           int early, size_t smem, unsigned *counter, int *err, unsigned long long *exec,
-                           cudaStream_t st) {
-    return pairs_dispatch<float>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, counter, err, exec, st);
+                           int early, size_t smem, size_t win_bytes, unsigned *counter, int *err,
+                           unsigned long long *exec, cudaStream_t st) {
+    return pairs_dispatch<float>(pairs, n_pairs, total, cfg, nbhd, pol, early, smem, win_bytes, counter, err, exec,
+                             st);
 }
 
 cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns,

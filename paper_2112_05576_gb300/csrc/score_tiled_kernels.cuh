@@ -246,7 +246,52 @@ struct TileWork {
     float inv_n, thresh;
     int early, sx, sy;
     unsigned long long *exec;   // executed pose-point counter
+    int emin;                   // edge-presence bound (0: off)
+    int byw;                    // window rows
+    uint32_t *bits;             // 2 edge bitmaps of the window (edge_bitmap_bytes)
 };
+
+// Edge bitmaps of a staged window (all threads of the CTA; ends with a CTA
+// barrier): E[r][x] = pixel x of window row r is an edge pixel (non-zero unit
+// vector), then D = E dilated by 3x3, so D at a point's projected centre is
+// set iff its neighbouring-search window holds an edge pixel.
+template <typename E, int NTHREADS>
+__device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *win, int pp, int byw, uint32_t *ebits,
+                                                uint32_t *dbits) {
+    const int dmw = edge_bitmap_words(2 * pp), nw = (2 * pp + 31) / 32;
+    for (int idx = threadIdx.x; idx < byw * dmw; idx += NTHREADS) {
+        const int r = idx / dmw, wi = idx - r * dmw;
+        uint32_t e = 0;
+        if (wi < nw) {
+            const typename Pairs<E>::Raw *row = win + (size_t)r * pp;
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+                const int pq = wi * 16 + q;
+                if (pq < pp) {
+                    const float4 v = Pairs<E>::get(row, pq);
+                    e |= (uint32_t)(v.x != 0.f || v.z != 0.f) << (2 * q);
+                    e |= (uint32_t)(v.y != 0.f || v.w != 0.f) << (2 * q + 1);
+                }
+            }
+        }
+        ebits[idx] = e;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < byw * dmw; idx += NTHREADS) {
+        const int r = idx / dmw, wi = idx - r * dmw;
+        uint32_t d = 0;
+        for (int dr = -1; dr <= 1; ++dr) {
+            const int rr = r + dr;
+            if (rr < 0 || rr >= byw)
+                continue;
+            const uint32_t *er = ebits + (size_t)rr * dmw;
+            const uint32_t c = er[wi], lw = wi > 0 ? er[wi - 1] : 0u, rw = wi + 1 < dmw ? er[wi + 1] : 0u;
+            d |= c | (c << 1) | (lw >> 31) | (c >> 1) | (rw << 31);
+        }
+        dbits[idx] = d;
+    }
+    __syncthreads();
+}
 
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
@@ -321,6 +366,11 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     t.sx = a.sx;
     t.sy = a.sy;
     t.exec = a.exec;
+    t.emin = a.emin;
+    t.byw = a.byw;
+    // the edge bitmaps follow the window (16-byte aligned)
+    t.bits = reinterpret_cast<uint32_t *>(smem_raw + pad +
+                                          (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15));
     score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], stx0, sty0, k_begin, k_end, t);
 }
 
@@ -335,6 +385,12 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
     const int lx = lane % LX, ly = lane / LX;
     const int items = (k_end - k_begin) * a.sx * a.sy;
     float *map = a.map;
+    // edge-presence bound (with early termination; needs the counts in 16 bit planes)
+    const bool bound = a.early && a.emin > 0 && a.n < 65536;
+    const int dmw = edge_bitmap_words(2 * pp);
+    const uint32_t *dbits = a.bits + (size_t)a.byw * dmw;
+    if (bound)
+        build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
 
     for (int it = warp; it < items; it += WARPS) {
         const int k = k_begin + it / (a.sx * a.sy);
@@ -353,14 +409,98 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         const RotPt *P = a.rot + (size_t)k * a.n;
         bool pruned = false;
         int done = a.n;
+        // Bound pass: lane L counts, for the BW poses of one pose row it owns,
+        // how many points have an edge pixel in their window (bit-sliced
+        // counters, one bit per pose), then marks the poses whose count can
+        // still reach min_score.  A thread whose 8 x TC block has no such
+        // pose skips the dot products; a warp tile with none writes -inf.
+        bool active = true;
+        if (bound) {
+            constexpr int LPR = 32 / WTY;       // lanes per pose row
+            constexpr int BW = WTX / LPR;       // poses per lane (8 TC <= 80)
+            const int xseg = stx0 + (wt % a.sx) * WTX + (lane % LPR) * BW;
+            const int yrow = sty0 + (wt / a.sx) * WTY + lane / LPR;
+            uint32_t pl[16][3];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                pl[q][0] = pl[q][1] = pl[q][2] = 0u;
+            for (int i = 0; i < a.n; ++i) {
+                const RotPt q = P[i];
+                const int b = xseg + q.ox - wx0;   // window column of the first pose's centre
+                const uint32_t *row = dbits + (size_t)(yrow + q.oy - wy0) * dmw + (b >> 5);
+                const int sh = b & 31;
+                const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+                uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
+                         m2 = __funnelshift_r(w2, w3, sh);
+                if (BW <= 64) {
+                    m1 &= BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u);
+                    m2 = 0u;
+                } else {
+                    m2 &= (1u << (BW - 64)) - 1u;
+                }
+#pragma unroll
+                for (int pq = 0; pq < 16; ++pq) {
+                    if ((m0 | m1 | m2) == 0u)
+                        break;
+                    const uint32_t c0 = pl[pq][0] & m0, c1 = pl[pq][1] & m1, c2 = pl[pq][2] & m2;
+                    pl[pq][0] ^= m0;
+                    pl[pq][1] ^= m1;
+                    pl[pq][2] ^= m2;
+                    m0 = c0;
+                    m1 = c1;
+                    m2 = c2;
+                }
+            }
+            // counts >= emin, bit-serially from the top plane
+            uint32_t gt0 = 0u, gt1 = 0u, gt2 = 0u, eq0 = ~0u, eq1 = ~0u, eq2 = ~0u;
+#pragma unroll
+            for (int pq = 15; pq >= 0; --pq) {
+                if ((a.emin >> pq) & 1) {
+                    eq0 &= pl[pq][0];
+                    eq1 &= pl[pq][1];
+                    eq2 &= pl[pq][2];
+                } else {
+                    gt0 |= eq0 & pl[pq][0];
+                    gt1 |= eq1 & pl[pq][1];
+                    gt2 |= eq2 & pl[pq][2];
+                    eq0 &= ~pl[pq][0];
+                    eq1 &= ~pl[pq][1];
+                    eq2 &= ~pl[pq][2];
+                }
+            }
+            const uint32_t o0 = gt0 | eq0;
+            const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u));
+            const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << (BW - 64)) - 1u)) : 0u;
+            if (!__any_sync(0xffffffffu, (o0 | o1 | o2) != 0u)) {
+                active = false;
+                pruned = true;
+                done = 0;
+            } else {
+                // this thread's 8 x TC block: rows ly*TR .., columns lx*TC ..
+                const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
+                uint32_t act = 0u;
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                    const int src = (ly * TR + r) * LPR + seg;
+                    const uint32_t v0 = __shfl_sync(0xffffffffu, o0, src);
+                    const uint32_t v1 = __shfl_sync(0xffffffffu, o1, src);
+                    const uint32_t v2 = __shfl_sync(0xffffffffu, o2, src);
+                    const uint32_t lo = c0 < 32 ? v0 : (c0 < 64 ? v1 : v2);
+                    const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
+                    act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
+                }
+                active = act != 0u;
+            }
+        }
         RotPt p = P[0];
-        for (int i = 0; i < a.n; ++i) {
+        for (int i = 0; i < (pruned ? 0 : a.n); ++i) {
             const RotPt cur = p;
             if (i + 1 < a.n)
                 p = P[i + 1];
             const float2 pxx = make_float2(cur.px, cur.px);
             const float2 pyy = make_float2(cur.py, cur.py);
-            if (NB == 3) {
+            if (!active) {
+            } else if (NB == 3) {
                 const int xs = bx + cur.ox;   // first pixel column (>= 0)
                 const int row0 = by + cur.oy;
                 if (xs & 1)
@@ -378,11 +518,13 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             if (a.early && ((i + 1) % PRUNE_EVERY) == 0) {
                 const float lim = a.thresh - (float)(a.n - 1 - i);
                 bool low = true;
+                if (active) {
 #pragma unroll
-                for (int r = 0; r < TR; ++r)
+                    for (int r = 0; r < TR; ++r)
 #pragma unroll
-                    for (int j = 0; j < TC / 2; ++j)
-                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                        for (int j = 0; j < TC / 2; ++j)
+                            low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                }
                 if (__all_sync(0xffffffffu, low)) {
                     pruned = true;
                     done = i + 1;
@@ -393,7 +535,7 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         {
             // poses of this thread's block that lie inside the map
             const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
-            const unsigned valid = __reduce_add_sync(0xffffffffu, (unsigned)(vx * vy));
+            const unsigned valid = __reduce_add_sync(0xffffffffu, active ? (unsigned)(vx * vy) : 0u);
             if (lane == 0)
                 atomicAdd(a.exec, (unsigned long long)done * valid);
         }
@@ -408,8 +550,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
 #pragma unroll
             for (int j = 0; j < TC / 2; ++j) {
                 const int x = x0 + 2 * j - a.ox;
-                const float v0 = pruned ? -INFINITY : acc[r][j].x * a.inv_n;
-                const float v1 = pruned ? -INFINITY : acc[r][j].y * a.inv_n;
+                const float v0 = (pruned || !active) ? -INFINITY : acc[r][j].x * a.inv_n;
+                const float v1 = (pruned || !active) ? -INFINITY : acc[r][j].y * a.inv_n;
                 if (x + 1 < a.W && (a.W & 1) == 0) {
                     *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
                 } else {
@@ -433,7 +575,7 @@ template <typename E, int NB, bool POL, int WARPS, int TC>
 __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore *__restrict__ pairs, int n_pairs,
                                                                   int total, int sx, int sy, int tg, int early,
                                                                   unsigned *__restrict__ counter, int *err,
-                                                                  unsigned long long *exec) {
+                                                                  unsigned long long *exec, unsigned win_bytes) {
     using Raw = typename Pairs<E>::Raw;
     constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
     constexpr int WTX = LX * TC, WTY = LY * TR;
@@ -523,6 +665,9 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         t.sx = sx;
         t.sy = sy;
         t.exec = exec;
+        t.emin = P.emin;
+        t.byw = P.byw;
+        t.bits = reinterpret_cast<uint32_t *>(smem_raw + pad + ((win_bytes + 15u) & ~15u));
         score_items<E, NB, POL, WARPS, TC>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
                                        min(group * tg + tg, P.nth), t);
         __syncthreads();   // every warp is done with the window before the next copy
@@ -769,7 +914,8 @@ cudaError_t chunked_dispatch(const CUtensorMap &tm, const ChunkArgs &a, dim3 gri
 
 template <typename E, int NB, bool POL, int WARPS, int TC>
 cudaError_t launch_pairs_t(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int early,
-                           size_t smem, unsigned *counter, int *err, unsigned long long *exec, cudaStream_t st) {
+                           size_t smem, size_t win_bytes, unsigned *counter, int *err, unsigned long long *exec,
+                           cudaStream_t st) {
     auto kern = score_pairs_kernel<E, NB, POL, WARPS, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -784,24 +930,27 @@ cudaError_t launch_pairs_t(const PairScore *pairs, int n_pairs, int total, const
     if (e != cudaSuccess)
         return e;
     const int grid = std::max(1, std::min(total, sms * std::max(1, per_sm)));
-    kern<<<grid, WARPS * 32, smem, st>>>(pairs, n_pairs, total, cfg.sx, cfg.sy, cfg.tg, early, counter, err, exec);
+    kern<<<grid, WARPS * 32, smem, st>>>(pairs, n_pairs, total, cfg.sx, cfg.sy, cfg.tg, early, counter, err, exec,
+                                         (unsigned)win_bytes);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename E, int NB, bool POL, int WARPS>
 cudaError_t launch_pairs_tc(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int early,
-                            size_t smem, unsigned *counter, int *err, unsigned long long *exec, cudaStream_t st) {
-    return cfg.tc == 10
-               ? launch_pairs_t<E, NB, POL, WARPS, 10>(pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st)
-               : launch_pairs_t<E, NB, POL, WARPS, 6>(pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st);
+                            size_t smem, size_t win_bytes, unsigned *counter, int *err, unsigned long long *exec,
+                            cudaStream_t st) {
+    return cfg.tc == 10 ? launch_pairs_t<E, NB, POL, WARPS, 10>(pairs, n_pairs, total, cfg, early, smem, win_bytes,
+                                                                counter, err, exec, st)
+                        : launch_pairs_t<E, NB, POL, WARPS, 6>(pairs, n_pairs, total, cfg, early, smem, win_bytes,
+                                                               counter, err, exec, st);
 }
 
 template <typename E>
 cudaError_t pairs_dispatch(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
-                           int early, size_t smem, unsigned *counter, int *err, unsigned long long *exec,
-                           cudaStream_t st) {
-#define SAM_PAIRS_ARGS pairs, n_pairs, total, cfg, early, smem, counter, err, exec, st
+                           int early, size_t smem, size_t win_bytes, unsigned *counter, int *err,
+                           unsigned long long *exec, cudaStream_t st) {
+#define SAM_PAIRS_ARGS pairs, n_pairs, total, cfg, early, smem, win_bytes, counter, err, exec, st
     if (cfg.warps == 4) {
         if (nbhd == 3)
             return pol ? launch_pairs_tc<E, 3, true, 4>(SAM_PAIRS_ARGS) : launch_pairs_tc<E, 3, false, 4>(SAM_PAIRS_ARGS);
