@@ -374,8 +374,104 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], stx0, sty0, k_begin, k_end, t);
 }
 
+// One thread's 8 x TC pose block for one angle: the sum of every point's
+// 3x3-window vote into acc (all lanes of the warp call it; `work` false
+// lanes only keep the warp's loop company).  With early termination a lane
+// stops once its block's partial sums prove M < min_score (exact-safe); the
+// warp leaves the loop when every lane has stopped.  Returns the points the
+// lane processed; `pruned` tells whether it stopped early.
+template <typename E, int NB, bool POL, int TC>
+__device__ __forceinline__ int block_dot(const typename Pairs<E>::Raw *win, int pp, int bx, int by,
+                                         const RotPt *P, int n, bool work, int early, float thresh,
+                                         float2 (&acc)[TR][TC / 2], bool &pruned) {
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j)
+            acc[r][j] = make_float2(0.f, 0.f);
+    pruned = false;
+    bool ldone = !work;
+    int done = work ? n : 0;
+    RotPt p = work ? P[0] : RotPt{0, 0, 0.f, 0.f};
+    for (int i = 0; i < n; ++i) {
+        const RotPt cur = p;
+        if (work && i + 1 < n)
+            p = P[i + 1];
+        if (!ldone) {
+            const float2 pxx = make_float2(cur.px, cur.px);
+            const float2 pyy = make_float2(cur.py, cur.py);
+            if (NB == 3) {
+                const int xs = bx + cur.ox;   // first pixel column (>= 0)
+                const int row0 = by + cur.oy;
+                if (xs & 1)
+                    point_nb3<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                else
+                    point_nb3<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+            } else {
+                const int xs = bx + 1 + cur.ox;   // centre column
+                const int row0 = by + 1 + cur.oy;
+                if (xs & 1)
+                    point_nb1<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                else
+                    point_nb1<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+            }
+        }
+        if (early && ((i + 1) % PRUNE_EVERY) == 0) {
+            if (!ldone) {
+                const float lim = thresh - (float)(n - 1 - i);
+                bool low = true;
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int j = 0; j < TC / 2; ++j)
+                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                if (low) {
+                    ldone = true;
+                    pruned = true;
+                    done = i + 1;
+                }
+            }
+            if (__all_sync(0xffffffffu, ldone))
+                break;
+        }
+    }
+    return done;
+}
+
+// Scores (or -inf) of one thread's block into the map, clipped to the map.
+template <int TC>
+__device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int yl, const float2 (&acc)[TR][TC / 2],
+                                            float inv_n, bool neg) {
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+        const int y = yl + r;
+        if (y >= H)
+            break;
+        float *row = mk + (size_t)y * W;
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j) {
+            const int x = xl + 2 * j;
+            const float v0 = neg ? -INFINITY : acc[r][j].x * inv_n;
+            const float v1 = neg ? -INFINITY : acc[r][j].y * inv_n;
+            if (x + 1 < W && (W & 1) == 0) {
+                *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
+            } else {
+                if (x < W)
+                    row[x] = v0;
+                if (x + 1 < W)
+                    row[x + 1] = v1;
+            }
+        }
+    }
+}
+
 // The (angle, warp tile) items of one CTA work unit over its staged window
 // (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
+//
+// With the edge-presence bound (early termination on) a bound pass first
+// marks which 8 x TC thread blocks can still hold a pose reaching min_score;
+// blocks that cannot are written -inf without a dot product, and only the
+// lanes of the others take part in the vote loop.
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
                                             int sty0, int k_begin, int k_end, const TileWork &a) {
@@ -383,74 +479,146 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
     constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lx = lane % LX, ly = lane / LX;
-    const int items = (k_end - k_begin) * a.sx * a.sy;
-    float *map = a.map;
-    // edge-presence bound (with early termination; needs the counts in 16 bit planes)
+    const int tiles = a.sx * a.sy;
+    const int items = (k_end - k_begin) * tiles;
+    // edge-presence bound (with early termination; counts in 16 bit planes)
     const bool bound = a.early && a.emin > 0 && a.n < 65536;
     const int dmw = edge_bitmap_words(2 * pp);
     const uint32_t *dbits = a.bits + (size_t)a.byw * dmw;
     if (bound)
         build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
+    unsigned long long executed = 0;
+    float2 acc[TR][TC / 2];
 
     for (int it = warp; it < items; it += WARPS) {
-        const int k = k_begin + it / (a.sx * a.sy);
-        const int wt = it % (a.sx * a.sy);
+        const int k = k_begin + it / tiles;
+        const int wt = it % tiles;
         const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC;   // thread's first pose
         const int y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
-        // window coordinates of the first needed pixel for offset (0, 0)
-        const int bx = x0 - 1 - wx0;
-        const int by = y0 - 1 - wy0;
-        float2 acc[TR][TC / 2];
-#pragma unroll
-        for (int r = 0; r < TR; ++r)
-#pragma unroll
-            for (int j = 0; j < TC / 2; ++j)
-                acc[r][j] = make_float2(0.f, 0.f);
+        const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
         const RotPt *P = a.rot + (size_t)k * a.n;
-        bool pruned = false;
-        int done = a.n;
-        // Bound pass: lane L counts, for the BW poses of one pose row it owns,
-        // how many points have an edge pixel in their window (bit-sliced
-        // counters, one bit per pose), then marks the poses whose count can
-        // still reach min_score.  A thread whose 8 x TC block has no such
-        // pose skips the dot products; a warp tile with none writes -inf.
-        bool active = true;
-        if (bound) {
+        float *mk = a.map + (size_t)(k - a.k0) * a.H * a.W;
+        if (!bound) {
+            bool pruned;
+            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, P, a.n, true,
+                                                       a.early, a.thresh, acc, pruned);
+            executed += (unsigned long long)done * (vx * vy);
+            block_store<TC>(mk, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, pruned);
+        } else {
+            // Bound pass: lane L counts, for the BW poses of one pose row
+            // it owns, how many points have an edge pixel in their window
+            // (bit-sliced counters, one bit per pose), then marks the poses
+            // whose count can still reach min_score.
             constexpr int LPR = 32 / WTY;       // lanes per pose row
             constexpr int BW = WTX / LPR;       // poses per lane (8 TC <= 80)
             const int xseg = stx0 + (wt % a.sx) * WTX + (lane % LPR) * BW;
             const int yrow = sty0 + (wt / a.sx) * WTY + lane / LPR;
+            // Counts over all points with carry-save adders
+            // (Harley-Seal): ones, twos, fours hold the low bits of every
+            // pose's count, pl the count of eights in bit planes 3 ..
+            uint32_t ones0 = 0u, ones1 = 0u, ones2 = 0u, twos0 = 0u, twos1 = 0u, twos2 = 0u;
+            uint32_t fours0 = 0u, fours1 = 0u, fours2 = 0u;
             uint32_t pl[16][3];
 #pragma unroll
             for (int q = 0; q < 16; ++q)
                 pl[q][0] = pl[q][1] = pl[q][2] = 0u;
-            for (int i = 0; i < a.n; ++i) {
-                const RotPt q = P[i];
-                const int b = xseg + q.ox - wx0;   // window column of the first pose's centre
-                const uint32_t *row = dbits + (size_t)(yrow + q.oy - wy0) * dmw + (b >> 5);
-                const int sh = b & 31;
-                const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
-                uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
-                         m2 = __funnelshift_r(w2, w3, sh);
-                if (BW <= 64) {
-                    m1 &= BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u);
-                    m2 = 0u;
-                } else {
-                    m2 &= (1u << (BW - 64)) - 1u;
+            // the points' offsets 32 at a time: one coalesced load, then a
+            // warp broadcast per point
+            int2 qo = make_int2(0, 0);
+            const int np8 = (a.n + 7) & ~7;
+            for (int i0 = 0; i0 < np8; i0 += 8) {
+                if ((i0 & 31) == 0) {
+                    const int ii = i0 + lane;
+                    qo = make_int2(0, 0);
+                    if (ii < a.n) {
+                        const RotPt t = P[ii];
+                        qo = make_int2(t.ox, t.oy);
+                    }
                 }
+                uint32_t mm0[8], mm1[8], mm2[8];
 #pragma unroll
-                for (int pq = 0; pq < 16; ++pq) {
-                    if ((m0 | m1 | m2) == 0u)
+                for (int j = 0; j < 8; ++j) {
+                    const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
+                    const int qoy = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+                    const int b = xseg + qox - wx0;   // window column of the first pose's centre
+                    const uint32_t *row = dbits + (size_t)(yrow + qoy - wy0) * dmw + (b >> 5);
+                    const int sh = b & 31;
+                    const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
+                    uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
+                             m2 = __funnelshift_r(w2, w3, sh);
+                    if (BW <= 64) {
+                        m1 &= BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u);
+                        m2 = 0u;
+                    } else {
+                        m2 &= (1u << (BW - 64)) - 1u;
+                    }
+                    const bool in = i0 + j < a.n;
+                    mm0[j] = in ? m0 : 0u;
+                    mm1[j] = in ? m1 : 0u;
+                    mm2[j] = in ? m2 : 0u;
+                }
+                // carry-save tree over the 8 masks
+                auto csa = [](uint32_t &h, uint32_t &l, uint32_t a_, uint32_t b_, uint32_t c_) {
+                    const uint32_t u = a_ ^ b_;
+                    h = (a_ & b_) | (u & c_);
+                    l = u ^ c_;
+                };
+                uint32_t e0, e1, e2;
+                {
+                    uint32_t t1, t2, t3, t4, f1, f2;
+                    csa(t1, ones0, ones0, mm0[0], mm0[1]);
+                    csa(t2, ones0, ones0, mm0[2], mm0[3]);
+                    csa(f1, twos0, twos0, t1, t2);
+                    csa(t3, ones0, ones0, mm0[4], mm0[5]);
+                    csa(t4, ones0, ones0, mm0[6], mm0[7]);
+                    csa(f2, twos0, twos0, t3, t4);
+                    csa(e0, fours0, fours0, f1, f2);
+                }
+                {
+                    uint32_t t1, t2, t3, t4, f1, f2;
+                    csa(t1, ones1, ones1, mm1[0], mm1[1]);
+                    csa(t2, ones1, ones1, mm1[2], mm1[3]);
+                    csa(f1, twos1, twos1, t1, t2);
+                    csa(t3, ones1, ones1, mm1[4], mm1[5]);
+                    csa(t4, ones1, ones1, mm1[6], mm1[7]);
+                    csa(f2, twos1, twos1, t3, t4);
+                    csa(e1, fours1, fours1, f1, f2);
+                }
+                if (BW > 64) {
+                    uint32_t t1, t2, t3, t4, f1, f2;
+                    csa(t1, ones2, ones2, mm2[0], mm2[1]);
+                    csa(t2, ones2, ones2, mm2[2], mm2[3]);
+                    csa(f1, twos2, twos2, t1, t2);
+                    csa(t3, ones2, ones2, mm2[4], mm2[5]);
+                    csa(t4, ones2, ones2, mm2[6], mm2[7]);
+                    csa(f2, twos2, twos2, t3, t4);
+                    csa(e2, fours2, fours2, f1, f2);
+                } else {
+                    e2 = 0u;
+                }
+                // eights into the bit planes (short carry chains)
+#pragma unroll
+                for (int pq = 3; pq < 16; ++pq) {
+                    if ((e0 | e1 | e2) == 0u)
                         break;
-                    const uint32_t c0 = pl[pq][0] & m0, c1 = pl[pq][1] & m1, c2 = pl[pq][2] & m2;
-                    pl[pq][0] ^= m0;
-                    pl[pq][1] ^= m1;
-                    pl[pq][2] ^= m2;
-                    m0 = c0;
-                    m1 = c1;
-                    m2 = c2;
+                    const uint32_t c0 = pl[pq][0] & e0, c1 = pl[pq][1] & e1, c2 = pl[pq][2] & e2;
+                    pl[pq][0] ^= e0;
+                    pl[pq][1] ^= e1;
+                    pl[pq][2] ^= e2;
+                    e0 = c0;
+                    e1 = c1;
+                    e2 = c2;
                 }
             }
+            pl[0][0] = ones0;
+            pl[0][1] = ones1;
+            pl[0][2] = ones2;
+            pl[1][0] = twos0;
+            pl[1][1] = twos1;
+            pl[1][2] = twos2;
+            pl[2][0] = fours0;
+            pl[2][1] = fours1;
+            pl[2][2] = fours2;
             // counts >= emin, bit-serially from the top plane
             uint32_t gt0 = 0u, gt1 = 0u, gt2 = 0u, eq0 = ~0u, eq1 = ~0u, eq2 = ~0u;
 #pragma unroll
@@ -471,98 +639,35 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const uint32_t o0 = gt0 | eq0;
             const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u));
             const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << (BW - 64)) - 1u)) : 0u;
-            if (!__any_sync(0xffffffffu, (o0 | o1 | o2) != 0u)) {
-                active = false;
-                pruned = true;
-                done = 0;
-            } else {
-                // this thread's 8 x TC block: rows ly*TR .., columns lx*TC ..
-                const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
-                uint32_t act = 0u;
+            // this thread's 8 x TC block: rows ly*TR .., columns lx*TC ..
+            const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
+            uint32_t act = 0u;
 #pragma unroll
-                for (int r = 0; r < TR; ++r) {
-                    const int src = (ly * TR + r) * LPR + seg;
-                    const uint32_t v0 = __shfl_sync(0xffffffffu, o0, src);
-                    const uint32_t v1 = __shfl_sync(0xffffffffu, o1, src);
-                    const uint32_t v2 = __shfl_sync(0xffffffffu, o2, src);
-                    const uint32_t lo = c0 < 32 ? v0 : (c0 < 64 ? v1 : v2);
-                    const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
-                    act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
-                }
-                active = act != 0u;
+            for (int r = 0; r < TR; ++r) {
+                const int src = (ly * TR + r) * LPR + seg;
+                const uint32_t v0 = __shfl_sync(0xffffffffu, o0, src);
+                const uint32_t v1 = __shfl_sync(0xffffffffu, o1, src);
+                const uint32_t v2 = __shfl_sync(0xffffffffu, o2, src);
+                const uint32_t lo = c0 < 32 ? v0 : (c0 < 64 ? v1 : v2);
+                const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
+                act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
             }
-        }
-        RotPt p = P[0];
-        for (int i = 0; i < (pruned ? 0 : a.n); ++i) {
-            const RotPt cur = p;
-            if (i + 1 < a.n)
-                p = P[i + 1];
-            const float2 pxx = make_float2(cur.px, cur.px);
-            const float2 pyy = make_float2(cur.py, cur.py);
-            if (!active) {
-            } else if (NB == 3) {
-                const int xs = bx + cur.ox;   // first pixel column (>= 0)
-                const int row0 = by + cur.oy;
-                if (xs & 1)
-                    point_nb3<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
-                else
-                    point_nb3<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
-            } else {
-                const int xs = bx + 1 + cur.ox;   // centre column
-                const int row0 = by + 1 + cur.oy;
-                if (xs & 1)
-                    point_nb1<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
-                else
-                    point_nb1<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
-            }
-            if (a.early && ((i + 1) % PRUNE_EVERY) == 0) {
-                const float lim = a.thresh - (float)(a.n - 1 - i);
-                bool low = true;
-                if (active) {
-#pragma unroll
-                    for (int r = 0; r < TR; ++r)
-#pragma unroll
-                        for (int j = 0; j < TC / 2; ++j)
-                            low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
-                }
-                if (__all_sync(0xffffffffu, low)) {
-                    pruned = true;
-                    done = i + 1;
-                    break;
-                }
-            }
-        }
-        {
-            // poses of this thread's block that lie inside the map
-            const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
-            const unsigned valid = __reduce_add_sync(0xffffffffu, active ? (unsigned)(vx * vy) : 0u);
-            if (lane == 0)
-                atomicAdd(a.exec, (unsigned long long)done * valid);
-        }
-        // epilogue: M = sum / n, or -inf where pruned; clip to the window
-        float *mk = map + (size_t)(k - a.k0) * a.H * a.W;
-#pragma unroll
-        for (int r = 0; r < TR; ++r) {
-            const int y = y0 + r - a.oy;
-            if (y >= a.H)
-                break;
-            float *row = mk + (size_t)y * a.W;
-#pragma unroll
-            for (int j = 0; j < TC / 2; ++j) {
-                const int x = x0 + 2 * j - a.ox;
-                const float v0 = (pruned || !active) ? -INFINITY : acc[r][j].x * a.inv_n;
-                const float v1 = (pruned || !active) ? -INFINITY : acc[r][j].y * a.inv_n;
-                if (x + 1 < a.W && (a.W & 1) == 0) {
-                    *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
-                } else {
-                    if (x < a.W)
-                        row[x] = v0;
-                    if (x + 1 < a.W)
-                        row[x + 1] = v1;
-                }
-            }
+            const bool active = act != 0u;
+            bool pruned;
+            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, P, a.n, active,
+                                                       a.early, a.thresh, acc, pruned);
+            if (active)
+                executed += (unsigned long long)done * (vx * vy);
+            block_store<TC>(mk, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, pruned || !active);
         }
     }
+    // executed pose-points of this thread's blocks, one atomic per warp
+    unsigned long long tot = executed;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot)
+        atomicAdd(a.exec, tot);
 }
 
 // Persistent form for batches of uneven (image, model) pairs: every CTA
