@@ -293,6 +293,24 @@ __device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *wi
     __syncthreads();
 }
 
+// Items (angle x warp tile) whose surviving blocks one queue round holds.
+constexpr int kQueueItems = 128;
+
+// Position of the r-th (0-based) set bit of m; r < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
                                             int sty0, int k_begin, int k_end, const TileWork &a);
@@ -468,10 +486,12 @@ __device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int
 // The (angle, warp tile) items of one CTA work unit over its staged window
 // (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
 //
-// With the edge-presence bound (early termination on) a bound pass first
-// marks which 8 x TC thread blocks can still hold a pose reaching min_score;
-// blocks that cannot are written -inf without a dot product, and only the
-// lanes of the others take part in the vote loop.
+// With the edge-presence bound (early termination on) a bound pass over the
+// CTA's items first marks which 8 x TC thread blocks can still hold a pose
+// reaching min_score; blocks that cannot are written -inf without a dot
+// product.  The surviving blocks, in (angle, tile, lane) order, are then
+// packed 32 to a warp, one per lane, so the vote loops run on full warps
+// (consecutive lanes mostly share an angle, hence the point offsets).
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
                                             int sty0, int k_begin, int k_end, const TileWork &a) {
@@ -489,22 +509,30 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
     unsigned long long executed = 0;
     float2 acc[TR][TC / 2];
+    __shared__ uint32_t s_mask[kQueueItems];   // surviving blocks (lanes) of each item
+    __shared__ int s_off[kQueueItems + 1];     // their first queue slot
 
-    for (int it = warp; it < items; it += WARPS) {
-        const int k = k_begin + it / tiles;
-        const int wt = it % tiles;
-        const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC;   // thread's first pose
-        const int y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
-        const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
-        const RotPt *P = a.rot + (size_t)k * a.n;
-        float *mk = a.map + (size_t)(k - a.k0) * a.H * a.W;
-        if (!bound) {
+    if (!bound) {
+        for (int it = warp; it < items; it += WARPS) {
+            const int k = k_begin + it / tiles;
+            const int wt = it % tiles;
+            const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC;   // thread's first pose
+            const int y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
+            const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
             bool pruned;
-            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, P, a.n, true,
-                                                       a.early, a.thresh, acc, pruned);
+            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, a.rot + (size_t)k * a.n,
+                                                       a.n, true, a.early, a.thresh, acc, pruned);
             executed += (unsigned long long)done * (vx * vy);
-            block_store<TC>(mk, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, pruned);
-        } else {
+            block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n,
+                            pruned);
+        }
+    }
+    for (int r0 = 0; bound && r0 < items; r0 += kQueueItems) {
+        const int ni = min(kQueueItems, items - r0);
+        for (int it = warp; it < ni; it += WARPS) {
+            const int k = k_begin + (r0 + it) / tiles;
+            const int wt = (r0 + it) % tiles;
+            const RotPt *P = a.rot + (size_t)k * a.n;
             // Bound pass: lane L counts, for the BW poses of one pose row
             // it owns, how many points have an edge pixel in their window
             // (bit-sliced counters, one bit per pose), then marks the poses
@@ -653,13 +681,68 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
             }
             const bool active = act != 0u;
-            bool pruned;
-            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, P, a.n, active,
-                                                       a.early, a.thresh, acc, pruned);
-            if (active)
-                executed += (unsigned long long)done * (vx * vy);
-            block_store<TC>(mk, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, pruned || !active);
+            if (!active) {
+                const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC, y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
+                block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc,
+                                a.inv_n, true);
+            }
+            const unsigned am = __ballot_sync(0xffffffffu, active);
+            if (lane == 0)
+                s_mask[it] = am;
         }
+        __syncthreads();
+        if (warp == 0) {   // queue offsets: exclusive prefix sum of the surviving counts
+            int carry = 0;
+            for (int b0 = 0; b0 < ni; b0 += 32) {
+                const int i = b0 + lane;
+                const int c = i < ni ? __popc(s_mask[i]) : 0;
+                int v = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o)
+                        v += t;
+                }
+                if (i < ni)
+                    s_off[i] = carry + v - c;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+            if (lane == 0)
+                s_off[ni] = carry;
+        }
+        __syncthreads();
+        const int total = s_off[ni];
+        for (int e0 = warp * 32; e0 < total; e0 += WARPS * 32) {
+            const int e = e0 + lane;
+            const bool has = e < total;
+            int it = 0, src = 0;
+            if (has) {
+                int lo = 0, hi = ni - 1;   // last item whose first slot <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= e)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                it = lo;
+                src = nth_set_bit(s_mask[it], e - s_off[it]);
+            }
+            const int k = k_begin + (r0 + it) / tiles;
+            const int wt = (r0 + it) % tiles;
+            const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
+            const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR;
+            bool pruned;
+            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, a.rot + (size_t)k * a.n,
+                                                       a.n, has, a.early, a.thresh, acc, pruned);
+            if (has) {
+                const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
+                executed += (unsigned long long)done * (vx * vy);
+                block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc,
+                                a.inv_n, pruned);
+            }
+        }
+        __syncthreads();   // s_mask and s_off are refilled by the next round
     }
     // executed pose-points of this thread's blocks, one atomic per warp
     unsigned long long tot = executed;
