@@ -185,15 +185,15 @@ __device__ __forceinline__ void dots_row(const typename Pairs<E>::Raw *row, int 
     }
 }
 
-// One model point over the thread's R x C pose block, 3x3 neighbourhood.
-template <typename E, bool POL, bool ODD, int TC>
+// One model point over the thread's R x TC pose block, 3x3 neighbourhood.
+template <typename E, bool POL, bool ODD, int TC, int R = TR>
 __device__ __forceinline__ void point_nb3(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
-                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
+                                          float2 pxx, float2 pyy, float2 (&acc)[R][TC / 2]) {
     constexpr int NP = ODD ? (TC + 4) / 2 : (TC + 2) / 2;   // pixel pairs per row
     constexpr int OFF = ODD ? 1 : 0;
     float hp2[TC], hp1[TC];
 #pragma unroll
-    for (int r = 0; r < TR + 2; ++r) {
+    for (int r = 0; r < R + 2; ++r) {
         const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
         float d[TC + 4];
         dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
@@ -218,12 +218,12 @@ __device__ __forceinline__ void point_nb3(const typename Pairs<E>::Raw *win, int
 }
 
 // One model point, neighbourhood 1 (no search): the centre pixel only.
-template <typename E, bool POL, bool ODD, int TC>
+template <typename E, bool POL, bool ODD, int TC, int R = TR>
 __device__ __forceinline__ void point_nb1(const typename Pairs<E>::Raw *win, int pp, int row0, int pair0,
-                                          float2 pxx, float2 pyy, float2 (&acc)[TR][TC / 2]) {
+                                          float2 pxx, float2 pyy, float2 (&acc)[R][TC / 2]) {
     constexpr int NP = ODD ? (TC + 2) / 2 : TC / 2;
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
+    for (int r = 0; r < R; ++r) {
         const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
         float d[TC + 4];
         dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
@@ -295,6 +295,12 @@ __device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *wi
 
 // Items (angle x warp tile) whose surviving blocks one queue round holds.
 constexpr int kQueueItems = 128;
+// Pose rows per lane when the surviving blocks are scored (TR / RD lanes
+// share one block).
+#ifndef SAM_DRAIN_ROWS
+#define SAM_DRAIN_ROWS 2
+#endif
+constexpr int RD = SAM_DRAIN_ROWS;
 
 // Position of the r-th (0-based) set bit of m; r < popc(m).
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
@@ -398,12 +404,12 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
 // stops once its block's partial sums prove M < min_score (exact-safe); the
 // warp leaves the loop when every lane has stopped.  Returns the points the
 // lane processed; `pruned` tells whether it stopped early.
-template <typename E, int NB, bool POL, int TC>
+template <typename E, int NB, bool POL, int TC, int R = TR>
 __device__ __forceinline__ int block_dot(const typename Pairs<E>::Raw *win, int pp, int bx, int by,
                                          const RotPt *P, int n, bool work, int early, float thresh,
-                                         float2 (&acc)[TR][TC / 2], bool &pruned) {
+                                         float2 (&acc)[R][TC / 2], bool &pruned) {
 #pragma unroll
-    for (int r = 0; r < TR; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int j = 0; j < TC / 2; ++j)
             acc[r][j] = make_float2(0.f, 0.f);
@@ -422,16 +428,16 @@ __device__ __forceinline__ int block_dot(const typename Pairs<E>::Raw *win, int 
                 const int xs = bx + cur.ox;   // first pixel column (>= 0)
                 const int row0 = by + cur.oy;
                 if (xs & 1)
-                    point_nb3<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    point_nb3<E, POL, true, TC, R>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
                 else
-                    point_nb3<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                    point_nb3<E, POL, false, TC, R>(win, pp, row0, xs >> 1, pxx, pyy, acc);
             } else {
                 const int xs = bx + 1 + cur.ox;   // centre column
                 const int row0 = by + 1 + cur.oy;
                 if (xs & 1)
-                    point_nb1<E, POL, true, TC>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
+                    point_nb1<E, POL, true, TC, R>(win, pp, row0, (xs - 1) >> 1, pxx, pyy, acc);
                 else
-                    point_nb1<E, POL, false, TC>(win, pp, row0, xs >> 1, pxx, pyy, acc);
+                    point_nb1<E, POL, false, TC, R>(win, pp, row0, xs >> 1, pxx, pyy, acc);
             }
         }
         if (early && ((i + 1) % PRUNE_EVERY) == 0) {
@@ -439,7 +445,7 @@ __device__ __forceinline__ int block_dot(const typename Pairs<E>::Raw *win, int 
                 const float lim = thresh - (float)(n - 1 - i);
                 bool low = true;
 #pragma unroll
-                for (int r = 0; r < TR; ++r)
+                for (int r = 0; r < R; ++r)
 #pragma unroll
                     for (int j = 0; j < TC / 2; ++j)
                         low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
@@ -457,11 +463,11 @@ __device__ __forceinline__ int block_dot(const typename Pairs<E>::Raw *win, int 
 }
 
 // Scores (or -inf) of one thread's block into the map, clipped to the map.
-template <int TC>
-__device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int yl, const float2 (&acc)[TR][TC / 2],
+template <int TC, int R = TR>
+__device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int yl, const float2 (&acc)[R][TC / 2],
                                             float inv_n, bool neg) {
 #pragma unroll
-    for (int r = 0; r < TR; ++r) {
+    for (int r = 0; r < R; ++r) {
         const int y = yl + r;
         if (y >= H)
             break;
@@ -712,8 +718,12 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         }
         __syncthreads();
         const int total = s_off[ni];
-        for (int e0 = warp * 32; e0 < total; e0 += WARPS * 32) {
-            const int e = e0 + lane;
+        // each surviving block is scored by SPLIT lanes (RD rows each) in
+        // different quarter-warps; a warp takes 32 / SPLIT blocks at a time
+        constexpr int SPLIT = TR / RD, BPW = 32 / SPLIT;
+        const int part = lane / BPW;
+        for (int e0 = warp * BPW; e0 < total; e0 += WARPS * BPW) {
+            const int e = e0 + lane % BPW;
             const bool has = e < total;
             int it = 0, src = 0;
             if (has) {
@@ -731,15 +741,17 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const int k = k_begin + (r0 + it) / tiles;
             const int wt = (r0 + it) % tiles;
             const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
-            const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR;
+            const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
             bool pruned;
-            const int done = block_dot<E, NB, POL, TC>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, a.rot + (size_t)k * a.n,
-                                                       a.n, has, a.early, a.thresh, acc, pruned);
+            float2 accd[RD][TC / 2];
+            const int done = block_dot<E, NB, POL, TC, RD>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0,
+                                                           a.rot + (size_t)k * a.n, a.n, has, a.early, a.thresh, accd,
+                                                           pruned);
             if (has) {
-                const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(TR, a.H - (y0 - a.oy)));
+                const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(RD, a.H - (y0 - a.oy)));
                 executed += (unsigned long long)done * (vx * vy);
-                block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc,
-                                a.inv_n, pruned);
+                block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, accd,
+                                    a.inv_n, pruned);
             }
         }
         __syncthreads();   // s_mask and s_off are refilled by the next round
