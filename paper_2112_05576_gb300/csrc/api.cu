@@ -100,6 +100,7 @@ struct Plan {
     size_t off_scratch = 0;
     size_t off_rescore = 0;          // FP32 rescoring list (16-bit precisions)
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
+    size_t off_queue = 0, queue_bytes = 0;   // two-launch storage of the tiled scorer
     size_t total = 0;
 };
 
@@ -165,6 +166,11 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
     off += al((size_t)p.max_detections * sizeof(sam_pose) * count);
     P.off_nout = off;
     off += al((size_t)4 * count);
+    if (p.early_termination && p.step_x == 1 && p.step_y == 1) {
+        P.off_queue = off;
+        P.queue_bytes = drain_queue_bytes(count, P.gw, P.gh, P.nth);
+        off += al(P.queue_bytes);
+    }
     P.total = off;
     return P;
 }
@@ -252,6 +258,8 @@ ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_par
     sa.map = (float *)(ws + P.off_map);
     sa.map_img = P.map_img;
     sa.count = P.count;
+    sa.queue = P.queue_bytes ? ws + P.off_queue : nullptr;
+    sa.queue_bytes = P.queue_bytes;
     return sa;
 }
 
@@ -464,8 +472,10 @@ cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a
     if (cfg.tg == 0)
         return launch_score_chunked(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
                                     a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
+    const DrainQueue q{a.queue, a.queue_bytes};
     return launch_score_tiled(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
-                              a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
+                              a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window,
+                              a.queue && !window ? &q : nullptr);
 }
 
 // The model's tuned tiling for field `precision` and a call over `count`

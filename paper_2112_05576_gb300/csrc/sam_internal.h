@@ -78,6 +78,9 @@ constexpr int kTileRows = 8;
 constexpr int kLanesXF32 = 8;
 constexpr int kLanesX16 = 16;
 constexpr int kChunkCols = 6;
+// Pose rows each lane scores of a block that survives the edge-presence
+// bound (kTileRows / kDrainRows lanes share the block).
+constexpr int kDrainRows = 2;
 
 struct TileConfig {
     int sx = 2, sy = 1;   // super-tile in warp tiles (8 x tc lanes-along-x poses wide, 32 rows tall for FP32)
@@ -175,6 +178,8 @@ struct ScoreArgs {
     float *map;
     size_t map_img;   // floats per image
     int count;
+    void *queue = nullptr;     // two-launch storage of the tiled scorer (optional)
+    size_t queue_bytes = 0;
 };
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
 
@@ -192,10 +197,21 @@ struct PoseWindow {
     int x0, y0, gw, gh, k0, nk;
 };
 
+// Device storage of the two-launch form (a slice of the caller's workspace).
+struct DrainQueue {
+    void *base;    // 256-byte aligned
+    size_t bytes;
+};
+// Workspace bytes that cover the two-launch form of every tiling the
+// autotuner tries for a gw x gh map with nth angles over `count` images.
+size_t drain_queue_bytes(int count, int gw, int gh, int nth);
+
+// The tiled scorer; with `queue` (and early termination) in the two-launch
+// form, else in one launch.
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
                                int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
-                               const PoseWindow *window = nullptr);
+                               const PoseWindow *window = nullptr, const DrainQueue *queue = nullptr);
 
 // Kernel arguments of the single-level tiled scorer (score_tiled_kernels.cuh).
 struct TiledArgs {
@@ -216,7 +232,17 @@ struct TiledArgs {
     int emin;                   // edge-presence bound: fewest edge windows a surviving pose needs
     int *err;                   // device error flag (bounded waits)
     unsigned long long *exec;   // executed pose-point counter
+    int tiles_y;                // super-tiles along y
+    // Two-launch form (queue non-null, bound on): the bound launch appends
+    // each CTA's surviving blocks to `queue` and one task per CTA-sized batch
+    // of them to `tasks`; the drain launch scores the tasks on every SM.
+    uint32_t *queue;            // (item << 5) | lane, one contiguous run per CTA round
+    int4 *tasks;                // {unit, first entry, entries, 0}
+    unsigned *qctr;             // [0] entries, [1] tasks, [2] next task (zeroed before the bound launch)
+    unsigned qcap, tcap;        // capacities (entries, tasks)
+    int units;                  // work units (CTAs) of the bound launch
 };
+
 
 // Kernel arguments of the chunked scorer.
 struct ChunkArgs {

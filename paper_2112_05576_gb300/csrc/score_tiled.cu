@@ -148,10 +148,18 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int t
 
 // Launch over `count` images whose pairs-layout fields start at `field`
 // (row pitch wp pixels, a multiple of 4; image stride field_img_px pixels).
+size_t drain_queue_bytes(int count, int gw, int gh, int nth) {
+    // blocks of every tiling the autotuner tries (super-tiles of up to 3 x 2
+    // warp tiles of at most 16 x 4 lanes, angle groups of at most nth)
+    const size_t blocks = (size_t)count * (size_t)(2 * nth) * (size_t)(gw / 6 + 49) * (size_t)(gh / 8 + 9);
+    const size_t slices = blocks * (kTileRows / kDrainRows);
+    return 256 + (slices / 32 + 64) * 16 + slices * 4;
+}
+
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
                                int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
-                               const PoseWindow *window) {
+                               const PoseWindow *window, const DrainQueue *queue) {
     const LevelHost &L = m->lv[level];
     const PoseWindow pw = window ? *window : PoseWindow{0, 0, W, H, 0, L.ntheta};
     int bxw = 0, byw = 0;
@@ -201,8 +209,35 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.emin = early ? edge_count_threshold(a.thresh, precision) : 0;
     a.err = fl.err;
     a.exec = fl.exec;
+    a.tiles_y = tiles_y;
     const int groups = (pw.nk + cfg.tg - 1) / cfg.tg;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)groups, (unsigned)count);
+    // two-launch form when the bound is on and the storage holds every block
+    a.queue = nullptr;
+    a.tasks = nullptr;
+    a.qctr = nullptr;
+    a.qcap = a.tcap = 0;
+    a.units = (int)(grid.x * grid.y * grid.z);
+    if (queue && queue->base && a.emin > 0 && L.n < 65536) {
+        const size_t items = (size_t)cfg.tg * cfg.sx * cfg.sy;
+        const size_t rounds = (items + 127) / 128;
+        const size_t ch = (size_t)cfg.warps * 32;   // slices per task
+        const size_t units = (size_t)a.units;
+        const size_t per_item = 32 * (kTileRows / kDrainRows);
+        const size_t qcap = units * items * per_item, tcap = units * (items * per_item / ch + rounds);
+        const size_t need = 256 + tcap * 16 + qcap * 4;
+        if (need <= queue->bytes && qcap < (1u << 31) && tcap < (1u << 31)) {
+            char *b = (char *)queue->base;
+            a.qctr = (unsigned *)b;
+            a.tasks = (int4 *)(b + 256);
+            a.queue = (uint32_t *)(b + 256 + tcap * 16);
+            a.qcap = (unsigned)qcap;
+            a.tcap = (unsigned)tcap;
+            cudaError_t e = cudaMemsetAsync(a.qctr, 0, 16, st);
+            if (e != cudaSuccess)
+                return e;
+        }
+    }
     const size_t smem =
         (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) + edge_bitmap_bytes(bxw, byw) + 128;
     const bool pol = polarity != 0;

@@ -249,6 +249,13 @@ struct TileWork {
     int emin;                   // edge-presence bound (0: off)
     int byw;                    // window rows
     uint32_t *bits;             // 2 edge bitmaps of the window (edge_bitmap_bytes)
+    int *err;                   // device error flag
+    // two-launch form (queue non-null): where the surviving blocks go
+    uint32_t *queue;
+    int4 *tasks;
+    unsigned *qctr;
+    unsigned qcap, tcap;
+    int unit;                   // this CTA's work unit
 };
 
 // Edge bitmaps of a staged window (all threads of the CTA; ends with a CTA
@@ -297,10 +304,8 @@ __device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *wi
 constexpr int kQueueItems = 128;
 // Pose rows per lane when the surviving blocks are scored (TR / RD lanes
 // share one block).
-#ifndef SAM_DRAIN_ROWS
-#define SAM_DRAIN_ROWS 2
-#endif
-constexpr int RD = SAM_DRAIN_ROWS;
+constexpr int RD = kDrainRows;
+static_assert(kTileRows / kDrainRows == 4, "queue entries hold the slice index in 2 bits");
 
 // Position of the r-th (0-based) set bit of m; r < popc(m).
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
@@ -317,64 +322,58 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
     return pos;
 }
 
-template <typename E, int NB, bool POL, int WARPS, int TC>
-__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
-                                            int sty0, int k_begin, int k_end, const TileWork &a);
-
-template <typename E, int NB, bool POL, int WARPS, int TC>
-__global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                  const TiledArgs a) {
-    using Raw = typename Pairs<E>::Raw;
+// Where a work unit of the tiled scorer lies: image, super-tile origin
+// (poses), angles [k_begin, k_end).  unit = super-tile + tiles * (angle
+// group + groups * image), the bound launch's linear CTA index.
+struct UnitPos {
+    int img, stx0, sty0, k_begin, k_end;
+};
+template <typename E, int TC>
+__device__ __forceinline__ UnitPos unit_pos(const TiledArgs &a, int unit) {
     constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
-    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // the TMA destination must be 128-byte aligned: round the base up (the
-    // launch adds 128 bytes of slack)
-    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
-    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
-    __shared__ __align__(8) unsigned long long mbar;
-    __shared__ int s_org[2];   // window origin (pixel x, row y), global coords
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    const int tiles = a.tiles_x * a.tiles_y, groups = (a.nk + a.tg - 1) / a.tg;
+    const int st = unit % tiles, rest = unit / tiles;
+    UnitPos u;
+    u.img = rest / groups;
+    u.stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
+    u.sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
+    u.k_begin = a.k0 + (rest % groups) * a.tg;
+    u.k_end = min(u.k_begin + a.tg, a.k0 + a.nk);
+    return u;
+}
 
-    const int img = blockIdx.z;
-    const int group = blockIdx.y;
-    const int st = blockIdx.x;
-    const int stx0 = a.ox + (st % a.tiles_x) * a.sx * WTX;
-    const int sty0 = a.oy + (st / a.tiles_x) * a.sy * WTY;
-    const int k_begin = a.k0 + group * a.tg;
-    const int k_end = min(k_begin + a.tg, a.k0 + a.nk);
-    const int pp = a.bxw / 2;   // window row pitch in pixel pairs
-    const uint32_t bar = smem_addr(&mbar);
+// Thread 0: the unit's window origin into s_org and its TMA copy, completing
+// on mbarrier `bar`.  The previous reads of the window (generic proxy) are
+// ordered before the copy into it (async proxy).
+template <typename E>
+__device__ __forceinline__ void stage_window(const CUtensorMap &tmap, const TiledArgs &a, const UnitPos &u,
+                                             const void *win, uint32_t bar, int *s_org) {
+    int xmin = 1 << 30, ymin = 1 << 30;
+    for (int k = u.k_begin; k < u.k_end; ++k) {
+        const int4 b = a.bbox[k];
+        xmin = min(xmin, b.x);
+        ymin = min(ymin, b.z);
+    }
+    // aligned start: the TMA x coordinate times the element size must be a
+    // multiple of 16 bytes
+    const int wx0 = (u.stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
+    const int wy0 = u.sty0 + ymin - 1;
+    s_org[0] = wx0;
+    s_org[1] = wy0;
+    const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    const int xe = wx0 * Pairs<E>::BYTES / 16;   // 8-byte elements
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(win)),
+        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(u.img), "r"(bar)
+        : "memory");
+}
 
-    if (threadIdx.x == 0) {
-        int xmin = 1 << 30, ymin = 1 << 30;
-        for (int k = k_begin; k < k_end; ++k) {
-            const int4 b = a.bbox[k];
-            xmin = min(xmin, b.x);
-            ymin = min(ymin, b.z);
-        }
-        // aligned start: the TMA x coordinate times the element size must be a
-        // multiple of 16 bytes
-        const int wx0 = (stx0 + xmin - 1) & ~(Pairs<E>::XALIGN - 1);
-        const int wy0 = sty0 + ymin - 1;
-        s_org[0] = wx0;
-        s_org[1] = wy0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-        const int xe = wx0 * Pairs<E>::BYTES / 16;   // 8-byte elements
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];" ::"r"(smem_addr(win)),
-            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(img), "r"(bar)
-            : "memory");
-    }
-    __syncthreads();
-    if (!mbar_wait(bar, 0)) {
-        if (threadIdx.x == 0)
-            atomicExch(a.err, 1);
-        return;
-    }
+// The per-image work description of a tiled launch (bits and unit unset).
+__device__ __forceinline__ TileWork tile_work(const TiledArgs &a, int img) {
     TileWork t;
     t.rot = a.rot;
     t.n = a.n;
@@ -392,10 +391,144 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     t.exec = a.exec;
     t.emin = a.emin;
     t.byw = a.byw;
+    t.bits = nullptr;
+    t.err = a.err;
+    t.queue = a.queue;
+    t.tasks = a.tasks;
+    t.qctr = a.qctr;
+    t.qcap = a.qcap;
+    t.tcap = a.tcap;
+    t.unit = 0;
+    return t;
+}
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int k_end, const TileWork &a);
+template <typename E, int NB, bool POL, int TC>
+__device__ __forceinline__ void score_slice(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int item, int src, int part, bool has,
+                                            const TileWork &a, unsigned long long &executed);
+
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  const TiledArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the TMA destination must be 128-byte aligned: round the base up (the
+    // launch adds 128 bytes of slack)
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_org[2];   // window origin (pixel x, row y), global coords
+
+    const int unit = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const UnitPos u = unit_pos<E, TC>(a, unit);
+    const int pp = a.bxw / 2;   // window row pitch in pixel pairs
+    const uint32_t bar = smem_addr(&mbar);
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_window<E>(tmap, a, u, win, bar, s_org);
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0)) {
+        if (threadIdx.x == 0)
+            atomicExch(a.err, 1);
+        return;
+    }
+    TileWork t = tile_work(a, u.img);
     // the edge bitmaps follow the window (16-byte aligned)
     t.bits = reinterpret_cast<uint32_t *>(smem_raw + pad +
                                           (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15));
-    score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], stx0, sty0, k_begin, k_end, t);
+    t.unit = unit;
+    score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
+}
+
+// Drain launch of the two-launch form: persistent CTAs pull tasks (a work
+// unit and a run of its surviving blocks from the bound launch), stage the
+// unit's window and score the run, TR / RD lanes per block as in the
+// one-launch form.  A heavy unit's blocks so spread over many SMs.
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__global__ void __launch_bounds__(WARPS * 32) score_drain_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  const TiledArgs a) {
+    using Raw = typename Pairs<E>::Raw;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_org[2];
+    __shared__ int s_task[4];   // state (-1 end, 0 skip, 1 run), unit, first entry, entries
+    const uint32_t bar = smem_addr(&mbar);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    unsigned long long executed = 0;
+    const unsigned ntasks = min(a.qctr[1], a.tcap);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned ti = atomicAdd(&a.qctr[2], 1u);
+            int state = -1;
+            if (ti < ntasks) {
+                const int4 tk = a.tasks[ti];
+                state = 0;
+                if (tk.x >= 0 && tk.x < a.units && tk.y >= 0 && tk.z > 0 &&
+                    (unsigned)tk.y + (unsigned)tk.z <= a.qcap) {
+                    const UnitPos u = unit_pos<E, TC>(a, tk.x);
+                    if (u.k_begin < u.k_end) {
+                        state = 1;
+                        s_task[1] = tk.x;
+                        s_task[2] = tk.y;
+                        s_task[3] = tk.z;
+                        stage_window<E>(tmap, a, u, win, bar, s_org);
+                    }
+                }
+                if (state == 0)
+                    atomicExch(a.err, 1);
+            }
+            s_task[0] = state;
+        }
+        __syncthreads();
+        const int state = s_task[0];
+        if (state < 0)
+            break;
+        if (state == 0) {
+            __syncthreads();
+            continue;
+        }
+        const bool ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0)
+                atomicExch(a.err, 1);
+            break;
+        }
+        const UnitPos u = unit_pos<E, TC>(a, s_task[1]);
+        const TileWork t = tile_work(a, u.img);
+        const int first = s_task[2], cnt = s_task[3];
+        for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
+            const int e = e0 + lane;
+            const bool has = e < cnt;
+            const uint32_t code = has ? a.queue[first + e] : 0u;
+            score_slice<E, NB, POL, TC>(win, a.bxw / 2, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
+                                        (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
+                                        executed);
+        }
+        __syncthreads();   // every warp is done with the window before the next copy
+    }
+    unsigned long long tot = executed;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot)
+        atomicAdd(a.exec, tot);
 }
 
 // One thread's 8 x TC pose block for one angle: the sum of every point's
@@ -489,6 +622,49 @@ __device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int
     }
 }
 
+// -inf into an R x TC pose block of the map, clipped to the map.
+template <int TC, int R>
+__device__ __forceinline__ void fill_neg(float *mk, int W, int H, int xl, int yl) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = yl + r;
+        if (y >= H)
+            break;
+        float *row = mk + (size_t)y * W;
+#pragma unroll
+        for (int c = 0; c < TC; ++c)
+            if (xl + c < W)
+                row[xl + c] = -INFINITY;
+    }
+}
+
+// One lane's RD-row slice `part` of surviving block `src` (lane index within
+// the warp tile) of item `item` (angle k_begin + item / tiles, warp tile
+// item % tiles): scored and stored; `has` false lanes only keep the warp's
+// loop company.
+template <typename E, int NB, bool POL, int TC>
+__device__ __forceinline__ void score_slice(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                            int sty0, int k_begin, int item, int src, int part, bool has,
+                                            const TileWork &a, unsigned long long &executed) {
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    const int tiles = a.sx * a.sy;
+    const int k = k_begin + item / tiles;
+    const int wt = item % tiles;
+    const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
+    const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
+    bool pruned;
+    float2 acc[RD][TC / 2];
+    const int done = block_dot<E, NB, POL, TC, RD>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0, a.rot + (size_t)k * a.n, a.n,
+                                                   has, a.early, a.thresh, acc, pruned);
+    if (has) {
+        const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(RD, a.H - (y0 - a.oy)));
+        executed += (unsigned long long)done * (vx * vy);
+        block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n,
+                            pruned);
+    }
+}
+
 // The (angle, warp tile) items of one CTA work unit over its staged window
 // (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
 //
@@ -515,7 +691,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
     unsigned long long executed = 0;
     float2 acc[TR][TC / 2];
-    __shared__ uint32_t s_mask[kQueueItems];   // surviving blocks (lanes) of each item
+    constexpr int SPLIT = TR / RD;                 // slices per thread block
+    __shared__ uint32_t s_mask[kQueueItems][SPLIT];   // surviving slices (lanes) of each item
     __shared__ int s_off[kQueueItems + 1];     // their first queue slot
 
     if (!bound) {
@@ -673,35 +850,42 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const uint32_t o0 = gt0 | eq0;
             const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u));
             const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << (BW - 64)) - 1u)) : 0u;
-            // this thread's 8 x TC block: rows ly*TR .., columns lx*TC ..
+            // this thread's 8 x TC block (rows ly*TR .., columns lx*TC ..) in
+            // RD-row slices: a slice with no surviving pose is written -inf,
+            // the others go to the queue
             const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
-            uint32_t act = 0u;
+            const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC, y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
+            float *mk = a.map + (size_t)(k - a.k0) * a.H * a.W;
 #pragma unroll
-            for (int r = 0; r < TR; ++r) {
-                const int src = (ly * TR + r) * LPR + seg;
-                const uint32_t v0 = __shfl_sync(0xffffffffu, o0, src);
-                const uint32_t v1 = __shfl_sync(0xffffffffu, o1, src);
-                const uint32_t v2 = __shfl_sync(0xffffffffu, o2, src);
-                const uint32_t lo = c0 < 32 ? v0 : (c0 < 64 ? v1 : v2);
-                const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
-                act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
+            for (int sp = 0; sp < SPLIT; ++sp) {
+                uint32_t act = 0u;
+#pragma unroll
+                for (int r = sp * RD; r < (sp + 1) * RD; ++r) {
+                    const int src = (ly * TR + r) * LPR + seg;
+                    const uint32_t v0 = __shfl_sync(0xffffffffu, o0, src);
+                    const uint32_t v1 = __shfl_sync(0xffffffffu, o1, src);
+                    const uint32_t v2 = __shfl_sync(0xffffffffu, o2, src);
+                    const uint32_t lo = c0 < 32 ? v0 : (c0 < 64 ? v1 : v2);
+                    const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
+                    act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
+                }
+                if (!act)
+                    fill_neg<TC, RD>(mk, a.W, a.H, x0 - a.ox, y0 + sp * RD - a.oy);
+                const unsigned am = __ballot_sync(0xffffffffu, act != 0u);
+                if (lane == 0)
+                    s_mask[it][sp] = am;
             }
-            const bool active = act != 0u;
-            if (!active) {
-                const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC, y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
-                block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc,
-                                a.inv_n, true);
-            }
-            const unsigned am = __ballot_sync(0xffffffffu, active);
-            if (lane == 0)
-                s_mask[it] = am;
         }
         __syncthreads();
         if (warp == 0) {   // queue offsets: exclusive prefix sum of the surviving counts
             int carry = 0;
             for (int b0 = 0; b0 < ni; b0 += 32) {
                 const int i = b0 + lane;
-                const int c = i < ni ? __popc(s_mask[i]) : 0;
+                int c = 0;
+                if (i < ni)
+#pragma unroll
+                    for (int sp = 0; sp < SPLIT; ++sp)
+                        c += __popc(s_mask[i][sp]);
                 int v = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -718,40 +902,71 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         }
         __syncthreads();
         const int total = s_off[ni];
-        // each surviving block is scored by SPLIT lanes (RD rows each) in
-        // different quarter-warps; a warp takes 32 / SPLIT blocks at a time
-        constexpr int SPLIT = TR / RD, BPW = 32 / SPLIT;
-        const int part = lane / BPW;
-        for (int e0 = warp * BPW; e0 < total; e0 += WARPS * BPW) {
-            const int e = e0 + lane % BPW;
-            const bool has = e < total;
-            int it = 0, src = 0;
-            if (has) {
-                int lo = 0, hi = ni - 1;   // last item whose first slot <= e
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= e)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
+        // one surviving slice per lane, in (item, slice, lane) order
+        constexpr int CH = WARPS * 32;
+        if (a.queue) {
+            // two-launch form: the blocks to the global queue, one task per
+            // CH of them (a CTA's worth for the drain launch)
+            __shared__ unsigned s_qb;
+            if (threadIdx.x == 0) {
+                const unsigned nt = (unsigned)((total + CH - 1) / CH);
+                unsigned qb = ~0u;
+                if (total > 0) {
+                    qb = atomicAdd(&a.qctr[0], (unsigned)total);
+                    const unsigned tb = atomicAdd(&a.qctr[1], nt);
+                    if (qb + (unsigned)total > a.qcap || tb + nt > a.tcap) {
+                        atomicExch(a.err, 1);   // capacities cover every block: cannot happen
+                        qb = ~0u;
+                    } else {
+                        for (unsigned j = 0; j < nt; ++j)
+                            a.tasks[tb + j] = make_int4(a.unit, (int)(qb + j * CH), min(CH, total - (int)(j * CH)), 0);
+                    }
                 }
-                it = lo;
-                src = nth_set_bit(s_mask[it], e - s_off[it]);
+                s_qb = qb;
             }
-            const int k = k_begin + (r0 + it) / tiles;
-            const int wt = (r0 + it) % tiles;
-            const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
-            const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
-            bool pruned;
-            float2 accd[RD][TC / 2];
-            const int done = block_dot<E, NB, POL, TC, RD>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0,
-                                                           a.rot + (size_t)k * a.n, a.n, has, a.early, a.thresh, accd,
-                                                           pruned);
-            if (has) {
-                const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(RD, a.H - (y0 - a.oy)));
-                executed += (unsigned long long)done * (vx * vy);
-                block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, accd,
-                                    a.inv_n, pruned);
+            __syncthreads();
+            const unsigned qb = s_qb;
+            if (qb != ~0u) {
+                for (int it = warp; it < ni; it += WARPS) {
+                    unsigned slot = qb + (unsigned)s_off[it];
+#pragma unroll
+                    for (int sp = 0; sp < SPLIT; ++sp) {
+                        const uint32_t m = s_mask[it][sp];
+                        if ((m >> lane) & 1u)
+                            a.queue[slot + (unsigned)__popc(m & ((1u << lane) - 1u))] =
+                                ((uint32_t)(r0 + it) << 7) | ((uint32_t)sp << 5) | (uint32_t)lane;
+                        slot += (unsigned)__popc(m);
+                    }
+                }
+            }
+        } else {
+            for (int e0 = warp * 32; e0 < total; e0 += WARPS * 32) {
+                const int e = e0 + lane;
+                const bool has = e < total;
+                int it = 0, src = 0, part = 0;
+                if (has) {
+                    int lo = 0, hi = ni - 1;   // last item whose first slot <= e
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= e)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    it = lo;
+                    int rank = e - s_off[it];
+#pragma unroll
+                    for (int sp = 0; sp < SPLIT; ++sp) {
+                        const int c = __popc(s_mask[it][sp]);
+                        if (rank >= 0 && rank < c) {
+                            part = sp;
+                            src = nth_set_bit(s_mask[it][sp], rank);
+                        }
+                        rank -= c;
+                    }
+                }
+                score_slice<E, NB, POL, TC>(win, pp, wx0, wy0, stx0, sty0, k_begin, r0 + it, src, part, has, a,
+                                            executed);
             }
         }
         __syncthreads();   // s_mask and s_off are refilled by the next round
@@ -868,6 +1083,12 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         t.emin = P.emin;
         t.byw = P.byw;
         t.bits = reinterpret_cast<uint32_t *>(smem_raw + pad + ((win_bytes + 15u) & ~15u));
+        t.err = err;
+        t.queue = nullptr;
+        t.tasks = nullptr;
+        t.qctr = nullptr;
+        t.qcap = t.tcap = 0;
+        t.unit = 0;
         score_items<E, NB, POL, WARPS, TC>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
                                        min(group * tg + tg, P.nth), t);
         __syncthreads();   // every warp is done with the window before the next copy
@@ -1058,6 +1279,26 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
     if (e != cudaSuccess)
         return e;
     kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !a.queue)
+        return e;
+    // drain launch: persistent, as many CTAs as are resident at once
+    auto dk = score_drain_kernel<E, NB, POL, WARPS, TC>;
+    const size_t dsmem = (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15) + 128;
+    e = cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(dk, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dk, WARPS * 32, dsmem)) != cudaSuccess)
+        return e;
+    const unsigned ctas = (unsigned)std::max(1, std::min(sms * std::max(occ, 1), (int)std::min(a.tcap, 1u << 20)));
+    dk<<<ctas, WARPS * 32, dsmem, st>>>(tm, a);
     count_launches(1);
     return cudaGetLastError();
 }
