@@ -139,6 +139,11 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int t
     }
     int bx = sx * g.wtx + spx + 2 + (g.xalign - 1) + 1;
     bx = (bx + g.xalign - 1) / g.xalign * g.xalign;
+    // row pitch: an odd number of 16-byte units (FP32 pixel pairs) or twice
+    // an odd number of 8-byte units (16-bit pairs), so rows 2 apart fall in
+    // other shared-memory banks
+    if (g.pair_bytes == 16 ? ((bx / 2) % 2 == 0) : ((bx / 2) % 4 == 0))
+        bx += g.xalign;
     const int by = sy * g.wty + spy + 2;
     *bxw = bx;
     *byw = by;

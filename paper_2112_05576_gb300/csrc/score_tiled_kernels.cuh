@@ -691,8 +691,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
     unsigned long long executed = 0;
     float2 acc[TR][TC / 2];
-    constexpr int SPLIT = TR / RD;                 // slices per thread block
-    __shared__ uint32_t s_mask[kQueueItems][SPLIT];   // surviving slices (lanes) of each item
+    constexpr int SPLIT = TR / RD;                 // slices per thread block (4)
+    __shared__ uint32_t s_mask[kQueueItems][4];    // surviving slices of each item (see the bound pass)
     __shared__ int s_off[kQueueItems + 1];     // their first queue slot
 
     if (!bound) {
@@ -856,6 +856,7 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
             const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC, y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
             float *mk = a.map + (size_t)(k - a.k0) * a.H * a.W;
+            uint32_t nib = 0u;   // surviving slices of this lane's block
 #pragma unroll
             for (int sp = 0; sp < SPLIT; ++sp) {
                 uint32_t act = 0u;
@@ -871,10 +872,18 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 }
                 if (!act)
                     fill_neg<TC, RD>(mk, a.W, a.H, x0 - a.ox, y0 + sp * RD - a.oy);
-                const unsigned am = __ballot_sync(0xffffffffu, act != 0u);
-                if (lane == 0)
-                    s_mask[it][sp] = am;
+                nib |= (act != 0u ? 1u : 0u) << sp;
             }
+            // queue order (item, lane, slice): word q of the item's mask holds
+            // lanes 8q .. 8q + 7, four slice bits each, so the slices of one
+            // block are neighbours in the queue (distinct rows, and with an
+            // odd window pitch distinct shared-memory banks)
+            uint32_t wq = nib << (4 * (lane & 7));
+            wq |= __shfl_xor_sync(0xffffffffu, wq, 1);
+            wq |= __shfl_xor_sync(0xffffffffu, wq, 2);
+            wq |= __shfl_xor_sync(0xffffffffu, wq, 4);
+            if ((lane & 7) == 0)
+                s_mask[it][lane >> 3] = wq;
         }
         __syncthreads();
         if (warp == 0) {   // queue offsets: exclusive prefix sum of the surviving counts
@@ -884,8 +893,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 int c = 0;
                 if (i < ni)
 #pragma unroll
-                    for (int sp = 0; sp < SPLIT; ++sp)
-                        c += __popc(s_mask[i][sp]);
+                    for (int q = 0; q < 4; ++q)
+                        c += __popc(s_mask[i][q]);
                 int v = c;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -928,15 +937,17 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const unsigned qb = s_qb;
             if (qb != ~0u) {
                 for (int it = warp; it < ni; it += WARPS) {
+                    const int q = lane >> 3, sh = 4 * (lane & 7);
                     unsigned slot = qb + (unsigned)s_off[it];
+                    for (int q2 = 0; q2 < q; ++q2)
+                        slot += (unsigned)__popc(s_mask[it][q2]);
+                    const uint32_t w = s_mask[it][q];
+                    slot += (unsigned)__popc(w & ((1u << sh) - 1u));
+                    const uint32_t nb = (w >> sh) & 15u;
 #pragma unroll
-                    for (int sp = 0; sp < SPLIT; ++sp) {
-                        const uint32_t m = s_mask[it][sp];
-                        if ((m >> lane) & 1u)
-                            a.queue[slot + (unsigned)__popc(m & ((1u << lane) - 1u))] =
-                                ((uint32_t)(r0 + it) << 7) | ((uint32_t)sp << 5) | (uint32_t)lane;
-                        slot += (unsigned)__popc(m);
-                    }
+                    for (int sp = 0; sp < SPLIT; ++sp)
+                        if ((nb >> sp) & 1u)
+                            a.queue[slot++] = ((uint32_t)(r0 + it) << 7) | ((uint32_t)sp << 5) | (uint32_t)lane;
                 }
             }
         } else {
@@ -956,11 +967,12 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     it = lo;
                     int rank = e - s_off[it];
 #pragma unroll
-                    for (int sp = 0; sp < SPLIT; ++sp) {
-                        const int c = __popc(s_mask[it][sp]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = __popc(s_mask[it][q]);
                         if (rank >= 0 && rank < c) {
-                            part = sp;
-                            src = nth_set_bit(s_mask[it][sp], rank);
+                            const int bit = nth_set_bit(s_mask[it][q], rank);
+                            src = 8 * q + (bit >> 2);
+                            part = bit & 3;
                         }
                         rank -= c;
                     }
