@@ -769,7 +769,7 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
     const ScoreArgs sa = top_score_args(m, P, *params);
     const int top = P.L - 1;
     const int nth = m->lv[top].ntheta;
-    const int tgs[] = {1, 3, 5, 9, 15, nth};
+    const int tgs[] = {1, 2, 3, 4, 5, 6, 8, 9, 11, 12, 15, 23, nth};
     cudaEvent_t e0, e1;
     SAM_CU(cudaEventCreate(&e0));
     SAM_CU(cudaEventCreate(&e1));

@@ -396,7 +396,7 @@ def candidates_noalloc(smap, min_score, K, out_kyx, out_s, count, stream=None):
                                         _ptr(out_s), _ptr(count), _stream(stream)), "sam_candidates_noalloc")
 
 
-def autotune(model: Model, images, params: Optional[DetectParams] = None, stream=None, max_out=256):
+def autotune(model: Model, images, params: Optional[DetectParams] = None, stream=None, max_out=512):
     """Time every tiling of the tiled scorer on a (N, H, W) uint8 CUDA batch and keep
     the fastest for `model`.  Returns a list of ((sx, sy, tg, warps), ms) sorted by time."""
     params = params or default_detect_params()
