@@ -148,11 +148,34 @@ CMP_PER_PP = 4
 CMP_PER_CLK_SM = 128.0
 
 
-# DRAM bytes (read + write) of one score_tiled_kernel launch of this
-# workload, from an ncu capture at the tiling below (summary and command in
-# profiles/score_tiled_config2_batch16.md); reported only when the bench
-# runs that tiling, and to be re-taken whenever the kernel changes.
-NCU_SCORE_TRAFFIC = {"tiling": (1, 1, 3, 4, 10), "bytes": 2836992 + 3915264}
+# With early termination the detection path scores the top level in two
+# launches: the edge-presence bound launch (every pose: a bit-sliced count of
+# the points whose 3x3 window holds an edge pixel; poses that cannot reach
+# min_score are written -inf) and the drain launch, in which a lane scores a
+# 2 x TC slice of surviving poses.  Per model point the slice reads
+# (2 + 2) x (TC + 2) staged pixels for 2 x TC poses: 19.2 bytes per
+# pose-point at TC 10, 21.3 at TC 6 (FP32 fields; 16-bit fields half).
+DRAIN_ROWS = 2
+
+
+def slice_bytes_per_pp(cols, precision):
+    px = 8.0 if precision == "fp32" else 4.0
+    return (DRAIN_ROWS + 2) * (cols + 2) * px / (DRAIN_ROWS * cols)
+
+
+# The bound launch's algorithmic work, bit-parallel over 32 poses per word:
+# per model point and pose word one funnel-shift extraction of the dilated
+# edge bitmap and a 3-operation carry-save full adder, 4 logical operations
+# per 32 pose-points; against 64 32-bit logical operations per clock per SM
+# (nominal integer throughput, not measured).
+BOUND_OPS_PER_PP = 4.0 / 32.0
+LOGIC_OPS_PER_CLK_SM = 64.0
+
+# DRAM bytes (read + write) of one drain launch of this workload, from an ncu
+# capture at the tiling below (summary and command in
+# profiles/score_drain_config2_batch16.md); reported only when the bench runs
+# that tiling, and to be re-taken whenever the kernel changes.
+NCU_DRAIN_TRAFFIC = {"tiling": (2, 1, 9, 4, 10), "bytes": 2196992 + 33536}
 
 
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
@@ -603,29 +626,58 @@ def run_gpu(args):
 
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = props.multi_processor_count
     score_ms, score_calls = prof["score_map"]
-    rl = roofline(exec_pp, score_ms / max(1, score_calls), props.multi_processor_count,
-                  float(peaks.get("sm_max_mhz", 2070.0)),
-                  traffic=args.traffic if args.traffic is not None else (
-                      NCU_SCORE_TRAFFIC["bytes"]
-                      if tuple(sam.model_tiling(model, params.precision, B)) == NCU_SCORE_TRAFFIC["tiling"] else None))
-    rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {props.multi_processor_count} SMs x 128 shared-memory "
-                         f"bytes/clk; 13.33 algorithmic bytes per pose-point (8x6 translation block)")
+    tiling = tuple(sam.model_tiling(model, params.precision, B))
+    bound_ms, bound_calls = prof.get("score_bound", (0.0, 0))
+    drain_ms, drain_calls = prof.get("score_drain", (0.0, 0))
+    smem_peak = SMEM_B_PER_CLK_SM * nsm * sm_mhz * 1e6 / 1e12
+    if drain_calls:
+        # two-launch form: the roofline of the drain launch (the slower of
+        # the two at this workload), the bound launch beside it
+        d_ms = drain_ms / drain_calls
+        b_ms = bound_ms / max(1, bound_calls)
+        bpp = slice_bytes_per_pp(tiling[4], args.precision)
+        ach = exec_pp * bpp / (d_ms * 1e-3) / 1e12
+        rl = {"bound": "smem", "achieved": round(ach, 3), "peak": round(smem_peak, 3), "unit": "TB/s",
+              "frac": round(ach / smem_peak, 4),
+              "traffic": args.traffic if args.traffic is not None else (
+                  NCU_DRAIN_TRAFFIC["bytes"] if tiling == NCU_DRAIN_TRAFFIC["tiling"] else None),
+              "kernel": "score_drain_kernel (surviving 2-row slices of the top-level search)",
+              "ms_per_launch": round(d_ms, 4),
+              "peak_source": (f"{peak_kind} sm_max_mhz x {nsm} SMs x 128 shared-memory bytes/clk; "
+                              f"{bpp:.2f} algorithmic bytes per executed pose-point (2 x {tiling[4]} slice)")}
+        ops_peak = LOGIC_OPS_PER_CLK_SM * nsm * sm_mhz * 1e6 / 1e12
+        ops_ach = pp_step * BOUND_OPS_PER_PP / (b_ms * 1e-3) / 1e12
+        rl["bound_launch"] = {"kernel": "score_tiled_kernel (edge-presence bound of every pose)",
+                              "ms_per_launch": round(b_ms, 4), "bound": "alu",
+                              "achieved": round(ops_ach, 3), "peak": round(ops_peak, 3), "unit": "Tops/s",
+                              "frac": round(ops_ach / ops_peak, 4),
+                              "peak_source": "nominal 64 logical ops/clk/SM x SMs x sm_max_mhz; 4 ops per "
+                                             "32 pose-points (bit extraction + carry-save adder)"}
+        rl["score_map_ms_per_step"] = round(score_ms / max(1, score_calls), 4)
+        rl["dominant"] = "drain" if d_ms >= b_ms else "bound"
+    else:
+        rl = roofline(exec_pp, score_ms / max(1, score_calls), nsm, sm_mhz, traffic=args.traffic)
+        rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {nsm} SMs x 128 shared-memory "
+                             f"bytes/clk; 13.33 algorithmic bytes per pose-point (8x6 translation block)")
+        rl["ms_per_launch"] = round(score_ms / max(1, score_calls), 4)
     clocks = clk.summary()
     if clocks.get("sm_mhz"):
-        rl["frac_at_observed_clock"] = round(rl["frac"] * float(peaks.get("sm_max_mhz", 2070.0)) / clocks["sm_mhz"], 4)
+        rl["frac_at_observed_clock"] = round(rl["frac"] * sm_mhz / clocks["sm_mhz"], 4)
     fms, fcalls = prof_full["score_map"]
     rl_full = roofline(pp_step, fms / max(1, fcalls), props.multi_processor_count,
                        float(peaks.get("sm_max_mhz", 2070.0)))
     rl["no_early_termination"] = {"ms_per_launch": round(fms / max(1, fcalls), 4), "achieved": rl_full["achieved"],
-                                  "frac": rl_full["frac"]}
-    rl["ms_per_launch"] = round(score_ms / max(1, score_calls), 4)
+                                  "frac": rl_full["frac"], "bound": "smem",
+                                  "what": "score_tiled_kernel, every pose fully scored, 13.33 B per pose-point"}
     rl_nom = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
                       float(peaks.get("sm_max_mhz", 2070.0)))
     rl["executed_pose_points_per_launch"] = int(exec_pp)
     rl["nominal_pose_points_per_launch"] = int(pp_step)
     rl["nominal"] = {"achieved": rl_nom["achieved"], "frac": rl_nom["frac"],
-                     "what": "nominal pose-points (early termination not subtracted) x 13.33 B / launch time"}
+                     "what": "nominal pose-points (early termination not subtracted) x 13.33 B / score-map time"}
     rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, B)))
     rl["tiling"]["autotuned"] = bool(tuning)
     if tuning:

@@ -429,11 +429,14 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
  * stage; sam_profile_read waits for the recorded events and adds their
  * elapsed device times to per-stage totals (so an enabled profiler adds no
  * host work between calls).  Stages: 0 pyramid, 1 gradient,
- * 2 exhaustive score map, 3 candidates, 4 refinement, 5 NMS.
+ * 2 exhaustive score map, 3 candidates, 4 refinement, 5 NMS, and within
+ * stage 2 the tiled scorer's launches: 6 the edge-presence bound launch (the
+ * whole scorer when it runs in one launch), 7 the launch that scores the
+ * surviving poses (two-launch form only).
  * sam_profile_read copies up to n totals (milliseconds) and call counts and
  * resets them.  Process-wide; not thread-safe.
  * ------------------------------------------------------------------------- */
-#define SAM_NUM_STAGES 6
+#define SAM_NUM_STAGES 8
 void sam_profile_enable(int on);
 
 /* Graph mode (process-wide, on by default; the paper has no counterpart).

@@ -24,25 +24,30 @@ namespace {
 
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
+}  // namespace
+
 // ---- stage timing ----
 // Stage events go to a pool of event pairs; their elapsed times are summed
 // only when the totals are read (or the pool is full), so an enabled profiler
 // adds two event records per stage to a call and no host work after it.
+// Stages may nest (the score map's launches inside the score-map stage).
 struct Profiler {
     bool on = false;
     static constexpr int kPool = 4096;
     std::vector<cudaEvent_t> ev;     // 2 per slot
     std::vector<int> stage_of;       // stage of each recorded slot
-    int used = 0;
-    int open[SAM_NUM_STAGES] = {};   // slot of each stage's begin
+    int used = 0;                    // slots taken
+    int n_open = 0;                  // stages begun and not yet ended
+    int open[SAM_NUM_STAGES] = {};   // slot of each open stage (-1: not recorded)
     double ms[SAM_NUM_STAGES] = {};
     int calls[SAM_NUM_STAGES] = {};
 };
-Profiler g_prof;
+static Profiler g_prof;
 
-// Sum every recorded pair (waits for the last one) and empty the pool.
+// Sum every recorded pair (waits for the last one) and empty the pool; only
+// while no stage is open.
 void prof_flush() {
-    if (g_prof.used == 0)
+    if (g_prof.used == 0 || g_prof.n_open > 0)
         return;
     cudaEventSynchronize(g_prof.ev[2 * (g_prof.used - 1) + 1]);
     for (int i = 0; i < g_prof.used; ++i) {
@@ -56,10 +61,14 @@ void prof_flush() {
 }
 
 void prof_begin(int stage, cudaStream_t st) {
-    if (!g_prof.on)
+    if (!g_prof.on || stage < 0 || stage >= SAM_NUM_STAGES)
         return;
+    ++g_prof.n_open;
+    g_prof.open[stage] = -1;
     if (g_prof.used == Profiler::kPool)
         prof_flush();
+    if (g_prof.used == Profiler::kPool)
+        return;   // pool full inside an open stage: this one is not recorded
     const int slot = g_prof.used;
     if ((int)g_prof.stage_of.size() <= slot) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -69,20 +78,25 @@ void prof_begin(int stage, cudaStream_t st) {
         g_prof.ev.push_back(b);
         g_prof.stage_of.push_back(0);
     }
+    ++g_prof.used;
     g_prof.open[stage] = slot;
     g_prof.stage_of[slot] = stage;
     cudaEventRecord(g_prof.ev[2 * slot], st);
+    cudaEventRecord(g_prof.ev[2 * slot + 1], st);   // replaced by prof_end
 }
 
 void prof_end(int stage, cudaStream_t st) {
-    if (!g_prof.on)
+    if (!g_prof.on || stage < 0 || stage >= SAM_NUM_STAGES)
         return;
+    if (g_prof.n_open > 0)
+        --g_prof.n_open;
     const int slot = g_prof.open[stage];
-    if (slot != g_prof.used || (int)g_prof.stage_of.size() <= slot)
-        return;
-    cudaEventRecord(g_prof.ev[2 * slot + 1], st);
-    ++g_prof.used;
+    g_prof.open[stage] = -1;
+    if (slot >= 0)
+        cudaEventRecord(g_prof.ev[2 * slot + 1], st);
 }
+
+namespace {
 
 // Device buffers of one detection call (all images of a batch).
 struct Plan {
@@ -1005,6 +1019,9 @@ void sam_set_graph_mode(int on) { g_graph_mode = on != 0; }
 long long sam_kernel_launches(void) { return g_launches.load(); }
 
 int sam_profile_read(float *ms, int *calls, int n) {
+    // no call is in flight between API calls: a stage an error path left
+    // open has both its events recorded
+    g_prof.n_open = 0;
     prof_flush();
     const int m = n < SAM_NUM_STAGES ? n : SAM_NUM_STAGES;
     for (int s = 0; s < m; ++s) {

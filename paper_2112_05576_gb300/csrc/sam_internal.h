@@ -197,6 +197,11 @@ struct PoseWindow {
     int x0, y0, gw, gh, k0, nk;
 };
 
+// Stage timing (api.cu): events around a stage when sam_profile_enable is on.
+void prof_begin(int stage, cudaStream_t st);
+void prof_end(int stage, cudaStream_t st);
+constexpr int kStageScoreBound = 6, kStageScoreDrain = 7;
+
 // Device storage of the two-launch form (a slice of the caller's workspace).
 struct DrainQueue {
     void *base;    // 256-byte aligned

@@ -1290,8 +1290,10 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
+    prof_begin(kStageScoreBound, st);
     kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
     count_launches(1);
+    prof_end(kStageScoreBound, st);
     e = cudaGetLastError();
     if (e != cudaSuccess || !a.queue)
         return e;
@@ -1310,8 +1312,10 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
         (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dk, WARPS * 32, dsmem)) != cudaSuccess)
         return e;
     const unsigned ctas = (unsigned)std::max(1, std::min(sms * std::max(occ, 1), (int)std::min(a.tcap, 1u << 20)));
+    prof_begin(kStageScoreDrain, st);
     dk<<<ctas, WARPS * 32, dsmem, st>>>(tm, a);
     count_launches(1);
+    prof_end(kStageScoreDrain, st);
     return cudaGetLastError();
 }
 
