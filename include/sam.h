@@ -250,7 +250,11 @@ sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, i
  *   map     device float array of num_angles * gh * gw.
  * With early_termination, poses proved below min_score are written -inf.
  * The tiled kernel serves FP32 SAM_LAYOUT_PAIRS fields at step 1 when its
- * shared-memory window fits; everything else uses the generic kernel.
+ * shared-memory window fits; everything else uses the generic kernel.  With
+ * early termination the tiled kernel runs in its two-launch form (an
+ * edge-presence bound launch, then a launch over the surviving poses) with a
+ * queue taken from the device's default stream-ordered memory pool
+ * (cudaMallocAsync / cudaFreeAsync on `stream`).
  * Errors: SAM_ERR_ARG, SAM_ERR_CUDA, SAM_ERR_TIMEOUT (a bounded wait for the
  * window's TMA copy gave up; checked on the next synchronising call). */
 sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int layout,
@@ -300,7 +304,8 @@ void sam_get_score_kernel(int *kernel, int *sx, int *sy, int *tg, int *warps, in
  * Prepares the top-level field of the caller's batch (arguments as for
  * sam_detect_batch, images on the device), then times the tiled kernel with
  * every tiling of its candidate set (super-tile 1..3 x 1..2 warp tiles,
- * angles per CTA 1, 3, 5, 9, 15 or all, 4 or 8 warps, 6 or 10 pose columns
+ * angles per CTA 1, 2, 3, 4, 5, 6, 8, 9, 11, 12, 15, 23 or all, 4 or 8
+ * warps, 6 or 10 pose columns
  * per thread; tilings whose window does not fit are skipped) and the
  * chunked kernel with its CTA tiles (2x2, 4x1, 1x4 of 4 warps; 2x4, 4x2 of
  * 8 warps; reported with tg = 0) using CUDA events on `stream`, and keeps

@@ -926,7 +926,25 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
     sa.map = map;
     sa.map_img = 0;
     sa.count = 1;
-    return launch_score_map(m, level, sa, nullptr, (cudaStream_t)stream) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    // early termination at step 1: the tiled scorer's two-launch form, its
+    // queue in stream-ordered memory of the device's default pool (else one
+    // launch)
+    void *q = nullptr;
+    if (early_termination && step_x == 1 && step_y == 1) {
+        const size_t qb = drain_queue_bytes(1, w, h, m->lv[level].ntheta);
+        if (cudaMallocAsync(&q, qb, st) == cudaSuccess) {
+            sa.queue = q;
+            sa.queue_bytes = qb;
+        } else {
+            (void)cudaGetLastError();
+            q = nullptr;
+        }
+    }
+    const cudaError_t e = launch_score_map(m, level, sa, nullptr, st);
+    if (q && cudaFreeAsync(q, st) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    return e == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 size_t sam_score_window_scratch_bytes(size_t max_rescored) { return rescore_scratch_bytes(max_rescored); }

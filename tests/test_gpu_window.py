@@ -234,3 +234,32 @@ def test_angle_blocks_with_library_steps_merge_to_full_search(big_case):
         lists = [shard.block_candidates(*shard.angle_block(nth, world, r), nth, h, w, 0.05, K, score_fn, cand_fn)
                  for r in range(world)]
         assert shard.merge_candidates(lists, K, h, w) == want
+
+
+def test_tiled_window_early_termination_exact_safe(small_case):
+    # the tiled scorer over a pose window runs in one launch (bound pass,
+    # then the surviving slices drained by the same CTA): every pose proved
+    # below min_score is -inf and below it in the oracle, every other pose
+    # matches the oracle, and no pose at or above min_score is pruned
+    tmpl, img, model = small_case
+    truth = synth.config1_scene()[2]
+    om = oracle.create_model(tmpl, 30, 60, 1, 4.0)
+    ofield = oracle.search_fields(img, 1, 30)[0]
+    k0 = int(round(truth[0][2] / 4.0)) % 90 - 1
+    ref = oracle.score_map_range(ofield, om.points[0], k0, 3, om.dtheta(0), nbhd=3, polarity=om.polarity)
+    f = _pairs_field(img, 30, sam.FP32)
+    h, w = img.shape
+    sam.set_score_kernel(2, 2, 1, 3, 8)
+    try:
+        for win in ((0, 0, w, h, k0, 3), (37, 11, 201, 157, k0 + 1, 2)):
+            x0, y0, gw, gh, wk0, nk = win
+            sl = ref[wk0 - k0:wk0 - k0 + nk, y0:y0 + gh, x0:x0 + gw]
+            for ms in (0.5, 0.7):
+                got = _window(model, f, img, sam.FP32, win, early=1, min_score=ms)
+                pruned = np.isneginf(got)
+                assert pruned.any() and not pruned.all()
+                assert np.all(sl[pruned] < ms)
+                assert not np.any(pruned & (sl >= ms))
+                assert np.max(np.abs(got[~pruned] - sl[~pruned])) < TOL
+    finally:
+        sam.set_score_kernel(0)
