@@ -173,9 +173,9 @@ LOGIC_OPS_PER_CLK_SM = 64.0
 
 # DRAM bytes (read + write) of one drain launch of this workload, from an ncu
 # capture at the tiling below (summary and command in
-# profiles/score_drain_config2_batch16.md); reported only when the bench runs
+# profiles/score_map_config2_batch16.md); reported only when the bench runs
 # that tiling, and to be re-taken whenever the kernel changes.
-NCU_DRAIN_TRAFFIC = {"tiling": (2, 1, 9, 4, 10), "bytes": 2196992 + 33536}
+NCU_DRAIN_TRAFFIC = {"tiling": (2, 1, 11, 4, 10), "bytes": 2197248 + 35072}
 
 
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
