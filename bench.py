@@ -148,13 +148,14 @@ CMP_PER_PP = 4
 CMP_PER_CLK_SM = 128.0
 
 
-# With early termination the detection path scores the top level in two
-# launches: the edge-presence bound launch (every pose: a bit-sliced count of
-# the points whose 3x3 window holds an edge pixel; poses that cannot reach
-# min_score are written -inf) and the drain launch, in which a lane scores a
-# 2 x TC slice of surviving poses.  Per model point the slice reads
-# (2 + 2) x (TC + 2) staged pixels for 2 x TC poses: 19.2 bytes per
-# pose-point at TC 10, 21.3 at TC 6 (FP32 fields; 16-bit fields half).
+# With early termination the detection path scores the top level with one
+# persistent kernel (score_fused_kernel) doing two kinds of work: the
+# edge-presence bound of every pose (a bit-sliced count of the points whose
+# 3x3 window holds an edge pixel; poses that cannot reach min_score are
+# written -inf) and the dot products of the surviving poses, a lane scoring a
+# 2 x TC slice.  Per model point the slice reads (2 + 2) x (TC + 2) staged
+# pixels for 2 x TC poses: 19.2 bytes per pose-point at TC 10, 21.3 at TC 6
+# (FP32 fields; 16-bit fields half).
 DRAIN_ROWS = 2
 
 
@@ -163,19 +164,19 @@ def slice_bytes_per_pp(cols, precision):
     return (DRAIN_ROWS + 2) * (cols + 2) * px / (DRAIN_ROWS * cols)
 
 
-# The bound launch's algorithmic work, bit-parallel over 32 poses per word:
-# per model point and pose word one funnel-shift extraction of the dilated
-# edge bitmap and a 3-operation carry-save full adder, 4 logical operations
-# per 32 pose-points; against 64 32-bit logical operations per clock per SM
+# The bound's algorithmic work, bit-parallel over 32 poses per word: per
+# model point and pose word one funnel-shift extraction of the dilated edge
+# bitmap and a 3-operation carry-save full adder, 4 logical operations per 32
+# pose-points; against 64 32-bit logical operations per clock per SM
 # (nominal integer throughput, not measured).
 BOUND_OPS_PER_PP = 4.0 / 32.0
 LOGIC_OPS_PER_CLK_SM = 64.0
 
-# DRAM bytes (read + write) of one drain launch of this workload, from an ncu
-# capture at the tiling below (summary and command in
+# DRAM bytes (read + write) of one score_fused_kernel launch of this
+# workload, from an ncu capture at the tiling below (summary and command in
 # profiles/score_map_config2_batch16.md); reported only when the bench runs
 # that tiling, and to be re-taken whenever the kernel changes.
-NCU_DRAIN_TRAFFIC = {"tiling": (2, 1, 11, 4, 10), "bytes": 2197248 + 35072}
+NCU_FUSED_TRAFFIC = None
 
 
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
@@ -630,34 +631,32 @@ def run_gpu(args):
     nsm = props.multi_processor_count
     score_ms, score_calls = prof["score_map"]
     tiling = tuple(sam.model_tiling(model, params.precision, B))
-    bound_ms, bound_calls = prof.get("score_bound", (0.0, 0))
-    drain_ms, drain_calls = prof.get("score_drain", (0.0, 0))
+    tiled_ms, tiled_calls = prof.get("score_tiled", (0.0, 0))
     smem_peak = SMEM_B_PER_CLK_SM * nsm * sm_mhz * 1e6 / 1e12
-    if drain_calls:
-        # two-launch form: the roofline of the drain launch (the slower of
-        # the two at this workload), the bound launch beside it
-        d_ms = drain_ms / drain_calls
-        b_ms = bound_ms / max(1, bound_calls)
+    if args.early and tiled_calls:
+        # the persistent scorer: its dot products against the shared-memory
+        # roofline, its bound against the logic-op one, and their sum
+        k_ms = tiled_ms / tiled_calls
         bpp = slice_bytes_per_pp(tiling[4], args.precision)
-        ach = exec_pp * bpp / (d_ms * 1e-3) / 1e12
+        ach = exec_pp * bpp / (k_ms * 1e-3) / 1e12
+        ops_peak = LOGIC_OPS_PER_CLK_SM * nsm * sm_mhz * 1e6 / 1e12
+        ops_ach = pp_step * BOUND_OPS_PER_PP / (k_ms * 1e-3) / 1e12
         rl = {"bound": "smem", "achieved": round(ach, 3), "peak": round(smem_peak, 3), "unit": "TB/s",
               "frac": round(ach / smem_peak, 4),
               "traffic": args.traffic if args.traffic is not None else (
-                  NCU_DRAIN_TRAFFIC["bytes"] if tiling == NCU_DRAIN_TRAFFIC["tiling"] else None),
-              "kernel": "score_drain_kernel (surviving 2-row slices of the top-level search)",
-              "ms_per_launch": round(d_ms, 4),
+                  NCU_FUSED_TRAFFIC["bytes"] if NCU_FUSED_TRAFFIC and tiling == NCU_FUSED_TRAFFIC["tiling"] else None),
+              "kernel": "score_fused_kernel (persistent: edge-presence bound of every pose, then the surviving "
+                        "2-row slices)",
+              "ms_per_launch": round(k_ms, 4),
               "peak_source": (f"{peak_kind} sm_max_mhz x {nsm} SMs x 128 shared-memory bytes/clk; "
-                              f"{bpp:.2f} algorithmic bytes per executed pose-point (2 x {tiling[4]} slice)")}
-        ops_peak = LOGIC_OPS_PER_CLK_SM * nsm * sm_mhz * 1e6 / 1e12
-        ops_ach = pp_step * BOUND_OPS_PER_PP / (b_ms * 1e-3) / 1e12
-        rl["bound_launch"] = {"kernel": "score_tiled_kernel (edge-presence bound of every pose)",
-                              "ms_per_launch": round(b_ms, 4), "bound": "alu",
-                              "achieved": round(ops_ach, 3), "peak": round(ops_peak, 3), "unit": "Tops/s",
-                              "frac": round(ops_ach / ops_peak, 4),
-                              "peak_source": "nominal 64 logical ops/clk/SM x SMs x sm_max_mhz; 4 ops per "
-                                             "32 pose-points (bit extraction + carry-save adder)"}
-        rl["score_map_ms_per_step"] = round(score_ms / max(1, score_calls), 4)
-        rl["dominant"] = "drain" if d_ms >= b_ms else "bound"
+                              f"{bpp:.2f} algorithmic bytes per executed pose-point (2 x {tiling[4]} slice)"),
+              "alu": {"what": "the bound: 4 logical ops per 32 pose-points, all poses", "achieved": round(ops_ach, 3),
+                      "peak": round(ops_peak, 3), "unit": "Tops/s", "frac": round(ops_ach / ops_peak, 4),
+                      "peak_source": "nominal 64 logical ops/clk/SM x SMs x sm_max_mhz"},
+              "combined_frac": round(ach / smem_peak + ops_ach / ops_peak, 4),
+              "combined_what": "(dot-product time at the shared-memory peak + bound time at the logic-op peak) "
+                               "/ kernel time",
+              "score_map_ms_per_step": round(score_ms / max(1, score_calls), 4)}
     else:
         rl = roofline(exec_pp, score_ms / max(1, score_calls), nsm, sm_mhz, traffic=args.traffic)
         rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {nsm} SMs x 128 shared-memory "

@@ -251,10 +251,10 @@ sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, i
  * With early_termination, poses proved below min_score are written -inf.
  * The tiled kernel serves FP32 SAM_LAYOUT_PAIRS fields at step 1 when its
  * shared-memory window fits; everything else uses the generic kernel.  With
- * early termination the tiled kernel runs in its two-launch form (an
- * edge-presence bound launch, then a launch over the surviving poses) with a
- * queue taken from the device's default stream-ordered memory pool
- * (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * early termination the tiled kernel runs in its persistent form (work units
+ * of the edge-presence bound, then the surviving poses, pulled by resident
+ * CTAs) with a queue taken from the device's default stream-ordered memory
+ * pool (cudaMallocAsync / cudaFreeAsync on `stream`).
  * Errors: SAM_ERR_ARG, SAM_ERR_CUDA, SAM_ERR_TIMEOUT (a bounded wait for the
  * window's TMA copy gave up; checked on the next synchronising call). */
 sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int h, int precision, int layout,
@@ -435,13 +435,11 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
  * elapsed device times to per-stage totals (so an enabled profiler adds no
  * host work between calls).  Stages: 0 pyramid, 1 gradient,
  * 2 exhaustive score map, 3 candidates, 4 refinement, 5 NMS, and within
- * stage 2 the tiled scorer's launches: 6 the edge-presence bound launch (the
- * whole scorer when it runs in one launch), 7 the launch that scores the
- * surviving poses (two-launch form only).
+ * stage 2: 6 the tiled scorer's launch.
  * sam_profile_read copies up to n totals (milliseconds) and call counts and
  * resets them.  Process-wide; not thread-safe.
  * ------------------------------------------------------------------------- */
-#define SAM_NUM_STAGES 8
+#define SAM_NUM_STAGES 7
 void sam_profile_enable(int on);
 
 /* Graph mode (process-wide, on by default; the paper has no counterpart).

@@ -114,7 +114,7 @@ struct Plan {
     size_t off_scratch = 0;
     size_t off_rescore = 0;          // FP32 rescoring list (16-bit precisions)
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
-    size_t off_queue = 0, queue_bytes = 0;   // two-launch storage of the tiled scorer
+    size_t off_queue = 0, queue_bytes = 0;   // persistent-form storage of the tiled scorer
     size_t total = 0;
 };
 
@@ -927,9 +927,9 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
     sa.map_img = 0;
     sa.count = 1;
     cudaStream_t st = (cudaStream_t)stream;
-    // early termination at step 1: the tiled scorer's two-launch form, its
+    // early termination at step 1: the tiled scorer's persistent form, its
     // queue in stream-ordered memory of the device's default pool (else one
-    // launch)
+    // CTA per work unit)
     void *q = nullptr;
     if (early_termination && step_x == 1 && step_y == 1) {
         const size_t qb = drain_queue_bytes(1, w, h, m->lv[level].ntheta);

@@ -178,7 +178,7 @@ struct ScoreArgs {
     float *map;
     size_t map_img;   // floats per image
     int count;
-    void *queue = nullptr;     // two-launch storage of the tiled scorer (optional)
+    void *queue = nullptr;     // persistent-form storage of the tiled scorer (optional)
     size_t queue_bytes = 0;
 };
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
@@ -200,19 +200,19 @@ struct PoseWindow {
 // Stage timing (api.cu): events around a stage when sam_profile_enable is on.
 void prof_begin(int stage, cudaStream_t st);
 void prof_end(int stage, cudaStream_t st);
-constexpr int kStageScoreBound = 6, kStageScoreDrain = 7;
+constexpr int kStageScoreBound = 6;   // the tiled scorer's launch (inside stage 2)
 
-// Device storage of the two-launch form (a slice of the caller's workspace).
+// Device storage of the persistent form (a slice of the caller's workspace).
 struct DrainQueue {
     void *base;    // 256-byte aligned
     size_t bytes;
 };
-// Workspace bytes that cover the two-launch form of every tiling the
+// Workspace bytes that cover the persistent form of every tiling the
 // autotuner tries for a gw x gh map with nth angles over `count` images.
 size_t drain_queue_bytes(int count, int gw, int gh, int nth);
 
-// The tiled scorer; with `queue` (and early termination) in the two-launch
-// form, else in one launch.
+// The tiled scorer; with `queue` (and early termination) in the persistent
+// form, else one CTA per work unit.
 cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field, int precision, int wp,
                                size_t field_img_px, int W, int H, int count, int nbhd, int polarity, float min_score,
                                int early, float *map, size_t map_img, const TileConfig &cfg, cudaStream_t st,
@@ -238,14 +238,14 @@ struct TiledArgs {
     int *err;                   // device error flag (bounded waits)
     unsigned long long *exec;   // executed pose-point counter
     int tiles_y;                // super-tiles along y
-    // Two-launch form (queue non-null, bound on): the bound launch appends
-    // each CTA's surviving blocks to `queue` and one task per CTA-sized batch
-    // of them to `tasks`; the drain launch scores the tasks on every SM.
-    uint32_t *queue;            // (item << 5) | lane, one contiguous run per CTA round
-    int4 *tasks;                // {unit, first entry, entries, 0}
-    unsigned *qctr;             // [0] entries, [1] tasks, [2] next task (zeroed before the bound launch)
+    // Persistent form (queue non-null, bound on): a unit's bound pass
+    // appends its surviving slices to `queue` and one task per CTA-sized
+    // batch of them to `tasks`; CTAs score the tasks once the units are out.
+    uint32_t *queue;            // (item << 7) | (slice << 5) | lane, one contiguous run per CTA round
+    int4 *tasks;                // {unit, first entry, entries, published flag}
+    unsigned *qctr;             // [0] entries, [1] tasks, [2] next task, [3] next unit, [4] units done
     unsigned qcap, tcap;        // capacities (entries, tasks)
-    int units;                  // work units (CTAs) of the bound launch
+    int units;                  // work units (super-tile x angle group x image)
 };
 
 
@@ -313,7 +313,9 @@ cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_it
 // bxw x byw pixels (edge pixels and their 3x3 dilation, one bit per pixel,
 // rows padded by 3 words for the funnel shifts of the bound pass).
 __host__ __device__ inline int edge_bitmap_words(int bxw) { return (bxw + 31) / 32 + 3; }
-__host__ __device__ inline size_t edge_bitmap_bytes(int bxw, int byw) { return 2 * (size_t)byw * edge_bitmap_words(bxw) * 4; }
+// 4 planes of edge pixels by the quadrants they can serve and their 4 dilated
+// copies (score_tiled_kernels.cuh, build_edge_bits).
+__host__ __device__ inline size_t edge_bitmap_bytes(int bxw, int byw) { return 8 * (size_t)byw * edge_bitmap_words(bxw) * 4; }
 
 // Score-kernel selection (process-wide; sam_set_score_kernel).
 struct ScoreChoice {

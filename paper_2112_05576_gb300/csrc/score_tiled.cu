@@ -217,7 +217,7 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.tiles_y = tiles_y;
     const int groups = (pw.nk + cfg.tg - 1) / cfg.tg;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)groups, (unsigned)count);
-    // two-launch form when the bound is on and the storage holds every block
+    // persistent form when the bound is on and the storage holds every slice
     a.queue = nullptr;
     a.tasks = nullptr;
     a.qctr = nullptr;
@@ -238,7 +238,8 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
             a.queue = (uint32_t *)(b + 256 + tcap * 16);
             a.qcap = (unsigned)qcap;
             a.tcap = (unsigned)tcap;
-            cudaError_t e = cudaMemsetAsync(a.qctr, 0, 16, st);
+            // counters and the tasks' publication flags start at zero
+            cudaError_t e = cudaMemsetAsync(b, 0, 256 + tcap * 16, st);
             if (e != cudaSuccess)
                 return e;
         }

@@ -248,9 +248,9 @@ struct TileWork {
     unsigned long long *exec;   // executed pose-point counter
     int emin;                   // edge-presence bound (0: off)
     int byw;                    // window rows
-    uint32_t *bits;             // 2 edge bitmaps of the window (edge_bitmap_bytes)
+    uint32_t *bits;             // edge bitmaps of the window (edge_bitmap_bytes: 4 + 4 planes)
     int *err;                   // device error flag
-    // two-launch form (queue non-null): where the surviving blocks go
+    // persistent form (queue non-null): where the surviving slices go
     uint32_t *queue;
     int4 *tasks;
     unsigned *qctr;
@@ -258,48 +258,91 @@ struct TileWork {
     int unit;                   // this CTA's work unit
 };
 
+// Quadrant of a non-zero vector: 0 for angles in [0, 90) degrees, 1 for
+// [90, 180), 2 for [180, 270), 3 for [270, 360), decided by signs alone.  For
+// u in quadrant q and v in quadrant q + 2 (mod 4) both products of u . v are
+// <= 0 and one is < 0, and a rounded product keeps its sign, so the dot
+// product is <= 0 however it is rounded.
+__device__ __forceinline__ int quadrant(float x, float y) {
+    return y > 0.f ? (x > 0.f ? 0 : 1) : (y < 0.f ? (x < 0.f ? 2 : 3) : (x > 0.f ? 0 : 2));
+}
+
 // Edge bitmaps of a staged window (all threads of the CTA; ends with a CTA
-// barrier): E[r][x] = pixel x of window row r is an edge pixel (non-zero unit
-// vector), then D = E dilated by 3x3, so D at a point's projected centre is
-// set iff its neighbouring-search window holds an edge pixel.
-template <typename E, int NTHREADS>
-__device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *win, int pp, int byw, uint32_t *ebits,
-                                                uint32_t *dbits) {
+// barrier).  Plane q (q < 4, or only q = 0 with POL) of N: bit x of window row
+// r is set iff pixel x is an edge pixel (non-zero unit vector) whose
+// direction is not in the quadrant opposite q (with POL: any edge pixel).
+// C = each plane of N dilated by 3x3: C_q at a point's projected centre is
+// set iff its neighbouring-search window holds an edge pixel that can give a
+// positive vote to a model direction in quadrant q (Eq. (1): p . w <= 0 for
+// opposite quadrants, and pixels that are not edges give 0).
+template <typename E, int NTHREADS, bool POL>
+__device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *win, int pp, int byw, uint32_t *nbits,
+                                                uint32_t *cbits) {
+    constexpr int NQ = POL ? 1 : 4;
     const int dmw = edge_bitmap_words(2 * pp), nw = (2 * pp + 31) / 32;
+    const size_t plane = (size_t)byw * dmw;
     for (int idx = threadIdx.x; idx < byw * dmw; idx += NTHREADS) {
         const int r = idx / dmw, wi = idx - r * dmw;
-        uint32_t e = 0;
+        uint32_t e[NQ];
+#pragma unroll
+        for (int b = 0; b < NQ; ++b)
+            e[b] = 0u;
         if (wi < nw) {
             const typename Pairs<E>::Raw *row = win + (size_t)r * pp;
 #pragma unroll 4
             for (int q = 0; q < 16; ++q) {
                 const int pq = wi * 16 + q;
                 if (pq < pp) {
-                    const float4 v = Pairs<E>::get(row, pq);
-                    e |= (uint32_t)(v.x != 0.f || v.z != 0.f) << (2 * q);
-                    e |= (uint32_t)(v.y != 0.f || v.w != 0.f) << (2 * q + 1);
+                    const float4 v = Pairs<E>::get(row, pq);   // {x0, x1, y0, y1}
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float x = h ? v.y : v.x, y = h ? v.w : v.z;
+                        if (x != 0.f || y != 0.f) {
+                            if (POL) {
+                                e[0] |= 1u << (2 * q + h);
+                            } else {
+                                const int opp = (quadrant(x, y) + 2) & 3;   // the plane it cannot serve
+#pragma unroll
+                                for (int b = 0; b < NQ; ++b)
+                                    if (b != opp)
+                                        e[b] |= 1u << (2 * q + h);
+                            }
+                        }
+                    }
                 }
             }
         }
-        ebits[idx] = e;
+#pragma unroll
+        for (int b = 0; b < NQ; ++b)
+            nbits[b * plane + idx] = e[b];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < byw * dmw; idx += NTHREADS) {
-        const int r = idx / dmw, wi = idx - r * dmw;
+    for (int idx = threadIdx.x; idx < NQ * byw * dmw; idx += NTHREADS) {
+        const int b = idx / (byw * dmw), rest = idx - b * (byw * dmw);
+        const int r = rest / dmw, wi = rest - r * dmw;
         uint32_t d = 0;
         for (int dr = -1; dr <= 1; ++dr) {
             const int rr = r + dr;
             if (rr < 0 || rr >= byw)
                 continue;
-            const uint32_t *er = ebits + (size_t)rr * dmw;
+            const uint32_t *er = nbits + b * plane + (size_t)rr * dmw;
             const uint32_t c = er[wi], lw = wi > 0 ? er[wi - 1] : 0u, rw = wi + 1 < dmw ? er[wi + 1] : 0u;
             d |= c | (c << 1) | (lw >> 31) | (c >> 1) | (rw << 31);
         }
-        dbits[idx] = d;
+        cbits[idx] = d;
     }
     __syncthreads();
 }
 
+// Global-memory flag accesses of the persistent form (GPU scope).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 // Items (angle x warp tile) whose surviving blocks one queue round holds.
 constexpr int kQueueItems = 128;
 // Pose rows per lane when the surviving blocks are scored (TR / RD lanes
@@ -448,61 +491,85 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
 }
 
-// Drain launch of the two-launch form: persistent CTAs pull tasks (a work
-// unit and a run of its surviving blocks from the bound launch), stage the
-// unit's window and score the run, TR / RD lanes per block as in the
-// one-launch form.  A heavy unit's blocks so spread over many SMs.
+// Persistent form (detection with early termination): CTAs pull work from
+// two lists.  First the work units of the bound pass (counter qctr[3]): a
+// unit's window is staged, every pose's edge-presence bound computed, slices
+// with no pose that can reach min_score written -inf and the others queued
+// as tasks of CH slices, each published by a release flag.  Once the units
+// are handed out, the tasks (counter qctr[2]): the task's unit window is
+// staged and its slices scored, one per lane.  A CTA waits for a task that
+// is claimed but not yet published; the wait ends when its producer (a
+// resident CTA working on a unit) publishes it, when every unit is done
+// (qctr[4]) and no such task exists, or after 1 s (error flag).
 template <typename E, int NB, bool POL, int WARPS, int TC>
-__global__ void __launch_bounds__(WARPS * 32) score_drain_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TiledArgs a) {
     using Raw = typename Pairs<E>::Raw;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(smem_raw + pad +
+                                                  (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15));
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_org[2];
-    __shared__ int s_task[4];   // state (-1 end, 0 skip, 1 run), unit, first entry, entries
+    __shared__ int s_job[4];   // kind (0 end, 1 unit, 2 task), unit, first entry, entries
     const uint32_t bar = smem_addr(&mbar);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pp = a.bxw / 2;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     uint32_t parity = 0;
+    bool units_left = true;   // thread 0's view
     unsigned long long executed = 0;
-    const unsigned ntasks = min(a.qctr[1], a.tcap);
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned ti = atomicAdd(&a.qctr[2], 1u);
-            int state = -1;
-            if (ti < ntasks) {
-                const int4 tk = a.tasks[ti];
-                state = 0;
-                if (tk.x >= 0 && tk.x < a.units && tk.y >= 0 && tk.z > 0 &&
-                    (unsigned)tk.y + (unsigned)tk.z <= a.qcap) {
-                    const UnitPos u = unit_pos<E, TC>(a, tk.x);
-                    if (u.k_begin < u.k_end) {
-                        state = 1;
-                        s_task[1] = tk.x;
-                        s_task[2] = tk.y;
-                        s_task[3] = tk.z;
-                        stage_window<E>(tmap, a, u, win, bar, s_org);
-                    }
+            int kind = 0;
+            if (units_left) {
+                const unsigned un = atomicAdd(&a.qctr[3], 1u);
+                if (un < (unsigned)a.units) {
+                    kind = 1;
+                    s_job[1] = (int)un;
+                    stage_window<E>(tmap, a, unit_pos<E, TC>(a, (int)un), win, bar, s_org);
+                } else {
+                    units_left = false;
                 }
-                if (state == 0)
-                    atomicExch(a.err, 1);
             }
-            s_task[0] = state;
+            if (!units_left) {
+                const unsigned ti = atomicAdd(&a.qctr[2], 1u);
+                const unsigned long long t0 = global_ns();
+                for (unsigned polls = 0;; ++polls) {
+                    if (ti < a.tcap && ld_acquire_u32(reinterpret_cast<const unsigned *>(&a.tasks[ti].w)) == 1u) {
+                        const int4 tk = a.tasks[ti];
+                        if (tk.x >= 0 && tk.x < a.units && tk.y >= 0 && tk.z > 0 &&
+                            (unsigned)tk.y + (unsigned)tk.z <= a.qcap) {
+                            kind = 2;
+                            s_job[1] = tk.x;
+                            s_job[2] = tk.y;
+                            s_job[3] = tk.z;
+                            stage_window<E>(tmap, a, unit_pos<E, TC>(a, tk.x), win, bar, s_org);
+                        } else {
+                            atomicExch(a.err, 1);
+                        }
+                        break;
+                    }
+                    if (ld_acquire_u32(&a.qctr[4]) >= (unsigned)a.units && ti >= ld_acquire_u32(&a.qctr[1]))
+                        break;   // every unit is done and published no task ti
+                    if ((polls & 15u) == 15u && global_ns() - t0 > 1000000000ull) {
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            s_job[0] = kind;
         }
         __syncthreads();
-        const int state = s_task[0];
-        if (state < 0)
+        const int kind = s_job[0];
+        if (kind == 0)
             break;
-        if (state == 0) {
-            __syncthreads();
-            continue;
-        }
         const bool ok = mbar_wait(bar, parity);
         parity ^= 1u;
         if (__syncthreads_or(!ok)) {
@@ -510,16 +577,26 @@ __global__ void __launch_bounds__(WARPS * 32) score_drain_kernel(const __grid_co
                 atomicExch(a.err, 1);
             break;
         }
-        const UnitPos u = unit_pos<E, TC>(a, s_task[1]);
-        const TileWork t = tile_work(a, u.img);
-        const int first = s_task[2], cnt = s_task[3];
-        for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
-            const int e = e0 + lane;
-            const bool has = e < cnt;
-            const uint32_t code = has ? a.queue[first + e] : 0u;
-            score_slice<E, NB, POL, TC>(win, a.bxw / 2, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
-                                        (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
-                                        executed);
+        const UnitPos u = unit_pos<E, TC>(a, s_job[1]);
+        TileWork t = tile_work(a, u.img);
+        t.bits = bits;
+        t.unit = s_job[1];
+        if (kind == 1) {
+            score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&a.qctr[4], 1u);   // this unit's tasks are all published
+            }
+        } else {
+            const int first = s_job[2], cnt = s_job[3];
+            for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
+                const int e = e0 + lane;
+                const bool has = e < cnt;
+                const uint32_t code = has ? a.queue[first + e] : 0u;
+                score_slice<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, (int)(code >> 7),
+                                            (int)(code & 31u), (int)((code >> 5) & 3u), has, t, executed);
+            }
         }
         __syncthreads();   // every warp is done with the window before the next copy
     }
@@ -686,9 +763,10 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
     // edge-presence bound (with early termination; counts in 16 bit planes)
     const bool bound = a.early && a.emin > 0 && a.n < 65536;
     const int dmw = edge_bitmap_words(2 * pp);
-    const uint32_t *dbits = a.bits + (size_t)a.byw * dmw;
+    const size_t plane = (size_t)a.byw * dmw;
+    const uint32_t *cbits = a.bits + 4 * plane;   // dilated planes, one per model-direction quadrant
     if (bound)
-        build_edge_bits<E, WARPS * 32>(win, pp, a.byw, a.bits, a.bits + (size_t)a.byw * dmw);
+        build_edge_bits<E, WARPS * 32, POL>(win, pp, a.byw, a.bits, a.bits + 4 * plane);
     unsigned long long executed = 0;
     float2 acc[TR][TC / 2];
     constexpr int SPLIT = TR / RD;                 // slices per thread block (4)
@@ -742,17 +820,20 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     const int ii = i0 + lane;
                     qo = make_int2(0, 0);
                     if (ii < a.n) {
+                        // the row offset times 4 plus the quadrant of the
+                        // point's rotated direction (its bitmap plane)
                         const RotPt t = P[ii];
-                        qo = make_int2(t.ox, t.oy);
+                        qo = make_int2(t.ox, t.oy * 4 + (POL ? 0 : quadrant(t.px, t.py)));
                     }
                 }
                 uint32_t mm0[8], mm1[8], mm2[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
-                    const int qoy = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+                    const int qyq = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+                    const int qoy = qyq >> 2;
                     const int b = xseg + qox - wx0;   // window column of the first pose's centre
-                    const uint32_t *row = dbits + (size_t)(yrow + qoy - wy0) * dmw + (b >> 5);
+                    const uint32_t *row = cbits + (size_t)(qyq & 3) * plane + (size_t)(yrow + qoy - wy0) * dmw + (b >> 5);
                     const int sh = b & 31;
                     const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
                     uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
@@ -914,17 +995,17 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         // one surviving slice per lane, in (item, slice, lane) order
         constexpr int CH = WARPS * 32;
         if (a.queue) {
-            // two-launch form: the blocks to the global queue, one task per
-            // CH of them (a CTA's worth for the drain launch)
-            __shared__ unsigned s_qb;
+            // persistent form: the slices to the global queue and one task
+            // per CH of them (a CTA's worth), each published once written
+            __shared__ unsigned s_qb, s_tb, s_nt;
             if (threadIdx.x == 0) {
                 const unsigned nt = (unsigned)((total + CH - 1) / CH);
-                unsigned qb = ~0u;
+                unsigned qb = ~0u, tb = 0;
                 if (total > 0) {
                     qb = atomicAdd(&a.qctr[0], (unsigned)total);
-                    const unsigned tb = atomicAdd(&a.qctr[1], nt);
+                    tb = atomicAdd(&a.qctr[1], nt);
                     if (qb + (unsigned)total > a.qcap || tb + nt > a.tcap) {
-                        atomicExch(a.err, 1);   // capacities cover every block: cannot happen
+                        atomicExch(a.err, 1);   // capacities cover every slice: cannot happen
                         qb = ~0u;
                     } else {
                         for (unsigned j = 0; j < nt; ++j)
@@ -932,6 +1013,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     }
                 }
                 s_qb = qb;
+                s_tb = tb;
+                s_nt = qb == ~0u ? 0u : nt;
             }
             __syncthreads();
             const unsigned qb = s_qb;
@@ -949,6 +1032,13 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                         if ((nb >> sp) & 1u)
                             a.queue[slot++] = ((uint32_t)(r0 + it) << 7) | ((uint32_t)sp << 5) | (uint32_t)lane;
                 }
+                __threadfence();   // this thread's entries before the tasks' flags
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && s_nt) {
+                __threadfence();
+                for (unsigned j = 0; j < s_nt; ++j)
+                    st_release_u32(reinterpret_cast<unsigned *>(&a.tasks[s_tb + j].w), 1u);
             }
         } else {
             for (int e0 = warp * 32; e0 < total; e0 += WARPS * 32) {
@@ -1290,32 +1380,31 @@ cudaError_t launch_t(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
-    prof_begin(kStageScoreBound, st);
-    kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
-    count_launches(1);
-    prof_end(kStageScoreBound, st);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || !a.queue)
-        return e;
-    // drain launch: persistent, as many CTAs as are resident at once
-    auto dk = score_drain_kernel<E, NB, POL, WARPS, TC>;
-    const size_t dsmem = (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15) + 128;
-    e = cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
+    if (!a.queue) {
+        prof_begin(kStageScoreBound, st);
+        kern<<<grid, WARPS * 32, smem, st>>>(tm, a);
+        count_launches(1);
+        prof_end(kStageScoreBound, st);
+        return cudaGetLastError();
+    }
+    // persistent form: as many CTAs as are resident at once
+    auto fk = score_fused_kernel<E, NB, POL, WARPS, TC>;
+    e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    e = cudaFuncSetAttribute(dk, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(fk, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
     int dev = 0, sms = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dk, WARPS * 32, dsmem)) != cudaSuccess)
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fk, WARPS * 32, smem)) != cudaSuccess)
         return e;
-    const unsigned ctas = (unsigned)std::max(1, std::min(sms * std::max(occ, 1), (int)std::min(a.tcap, 1u << 20)));
-    prof_begin(kStageScoreDrain, st);
-    dk<<<ctas, WARPS * 32, dsmem, st>>>(tm, a);
+    const unsigned ctas = (unsigned)std::max(1, sms * std::max(occ, 1));
+    prof_begin(kStageScoreBound, st);
+    fk<<<ctas, WARPS * 32, smem, st>>>(tm, a);
     count_launches(1);
-    prof_end(kStageScoreDrain, st);
+    prof_end(kStageScoreBound, st);
     return cudaGetLastError();
 }
 

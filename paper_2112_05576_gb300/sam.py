@@ -108,7 +108,7 @@ SIGNATURES = {
     "sam_executed_pose_points": (ctypes.c_longlong, [_c_int]),
 }
 
-STAGES = ("pyramid", "gradient", "score_map", "candidates", "refine", "nms", "score_bound", "score_drain")
+STAGES = ("pyramid", "gradient", "score_map", "candidates", "refine", "nms", "score_tiled")
 
 _lib = None
 
