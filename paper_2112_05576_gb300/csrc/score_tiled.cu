@@ -244,8 +244,11 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
                 return e;
         }
     }
-    const size_t smem =
-        (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) + edge_bitmap_bytes(bxw, byw) + 128;
+    // the edge bitmaps follow the window; the persistent form reuses their
+    // space for the partial sums of split tasks (warps x 32 lanes x slice)
+    const size_t red = (size_t)cfg.warps * 32 * kDrainRows * cfg.tc * 4;
+    const size_t smem = (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) +
+                        std::max(edge_bitmap_bytes(bxw, byw), red) + 128;
     const bool pol = polarity != 0;
     switch (precision) {
     case SAM_FP32:

@@ -452,6 +452,14 @@ template <typename E, int NB, bool POL, int TC>
 __device__ __forceinline__ void score_slice(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
                                             int sty0, int k_begin, int item, int src, int part, bool has,
                                             const TileWork &a, unsigned long long &executed);
+template <typename E, int NB, bool POL, int TC>
+__device__ __forceinline__ void slice_sum(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                          int sty0, int k_begin, int item, int src, int part, bool has,
+                                          const TileWork &a, int p0, int p1, float2 (&acc)[RD][TC / 2],
+                                          unsigned long long &executed);
+template <typename E, int TC>
+__device__ __forceinline__ void slice_store(int item, int src, int part, int stx0, int sty0, int k_begin,
+                                            const TileWork &a, const float2 (&acc)[RD][TC / 2]);
 
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -590,12 +598,49 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
             }
         } else {
             const int first = s_job[2], cnt = s_job[3];
-            for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
-                const int e = e0 + lane;
-                const bool has = e < cnt;
+            // a task fills ceil(cnt / 32) warps; with G = WARPS / that many
+            // warps per 32 slices, each of the G takes 1/G of the points
+            // (partial sums reduced in shared memory, in a fixed order)
+            const int groups = (cnt + 31) >> 5;
+            const int G = max(1, WARPS / groups);
+            if (G == 1) {
+                for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
+                    const int e = e0 + lane;
+                    const bool has = e < cnt;
+                    const uint32_t code = has ? a.queue[first + e] : 0u;
+                    score_slice<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
+                                                (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
+                                                executed);
+                }
+            } else {
+                float2 *red = reinterpret_cast<float2 *>(bits);   // [WARPS][RD][TC / 2][32] (the bitmaps are free)
+                const int gi = warp / G, g = warp - gi * G;
+                const int e = gi * 32 + lane;
+                const bool has = gi < groups && e < cnt;
                 const uint32_t code = has ? a.queue[first + e] : 0u;
-                score_slice<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, (int)(code >> 7),
-                                            (int)(code & 31u), (int)((code >> 5) & 3u), has, t, executed);
+                float2 acc[RD][TC / 2];
+                if (gi < groups) {
+                    const int p0 = (int)(((long long)a.n * g) / G), p1 = (int)(((long long)a.n * (g + 1)) / G);
+                    slice_sum<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
+                                              (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
+                                              p0, p1, acc, executed);
+#pragma unroll
+                    for (int r = 0; r < RD; ++r)
+#pragma unroll
+                        for (int j = 0; j < TC / 2; ++j)
+                            red[((warp * RD + r) * (TC / 2) + j) * 32 + lane] = acc[r][j];
+                }
+                __syncthreads();
+                if (g == 0 && has) {
+                    for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+                        for (int r = 0; r < RD; ++r)
+#pragma unroll
+                            for (int j = 0; j < TC / 2; ++j)
+                                acc[r][j] = __fadd2_rn(acc[r][j], red[(((warp + g2) * RD + r) * (TC / 2) + j) * 32 + lane]);
+                    slice_store<E, TC>((int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), u.stx0, u.sty0,
+                                       u.k_begin, t, acc);
+                }
             }
         }
         __syncthreads();   // every warp is done with the window before the next copy
@@ -740,6 +785,44 @@ __device__ __forceinline__ void score_slice(const typename Pairs<E>::Raw *win, i
         block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n,
                             pruned);
     }
+}
+
+// Partial sums of one lane's slice (as score_slice) over points [p0, p1),
+// without early termination.
+template <typename E, int NB, bool POL, int TC>
+__device__ __forceinline__ void slice_sum(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                          int sty0, int k_begin, int item, int src, int part, bool has,
+                                          const TileWork &a, int p0, int p1, float2 (&acc)[RD][TC / 2],
+                                          unsigned long long &executed) {
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    const int tiles = a.sx * a.sy;
+    const int k = k_begin + item / tiles;
+    const int wt = item % tiles;
+    const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
+    const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
+    bool pruned;
+    const int done = block_dot<E, NB, POL, TC, RD>(win, pp, x0 - 1 - wx0, y0 - 1 - wy0,
+                                                   a.rot + (size_t)k * a.n + p0, p1 - p0, has && p1 > p0, 0, 0.f, acc,
+                                                   pruned);
+    if (has) {
+        const int vx = max(0, min(TC, a.W - (x0 - a.ox))), vy = max(0, min(RD, a.H - (y0 - a.oy)));
+        executed += (unsigned long long)done * (vx * vy);
+    }
+}
+
+// Scores of one lane's slice (complete sums in acc) into the map.
+template <typename E, int TC>
+__device__ __forceinline__ void slice_store(int item, int src, int part, int stx0, int sty0, int k_begin,
+                                            const TileWork &a, const float2 (&acc)[RD][TC / 2]) {
+    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
+    constexpr int WTX = LX * TC, WTY = LY * TR;
+    const int tiles = a.sx * a.sy;
+    const int k = k_begin + item / tiles;
+    const int wt = item % tiles;
+    const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
+    const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
+    block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, false);
 }
 
 // The (angle, warp tile) items of one CTA work unit over its staged window
