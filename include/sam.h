@@ -333,6 +333,12 @@ sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_
  * completed.  Synchronises the device.  Errors: SAM_ERR_ARG, SAM_ERR_NOMEM,
  * SAM_ERR_CUDA. */
 sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms);
+/* The same for the other bounded wait of the tiled scorer: in its persistent
+ * form a CTA that has claimed a task of surviving poses waits (1 s limit)
+ * until the CTA producing it publishes it.  Here one thread waits for a task
+ * whose flag nothing sets, in a list whose one work unit never completes,
+ * limited to limit_us; returns as sam_selftest_wait_timeout. */
+sam_status sam_selftest_task_wait_timeout(int limit_us, double *waited_ms);
 
 /* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
  * clears it if any wait gave up since the last call (synchronises the

@@ -278,8 +278,8 @@ struct PairScore;
     cudaError_t launch_pairs_##suf(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, \
                                    bool pol, int early, size_t smem, size_t win_bytes, unsigned *counter, int *err, \
                                    unsigned long long *exec, cudaStream_t st);
-cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns,
-                                 cudaStream_t st);
+cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns, int mode,
+                                 unsigned *fake, cudaStream_t st);
 SAM_TILED_LAUNCHERS(f32)
 SAM_TILED_LAUNCHERS(f16)
 SAM_TILED_LAUNCHERS(bf16)

@@ -416,19 +416,27 @@ extern "C" long long sam_executed_pose_points(int reset) {
     return (long long)v;
 }
 
-extern "C" sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms) {
+namespace {
+
+// One bounded wait that nothing completes (mode 0: the window-copy mbarrier
+// wait, 1: the persistent scorer's wait for a task), reported through the
+// device error flag.
+sam_status selftest_wait(int mode, int limit_us, double *waited_ms) {
     if (limit_us < 1 || limit_us > 1000000)
         return SAM_ERR_ARG;
     sam::DeviceFlags fl;
     if (!sam::device_flags(&fl))
         return SAM_ERR_CUDA;
     unsigned long long *d_ns = nullptr;
-    if (cudaMalloc(&d_ns, sizeof(unsigned long long)) != cudaSuccess)
+    if (cudaMalloc(&d_ns, 64) != cudaSuccess)
         return SAM_ERR_NOMEM;
+    unsigned *fake = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(d_ns) + 16);   // task + 5 counters
     sam_status s = SAM_OK;
     unsigned long long ns = 0;
     int flag = 0;
-    if (sam::launch_wait_selftest(fl.err, (unsigned long long)limit_us * 1000ull, d_ns, 0) != cudaSuccess ||
+    if (cudaMemset(d_ns, 0, 64) != cudaSuccess ||
+        sam::launch_wait_selftest(fl.err, (unsigned long long)limit_us * 1000ull, d_ns, mode, fake, 0) !=
+            cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(&flag, fl.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -445,6 +453,16 @@ extern "C" sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms)
         return SAM_ERR_TIMEOUT;
     }
     return SAM_OK;
+}
+
+}  // namespace
+
+extern "C" sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms) {
+    return selftest_wait(0, limit_us, waited_ms);
+}
+
+extern "C" sam_status sam_selftest_task_wait_timeout(int limit_us, double *waited_ms) {
+    return selftest_wait(1, limit_us, waited_ms);
 }
 
 extern "C" int sam_take_device_error(void) {

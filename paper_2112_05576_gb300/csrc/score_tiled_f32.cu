@@ -22,9 +22,9 @@ cudaError_t launch_pairs_f32(const PairScore *pairs, int n_pairs, int total, con
                              st);
 }
 
-cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns,
-                                 cudaStream_t st) {
-    wait_selftest_kernel<<<1, 32, 0, st>>>(err, limit_ns, waited_ns);
+cudaError_t launch_wait_selftest(int *err, unsigned long long limit_ns, unsigned long long *waited_ns, int mode,
+                                 unsigned *fake, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(err, limit_ns, waited_ns, mode, fake);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -106,9 +106,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
 // Self-test of the bounded wait: one warp waits on a fresh mbarrier that
 // nothing arrives at (no copy is issued), gives up after limit_ns and
 // reports it through the error flag exactly as the scorers do.
-__global__ void wait_selftest_kernel(int *err, unsigned long long limit_ns, unsigned long long *waited_ns) {
+__device__ int wait_task(const int4 *tasks, unsigned tcap, const unsigned *qctr, unsigned units, unsigned ti,
+                          unsigned long long limit_ns);
+
+// mode 0: the mbarrier wait above; mode 1: thread 0's wait for a task of the
+// persistent scorer (wait_task) on a task list whose flag nothing sets and
+// whose one work unit never completes (`fake`: 16 zero bytes of task, then
+// the five zero counters).
+__global__ void wait_selftest_kernel(int *err, unsigned long long limit_ns, unsigned long long *waited_ns, int mode,
+                                     unsigned *fake) {
     __shared__ __align__(8) unsigned long long mbar;
     const uint32_t bar = smem_addr(&mbar);
+    if (mode == 1) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t0 = global_ns();
+            const int r = wait_task(reinterpret_cast<const int4 *>(fake), 1u, fake + 4, 1u, 0u, limit_ns);
+            *waited_ns = global_ns() - t0;
+            if (r < 0)
+                atomicExch(err, 1);
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -343,6 +361,23 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Thread 0 of a persistent-scorer CTA: waits until task ti is published.
+// Returns 1 when it is, 0 when every unit is done (qctr[4] >= units) and no
+// task ti exists, -1 after limit_ns (the caller reports it).
+__device__ int wait_task(const int4 *tasks, unsigned tcap, const unsigned *qctr, unsigned units, unsigned ti,
+                          unsigned long long limit_ns) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned polls = 0;; ++polls) {
+        if (ti < tcap && ld_acquire_u32(reinterpret_cast<const unsigned *>(&tasks[ti].w)) == 1u)
+            return 1;
+        if (ld_acquire_u32(&qctr[4]) >= units && ti >= ld_acquire_u32(&qctr[1]))
+            return 0;
+        if ((polls & 15u) == 15u && global_ns() - t0 > limit_ns)
+            return -1;
+        __nanosleep(64);
+    }
+}
+
 // Items (angle x warp tile) whose surviving blocks one queue round holds.
 constexpr int kQueueItems = 128;
 // Pose rows per lane when the surviving blocks are scored (TR / RD lanes
@@ -547,29 +582,21 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
             }
             if (!units_left) {
                 const unsigned ti = atomicAdd(&a.qctr[2], 1u);
-                const unsigned long long t0 = global_ns();
-                for (unsigned polls = 0;; ++polls) {
-                    if (ti < a.tcap && ld_acquire_u32(reinterpret_cast<const unsigned *>(&a.tasks[ti].w)) == 1u) {
-                        const int4 tk = a.tasks[ti];
-                        if (tk.x >= 0 && tk.x < a.units && tk.y >= 0 && tk.z > 0 &&
-                            (unsigned)tk.y + (unsigned)tk.z <= a.qcap) {
-                            kind = 2;
-                            s_job[1] = tk.x;
-                            s_job[2] = tk.y;
-                            s_job[3] = tk.z;
-                            stage_window<E>(tmap, a, unit_pos<E, TC>(a, tk.x), win, bar, s_org);
-                        } else {
-                            atomicExch(a.err, 1);
-                        }
-                        break;
-                    }
-                    if (ld_acquire_u32(&a.qctr[4]) >= (unsigned)a.units && ti >= ld_acquire_u32(&a.qctr[1]))
-                        break;   // every unit is done and published no task ti
-                    if ((polls & 15u) == 15u && global_ns() - t0 > 1000000000ull) {
+                const int w = wait_task(a.tasks, a.tcap, a.qctr, (unsigned)a.units, ti, kWaitLimitNs);
+                if (w > 0) {
+                    const int4 tk = a.tasks[ti];
+                    if (tk.x >= 0 && tk.x < a.units && tk.y >= 0 && tk.z > 0 &&
+                        (unsigned)tk.y + (unsigned)tk.z <= a.qcap) {
+                        kind = 2;
+                        s_job[1] = tk.x;
+                        s_job[2] = tk.y;
+                        s_job[3] = tk.z;
+                        stage_window<E>(tmap, a, unit_pos<E, TC>(a, tk.x), win, bar, s_org);
+                    } else {
                         atomicExch(a.err, 1);
-                        break;
                     }
-                    __nanosleep(64);
+                } else if (w < 0) {
+                    atomicExch(a.err, 1);   // a producer never published (cannot happen)
                 }
             }
             s_job[0] = kind;

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sam_get_score_kernel": (None, [_i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_take_device_error": (_c_int, []),
     "sam_selftest_wait_timeout": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sam_selftest_task_wait_timeout": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "sam_autotune": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams),
                               _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
     "sam_model_tiling": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
@@ -343,6 +344,14 @@ def selftest_wait_timeout(limit_us=2000):
     The expected status is SAM_ERR_TIMEOUT."""
     ms = ctypes.c_double()
     s = int(lib().sam_selftest_wait_timeout(int(limit_us), ctypes.byref(ms)))
+    return s, ms.value
+
+
+def selftest_task_wait_timeout(limit_us=2000):
+    """The persistent scorer's task wait on a task nothing publishes; returns
+    (status, milliseconds waited).  The expected status is SAM_ERR_TIMEOUT."""
+    ms = ctypes.c_double()
+    s = int(lib().sam_selftest_task_wait_timeout(int(limit_us), ctypes.byref(ms)))
     return s, ms.value
 
 
