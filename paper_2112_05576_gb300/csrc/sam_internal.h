@@ -81,6 +81,12 @@ constexpr int kChunkCols = 6;
 // Pose rows each lane scores of a block that survives the edge-presence
 // bound (kTileRows / kDrainRows lanes share the block).
 constexpr int kDrainRows = 2;
+// Most surviving slices in one task of the persistent scorer (a task that
+// fills fewer warps than the CTA has is split over the idle warps by points).
+#ifndef SAM_TASK_SLICES
+#define SAM_TASK_SLICES 64
+#endif
+constexpr int kTaskSlices = SAM_TASK_SLICES;
 
 struct TileConfig {
     int sx = 2, sy = 1;   // super-tile in warp tiles (8 x tc lanes-along-x poses wide, 32 rows tall for FP32)

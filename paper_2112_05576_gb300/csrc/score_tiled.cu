@@ -226,7 +226,7 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     if (queue && queue->base && a.emin > 0 && L.n < 65536) {
         const size_t items = (size_t)cfg.tg * cfg.sx * cfg.sy;
         const size_t rounds = (items + 127) / 128;
-        const size_t ch = (size_t)cfg.warps * 32;   // slices per task
+        const size_t ch = (size_t)std::min(cfg.warps * 32, kTaskSlices);   // slices per task
         const size_t units = (size_t)a.units;
         const size_t per_item = 32 * (kTileRows / kDrainRows);
         const size_t qcap = units * items * per_item, tcap = units * (items * per_item / ch + rounds);

@@ -1103,7 +1103,7 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
         __syncthreads();
         const int total = s_off[ni];
         // one surviving slice per lane, in (item, slice, lane) order
-        constexpr int CH = WARPS * 32;
+        constexpr int CH = WARPS * 32 < kTaskSlices ? WARPS * 32 : kTaskSlices;   // slices per task
         if (a.queue) {
             // persistent form: the slices to the global queue and one task
             // per CH of them (a CTA's worth), each published once written
