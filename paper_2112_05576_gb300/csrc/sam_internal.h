@@ -84,7 +84,7 @@ constexpr int kDrainRows = 2;
 // Most surviving slices in one task of the persistent scorer (a task that
 // fills fewer warps than the CTA has is split over the idle warps by points).
 #ifndef SAM_TASK_SLICES
-#define SAM_TASK_SLICES 64
+#define SAM_TASK_SLICES 32
 #endif
 constexpr int kTaskSlices = SAM_TASK_SLICES;
 
