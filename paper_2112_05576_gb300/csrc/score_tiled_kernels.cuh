@@ -534,6 +534,59 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
 }
 
+// One task of the persistent scorer: entries [first, first + cnt) of the
+// queue, slices of the staged unit (window origin wx0, wy0; super-tile
+// stx0, sty0; first angle k_begin), one per lane.  All threads of the CTA
+// call it (it may end with a CTA barrier); `bits` is the bitmap space, free
+// while a task is scored.
+template <typename E, int NB, bool POL, int WARPS, int TC>
+__device__ __forceinline__ void drain_task(const typename Pairs<E>::Raw *win, int pp, int wx0, int wy0, int stx0,
+                                           int sty0, int k_begin, const TileWork &t, int first, int cnt,
+                                           uint32_t *bits, unsigned long long &executed) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // a task fills ceil(cnt / 32) warps; with G = WARPS / that many warps per
+    // 32 slices, each of the G takes 1/G of the points (partial sums reduced
+    // in shared memory, in a fixed order)
+    const int groups = (cnt + 31) >> 5;
+    const int G = max(1, WARPS / groups);
+    if (G == 1) {
+        for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
+            const int e = e0 + lane;
+            const bool has = e < cnt;
+            const uint32_t code = has ? t.queue[first + e] : 0u;
+            score_slice<E, NB, POL, TC>(win, pp, wx0, wy0, stx0, sty0, k_begin, (int)(code >> 7), (int)(code & 31u),
+                                        (int)((code >> 5) & 3u), has, t, executed);
+        }
+        return;
+    }
+    float2 *red = reinterpret_cast<float2 *>(bits);   // [WARPS][RD][TC / 2][32] (the bitmaps are free)
+    const int gi = warp / G, g = warp - gi * G;
+    const int e = gi * 32 + lane;
+    const bool has = gi < groups && e < cnt;
+    const uint32_t code = has ? t.queue[first + e] : 0u;
+    float2 acc[RD][TC / 2];
+    if (gi < groups) {
+        const int p0 = (int)(((long long)t.n * g) / G), p1 = (int)(((long long)t.n * (g + 1)) / G);
+        slice_sum<E, NB, POL, TC>(win, pp, wx0, wy0, stx0, sty0, k_begin, (int)(code >> 7), (int)(code & 31u),
+                                  (int)((code >> 5) & 3u), has, t, p0, p1, acc, executed);
+#pragma unroll
+        for (int r = 0; r < RD; ++r)
+#pragma unroll
+            for (int j = 0; j < TC / 2; ++j)
+                red[((warp * RD + r) * (TC / 2) + j) * 32 + lane] = acc[r][j];
+    }
+    __syncthreads();
+    if (g == 0 && has) {
+        for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+            for (int r = 0; r < RD; ++r)
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j)
+                    acc[r][j] = __fadd2_rn(acc[r][j], red[(((warp + g2) * RD + r) * (TC / 2) + j) * 32 + lane]);
+        slice_store<E, TC>((int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), stx0, sty0, k_begin, t, acc);
+    }
+}
+
 // Persistent form (detection with early termination): CTAs pull work from
 // two lists.  First the work units of the bound pass (counter qctr[3]): a
 // unit's window is staged, every pose's edge-presence bound computed, slices
@@ -624,51 +677,8 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
                 atomicAdd(&a.qctr[4], 1u);   // this unit's tasks are all published
             }
         } else {
-            const int first = s_job[2], cnt = s_job[3];
-            // a task fills ceil(cnt / 32) warps; with G = WARPS / that many
-            // warps per 32 slices, each of the G takes 1/G of the points
-            // (partial sums reduced in shared memory, in a fixed order)
-            const int groups = (cnt + 31) >> 5;
-            const int G = max(1, WARPS / groups);
-            if (G == 1) {
-                for (int e0 = warp * 32; e0 < cnt; e0 += WARPS * 32) {
-                    const int e = e0 + lane;
-                    const bool has = e < cnt;
-                    const uint32_t code = has ? a.queue[first + e] : 0u;
-                    score_slice<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
-                                                (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
-                                                executed);
-                }
-            } else {
-                float2 *red = reinterpret_cast<float2 *>(bits);   // [WARPS][RD][TC / 2][32] (the bitmaps are free)
-                const int gi = warp / G, g = warp - gi * G;
-                const int e = gi * 32 + lane;
-                const bool has = gi < groups && e < cnt;
-                const uint32_t code = has ? a.queue[first + e] : 0u;
-                float2 acc[RD][TC / 2];
-                if (gi < groups) {
-                    const int p0 = (int)(((long long)a.n * g) / G), p1 = (int)(((long long)a.n * (g + 1)) / G);
-                    slice_sum<E, NB, POL, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin,
-                                              (int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), has, t,
-                                              p0, p1, acc, executed);
-#pragma unroll
-                    for (int r = 0; r < RD; ++r)
-#pragma unroll
-                        for (int j = 0; j < TC / 2; ++j)
-                            red[((warp * RD + r) * (TC / 2) + j) * 32 + lane] = acc[r][j];
-                }
-                __syncthreads();
-                if (g == 0 && has) {
-                    for (int g2 = 1; g2 < G; ++g2)
-#pragma unroll
-                        for (int r = 0; r < RD; ++r)
-#pragma unroll
-                            for (int j = 0; j < TC / 2; ++j)
-                                acc[r][j] = __fadd2_rn(acc[r][j], red[(((warp + g2) * RD + r) * (TC / 2) + j) * 32 + lane]);
-                    slice_store<E, TC>((int)(code >> 7), (int)(code & 31u), (int)((code >> 5) & 3u), u.stx0, u.sty0,
-                                       u.k_begin, t, acc);
-                }
-            }
+            drain_task<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, t, s_job[2],
+                                              s_job[3], bits, executed);
         }
         __syncthreads();   // every warp is done with the window before the next copy
     }
@@ -925,25 +935,28 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             // warp broadcast per point
             int2 qo = make_int2(0, 0);
             const int np8 = (a.n + 7) & ~7;
+            // this lane's pose row in the bitmaps and its first pose's column
+            const uint32_t *rbase = cbits + (size_t)(yrow - wy0) * dmw;
+            const int xb = xseg - wx0;
             for (int i0 = 0; i0 < np8; i0 += 8) {
                 if ((i0 & 31) == 0) {
                     const int ii = i0 + lane;
                     qo = make_int2(0, 0);
                     if (ii < a.n) {
-                        // the row offset times 4 plus the quadrant of the
-                        // point's rotated direction (its bitmap plane)
+                        // the column offset, and the word offset of the row
+                        // offset in the bitmap plane of the quadrant of the
+                        // point's rotated direction
                         const RotPt t = P[ii];
-                        qo = make_int2(t.ox, t.oy * 4 + (POL ? 0 : quadrant(t.px, t.py)));
+                        qo = make_int2(t.ox, (POL ? 0 : quadrant(t.px, t.py)) * (int)plane + t.oy * dmw);
                     }
                 }
                 uint32_t mm0[8], mm1[8], mm2[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
-                    const int qyq = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
-                    const int qoy = qyq >> 2;
-                    const int b = xseg + qox - wx0;   // window column of the first pose's centre
-                    const uint32_t *row = cbits + (size_t)(qyq & 3) * plane + (size_t)(yrow + qoy - wy0) * dmw + (b >> 5);
+                    const int qpo = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+                    const int b = xb + qox;   // window column of the first pose's centre
+                    const uint32_t *row = rbase + qpo + (b >> 5);
                     const int sh = b & 31;
                     const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
                     uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
