@@ -176,7 +176,7 @@ LOGIC_OPS_PER_CLK_SM = 64.0
 # workload, from an ncu capture at the tiling below (summary and command in
 # profiles/score_map_config2_batch16.md); reported only when the bench runs
 # that tiling, and to be re-taken whenever the kernel changes.
-NCU_FUSED_TRAFFIC = {"tiling": (2, 2, 4, 8, 6), "bytes": 3066112 + 5189632}
+NCU_FUSED_TRAFFIC = {"tiling": (2, 1, 11, 4, 10), "bytes": 2988288 + 2543872}
 
 
 def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
