@@ -98,6 +98,27 @@ def test_tiled_neighbourhood_and_polarity(nbhd, polarity):
     assert np.max(np.abs(got - ref)) < TOL
 
 
+@pytest.mark.parametrize("nbhd,polarity", [(1, 0), (3, 1), (1, 1), (3, 0)])
+def test_persistent_early_termination_exact_safe(nbhd, polarity):
+    # early termination runs the persistent form (edge-presence bound with a
+    # plane per quadrant for polarity 0, one plane for polarity 1; surviving
+    # slices scored as tasks split over the warps): every pruned pose is below
+    # min_score in the oracle, every other pose matches it, none at or above
+    # min_score is pruned
+    tm, sc, _, _ = synth.config2_scene(seed=4321)
+    m = sam.Model(tm, 30, 60, 4, 1.0, polarity)
+    om = oracle.create_model(tm, 30, 60, 4, 1.0, polarity)
+    top = oracle.pyramid(sc, 4)[3]
+    ref = _oracle_map(om, 3, top, nbhd=nbhd)
+    for ms, cfg in ((0.5, (2, 1, 11, 4, 10)), (0.7, (1, 2, 5, 8, 6))):
+        got = _map(m, 3, top, 2, cfg, nbhd=nbhd, min_score=ms, early=1)
+        pruned = np.isneginf(got)
+        assert pruned.any()
+        assert np.all(ref[pruned] < ms)
+        assert not np.any(pruned & (ref >= ms))
+        assert np.max(np.abs(got[~pruned] - ref[~pruned])) < TOL
+
+
 @pytest.mark.parametrize("h,w", [(61, 77), (33, 49), (7, 5), (97, 145), (32, 48), (1, 1)])
 def test_tiled_ragged_sizes_match_generic_and_oracle(h, w):
     tm, sc, _ = synth.tiny_case(h * 1000 + w, size=max(h, w, 24), tsize=11)
