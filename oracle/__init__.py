@@ -33,4 +33,7 @@ from .oracle import (  # noqa: F401
     score_bilinear,
     bilinear_border_mask,
     refine_gn,
+    subpixel_fit,
+    neighbourhood27,
+    subpixel_poses,
 )

@@ -79,6 +79,7 @@ def _L():
         lib.or_refine_gn.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
                                      _f64p, _c_int]
         lib.or_refine_gn.restype = _c_dbl
+        lib.or_subpixel_fit.argtypes = [_f64p, _f64p]
         _lib = lib
     return _lib
 
@@ -369,3 +370,39 @@ def refine_gn(field, pts, pose, iterations=20, polarity=0):
     p = np.array(pose, dtype=np.float64)
     s = _L().or_refine_gn(field, w, h, tx, ty, gx, gy, len(tx), int(polarity), p, int(iterations))
     return p, s
+
+
+# ---------------------------------------------------------------------------
+# sub-pixel / sub-angle final pose (quadratic fit of the 3x3x3 neighbourhood)
+# ---------------------------------------------------------------------------
+
+def subpixel_fit(s27):
+    """(dx, dy, dk) of the quadratic fit of a 3x3x3 score neighbourhood,
+    s27[(dk + 1) * 9 + (dy + 1) * 3 + (dx + 1)]; see or_subpixel_fit."""
+    s = _f64(np.asarray(s27, dtype=np.float64).reshape(27))
+    d = np.zeros(3, dtype=np.float64)
+    _L().or_subpixel_fit(s, d)
+    return d
+
+
+def neighbourhood27(field, pts, x, y, k, ntheta, dtheta_deg, nbhd=3, polarity=0):
+    """Eq. (1) scores of the 27 poses (x + dx, y + dy, k + dk), dx, dy, dk in
+    {-1, 0, 1}, angle index circular; layout of subpixel_fit."""
+    out = np.empty(27, dtype=np.float64)
+    for dk in (-1, 0, 1):
+        rot = rotate_points(pts, (k + dk) % ntheta, dtheta_deg)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                out[(dk + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = score_pose(field, rot, x + dx, y + dy, nbhd, polarity)
+    return out
+
+
+def subpixel_poses(field, pts, kyx, ntheta, dtheta_deg, nbhd=3, polarity=0):
+    """Sub-pixel poses of integer level-0 poses kyx[i] = (k, y, x):
+    rows (x + dx, y + dy, ((k + dk) * dtheta) mod 360, M(x, y, k))."""
+    res = []
+    for k, y, x in kyx:
+        s = neighbourhood27(field, pts, int(x), int(y), int(k), ntheta, dtheta_deg, nbhd, polarity)
+        d = subpixel_fit(s)
+        res.append((x + d[0], y + d[1], ((k + d[2]) * dtheta_deg) % 360.0, s[13]))
+    return np.array(res, dtype=np.float64).reshape(-1, 4)

@@ -686,3 +686,42 @@ double or_refine_gn(const double *field, int w, int h, const int32_t *tx, const 
     }
     return S;
 }
+
+/* Sub-pixel and sub-angle peak of a 3x3x3 neighbourhood of Eq. (1) scores
+ * (the quadratic-fit refinement of the digitised pose; not in the paper).
+ * s[(dk + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = M at (x + dx, y + dy, k + dk).
+ * Gradient g and Hessian H of M at the centre from central differences:
+ *   g_a = (M(+a) - M(-a)) / 2,  H_aa = M(+a) - 2 M(0) + M(-a),
+ *   H_ab = (M(+a+b) - M(+a-b) - M(-a+b) + M(-a-b)) / 4,
+ * the second-order Taylor model of M whose stationary point is
+ * delta = -H^-1 g.  That point is used when H is negative definite (the
+ * model has a maximum); otherwise every axis with H_aa < 0 takes its own
+ * parabola's vertex -g_a / H_aa and the others 0.  Each component is then
+ * clamped to [-1/2, 1/2] (a farther peak belongs to a neighbouring cell).
+ * delta[] = (dx, dy, dk): pixels, pixels, angle steps.                     */
+void or_subpixel_fit(const double *s, double *delta)
+{
+#define S(dk, dy, dx) s[((dk) + 1) * 9 + ((dy) + 1) * 3 + ((dx) + 1)]
+    const double c = S(0, 0, 0);
+    double g[3], hxx, hyy, hkk, hxy, hxk, hyk;
+    g[0] = 0.5 * (S(0, 0, 1) - S(0, 0, -1));
+    g[1] = 0.5 * (S(0, 1, 0) - S(0, -1, 0));
+    g[2] = 0.5 * (S(1, 0, 0) - S(-1, 0, 0));
+    hxx = S(0, 0, 1) - 2.0 * c + S(0, 0, -1);
+    hyy = S(0, 1, 0) - 2.0 * c + S(0, -1, 0);
+    hkk = S(1, 0, 0) - 2.0 * c + S(-1, 0, 0);
+    hxy = 0.25 * (S(0, 1, 1) - S(0, -1, 1) - S(0, 1, -1) + S(0, -1, -1));
+    hxk = 0.25 * (S(1, 0, 1) - S(-1, 0, 1) - S(1, 0, -1) + S(-1, 0, -1));
+    hyk = 0.25 * (S(1, 1, 0) - S(-1, 1, 0) - S(1, -1, 0) + S(-1, -1, 0));
+#undef S
+    /* -H, packed xx, xy, xk, yy, yk, kk */
+    const double A[6] = {-hxx, -hxy, -hxk, -hyy, -hyk, -hkk};
+    const int definite = A[0] > 0.0 && A[0] * A[3] - A[1] * A[1] > 0.0;
+    if (!(definite && or_solve3(A, g, delta))) {
+        delta[0] = hxx < 0.0 ? -g[0] / hxx : 0.0;
+        delta[1] = hyy < 0.0 ? -g[1] / hyy : 0.0;
+        delta[2] = hkk < 0.0 ? -g[2] / hkk : 0.0;
+    }
+    for (int a = 0; a < 3; ++a)
+        delta[a] = fmin(0.5, fmax(-0.5, delta[a]));
+}
