@@ -35,5 +35,6 @@ from .oracle import (  # noqa: F401
     refine_gn,
     subpixel_fit,
     neighbourhood27,
+    climb27,
     subpixel_poses,
 )

@@ -397,12 +397,35 @@ def neighbourhood27(field, pts, x, y, k, ntheta, dtheta_deg, nbhd=3, polarity=0)
     return out
 
 
-def subpixel_poses(field, pts, kyx, ntheta, dtheta_deg, nbhd=3, polarity=0):
-    """Sub-pixel poses of integer level-0 poses kyx[i] = (k, y, x):
-    rows (x + dx, y + dy, ((k + dk) * dtheta) mod 360, M(x, y, k))."""
+def climb27(s27):
+    """Index of the neighbour to move to, or 13 (the centre) when no
+    neighbour scores strictly higher; among equal best neighbours the first
+    in (dk, dy, dx) order."""
+    best, j = s27[13], 13
+    for i in range(27):
+        if s27[i] > best:
+            best, j = s27[i], i
+    return j
+
+
+def subpixel_poses(field, pts, kyx, ntheta, dtheta_deg, nbhd=3, polarity=0, max_moves=8):
+    """Sub-pixel poses of integer level-0 poses kyx[i] = (k, y, x).  The pose
+    first moves to the best of its 27 neighbours until no neighbour scores
+    higher (at most max_moves moves; the coarse-to-fine search can stop at
+    the edge of its window), then takes the quadratic fit of the
+    neighbourhood: rows (x + dx, y + dy, ((k + dk) * dtheta) mod 360,
+    M(x, y, k)) at the final integer pose."""
     res = []
     for k, y, x in kyx:
-        s = neighbourhood27(field, pts, int(x), int(y), int(k), ntheta, dtheta_deg, nbhd, polarity)
+        k, y, x = int(k), int(y), int(x)
+        for move in range(max_moves + 1):
+            s = neighbourhood27(field, pts, x, y, k, ntheta, dtheta_deg, nbhd, polarity)
+            j = climb27(s)
+            if j == 13 or move == max_moves:
+                break
+            k = (k + j // 9 - 1) % ntheta
+            y += (j // 3) % 3 - 1
+            x += j % 3 - 1
         d = subpixel_fit(s)
         res.append((x + d[0], y + d[1], ((k + d[2]) * dtheta_deg) % 360.0, s[13]))
     return np.array(res, dtype=np.float64).reshape(-1, 4)

@@ -107,3 +107,28 @@ def test_fit_moves_angle_toward_off_grid_truth():
                 errs_fit.append(dfit)
     assert len(errs_int) >= 2
     assert np.mean(errs_fit) < np.mean(errs_int)
+
+
+def test_climb_picks_the_strictly_best_neighbour():
+    s = np.zeros(27)
+    s[13] = 1.0
+    assert oracle.climb27(s) == 13                 # the centre is the best
+    s[4] = 1.0
+    assert oracle.climb27(s) == 13                 # a tie keeps the centre
+    s[22] = 1.5
+    s[5] = 1.5
+    assert oracle.climb27(s) == 5                  # first of the equal best
+    assert oracle.climb27(np.arange(27.0)) == 26
+
+
+def test_climb_reaches_the_same_peak_from_a_neighbouring_start():
+    tm, sc, gts = synth.config1_scene()
+    om = oracle.create_model(tm, 30, 60, 1, 4.0)
+    f = oracle.search_fields(sc, 1, 30)[0]
+    x, y, th = gts[0]
+    k = int(round(th / 4.0)) % 90
+    a = oracle.subpixel_poses(f, om.points[0], [(k, y, x)], 90, 4.0)[0]
+    b = oracle.subpixel_poses(f, om.points[0], [(k, y + 1, x - 1)], 90, 4.0)[0]
+    c = oracle.subpixel_poses(f, om.points[0], [(k, y + 1, x - 1)], 90, 4.0, max_moves=0)[0]
+    assert np.allclose(a, b, atol=1e-12)
+    assert not np.allclose(c[:2], a[:2], atol=1e-6)   # without moves the fit stays in the start's cell
