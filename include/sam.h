@@ -420,6 +420,28 @@ sam_status sam_score_bilinear_adjoint(sam_model *m, int level, const sam_field_r
                                       const int32_t *pose_field, const float *poses, int n_poses,
                                       const float *grad_score, float *grad_pose, void *stream);
 
+/* Sub-pixel and sub-angle poses by a quadratic fit (extends the digitised
+ * pose of Sec. II; the paper has no counterpart).  For each integer level-0
+ * pose (k, y, x) -- a detection's angle_index, level0_y, level0_x -- the
+ * Eq. (1) scores of the 27 poses (x + dx, y + dy, k + dk), dx, dy, dk in
+ * {-1, 0, 1} (angle index circular; neighbouring search `neighbourhood`, 1
+ * or 3; the model's polarity), then the stationary point of their
+ * second-order Taylor model (gradient and Hessian from central differences)
+ * when its Hessian is negative definite, else each axis that curves down
+ * takes its own parabola's vertex and the others stay; every offset is
+ * clamped to [-1/2, 1/2] (pixels, pixels, angle steps).
+ *   fields, n_fields, pose_field  as sam_score_bilinear: FP32 pixel-layout
+ *                    unit fields of level-0 search images; pose b uses
+ *                    fields[pose_field[b]] (pose_field NULL: field 0).
+ *   kyx              device int32 [n_poses][3] = (k, y, x).
+ *   out              device float [n_poses][4] = (x + dx, y + dy,
+ *                    theta_deg in [0, 360), M(x, y, theta_k)); NaN rows for
+ *                    a pose whose field index or angle index is out of range.
+ * One launch, stream-ordered, no allocation.  Errors: SAM_ERR_ARG (counts,
+ * null pointers, field sizes, neighbourhood), SAM_ERR_CUDA. */
+sam_status sam_subpixel_poses(sam_model *m, const sam_field_ref *fields, int n_fields, const int32_t *pose_field,
+                              const int32_t *kyx, int n_poses, int neighbourhood, float *out, void *stream);
+
 /* Sub-pixel and sub-degree refinement of n_poses poses (in place), one
  * launch: damped Gauss-Newton (Levenberg-Marquardt) on the terms of M_c,
  * each fitted to 1.  Per pose, lambda = 1e-3 and M_c with its normal

@@ -102,6 +102,7 @@ SIGNATURES = {
     "sam_score_bilinear_adjoint": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _vp,
                                             _vp, _vp]),
     "sam_refine_poses": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
+    "sam_subpixel_poses": (_c_int, [_vp, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
     "sam_profile_enable": (None, [_c_int]),
     "sam_set_graph_mode": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
@@ -584,6 +585,23 @@ def refine_poses(model: Model, fields, poses, pose_field=None, iterations=20, le
     _check(lib().sam_refine_poses(model.handle, int(level), refs, len(fields), _ptr(pf), _ptr(poses), B,
                                   int(iterations), _ptr(score), _stream(stream)), "sam_refine_poses")
     return score
+
+
+def subpixel_poses(model: Model, fields, kyx, pose_field=None, neighbourhood=3, stream=None):
+    """Sub-pixel / sub-angle poses of integer level-0 poses kyx (B, 3) int32 =
+    (k, y, x) by the quadratic fit of their 3x3x3 score neighbourhood (one
+    launch); returns a (B, 4) float32 tensor (x, y, theta_deg, M)."""
+    import torch
+    kyx = kyx.to(torch.int32).contiguous()
+    if kyx.dim() != 2 or kyx.shape[1] != 3 or not kyx.is_cuda:
+        raise ValueError("kyx is a (B, 3) CUDA tensor of (k, y, x)")
+    B = kyx.shape[0]
+    pf = _pose_field_arg(pose_field, B)
+    refs = _field_refs(fields)
+    out = torch.empty((B, 4), dtype=torch.float32, device=kyx.device)
+    _check(lib().sam_subpixel_poses(model.handle, refs, len(fields), _ptr(pf), _ptr(kyx), B, int(neighbourhood),
+                                    _ptr(out), _stream(stream)), "sam_subpixel_poses")
+    return out
 
 
 def _autograd_function():
