@@ -545,6 +545,44 @@ def run_gpu(args):
     e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
     e2e_value = shard.whole_job_rate(pp_step, args.steps, world, e2e_ms)
 
+    # ---- sub-pixel / sub-angle poses of the first batch's detections ----
+    subpixel = None
+    if rank == 0:
+        dets0 = step(0)
+        fields0 = [sam.unit_field(batches[0][i].contiguous(), LOW) for i in range(B)]
+        rows, owner = [], []
+        for i, ds in enumerate(dets0):
+            for d in ds:
+                rows.append((d["k"], d["y"], d["x"]))
+                owner.append(i)
+        if rows:
+            kyx = torch.tensor(rows, dtype=torch.int32, device=dev)
+            pft = torch.tensor(owner, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                sam.subpixel_poses(model, fields0, kyx, pft)
+            ms_sp = _event_ms(torch, dev, stream, lambda i: sam.subpixel_poses(model, fields0, kyx, pft), 20)
+            fit = sam.subpixel_poses(model, fields0, kyx, pft).cpu().numpy()
+            ang = lambda a, b: abs(((a - b) + 180.0) % 360.0 - 180.0)  # noqa: E731
+            e_int, e_fit, p_int, p_fit = [], [], [], []
+            for i, (k, y, x), f in zip(owner, rows, fit):
+                if not truth[i]:
+                    continue
+                gx, gy, gth = min(truth[i], key=lambda t: (t[0] - x) ** 2 + (t[1] - y) ** 2)
+                if (gx - x) ** 2 + (gy - y) ** 2 > 9:
+                    continue   # a detection of no instance
+                e_int.append(ang(k * STEP, gth))
+                e_fit.append(ang(float(f[2]), gth))
+                p_int.append(float(np.hypot(x - gx, y - gy)))
+                p_fit.append(float(np.hypot(f[0] - gx, f[1] - gy)))
+            subpixel = {"what": "quadratic fit of the 3x3x3 Eq. (1) neighbourhood of each detection of the first "
+                                "batch (sam_subpixel_poses, one launch)",
+                        "poses": len(rows), "ms": round(ms_sp, 4), "us_per_pose": round(1e3 * ms_sp / len(rows), 3),
+                        "instances": len(e_int),
+                        "mean_angle_err_deg": {"integer": round(float(np.mean(e_int)), 4) if e_int else None,
+                                               "fit": round(float(np.mean(e_fit)), 4) if e_fit else None},
+                        "mean_pos_err_px": {"integer": round(float(np.mean(p_int)), 4) if p_int else None,
+                                            "fit": round(float(np.mean(p_fit)), 4) if p_fit else None}}
+
     # ---- single-image latency (one detection, device-resident) ----
     one = batches[0][0].contiguous()
     # the scorer's tiling for one image per call is tuned on its own (setup)
@@ -718,6 +756,7 @@ def run_gpu(args):
         "forms": forms,
         "batched": batched,
         "differentiable": differentiable,
+        "subpixel": subpixel,
         "stress": stress,
         "wall_s": wall,
     }
