@@ -37,4 +37,7 @@ from .oracle import (  # noqa: F401
     neighbourhood27,
     climb27,
     subpixel_poses,
+    quant_bin,
+    score_map_quantized,
+    response_maps,
 )

@@ -80,6 +80,11 @@ def _L():
                                      _f64p, _c_int]
         lib.or_refine_gn.restype = _c_dbl
         lib.or_subpixel_fit.argtypes = [_f64p, _f64p]
+        lib.or_quant_bin.argtypes = [_c_dbl, _c_dbl, _c_int, _c_int]
+        lib.or_quant_bin.restype = _c_int
+        lib.or_score_map_quantized.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
+                                               _c_dbl, _c_int, _c_int, _c_int, _f64p]
+        lib.or_response_maps.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_int, _c_int, _f64p]
         _lib = lib
     return _lib
 
@@ -429,3 +434,33 @@ def subpixel_poses(field, pts, kyx, ntheta, dtheta_deg, nbhd=3, polarity=0, max_
         d = subpixel_fit(s)
         res.append((x + d[0], y + d[1], ((k + d[2]) * dtheta_deg) % 360.0, s[13]))
     return np.array(res, dtype=np.float64).reshape(-1, 4)
+
+
+# ---------------------------------------------------------------------------
+# quantised-direction form (response maps; an approximation of Eq. (1))
+# ---------------------------------------------------------------------------
+
+def quant_bin(px, py, nbins, polarity=0):
+    return int(_L().or_quant_bin(float(px), float(py), int(nbins), int(polarity)))
+
+
+def score_map_quantized(field, pts, ntheta, dtheta_deg, nbins, nbhd=3, polarity=0):
+    """M_q over the full step-1 pose grid: Eq. (1) with each rotated model
+    direction replaced by its bin centre; out[k, y, x]."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    out = np.empty((ntheta, h, w), dtype=np.float64)
+    _L().or_score_map_quantized(field, w, h, tx, ty, gx, gy, len(tx), int(ntheta), float(dtheta_deg), int(nbins),
+                                int(nbhd), int(polarity), out)
+    return out
+
+
+def response_maps(field, nbins, nbhd=3, polarity=0):
+    """R[b, y + 1, x + 1] = max over the window at (x, y) of u_b . w_hat, for
+    -1 <= x <= w, -1 <= y <= h."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    out = np.empty((nbins, h + 2, w + 2), dtype=np.float64)
+    _L().or_response_maps(field, w, h, int(nbhd), int(polarity), int(nbins), out)
+    return out

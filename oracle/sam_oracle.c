@@ -725,3 +725,79 @@ void or_subpixel_fit(const double *s, double *delta)
     for (int a = 0; a < 3; ++a)
         delta[a] = fmin(0.5, fmax(-0.5, delta[a]));
 }
+
+/* Quantised-direction form (an approximation of Eq. (1); not in the paper).
+ * Bin of a unit direction among nbins orientation bins: polarity 0 bins of
+ * width 2 pi / nbins centred on b 2 pi / nbins; polarity 1 (a direction and
+ * its opposite are one orientation) bins of width pi / nbins centred on
+ * b pi / nbins.  b = floor(a / width + 1/2) mod nbins, a = atan2(py, px),
+ * taken mod pi for polarity 1.                                             */
+int or_quant_bin(double px, double py, int nbins, int polarity)
+{
+    double a = atan2(py, px);
+    double width = (polarity ? OR_PI : 2.0 * OR_PI) / nbins;
+    if (polarity && a < 0.0)
+        a += OR_PI;
+    int b = (int)floor(a / width + 0.5);
+    b %= nbins;
+    if (b < 0)
+        b += nbins;
+    return b;
+}
+
+/* Unit vector of bin b's centre.                                           */
+static void or_bin_centre(int b, int nbins, int polarity, double *ux, double *uy)
+{
+    double phi = b * (polarity ? OR_PI : 2.0 * OR_PI) / nbins;
+    *ux = cos(phi);
+    *uy = sin(phi);
+}
+
+/* The quantised score: Eq. (1) with every rotated model direction replaced
+ * by the unit vector of its bin's centre,
+ *   M_q(u, theta_k) = (1/n) sum_i max_window u_{b_i} . w_hat  (|.| for
+ *   polarity 1; samples outside the image are 0, as in Eq. (1)),
+ * over the full pose grid (out[(k * h + y) * w + x], step 1).              */
+void or_score_map_quantized(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                            const int32_t *gx, const int32_t *gy, int n, int ntheta, double dtheta_deg,
+                            int nbins, int nbhd, int polarity, double *out)
+{
+    int32_t *ox = malloc(sizeof(int32_t) * (size_t)n), *oy = malloc(sizeof(int32_t) * (size_t)n);
+    double *px = malloc(sizeof(double) * (size_t)n), *py = malloc(sizeof(double) * (size_t)n);
+    double *qx = malloc(sizeof(double) * (size_t)n), *qy = malloc(sizeof(double) * (size_t)n);
+    for (int k = 0; k < ntheta; ++k) {
+        or_rotate_points(tx, ty, gx, gy, n, k, dtheta_deg, ox, oy, px, py);
+        for (int i = 0; i < n; ++i)
+            or_bin_centre(or_quant_bin(px[i], py[i], nbins, polarity), nbins, polarity, &qx[i], &qy[i]);
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                double sum = 0.0;
+                for (int i = 0; i < n; ++i)
+                    sum += or_vote(field, w, h, x + ox[i], y + oy[i], qx[i], qy[i], nbhd, polarity);
+                out[((size_t)k * h + y) * w + x] = sum / n;
+            }
+    }
+    free(ox);
+    free(oy);
+    free(px);
+    free(py);
+    free(qx);
+    free(qy);
+}
+
+/* Response maps of the quantised form: for every bin b and every window
+ * centre (x, y) with -1 <= x <= w, -1 <= y <= h,
+ *   R_b(x, y) = max_window u_b . w_hat (|.| for polarity 1),
+ * out[(b * (h + 2) + y + 1) * (w + 2) + x + 1]; a centre farther outside has
+ * an all-outside window, R = 0.                                            */
+void or_response_maps(const double *field, int w, int h, int nbhd, int polarity, int nbins, double *out)
+{
+    for (int b = 0; b < nbins; ++b) {
+        double ux, uy;
+        or_bin_centre(b, nbins, polarity, &ux, &uy);
+        for (int y = -1; y <= h; ++y)
+            for (int x = -1; x <= w; ++x)
+                out[((size_t)b * (h + 2) + y + 1) * (w + 2) + x + 1] =
+                    or_vote(field, w, h, x, y, ux, uy, nbhd, polarity);
+    }
+}
