@@ -583,6 +583,43 @@ def run_gpu(args):
                         "mean_pos_err_px": {"integer": round(float(np.mean(p_int)), 4) if p_int else None,
                                             "fit": round(float(np.mean(p_fit)), 4) if p_fit else None}}
 
+    # ---- quantised-direction form (response maps) on one top level ----
+    quantized = None
+    if rank == 0:
+        lvl = batches[0][0].contiguous()
+        for _ in range(LEVELS - 1):
+            hh, ww = lvl.shape
+            nxt = torch.empty((hh // 2, ww // 2), dtype=torch.uint8, device=dev)
+            sam.pyramid_down(lvl, nxt)
+            lvl = nxt
+        th_, tw_ = lvl.shape
+        top_l = LEVELS - 1
+        qfield = sam.unit_field(lvl, LOW)
+        pfield = torch.zeros((th_, sam.field_pitch(tw_, sam.LAYOUT_PAIRS), 2), dtype=torch.float32, device=dev)
+        sam.gradient(lvl, LOW, sam.FP32, pfield, layout=sam.LAYOUT_PAIRS)
+        exact = torch.empty((model.num_angles(top_l), th_, tw_), dtype=torch.float32, device=dev)
+        quantized = {"what": "one 160x128 top level, all 45 angles, every pose scored: response maps + gather-add "
+                             "(sam_score_map_quantized) against the exact Eq. (1) map (sam_score_map, no early "
+                             "termination)", "pose_points": int(exact.numel() * model.num_points(top_l))}
+        for _ in range(3):
+            sam.score_map(model, top_l, pfield, tw_, th_, sam.FP32, exact, 1, 1, 3, 0.0, 0, layout=sam.LAYOUT_PAIRS)
+        ms_exact = _event_ms(torch, dev, stream, lambda i: sam.score_map(model, top_l, pfield, tw_, th_, sam.FP32,
+                                                                         exact, 1, 1, 3, 0.0, 0,
+                                                                         layout=sam.LAYOUT_PAIRS), 20)
+        quantized["exact_ms"] = round(ms_exact, 4)
+        ex = exact.cpu().numpy()
+        for nb in (16, 32):
+            qmaps = torch.empty(sam.response_maps_bytes(tw_, th_, nb), dtype=torch.uint8, device=dev)
+            for _ in range(3):
+                q = sam.score_map_quantized(model, top_l, qfield, nb, 3, maps=qmaps)
+            ms_q = _event_ms(torch, dev, stream,
+                             lambda i: sam.score_map_quantized(model, top_l, qfield, nb, 3, maps=qmaps), 20)
+            err = np.abs(q.cpu().numpy() - ex)
+            quantized[f"bins{nb}"] = {"ms": round(ms_q, 4), "max_abs_err": round(float(err.max()), 5),
+                                      "mean_abs_err": round(float(err.mean()), 6),
+                                      "bound": round(2 * math.sin(2 * math.pi / nb / 4), 5),
+                                      "same_argmax": bool(int(np.argmax(q.cpu().numpy())) == int(np.argmax(ex)))}
+
     # ---- single-image latency (one detection, device-resident) ----
     one = batches[0][0].contiguous()
     # the scorer's tiling for one image per call is tuned on its own (setup)
@@ -757,6 +794,7 @@ def run_gpu(args):
         "batched": batched,
         "differentiable": differentiable,
         "subpixel": subpixel,
+        "quantized": quantized,
         "stress": stress,
         "wall_s": wall,
     }

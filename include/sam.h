@@ -420,6 +420,30 @@ sam_status sam_score_bilinear_adjoint(sam_model *m, int level, const sam_field_r
                                       const int32_t *pose_field, const float *poses, int n_poses,
                                       const float *grad_score, float *grad_pose, void *stream);
 
+/* Quantised-direction score map (response maps; an approximation of
+ * Eq. (1), the paper has no counterpart).  Every rotated model direction is
+ * replaced by the centre of its orientation bin (nbins bins over 360
+ * degrees, over 180 degrees for polarity 1; bin = nearest centre, computed
+ * on the host in FP64 and cached on the model), so the window maximum of
+ * Eq. (1) depends only on the bin: the response maps
+ *   R_b(x, y) = max over the window at (x, y) of u_b . w_hat (|.|), for
+ *   -1 <= x <= w, -1 <= y <= h,
+ * are computed once, then every pose of the step-1 grid is a gather-add
+ *   map[(k * h + y) * w + x] = (1/n) sum_i R_{b_i(k)}(x + ox_i, y + oy_i)
+ * (0 for a centre farther outside).  |map - Eq. (1)| <= 2 sin(bin width / 4).
+ *   field   device FP32 pixel-layout unit field (w x h x 2 floats, 8-byte
+ *           aligned), e.g. from sam_gradient.
+ *   nbins   2 .. 64.
+ *   maps    device scratch of sam_response_maps_bytes(w, h, nbins) bytes
+ *           (holds the response maps after the call).
+ *   map     device float array of num_angles(level) * h * w.
+ * Two launches, stream-ordered; the first call per (level, nbins) builds the
+ * bin table (a synchronous upload).  Errors: SAM_ERR_ARG, SAM_ERR_NOMEM,
+ * SAM_ERR_CUDA. */
+size_t sam_response_maps_bytes(int w, int h, int nbins);
+sam_status sam_score_map_quantized(sam_model *m, int level, const float *field, int w, int h, int nbins,
+                                   int neighbourhood, float *maps, size_t maps_bytes, float *map, void *stream);
+
 /* Sub-pixel and sub-angle poses by a quadratic fit (extends the digitised
  * pose of Sec. II; the paper has no counterpart).  For each integer level-0
  * pose (k, y, x) -- a detection's angle_index, level0_y, level0_x -- the

@@ -614,6 +614,8 @@ void sam_free_model(sam_model *m) {
         cudaFree(m->d_tables);
     if (m->ws.base)
         cudaFree(m->ws.base);
+    for (auto &q : m->qbins)
+        cudaFree(q.dev);
     delete m;
 }
 

@@ -129,6 +129,13 @@ struct sam_model {
     bool tuned[3][2] = {};
     sam::TileConfig tile[3][2];
     sam::GraphCache gc;
+    // orientation-bin tables of the quantised form, per (level, bins,
+    // polarity): device uint8 [ntheta][n], built on first use
+    struct QuantBins {
+        int level, nbins;
+        uint8_t *dev;
+    };
+    std::vector<QuantBins> qbins;
 };
 
 namespace sam {

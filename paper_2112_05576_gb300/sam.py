@@ -103,6 +103,9 @@ SIGNATURES = {
                                             _vp, _vp]),
     "sam_refine_poses": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
     "sam_subpixel_poses": (_c_int, [_vp, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _c_int, _vp, _vp]),
+    "sam_response_maps_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
+    "sam_score_map_quantized": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t,
+                                         _vp, _vp]),
     "sam_profile_enable": (None, [_c_int]),
     "sam_set_graph_mode": (None, [_c_int]),
     "sam_profile_read": (_c_int, [_f32p, _i32p, _c_int]),
@@ -585,6 +588,28 @@ def refine_poses(model: Model, fields, poses, pose_field=None, iterations=20, le
     _check(lib().sam_refine_poses(model.handle, int(level), refs, len(fields), _ptr(pf), _ptr(poses), B,
                                   int(iterations), _ptr(score), _stream(stream)), "sam_refine_poses")
     return score
+
+
+def response_maps_bytes(w, h, nbins):
+    return int(lib().sam_response_maps_bytes(int(w), int(h), int(nbins)))
+
+
+def score_map_quantized(model: Model, level, field, nbins=16, neighbourhood=3, maps=None, stream=None):
+    """Quantised-direction score map (num_angles, h, w) of an FP32 pixel-layout
+    unit field (h, w, 2) CUDA tensor; `maps` optional scratch (uint8 tensor of
+    response_maps_bytes) that holds the response maps afterwards."""
+    import torch
+    if field.dtype != torch.float32 or field.dim() != 3 or field.shape[2] != 2 or not field.is_contiguous():
+        raise ValueError("field is a contiguous (h, w, 2) float32 CUDA tensor")
+    h, w = field.shape[0], field.shape[1]
+    nb = response_maps_bytes(w, h, nbins)
+    if maps is None:
+        maps = torch.empty(max(nb, 1), dtype=torch.uint8, device=field.device)
+    out = torch.empty((model.num_angles(level), h, w), dtype=torch.float32, device=field.device)
+    _check(lib().sam_score_map_quantized(model.handle, int(level), _ptr(field), w, h, int(nbins), int(neighbourhood),
+                                         _ptr(maps), maps.numel() * maps.element_size(), _ptr(out), _stream(stream)),
+           "sam_score_map_quantized")
+    return out
 
 
 def subpixel_poses(model: Model, fields, kyx, pose_field=None, neighbourhood=3, stream=None):
