@@ -23,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -71,7 +72,10 @@ class ClockSampler:
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        # raw samples (the summary goes into the JSON line); BENCH_CLOCKS_DIR
+        # keeps them elsewhere
+        self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"sam_bench_clocks_gpu{gpu}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

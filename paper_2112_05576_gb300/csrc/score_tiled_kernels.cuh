@@ -402,7 +402,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
 
 // Where a work unit of the tiled scorer lies: image, super-tile origin
 // (poses), angles [k_begin, k_end).  unit = super-tile + tiles * (angle
-// group + groups * image), the bound launch's linear CTA index.
+// group + groups * image), the linear CTA index of the one-CTA-per-unit launch.
 struct UnitPos {
     int img, stx0, sty0, k_begin, k_end;
 };
