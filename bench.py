@@ -77,19 +77,36 @@ class ClockSampler:
         self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
                                  f"sam_bench_clocks_gpu{gpu}_{os.getpid()}.csv")
 
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for line in f if line.endswith("\n"))
+        except OSError:
+            return 0
+
+    def _wait_lines(self, n, limit_s):
+        t0 = time.perf_counter()
+        while self._lines() < n and time.perf_counter() - t0 < limit_s:
+            time.sleep(0.005)
+
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            # the sampler is running before the timed region starts
+            self._wait_lines(1, 5.0)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
         if self.proc is not None:
+            # and takes one more sample after it (a region shorter than the
+            # sampling interval still gets the samples on both sides)
+            self._wait_lines(self._lines() + 1, 1.0)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
