@@ -277,8 +277,15 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
  * pose within the storage error bound of min_score is rescored in FP32 and
  * every other pose written -inf, as in sam_detect; scratch (device, 8-byte
  * aligned) of sam_score_window_scratch_bytes(R) bytes holds up to R such
- * poses, and poses beyond R are written NaN.  Stream-ordered, no
- * allocation, no synchronisation.  Errors: SAM_ERR_ARG (ranges, alignment,
+ * poses, and poses beyond R are written NaN.  With early_termination the
+ * chunked kernel first applies the edge-presence bound (a pose is scored
+ * only if enough of its points have an edge pixel that can vote for them in
+ * their neighbouring-search window): whole-image edge bitmaps and one bit
+ * per pose, in scratch taken from and returned to the device's default
+ * stream-ordered pool on `stream` (cudaMallocAsync / cudaFreeAsync); when
+ * the pool has no room or `stream` is being captured, the bound is skipped
+ * and every pose scored.  Otherwise no allocation; stream-ordered, no
+ * synchronisation.  Errors: SAM_ERR_ARG (ranges, alignment,
  * nk * gw * gh >= 2^32, nk > 65535, a template no scorer's window fits),
  * SAM_ERR_CUDA. */
 size_t sam_score_window_scratch_bytes(size_t max_rescored);

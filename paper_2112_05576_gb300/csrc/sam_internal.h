@@ -279,6 +279,24 @@ struct ChunkArgs {
     int early;
     int *err;
     unsigned long long *exec;
+    const uint32_t *alive; // edge-presence bound: one bit per pose [count][nk][H][alive_w] (null: none)
+    int alive_w;
+};
+
+// The chunked form's edge-presence bound (score_tiled_kernels.cuh,
+// chunk_bound_kernel).
+struct ChunkBoundArgs {
+    const RotPt *rot;        // points [nth][n] (any order within an angle)
+    int n;
+    const uint32_t *dplanes; // dilated planes [count][4 or 1][H + 2][ppw]
+    int H, ppw;              // field rows; words per plane row
+    int gx0, gy0, k0;        // pose window origin (level pixels) and first angle
+    int gh, nk, count;
+    int aw;                  // alive words per pose row: (gw + 31) / 32
+    int lpr;                 // lanes per pose row (32, 16, 8, 4, 2 or 1; >= aw or 32)
+    int groups;              // word groups of lpr words per pose row
+    int emin;
+    uint32_t *alive;         // [count][nk][gh][aw]
 };
 
 struct PairScore;
@@ -288,6 +306,8 @@ struct PairScore;
                                    bool pol, int warps, int tc, cudaStream_t st);                                   \
     cudaError_t launch_chunked_##suf(const CUtensorMap &tm, const ChunkArgs &a, dim3 grid, size_t smem, int nbhd,   \
                                      bool pol, int warps, cudaStream_t st);                                         \
+    cudaError_t launch_chunk_bound_##suf(const void *field, int wp, int H, size_t img_px, bool pol,                \
+                                         uint32_t *nplanes, const ChunkBoundArgs &b, cudaStream_t st);              \
     cudaError_t launch_pairs_##suf(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, \
                                    bool pol, int early, size_t smem, size_t win_bytes, unsigned *counter, int *err, \
                                    unsigned long long *exec, cudaStream_t st);

@@ -334,17 +334,90 @@ cudaError_t launch_score_chunked(const sam_model *m, int level, const void *fiel
     a.early = early;
     a.err = fl.err;
     a.exec = fl.exec;
+    a.alive = nullptr;
+    a.alive_w = 0;
     dim3 grid((unsigned)(a.tiles_x * tiles_y), (unsigned)pw.nk, (unsigned)count);
     const size_t smem = (size_t)bxw * byw * g.pair_bytes / 2 + 128;
     const bool pol = polarity != 0;
-    switch (precision) {
-    case SAM_FP32:
-        return launch_chunked_f32(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
-    case SAM_FP16:
-        return launch_chunked_f16(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
-    default:
-        return launch_chunked_bf16(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+    cudaError_t e = cudaSuccess;
+    // The edge-presence bound (with early termination): whole-image planes
+    // and one alive bit per pose in stream-ordered scratch, freed after the
+    // scorer.  Skipped, and every pose scored, when the scratch cannot be had
+    // or the stream is being captured.
+    void *bound_mem = nullptr;
+    const int emin = early ? edge_count_threshold(a.thresh, precision) : 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    bool capturing = true;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess)
+        capturing = cs != cudaStreamCaptureStatusNone;
+    else
+        (void)cudaGetLastError();   // the query's own error
+    const long long bound_tasks = (long long)pw.gh * ((pw.gw + 31) / 32) * pw.nk * count;   // warps, at most
+    if (emin > 0 && L.n < 65536 && !capturing && wp % 2 == 0 && field_img_px % 2 == 0 && H + 2 <= 65535 &&
+        count * 4 <= 65535 && bound_tasks < 8LL * 0x7fffffffLL) {
+        const int nq = pol ? 1 : 4;
+        const int ppw = (wp + 2 + 31) / 32;
+        const size_t plane_words = (size_t)count * nq * (H + 2) * ppw;
+        const int aw = (pw.gw + 31) / 32;
+        const size_t alive_words = (size_t)count * pw.nk * pw.gh * aw;
+        if (cudaMallocAsync(&bound_mem, (2 * plane_words + alive_words) * 4, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            bound_mem = nullptr;
+        } else {
+            uint32_t *np = static_cast<uint32_t *>(bound_mem);
+            ChunkBoundArgs b;
+            b.rot = D.crot;
+            b.n = L.n;
+            b.dplanes = np + plane_words;
+            b.H = H;
+            b.ppw = ppw;
+            b.gx0 = pw.x0;
+            b.gy0 = pw.y0;
+            b.k0 = pw.k0;
+            b.gh = pw.gh;
+            b.nk = pw.nk;
+            b.count = count;
+            b.aw = aw;
+            b.lpr = 1;
+            while (b.lpr < 32 && b.lpr < aw)
+                b.lpr *= 2;
+            b.groups = (aw + b.lpr - 1) / b.lpr;
+            b.emin = emin;
+            b.alive = np + 2 * plane_words;
+            switch (precision) {
+            case SAM_FP32:
+                e = launch_chunk_bound_f32(field, wp, H, field_img_px, pol, np, b, st);
+                break;
+            case SAM_FP16:
+                e = launch_chunk_bound_f16(field, wp, H, field_img_px, pol, np, b, st);
+                break;
+            default:
+                e = launch_chunk_bound_bf16(field, wp, H, field_img_px, pol, np, b, st);
+                break;
+            }
+            a.alive = b.alive;
+            a.alive_w = aw;
+        }
     }
+    if (e == cudaSuccess) {
+        switch (precision) {
+        case SAM_FP32:
+            e = launch_chunked_f32(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+            break;
+        case SAM_FP16:
+            e = launch_chunked_f16(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+            break;
+        default:
+            e = launch_chunked_bf16(tm, a, grid, smem, nbhd, pol, cfg.warps, st);
+            break;
+        }
+    }
+    if (bound_mem) {
+        const cudaError_t fe = cudaFreeAsync(bound_mem, st);
+        if (e == cudaSuccess)
+            e = fe;
+    }
+    return e;
 }
 
 // 2-D tensor map of one image's pairs-layout field for the persistent kernel

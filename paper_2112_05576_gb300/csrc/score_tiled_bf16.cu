@@ -15,6 +15,11 @@ cudaError_t launch_chunked_bf16(const CUtensorMap &tm, const ChunkArgs &a, dim3 
     return chunked_dispatch<__nv_bfloat16>(tm, a, grid, smem, nbhd, pol, warps, st);
 }
 
+cudaError_t launch_chunk_bound_bf16(const void *field, int wp, int H, size_t img_px, bool pol, uint32_t *nplanes,
+                                 const ChunkBoundArgs &b, cudaStream_t st) {
+    return chunk_bound_dispatch<__nv_bfloat16>(field, wp, H, img_px, pol, nplanes, b, st);
+}
+
 cudaError_t launch_pairs_bf16(const PairScore *pairs, int n_pairs, int total, const TileConfig &cfg, int nbhd, bool pol,
                            int early, size_t smem, size_t win_bytes, unsigned *counter, int *err,
                            unsigned long long *exec, cudaStream_t st) {

@@ -1333,7 +1333,10 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
 // sum takes one rounding per chunk rather than one per point: with ~6000
 // points per pose a plain serial FP32 sum drifts by ~1e-5 of the mean.  The window buffer is reused chunk after chunk
 // (mbarrier phase alternates; a proxy fence orders the previous chunk's reads
-// before the next copy).
+// before the next copy).  With the edge-presence bound (a.alive, written by
+// chunk_bound_kernel) poses it proves below min_score are written -inf, a
+// warp none of whose poses is alive computes nothing, and a CTA none of whose
+// poses is alive stages no window.
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                     const ChunkArgs a) {
@@ -1373,9 +1376,34 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
     const RotPt *P = a.rot + (size_t)k * a.n;
     const int c_begin = a.cstart[k], c_end = a.cstart[k + 1];
     bool alive = true;
+    // poses the edge-presence bound leaves: bit 2j (2j + 1) of keep[r] for
+    // pose (x0 + 2j (+ 1), y0 + r); every pose when there is no bound
+    uint32_t keep[TR];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+        keep[r] = (1u << TC) - 1u;
+    if (a.alive) {
+        const uint32_t *am = a.alive + ((size_t)img * gridDim.y + kl) * (size_t)a.H * a.alive_w;
+        const int mx = x0 - a.ox, wi = mx >> 5, sh = mx & 31;
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            const int my = y0 - a.oy + r;
+            uint32_t v = 0u;
+            if (my < a.H && wi < a.alive_w) {
+                const uint32_t *row = am + (size_t)my * a.alive_w;
+                v = __funnelshift_r(row[wi], wi + 1 < a.alive_w ? row[wi + 1] : 0u, sh) & ((1u << TC) - 1u);
+            }
+            keep[r] = v;
+            any = any || v != 0u;
+        }
+        alive = __any_sync(0xffffffffu, any);
+    }
+    // a CTA none of whose poses survived the bound stages nothing
+    const int c_stop = (a.alive && !__syncthreads_or(alive)) ? c_begin : c_end;
     int done = 0;
     uint32_t parity = 0;
-    for (int c = c_begin; c < c_end; ++c) {
+    for (int c = c_begin; c < c_stop; ++c) {
         const int4 b = a.cbox[c];
         const int2 rg = a.crange[c];
         if (threadIdx.x == 0) {
@@ -1448,7 +1476,8 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
                 for (int r = 0; r < TR; ++r)
 #pragma unroll
                     for (int j = 0; j < TC / 2; ++j)
-                        low = low && (acc[r][j].x < lim) && (acc[r][j].y < lim);
+                        low = low && (!((keep[r] >> (2 * j)) & 1u) || acc[r][j].x < lim) &&
+                              (!((keep[r] >> (2 * j + 1)) & 1u) || acc[r][j].y < lim);
                 if (__all_sync(0xffffffffu, low))
                     alive = false;
             }
@@ -1474,8 +1503,8 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
 #pragma unroll
         for (int j = 0; j < TC / 2; ++j) {
             const int x = x0 + 2 * j - a.ox;
-            const float v0 = alive ? acc[r][j].x * a.inv_n : -INFINITY;
-            const float v1 = alive ? acc[r][j].y * a.inv_n : -INFINITY;
+            const float v0 = alive && ((keep[r] >> (2 * j)) & 1u) ? acc[r][j].x * a.inv_n : -INFINITY;
+            const float v1 = alive && ((keep[r] >> (2 * j + 1)) & 1u) ? acc[r][j].y * a.inv_n : -INFINITY;
             if (x + 1 < a.W && (a.W & 1) == 0) {
                 *reinterpret_cast<float2 *>(row + x) = make_float2(v0, v1);
             } else {
@@ -1486,6 +1515,178 @@ __global__ void __launch_bounds__(WARPS * 32) score_chunked_kernel(const __grid_
             }
         }
     }
+}
+
+// Edge-presence bound of the chunked form.  A chunked CTA cannot hold the
+// bitmaps of every point's reach (a 512-pixel template reaches ~724 pixels),
+// so the bound works from whole-image planes in global memory instead:
+//   1. chunk_edge_planes_kernel: plane q of N holds, for every pixel of the
+//      field's TMA extent (wp x H) and a one-pixel margin, whether it is an
+//      edge pixel that can give a positive vote to a model direction in
+//      quadrant q (the rule of build_edge_bits);
+//   2. chunk_dilate_kernel: D_q = N_q dilated by 3 x 3;
+//   3. chunk_bound_kernel: for each pose of the window, the number of points
+//      whose projected centre hits D of their direction's quadrant, counted
+//      bit-sliced 32 poses per word, and one alive bit per pose: count >=
+//      emin.  A pose with count < emin is below min_score (the argument of
+//      edge_count_threshold), so the chunked kernel writes it -inf and skips
+//      every CTA none of whose poses is alive.
+// Plane layout: [image][q][H + 2][ppw] words, bit c of word w of row r for
+// field pixel (32 w + c - 1, r - 1); ppw = (wp + 2 + 31) / 32.
+template <typename E, bool POL>
+__global__ void __launch_bounds__(256) chunk_edge_planes_kernel(const typename Pairs<E>::Raw *__restrict__ field,
+                                                                int wp, int H, size_t img_pairs, int ppw,
+                                                                uint32_t *__restrict__ nplanes) {
+    constexpr int NQ = POL ? 1 : 4;
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y, img = blockIdx.z;
+    if (wi >= ppw)
+        return;
+    uint32_t e[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        e[q] = 0u;
+    const int y = r - 1;
+    if (y >= 0 && y < H) {
+        const typename Pairs<E>::Raw *row = field + img * img_pairs + (size_t)y * (wp / 2);
+        for (int c = 0; c < 32; ++c) {
+            const int x = 32 * wi + c - 1;
+            if (x < 0 || x >= wp)
+                continue;
+            const float4 v = Pairs<E>::get(row, x >> 1);   // {x0, x1, y0, y1}
+            const float gx = (x & 1) ? v.y : v.x, gy = (x & 1) ? v.w : v.z;
+            if (gx != 0.f || gy != 0.f) {
+                if (POL) {
+                    e[0] |= 1u << c;
+                } else {
+                    const int opp = (quadrant(gx, gy) + 2) & 3;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (q != opp)
+                            e[q] |= 1u << c;
+                }
+            }
+        }
+    }
+    const size_t plane = (size_t)(H + 2) * ppw;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        nplanes[((size_t)img * NQ + q) * plane + (size_t)r * ppw + wi] = e[q];
+}
+
+// D = N dilated by 3 x 3 (grid: words x rows x image-planes).
+template <typename E>
+__global__ void __launch_bounds__(256) chunk_dilate_kernel(const uint32_t *__restrict__ nplanes, int rows, int ppw,
+                                                           uint32_t *__restrict__ dplanes) {
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (wi >= ppw)
+        return;
+    const uint32_t *pl = nplanes + (size_t)blockIdx.z * rows * ppw;
+    uint32_t d = 0u;
+    for (int rr = r - 1; rr <= r + 1; ++rr) {
+        if (rr < 0 || rr >= rows)
+            continue;
+        const uint32_t *row = pl + (size_t)rr * ppw;
+        const uint32_t c = row[wi];
+        const uint32_t lft = wi > 0 ? row[wi - 1] : 0u, rgt = wi + 1 < ppw ? row[wi + 1] : 0u;
+        // bit b of the result: pixels b - 1, b, b + 1
+        d |= c | (c << 1) | (lft >> 31) | (c >> 1) | (rgt << 31);
+    }
+    dplanes[(size_t)blockIdx.z * rows * ppw + (size_t)r * ppw + wi] = d;
+}
+
+// One warp per (image, angle, 32 / lpr pose rows, lpr words): lane L counts
+// for the 32 poses of word (g lpr + L % lpr) of pose row (rb + L / lpr).
+template <typename E, bool POL>
+__global__ void __launch_bounds__(256) chunk_bound_kernel(const ChunkBoundArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int rpw = 32 / a.lpr;
+    const long long task = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long row_tasks = (long long)((a.gh + rpw - 1) / rpw) * a.groups;
+    if (task >= row_tasks * a.nk * a.count)
+        return;
+    const int g = (int)(task % a.groups);
+    const int rb = (int)((task / a.groups) % ((a.gh + rpw - 1) / rpw)) * rpw;
+    const int kl = (int)((task / row_tasks) % a.nk);
+    const int img = (int)(task / (row_tasks * a.nk));
+    const int wi = g * a.lpr + lane % a.lpr;
+    const int y = rb + lane / a.lpr;
+    constexpr int NQ = POL ? 1 : 4;
+    const size_t plane = (size_t)(a.H + 2) * a.ppw;
+    const uint32_t *pl = a.dplanes + (size_t)img * NQ * plane;
+    // plane row and column of this lane's first pose's centre before the
+    // point's offset (+1: the planes' margin)
+    const int prow = a.gy0 + y + 1, pcol = a.gx0 + 32 * wi + 1;
+    const RotPt *P = a.rot + (size_t)(a.k0 + kl) * a.n;
+    uint32_t ones = 0u, twos = 0u, fours = 0u, pl16[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        pl16[q] = 0u;
+    int2 qo = make_int2(0, 0);
+    const int np8 = (a.n + 7) & ~7;
+    for (int i0 = 0; i0 < np8; i0 += 8) {
+        if ((i0 & 31) == 0) {
+            const int ii = i0 + lane;
+            qo = make_int2(0, 0);
+            if (ii < a.n) {
+                const RotPt t = P[ii];
+                qo = make_int2(t.ox, t.oy * 4 + (POL ? 0 : quadrant(t.px, t.py)));
+            }
+        }
+        uint32_t mm[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
+            const int qoy = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+            const int r = prow + (qoy >> 2);        // arithmetic shift: floor
+            const int c = pcol + qox;
+            const int w0 = c >> 5, sh = c & 31;
+            uint32_t lo = 0u, hi = 0u;
+            if (i0 + j < a.n && r >= 0 && r < a.H + 2) {
+                const uint32_t *row = pl + (size_t)(qoy & 3) * plane + (size_t)r * a.ppw;
+                if (w0 >= 0 && w0 < a.ppw)
+                    lo = row[w0];
+                if (w0 + 1 >= 0 && w0 + 1 < a.ppw)
+                    hi = row[w0 + 1];
+            }
+            mm[j] = __funnelshift_r(lo, hi, sh);
+        }
+        auto csa = [](uint32_t &h, uint32_t &l, uint32_t a_, uint32_t b_, uint32_t c_) {
+            const uint32_t u = a_ ^ b_;
+            h = (a_ & b_) | (u & c_);
+            l = u ^ c_;
+        };
+        uint32_t t1, t2, t3, t4, f1, f2, e8;
+        csa(t1, ones, ones, mm[0], mm[1]);
+        csa(t2, ones, ones, mm[2], mm[3]);
+        csa(f1, twos, twos, t1, t2);
+        csa(t3, ones, ones, mm[4], mm[5]);
+        csa(t4, ones, ones, mm[6], mm[7]);
+        csa(f2, twos, twos, t3, t4);
+        csa(e8, fours, fours, f1, f2);
+#pragma unroll
+        for (int q = 3; q < 16; ++q) {
+            const uint32_t cy = pl16[q] & e8;
+            pl16[q] ^= e8;
+            e8 = cy;
+        }
+    }
+    pl16[0] = ones;
+    pl16[1] = twos;
+    pl16[2] = fours;
+    uint32_t gt = 0u, eq = ~0u;
+#pragma unroll
+    for (int q = 15; q >= 0; --q) {
+        if ((a.emin >> q) & 1) {
+            eq &= pl16[q];
+        } else {
+            gt |= eq & pl16[q];
+            eq &= ~pl16[q];
+        }
+    }
+    if (wi < a.aw && y < a.gh)
+        a.alive[(((size_t)img * a.nk + kl) * a.gh + y) * a.aw + wi] = gt | eq;
 }
 
 // ---------------------------------------------------------------------------
@@ -1579,6 +1780,32 @@ cudaError_t chunked_dispatch(const CUtensorMap &tm, const ChunkArgs &a, dim3 gri
     if (nbhd == 3)
         return pol ? launch_c<E, 3, true, 8>(tm, a, grid, smem, st) : launch_c<E, 3, false, 8>(tm, a, grid, smem, st);
     return pol ? launch_c<E, 1, true, 8>(tm, a, grid, smem, st) : launch_c<E, 1, false, 8>(tm, a, grid, smem, st);
+}
+
+// The three bound kernels of the chunked form (buffers as chunk_bound_kernel).
+template <typename E>
+cudaError_t chunk_bound_dispatch(const void *field, int wp, int H, size_t img_px, bool pol, uint32_t *nplanes,
+                                 const ChunkBoundArgs &b, cudaStream_t st) {
+    using Raw = typename Pairs<E>::Raw;
+    const int nq = pol ? 1 : 4;
+    const dim3 gp((unsigned)((b.ppw + 255) / 256), (unsigned)(H + 2), (unsigned)b.count);
+    if (pol)
+        chunk_edge_planes_kernel<E, true><<<gp, 256, 0, st>>>(static_cast<const Raw *>(field), wp, H, img_px / 2,
+                                                                b.ppw, nplanes);
+    else
+        chunk_edge_planes_kernel<E, false><<<gp, 256, 0, st>>>(static_cast<const Raw *>(field), wp, H, img_px / 2,
+                                                                 b.ppw, nplanes);
+    const dim3 gd((unsigned)((b.ppw + 255) / 256), (unsigned)(H + 2), (unsigned)(b.count * nq));
+    chunk_dilate_kernel<E><<<gd, 256, 0, st>>>(nplanes, H + 2, b.ppw, const_cast<uint32_t *>(b.dplanes));
+    const int rpw = 32 / b.lpr;
+    const long long tasks = (long long)((b.gh + rpw - 1) / rpw) * b.groups * b.nk * b.count;
+    const unsigned blocks = (unsigned)((tasks + 7) / 8);
+    if (pol)
+        chunk_bound_kernel<E, true><<<blocks, 256, 0, st>>>(b);
+    else
+        chunk_bound_kernel<E, false><<<blocks, 256, 0, st>>>(b);
+    count_launches(3);
+    return cudaGetLastError();
 }
 
 template <typename E, int NB, bool POL, int WARPS, int TC>
