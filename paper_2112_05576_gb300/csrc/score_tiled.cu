@@ -354,7 +354,8 @@ cudaError_t launch_score_chunked(const sam_model *m, int level, const void *fiel
         (void)cudaGetLastError();   // the query's own error
     const long long bound_tasks = (long long)pw.gh * ((pw.gw + 31) / 32) * pw.nk * count;   // warps, at most
     if (emin > 0 && L.n < 65536 && !capturing && wp % 2 == 0 && field_img_px % 2 == 0 && H + 2 <= 65535 &&
-        count * 4 <= 65535 && bound_tasks < 8LL * 0x7fffffffLL) {
+        count * 4 <= 65535 && bound_tasks < 8LL * 0x7fffffffLL &&
+        4LL * (H + 2) * ((wp + 2 + 31) / 32) < 0x7fffffffLL) {
         const int nq = pol ? 1 : 4;
         const int ppw = (wp + 2 + 31) / 32;
         const size_t plane_words = (size_t)count * nq * (H + 2) * ppw;

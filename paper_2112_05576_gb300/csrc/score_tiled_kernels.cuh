@@ -1598,6 +1598,9 @@ __global__ void __launch_bounds__(256) chunk_dilate_kernel(const uint32_t *__res
 
 // One warp per (image, angle, 32 / lpr pose rows, lpr words): lane L counts
 // for the 32 poses of word (g lpr + L % lpr) of pose row (rb + L / lpr).
+// Lanes of one pose row read consecutive words, so the upper word a lane's
+// 32-bit window needs is its right neighbour's lower word (a shuffle); the
+// last lane of the row loads its own.
 template <typename E, bool POL>
 __global__ void __launch_bounds__(256) chunk_bound_kernel(const ChunkBoundArgs a) {
     const int lane = threadIdx.x & 31;
@@ -1610,46 +1613,56 @@ __global__ void __launch_bounds__(256) chunk_bound_kernel(const ChunkBoundArgs a
     const int rb = (int)((task / a.groups) % ((a.gh + rpw - 1) / rpw)) * rpw;
     const int kl = (int)((task / row_tasks) % a.nk);
     const int img = (int)(task / (row_tasks * a.nk));
-    const int wi = g * a.lpr + lane % a.lpr;
+    const int lw = lane % a.lpr;
+    const bool last = lw == a.lpr - 1;
+    const int wi = g * a.lpr + lw;
     const int y = rb + lane / a.lpr;
     constexpr int NQ = POL ? 1 : 4;
-    const size_t plane = (size_t)(a.H + 2) * a.ppw;
+    const int rows = a.H + 2;
+    const int plane = rows * a.ppw;   // 4 planes < 2^31 words (checked by the launcher)
     const uint32_t *pl = a.dplanes + (size_t)img * NQ * plane;
-    // plane row and column of this lane's first pose's centre before the
-    // point's offset (+1: the planes' margin)
-    const int prow = a.gy0 + y + 1, pcol = a.gx0 + 32 * wi + 1;
+    // plane row of this lane's pose row before the point's offset (+1: the
+    // planes' margin); the plane column of bit b of its word for a point
+    // with column offset ox is (gx0 + 1 + ox) + 32 wi + b
+    const int prow = a.gy0 + y + 1;
+    const uint32_t *lrow = pl + (size_t)max(prow, 0) * a.ppw;   // only used when the row is inside
     const RotPt *P = a.rot + (size_t)(a.k0 + kl) * a.n;
     uint32_t ones = 0u, twos = 0u, fours = 0u, pl16[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q)
         pl16[q] = 0u;
-    int2 qo = make_int2(0, 0);
+    // per point, computed by the lane that loads it: the plane column of the
+    // first pose's centre, the row offset, and the word offset of its
+    // quadrant plane and row
+    int qc = 0, qoy = 0, qoff = 0;
     const int np8 = (a.n + 7) & ~7;
     for (int i0 = 0; i0 < np8; i0 += 8) {
         if ((i0 & 31) == 0) {
             const int ii = i0 + lane;
-            qo = make_int2(0, 0);
+            qc = qoy = qoff = 0;
             if (ii < a.n) {
                 const RotPt t = P[ii];
-                qo = make_int2(t.ox, t.oy * 4 + (POL ? 0 : quadrant(t.px, t.py)));
+                const int q = POL ? 0 : quadrant(t.px, t.py);
+                qc = a.gx0 + 1 + t.ox;
+                qoy = t.oy;
+                qoff = q * plane + t.oy * a.ppw;
             }
         }
         uint32_t mm[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
-            const int qoy = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
-            const int r = prow + (qoy >> 2);        // arithmetic shift: floor
-            const int c = pcol + qox;
-            const int w0 = c >> 5, sh = c & 31;
-            uint32_t lo = 0u, hi = 0u;
-            if (i0 + j < a.n && r >= 0 && r < a.H + 2) {
-                const uint32_t *row = pl + (size_t)(qoy & 3) * plane + (size_t)r * a.ppw;
-                if (w0 >= 0 && w0 < a.ppw)
-                    lo = row[w0];
-                if (w0 + 1 >= 0 && w0 + 1 < a.ppw)
-                    hi = row[w0 + 1];
-            }
+            const int c = __shfl_sync(0xffffffffu, qc, (i0 + j) & 31) + 32 * wi;
+            const int oy = __shfl_sync(0xffffffffu, qoy, (i0 + j) & 31);
+            const int off = __shfl_sync(0xffffffffu, qoff, (i0 + j) & 31);
+            const int w0 = c >> 5, sh = c & 31;   // arithmetic shift: floor
+            const bool row_in = i0 + j < a.n && (unsigned)(prow + oy) < (unsigned)rows;
+            const uint32_t *src = lrow + off + w0;   // plane q, row prow + oy, word w0 (when inside)
+            uint32_t lo = 0u;
+            if (row_in && (unsigned)w0 < (unsigned)a.ppw)
+                lo = *src;
+            uint32_t hi = __shfl_down_sync(0xffffffffu, lo, 1);
+            if (last)
+                hi = row_in && (unsigned)(w0 + 1) < (unsigned)a.ppw ? src[1] : 0u;
             mm[j] = __funnelshift_r(lo, hi, sh);
         }
         auto csa = [](uint32_t &h, uint32_t &l, uint32_t a_, uint32_t b_, uint32_t c_) {
@@ -1667,6 +1680,8 @@ __global__ void __launch_bounds__(256) chunk_bound_kernel(const ChunkBoundArgs a
         csa(e8, fours, fours, f1, f2);
 #pragma unroll
         for (int q = 3; q < 16; ++q) {
+            if (e8 == 0u)
+                break;
             const uint32_t cy = pl16[q] & e8;
             pl16[q] ^= e8;
             e8 = cy;
