@@ -456,6 +456,7 @@ def run_stress(args, sam, torch, dev, stream):
             ms = _event_ms(torch, dev, stream, call, reps)
             ex = sam.executed_pose_points(reset=True) / reps
             res[label] = {"ms": round(ms, 3), "value": pp / (ms * 1e-3), "unit": UNIT,
+                          "edge_presence_bound": bool(early),
                           "executed_pose_points": int(ex),
                           "smem_frac": round(ex * SMEM_B_PER_PP * (1.0 if prec == 0 else 0.5) / (ms * 1e-3) / 1e12
                                              / smem_peak, 4),
