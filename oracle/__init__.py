@@ -40,4 +40,7 @@ from .oracle import (  # noqa: F401
     quant_bin,
     score_map_quantized,
     response_maps,
+    angle_codes,
+    angle_field,
+    search_angle_fields,
 )

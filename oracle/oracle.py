@@ -24,6 +24,7 @@ _lib = None
 
 _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_u16p = np.ctypeslib.ndpointer(dtype=np.uint16, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _c_int = ctypes.c_int
 _c_dbl = ctypes.c_double
@@ -85,6 +86,8 @@ def _L():
         lib.or_score_map_quantized.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _c_int,
                                                _c_dbl, _c_int, _c_int, _c_int, _f64p]
         lib.or_response_maps.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_int, _c_int, _f64p]
+        lib.or_angle_codes.argtypes = [_i32p, _i32p, _c_int, _c_int, _u16p]
+        lib.or_angle_field.argtypes = [_u16p, _c_int, _f64p]
         _lib = lib
     return _lib
 
@@ -463,4 +466,35 @@ def response_maps(field, nbins, nbhd=3, polarity=0):
     h, w = field.shape[:2]
     out = np.empty((nbins, h + 2, w + 2), dtype=np.float64)
     _L().or_response_maps(field, w, h, int(nbhd), int(polarity), int(nbins), out)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# angle-only 16-bit storage of the search field
+# ---------------------------------------------------------------------------
+
+def angle_codes(gx, gy, low):
+    """uint16 codes: 0x8000 | round(atan2(gy, gx) 32768 / 2 pi) mod 32768 on
+    search edges (gx^2 + gy^2 >= 16 low^2), 0 elsewhere."""
+    gx, gy = _i32(gx), _i32(gy)
+    out = np.empty(gx.shape, dtype=np.uint16)
+    _L().or_angle_codes(gx.ravel(), gy.ravel(), gx.size, int(low), out.reshape(-1))
+    return out
+
+
+def angle_field(codes):
+    """The FP64 unit field (H x W x 2) the codes stand for."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint16)
+    out = np.empty(codes.shape + (2,), dtype=np.float64)
+    _L().or_angle_field(codes.reshape(-1), codes.size, out.reshape(-1))
+    return out
+
+
+def search_angle_fields(img, levels, low):
+    """Per-level angle codes of the search image and the fields they decode to."""
+    out = []
+    for lvl_img in pyramid(img, levels):
+        gx, gy = sobel(lvl_img)
+        c = angle_codes(gx, gy, low)
+        out.append((c, angle_field(c)))
     return out

@@ -801,3 +801,43 @@ void or_response_maps(const double *field, int w, int h, int nbhd, int polarity,
                     or_vote(field, w, h, x, y, ux, uy, nbhd, polarity);
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Angle-only storage of the search field (a storage form; the paper keeps
+ * x- and y-gradients, Sec. II).  An edge pixel of the search threshold
+ * becomes the 16-bit code 0x8000 | a with
+ *     a = round(atan2(gy, gx) * 32768 / (2 pi)) mod 32768,
+ * its direction quantised to 2^15 steps of 2 pi / 32768 (round half up);
+ * any other pixel becomes 0.  The stored direction is then off by at most
+ * half a step, pi / 32768, and an Eq. (1) term by at most 2 sin(pi / 65536).
+ * ---------------------------------------------------------------------- */
+void or_angle_codes(const int32_t *gx, const int32_t *gy, int npx, int low, uint16_t *codes)
+{
+    for (int i = 0; i < npx; ++i) {
+        if (!or_is_edge(gx[i], gy[i], low)) {
+            codes[i] = 0;
+            continue;
+        }
+        double t = atan2((double)gy[i], (double)gx[i]) * 32768.0 / (2.0 * OR_PI);
+        long a = (long)floor(t + 0.5) % 32768;
+        if (a < 0)
+            a += 32768;
+        codes[i] = (uint16_t)(0x8000 | a);
+    }
+}
+
+/* The unit field the codes stand for: (cos phi, sin phi), phi = a 2 pi /
+ * 32768, where the edge bit is set; (0, 0) elsewhere.                      */
+void or_angle_field(const uint16_t *codes, int npx, double *field)
+{
+    for (int i = 0; i < npx; ++i) {
+        if (codes[i] & 0x8000) {
+            double phi = (double)(codes[i] & 0x7fff) * (2.0 * OR_PI) / 32768.0;
+            field[2 * i] = cos(phi);
+            field[2 * i + 1] = sin(phi);
+        } else {
+            field[2 * i] = 0.0;
+            field[2 * i + 1] = 0.0;
+        }
+    }
+}
