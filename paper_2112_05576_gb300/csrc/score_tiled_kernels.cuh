@@ -500,8 +500,6 @@ template <typename E, int NB, bool POL, int WARPS, int TC>
 __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TiledArgs a) {
     using Raw = typename Pairs<E>::Raw;
-    constexpr int LX = Pairs<E>::LX, LY = 32 / LX;
-    constexpr int WTX = LX * TC, WTY = LY * TR;   // warp tile (poses)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: round the base up (the
     // launch adds 128 bytes of slack)
@@ -610,7 +608,7 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
     __shared__ int s_org[2];
     __shared__ int s_job[4];   // kind (0 end, 1 unit, 2 task), unit, first entry, entries
     const uint32_t bar = smem_addr(&mbar);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const int pp = a.bxw / 2;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -962,10 +960,10 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
                              m2 = __funnelshift_r(w2, w3, sh);
                     if (BW <= 64) {
-                        m1 &= BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u);
+                        m1 &= BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u);
                         m2 = 0u;
                     } else {
-                        m2 &= (1u << (BW - 64)) - 1u;
+                        m2 &= (1u << ((BW - 64) & 31)) - 1u;
                     }
                     const bool in = i0 + j < a.n;
                     mm0[j] = in ? m0 : 0u;
@@ -1052,8 +1050,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 }
             }
             const uint32_t o0 = gt0 | eq0;
-            const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << (BW - 32)) - 1u));
-            const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << (BW - 64)) - 1u)) : 0u;
+            const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u));
+            const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << ((BW - 64) & 31)) - 1u)) : 0u;
             // this thread's 8 x TC block (rows ly*TR .., columns lx*TC ..) in
             // RD-row slices: a slice with no surviving pose is written -inf,
             // the others go to the queue
