@@ -86,8 +86,6 @@ namespace {
             return SAM_ERR_CUDA;     \
     } while (0)
 
-char *at(sam_multi *mp, size_t off) { return (char *)mp->base + off; }
-
 // Scoring cost and window of every pair for the plan's tiling; false if a
 // pair's window does not fit the tiled kernel.
 bool plan_tiling(sam_multi *mp) {
