@@ -110,13 +110,18 @@ typedef struct {
 
 const char *sam_status_str(sam_status s);
 
-/* Library version and the CUDA architecture it was compiled for (e.g. 1030). */
+/* Library version and the CUDA architecture it was compiled for (e.g. 1030).
+ * Library metadata; the paper has no counterpart.  Never fail. */
 int sam_version(void);
 int sam_compiled_arch(void);
 
-/* Fill `p` with defaults: low 30, high 60, levels 3, angle_step 1.0, polarity 0. */
+/* Fill `p` (host, caller-owned; NULL is ignored) with defaults: low 30,
+ * high 60, levels 3, angle_step 1.0, polarity 0.  The paper prints no
+ * thresholds or steps for these (Sec. III names its search steps only for
+ * its own samples); the values are this library's. */
 void sam_default_model_params(sam_model_params *p);
-/* Fill `p` with defaults: steps 1, neighbourhood 3, min_score 0.7,
+/* Fill `p` (host, caller-owned; NULL is ignored) with defaults: steps 1,
+ * neighbourhood 3 (the neighbouring-search size of Sec. II), min_score 0.7,
  * max_detections 16, top_k 64, FP32, early termination on. */
 void sam_default_detect_params(sam_detect_params *p);
 
@@ -134,7 +139,10 @@ sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const
                             sam_model **out);
 void sam_free_model(sam_model *m);
 
-/* Model inspection (host only, no device work). */
+/* Model inspection (host only, no device work; the paper has no
+ * counterpart).  The int getters return 0 for a NULL model or a level out of
+ * range; sam_model_template_size returns 1 and writes the level's template
+ * size (w, h; either pointer may be NULL) or returns 0. */
 int sam_model_levels(const sam_model *m);
 int sam_model_num_points(const sam_model *m, int level);
 int sam_model_num_angles(const sam_model *m, int level);
@@ -165,10 +173,12 @@ sam_status sam_model_child_shift(const sam_model *m, int level, int k_parent, in
 sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride, int img_on_device,
                       const sam_detect_params *params, void *stream, sam_pose *out, int capacity, int *n_out);
 
-/* Detection of `count` images of equal size stored back to back on the
- * device (image i at img + i * image_bytes), all steps batched into one
- * launch per stage.  Poses of image i go to out[i * capacity ...], their
- * count to n_out[i] (host arrays).  Synchronises `stream`. */
+/* Detection (Sec. II, as sam_detect) of `count` images of equal size
+ * stored back to back on the device (image i at img + i * image_bytes), all
+ * steps batched into one launch per stage.  Poses of image i go to
+ * out[i * capacity ...], their count to n_out[i] (host arrays, count *
+ * capacity and count entries).  Synchronises `stream`.  Errors as
+ * sam_detect. */
 sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h,
                             int stride, const sam_detect_params *params, void *stream, sam_pose *out,
                             int capacity, int *n_out);
@@ -327,7 +337,9 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                         const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
                         int *n_out);
 /* The tiling the model's next calls with field `precision` over `count`
- * images will use (tuned, else the default). */
+ * images will use (tuned, else the default; the paper has no counterpart).
+ * All outputs host ints.  Errors: SAM_ERR_ARG (NULL model or output,
+ * precision out of range, count < 1). */
 sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_t *sx, int32_t *sy, int32_t *tg,
                             int32_t *warps, int32_t *cols);
 /* Self-test of failure detection (the paper has no counterpart): one warp
@@ -347,14 +359,18 @@ sam_status sam_selftest_wait_timeout(int limit_us, double *waited_ms);
  * limited to limit_us; returns as sam_selftest_wait_timeout. */
 sam_status sam_selftest_task_wait_timeout(int limit_us, double *waited_ms);
 
-/* Device-side error flag of the tiled kernel's bounded waits: returns 1 and
- * clears it if any wait gave up since the last call (synchronises the
- * device). */
+/* Device-side error flag of the tiled kernel's bounded waits (failure
+ * detection; the paper has no counterpart): returns 1 and clears it if any
+ * wait gave up since the last call, else 0 (synchronises the device). */
 int sam_take_device_error(void);
 
-/* Candidate extraction from a score map [nth][gh][gw]: poses with score >=
- * min_score that beat all 26 neighbours in (theta circular, y, x) under the
- * order (higher score, then smaller (k, y, x)), the best K of them.
+/* Candidate extraction from a score map [nth][gh][gw] (Sec. II returns the
+ * best pose; for several instances this library reads it as the local
+ * maxima): poses with score >= min_score that beat all 26 neighbours in
+ * (theta circular, y, x) under the order (higher score, then smaller
+ * (k, y, x)), the best K of them (1 <= K <= 1024).  Stream-ordered, no
+ * synchronisation.  Errors: SAM_ERR_ARG (NULL pointers, sizes, K),
+ * SAM_ERR_CUDA.
  *   out_kyx  device int32 array of 3*K: (k, y, x) per candidate, best first.
  *   out_s    device float array of K.
  *   count    device int, receives min(K, number of local maxima).
@@ -488,7 +504,7 @@ sam_status sam_refine_poses(sam_model *m, int level, const sam_field_ref *fields
                             void *stream);
 
 /* ---------------------------------------------------------------------------
- * Stage timing (tracing).  When enabled, sam_detect / sam_detect_batch record
+ * Stage timing (tracing; the paper has no counterpart).  When enabled, sam_detect / sam_detect_batch record
  * CUDA events on the caller's stream before and after the launches of each
  * stage; sam_profile_read waits for the recorded events and adds their
  * elapsed device times to per-stage totals (so an enabled profiler adds no
@@ -513,7 +529,8 @@ void sam_profile_enable(int on);
 void sam_set_graph_mode(int on);
 int sam_profile_read(float *ms, int *calls, int n);
 
-/* Pose-points the tiled and chunked exhaustive scorers have evaluated on the
+/* Pose-points (the unit of the paper's Sec. II nested loops: one pose, one
+ * model point) the tiled and chunked exhaustive scorers have evaluated on the
  * current device since the last reset (each warp's poses inside the map
  * times the model points it processed before finishing or being pruned by
  * early termination; without early termination this is the nominal count,
@@ -523,7 +540,8 @@ int sam_profile_read(float *ms, int *calls, int n);
 long long sam_executed_pose_points(int reset);
 
 /* Number of CUDA kernels this library has launched in this process
- * (all entry points, all devices).  Monotonic; for accounting only. */
+ * (all entry points, all devices; the paper has no counterpart).
+ * Monotonic; for accounting only. */
 long long sam_kernel_launches(void);
 
 #ifdef __cplusplus
