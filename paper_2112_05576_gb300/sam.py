@@ -171,7 +171,9 @@ def default_detect_params(**kw) -> DetectParams:
 
 
 class Model:
-    """A template model (edge points per level and Eq. (2) tables)."""
+    """A template model (sam_create_model): the template's edge points at every
+    pyramid level (Sec. II edge extraction, hysteresis between `low` and
+    `high`) and per level and angle index the Eq. (2) tables."""
 
     def __init__(self, template: np.ndarray, low=30, high=60, levels=3, angle_step_deg=1.0, polarity=0):
         t = np.ascontiguousarray(template, dtype=np.uint8)
@@ -200,17 +202,21 @@ class Model:
             pass
 
     def num_points(self, level):
+        """n, the number of model points at `level` (Eq. (1)'s normaliser)."""
         return lib().sam_model_num_points(self._h, level)
 
     def num_angles(self, level):
+        """Angle indices searched at `level` (360 / (angle_step * 2^level))."""
         return lib().sam_model_num_angles(self._h, level)
 
     def template_size(self, level):
+        """(w, h) of the template at `level`."""
         w, h = ctypes.c_int32(), ctypes.c_int32()
         lib().sam_model_template_size(self._h, level, ctypes.byref(w), ctypes.byref(h))
         return w.value, h.value
 
     def rotated_points(self, level, k):
+        """Eq. (2) table of (level, k): int32 offsets ox, oy and FP32 unit directions px, py."""
         n = self.num_points(level)
         ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
         px, py = np.empty(n, np.float32), np.empty(n, np.float32)
@@ -220,12 +226,14 @@ class Model:
         return ox, oy, px, py
 
     def points(self, level):
+        """The level's points: template coordinates tx, ty and integer Sobel gx, gy."""
         n = self.num_points(level)
         a = [np.empty(n, np.int32) for _ in range(4)]
         _check(lib().sam_model_points(self._h, level, *[x.ctypes.data_as(_i32p) for x in a]), "sam_model_points")
         return tuple(a)
 
     def child_shift(self, level, k_parent):
+        """Coarse-to-fine shift: a level+1 pose (x, y, k_parent) maps to 2 (x, y) + shift."""
         sx, sy = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().sam_model_child_shift(self._h, level, k_parent, ctypes.byref(sx), ctypes.byref(sy)),
                "sam_model_child_shift")
@@ -238,7 +246,9 @@ def _poses(arr, n) -> List[dict]:
 
 
 def detect(model: Model, image, params: Optional[DetectParams] = None, stream=None, capacity=None):
-    """Detect the model in one image (numpy host array or torch CUDA uint8 tensor)."""
+    """sam_detect (Sec. II): detect the model in one image (numpy host array or
+    torch CUDA uint8 tensor); a list of pose dicts (x, y, theta_deg, score, k) at
+    level 0, best first."""
     params = params or default_detect_params()
     cap = capacity or params.max_detections
     out = (Pose * cap)()
@@ -270,7 +280,8 @@ def _has_cuda():
 
 
 def detect_batch(model: Model, images, params: Optional[DetectParams] = None, stream=None, capacity=None):
-    """Detect in a (N, H, W) torch.uint8 CUDA tensor; returns one pose list per image."""
+    """sam_detect_batch (Sec. II, per image): detect in a (N, H, W) torch.uint8
+    CUDA tensor; returns one pose list per image."""
     params = params or default_detect_params()
     cap = capacity or params.max_detections
     N, H, W = images.shape
@@ -286,6 +297,8 @@ def detect_batch(model: Model, images, params: Optional[DetectParams] = None, st
 # ---- individual steps on torch CUDA tensors ----
 
 def pyramid_down(src, dst, stream=None):
+    """sam_pyramid_down (Sec. II image pyramid): dst = the 2x2 rounded mean of src
+    (device uint8 tensors, 2-D, rows contiguous)."""
     h, w = src.shape
     _check(lib().sam_pyramid_down(_ptr(src), w, h, src.stride(0), _ptr(dst), dst.stride(0), _stream(stream)),
            "sam_pyramid_down")
@@ -297,6 +310,9 @@ def field_pitch(w, layout):
 
 
 def gradient(img, low, precision, field, gx=None, gy=None, stream=None, layout=None):
+    """sam_gradient (Sec. II edge extraction): Sobel gradients of a device uint8
+    image, edges by the `low` threshold, unit field written to `field` in
+    `precision` and `layout`; optional int16 gx, gy outputs."""
     h, w = img.shape
     layout = LAYOUT_PIXEL if layout is None else layout
     _check(lib().sam_gradient(_ptr(img), w, h, img.stride(0), int(low), int(precision), int(layout), _ptr(field),
@@ -305,6 +321,9 @@ def gradient(img, low, precision, field, gx=None, gy=None, stream=None, layout=N
 
 def score_map(model: Model, level, field, w, h, precision, out, step_x=1, step_y=1, nbhd=3, min_score=0.0,
               early=0, stream=None, layout=None):
+    """sam_score_map: the exhaustive Eq. (1) score of every pose of the step grid
+    at one level (points projected by Eq. (2)), written to out[k, y, x];
+    with `early`, poses proved below min_score are -inf."""
     layout = LAYOUT_PIXEL if layout is None else layout
     _check(lib().sam_score_map(model.handle, int(level), _ptr(field), int(w), int(h), int(precision), int(layout),
                                int(step_x), int(step_y), int(nbhd), float(min_score), int(early), _ptr(out),
@@ -312,6 +331,7 @@ def score_map(model: Model, level, field, w, h, precision, out, step_x=1, step_y
 
 
 def score_window_scratch_bytes(max_rescored):
+    """Device bytes of score_window's FP32 rescoring list for up to max_rescored poses."""
     return int(lib().sam_score_window_scratch_bytes(int(max_rescored)))
 
 
@@ -334,12 +354,14 @@ def set_score_kernel(kernel=0, sx=2, sy=1, tg=9, warps=8, cols=6):
 
 
 def get_score_kernel():
+    """The process-wide scorer selection (sam_get_score_kernel) as a dict."""
     v = [ctypes.c_int32() for _ in range(6)]
     lib().sam_get_score_kernel(*[ctypes.byref(x) for x in v])
     return dict(zip(("kernel", "sx", "sy", "tg", "warps", "cols"), (x.value for x in v)))
 
 
 def take_device_error():
+    """1 if a bounded wait of the scorers gave up since the last call (then cleared), else 0."""
     return int(lib().sam_take_device_error())
 
 
@@ -360,10 +382,14 @@ def selftest_task_wait_timeout(limit_us=2000):
 
 
 def candidates_scratch_bytes(nth, gh, gw):
+    """Device scratch bytes sam_candidates needs for an (nth, gh, gw) map."""
     return int(lib().sam_candidates_scratch_bytes(nth, gh, gw))
 
 
 def candidates(smap, min_score, K, out_kyx, out_s, count, scratch, stream=None):
+    """sam_candidates: strict 3x3x3 local maxima (angle circular) of a score map
+    at or above min_score, the best K (Sec. II returns the best pose; several
+    instances read as local maxima)."""
     nth, gh, gw = smap.shape
     _check(lib().sam_candidates(_ptr(smap), nth, gh, gw, float(min_score), int(K), _ptr(out_kyx), _ptr(out_s),
                                 _ptr(count), _ptr(scratch), _stream(stream)), "sam_candidates")
@@ -375,6 +401,7 @@ def set_graph_mode(on=True):
 
 
 def profile_enable(on=True):
+    """Turn per-stage CUDA-event timing of sam_detect / sam_detect_batch on or off."""
     lib().sam_profile_enable(1 if on else 0)
 
 
@@ -591,6 +618,7 @@ def refine_poses(model: Model, fields, poses, pose_field=None, iterations=20, le
 
 
 def response_maps_bytes(w, h, nbins):
+    """Bytes of the response maps score_map_quantized needs for a w x h field."""
     return int(lib().sam_response_maps_bytes(int(w), int(h), int(nbins)))
 
 
