@@ -173,7 +173,9 @@ __device__ __forceinline__ bool pose_field_ok(const BilArgs &a, const int32_t *p
     return f >= 0 && f < a.n_fields;
 }
 
-// Forward (K = 1, 4 or 13 accumulators).
+// Forward of the continuous-pose score (Eq. (1) without the neighbourhood
+// maximum, Eq. (2) without rounding, bilinear samples); K = 1, 4 or 13
+// accumulators.
 template <int K>
 __global__ void __launch_bounds__(kBilThreads) bilinear_kernel(const __grid_constant__ BilArgs a,
                                                                const int32_t *__restrict__ pose_field,
@@ -262,6 +264,8 @@ __device__ bool solve3(const double *A, const double *r, double *d) {
     return true;
 }
 
+// Gauss-Newton refinement of continuous poses (one CTA per pose, damped
+// normal equations of the continuous-pose score, FP64 3x3 solve).
 __global__ void __launch_bounds__(kBilThreads) refine_gn_kernel(const __grid_constant__ BilArgs a,
                                                                 const int32_t *__restrict__ pose_field,
                                                                 float *__restrict__ poses, int B, int iterations,

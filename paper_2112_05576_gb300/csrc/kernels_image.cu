@@ -66,6 +66,8 @@ __device__ __forceinline__ void pyramid_16(const uint8_t *__restrict__ src, int 
     }
 }
 
+// Pyramid step (Sec. II image pyramid) of `count` images of equal size,
+// image blockIdx.z, output row blockIdx.y, 16 output pixels per thread.
 __global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int h, int ss, size_t src_img,
                                     uint8_t *__restrict__ dst, int ds, size_t dst_img, int vec) {
     const int img = blockIdx.z;

@@ -26,6 +26,8 @@
 namespace sam {
 namespace {
 
+// One thread per pose (x, y) of angle blockIdx.y (Eq. (1) over the Eq. (2)
+// projections, neighbouring search NB), image blockIdx.z.
 template <typename E, int LAYOUT, int NB>
 __global__ void __launch_bounds__(256)
     score_map_generic(const E *__restrict__ field, size_t field_img_px, int pitch, int w, int h,

@@ -79,6 +79,9 @@ __device__ __forceinline__ void push_candidate(const float *map, size_t idx, Can
     }
 }
 
+// Candidates (the best pose of Sec. II, generalised to every strict 3x3x3
+// local maximum at or above min_score) of `count` equal maps, image
+// blockIdx.y; appended to the image's list by atomic counter.
 __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
                                  float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt) {
     const int img = blockIdx.y;
@@ -90,6 +93,7 @@ __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, 
             push_candidate(map, idx, cand + (size_t)img * cap, cap, cnt + img);
 }
 
+// The same over a job list of maps of different sizes (job blockIdx.y).
 __global__ void local_max_jobs_kernel(const CandJob *__restrict__ jobs, float min_score) {
     const CandJob j = jobs[blockIdx.y];
     const size_t total = (size_t)j.nth * j.gh * j.gw;
@@ -171,6 +175,8 @@ __device__ void topk_body(const Cand *__restrict__ cand, int total, int K, int g
         *out_count = have;
 }
 
+// Best K of each image's candidate list under the total order (one CTA per
+// image).
 __global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ cand, size_t cap,
                                                     const int *__restrict__ cnt, int K, int gh, int gw,
                                                     int32_t *__restrict__ out_kyx, float *__restrict__ out_s,
@@ -180,6 +186,7 @@ __global__ void __launch_bounds__(1024) topk_kernel(const Cand *__restrict__ can
               out_s + (size_t)img * K, out_count + img);
 }
 
+// The same per job.
 __global__ void __launch_bounds__(1024) topk_jobs_kernel(const CandJob *__restrict__ jobs, int K) {
     const CandJob j = jobs[blockIdx.x];
     topk_body(j.cand, (int)min((size_t)*j.cnt, j.cap), K, j.gh, j.gw, j.out_kyx, j.out_s, j.out_count);
@@ -350,6 +357,10 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                             state[3] ? sbest : -INFINITY);
 }
 
+// Coarse-to-fine refinement (Sec. II: the search starts at the top pyramid
+// level; the size-3 neighbouring search in x, y and theta at each lower
+// level): a cluster of kRefineCluster CTAs per candidate of image
+// blockIdx.y, all levels down to 0 in one launch.
 template <int NB>
 __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
     refine_kernel(RefineLevels lv, RefineArgs a) {
@@ -373,6 +384,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREAD
     refine_body<NB>(j, lv.L, blockIdx.x / kRefineCluster);
 }
 
+// The same per job (pair blockIdx.y).
 template <int NB>
 __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
     refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
@@ -448,12 +460,16 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
     }
 }
 
+// Final non-maximum suppression of each image's refined poses (one CTA per
+// image): greedy in the total order, dropping poses closer than half the
+// smaller template side to a kept one.
 __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
     const int img = blockIdx.x;
     nms_body(a.refined + (size_t)img * a.K, min(a.cand_count[img], a.K), a.w0, a.h0, a.min_side, a.max_out,
              a.angle_step, a.out + (size_t)img * a.max_out, a.n_out + img);
 }
 
+// The same per job.
 __global__ void __launch_bounds__(256) nms_jobs_kernel(const NmsJob *__restrict__ jobs, int K) {
     const NmsJob j = jobs[blockIdx.x];
     nms_body(j.refined, min(*j.count, K), j.w0, j.h0, j.min_side, j.max_out, j.angle_step, j.out, j.n_out);

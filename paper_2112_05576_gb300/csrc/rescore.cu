@@ -25,6 +25,7 @@
 namespace sam {
 namespace {
 
+// The -inf rule and the rescoring list over `count` maps (grid-stride).
 __global__ void rescore_select_kernel(float *__restrict__ map, size_t map_img, size_t per_img, float thr,
                                       unsigned *__restrict__ list, unsigned *__restrict__ count, unsigned cap) {
     const int img = blockIdx.y;
@@ -45,6 +46,7 @@ __global__ void rescore_select_kernel(float *__restrict__ map, size_t map_img, s
     }
 }
 
+// Eq. (1) in FP32 from the FP32 field for every listed pose, one warp each.
 template <int NB>
 __global__ void __launch_bounds__(256) rescore_kernel(const float2 *__restrict__ field, size_t field_img_px, int w,
                                                       int h, int gw, int gh, int step_x, int step_y, int x0, int y0,

@@ -496,6 +496,9 @@ template <typename E, int TC>
 __device__ __forceinline__ void slice_store(int item, int src, int part, int stx0, int sty0, int k_begin,
                                             const TileWork &a, const float2 (&acc)[RD][TC / 2]);
 
+// Exhaustive score (Eq. (1) over the Eq. (2) projections, neighbouring
+// search NB) of one work unit per CTA: its TMA-staged window, then
+// score_items over the unit's angles and warp tiles.
 template <typename E, int NB, bool POL, int WARPS, int TC>
 __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const TiledArgs a) {
