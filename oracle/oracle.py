@@ -109,6 +109,8 @@ def _f64(a):
 # ---------------------------------------------------------------------------
 
 def pyramid_down(img):
+    """One pyramid step (Sec. II image pyramid, of intensities): 2x2 mean rounded half up, odd row/column
+    dropped."""
     img = _u8(img)
     h, w = img.shape
     out = np.empty((h // 2, w // 2), dtype=np.uint8)
@@ -117,6 +119,7 @@ def pyramid_down(img):
 
 
 def pyramid(img, levels):
+    """The intensity pyramid (Sec. II), level 0 first."""
     out = [_u8(img)]
     for _ in range(1, levels):
         out.append(pyramid_down(out[-1]))
@@ -124,6 +127,7 @@ def pyramid(img, levels):
 
 
 def sobel(img):
+    """Integer 3x3 Sobel gx, gy (Sec. II x- and y-gradients; x right, y down), zero on the 1-pixel border."""
     img = _u8(img)
     h, w = img.shape
     gx = np.empty((h, w), dtype=np.int32)
@@ -133,6 +137,7 @@ def sobel(img):
 
 
 def search_mask(gx, gy, low):
+    """Search-image edges (Sec. II edge thresholds, magnitude |g|/4): gx^2 + gy^2 >= 16 low^2."""
     gx, gy = _i32(gx), _i32(gy)
     m = np.empty(gx.shape, dtype=np.uint8)
     _L().or_search_mask(gx, gy, gx.size, int(low), m)
@@ -140,6 +145,7 @@ def search_mask(gx, gy, low):
 
 
 def hysteresis(gx, gy, low, high):
+    """Model edges (Sec. II edge thresholds, magnitude |g|/4): >= high seeds grown 8-connected through >= low."""
     gx, gy = _i32(gx), _i32(gy)
     h, w = gx.shape
     m = np.empty(gx.shape, dtype=np.uint8)
@@ -148,6 +154,7 @@ def hysteresis(gx, gy, low, high):
 
 
 def unit_field(gx, gy, mask):
+    """The unit field g/|g| on edges, (0, 0) elsewhere (the normalised gradients of Eq. (1))."""
     gx, gy, mask = _i32(gx), _i32(gy), _u8(mask)
     f = np.empty(gx.shape + (2,), dtype=np.float64)
     _L().or_unit_field(gx, gy, mask, gx.size, f)
@@ -183,6 +190,7 @@ class OracleModel:
 
 
 def create_model(tmpl, low, high, levels, angle_step_deg, polarity=0):
+    """The model of Sec. II: template pyramid and per-level edge points (t, g)."""
     n0 = int(round(360.0 / angle_step_deg))
     if abs(n0 * angle_step_deg - 360.0) > 1e-9 or n0 % (1 << (levels - 1)) != 0:
         raise ValueError("360 / angle_step must be an integer divisible by 2^(levels-1)")
@@ -210,6 +218,8 @@ def search_fields(img, levels, low):
 # ---------------------------------------------------------------------------
 
 def rotate_points(pts, k, dtheta_deg):
+    """Eq. (2) for angle index k: integer offsets floor(R(theta) t + 1/2) in FP64 and the model gradients
+    turned by the same R(theta), as unit directions."""
     tx, ty, gx, gy = pts
     n = len(tx)
     ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
@@ -219,6 +229,7 @@ def rotate_points(pts, k, dtheta_deg):
 
 
 def score_pose(field, rot, ux, uy, nbhd=3, polarity=0):
+    """Eq. (1) at one pose with the neighbouring search of size nbhd (Fig. 3; readings 8-9)."""
     field = _f64(field)
     h, w = field.shape[:2]
     ox, oy, px, py = rot
@@ -269,6 +280,8 @@ def _ref_shift_d(model, level):
 
 
 def child_shift(model, level, k_parent):
+    """Coarse-to-fine child shift of a level+1 parent with angle index k_parent: its level-`level` centre is
+    2 (x, y) + shift (the reference-point offset between levels, turned by the parent's angle)."""
     dx, dy = _ref_shift_d(model, level)
     sx, sy = ctypes.c_int32(), ctypes.c_int32()
     _L().or_child_shift(int(k_parent), float(model.dtheta(level + 1)), dx, dy, ctypes.byref(sx), ctypes.byref(sy))
@@ -291,6 +304,8 @@ def refine_level(model, level, field, xs, ys, ks, nbhd, polarity, min_score):
 
 
 def nms(xs, ys, ks, ss, w, h, min_side, max_out):
+    """Final non-maximum suppression: greedy by score (ties: smaller (k, y, x) key), dropping poses closer
+    than half the smaller template side to a kept one."""
     n = len(xs)
     keep = np.empty(max(n, 1), np.int32)
     nk = _L().or_nms(n, _i32(xs), _i32(ys), _i32(ks), _f64(ss), int(w), int(h), int(min_side), int(max_out), keep)
@@ -444,6 +459,8 @@ def subpixel_poses(field, pts, kyx, ntheta, dtheta_deg, nbhd=3, polarity=0, max_
 # ---------------------------------------------------------------------------
 
 def quant_bin(px, py, nbins, polarity=0):
+    """Orientation bin of a unit direction for the quantised-direction form: the nearest of nbins centres
+    b 2 pi / nbins (pi / nbins with polarity 1), by FP64 atan2."""
     return int(_L().or_quant_bin(float(px), float(py), int(nbins), int(polarity)))
 
 
