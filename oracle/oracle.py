@@ -229,7 +229,8 @@ def rotate_points(pts, k, dtheta_deg):
 
 
 def score_pose(field, rot, ux, uy, nbhd=3, polarity=0):
-    """Eq. (1) at one pose with the neighbouring search of size nbhd (Fig. 3; readings 8-9)."""
+    """Eq. (1) at one pose with the neighbouring search of size nbhd (Fig. 3): per point the best vote over
+    its window, 0 outside the image and on non-edge pixels, |vote| with polarity 1."""
     field = _f64(field)
     h, w = field.shape[:2]
     ox, oy, px, py = rot
