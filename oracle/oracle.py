@@ -230,7 +230,7 @@ def rotate_points(pts, k, dtheta_deg):
 
 def score_pose(field, rot, ux, uy, nbhd=3, polarity=0):
     """Eq. (1) at one pose with the neighbouring search of size nbhd (Fig. 3): per point the best vote over
-    its window, 0 outside the image and on non-edge pixels, |vote| with polarity 1."""
+    its window of p . w (|p . w| with polarity 1), 0 outside the image and on non-edge pixels."""
     field = _f64(field)
     h, w = field.shape[:2]
     ox, oy, px, py = rot
