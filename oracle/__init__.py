@@ -43,4 +43,6 @@ from .oracle import (  # noqa: F401
     angle_codes,
     angle_field,
     search_angle_fields,
+    project_affine,
+    similarity,
 )

@@ -88,6 +88,9 @@ def _L():
         lib.or_response_maps.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_int, _c_int, _f64p]
         lib.or_angle_codes.argtypes = [_i32p, _i32p, _c_int, _c_int, _u16p]
         lib.or_angle_field.argtypes = [_u16p, _c_int, _f64p]
+        lib.or_project_affine.argtypes = [_i32p, _i32p, _i32p, _i32p, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl,
+                                          _i32p, _i32p, _f64p, _f64p]
+        lib.or_project_affine.restype = _c_int
         _lib = lib
     return _lib
 
@@ -516,3 +519,29 @@ def search_angle_fields(img, levels, low):
         c = angle_codes(gx, gy, low)
         out.append((c, angle_field(c)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# affine (scaled) poses: a generalisation of Eq. (2)
+# ---------------------------------------------------------------------------
+
+def project_affine(pts, A):
+    """Eq. (2) with the rotation replaced by a 2x2 matrix A (A = s R(theta) for a
+    scaled pose): offsets floor(A t + 1/2), directions A^-T g normalised (the
+    gradient of the warped image).  Returns (ox, oy, px, py) like rotate_points."""
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    A = np.asarray(A, dtype=np.float64)
+    n = len(tx)
+    ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
+    px, py = np.empty(n, np.float64), np.empty(n, np.float64)
+    if not _L().or_project_affine(tx, ty, gx, gy, n, float(A[0, 0]), float(A[0, 1]), float(A[1, 0]),
+                                  float(A[1, 1]), ox, oy, px, py):
+        raise ValueError("singular projection matrix")
+    return ox, oy, px, py
+
+
+def similarity(scale, theta_deg):
+    """A = scale R(theta) (x right, y down, theta in degrees as in Eq. (2))."""
+    th = math.radians(theta_deg)
+    c, s = math.cos(th), math.sin(th)
+    return np.array([[scale * c, -scale * s], [scale * s, scale * c]])

@@ -841,3 +841,33 @@ void or_angle_field(const uint16_t *codes, int npx, double *field)
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Affine projection, a generalisation of Eq. (2) (the paper notes that other
+ * kinds of projection could be implemented; a scaled pose is A = s R(theta)):
+ * p = A t + u, A = [[a11, a12], [a21, a22]], offsets rounded to the nearest
+ * pixel as in Eq. (2), floor(v + 1/2).  The model gradient is carried by the
+ * inverse transpose: the gradient of the warped image I(A^-1 x) at A t is
+ * A^-T times the gradient of I at t, so p_hat = A^-T g / |A^-T g|, with
+ * A^-T = (1 / det A) [[a22, -a21], [-a12, a11]].  Returns 0 (and writes
+ * nothing) when det A = 0, else 1.
+ * ---------------------------------------------------------------------- */
+int or_project_affine(const int32_t *tx, const int32_t *ty, const int32_t *gx, const int32_t *gy, int n,
+                      double a11, double a12, double a21, double a22, int32_t *ox, int32_t *oy, double *px,
+                      double *py)
+{
+    double det = a11 * a22 - a12 * a21;
+    if (det == 0.0)
+        return 0;
+    for (int i = 0; i < n; ++i) {
+        double x = (double)tx[i], y = (double)ty[i];
+        ox[i] = (int32_t)floor(a11 * x + a12 * y + 0.5);
+        oy[i] = (int32_t)floor(a21 * x + a22 * y + 0.5);
+        double vx = (a22 * gx[i] - a21 * gy[i]) / det;
+        double vy = (a11 * gy[i] - a12 * gx[i]) / det;
+        double m = sqrt(vx * vx + vy * vy);
+        px[i] = vx / m;
+        py[i] = vy / m;
+    }
+    return 1;
+}
