@@ -6,15 +6,13 @@ transpose A^-T g.  What fixes it, independently of the oracle's own code:
   * A = R(theta_k) gives exactly the integer offsets of Eq. (2) (rotate_points)
     and its directions up to FP64 rounding; A = 2 I doubles the offsets;
   * the direction rule is the gradient of the warped image: linear ramps
-    warped by a scale or a shear, differentiated by the oracle's own Sobel,
+    warped by a squeeze, a shear or a scale, differentiated by the oracle's own Sobel,
     point exactly where the projected model directions point (A instead of
     A^-T, or A^-1 untransposed, fails it);
   * a template enlarged 2x by pixel replication scores exactly 1 at scale 2
     (and turned a quarter turn, at scale 2 and 90 degrees), well above the
     other scales tried.
 """
-
-import math
 
 import numpy as np
 import pytest
