@@ -194,13 +194,14 @@ BOUND_OPS_PER_PP = 4.0 / 32.0
 LOGIC_OPS_PER_CLK_SM = 64.0
 
 # DRAM bytes (read + write) of one score_fused_kernel launch of this
-# workload, from an ncu capture at the tiling below (summary and command in
-# profiles/score_map_config2_batch16.md); reported only when the bench runs
-# that tiling, and to be re-taken whenever the kernel changes.
+# workload, from an ncu capture at the tiling below; reported only when the
+# bench runs that tiling, and to be re-taken whenever the kernel changes.
 NCU_FUSED_TRAFFIC = {"tiling": (2, 1, 11, 4, 10), "bytes": 2988288 + 2543872}
 
 
-def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
+def dense_roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
+    """Shared-memory roofline of the dense tiled scorer (every pose scored,
+    8 x 6 block, 13.33 B per pose-point) and its 3 x 3 maximum on the ALU."""
     sec = ms_per_launch * 1e-3
     achieved = pp_per_launch * SMEM_B_PER_PP / sec / 1e12
     peak = SMEM_B_PER_CLK_SM * sm_count * sm_mhz_peak * 1e6 / 1e12
@@ -208,7 +209,7 @@ def roofline(pp_per_launch, ms_per_launch, sm_count, sm_mhz_peak, traffic=None):
     alu_peak = CMP_PER_CLK_SM * sm_count * sm_mhz_peak * 1e6 / 1e12
     return {"bound": "smem", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
-            "kernel": "score_tiled_kernel (exhaustive top level)",
+            "kernel": "score_tiled_kernel (dense: every pose of the top level scored)",
             "alu": {"achieved": round(alu_ach, 3), "peak": round(alu_peak, 3), "unit": "Tcmp/s",
                     "frac": round(alu_ach / alu_peak, 4)}}
 
@@ -470,6 +471,72 @@ def run_stress(args, sam, torch, dev, stream):
 
 
 # ---------------------------------------------------------------------------
+# HBM-bound kernels (a) gradient and (b) pyramid on images larger than L2
+# ---------------------------------------------------------------------------
+# Algorithmic bytes: the gradient kernel reads each 8-bit pixel once and
+# writes its unit-field pixel once (8 B FP32 pair, 4 B 16-bit pair; pairs
+# layout, row pitch rounded up to 4 pixels); the pyramid kernel reads the
+# 2 x 2 block of 8-bit pixels under each output pixel and writes it (4 + 1 B).
+# DRAM bytes per launch, from an ncu capture of `bench.py --only hbm`, keyed
+# by kernel, precision and image size; None until taken.
+NCU_HBM_TRAFFIC = {}
+
+
+def _hbm_images(torch, dev, n, W_, H_):
+    """n distinct W_ x H_ uint8 device images cut from shifted config-5 scenes."""
+    _, img5, _ = synth.config5_scene()
+    rng = np.random.default_rng(77)
+    reps_y, reps_x = -(-H_ // img5.shape[0]), -(-W_ // img5.shape[1])
+    big = np.tile(img5, (reps_y, reps_x))
+    out = []
+    for _ in range(n):
+        sh = np.roll(big, (int(rng.integers(0, big.shape[0])), int(rng.integers(0, big.shape[1]))), axis=(0, 1))
+        out.append(torch.from_numpy(np.ascontiguousarray(sh[:H_, :W_])).to(dev))
+    return out
+
+
+def run_hbm(args, sam, torch, dev, stream):
+    peaks, kind = _peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"peak_gbs": peak, "peak_source": f"{kind} hbm_gbs (STREAM-style copy)",
+           "what": "per-launch CUDA-event time of back-to-back launches over distinct buffers "
+                   "(working set several times the 129 MB L2)"}
+    for label, (W_, H_, n, reps) in (("config5_4096x3072", (4096, 3072, 8, 40)),
+                                     ("mosaic_8192x6144", (8192, 6144, 3, 12))):
+        srcs = _hbm_images(torch, dev, n, W_, H_)
+        wp = sam.field_pitch(W_, sam.LAYOUT_PAIRS)
+        res = {}
+        for prec, dt, bpx in ((sam.FP32, torch.float32, 8), (sam.BF16, torch.bfloat16, 4)):
+            dsts = [torch.empty((H_, wp, 2), dtype=dt, device=dev) for _ in range(n)]
+            call = (lambda i, dsts=dsts, prec=prec:
+                    sam.gradient(srcs[i % n], LOW, prec, dsts[i % n], layout=sam.LAYOUT_PAIRS))
+            for i in range(3):
+                call(i)
+            ms = _event_ms(torch, dev, stream, call, reps)
+            alg = W_ * H_ + H_ * wp * bpx
+            gbs = alg / (ms * 1e-3) / 1e9
+            key = ("gradient_kernel", "fp32" if prec == sam.FP32 else "bf16", W_, H_)
+            res["gradient_" + ("fp32" if prec == sam.FP32 else "bf16")] = {
+                "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                "traffic": NCU_HBM_TRAFFIC.get(key), "algorithmic_bytes": alg, "us_per_launch": round(ms * 1e3, 2)}
+            del dsts
+        dsts = [torch.empty((H_ // 2, W_ // 2), dtype=torch.uint8, device=dev) for _ in range(n)]
+        call = lambda i: sam.pyramid_down(srcs[i % n], dsts[i % n])  # noqa: E731
+        for i in range(3):
+            call(i)
+        ms = _event_ms(torch, dev, stream, call, reps * 4)
+        alg = 5 * (W_ // 2) * (H_ // 2)
+        gbs = alg / (ms * 1e-3) / 1e9
+        res["pyramid"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(gbs / peak, 4), "traffic": NCU_HBM_TRAFFIC.get(("pyramid_down_kernel", W_, H_)),
+                          "algorithmic_bytes": alg, "us_per_launch": round(ms * 1e3, 2)}
+        out[label] = res
+        del srcs, dsts
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -700,6 +767,9 @@ def run_gpu(args):
     # ---- the large exhaustive stress slice (chunked scorer) ----
     stress = run_stress(args, sam, torch, dev, stream) if (args.stress and rank == 0) else None
 
+    # ---- kernels (a) gradient and (b) pyramid against HBM ----
+    hbm = run_hbm(args, sam, torch, dev, stream) if (args.hbm and rank == 0) else None
+
     # ---- the differentiable form: continuous-pose score, adjoint, refinement ----
     differentiable = (run_differentiable(args, sam, torch, dev, stream, world == 1 and not args.no_cpu)
                       if (args.refine > 0 and rank == 0) else None)
@@ -755,7 +825,7 @@ def run_gpu(args):
                                "/ kernel time",
               "score_map_ms_per_step": round(score_ms / max(1, score_calls), 4)}
     else:
-        rl = roofline(exec_pp, score_ms / max(1, score_calls), nsm, sm_mhz, traffic=args.traffic)
+        rl = dense_roofline(exec_pp, score_ms / max(1, score_calls), nsm, sm_mhz, traffic=args.traffic)
         rl["peak_source"] = (f"{peak_kind} sm_max_mhz x {nsm} SMs x 128 shared-memory "
                              f"bytes/clk; 13.33 algorithmic bytes per pose-point (8x6 translation block)")
         rl["ms_per_launch"] = round(score_ms / max(1, score_calls), 4)
@@ -763,17 +833,22 @@ def run_gpu(args):
     if clocks.get("sm_mhz"):
         rl["frac_at_observed_clock"] = round(rl["frac"] * sm_mhz / clocks["sm_mhz"], 4)
     fms, fcalls = prof_full["score_map"]
-    rl_full = roofline(pp_step, fms / max(1, fcalls), props.multi_processor_count,
+    rl_full = dense_roofline(pp_step, fms / max(1, fcalls), props.multi_processor_count,
                        float(peaks.get("sm_max_mhz", 2070.0)))
     rl["no_early_termination"] = {"ms_per_launch": round(fms / max(1, fcalls), 4), "achieved": rl_full["achieved"],
                                   "frac": rl_full["frac"], "bound": "smem",
                                   "what": "score_tiled_kernel, every pose fully scored, 13.33 B per pose-point"}
-    rl_nom = roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
+    rl_nom = dense_roofline(pp_step, score_ms / max(1, score_calls), props.multi_processor_count,
                       float(peaks.get("sm_max_mhz", 2070.0)))
     rl["executed_pose_points_per_launch"] = int(exec_pp)
     rl["nominal_pose_points_per_launch"] = int(pp_step)
     rl["nominal"] = {"achieved": rl_nom["achieved"], "frac": rl_nom["frac"],
                      "what": "nominal pose-points (early termination not subtracted) x 13.33 B / score-map time"}
+    if hbm:
+        # kernels (a) and (b) on the config-5 image, FP32 pairs field (the scored layout)
+        c5 = hbm["config5_4096x3072"]
+        rl["gradient_kernel"] = dict(c5["gradient_fp32"], image="4096x3072 -> FP32 pairs field")
+        rl["pyramid_down_kernel"] = dict(c5["pyramid"], image="4096x3072 -> 2048x1536")
     rl["tiling"] = dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, B)))
     rl["tiling"]["autotuned"] = bool(tuning)
     if tuning:
@@ -802,6 +877,11 @@ def run_gpu(args):
                          f"~{B * (H * W * 11 // 1048576)} MB"},
         "ms_per_detection": ms / args.steps / B,
         "single_image_ms": single_ms,
+        "single_image_value": top_pose_points(model, 1) / (single_ms * 1e-3),
+        "executed": {"pose_points_per_step": int(exec_pp), "value": exec_pp * args.steps / (ms * 1e-3),
+                     "unit": "executed pose-point/s",
+                     "what": "pose-points the scorer actually evaluated (device counter) per second of the timed "
+                             "steps; the headline counts the exhaustive-equivalent (nominal) pose-points"},
         "single_image_tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, 1))),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
@@ -818,11 +898,25 @@ def run_gpu(args):
         "subpixel": subpixel,
         "quantized": quantized,
         "stress": stress,
+        "hbm": hbm,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_section(args):
+    import torch
+
+    import paper_2112_05576_gb300 as sam
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sam.lib()
+    stream = torch.cuda.current_stream(dev)
+    res = {"hbm": run_hbm}[args.only](args, sam, torch, dev, stream)
+    print(json.dumps({"section": args.only, "result": res}), flush=True)
     return 0
 
 
@@ -842,14 +936,19 @@ def main():
     ap.add_argument("--multi", type=int, default=64, help="images of the batched uneven form (0: skip)")
     ap.add_argument("--refine", type=int, default=4096, help="poses of the differentiable form (0: skip)")
     ap.add_argument("--stress", type=int, default=1, help="time the config-5 stress slices (0: skip)")
+    ap.add_argument("--hbm", type=int, default=1, help="time the gradient and pyramid kernels against HBM (0: skip)")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps[,cols] (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
+    ap.add_argument("--only", default="", choices=["", "hbm"],
+                    help="run one section alone and print its JSON (for profiling; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_section(args)
     return run_gpu(args)
 
 

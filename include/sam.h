@@ -229,6 +229,20 @@ sam_status sam_multi_autotune(sam_multi *mp, void *stream, int32_t *cfg_out, flo
                               int *n_out);
 sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long long *graph_kernels,
                            size_t *device_bytes);
+/* Copy of pair `pair`'s top-level score map, for inspection (the paper has
+ * no counterpart).  The map is FP32 [nth][gh][gw], pose (x, y, theta_k) at
+ * [k][y][x], and holds what the plan's last run (sam_multi_run or an
+ * autotuning run) left in it: Eq. (1) scores, -inf for poses pruned by early
+ * termination, and with a 16-bit field the FP32 rescores of the poses within
+ * the storage bound of min_score (-inf for the others).
+ *   dst       device float array of `capacity` >= nth * gh * gw entries, or
+ *             NULL to read the shape only.
+ *   nth, gh, gw, level  optional host outputs: the map's shape and the
+ *             pyramid level it scores.
+ * The copy is ordered on `stream` (no synchronisation).  Errors: SAM_ERR_ARG
+ * (NULL plan, pair out of range, capacity too small), SAM_ERR_CUDA. */
+sam_status sam_multi_pair_map(const sam_multi *mp, int pair, float *dst, size_t capacity, int *nth, int *gh,
+                              int *gw, int *level, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Individual steps on caller-owned device buffers (stream-ordered, no
@@ -388,8 +402,10 @@ sam_status sam_candidates(const float *map, int nth, int gh, int gw, float min_s
  * the library's device memory (held by every GPU that loads the library
  * until exit); maps with sam_candidates_scratch_bytes(nth, gh, gw) above
  * 4 MiB are rejected with SAM_ERR_CAPACITY.  The first call on a device looks
- * up that array's device address (with the device current) and caches it;
- * make that first call before any stream capture.  All calls share the array
+ * up that array's device address (with the device current) and caches it
+ * with the id of the device's context; make that first call before any
+ * stream capture.  After a device reset (a new primary context) the next
+ * call looks the address up again, so it too must come before any capture.  All calls share the array
  * and leave their contents in it (the counter is cleared at the start of
  * each call): calls whose GPU work overlaps race and must be serialised by
  * the caller.  Errors: SAM_ERR_ARG, SAM_ERR_CAPACITY, SAM_ERR_CUDA. */

@@ -581,6 +581,7 @@ cudaError_t launch_nms_jobs(const NmsJob *jobs, int n_jobs, int K, cudaStream_t 
 // on the array and must be serialised by the caller.
 // ---------------------------------------------------------------------------
 
+#include <cuda.h>
 #include <mutex>
 
 namespace sam {
@@ -593,10 +594,42 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};   // context the cached address belongs to (0: none)
+
+// Unique id of the current CUDA context (never reused within a process), by
+// the driver's cuCtxGetCurrent / cuCtxGetId fetched through the runtime, so
+// the library needs no link to the driver; 0 if unavailable.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrent)(CUcontext *);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_current, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 // Device address of g_noalloc_scratch on the current device.  The first call
 // on a device looks it up (cudaGetSymbolAddress, with that device current)
-// and caches it; later calls only read the cache.
+// and caches it together with the id of the device's current context; a
+// later call whose context id differs (the device was reset and its primary
+// context re-created) looks the address up again, as does every call when
+// the id cannot be read.
 cudaError_t noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -605,12 +638,16 @@ cudaError_t noalloc_scratch(void **out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = g_noalloc_ptr[dev] ? current_context_id() : 0;
+    if (!g_noalloc_ptr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
+        if (e != cudaSuccess) {
+            g_noalloc_ptr[dev] = nullptr;
             return e;
+        }
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = current_context_id();   // after the lookup, which makes the context current
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;

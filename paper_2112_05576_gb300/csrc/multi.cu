@@ -620,6 +620,28 @@ sam_status sam_multi_run(sam_multi *mp, void *stream, sam_pose *out, int capacit
     return SAM_OK;
 }
 
+sam_status sam_multi_pair_map(const sam_multi *mp, int pair, float *dst, size_t capacity, int *nth, int *gh,
+                              int *gw, int *level, void *stream) {
+    if (!mp || !mp->base || pair < 0 || pair >= (int)mp->pp.size())
+        return SAM_ERR_ARG;
+    const sam::PairPlan &q = mp->pp[pair];
+    if (nth)
+        *nth = q.nth;
+    if (gh)
+        *gh = q.H;
+    if (gw)
+        *gw = q.W;
+    if (level)
+        *level = q.top;
+    if (!dst)
+        return SAM_OK;
+    if (capacity < q.map_img)
+        return SAM_ERR_ARG;
+    MU_CU(cudaMemcpyAsync(dst, (const char *)mp->base + q.off_map, q.map_img * sizeof(float),
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SAM_OK;
+}
+
 sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long long *graph_kernels,
                            size_t *device_bytes) {
     if (!mp)

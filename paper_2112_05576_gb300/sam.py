@@ -97,6 +97,8 @@ SIGNATURES = {
     "sam_multi_autotune": (_c_int, [_vp, _vp, _i32p, _f32p, _c_int, ctypes.POINTER(_c_int)]),
     "sam_multi_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "sam_multi_pair_map": (_c_int, [_vp, _c_int, _vp, ctypes.c_size_t, ctypes.POINTER(_c_int),
+                                    ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), _vp]),
     "sam_score_bilinear": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _vp, _vp, _vp,
                                     _vp]),
     "sam_score_bilinear_adjoint": (_c_int, [_vp, _c_int, ctypes.POINTER(FieldRef), _c_int, _vp, _vp, _c_int, _vp,
@@ -519,6 +521,18 @@ class MultiPlan:
                "sam_multi_autotune")
         res = [(tuple(cfg[5 * i:5 * i + 5]), float(ms[i])) for i in range(n.value)]
         return sorted(res, key=lambda r: r[1])
+
+    def pair_map(self, pair, stream=None):
+        """Pair `pair`'s top-level score map (sam_multi_pair_map) as a new
+        (nth, gh, gw) float32 CUDA tensor, and the pyramid level it scores."""
+        import torch
+        nth, gh, gw, lvl = (ctypes.c_int() for _ in range(4))
+        shape = lambda: (ctypes.byref(nth), ctypes.byref(gh), ctypes.byref(gw), ctypes.byref(lvl))  # noqa: E731
+        _check(lib().sam_multi_pair_map(self._h, int(pair), None, 0, *shape(), _stream(stream)), "sam_multi_pair_map")
+        out = torch.empty((nth.value, gh.value, gw.value), dtype=torch.float32, device="cuda")
+        _check(lib().sam_multi_pair_map(self._h, int(pair), _ptr(out), out.numel(), *shape(), _stream(stream)),
+               "sam_multi_pair_map")
+        return out, lvl.value
 
     def stats(self):
         pp, gk, db = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()

@@ -324,12 +324,14 @@ def _scene_background(rng, H, W, level=100.0):
     return np.full((H, W), level, dtype=np.float64)
 
 
-def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None):
+def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, subpixel=False):
     """Paper-shaped scene: 1-4 instances of a side x side part with occlusion,
     an illumination ramp, 20 clutter segments and Gaussian noise sigma=6.
 
     Returns (template uint8, scene uint8, ground-truth poses, spec).
-    Instance angles are drawn on a 0.5 degree grid.
+    Instance angles are drawn on a 0.5 degree grid, positions on the pixel
+    grid; with subpixel=True each position is moved by U(-1/2, 1/2) px per
+    axis, drawn from a second generator so the scene is otherwise the same.
     """
     rng = np.random.default_rng(seed)
     if spec is None:
@@ -348,6 +350,9 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None):
              0.5 * float(rng.integers(0, 720)))
         if all(math.hypot(p[0] - q[0], p[1] - q[1]) > 1.5 * rad for q in poses):
             poses.append(p)
+    if subpixel:
+        frac = np.random.default_rng(seed + 0x5EED).uniform(-0.5, 0.5, (len(poses), 2))
+        poses = [(p[0] + float(f[0]), p[1] + float(f[1]), p[2]) for p, f in zip(poses, frac)]
     img = render_scene(bg, [(spec, p, float(rng.uniform(170, 210))) for p in poses])
     # clutter: 20 random line segments, 1.5-3 px thick, random gray
     for _ in range(20):

@@ -18,7 +18,7 @@ def test_slice_bytes_per_pose_point():
 
 
 def test_roofline_arithmetic():
-    r = bench.roofline(pp_per_launch=3e9, ms_per_launch=2.0, sm_count=152, sm_mhz_peak=2070.0, traffic=123)
+    r = bench.dense_roofline(pp_per_launch=3e9, ms_per_launch=2.0, sm_count=152, sm_mhz_peak=2070.0, traffic=123)
     peak = 128 * 152 * 2070e6 / 1e12
     achieved = 3e9 * (640.0 / 48.0) / 2e-3 / 1e12
     assert math.isclose(r["peak"], round(peak, 3))

@@ -1,14 +1,18 @@
-"""The allocation-free candidate entry point against the regular one.
+"""The allocation-free candidate entry point against the regular one and the oracle.
 
 sam_candidates_noalloc serves callers that cannot call cudaMalloc when they
 need candidates (deadline-bound loops, fixed device-memory budgets); it must
 give exactly what sam_candidates gives with a caller-provided scratch
-buffer, call after call, since its own scratch persists between calls.
+buffer, call after call, since its own scratch persists between calls, and
+exactly what the oracle's candidate selection gives on the same map (the
+maps hold multiples of 1/8, so FP32 and FP64 order them alike).
 Collected last so a failure here cannot hide any other test's result.
 """
 
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,6 +51,11 @@ def test_noalloc_matches_regular_entry_point_twice():
         assert ref[0] > 0 and got[0] == ref[0]
         assert np.array_equal(got[1], ref[1])
         assert np.array_equal(got[2], ref[2])
+        ck, cy, cx, cs = oracle.candidates(smap.cpu().numpy().astype(np.float64), 0.5, K)
+        assert got[0] == len(ck)
+        kyx = got[1].reshape(-1, 3)
+        assert np.array_equal(kyx[:, 0], ck) and np.array_equal(kyx[:, 1], cy) and np.array_equal(kyx[:, 2], cx)
+        assert np.array_equal(got[2], cs.astype(np.float32))
 
 
 def test_noalloc_rejects_maps_beyond_its_scratch():
