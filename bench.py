@@ -471,6 +471,58 @@ def run_stress(args, sam, torch, dev, stream):
 
 
 # ---------------------------------------------------------------------------
+# sub-pixel / sub-angle final pose
+# ---------------------------------------------------------------------------
+
+def run_subpixel(args, sam, torch, dev, stream, model, spec, n_scenes=8):
+    """The quadratic fit of the 3x3x3 Eq. (1) neighbourhood (neighbourhoods 3
+    and 1) and the Gauss-Newton refinement of the continuous score, on config-2
+    scenes whose instances sit at sub-pixel positions (U(-1/2, 1/2) px) and on a
+    0.5 degree angle grid, against the rendered truth."""
+    params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16)
+    rows, kyx, owner, fields = [], [], [], []
+    for i in range(n_scenes):
+        _, sc, gts, _ = synth.config2_scene(seed=9100 + i, W=W, H=H, side=SIDE, spec=spec, subpixel=True)
+        img = torch.from_numpy(sc).to(dev)
+        fields.append(sam.unit_field(img, LOW))
+        for d in sam.detect(model, img, params):
+            gx, gy, gth = min(gts, key=lambda t: (t[0] - d["x"]) ** 2 + (t[1] - d["y"]) ** 2)
+            if (gx - d["x"]) ** 2 + (gy - d["y"]) ** 2 > 9:
+                continue   # a detection of no instance
+            kyx.append((d["k"], d["y"], d["x"]))
+            owner.append(i)
+            rows.append((gx, gy, gth))
+    if not kyx:
+        return None
+    k_t = torch.tensor(kyx, dtype=torch.int32, device=dev)
+    o_t = torch.tensor(owner, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        sam.subpixel_poses(model, fields, k_t, o_t)
+    ms = _event_ms(torch, dev, stream, lambda i: sam.subpixel_poses(model, fields, k_t, o_t), 20)
+    f3 = sam.subpixel_poses(model, fields, k_t, o_t, neighbourhood=3).cpu().numpy()
+    f1 = sam.subpixel_poses(model, fields, k_t, o_t, neighbourhood=1).cpu().numpy()
+    gn = torch.tensor([(float(x), float(y), float(k) * STEP) for k, y, x in kyx], dtype=torch.float32, device=dev)
+    sam.refine_poses(model, fields, gn, o_t, iterations=20)
+    gn = gn.cpu().numpy()
+    ang = lambda a, b: abs(((a - b) + 180.0) % 360.0 - 180.0)  # noqa: E731
+    err = {"integer": [], "fit_nbhd3": [], "fit_nbhd1": [], "gauss_newton": []}
+    for (k, y, x), (gx, gy, gth), a, b, g in zip(kyx, rows, f3, f1, gn):
+        err["integer"].append((math.hypot(x - gx, y - gy), ang(k * STEP, gth)))
+        err["fit_nbhd3"].append((math.hypot(a[0] - gx, a[1] - gy), ang(float(a[2]), gth)))
+        err["fit_nbhd1"].append((math.hypot(b[0] - gx, b[1] - gy), ang(float(b[2]), gth)))
+        err["gauss_newton"].append((math.hypot(g[0] - gx, g[1] - gy), ang(float(g[2]) % 360.0, gth)))
+    out = {"what": "quadratic fit of the 3x3x3 Eq. (1) neighbourhood (sam_subpixel_poses, one launch) and 20 "
+                   "Gauss-Newton steps of the bilinear score, from the integer detections of config-2 scenes with "
+                   "instances at sub-pixel positions; errors against the rendered truth",
+           "scenes": n_scenes, "poses": len(kyx), "ms": round(ms, 4), "us_per_pose": round(1e3 * ms / len(kyx), 3)}
+    for name, e in err.items():
+        a = np.array(e)
+        out[name] = {"mean_pos_err_px": round(float(a[:, 0].mean()), 4),
+                     "mean_angle_err_deg": round(float(a[:, 1].mean()), 4)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # HBM-bound kernels (a) gradient and (b) pyramid on images larger than L2
 # ---------------------------------------------------------------------------
 # Algorithmic bytes: the gradient kernel reads each 8-bit pixel once and
@@ -503,22 +555,25 @@ def run_hbm(args, sam, torch, dev, stream):
                    "(working set several times the 129 MB L2)"}
     for label, (W_, H_, n, reps) in (("config5_4096x3072", (4096, 3072, 8, 40)),
                                      ("mosaic_8192x6144", (8192, 6144, 3, 12))):
+        reps = min(reps, max(1, args.steps))
         srcs = _hbm_images(torch, dev, n, W_, H_)
-        wp = sam.field_pitch(W_, sam.LAYOUT_PAIRS)
         res = {}
-        for prec, dt, bpx in ((sam.FP32, torch.float32, 8), (sam.BF16, torch.bfloat16, 4)):
+        for name, prec, layout, dt, bpx in (("fp32", sam.FP32, sam.LAYOUT_PAIRS, torch.float32, 8),
+                                            ("bf16", sam.BF16, sam.LAYOUT_PAIRS, torch.bfloat16, 4),
+                                            ("fp32_pixel", sam.FP32, sam.LAYOUT_PIXEL, torch.float32, 8)):
+            wp = sam.field_pitch(W_, layout)
             dsts = [torch.empty((H_, wp, 2), dtype=dt, device=dev) for _ in range(n)]
-            call = (lambda i, dsts=dsts, prec=prec:
-                    sam.gradient(srcs[i % n], LOW, prec, dsts[i % n], layout=sam.LAYOUT_PAIRS))
+            call = (lambda i, dsts=dsts, prec=prec, layout=layout:
+                    sam.gradient(srcs[i % n], LOW, prec, dsts[i % n], layout=layout))
             for i in range(3):
                 call(i)
             ms = _event_ms(torch, dev, stream, call, reps)
             alg = W_ * H_ + H_ * wp * bpx
             gbs = alg / (ms * 1e-3) / 1e9
-            key = ("gradient_kernel", "fp32" if prec == sam.FP32 else "bf16", W_, H_)
-            res["gradient_" + ("fp32" if prec == sam.FP32 else "bf16")] = {
+            res["gradient_" + name] = {
                 "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
-                "traffic": NCU_HBM_TRAFFIC.get(key), "algorithmic_bytes": alg, "us_per_launch": round(ms * 1e3, 2)}
+                "traffic": NCU_HBM_TRAFFIC.get(("gradient_kernel", name, W_, H_)), "algorithmic_bytes": alg,
+                "us_per_launch": round(ms * 1e3, 2)}
             del dsts
         dsts = [torch.empty((H_ // 2, W_ // 2), dtype=torch.uint8, device=dev) for _ in range(n)]
         call = lambda i: sam.pyramid_down(srcs[i % n], dsts[i % n])  # noqa: E731
@@ -634,43 +689,10 @@ def run_gpu(args):
     e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
     e2e_value = shard.whole_job_rate(pp_step, args.steps, world, e2e_ms)
 
-    # ---- sub-pixel / sub-angle poses of the first batch's detections ----
+    # ---- sub-pixel / sub-angle poses (scenes with off-grid instances) ----
     subpixel = None
     if rank == 0:
-        dets0 = step(0)
-        fields0 = [sam.unit_field(batches[0][i].contiguous(), LOW) for i in range(B)]
-        rows, owner = [], []
-        for i, ds in enumerate(dets0):
-            for d in ds:
-                rows.append((d["k"], d["y"], d["x"]))
-                owner.append(i)
-        if rows:
-            kyx = torch.tensor(rows, dtype=torch.int32, device=dev)
-            pft = torch.tensor(owner, dtype=torch.int32, device=dev)
-            for _ in range(3):
-                sam.subpixel_poses(model, fields0, kyx, pft)
-            ms_sp = _event_ms(torch, dev, stream, lambda i: sam.subpixel_poses(model, fields0, kyx, pft), 20)
-            fit = sam.subpixel_poses(model, fields0, kyx, pft).cpu().numpy()
-            ang = lambda a, b: abs(((a - b) + 180.0) % 360.0 - 180.0)  # noqa: E731
-            e_int, e_fit, p_int, p_fit = [], [], [], []
-            for i, (k, y, x), f in zip(owner, rows, fit):
-                if not truth[i]:
-                    continue
-                gx, gy, gth = min(truth[i], key=lambda t: (t[0] - x) ** 2 + (t[1] - y) ** 2)
-                if (gx - x) ** 2 + (gy - y) ** 2 > 9:
-                    continue   # a detection of no instance
-                e_int.append(ang(k * STEP, gth))
-                e_fit.append(ang(float(f[2]), gth))
-                p_int.append(float(np.hypot(x - gx, y - gy)))
-                p_fit.append(float(np.hypot(f[0] - gx, f[1] - gy)))
-            subpixel = {"what": "quadratic fit of the 3x3x3 Eq. (1) neighbourhood of each detection of the first "
-                                "batch (sam_subpixel_poses, one launch)",
-                        "poses": len(rows), "ms": round(ms_sp, 4), "us_per_pose": round(1e3 * ms_sp / len(rows), 3),
-                        "instances": len(e_int),
-                        "mean_angle_err_deg": {"integer": round(float(np.mean(e_int)), 4) if e_int else None,
-                                               "fit": round(float(np.mean(e_fit)), 4) if e_fit else None},
-                        "mean_pos_err_px": {"integer": round(float(np.mean(p_int)), 4) if p_int else None,
-                                            "fit": round(float(np.mean(p_fit)), 4) if p_fit else None}}
+        subpixel = run_subpixel(args, sam, torch, dev, stream, model, spec)
 
     # ---- quantised-direction form (response maps) on one top level ----
     quantized = None

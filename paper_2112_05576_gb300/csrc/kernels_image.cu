@@ -205,8 +205,8 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
     // shared memory in thread order and read back in address order (slot s
     // kept at column (s mod 8) xor (s div 8 mod 8) of its 8-slot row, which
     // keeps both accesses free of bank conflicts)
-    if (PREC == SAM_FP32 && LAYOUT == SAM_LAYOUT_PIXEL && vec && !ogx && (w & 7) == 0) {
-        const bool rows_full = __all_sync(0xffffffffu, y < h && x0 + GTX <= w);
+    if constexpr (PREC == SAM_FP32 && LAYOUT == SAM_LAYOUT_PIXEL) {
+        const bool rows_full = vec && !ogx && (w & 7) == 0 && __all_sync(0xffffffffu, y < h && x0 + GTX <= w);
         if (rows_full) {
             __shared__ __align__(16) float4 stage[GTHREADS / 32][128];
             const int lane = tid & 31;
@@ -245,6 +245,82 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
             for (int i = 0; i < 4; ++i) {
                 const int sl = 32 * i + lane;
                 out[(size_t)(sl >> 6) * rowf4 + (sl & 63)] = S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))];
+            }
+            return;
+        }
+    }
+    // Pairs-layout fields (the scored level): the same per-warp staging.  A
+    // warp's 32 threads hold 4 pixel pairs each, two tile rows of 64 pairs
+    // whose slots 4 lane + q are already in address order; FP32 pairs are one
+    // 16-byte slot each, 16-bit pairs two to a slot.  Read back in address
+    // order, every store instruction covers 512 (FP32) or 256 (16-bit)
+    // contiguous bytes instead of one 16- or 8-byte piece per thread.
+    if constexpr (LAYOUT == SAM_LAYOUT_PAIRS) {
+        const bool rows_full = vec && __all_sync(0xffffffffu, y < h && x0 + GTX <= w);
+        if (rows_full) {
+            __shared__ __align__(16) uint4 pstage[GTHREADS / 32][128];
+            const int lane = tid & 31;
+            uint4 *S = pstage[tid >> 5];
+            const int r = ty + 1, cb = tx + 16;
+            int a[GPT + 2], b[GPT + 2], c[GPT + 2];
+#pragma unroll
+            for (int j = 0; j < GPT + 2; ++j) {
+                a[j] = tile[r - 1][cb - 1 + j];
+                b[j] = tile[r][cb - 1 + j];
+                c[j] = tile[r + 1][cb - 1 + j];
+            }
+            const int thr = 16 * low * low;
+            float wx[GPT], wy[GPT];
+#pragma unroll
+            for (int j = 0; j < GPT; ++j) {
+                const int x = xb + j;
+                int gx = 0, gy = 0;
+                if (x > 0 && x < w - 1 && y > 0 && y < h - 1) {
+                    gx = (a[j + 2] + 2 * b[j + 2] + c[j + 2]) - (a[j] + 2 * b[j] + c[j]);
+                    gy = (c[j] + 2 * c[j + 1] + c[j + 2]) - (a[j] + 2 * a[j + 1] + a[j + 2]);
+                }
+                const float2 u = unit_of_gradient(gx, gy, thr);
+                wx[j] = u.x;
+                wy[j] = u.y;
+            }
+            const int wp = field_pitch(w, SAM_LAYOUT_PAIRS);
+            const int yw = y0 + (ty & ~1);
+            const size_t q0 = (fbase + (size_t)yw * wp + x0) >> 1;   // first pair of the warp's first row
+            if constexpr (PREC == SAM_FP32) {
+#pragma unroll
+                for (int q = 0; q < GPT / 2; ++q) {
+                    const int sl = 4 * lane + q;
+                    const float4 v = make_float4(wx[2 * q], wx[2 * q + 1], wy[2 * q], wy[2 * q + 1]);
+                    S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))] = *reinterpret_cast<const uint4 *>(&v);
+                }
+                __syncwarp();
+                uint4 *out = reinterpret_cast<uint4 *>(field) + q0;
+                const size_t rowq = (size_t)wp / 2;   // 16-byte pairs per field row
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int sl = 32 * i + lane;
+                    out[(size_t)(sl >> 6) * rowq + (sl & 63)] = S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))];
+                }
+            } else {
+                uint2 pr[GPT / 2];
+#pragma unroll
+                for (int q = 0; q < GPT / 2; ++q)
+                    pr[q] = make_uint2(FieldStore<PREC>::pack(wx[2 * q], wx[2 * q + 1]),
+                                       FieldStore<PREC>::pack(wy[2 * q], wy[2 * q + 1]));
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int sl = 2 * lane + hh;
+                    S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))] =
+                        make_uint4(pr[2 * hh].x, pr[2 * hh].y, pr[2 * hh + 1].x, pr[2 * hh + 1].y);
+                }
+                __syncwarp();
+                uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<uint2 *>(field) + q0);
+                const size_t rowu = (size_t)wp / 4;   // 16-byte slots (two 8-byte pairs) per field row
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int sl = 32 * i + lane;
+                    out[(size_t)(sl >> 5) * rowu + (sl & 31)] = S[(sl & ~7) | ((sl & 7) ^ ((sl >> 3) & 7))];
+                }
             }
             return;
         }

@@ -142,7 +142,9 @@ def test_plan_matches_oracle(plan_batch, prec):
         got = plan.run()
         for p, (g, r) in enumerate(zip(got, ref)):
             assert_same_detections(g, r, what=(prec, rep, p, pairs[p]))
-    # every pair's top-level map as the last run left it
+    # every pair's top-level map as the last run left it (a pair whose
+    # template is absent from its image may have every pose pruned)
+    n_live = 0
     for p, om in enumerate(maps):
         gm, lvl = plan.pair_map(p)
         gm = gm.cpu().numpy().astype(np.float64)
@@ -150,10 +152,10 @@ def test_plan_matches_oracle(plan_batch, prec):
         pruned = np.isneginf(gm)
         assert np.all(om[pruned] < MIN_SCORE), (prec, p)
         live = ~pruned
-        assert live.any()
-        assert np.max(np.abs(gm[live] - om[live])) < SCORE_TOL, (prec, p)
-        # every pose the oracle puts at or above min_score survives
-        assert not np.any(pruned & (om >= MIN_SCORE)), (prec, p)
+        n_live += int(live.sum())
+        if live.any():
+            assert np.max(np.abs(gm[live] - om[live])) < SCORE_TOL, (prec, p)
+    assert n_live > 0
     plan.close()
 
 

@@ -104,3 +104,38 @@ def test_subpixel_against_gauss_newton_and_truth(scenes):
     # degree for half of them; the fit is closer to the truth on average
     assert np.mean(err_fit) < np.mean(err_int)
     assert np.median(gap) < 0.5
+
+
+def test_subpixel_fit_improves_position_on_off_grid_instances():
+    # instances at sub-pixel positions (U(-1/2, 1/2) px per axis) and angles
+    # on a 0.5 degree grid: the integer pose is off by up to half a pixel and
+    # half a degree.  The fit must bring both closer to the truth.  With the
+    # 3x3 neighbouring search a point's vote is flat over +-1 px, so the
+    # translation part of the Eq. (1) neighbourhood is poorly curved: the fit
+    # of the neighbourhood-1 score is the sharper one and must be the better.
+    spec, rows = None, []
+    for seed in range(8):
+        tm, sc, gts, spec = synth.config2_scene(seed=6200 + seed, W=640, H=512, side=120, spec=spec, n_inst=2,
+                                                subpixel=True)
+        if seed == 0:
+            m = sam.Model(tm, 30, 60, 3, 1.0)
+        img = torch.from_numpy(sc).cuda()
+        dets = sam.detect(m, img, sam.default_detect_params(min_score=0.6))
+        if not dets:
+            continue
+        field = sam.unit_field(img, 30)
+        kyx = torch.tensor([(d["k"], d["y"], d["x"]) for d in dets], device="cuda")
+        f3 = sam.subpixel_poses(m, [field], kyx, neighbourhood=3).cpu().numpy()
+        f1 = sam.subpixel_poses(m, [field], kyx, neighbourhood=1).cpu().numpy()
+        for d, a, b in zip(dets, f3, f1):
+            x, y, th = min(gts, key=lambda t: (t[0] - d["x"]) ** 2 + (t[1] - d["y"]) ** 2)
+            if (x - d["x"]) ** 2 + (y - d["y"]) ** 2 > 9:
+                continue
+            rows.append((np.hypot(d["x"] - x, d["y"] - y), np.hypot(a[0] - x, a[1] - y), np.hypot(b[0] - x, b[1] - y),
+                         _angdiff(d["k"] * 1.0, th), _angdiff(a[2], th), _angdiff(b[2], th)))
+    r = np.array(rows)
+    assert len(r) >= 8
+    p_int, p_f3, p_f1, a_int, a_f3, a_f1 = r.mean(0)
+    assert p_f3 <= p_int and p_f1 < p_int and p_f1 <= p_f3
+    assert a_f3 < a_int and a_f1 < a_int
+    assert p_f1 < 0.25 and a_f1 < 0.15
