@@ -529,9 +529,21 @@ def run_subpixel(args, sam, torch, dev, stream, model, spec, n_scenes=8):
 # writes its unit-field pixel once (8 B FP32 pair, 4 B 16-bit pair; pairs
 # layout, row pitch rounded up to 4 pixels); the pyramid kernel reads the
 # 2 x 2 block of 8-bit pixels under each output pixel and writes it (4 + 1 B).
-# DRAM bytes per launch, from an ncu capture of `bench.py --only hbm`, keyed
-# by kernel, precision and image size; None until taken.
-NCU_HBM_TRAFFIC = {}
+# DRAM bytes (read + write) per launch, from an ncu capture of
+# `bench.py --only hbm --steps 1` (mean over the captured launches), keyed by
+# kernel, field form and image size.  Writes that are still in L2 when a
+# launch ends are not counted, so a field that fits L2 shows less write
+# traffic than it has algorithmic bytes.
+NCU_HBM_TRAFFIC = {
+    ("gradient_kernel", "fp32", 4096, 3072): 48_818_000,
+    ("gradient_kernel", "bf16", 4096, 3072): 12_607_000,
+    ("gradient_kernel", "fp32_pixel", 4096, 3072): 48_655_000,
+    ("pyramid_down_kernel", 4096, 3072): 12_589_000,
+    ("gradient_kernel", "fp32", 8192, 6144): 387_774_000,
+    ("gradient_kernel", "bf16", 8192, 6144): 187_279_000,
+    ("gradient_kernel", "fp32_pixel", 8192, 6144): 387_699_000,
+    ("pyramid_down_kernel", 8192, 6144): 50_340_000,
+}
 
 
 def _hbm_images(torch, dev, n, W_, H_):

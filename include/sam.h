@@ -48,8 +48,17 @@ typedef enum {
     SAM_ERR_CAPACITY = 6      /* a fixed-capacity device buffer would overflow */
 } sam_status;
 
-/* Field precisions of the normalised search gradients w_hat. */
-enum { SAM_FP32 = 0, SAM_BF16 = 1, SAM_FP16 = 2 };
+/* Field precisions of the normalised search gradients w_hat.
+ * SAM_ANGLE16 (angle-only storage; the paper stores x/y gradients, this form
+ * keeps their direction alone): one 16-bit code per pixel, 0x8000 | a on an
+ * edge with a = round(atan2(gy, gx) * 32768 / (2 pi)) mod 32768 from the
+ * integer Sobel gradient, 0 elsewhere; it stands for the unit vector
+ * (cos, sin)(a 2 pi / 32768), so a term of Eq. (1) moves by at most
+ * 2 sin(pi / 65536) < 9.6e-5 against the exact direction.  Code rows have
+ * pitch w (SAM_LAYOUT_PIXEL) or w rounded up to a multiple of 8 codes,
+ * 16-byte rows, padding codes 0 (SAM_LAYOUT_PAIRS, the layout the scorers
+ * read).  Served by sam_gradient, sam_score_map and sam_score_window. */
+enum { SAM_FP32 = 0, SAM_BF16 = 1, SAM_FP16 = 2, SAM_ANGLE16 = 3 };
 
 /* Field layouts.  SAM_LAYOUT_PIXEL: each row holds w pixels, each pixel the
  * pair (wx, wy); row pitch w pixels.  SAM_LAYOUT_PAIRS: each row holds pixel
@@ -260,8 +269,14 @@ sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, ui
  * w_hat = g/|g| on edges, (0,0) elsewhere.
  *   field   device, h rows in `layout` (SAM_LAYOUT_PIXEL or SAM_LAYOUT_PAIRS),
  *           float components (8 B/px) for SAM_FP32, bf16 or fp16 (4 B/px)
- *           otherwise; 16-byte aligned for SAM_LAYOUT_PAIRS.
- *   gx, gy  optional device int16 outputs (w*h, dense), NULL to skip. */
+ *           for SAM_BF16 / SAM_FP16, 16-bit angle codes (2 B/px; rows as
+ *           described at SAM_ANGLE16) for SAM_ANGLE16; 16-byte aligned for
+ *           SAM_LAYOUT_PAIRS.  The angle codes are computed from the integer
+ *           gradient with an FP32 atan2, redone in FP64 where the FP32 value
+ *           lies within 0.02 of a rounding boundary, so they equal the
+ *           rounding of the exact angle.
+ *   gx, gy  optional device int16 outputs (w*h, dense), NULL to skip; not
+ *           with SAM_LAYOUT_PAIRS or SAM_ANGLE16. */
 sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, int layout,
                         void *field, int16_t *gx, int16_t *gy, void *stream);
 
@@ -273,8 +288,13 @@ sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, i
  *           precision as produced by sam_gradient).
  *   map     device float array of num_angles * gh * gw.
  * With early_termination, poses proved below min_score are written -inf.
- * The tiled kernel serves FP32 SAM_LAYOUT_PAIRS fields at step 1 when its
- * shared-memory window fits; everything else uses the generic kernel.  With
+ * The tiled kernel serves SAM_LAYOUT_PAIRS fields at step 1 when its
+ * shared-memory window fits; everything else uses the generic kernel.
+ * SAM_ANGLE16 code fields (SAM_LAYOUT_PAIRS, step 1, a template whose window
+ * fits) are scored by the tiled kernel only: each CTA stages its window of
+ * codes by TMA and expands it to FP32 unit vectors in shared memory (sincospi
+ * in FP32, within 2.4e-7 of the FP64 decoding) before scoring; other calls
+ * with codes return SAM_ERR_ARG.  With
  * early termination the tiled kernel runs in its persistent form (work units
  * of the edge-presence bound, then the surviving poses, pulled by resident
  * CTAs) with a queue taken from the device's default stream-ordered memory
@@ -293,9 +313,11 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
  * resolution search of a large template over a large image is scored slice
  * by slice) and the single-image path of the tiled scorers: `field` is the
  * level's SAM_LAYOUT_PAIRS field in `precision` (16-byte aligned, pitch
- * field_pitch(w)).  Templates whose rotated extent exceeds one shared-memory
- * window are scored by the chunked kernel (points grouped by 16 x 16 offset
- * cell, one staged window per cell).  early_termination as in
+ * field_pitch(w); SAM_ANGLE16 codes: pitch w rounded up to 8 codes).
+ * Templates whose rotated extent exceeds one shared-memory window are scored
+ * by the chunked kernel (points grouped by 16 x 16 offset cell, one staged
+ * window per cell; not for SAM_ANGLE16, which then returns SAM_ERR_ARG).
+ * field32 rescoring applies to SAM_BF16 / SAM_FP16 only.  early_termination as in
  * sam_score_map (-inf for pruned poses).  For a 16-bit `precision` with a
  * non-NULL field32 (the level's FP32 SAM_LAYOUT_PIXEL field, pitch w), every
  * pose within the storage error bound of min_score is rescored in FP32 and

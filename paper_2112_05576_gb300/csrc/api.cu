@@ -460,7 +460,8 @@ ScoreChoice &score_choice() {
 bool tiled_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg) {
     int bxw = 0, byw = 0;
     return cfg.tg >= 1 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
-           ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) &&
+           ((uintptr_t)a.field % 16 == 0) &&
+           (a.count == 1 || a.field_img_px % (a.precision == SAM_ANGLE16 ? 8 : 4) == 0) &&
            tiled_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, cfg.tg, cfg.tc, &bxw, &byw);
 }
 
@@ -473,7 +474,7 @@ constexpr TileConfig kChunkCfg = {2, 2, 0, 4, kChunkCols};
 bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg = kChunkCfg) {
     int bxw = 0, byw = 0;
     return cfg.tg == 0 && cfg.sx * cfg.sy == cfg.warps && (cfg.warps == 4 || cfg.warps == 8) &&
-           a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
+           a.precision != SAM_ANGLE16 && a.layout == SAM_LAYOUT_PAIRS && a.step_x == 1 && a.step_y == 1 && (a.nbhd == 1 || a.nbhd == 3) &&
            ((uintptr_t)a.field % 16 == 0) && (a.count == 1 || a.field_img_px % 4 == 0) && a.count <= 65535 &&
            m->dev[level].crot && m->lv[level].ntheta <= 65535 &&
            chunked_plan(m->lv[level], a.precision, cfg.sx, cfg.sy, &bxw, &byw);
@@ -482,7 +483,7 @@ bool chunked_ok(const sam_model *m, int level, const ScoreArgs &a, const TileCon
 // The tiled or chunked scorer for `cfg` over the map (or pose window) of `a`.
 cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, const TileConfig &cfg,
                                cudaStream_t st, const PoseWindow *window = nullptr) {
-    const int wp = field_pitch(a.w, SAM_LAYOUT_PAIRS);
+    const int wp = any_field_pitch(a.w, SAM_LAYOUT_PAIRS, a.precision);
     if (cfg.tg == 0)
         return launch_score_chunked(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
                                     a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
@@ -496,6 +497,9 @@ cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a
 // images: the one tuned for that batch class (one image / several), else the
 // other class's, else none.
 const TileConfig *tuned_tiling(const sam_model *m, int precision, int count) {
+    // angle codes are scored by the FP32 arithmetic: they use its tuning
+    if (precision == SAM_ANGLE16)
+        precision = SAM_FP32;
     const int cls = count > 1 ? 1 : 0;
     if (m->tuned[precision][cls])
         return &m->tile[precision][cls];
@@ -518,6 +522,16 @@ bool pick_fast_scorer(const sam_model *m, int level, const ScoreArgs &a, TileCon
         *out = cfg;
         return true;
     }
+    if (a.precision == SAM_ANGLE16) {
+        // codes have no chunked or generic scorer: the default tiling, or
+        // one angle per CTA when its window is too large
+        for (const TileConfig &d : {TileConfig{}, TileConfig{1, 1, 1, 4, 6}})
+            if (tiled_ok(m, level, a, d)) {
+                *out = d;
+                return true;
+            }
+        return false;
+    }
     if (chunked_ok(m, level, a)) {
         *out = kChunkCfg;
         return true;
@@ -530,6 +544,8 @@ cudaError_t launch_score_map(const sam_model *m, int level, const ScoreArgs &a, 
     TileConfig cfg;
     if (pick_fast_scorer(m, level, a, &cfg))
         return launch_fast_scorer(m, level, a, cfg, st);
+    if (a.precision == SAM_ANGLE16)
+        return cudaErrorInvalidValue;
     return launch_score_map_generic(m->dev[level], a, st);
 }
 
@@ -893,11 +909,13 @@ sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, ui
 sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, int precision, int layout,
                         void *field, int16_t *gx, int16_t *gy, void *stream) {
     if (!img || !field || w < 1 || h < 1 || stride < w || low < 1 || low > 1024 || precision < SAM_FP32 ||
-        precision > SAM_FP16 || (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS) ||
-        ((gx == nullptr) != (gy == nullptr)) || (layout == SAM_LAYOUT_PAIRS && (gx || (uintptr_t)field % 16)))
+        precision > SAM_ANGLE16 || (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS) ||
+        ((gx == nullptr) != (gy == nullptr)) || (precision == SAM_ANGLE16 && gx) ||
+        (layout == SAM_LAYOUT_PAIRS && (gx || (uintptr_t)field % 16)))
         return SAM_ERR_ARG;
     return launch_gradient(img, w, h, stride, 0, low, precision, layout, field,
-                           (size_t)field_pitch(w, layout) * h, gx, gy, 1, (cudaStream_t)stream) == cudaSuccess
+                           (size_t)any_field_pitch(w, layout, precision) * h, gx, gy, 1,
+                           (cudaStream_t)stream) == cudaSuccess
                ? SAM_OK
                : SAM_ERR_CUDA;
 }
@@ -906,15 +924,16 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
                          int step_x, int step_y, int neighbourhood, float min_score, int early_termination,
                          float *map, void *stream) {
     if (!m || level < 0 || level >= m->levels || !field || !map || w < 1 || h < 1 || step_x < 1 || step_y < 1 ||
-        (neighbourhood != 1 && neighbourhood != 3) || precision < SAM_FP32 || precision > SAM_FP16 ||
-        (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS))
+        (neighbourhood != 1 && neighbourhood != 3) || precision < SAM_FP32 || precision > SAM_ANGLE16 ||
+        (layout != SAM_LAYOUT_PIXEL && layout != SAM_LAYOUT_PAIRS) ||
+        (precision == SAM_ANGLE16 && (layout != SAM_LAYOUT_PAIRS || step_x != 1 || step_y != 1)))
         return SAM_ERR_ARG;
     sam_status s = upload_model(m);
     if (s != SAM_OK)
         return s;
     ScoreArgs sa;
     sa.field = field;
-    sa.field_img_px = (size_t)field_pitch(w, layout) * h;
+    sa.field_img_px = (size_t)any_field_pitch(w, layout, precision) * h;
     sa.w = w;
     sa.h = h;
     sa.precision = precision;
@@ -943,6 +962,12 @@ sam_status sam_score_map(sam_model *m, int level, const void *field, int w, int 
             q = nullptr;
         }
     }
+    TileConfig probe;
+    if (precision == SAM_ANGLE16 && !pick_fast_scorer(m, level, sa, &probe)) {
+        if (q)
+            cudaFreeAsync(q, st);
+        return SAM_ERR_ARG;   // codes are scored by the tiled kernel only
+    }
     const cudaError_t e = launch_score_map(m, level, sa, nullptr, st);
     if (q && cudaFreeAsync(q, st) != cudaSuccess)
         return SAM_ERR_CUDA;
@@ -955,11 +980,11 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
                             int gw, int gh, int k0, int nk, int neighbourhood, float min_score, int early_termination,
                             const float *field32, void *scratch, size_t scratch_bytes, float *map, void *stream) {
     if (!m || level < 0 || level >= m->levels || !field || !map || w < 1 || h < 1 || precision < SAM_FP32 ||
-        precision > SAM_FP16 || (neighbourhood != 1 && neighbourhood != 3) || x0 < 0 || y0 < 0 || gw < 1 ||
+        precision > SAM_ANGLE16 || (neighbourhood != 1 && neighbourhood != 3) || x0 < 0 || y0 < 0 || gw < 1 ||
         gh < 1 || x0 > w - gw || y0 > h - gh || k0 < 0 || nk < 1 || nk > 65535 || k0 > m->lv[level].ntheta - nk ||
         (size_t)nk * gw * gh > 0xFFFFFFFFull || (uintptr_t)field % 16 || (uintptr_t)map % 8)
         return SAM_ERR_ARG;
-    const bool rescore = precision != SAM_FP32 && field32;
+    const bool rescore = (precision == SAM_BF16 || precision == SAM_FP16) && field32;
     if (rescore && (!scratch || scratch_bytes < rescore_scratch_bytes(1) || (uintptr_t)field32 % 8 ||
                     (uintptr_t)scratch % 8))
         return SAM_ERR_ARG;
@@ -969,7 +994,7 @@ sam_status sam_score_window(sam_model *m, int level, const void *field, int w, i
     cudaStream_t st = (cudaStream_t)stream;
     ScoreArgs a;
     a.field = field;
-    a.field_img_px = (size_t)field_pitch(w, SAM_LAYOUT_PAIRS) * h;
+    a.field_img_px = (size_t)any_field_pitch(w, SAM_LAYOUT_PAIRS, precision) * h;
     a.w = w;
     a.h = h;
     a.precision = precision;

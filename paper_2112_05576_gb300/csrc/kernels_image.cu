@@ -153,6 +153,29 @@ struct FieldStore<SAM_FP16> {
     }
 };
 
+// Angle-only storage: the 16-bit code of an integer gradient, 0x8000 | a with
+// a = round(atan2(gy, gx) 32768 / (2 pi)) mod 32768 on an edge, else 0.  The
+// FP32 atan2 (a few ulp, below 0.01 of a step with the scaling) decides the
+// code unless its scaled value lies within 0.02 of a rounding boundary; there
+// the FP64 atan2 decides.  No Sobel gradient has its exact angle within
+// 1.2e-6 steps of a boundary, so both give the rounding of the exact angle.
+__device__ __forceinline__ uint32_t angle_code(int gx, int gy, int thr) {
+    const int m2 = gx * gx + gy * gy;
+    if (m2 < thr || m2 == 0)
+        return 0u;
+    const float sf = atan2f((float)gy, (float)gx) * (32768.0f / 6.28318530717958648f) + 0.5f;
+    const float fl = floorf(sf);
+    const float d = sf - fl;
+    int a;
+    if (d > 0.02f && d < 0.98f) {
+        a = (int)fl;
+    } else {
+        const double t = atan2((double)gy, (double)gx) * 32768.0 / (2.0 * 3.14159265358979323846);
+        a = (int)floor(t + 0.5);
+    }
+    return 0x8000u | ((uint32_t)a & 0x7FFFu);
+}
+
 // One GTX x GTY tile of one image whose field starts fbase pixels into
 // `field` (the caller returns early, block-uniformly, for tiles outside).
 template <int PREC, int LAYOUT>
@@ -198,6 +221,44 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
     const int tx = (tid - ty * (GTX / GPT)) * GPT;
     const int y = y0 + ty;
     const int xb = x0 + tx;
+    if constexpr (PREC == SAM_ANGLE16) {
+        // 8 codes (16 bytes) per thread; with the padded pitch (a multiple of
+        // 8) a thread's group never straddles the row end, and its codes
+        // beyond w are 0 (zero gradient)
+        const int cp = code_pitch(w, LAYOUT);
+        if (y >= h || xb >= cp)
+            return;
+        const int r = ty + 1, cb = tx + 16;
+        int a[GPT + 2], b[GPT + 2], c[GPT + 2];
+#pragma unroll
+        for (int j = 0; j < GPT + 2; ++j) {
+            a[j] = tile[r - 1][cb - 1 + j];
+            b[j] = tile[r][cb - 1 + j];
+            c[j] = tile[r + 1][cb - 1 + j];
+        }
+        const int thr = 16 * low * low;
+        uint32_t code[GPT];
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+            const int x = xb + j;
+            int gx = 0, gy = 0;
+            if (x > 0 && x < w - 1 && y > 0 && y < h - 1) {
+                gx = (a[j + 2] + 2 * b[j + 2] + c[j + 2]) - (a[j] + 2 * b[j] + c[j]);
+                gy = (c[j] + 2 * c[j + 1] + c[j + 2]) - (a[j] + 2 * a[j + 1] + a[j + 2]);
+            }
+            code[j] = angle_code(gx, gy, thr);
+        }
+        uint16_t *out = reinterpret_cast<uint16_t *>(field) + fbase + (size_t)y * cp + xb;
+        if (vec && xb + GPT <= cp) {
+            *reinterpret_cast<uint4 *>(out) = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16),
+                                                         code[4] | (code[5] << 16), code[6] | (code[7] << 16));
+        } else {
+#pragma unroll
+            for (int j = 0; j < GPT; ++j)
+                if (xb + j < cp)
+                    out[j] = (uint16_t)code[j];
+        }
+    } else {
     // FP32 pixel-layout fields of whole rows (the large fields of the lower
     // levels) are written through a per-warp staging buffer so that every
     // store instruction covers 512 contiguous bytes: a warp owns two rows of
@@ -395,6 +456,7 @@ __device__ __forceinline__ void gradient_tile(const uint8_t *__restrict__ img, i
             }
         }
     }
+    }   // PREC != SAM_ANGLE16
 }
 
 // `count` images of equal size, image blockIdx.z.
@@ -495,9 +557,9 @@ cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t
                             cudaStream_t st) {
     if (w <= 0 || h <= 0 || count <= 0)
         return cudaSuccess;
-    if (layout == SAM_LAYOUT_PAIRS && gx)
+    if ((layout == SAM_LAYOUT_PAIRS || precision == SAM_ANGLE16) && gx)
         return cudaErrorInvalidValue;
-    const size_t esz = precision == SAM_FP32 ? 8 : 4;
+    const size_t esz = precision == SAM_FP32 ? 8 : (precision == SAM_ANGLE16 ? 2 : 4);
     const int vec = ((uintptr_t)img % 16 == 0) && (stride % 16 == 0) && (count == 1 || img_bytes % 16 == 0) &&
                     ((uintptr_t)field % 16 == 0) && (count == 1 || (field_img_px * esz) % 16 == 0) &&
                     (!gx || (((uintptr_t)gx % 16 == 0) && ((uintptr_t)gy % 16 == 0) &&
@@ -507,6 +569,12 @@ cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t
     case SAM_FP32:
         gradient_dispatch<SAM_FP32>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px, gx, gy,
                                     vec);
+        break;
+    case SAM_ANGLE16:
+        // 16-byte code stores need 8-code-aligned rows and images
+        gradient_dispatch<SAM_ANGLE16>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px,
+                                       nullptr, nullptr,
+                                       vec && code_pitch(w, layout) % 8 == 0 && (count == 1 || field_img_px % 8 == 0));
         break;
     case SAM_BF16:
         gradient_dispatch<SAM_BF16>(layout, grid, st, img, w, h, stride, img_bytes, low, field, field_img_px, gx, gy,

@@ -175,6 +175,15 @@ cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t
 __host__ __device__ inline int field_pitch(int w, int layout) {
     return layout == SAM_LAYOUT_PAIRS ? ((w + 3) & ~3) : w;
 }
+// Angle-code fields (SAM_ANGLE16): one 16-bit code per pixel, row pitch w, or
+// w rounded up to a multiple of 8 codes (16-byte rows, the TMA-read layout).
+__host__ __device__ inline int code_pitch(int w, int layout) {
+    return layout == SAM_LAYOUT_PAIRS ? ((w + 7) & ~7) : w;
+}
+// Row pitch of a field of any precision, in pixels.
+__host__ __device__ inline int any_field_pitch(int w, int layout, int precision) {
+    return precision == SAM_ANGLE16 ? code_pitch(w, layout) : field_pitch(w, layout);
+}
 
 // (c) exhaustive score map of one level for `count` fields
 struct ScoreArgs {
@@ -317,6 +326,10 @@ SAM_TILED_LAUNCHERS(f32)
 SAM_TILED_LAUNCHERS(f16)
 SAM_TILED_LAUNCHERS(bf16)
 #undef SAM_TILED_LAUNCHERS
+// Angle-code fields (score_tiled_a16.cu): the single-level tiled scorer and
+// its persistent form only.
+cudaError_t launch_tiled_a16(const CUtensorMap &tm, const TiledArgs &a, dim3 grid, size_t smem, int nbhd, bool pol,
+                             int warps, int tc, cudaStream_t st);
 
 // Chunked tiled scorer for levels with chunk tables (score_tiled.cu).
 cudaError_t launch_score_chunked(const sam_model *m, int level, const void *field, int precision, int wp,

@@ -47,7 +47,11 @@ __device__ __forceinline__ float dir_round<__nv_bfloat16>(float v) {
 // 2^-12 (FP16) or 2^-9 (BF16), so a term moves by at most 2 sqrt(2) times
 // that (6.9e-4, 5.5e-3), plus FP32 rounding.
 inline float term_eps(int precision) {
-    return precision == SAM_FP32 ? 1e-6f : (precision == SAM_FP16 ? 1e-3f : 6e-3f);
+    // angle codes are expanded to FP32 unit vectors (within 2.4e-7 of exact)
+    // and scored in FP32 like an FP32 field
+    if (precision == SAM_FP32 || precision == SAM_ANGLE16)
+        return 1e-6f;
+    return precision == SAM_FP16 ? 1e-3f : 6e-3f;
 }
 
 // Early termination: prune when S_j + (n - j) < n * min_score - margin,

@@ -113,8 +113,16 @@ struct Geometry {
 Geometry geometry(int precision, int tc) {
     if (precision == SAM_FP32)
         return {kLanesXF32 * tc, (32 / kLanesXF32) * kTileRows, 2, 16};
+    // angle codes: scored as FP32 pairs in shared memory, staged as 2-byte
+    // codes whose TMA start must be a multiple of 8 pixels
+    if (precision == SAM_ANGLE16)
+        return {kLanesXF32 * tc, (32 / kLanesXF32) * kTileRows, 8, 16};
     return {kLanesX16 * tc, (32 / kLanesX16) * kTileRows, 4, 8};
 }
+
+// Bytes of the staged angle codes of a window (the expanded window is two
+// pixels wider than the staged one).
+size_t staged_code_bytes(int bxw, int byw) { return (size_t)(bxw - 2) * byw * 2; }
 
 }  // namespace
 
@@ -139,12 +147,21 @@ bool tiled_plan(const LevelHost &L, int precision, int sx, int sy, int tg, int t
     }
     int bx = sx * g.wtx + spx + 2 + (g.xalign - 1) + 1;
     bx = (bx + g.xalign - 1) / g.xalign * g.xalign;
+    const int by = sy * g.wty + spy + 2;
+    if (precision == SAM_ANGLE16) {
+        // staged: bx codes per row (a multiple of 8, 16-byte TMA rows);
+        // expanded: bx + 2 pixels, an odd number of 16-byte pairs per row
+        *bxw = bx + 2;
+        *byw = by;
+        const size_t win = ((size_t)(bx + 2) * by * 8 + 127) & ~(size_t)127;
+        const size_t bytes = win + std::max(edge_bitmap_bytes(bx + 2, by), staged_code_bytes(bx + 2, by));
+        return bx <= 256 && by <= 256 && bytes <= 200 * 1024;
+    }
     // row pitch: an odd number of 16-byte units (FP32 pixel pairs) or twice
     // an odd number of 8-byte units (16-bit pairs), so rows 2 apart fall in
     // other shared-memory banks
     if (g.pair_bytes == 16 ? ((bx / 2) % 2 == 0) : ((bx / 2) % 4 == 0))
         bx += g.xalign;
-    const int by = sy * g.wty + spy + 2;
     *bxw = bx;
     *byw = by;
     const size_t bytes = (((size_t)bx * by * g.pair_bytes / 2 + 15) & ~(size_t)15) + edge_bitmap_bytes(bx, by);
@@ -178,15 +195,20 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     if (!device_flags(&fl))
         return cudaErrorUnknown;
     // the field as a 3-D tensor of 8-byte elements: a pixel pair is 2 (FP32)
-    // or 1 (16-bit) element(s)
+    // or 1 (16-bit) element(s); angle codes: 2-byte elements, one per pixel,
+    // row pitch wp codes, the box two pixels narrower than the expanded window
     CUtensorMap tm;
-    const cuuint64_t dims[3] = {(cuuint64_t)wp * g.pair_bytes / 16, (cuuint64_t)H, (cuuint64_t)count};
-    const cuuint64_t strides[2] = {(cuuint64_t)wp * g.pair_bytes / 2, (cuuint64_t)field_img_px * g.pair_bytes / 2};
-    const cuuint32_t box[3] = {(cuuint32_t)(bxw * g.pair_bytes / 16), (cuuint32_t)byw, 1};
+    const bool codes = precision == SAM_ANGLE16;
+    const cuuint64_t dims[3] = {codes ? (cuuint64_t)wp : (cuuint64_t)wp * g.pair_bytes / 16, (cuuint64_t)H,
+                                (cuuint64_t)count};
+    const cuuint64_t strides[2] = {codes ? (cuuint64_t)wp * 2 : (cuuint64_t)wp * g.pair_bytes / 2,
+                                   codes ? (cuuint64_t)field_img_px * 2 : (cuuint64_t)field_img_px * g.pair_bytes / 2};
+    const cuuint32_t box[3] = {codes ? (cuuint32_t)(bxw - 2) : (cuuint32_t)(bxw * g.pair_bytes / 16), (cuuint32_t)byw,
+                               1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(field), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (enc(&tm, codes ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(field),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     TiledArgs a;
     a.rot = m->dev[level].rot;
@@ -247,12 +269,17 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     // the edge bitmaps follow the window; the persistent form reuses their
     // space for the partial sums of split tasks (warps x 32 lanes x slice)
     const size_t red = (size_t)cfg.warps * 32 * kDrainRows * cfg.tc * 4;
-    const size_t smem = (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) +
-                        std::max(edge_bitmap_bytes(bxw, byw), red) + 128;
+    const size_t smem = codes ? (((size_t)bxw * byw * 8 + 127) & ~(size_t)127) +
+                                    std::max(std::max(edge_bitmap_bytes(bxw, byw), red), staged_code_bytes(bxw, byw)) +
+                                    128
+                              : (((size_t)bxw * byw * g.pair_bytes / 2 + 15) & ~(size_t)15) +
+                                    std::max(edge_bitmap_bytes(bxw, byw), red) + 128;
     const bool pol = polarity != 0;
     switch (precision) {
     case SAM_FP32:
         return launch_tiled_f32(tm, a, grid, smem, nbhd, pol, cfg.warps, cfg.tc, st);
+    case SAM_ANGLE16:
+        return launch_tiled_a16(tm, a, grid, smem, nbhd, pol, cfg.warps, cfg.tc, st);
     case SAM_FP16:
         return launch_tiled_f16(tm, a, grid, smem, nbhd, pol, cfg.warps, cfg.tc, st);
     default:

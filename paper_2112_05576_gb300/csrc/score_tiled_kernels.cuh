@@ -34,6 +34,24 @@ struct Pairs<float> {
     static constexpr int BYTES = 16;   // one pixel pair
     static constexpr int LX = kLanesXF32;   // lanes along x
     static constexpr int XALIGN = 2;   // window start (pixels) for a 16-byte TMA start
+    static constexpr bool CODES = false;   // the window is staged as stored
+    static __device__ __forceinline__ float4 get(const Raw *row, int q) { return row[q]; }
+};
+
+// Angle-only storage (SAM_ANGLE16): the field holds one 16-bit code per
+// pixel; the window is staged as codes (2 bytes per pixel, TMA starts at
+// multiples of 8 pixels) and expanded in shared memory to FP32 pixel pairs,
+// which the FP32 arithmetic then scores.  The expanded window is two pixels
+// wider than the staged one (a zero pair column), which keeps its row pitch
+// an odd number of 16-byte pairs.
+struct AngleCode {};
+template <>
+struct Pairs<AngleCode> {
+    using Raw = float4;
+    static constexpr int BYTES = 16;   // one expanded pixel pair in shared memory
+    static constexpr int LX = kLanesXF32;
+    static constexpr int XALIGN = 8;
+    static constexpr bool CODES = true;
     static __device__ __forceinline__ float4 get(const Raw *row, int q) { return row[q]; }
 };
 
@@ -43,6 +61,7 @@ struct Pairs<__half> {
     static constexpr int BYTES = 8;
     static constexpr int LX = kLanesX16;
     static constexpr int XALIGN = 4;
+    static constexpr bool CODES = false;
     static __device__ __forceinline__ float4 get(const Raw *row, int q) {
         const uint2 u = row[q];
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
@@ -57,6 +76,7 @@ struct Pairs<__nv_bfloat16> {
     static constexpr int BYTES = 8;
     static constexpr int LX = kLanesX16;
     static constexpr int XALIGN = 4;
+    static constexpr bool CODES = false;
     static __device__ __forceinline__ float4 get(const Raw *row, int q) {
         const uint2 u = row[q];
         // bf16 -> fp32 is a 16-bit left shift of the bit pattern
@@ -439,15 +459,57 @@ __device__ __forceinline__ void stage_window(const CUtensorMap &tmap, const Tile
     const int wy0 = u.sty0 + ymin - 1;
     s_org[0] = wx0;
     s_org[1] = wy0;
-    const uint32_t bytes = (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
+    // codes: (bxw - 2) 2-byte elements per staged row; pairs: 8-byte elements
+    const uint32_t bytes = Pairs<E>::CODES ? (uint32_t)(a.bxw - 2) * (uint32_t)a.byw * 2u
+                                           : (uint32_t)a.bxw * (uint32_t)a.byw * (uint32_t)(Pairs<E>::BYTES / 2);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    const int xe = wx0 * Pairs<E>::BYTES / 16;   // 8-byte elements
+    const int xe = Pairs<E>::CODES ? wx0 : wx0 * Pairs<E>::BYTES / 16;
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
         "[%5];" ::"r"(smem_addr(win)),
         "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xe), "r"(wy0), "r"(u.img), "r"(bar)
         : "memory");
+}
+
+// Shared-memory layout of the single-level tiled scorers: the window (as
+// scored), then the region of the edge bitmaps (and of the persistent form's
+// partial sums); with angle codes the staged codes also go to that region,
+// 128-byte aligned for the TMA copy, and are expanded before it is used.
+template <typename E>
+__device__ __forceinline__ size_t window_region_bytes(int bxw, int byw) {
+    const size_t b = (size_t)bxw * byw * (Pairs<E>::BYTES / 2);
+    return Pairs<E>::CODES ? (b + 127) & ~(size_t)127 : (b + 15) & ~(size_t)15;
+}
+
+// One angle code as the unit vector it stands for: (cos, sin)(a 2 pi /
+// 32768) = (cospi, sinpi)(a / 16384) on an edge (bit 15), (0, 0) elsewhere.
+__device__ __forceinline__ float2 decode_angle(uint32_t c) {
+    float sn = 0.f, cs = 0.f;
+    if (c & 0x8000u)
+        sincospif((float)(c & 0x7FFFu) * (1.0f / 16384.0f), &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+// Expand the staged codes (byw rows of bxw - 2 codes) into the FP32 pairs
+// window (byw rows of bxw / 2 pairs {wx0, wx1, wy0, wy1}, the last pair of a
+// row zero).  All threads of the CTA; the caller synchronises afterwards.
+__device__ __forceinline__ void expand_codes(const uint32_t *codes, float4 *win, int bxw, int byw) {
+    const int pp = bxw / 2, cpp = pp - 1;
+    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < byw; r += warps) {
+        const uint32_t *cr = codes + (size_t)r * cpp;
+        float4 *wr = win + (size_t)r * pp;
+        for (int j = lane; j < pp; j += 32) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < cpp) {
+                const uint32_t c = cr[j];
+                const float2 u0 = decode_angle(c & 0xFFFFu), u1 = decode_angle(c >> 16);
+                v = make_float4(u0.x, u1.x, u0.y, u1.y);
+            }
+            wr[j] = v;
+        }
+    }
 }
 
 // The per-image work description of a tiled launch (bits and unit unset).
@@ -515,11 +577,13 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
     const UnitPos u = unit_pos<E, TC>(a, unit);
     const int pp = a.bxw / 2;   // window row pitch in pixel pairs
     const uint32_t bar = smem_addr(&mbar);
+    // the region after the window: edge bitmaps (and staged angle codes)
+    unsigned char *region = smem_raw + pad + window_region_bytes<E>(a.bxw, a.byw);
 
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        stage_window<E>(tmap, a, u, win, bar, s_org);
+        stage_window<E>(tmap, a, u, Pairs<E>::CODES ? (const void *)region : (const void *)win, bar, s_org);
     }
     __syncthreads();
     if (!mbar_wait(bar, 0)) {
@@ -527,10 +591,12 @@ __global__ void __launch_bounds__(WARPS * 32) score_tiled_kernel(const __grid_co
             atomicExch(a.err, 1);
         return;
     }
+    if constexpr (Pairs<E>::CODES) {
+        expand_codes(reinterpret_cast<const uint32_t *>(region), const_cast<float4 *>(win), a.bxw, a.byw);
+        __syncthreads();
+    }
     TileWork t = tile_work(a, u.img);
-    // the edge bitmaps follow the window (16-byte aligned)
-    t.bits = reinterpret_cast<uint32_t *>(smem_raw + pad +
-                                          (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15));
+    t.bits = reinterpret_cast<uint32_t *>(region);
     t.unit = unit;
     score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
 }
@@ -605,8 +671,9 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
     const Raw *win = reinterpret_cast<const Raw *>(smem_raw + pad);
-    uint32_t *bits = reinterpret_cast<uint32_t *>(smem_raw + pad +
-                                                  (((size_t)a.bxw * a.byw * (Pairs<E>::BYTES / 2) + 15) & ~(size_t)15));
+    uint32_t *bits = reinterpret_cast<uint32_t *>(smem_raw + pad + window_region_bytes<E>(a.bxw, a.byw));
+    // TMA destination: the window, or (angle codes) the region after it
+    const void *dst = Pairs<E>::CODES ? (const void *)bits : (const void *)win;
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_org[2];
     __shared__ int s_job[4];   // kind (0 end, 1 unit, 2 task), unit, first entry, entries
@@ -629,7 +696,7 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
                 if (un < (unsigned)a.units) {
                     kind = 1;
                     s_job[1] = (int)un;
-                    stage_window<E>(tmap, a, unit_pos<E, TC>(a, (int)un), win, bar, s_org);
+                    stage_window<E>(tmap, a, unit_pos<E, TC>(a, (int)un), dst, bar, s_org);
                 } else {
                     units_left = false;
                 }
@@ -645,7 +712,7 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
                         s_job[1] = tk.x;
                         s_job[2] = tk.y;
                         s_job[3] = tk.z;
-                        stage_window<E>(tmap, a, unit_pos<E, TC>(a, tk.x), win, bar, s_org);
+                        stage_window<E>(tmap, a, unit_pos<E, TC>(a, tk.x), dst, bar, s_org);
                     } else {
                         atomicExch(a.err, 1);
                     }
@@ -665,6 +732,10 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
             if (threadIdx.x == 0)
                 atomicExch(a.err, 1);
             break;
+        }
+        if constexpr (Pairs<E>::CODES) {
+            expand_codes(reinterpret_cast<const uint32_t *>(bits), const_cast<float4 *>(win), a.bxw, a.byw);
+            __syncthreads();
         }
         const UnitPos u = unit_pos<E, TC>(a, s_job[1]);
         TileWork t = tile_work(a, u.img);

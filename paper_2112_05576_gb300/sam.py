@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 SAM_OK, SAM_ERR_ARG, SAM_ERR_NOMEM, SAM_ERR_CUDA, SAM_ERR_TIMEOUT, SAM_ERR_EMPTY_MODEL, SAM_ERR_CAPACITY = range(7)
-FP32, BF16, FP16 = 0, 1, 2
+FP32, BF16, FP16, ANGLE16 = 0, 1, 2, 3
 LAYOUT_PIXEL, LAYOUT_PAIRS = 0, 1
 
 _c_int, _c_float, _c_double, _vp = ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
@@ -306,9 +306,24 @@ def pyramid_down(src, dst, stream=None):
            "sam_pyramid_down")
 
 
-def field_pitch(w, layout):
-    """Row pitch in pixels of a field of width w in the given layout."""
+def field_pitch(w, layout, precision=FP32):
+    """Row pitch in pixels of a field of width w in the given layout (angle
+    codes: 16-byte rows of 8 codes in the pairs layout)."""
+    if precision == ANGLE16:
+        return (w + 7) & ~7 if layout == LAYOUT_PAIRS else w
     return (w + 3) & ~3 if layout == LAYOUT_PAIRS else w
+
+
+def angle_codes(img, low, stream=None, layout=None):
+    """SAM_ANGLE16 field of a device uint8 image (sam_gradient): an (H, pitch)
+    int16 CUDA tensor of 16-bit angle codes, pairs layout (pitch a multiple of
+    8) unless `layout` says otherwise."""
+    import torch
+    h, w = img.shape
+    layout = LAYOUT_PAIRS if layout is None else layout
+    codes = torch.empty((h, field_pitch(w, layout, ANGLE16)), dtype=torch.int16, device=img.device)
+    gradient(img, low, ANGLE16, codes, stream=stream, layout=layout)
+    return codes
 
 
 def gradient(img, low, precision, field, gx=None, gy=None, stream=None, layout=None):
