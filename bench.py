@@ -523,6 +523,65 @@ def run_subpixel(args, sam, torch, dev, stream, model, spec, n_scenes=8):
 
 
 # ---------------------------------------------------------------------------
+# field storage forms on the exhaustive top-level map
+# ---------------------------------------------------------------------------
+
+def run_storage_forms(args, sam, torch, dev, stream, model, batch):
+    """The top level (160 x 128, 45 angles) of each config-2 scene of one batch
+    scored exhaustively with sam_score_map from an FP32 pairs field, a BF16
+    pairs field and an angle-code field (SAM_ANGLE16), every pose scored and
+    with early termination (the persistent scorer); field bytes, time per map
+    and the largest score difference from the FP32 map."""
+    top = LEVELS - 1
+    imgs = []
+    for i in range(batch.shape[0]):
+        lvl = batch[i].contiguous()
+        for _ in range(top):
+            nxt = torch.empty((lvl.shape[0] // 2, lvl.shape[1] // 2), dtype=torch.uint8, device=dev)
+            sam.pyramid_down(lvl, nxt)
+            lvl = nxt
+        imgs.append(lvl)
+    th, tw = imgs[0].shape
+    nth, n = model.num_angles(top), model.num_points(top)
+    fields = {}
+    for name, prec, dt in (("fp32", sam.FP32, torch.float32), ("bf16", sam.BF16, torch.bfloat16),
+                           ("angle16", sam.ANGLE16, torch.int16)):
+        wp = sam.field_pitch(tw, sam.LAYOUT_PAIRS, prec)
+        fl = []
+        for im in imgs:
+            f = torch.empty((th, wp) if prec == sam.ANGLE16 else (th, wp, 2), dtype=dt, device=dev)
+            sam.gradient(im, LOW, prec, f, layout=sam.LAYOUT_PAIRS)
+            fl.append(f)
+        fields[name] = (prec, fl, fl[0].numel() * fl[0].element_size())
+    maps = [torch.empty((nth, th, tw), dtype=torch.float32, device=dev) for _ in imgs]
+    out = {"what": f"sam_score_map of the {tw}x{th} top level, {nth} angles, {n} points, of {len(imgs)} config-2 "
+                   "scenes, one call per scene; error = max |M - M_fp32| over every pose (early termination off)",
+           "pose_points_per_map": nth * th * tw * n}
+    ref = None
+    for early in (0, 1):
+        key = "early_termination" if early else "every_pose"
+        out[key] = {}
+        for name, (prec, fl, fbytes) in fields.items():
+            def call(i, prec=prec, fl=fl, early=early):
+                j = i % len(fl)
+                sam.score_map(model, top, fl[j], tw, th, prec, maps[j], 1, 1, 3, MIN_SCORE, early,
+                              layout=sam.LAYOUT_PAIRS)
+            for i in range(len(imgs)):
+                call(i)
+            ms = _event_ms(torch, dev, stream, call, 4 * len(imgs))
+            res = {"ms_per_map": round(ms, 4), "value": out["pose_points_per_map"] / (ms * 1e-3), "unit": UNIT,
+                   "field_bytes": int(fbytes)}
+            if not early:
+                cur = torch.stack(maps).cpu().numpy()
+                if name == "fp32":
+                    ref = cur
+                res["max_abs_err_vs_fp32"] = float(np.max(np.abs(cur - ref)))
+            out[key][name] = res
+    out["angle16_bound"] = round(2 * math.sin(math.pi / 65536), 7)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # HBM-bound kernels (a) gradient and (b) pyramid on images larger than L2
 # ---------------------------------------------------------------------------
 # Algorithmic bytes: the gradient kernel reads each 8-bit pixel once and
@@ -572,9 +631,11 @@ def run_hbm(args, sam, torch, dev, stream):
         res = {}
         for name, prec, layout, dt, bpx in (("fp32", sam.FP32, sam.LAYOUT_PAIRS, torch.float32, 8),
                                             ("bf16", sam.BF16, sam.LAYOUT_PAIRS, torch.bfloat16, 4),
-                                            ("fp32_pixel", sam.FP32, sam.LAYOUT_PIXEL, torch.float32, 8)):
-            wp = sam.field_pitch(W_, layout)
-            dsts = [torch.empty((H_, wp, 2), dtype=dt, device=dev) for _ in range(n)]
+                                            ("fp32_pixel", sam.FP32, sam.LAYOUT_PIXEL, torch.float32, 8),
+                                            ("angle16", sam.ANGLE16, sam.LAYOUT_PAIRS, torch.int16, 2)):
+            wp = sam.field_pitch(W_, layout, prec)
+            shape = (H_, wp) if prec == sam.ANGLE16 else (H_, wp, 2)
+            dsts = [torch.empty(shape, dtype=dt, device=dev) for _ in range(n)]
             call = (lambda i, dsts=dsts, prec=prec, layout=layout:
                     sam.gradient(srcs[i % n], LOW, prec, dsts[i % n], layout=layout))
             for i in range(3):
@@ -684,18 +745,18 @@ def run_gpu(args):
     pp_step = top_pose_points(model, B)
     value = shard.whole_job_rate(pp_step, args.steps, world, ms)
 
-    # ---- end to end through the public API with host buffers ----
+    # ---- end to end through the public API with host buffers: one library
+    # call per step takes the pinned host batch (its host-to-device copy is
+    # inside the call, on the stream) and returns the poses in host memory ----
     h2d = B * H * W
     d2h = B * (params.max_detections * 32 + 4)
     for i in range(2):
-        x = pinned[i % pools].to(dev, non_blocking=True)
-        sam.detect_batch(model, x, params)
+        sam.detect_batch(model, pinned[i % pools], params)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        x = pinned[i % pools].to(dev, non_blocking=True)
-        sam.detect_batch(model, x, params)     # ends with the device-to-host read of the poses
+        sam.detect_batch(model, pinned[i % pools], params)   # host images in, host poses out
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
@@ -800,6 +861,9 @@ def run_gpu(args):
 
     # ---- the large exhaustive stress slice (chunked scorer) ----
     stress = run_stress(args, sam, torch, dev, stream) if (args.stress and rank == 0) else None
+
+    # ---- field storage forms (FP32 / BF16 pairs / angle codes) on one top-level map ----
+    storage = run_storage_forms(args, sam, torch, dev, stream, model, batches[0]) if rank == 0 else None
 
     # ---- kernels (a) gradient and (b) pyramid against HBM ----
     hbm = run_hbm(args, sam, torch, dev, stream) if (args.hbm and rank == 0) else None
@@ -918,7 +982,9 @@ def run_gpu(args):
                              "steps; the headline counts the exhaustive-equivalent (nominal) pose-points"},
         "single_image_tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, params.precision, 1))),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_ms / args.steps},
+                "ms_per_step": e2e_ms / args.steps,
+                "what": "sam_detect_batch with the batch in pinned host memory (img_on_device = 0): the copy in "
+                        "and the pose readback are inside the library call"},
         "gpu_launches": int(launches),
         "stages": stages,
         "stages_note": "per-stage device times from a second pass of the same steps with stage events on (direct launches); the timed steps replay the captured pipeline graph",
@@ -932,6 +998,7 @@ def run_gpu(args):
         "subpixel": subpixel,
         "quantized": quantized,
         "stress": stress,
+        "storage_forms": storage,
         "hbm": hbm,
         "wall_s": wall,
     }

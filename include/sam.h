@@ -183,14 +183,17 @@ sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride
                       const sam_detect_params *params, void *stream, sam_pose *out, int capacity, int *n_out);
 
 /* Detection (Sec. II, as sam_detect) of `count` images of equal size
- * stored back to back on the device (image i at img + i * image_bytes), all
- * steps batched into one launch per stage.  Poses of image i go to
- * out[i * capacity ...], their count to n_out[i] (host arrays, count *
- * capacity and count entries).  Synchronises `stream`.  Errors as
- * sam_detect. */
+ * stored back to back (image i at img + i * image_bytes, rows `stride`
+ * bytes apart), all steps batched into one launch per stage.  img is a
+ * device pointer if img_on_device != 0, else a host pointer: the images are
+ * then copied into the model's workspace on `stream` inside the call (one
+ * copy when image_bytes == stride * h; page-locked host memory makes it
+ * asynchronous).  Poses of image i go to out[i * capacity ...], their count
+ * to n_out[i] (host arrays, count * capacity and count entries).
+ * Synchronises `stream`.  Errors as sam_detect. */
 sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h,
-                            int stride, const sam_detect_params *params, void *stream, sam_pose *out,
-                            int capacity, int *n_out);
+                            int stride, int img_on_device, const sam_detect_params *params, void *stream,
+                            sam_pose *out, int capacity, int *n_out);
 
 /* ---------------------------------------------------------------------------
  * Batched detection of uneven workloads (Sec. II detection applied to many

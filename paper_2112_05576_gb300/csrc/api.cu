@@ -734,8 +734,8 @@ sam_status sam_detect(sam_model *m, const uint8_t *img, int w, int h, int stride
 }
 
 sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t image_bytes, int w, int h,
-                            int stride, const sam_detect_params *params, void *stream, sam_pose *out,
-                            int capacity, int *n_out) {
+                            int stride, int img_on_device, const sam_detect_params *params, void *stream,
+                            sam_pose *out, int capacity, int *n_out) {
     if (!m || !img || !out || !n_out || count < 1 || capacity < 0 || stride < w ||
         image_bytes < (size_t)stride * (h - 1) + w)
         return SAM_ERR_ARG;
@@ -748,23 +748,32 @@ sam_status sam_detect_batch(sam_model *m, const uint8_t *img, int count, size_t 
     if (s != SAM_OK)
         return s;
     const bool graph = graph_path();
-    const Plan P = make_plan(m, w, h, count, graph, *params);
+    // the workspace holds the level-0 images in graph mode and for host input
+    const bool staged = graph || !img_on_device;
+    const Plan P = make_plan(m, w, h, count, staged, *params);
     s = ensure_workspace(m, P.total);
     if (s != SAM_OK)
         return s;
     cudaStream_t st = (cudaStream_t)stream;
-    if (graph) {
-        // the batch into the workspace's level-0 images, then the captured pipeline
+    if (staged) {
+        // the batch into the workspace's level-0 images (one copy when the
+        // rows of all images are evenly spaced), then the pipeline
+        const cudaMemcpyKind kind = img_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         uint8_t *dst = (uint8_t *)m->ws.base + P.off_img[0];
         if (image_bytes == (size_t)stride * h && P.img_bytes[0] == (size_t)P.pitch[0] * h) {
-            SAM_CU(cudaMemcpy2DAsync(dst, P.pitch[0], img, stride, w, (size_t)h * count, cudaMemcpyDeviceToDevice,
-                                     st));
+            SAM_CU(cudaMemcpy2DAsync(dst, P.pitch[0], img, stride, w, (size_t)h * count, kind, st));
         } else {
             for (int i = 0; i < count; ++i)
                 SAM_CU(cudaMemcpy2DAsync(dst + (size_t)i * P.img_bytes[0], P.pitch[0], img + (size_t)i * image_bytes,
-                                         stride, w, h, cudaMemcpyDeviceToDevice, st));
+                                         stride, w, h, kind, st));
         }
-        s = run_graph(m, P, *params, st);
+        if (graph) {
+            s = run_graph(m, P, *params, st);
+            if (s != SAM_OK)
+                return s;
+            return read_results(m, P, *params, st, out, capacity, n_out);
+        }
+        s = run_pipeline(m, P, dst, P.pitch[0], P.img_bytes[0], *params, st);
         if (s != SAM_OK)
             return s;
         return read_results(m, P, *params, st, out, capacity, n_out);

@@ -66,7 +66,7 @@ SIGNATURES = {
     "sam_model_child_shift": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p]),
     "sam_detect": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _c_int, ctypes.POINTER(DetectParams), _vp,
                             ctypes.POINTER(Pose), _c_int, ctypes.POINTER(_c_int)]),
-    "sam_detect_batch": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int,
+    "sam_detect_batch": (_c_int, [_vp, _vp, _c_int, ctypes.c_size_t, _c_int, _c_int, _c_int, _c_int,
                                   ctypes.POINTER(DetectParams), _vp, ctypes.POINTER(Pose), _c_int,
                                   ctypes.POINTER(_c_int)]),
     "sam_pyramid_down": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
@@ -282,17 +282,29 @@ def _has_cuda():
 
 
 def detect_batch(model: Model, images, params: Optional[DetectParams] = None, stream=None, capacity=None):
-    """sam_detect_batch (Sec. II, per image): detect in a (N, H, W) torch.uint8
-    CUDA tensor; returns one pose list per image."""
+    """sam_detect_batch (Sec. II, per image): detect in a (N, H, W) uint8 batch,
+    a torch CUDA tensor or a host torch tensor / numpy array (copied by the
+    library; pinned host memory makes the copy asynchronous); returns one pose
+    list per image."""
     params = params or default_detect_params()
     cap = capacity or params.max_detections
-    N, H, W = images.shape
-    if images.stride(2) != 1 or images.stride(1) < W:
-        raise ValueError("rows must be contiguous")
+    if isinstance(images, np.ndarray):
+        keep = np.ascontiguousarray(images, dtype=np.uint8)
+        N, H, W = keep.shape
+        ptr, on_dev, strides = keep.ctypes.data_as(_vp), 0, (H * W, W)
+    else:
+        if images.dtype.__str__() != "torch.uint8" or images.dim() != 3:
+            raise ValueError("images: a (N, H, W) uint8 tensor")
+        N, H, W = images.shape
+        if images.stride(2) != 1 or images.stride(1) < W:
+            raise ValueError("rows must be contiguous")
+        keep, ptr, on_dev, strides = images, _ptr(images), 1 if images.is_cuda else 0, (images.stride(0),
+                                                                                          images.stride(1))
     out = (Pose * (cap * N))()
     nout = (ctypes.c_int * N)()
-    _check(lib().sam_detect_batch(model.handle, _ptr(images), N, images.stride(0), W, H, images.stride(1),
-                                  ctypes.byref(params), _stream(stream), out, cap, nout), "sam_detect_batch")
+    _check(lib().sam_detect_batch(model.handle, ptr, N, strides[0], W, H, strides[1], on_dev, ctypes.byref(params),
+                                  _stream(stream), out, cap, nout), "sam_detect_batch")
+    del keep
     return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(N)]
 
 

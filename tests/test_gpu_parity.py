@@ -250,6 +250,18 @@ def test_detect_batch_equals_single():
     for i, sc in enumerate(imgs):
         single = sam.detect(m, _dev(sc), p)
         assert got[i] == single
+    # host input (the library copies the batch in): numpy, pinned torch, and
+    # a strided host view, with graph mode on and off
+    host = np.stack(imgs)
+    wide = np.zeros((3, 480, 700), np.uint8)
+    wide[:, :, :640] = host
+    for graph in (1, 0):
+        sam.set_graph_mode(graph)
+        assert sam.detect_batch(m, host, p) == got
+        assert sam.detect_batch(m, torch.from_numpy(host).pin_memory(), p) == got
+        assert sam.detect_batch(m, torch.from_numpy(wide)[:, :, :640], p) == got
+        assert sam.detect_batch(m, batch, p) == got
+    sam.set_graph_mode(1)
 
 
 def test_detect_edge_cases():
