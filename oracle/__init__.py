@@ -45,4 +45,11 @@ from .oracle import (  # noqa: F401
     search_angle_fields,
     project_affine,
     similarity,
+    scale_grid,
+    scaled_points,
+    score_map_scaled,
+    candidates_scaled,
+    child_shift_scaled,
+    refine_level_scaled,
+    detect_scaled,
 )

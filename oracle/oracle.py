@@ -91,6 +91,19 @@ def _L():
         lib.or_project_affine.argtypes = [_i32p, _i32p, _i32p, _i32p, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl,
                                           _i32p, _i32p, _f64p, _f64p]
         lib.or_project_affine.restype = _c_int
+        lib.or_scaled_points.argtypes = [_i32p, _i32p, _i32p, _i32p, _c_int, _c_int, _c_dbl, _c_dbl,
+                                         _i32p, _i32p, _f64p, _f64p]
+        lib.or_scaled_points.restype = _c_int
+        lib.or_score_map_scaled.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _f64p, _c_int,
+                                            _c_int, _c_dbl, _c_int, _c_int, _f64p]
+        lib.or_candidates_scaled.argtypes = [_f64p, _c_int, _c_int, _c_int, _c_int, _c_dbl, _c_int, _i32p, _i32p,
+                                             _i32p, _i32p, _f64p]
+        lib.or_candidates_scaled.restype = _c_int
+        lib.or_child_shift_scaled.argtypes = [_c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32)]
+        lib.or_refine_level_scaled.argtypes = [_f64p, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _c_int, _f64p,
+                                               _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_int, _c_int, _c_dbl, _c_int,
+                                               _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p]
         _lib = lib
     return _lib
 
@@ -545,3 +558,103 @@ def similarity(scale, theta_deg):
     th = math.radians(theta_deg)
     c, s = math.cos(th), math.sin(th)
     return np.array([[scale * c, -scale * s], [scale * s, scale * c]])
+
+
+# ---------------------------------------------------------------------------
+# scaled poses: A = s R(theta) over a grid of scales (generalised Eq. (2))
+# ---------------------------------------------------------------------------
+
+def scale_grid(scale_min, scale_step, n_scales):
+    """s_j = scale_min + j scale_step, j < n_scales (the same grid at every level)."""
+    return [float(scale_min) + j * float(scale_step) for j in range(int(n_scales))]
+
+
+def scaled_points(pts, k, dtheta_deg, scale):
+    """Offsets and directions of the model points for scale `scale` and angle
+    index k: project_affine with A = scale R(theta_k), the angle computed as
+    in rotate_points."""
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    n = len(tx)
+    ox, oy = np.empty(n, np.int32), np.empty(n, np.int32)
+    px, py = np.empty(n, np.float64), np.empty(n, np.float64)
+    if not _L().or_scaled_points(tx, ty, gx, gy, n, int(k), float(dtheta_deg), float(scale), ox, oy, px, py):
+        raise ValueError("scale 0")
+    return ox, oy, px, py
+
+
+def score_map_scaled(field, pts, scales, ntheta, dtheta_deg, nbhd=3, polarity=0):
+    """Exhaustive step-1 map M[j, k, y, x] over scales, angles and translations."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = (_i32(a) for a in pts)
+    sc = _f64(scales)
+    out = np.empty((len(sc), ntheta, h, w), dtype=np.float64)
+    _L().or_score_map_scaled(field, w, h, tx, ty, gx, gy, len(tx), sc, len(sc), int(ntheta), float(dtheta_deg),
+                             int(nbhd), int(polarity), out)
+    return out
+
+
+def candidates_scaled(smap, min_score, K):
+    """Top-K strict local maxima over (scale, angle circular, y, x) with M >= min_score.
+
+    Returns arrays (j, k, gy, gx, score) sorted best first."""
+    smap = _f64(smap)
+    ns, nth, gh, gw = smap.shape
+    cj, ck, cy, cx = (np.empty(K, np.int32) for _ in range(4))
+    cs = np.empty(K, np.float64)
+    n = _L().or_candidates_scaled(smap, ns, nth, gh, gw, float(min_score), int(K), cj, ck, cy, cx, cs)
+    return cj[:n].copy(), ck[:n].copy(), cy[:n].copy(), cx[:n].copy(), cs[:n].copy()
+
+
+def child_shift_scaled(model, level, k_parent, scale):
+    """child_shift for a parent of scale `scale`."""
+    dx, dy = _ref_shift_d(model, level)
+    sx, sy = ctypes.c_int32(), ctypes.c_int32()
+    _L().or_child_shift_scaled(int(k_parent), float(model.dtheta(level + 1)), float(scale), dx, dy,
+                               ctypes.byref(sx), ctypes.byref(sy))
+    return sx.value, sy.value
+
+
+def refine_level_scaled(model, level, field, scales, xs, ys, js, ks, nbhd, polarity, min_score):
+    """Best of the up to 81 level-`level` poses (x, y, angle, scale +- 1) around each level+1 parent."""
+    field = _f64(field)
+    h, w = field.shape[:2]
+    tx, ty, gx, gy = model.points[level]
+    n = len(xs)
+    ox, oy, oj, ok = (np.empty(n, np.int32) for _ in range(4))
+    os_ = np.empty(n, np.float64)
+    dx, dy = _ref_shift_d(model, level)
+    sc = _f64(scales)
+    _L().or_refine_level_scaled(field, w, h, tx, ty, gx, gy, len(tx), sc, len(sc), model.ntheta(level),
+                                float(model.dtheta(level)), dx, dy, int(nbhd), int(polarity), float(min_score), n,
+                                _i32(xs), _i32(ys), _i32(js), _i32(ks), ox, oy, oj, ok, os_)
+    return ox, oy, oj, ok, os_
+
+
+def detect_scaled(model: OracleModel, img, params: DetectParams, scales, trace=None):
+    """Full detection over scales, angles and translations, in Sec. II order
+    (edge extraction, pyramid, exhaustive top level, refinement down the
+    pyramid with the scale searched +- 1 too, NMS keyed by (scale, angle, y,
+    x)).  Returns (x, y, theta_deg, score, k, j) at level 0, best first."""
+    L = model.levels
+    fields = search_fields(img, L, model.low)
+    top = L - 1
+    smap = score_map_scaled(fields[top], model.points[top], scales, model.ntheta(top), model.dtheta(top),
+                            params.nbhd, model.polarity)
+    cj, ck, cy, cx, cs = candidates_scaled(smap, params.min_score, params.top_k)
+    xs, ys, js, ks, ss = cx, cy, cj, ck, cs
+    if trace is not None:
+        trace["fields"] = fields
+        trace["map"] = smap
+        trace["cand"] = (xs.copy(), ys.copy(), js.copy(), ks.copy(), ss.copy())
+    for lvl in range(top - 1, -1, -1):
+        alive = np.isfinite(ss)
+        xs, ys, js, ks, ss = xs[alive], ys[alive], js[alive], ks[alive], ss[alive]
+        xs, ys, js, ks, ss = refine_level_scaled(model, lvl, fields[lvl], scales, xs, ys, js, ks, params.nbhd,
+                                                 model.polarity, params.min_score)
+    w0, h0 = model.sizes[0]
+    H, W = img.shape
+    nth0 = model.ntheta(0)
+    keep = nms(xs, ys, js * nth0 + ks, ss, W, H, min(w0, h0), params.max_detections)
+    return [(int(xs[i]), int(ys[i]), float(ks[i]) * model.angle_step_deg, float(ss[i]), int(ks[i]), int(js[i]))
+            for i in keep]

@@ -871,3 +871,200 @@ int or_project_affine(const int32_t *tx, const int32_t *ty, const int32_t *gx, c
     }
     return 1;
 }
+
+/* ======================================================================== */
+/* Scaled poses: Eq. (2) with R(theta) replaced by A = s R(theta) (the      */
+/* paper notes that other kinds of projection could be implemented).  The   */
+/* search runs over a grid of scales s_j (j < nscales) as well as angles    */
+/* theta_k and translations; the scale grid is the same at every pyramid    */
+/* level (a scale is a ratio of sizes).  Readings, listed in the design     */
+/* notes: a pose (x, y, k, j) is keyed ((j nth + k) H + y) W + x in every   */
+/* selection; candidates are strict local maxima over the up to 80          */
+/* neighbours in (j, theta circular, y, x), j not circular; the descent     */
+/* searches j - 1 .. j + 1 (clipped to the grid) as well as x, y and theta, */
+/* up to 81 poses per level; the child shift turns and scales d by A.       */
+/* ======================================================================== */
+
+/* The model points projected for scale `scale` and angle index k (angle as
+ * in or_rotate_points): A = [[s c, -(s sn)], [s sn, s c]].                 */
+int or_scaled_points(const int32_t *tx, const int32_t *ty, const int32_t *gx, const int32_t *gy, int n, int k,
+                     double dtheta_deg, double scale, int32_t *ox, int32_t *oy, double *px, double *py)
+{
+    double th = ((double)k * dtheta_deg) * OR_PI / 180.0;
+    double c = cos(th), sn = sin(th);
+    return or_project_affine(tx, ty, gx, gy, n, scale * c, -(scale * sn), scale * sn, scale * c, ox, oy, px, py);
+}
+
+/* Exhaustive map over scales, angles and step-1 translations (the three
+ * nested loops of Sec. II with a scale loop around them):
+ * out[((j * nth + k) * h + y) * w + x] = M(x, y, theta_k, s_j).            */
+void or_score_map_scaled(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                         const int32_t *gx, const int32_t *gy, int n, const double *scales, int nscales, int nth,
+                         double dtheta_deg, int nbhd, int polarity, double *out)
+{
+    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *px = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *py = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int j = 0; j < nscales; ++j) {
+        for (int k = 0; k < nth; ++k) {
+            or_scaled_points(tx, ty, gx, gy, n, k, dtheta_deg, scales[j], ox, oy, px, py);
+            for (int y = 0; y < h; ++y)
+                for (int x = 0; x < w; ++x)
+                    out[(((size_t)j * nth + k) * h + y) * w + x] =
+                        or_score_pose(field, w, h, ox, oy, px, py, n, x, y, nbhd, polarity);
+        }
+    }
+    free(ox);
+    free(oy);
+    free(px);
+    free(py);
+}
+
+/* Candidates over (scale, angle, y, x): poses with M >= min_score that beat
+ * each of their up to 80 neighbours (j +- 1 inside the grid, theta
+ * circular, y and x clipped), the K best by the total order.  Returns the
+ * number written (<= K).                                                   */
+int or_candidates_scaled(const double *map, int ns, int nth, int gh, int gw, double min_score, int K,
+                         int32_t *cj, int32_t *ck, int32_t *cy, int32_t *cx, double *cs)
+{
+    int cap = 1024, cnt = 0;
+    double *sc = (double *)malloc(sizeof(double) * cap);
+    long *key = (long *)malloc(sizeof(long) * cap);
+    for (int j = 0; j < ns; ++j) {
+        for (int k = 0; k < nth; ++k) {
+            for (int y = 0; y < gh; ++y) {
+                for (int x = 0; x < gw; ++x) {
+                    long kp = (((long)j * nth + k) * gh + y) * gw + x;
+                    double s = map[kp];
+                    if (!(s >= min_score))
+                        continue;
+                    int ok = 1;
+                    for (int dj = -1; dj <= 1 && ok; ++dj) {
+                        int j2 = j + dj;
+                        if (j2 < 0 || j2 >= ns)
+                            continue;
+                        for (int dk = -1; dk <= 1 && ok; ++dk) {
+                            if (dk != 0 && nth == 1)
+                                continue;
+                            int k2 = ((k + dk) % nth + nth) % nth;
+                            for (int dy = -1; dy <= 1 && ok; ++dy) {
+                                for (int dx = -1; dx <= 1 && ok; ++dx) {
+                                    int y2 = y + dy, x2 = x + dx;
+                                    if (y2 < 0 || x2 < 0 || y2 >= gh || x2 >= gw)
+                                        continue;
+                                    long kq = (((long)j2 * nth + k2) * gh + y2) * gw + x2;
+                                    if (kq == kp)
+                                        continue;
+                                    if (!or_beats(s, kp, map[kq], kq))
+                                        ok = 0;
+                                }
+                            }
+                        }
+                    }
+                    if (!ok)
+                        continue;
+                    if (cnt == cap) {
+                        cap *= 2;
+                        sc = (double *)realloc(sc, sizeof(double) * cap);
+                        key = (long *)realloc(key, sizeof(long) * cap);
+                    }
+                    sc[cnt] = s;
+                    key[cnt] = kp;
+                    ++cnt;
+                }
+            }
+        }
+    }
+    int *idx = (int *)malloc(sizeof(int) * (size_t)(cnt > 0 ? cnt : 1));
+    for (int i = 0; i < cnt; ++i)
+        idx[i] = i;
+    or_sort_scores = sc;
+    or_sort_keys = key;
+    qsort(idx, (size_t)cnt, sizeof(int), or_cmp_idx);
+    int nout = cnt < K ? cnt : K;
+    for (int i = 0; i < nout; ++i) {
+        long kp = key[idx[i]];
+        cx[i] = (int32_t)(kp % gw);
+        cy[i] = (int32_t)((kp / gw) % gh);
+        ck[i] = (int32_t)((kp / ((long)gw * gh)) % nth);
+        cj[i] = (int32_t)(kp / ((long)gw * gh * nth));
+        cs[i] = sc[idx[i]];
+    }
+    free(idx);
+    free(sc);
+    free(key);
+    return nout;
+}
+
+/* Coarse-to-fine shift of a scaled parent (as or_child_shift, with d turned
+ * and scaled by the parent's A = s R(theta)).                              */
+void or_child_shift_scaled(int k_parent, double dtheta_parent_deg, double scale, double dx, double dy, int32_t *sx,
+                           int32_t *sy)
+{
+    double th = ((double)k_parent * dtheta_parent_deg) * OR_PI / 180.0;
+    double c = cos(th), sn = sin(th);
+    double a11 = scale * c, a12 = -(scale * sn), a21 = scale * sn, a22 = scale * c;
+    *sx = (int32_t)floor(0.5 - (a11 * dx + a12 * dy) + 0.5);
+    *sy = (int32_t)floor(0.5 - (a21 * dx + a22 * dy) + 0.5);
+}
+
+/* One refinement level with scales: for each level-(l+1) parent (x', y', k',
+ * j') the level-l poses x, y in centre +- 1, k in 2k' + {-1, 0, 1} (mod nth)
+ * and j in j' + {-1, 0, 1} inside the scale grid, centre = 2 (x', y') +
+ * shift(k', s_j'); the best by the total order; -inf below min_score.      */
+void or_refine_level_scaled(const double *field, int w, int h, const int32_t *tx, const int32_t *ty,
+                            const int32_t *gx, const int32_t *gy, int n, const double *scales, int ns, int nth,
+                            double dtheta_deg, double dx, double dy, int nbhd, int polarity, double min_score,
+                            int ncand, const int32_t *in_x, const int32_t *in_y, const int32_t *in_j,
+                            const int32_t *in_k, int32_t *out_x, int32_t *out_y, int32_t *out_j, int32_t *out_k,
+                            double *out_s)
+{
+    int32_t *ox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *oy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *px = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *py = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int c = 0; c < ncand; ++c) {
+        int32_t sx, sy;
+        or_child_shift_scaled(in_k[c], 2.0 * dtheta_deg, scales[in_j[c]], dx, dy, &sx, &sy);
+        int cxp = 2 * in_x[c] + sx, cyp = 2 * in_y[c] + sy;
+        double best = -INFINITY;
+        long bkey = 0;
+        int bx = 0, by = 0, bk = 0, bj = 0;
+        for (int dj = -1; dj <= 1; ++dj) {
+            int j = in_j[c] + dj;
+            if (j < 0 || j >= ns)
+                continue;
+            for (int dk = -1; dk <= 1; ++dk) {
+                int k = ((2 * in_k[c] + dk) % nth + nth) % nth;
+                or_scaled_points(tx, ty, gx, gy, n, k, dtheta_deg, scales[j], ox, oy, px, py);
+                for (int ddy = -1; ddy <= 1; ++ddy) {
+                    for (int ddx = -1; ddx <= 1; ++ddx) {
+                        int x = cxp + ddx, y = cyp + ddy;
+                        if (x < 0 || y < 0 || x >= w || y >= h)
+                            continue;
+                        double s = or_score_pose(field, w, h, ox, oy, px, py, n, x, y, nbhd, polarity);
+                        long key = (((long)j * nth + k) * h + y) * w + x;
+                        if (best == -INFINITY || or_beats(s, key, best, bkey)) {
+                            best = s;
+                            bkey = key;
+                            bx = x;
+                            by = y;
+                            bk = k;
+                            bj = j;
+                        }
+                    }
+                }
+            }
+        }
+        out_x[c] = bx;
+        out_y[c] = by;
+        out_k[c] = bk;
+        out_j[c] = bj;
+        out_s[c] = (best >= min_score) ? best : -INFINITY;
+    }
+    free(ox);
+    free(oy);
+    free(px);
+    free(py);
+}
