@@ -109,12 +109,14 @@ typedef struct {
 } sam_detect_params;
 
 /* One detection at level 0: reference point (x, y) in pixels, rotation in
- * degrees, score M of Eq. (1) (FP32).  angle_index is k at level 0. */
+ * degrees, score M of Eq. (1) (FP32).  angle_index is k at level 0;
+ * scale_index is j of a scaled model's grid (scale sam_model_scale(m, j)),
+ * 0 for a rigid model. */
 typedef struct {
     float x, y, theta_deg, score;
     int angle_index;
     int level0_x, level0_y;
-    int reserved;
+    int scale_index;
 } sam_pose;
 
 const char *sam_status_str(sam_status s);
@@ -148,10 +150,37 @@ sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const
                             sam_model **out);
 void sam_free_model(sam_model *m);
 
+/* A scaled model (Sec. II, after Eq. (2): the paper notes that other types
+ * of projection could be implemented; here Eq. (2) with R(theta) replaced by
+ * A = s R(theta)).  As sam_create_model, plus a grid of scales
+ * s_j = scale_min + j * scale_step, j < n_scales (1 <= n_scales <= 64,
+ * 0 < s_j <= 16), the same at every pyramid level.  Per level and table
+ * K = j * num_angles + k the projection of each point is the integer offset
+ * floor(A t + 1/2) (A = [[s c, -(s sn)], [s sn, s c]] evaluated in FP64 as
+ * written) and the unit direction R(theta) g/|g|.  Score maps of a scaled
+ * model have num_scales x num_angles planes (plane K); detection searches
+ * the scales too (candidates are strict local maxima over the up to 80
+ * neighbours in (scale, angle circular, y, x), the scale axis not circular;
+ * the descent searches scale j +- 1 inside the grid with x, y and angle, up
+ * to 81 poses per level; the child shift turns and scales the reference
+ * offset by the parent's A) and returns each pose's scale_index.  Scaled
+ * models are not served by the batched plan (sam_multi_create), the
+ * continuous-pose score and refinement or the sub-pixel fit (SAM_ERR_ARG).
+ * n_scales = 1 with scale_min = 1 gives the rigid model.
+ * Errors: SAM_ERR_ARG, SAM_ERR_EMPTY_MODEL, SAM_ERR_NOMEM. */
+sam_status sam_create_model_scaled(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params *params,
+                                   double scale_min, double scale_step, int n_scales, sam_model **out);
+/* The scale grid (host only; the paper has no counterpart): number of
+ * scales (1 for a rigid model, 0 for NULL) and s_j (0.0 for j out of range). */
+int sam_model_num_scales(const sam_model *m);
+double sam_model_scale(const sam_model *m, int j);
+
 /* Model inspection (host only, no device work; the paper has no
  * counterpart).  The int getters return 0 for a NULL model or a level out of
  * range; sam_model_template_size returns 1 and writes the level's template
- * size (w, h; either pointer may be NULL) or returns 0. */
+ * size (w, h; either pointer may be NULL) or returns 0.  num_angles counts
+ * the angles of one scale; the table index k of the calls below runs over
+ * num_scales x num_angles tables (k = scale j * num_angles + angle). */
 int sam_model_levels(const sam_model *m);
 int sam_model_num_points(const sam_model *m, int level);
 int sam_model_num_angles(const sam_model *m, int level);
@@ -174,6 +203,8 @@ sam_status sam_model_child_shift(const sam_model *m, int level, int k_parent, in
  *                  img_on_device != 0, else a host pointer.
  *   out            host array of `capacity` poses, best first.
  *   n_out          host int, receives the number of poses written.
+ * With a scaled model (sam_create_model_scaled) the search also runs over
+ * its scales and each pose carries its scale_index.
  * The model keeps an internal device workspace that grows to the largest
  * image seen: calls on one model must not overlap (serialise them on one
  * stream or host thread).  Synchronises `stream` before returning.
@@ -286,7 +317,9 @@ sam_status sam_gradient(const uint8_t *img, int w, int h, int stride, int low, i
 /* Exhaustive score map of one model level (Eq. (1) with the neighbouring
  * search, Eq. (2) projection, Sec. II three nested loops):
  *   map[(k * gh + gyi) * gw + gxi] = M(gxi * step_x, gyi * step_y, theta_k)
- * for k < num_angles(level), gh = ceil(h/step_y), gw = ceil(w/step_x).
+ * for k < num_angles(level), gh = ceil(h/step_y), gw = ceil(w/step_x); for
+ * a scaled model k runs over the num_scales x num_angles tables (plane
+ * j * num_angles + k: scale j, angle k).
  *   field   device w_hat field of the search image at that level (layout and
  *           precision as produced by sam_gradient).
  *   map     device float array of num_angles * gh * gw.
@@ -402,6 +435,19 @@ sam_status sam_selftest_task_wait_timeout(int limit_us, double *waited_ms);
  * detection; the paper has no counterpart): returns 1 and clears it if any
  * wait gave up since the last call, else 0 (synchronises the device). */
 int sam_take_device_error(void);
+
+/* Candidates of a scaled model's map [n_scales * n_angles][gh][gw] (plane
+ * j * n_angles + k for scale j, angle k; generalises sam_candidates, the
+ * paper has no scale axis): poses with score >= min_score that beat each
+ * of their up to 80 neighbours in (scale j +- 1 inside the grid, angle
+ * circular, y, x), the best K (1 <= K <= 1024) by the same order, written as
+ * (plane, y, x) triples to out_kyx.  Scratch: device buffer of
+ * sam_candidates_scaled_scratch_bytes(n_scales, n_angles, gh, gw) bytes.
+ * n_scales = 1 is sam_candidates.  Stream-ordered, no synchronisation.
+ * Errors: SAM_ERR_ARG, SAM_ERR_CUDA. */
+size_t sam_candidates_scaled_scratch_bytes(int n_scales, int n_angles, int gh, int gw);
+sam_status sam_candidates_scaled(const float *map, int n_scales, int n_angles, int gh, int gw, float min_score, int K,
+                                 int32_t *out_kyx, float *out_s, int *count, void *scratch, void *stream);
 
 /* Candidate extraction from a score map [nth][gh][gw] (Sec. II returns the
  * best pose; for several instances this library reads it as the local

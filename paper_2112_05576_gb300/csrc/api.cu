@@ -163,7 +163,7 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
     P.off_map = off;
     off += al(P.map_img * 4 * count);
     P.off_scratch = off;
-    off += al(candidates_scratch_bytes_batch(P.nth, P.gh, P.gw, count));
+    off += al(candidates_scratch_bytes_batch(P.nth, P.gh, P.gw, count, m->nscales));
     P.off_rescore = off;
     if (p.precision != SAM_FP32)
         off += al(rescore_scratch_bytes(P.map_img * count));
@@ -299,7 +299,7 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     int *ccount = (int *)(ws + P.off_ccount);
     prof_begin(3, st);
     SAM_CU(launch_candidates(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
-                             ws + P.off_scratch, 0, count, st));
+                             ws + P.off_scratch, 0, count, st, m->nscales));
     prof_end(3, st);
     RefineArgs ra;
     memset(&ra, 0, sizeof(ra));
@@ -321,6 +321,7 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     ra.cand_count = ccount;
     ra.refined = (float4 *)(ws + P.off_refined);
     ra.count = count;
+    ra.nscales = m->nscales;
     prof_begin(4, st);
     SAM_CU(launch_refine(m, ra, st));
     prof_end(4, st);
@@ -333,6 +334,7 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     na.min_side = std::min(m->lv[0].tw, m->lv[0].th);
     na.max_out = p.max_detections;
     na.angle_step = m->p.angle_step_deg;
+    na.nang0 = m->lv[0].nangles;
     na.out = (sam_pose *)(ws + P.off_out);
     na.n_out = (int *)(ws + P.off_nout);
     na.count = count;
@@ -619,6 +621,31 @@ sam_status sam_create_model(const uint8_t *tmpl, int w, int h, int stride, const
     return SAM_OK;
 }
 
+sam_status sam_create_model_scaled(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params *params,
+                                   double scale_min, double scale_step, int n_scales, sam_model **out) {
+    if (!out || !params)
+        return SAM_ERR_ARG;
+    *out = nullptr;
+    if (params->low > 1024 || params->high > 1024)
+        return SAM_ERR_ARG;
+    sam_model *m = new (std::nothrow) sam_model();
+    if (!m)
+        return SAM_ERR_NOMEM;
+    const sam_status s = build_model(tmpl, w, h, stride, *params, m, n_scales, scale_min, scale_step);
+    if (s != SAM_OK) {
+        delete m;
+        return s;
+    }
+    *out = m;
+    return SAM_OK;
+}
+
+int sam_model_num_scales(const sam_model *m) { return m ? m->nscales : 0; }
+
+double sam_model_scale(const sam_model *m, int j) {
+    return (m && j >= 0 && j < m->nscales) ? m->scale_min + j * m->scale_step : 0.0;
+}
+
 void sam_free_model(sam_model *m) {
     if (!m)
         return;
@@ -642,7 +669,7 @@ int sam_model_num_points(const sam_model *m, int level) {
 }
 
 int sam_model_num_angles(const sam_model *m, int level) {
-    return (m && level >= 0 && level < m->levels) ? m->lv[level].ntheta : 0;
+    return (m && level >= 0 && level < m->levels) ? m->lv[level].nangles : 0;
 }
 
 int sam_model_template_size(const sam_model *m, int level, int *w, int *h) {
@@ -1089,6 +1116,23 @@ int sam_profile_read(float *ms, int *calls, int n) {
         g_prof.calls[s] = 0;
     }
     return m;
+}
+
+size_t sam_candidates_scaled_scratch_bytes(int n_scales, int n_angles, int gh, int gw) {
+    if (n_scales < 1 || n_angles < 1 || gh < 1 || gw < 1)
+        return 0;
+    return candidates_scratch_bytes(n_scales * n_angles, gh, gw, n_scales);
+}
+
+sam_status sam_candidates_scaled(const float *map, int n_scales, int n_angles, int gh, int gw, float min_score, int K,
+                                 int32_t *out_kyx, float *out_s, int *count, void *scratch, void *stream) {
+    if (!map || !out_kyx || !out_s || !count || !scratch || n_scales < 1 || n_angles < 1 || gh < 1 || gw < 1 ||
+        K < 1 || K > kMaxTopK || (long long)n_scales * n_angles > (1LL << 30))
+        return SAM_ERR_ARG;
+    return launch_candidates(map, 0, n_scales * n_angles, gh, gw, min_score, K, out_kyx, out_s, count, scratch, 0, 1,
+                             (cudaStream_t)stream, n_scales) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
 }
 
 sam_status sam_candidates(const float *map, int nth, int gh, int gw, float min_score, int K, int32_t *out_kyx,

@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(kBilThreads) refine_gn_kernel(const __grid_con
 }
 
 sam_status make_args(sam_model *m, int level, const sam_field_ref *fields, int n_fields, BilArgs *a) {
-    if (!m || level < 0 || level >= m->levels || !fields || n_fields < 1 || n_fields > SAM_MAX_BILINEAR_FIELDS)
+    // the continuous pose (x, y, theta) is rigid: scaled models are not served
+    if (!m || level < 0 || level >= m->levels || !fields || n_fields < 1 || n_fields > SAM_MAX_BILINEAR_FIELDS ||
+        m->nscales != 1 || m->scale_min != 1.0)
         return SAM_ERR_ARG;
     for (int i = 0; i < n_fields; ++i) {
         const sam_field_ref &f = fields[i];

@@ -35,33 +35,43 @@ __device__ __forceinline__ bool beats(float sa, unsigned long long ka, float sb,
 // ---------------------------------------------------------------------------
 
 // Whether map entry idx is a strict local maximum >= min_score over its up to
-// 26 neighbours in (theta circular, y, x).
+// 26 neighbours in (theta circular, y, x); with ns > 1 scales the map's nth
+// planes are ns blocks of nth / ns angles (plane j * nang + k for scale j,
+// angle k) and the neighbours, up to 80, also span scales j - 1 .. j + 1
+// inside the grid (not circular).
 __device__ __forceinline__ bool is_candidate(const float *__restrict__ map, int nth, int gh, int gw, float min_score,
-                                             size_t idx) {
+                                             size_t idx, int ns) {
     const float s = map[idx];
     if (!(s >= min_score))
         return false;
     const size_t plane = (size_t)gh * gw;
-    const int k = (int)(idx / plane);
-    const int r = (int)(idx - (size_t)k * plane);
+    const int kk = (int)(idx / plane);
+    const int r = (int)(idx - (size_t)kk * plane);
     const int y = r / gw, x = r - y * gw;
-    for (int dk = -1; dk <= 1; ++dk) {
-        if (dk != 0 && nth == 1)
+    const int nang = nth / ns;
+    const int js = kk / nang, k = kk - js * nang;
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int j2 = js + dj;
+        if (j2 < 0 || j2 >= ns)
             continue;
-        const int k2 = (k + dk + nth) % nth;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int y2 = y + dy;
-            if (y2 < 0 || y2 >= gh)
+        for (int dk = -1; dk <= 1; ++dk) {
+            if (dk != 0 && nang == 1)
                 continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int x2 = x + dx;
-                if (x2 < 0 || x2 >= gw)
+            const int k2 = j2 * nang + (k + dk + nang) % nang;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y2 = y + dy;
+                if (y2 < 0 || y2 >= gh)
                     continue;
-                const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
-                if (j == idx)
-                    continue;
-                if (!beats(s, idx, map[j], j))
-                    return false;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x2 = x + dx;
+                    if (x2 < 0 || x2 >= gw)
+                        continue;
+                    const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
+                    if (j == idx)
+                        continue;
+                    if (!beats(s, idx, map[j], j))
+                        return false;
+                }
             }
         }
     }
@@ -83,13 +93,14 @@ __device__ __forceinline__ void push_candidate(const float *map, size_t idx, Can
 // local maximum at or above min_score) of `count` equal maps, image
 // blockIdx.y; appended to the image's list by atomic counter.
 __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
-                                 float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt) {
+                                 float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt,
+                                 int ns) {
     const int img = blockIdx.y;
     map += (size_t)img * map_img;
     const size_t total = (size_t)nth * gh * gw;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x)
-        if (is_candidate(map, nth, gh, gw, min_score, idx))
+        if (is_candidate(map, nth, gh, gw, min_score, idx, ns))
             push_candidate(map, idx, cand + (size_t)img * cap, cap, cnt + img);
 }
 
@@ -99,7 +110,7 @@ __global__ void local_max_jobs_kernel(const CandJob *__restrict__ jobs, float mi
     const size_t total = (size_t)j.nth * j.gh * j.gw;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x)
-        if (is_candidate(j.map, j.nth, j.gh, j.gw, min_score, idx))
+        if (is_candidate(j.map, j.nth, j.gh, j.gw, min_score, idx, j.ns))
             push_candidate(j.map, idx, j.cand, j.cap, j.cnt);
 }
 
@@ -231,114 +242,125 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ns = j.nscales;
     for (int l = j.top - 1; l >= 0; --l) {
         const LevelDev &L = lv[l];
-        const int2 sh = lv[l + 1].shift[state[2]];
+        // parent table Kp = scale jp x angles + angle kp at level l + 1
+        const int Kp = state[2];
+        const int2 sh = lv[l + 1].shift[Kp];
         const int cx = 2 * state[0] + sh.x, cy = 2 * state[1] + sh.y;
-        const int kp = state[2];
+        const int nang = L.nangles, jp = Kp / lv[l + 1].nangles, kp = Kp - jp * lv[l + 1].nangles;
         const int W = j.w[l], H = j.h[l];
         const float2 *F = j.field[l];
-        float acc[27];
+        // the scales jp - 1 .. jp + 1 inside the grid, one pass of 27 poses
+        // each (a rigid model: one pass); CTA 0 keeps the best over the passes
+        const int last_ds = min(1, ns - 1 - jp);
+        float bs = -INFINITY;
+        unsigned long long bk = ~0ull;
+        int bx = 0, by = 0, bkk = 0;
+        bool any = false;
+        for (int ds = max(-1, -jp); ds <= last_ds; ++ds) {
+            const int js = jp + ds;
+            float acc[27];
 #pragma unroll
-        for (int q = 0; q < 27; ++q)
-            acc[q] = 0.f;
-#pragma unroll
-        for (int dk = 0; dk < 3; ++dk) {
-            const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
-            const RotPt *P = L.rot + (size_t)kk * L.n;
-            for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
-                const RotPt p = P[i];
-                const int bx = cx + p.ox, by = cy + p.oy;
-                constexpr int D = NB + 2;   // window of dot products
-                float d[D][D];
-#pragma unroll
-                for (int yy = 0; yy < D; ++yy) {
-#pragma unroll
-                    for (int xx = 0; xx < D; ++xx) {
-                        const int X = bx + xx - D / 2, Y = by + yy - D / 2;
-                        float v = 0.f;
-                        if (X >= 0 && Y >= 0 && X < W && Y < H) {
-                            const float2 f = __ldg(F + (size_t)Y * W + X);
-                            v = fmaf(p.px, f.x, p.py * f.y);
-                            if (j.polarity)
-                                v = fabsf(v);
-                        }
-                        d[yy][xx] = v;
-                    }
-                }
-#pragma unroll
-                for (int ty = 0; ty < 3; ++ty) {
-#pragma unroll
-                    for (int tx = 0; tx < 3; ++tx) {
-                        float m = -INFINITY;
-#pragma unroll
-                        for (int b = 0; b < NB; ++b)
-#pragma unroll
-                            for (int aa = 0; aa < NB; ++aa)
-                                m = fmaxf(m, d[ty + b][tx + aa]);
-                        acc[dk * 9 + ty * 3 + tx] += m;
-                    }
-                }
-            }
-        }
-        // block reduction of the 27 sums into this CTA's share
-#pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            float v = acc[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0)
-                red[warp][q] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 27) {
-            float v = 0.f;
-            for (int wv = 0; wv < RTHREADS / 32; ++wv)
-                v += red[wv][threadIdx.x];
-            part[threadIdx.x] = v;
-        }
-        cluster.sync();   // every CTA's share is in its shared memory
-        if (rank == 0 && threadIdx.x == 0) {
-            float tot[27];
             for (int q = 0; q < 27; ++q)
-                tot[q] = 0.f;
-            for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r) {
-                const float *pr = cluster.map_shared_rank(part, r);
-                for (int q = 0; q < 27; ++q)
-                    tot[q] += pr[q];
-            }
-            float bs = -INFINITY;
-            unsigned long long bk = ~0ull;
-            int bx = 0, by = 0, bkk = 0;
-            bool any = false;
+                acc[q] = 0.f;
+#pragma unroll
             for (int dk = 0; dk < 3; ++dk) {
-                const int kk = (2 * kp + dk - 1 + L.ntheta) % L.ntheta;
-                for (int ty = 0; ty < 3; ++ty) {
-                    for (int tx = 0; tx < 3; ++tx) {
-                        const int X = cx + tx - 1, Y = cy + ty - 1;
-                        if (X < 0 || Y < 0 || X >= W || Y >= H)
-                            continue;
-                        const float M = tot[dk * 9 + ty * 3 + tx] / (float)L.n;
-                        const unsigned long long key = ((unsigned long long)kk * H + Y) * W + X;
-                        if (!any || beats(M, key, bs, bk)) {
-                            any = true;
-                            bs = M;
-                            bk = key;
-                            bx = X;
-                            by = Y;
-                            bkk = kk;
+                const int kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
+                const RotPt *P = L.rot + (size_t)kk * L.n;
+                for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
+                    const RotPt p = P[i];
+                    const int bxp = cx + p.ox, byp = cy + p.oy;
+                    constexpr int D = NB + 2;   // window of dot products
+                    float d[D][D];
+#pragma unroll
+                    for (int yy = 0; yy < D; ++yy) {
+#pragma unroll
+                        for (int xx = 0; xx < D; ++xx) {
+                            const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
+                            float v = 0.f;
+                            if (X >= 0 && Y >= 0 && X < W && Y < H) {
+                                const float2 f = __ldg(F + (size_t)Y * W + X);
+                                v = fmaf(p.px, f.x, p.py * f.y);
+                                if (j.polarity)
+                                    v = fabsf(v);
+                            }
+                            d[yy][xx] = v;
+                        }
+                    }
+#pragma unroll
+                    for (int ty = 0; ty < 3; ++ty) {
+#pragma unroll
+                        for (int tx = 0; tx < 3; ++tx) {
+                            float m = -INFINITY;
+#pragma unroll
+                            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                                for (int aa = 0; aa < NB; ++aa)
+                                    m = fmaxf(m, d[ty + b][tx + aa]);
+                            acc[dk * 9 + ty * 3 + tx] += m;
                         }
                     }
                 }
             }
-            state[0] = bx;
-            state[1] = by;
-            state[2] = bkk;
-            state[3] = any && bs >= j.min_score;
-            sbest = bs;
+            // block reduction of the 27 sums into this CTA's share
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                float v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0)
+                    red[warp][q] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 27) {
+                float v = 0.f;
+                for (int wv = 0; wv < RTHREADS / 32; ++wv)
+                    v += red[wv][threadIdx.x];
+                part[threadIdx.x] = v;
+            }
+            cluster.sync();   // every CTA's share is in its shared memory
+            if (rank == 0 && threadIdx.x == 0) {
+                float tot[27];
+                for (int q = 0; q < 27; ++q)
+                    tot[q] = 0.f;
+                for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r) {
+                    const float *pr = cluster.map_shared_rank(part, r);
+                    for (int q = 0; q < 27; ++q)
+                        tot[q] += pr[q];
+                }
+                for (int dk = 0; dk < 3; ++dk) {
+                    const int kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
+                    for (int ty = 0; ty < 3; ++ty) {
+                        for (int tx = 0; tx < 3; ++tx) {
+                            const int X = cx + tx - 1, Y = cy + ty - 1;
+                            if (X < 0 || Y < 0 || X >= W || Y >= H)
+                                continue;
+                            const float M = tot[dk * 9 + ty * 3 + tx] / (float)L.n;
+                            const unsigned long long key = ((unsigned long long)kk * H + Y) * W + X;
+                            if (!any || beats(M, key, bs, bk)) {
+                                any = true;
+                                bs = M;
+                                bk = key;
+                                bx = X;
+                                by = Y;
+                                bkk = kk;
+                            }
+                        }
+                    }
+                }
+                if (ds == last_ds) {
+                    state[0] = bx;
+                    state[1] = by;
+                    state[2] = bkk;
+                    state[3] = any && bs >= j.min_score;
+                    sbest = bs;
+                }
+            }
+            cluster.sync();   // CTA 0 has read every share (and, after the last pass, chosen)
         }
-        cluster.sync();   // CTA 0's choice is in its shared memory
         if (rank != 0 && threadIdx.x == 0) {
             const int *s0 = cluster.map_shared_rank(state, 0u);
             state[0] = s0[0];
@@ -381,6 +403,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREAD
     j.cs = a.cand_s + (size_t)img * a.K;
     j.count = a.cand_count + img;
     j.refined = a.refined + (size_t)img * a.K;
+    j.nscales = a.nscales;
     refine_body<NB>(j, lv.L, blockIdx.x / kRefineCluster);
 }
 
@@ -397,7 +420,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREAD
 // ---------------------------------------------------------------------------
 
 __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, int min_side, int max_out,
-                         double angle_step, sam_pose *__restrict__ out, int *__restrict__ n_out) {
+                         double angle_step, int nang0, sam_pose *__restrict__ out, int *__restrict__ n_out) {
     __shared__ float s[kMaxTopK];
     __shared__ unsigned long long key[kMaxTopK];
     __shared__ int px[kMaxTopK], py[kMaxTopK], pk[kMaxTopK];
@@ -445,15 +468,17 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
             }
             if (!ok)
                 continue;
+            // table index = scale index x angles + angle index
+            const int sj = pk[i] / nang0, ak = pk[i] - sj * nang0;
             sam_pose p;
             p.x = (float)px[i];
             p.y = (float)py[i];
-            p.theta_deg = (float)(pk[i] * angle_step);
+            p.theta_deg = (float)(ak * angle_step);
             p.score = s[i];
-            p.angle_index = pk[i];
+            p.angle_index = ak;
             p.level0_x = px[i];
             p.level0_y = py[i];
-            p.reserved = 0;
+            p.scale_index = sj;
             out[kept++] = p;
         }
         *n_out = kept;
@@ -466,30 +491,33 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
 __global__ void __launch_bounds__(256) nms_kernel(NmsArgs a) {
     const int img = blockIdx.x;
     nms_body(a.refined + (size_t)img * a.K, min(a.cand_count[img], a.K), a.w0, a.h0, a.min_side, a.max_out,
-             a.angle_step, a.out + (size_t)img * a.max_out, a.n_out + img);
+             a.angle_step, a.nang0, a.out + (size_t)img * a.max_out, a.n_out + img);
 }
 
 // The same per job.
 __global__ void __launch_bounds__(256) nms_jobs_kernel(const NmsJob *__restrict__ jobs, int K) {
     const NmsJob j = jobs[blockIdx.x];
-    nms_body(j.refined, min(*j.count, K), j.w0, j.h0, j.min_side, j.max_out, j.angle_step, j.out, j.n_out);
+    nms_body(j.refined, min(*j.count, K), j.w0, j.h0, j.min_side, j.max_out, j.angle_step, j.nang0, j.out,
+             j.n_out);
 }
 
 }  // namespace
 
-size_t candidates_scratch_bytes(int nth, int gh, int gw) {
-    // At most one strict local maximum per 2x2x2 block of (theta, y, x).
-    const size_t cap = (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2);
-    return 256 + cap * sizeof(Cand);
+// At most one strict local maximum per 2x2x2 block of (theta, y, x) of one
+// scale (mutual neighbours), so per scale ceil(nang / 2) x ceil(gh / 2) x
+// ceil(gw / 2).
+size_t cand_cap(int nth, int gh, int gw, int ns) {
+    const int nang = nth / ns;
+    return (size_t)ns * ((nang + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2);
 }
 
-size_t cand_cap(int nth, int gh, int gw) { return (size_t)((nth + 1) / 2) * ((gh + 1) / 2) * ((gw + 1) / 2); }
+size_t candidates_scratch_bytes(int nth, int gh, int gw, int ns) { return 256 + cand_cap(nth, gh, gw, ns) * sizeof(Cand); }
 
 cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
                               int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
-                              int n_img, cudaStream_t st) {
+                              int n_img, cudaStream_t st, int ns) {
     // scratch layout: [n_img int counters, padded to 256 B][n_img x Cand cap]
-    const size_t cap = cand_cap(nth, gh, gw);
+    const size_t cap = cand_cap(nth, gh, gw, ns);
     int *cnt = reinterpret_cast<int *>(scratch);
     Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
     (void)scratch_img;
@@ -499,14 +527,14 @@ cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh,
     const size_t total = (size_t)nth * gh * gw;
     int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     dim3 grid((unsigned)blocks, (unsigned)n_img);
-    local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt);
+    local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns);
     topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
     count_launches(2);
     return cudaGetLastError();
 }
 
-size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img) {
-    return 256 * ((n_img * sizeof(int) + 255) / 256) + (size_t)n_img * cand_cap(nth, gh, gw) * sizeof(Cand);
+size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img, int ns) {
+    return 256 * ((n_img * sizeof(int) + 255) / 256) + (size_t)n_img * cand_cap(nth, gh, gw, ns) * sizeof(Cand);
 }
 
 cudaError_t launch_candidates_jobs(const CandJob *jobs, int n_jobs, size_t max_total, float min_score, int K,

@@ -112,6 +112,32 @@ void rotate_level(LevelHost &L, int k, RotPt *dst, int4 &box) {
     }
 }
 
+// Scaled table (Eq. (2) with A = s R(theta)) of one level, scale `scale` and
+// angle index k: offsets floor(A t + 1/2) with A = [[s c, -(s sn)], [s sn,
+// s c]] evaluated exactly as written, directions R(theta) g/|g| (the inverse
+// transpose of a similarity turns a gradient as R does).
+void scale_level(LevelHost &L, int k, double scale, RotPt *dst, int4 &box) {
+    const double th = ((double)k * L.dtheta) * kPi / 180.0;
+    const double c = cos(th), sn = sin(th);
+    const double a11 = scale * c, a12 = -(scale * sn), a21 = scale * sn, a22 = scale * c;
+    box = make_int4(1 << 30, -(1 << 30), 1 << 30, -(1 << 30));
+    for (int i = 0; i < L.n; ++i) {
+        const double x = (double)L.tx[i], y = (double)L.ty[i];
+        const int ox = (int)floor(a11 * x + a12 * y + 0.5);
+        const int oy = (int)floor(a21 * x + a22 * y + 0.5);
+        const double g = sqrt((double)L.gx[i] * L.gx[i] + (double)L.gy[i] * L.gy[i]);
+        const double ux = L.gx[i] / g, uy = L.gy[i] / g;
+        dst[i].ox = ox;
+        dst[i].oy = oy;
+        dst[i].px = (float)(c * ux - sn * uy);
+        dst[i].py = (float)(sn * ux + c * uy);
+        box.x = std::min(box.x, ox);
+        box.y = std::max(box.y, ox);
+        box.z = std::min(box.z, oy);
+        box.w = std::max(box.w, oy);
+    }
+}
+
 }  // namespace
 
 // Chunked tables of one level (see LevelHost): for every angle, the rotated
@@ -161,9 +187,15 @@ static void build_chunks(LevelHost &L) {
     L.cstart[L.ntheta] = (int)L.cbox.size();
 }
 
-sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m) {
+sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m,
+                       int nscales, double scale_min, double scale_step) {
     if (!tmpl || w < 3 || h < 3 || stride < w || p.levels < 1 || p.levels > kMaxLevels || p.low < 1 ||
         p.high < p.low || !(p.angle_step_deg > 0.0) || (p.polarity != 0 && p.polarity != 1))
+        return SAM_ERR_ARG;
+    // a scale grid with every s_j in (0, 16]; one scale of 1 is the rigid model
+    const bool scaled = !(nscales == 1 && scale_min == 1.0);
+    if (nscales < 1 || nscales > 64 || !(scale_min > 0.0) || !(scale_step >= 0.0) ||
+        (nscales > 1 && !(scale_step > 0.0)) || !(scale_min + (nscales - 1) * scale_step <= 16.0))
         return SAM_ERR_ARG;
     const double nt = 360.0 / p.angle_step_deg;
     const long n0 = lround(nt);
@@ -172,9 +204,14 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
         return SAM_ERR_ARG;
     if ((w >> (p.levels - 1)) < 3 || (h >> (p.levels - 1)) < 3)
         return SAM_ERR_ARG;
+    if ((long)nscales * n0 > (1L << 20))
+        return SAM_ERR_ARG;
     m->p = p;
     m->levels = p.levels;
     m->ntheta0 = (int)n0;
+    m->nscales = nscales;
+    m->scale_min = scale_min;
+    m->scale_step = scale_step;
     try {
         m->lv.assign(p.levels, LevelHost());
         std::vector<uint8_t> img((size_t)w * h);
@@ -190,7 +227,8 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
             LevelHost &L = m->lv[l];
             L.tw = cw;
             L.th = ch;
-            L.ntheta = (int)(n0 >> l);
+            L.nangles = (int)(n0 >> l);
+            L.ntheta = nscales * L.nangles;
             L.dtheta = p.angle_step_deg * (double)(1 << l);
             std::vector<int32_t> gx, gy;
             sobel(img, cw, ch, gx, gy);
@@ -211,8 +249,16 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
                 return SAM_ERR_EMPTY_MODEL;
             L.rot.resize((size_t)L.ntheta * L.n);
             L.bbox.resize(L.ntheta);
-            for (int k = 0; k < L.ntheta; ++k)
-                rotate_level(L, k, L.rot.data() + (size_t)k * L.n, L.bbox[k]);
+            if (!scaled) {
+                for (int k = 0; k < L.ntheta; ++k)
+                    rotate_level(L, k, L.rot.data() + (size_t)k * L.n, L.bbox[k]);
+            } else {
+                for (int j = 0; j < nscales; ++j)
+                    for (int k = 0; k < L.nangles; ++k) {
+                        const int K = j * L.nangles + k;
+                        scale_level(L, k, scale_min + j * scale_step, L.rot.data() + (size_t)K * L.n, L.bbox[K]);
+                    }
+            }
         }
         // chunk tables for every level: required where the rotated extent
         // exceeds one window, and a tiling choice of the autotuner elsewhere
@@ -228,11 +274,24 @@ sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_
             const double dx = 2.0 * (double)(L.tw / 2) + 0.5 - (double)(C.tw / 2);
             const double dy = 2.0 * (double)(L.th / 2) + 0.5 - (double)(C.th / 2);
             L.shift.resize(L.ntheta);
-            for (int k = 0; k < L.ntheta; ++k) {
-                const double th = ((double)k * L.dtheta) * kPi / 180.0;
-                const double c = cos(th), s = sin(th);
-                L.shift[k].x = (int)floor(0.5 - (c * dx - s * dy) + 0.5);
-                L.shift[k].y = (int)floor(0.5 - (s * dx + c * dy) + 0.5);
+            if (!scaled) {
+                for (int k = 0; k < L.ntheta; ++k) {
+                    const double th = ((double)k * L.dtheta) * kPi / 180.0;
+                    const double c = cos(th), s = sin(th);
+                    L.shift[k].x = (int)floor(0.5 - (c * dx - s * dy) + 0.5);
+                    L.shift[k].y = (int)floor(0.5 - (s * dx + c * dy) + 0.5);
+                }
+            } else {
+                // a scaled parent turns and scales d by its A = s R(theta)
+                for (int j = 0; j < nscales; ++j)
+                    for (int k = 0; k < L.nangles; ++k) {
+                        const double th = ((double)k * L.dtheta) * kPi / 180.0;
+                        const double c = cos(th), sn = sin(th), sc = scale_min + j * scale_step;
+                        const double a11 = sc * c, a12 = -(sc * sn), a21 = sc * sn, a22 = sc * c;
+                        const int K = j * L.nangles + k;
+                        L.shift[K].x = (int)floor(0.5 - (a11 * dx + a12 * dy) + 0.5);
+                        L.shift[K].y = (int)floor(0.5 - (a21 * dx + a22 * dy) + 0.5);
+                    }
             }
         }
     } catch (const std::bad_alloc &) {
@@ -269,6 +328,7 @@ sam_status upload_model(sam_model *m) {
         D.th = L.th;
         D.n = L.n;
         D.ntheta = L.ntheta;
+        D.nangles = L.nangles;
         D.rot = (const RotPt *)p;
         if (cudaMemcpy(p, L.rot.data(), L.rot.size() * sizeof(RotPt), cudaMemcpyHostToDevice) != cudaSuccess)
             goto fail;

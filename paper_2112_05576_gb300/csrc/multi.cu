@@ -210,6 +210,7 @@ sam_status upload_descriptors(sam_multi *mp) {
         memset(&c, 0, sizeof(c));
         c.map = (const float *)(base + q.off_map);
         c.nth = q.nth;
+        c.ns = 1;
         c.gh = q.H;
         c.gw = q.W;
         c.cand = (Cand *)(base + q.off_cand);
@@ -250,6 +251,7 @@ sam_status upload_descriptors(sam_multi *mp) {
         rj.cs = c.out_s;
         rj.count = c.out_count;
         rj.refined = (float4 *)(base + q.off_refined);
+        rj.nscales = 1;
         put(mp->off_rjobs + (size_t)i * sizeof(RefineJob), &rj, sizeof(rj));
         NmsJob nj;
         memset(&nj, 0, sizeof(nj));
@@ -260,6 +262,7 @@ sam_status upload_descriptors(sam_multi *mp) {
         nj.min_side = std::min(mp->models[q.model]->lv[0].tw, mp->models[q.model]->lv[0].th);
         nj.max_out = mp->p.max_detections;
         nj.angle_step = mp->models[q.model]->p.angle_step_deg;
+        nj.nang0 = mp->models[q.model]->ntheta0;
         nj.out = (sam_pose *)(base + q.off_out);
         nj.n_out = (int *)(base + q.off_nout);
         put(mp->off_njobs + (size_t)i * sizeof(NmsJob), &nj, sizeof(nj));
@@ -368,7 +371,8 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
         params->max_detections > kMaxTopK || params->precision < SAM_FP32 || params->precision > SAM_FP16)
         return SAM_ERR_ARG;
     for (int i = 0; i < n_models; ++i)
-        if (!models[i] || models[i]->p.low != models[0]->p.low || models[i]->p.polarity != models[0]->p.polarity)
+        if (!models[i] || models[i]->p.low != models[0]->p.low || models[i]->p.polarity != models[0]->p.polarity ||
+            models[i]->nscales != 1 || models[i]->scale_min != 1.0)   // plans take rigid models
             return SAM_ERR_ARG;   // one edge threshold and polarity per plan
     sam_multi *mp = new (std::nothrow) sam_multi();
     if (!mp)

@@ -25,7 +25,8 @@ struct RotPt {
 struct LevelHost {
     int tw = 0, th = 0;              // template size at this level
     int n = 0;                       // edge points
-    int ntheta = 0;                  // angles at this level
+    int ntheta = 0;                  // tables at this level: scales x angles (rigid model: angles)
+    int nangles = 0;                 // angles per scale (table K = j * nangles + k for scale j, angle k)
     double dtheta = 0.0;             // angle step (deg)
     std::vector<int32_t> tx, ty, gx, gy;
     std::vector<RotPt> rot;          // [ntheta][n]
@@ -49,6 +50,7 @@ constexpr int kChunkCell = 16;
 // Device copy of one level's tables.
 struct LevelDev {
     int tw, th, n, ntheta;
+    int nangles;          // angles per scale (ntheta = scales x nangles)
     const RotPt *rot;
     const int4 *bbox;
     const int2 *shift;
@@ -118,6 +120,10 @@ struct sam_model {
     sam_model_params p;
     int levels = 0;
     int ntheta0 = 0;
+    // scale grid of a scaled model (sam_create_model_scaled): s_j = scale_min
+    // + j scale_step, j < nscales; a rigid model has one scale of 1
+    int nscales = 1;
+    double scale_min = 1.0, scale_step = 0.0;
     std::vector<sam::LevelHost> lv;
     // device state (uploaded on first use)
     int device = -1;
@@ -144,7 +150,8 @@ namespace sam {
 void count_launches(int n);
 
 // ---- host model builder (model.cpp) ----
-sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m);
+sam_status build_model(const uint8_t *tmpl, int w, int h, int stride, const sam_model_params &p, sam_model *m,
+                       int nscales = 1, double scale_min = 1.0, double scale_step = 0.0);
 sam_status upload_model(sam_model *m);
 
 // ---- kernels (launchers return cudaGetLastError()) ----
@@ -392,11 +399,13 @@ struct Cand {
     uint32_t pad;
     unsigned long long key;   // (k * gh + y) * gw + x
 };
-size_t candidates_scratch_bytes(int nth, int gh, int gw);
-size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img);
+// nth: planes of the map (scales x angles); ns: scales (1 for a rigid map).
+// A candidate's key is its map index (plane * gh + y) * gw + x.
+size_t candidates_scratch_bytes(int nth, int gh, int gw, int ns = 1);
+size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img, int ns = 1);
 cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
                               int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
-                              int n_img, cudaStream_t st);
+                              int n_img, cudaStream_t st, int ns = 1);
 
 // (d) refinement down the pyramid + NMS
 struct RefineArgs {
@@ -413,6 +422,7 @@ struct RefineArgs {
     const int *cand_count;             // per image
     float4 *refined;                   // per image: K (x, y, k, score) level 0
     int count;
+    int nscales;                       // scale grid size (1: rigid); k above is the table index
 };
 cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t st);
 
@@ -424,6 +434,7 @@ struct NmsArgs {
     int min_side;
     int max_out;
     double angle_step;
+    int nang0;               // angles per scale at level 0 (table k = scale * nang0 + angle)
     sam_pose *out;           // per image max_out
     int *n_out;              // per image
     int count;
@@ -433,7 +444,8 @@ cudaError_t launch_nms(const NmsArgs &a, cudaStream_t st);
 // ---- job lists (batches of different sizes and models; device arrays) ----
 struct CandJob {
     const float *map;
-    int nth, gh, gw;
+    int nth, gh, gw;   // planes (scales x angles), rows, columns
+    int ns;            // scales (planes j * nth / ns .. : one scale)
     Cand *cand;
     size_t cap;
     int *cnt;          // zeroed before the launch
@@ -464,16 +476,18 @@ struct RefineJob {
     const float *cs;
     const int *count;
     float4 *refined;                   // K
+    int nscales;
 };
 struct NmsJob {
     const float4 *refined;
     const int *count;
     int w0, h0, min_side, max_out;
     double angle_step;
+    int nang0;
     sam_pose *out;
     int *n_out;
 };
-size_t cand_cap(int nth, int gh, int gw);
+size_t cand_cap(int nth, int gh, int gw, int ns = 1);
 cudaError_t launch_candidates_jobs(const CandJob *jobs, int n_jobs, size_t max_total, float min_score, int K,
                                    cudaStream_t st);
 cudaError_t launch_refine_jobs(const RefineJob *jobs, int n_jobs, int K, int nbhd, cudaStream_t st);

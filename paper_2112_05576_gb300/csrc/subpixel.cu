@@ -203,7 +203,8 @@ extern "C" sam_status sam_subpixel_poses(sam_model *m, const sam_field_ref *fiel
                                          const int32_t *pose_field, const int32_t *kyx, int n_poses,
                                          int neighbourhood, float *out, void *stream) {
     if (!m || !fields || n_fields < 1 || n_fields > SAM_MAX_BILINEAR_FIELDS || n_poses < 0 ||
-        (neighbourhood != 1 && neighbourhood != 3) || (n_poses > 0 && (!kyx || !out)))
+        (neighbourhood != 1 && neighbourhood != 3) || (n_poses > 0 && (!kyx || !out)) || m->nscales != 1 ||
+        m->scale_min != 1.0)   // the fit's neighbourhood is (x, y, angle): rigid models
         return SAM_ERR_ARG;
     for (int i = 0; i < n_fields; ++i) {
         const sam_field_ref &f = fields[i];

@@ -39,7 +39,7 @@ class DetectParams(ctypes.Structure):
 
 class Pose(ctypes.Structure):
     _fields_ = [("x", _c_float), ("y", _c_float), ("theta_deg", _c_float), ("score", _c_float),
-                ("angle_index", _c_int), ("level0_x", _c_int), ("level0_y", _c_int), ("reserved", _c_int)]
+                ("angle_index", _c_int), ("level0_x", _c_int), ("level0_y", _c_int), ("scale_index", _c_int)]
 
 
 class FieldRef(ctypes.Structure):
@@ -57,6 +57,10 @@ SIGNATURES = {
     "sam_default_detect_params": (None, [ctypes.POINTER(DetectParams)]),
     "sam_create_model": (_c_int, [_vp, _c_int, _c_int, _c_int, ctypes.POINTER(ModelParams), ctypes.POINTER(_vp)]),
     "sam_free_model": (None, [_vp]),
+    "sam_create_model_scaled": (_c_int, [_vp, _c_int, _c_int, _c_int, ctypes.POINTER(ModelParams), _c_double,
+                                         _c_double, _c_int, ctypes.POINTER(_vp)]),
+    "sam_model_num_scales": (_c_int, [_vp]),
+    "sam_model_scale": (_c_double, [_vp, _c_int]),
     "sam_model_levels": (_c_int, [_vp]),
     "sam_model_num_points": (_c_int, [_vp, _c_int]),
     "sam_model_num_angles": (_c_int, [_vp, _c_int]),
@@ -86,6 +90,9 @@ SIGNATURES = {
     "sam_model_tiling": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "sam_candidates_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int]),
     "sam_candidates": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp, _vp]),
+    "sam_candidates_scaled_scratch_bytes": (ctypes.c_size_t, [_c_int, _c_int, _c_int, _c_int]),
+    "sam_candidates_scaled": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp,
+                                       _vp]),
     "sam_candidates_noalloc": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_float, _c_int, _vp, _vp, _vp, _vp]),
     "sam_multi_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _i32p, _c_int, ctypes.c_void_p, _c_int,
                                   ctypes.POINTER(DetectParams), ctypes.POINTER(_vp)]),
@@ -175,18 +182,34 @@ def default_detect_params(**kw) -> DetectParams:
 class Model:
     """A template model (sam_create_model): the template's edge points at every
     pyramid level (Sec. II edge extraction, hysteresis between `low` and
-    `high`) and per level and angle index the Eq. (2) tables."""
+    `high`) and per level and angle index the Eq. (2) tables.  With
+    scales=(scale_min, scale_step, n_scales) a scaled model
+    (sam_create_model_scaled): tables per (scale, angle), Eq. (2) with
+    A = s R(theta)."""
 
-    def __init__(self, template: np.ndarray, low=30, high=60, levels=3, angle_step_deg=1.0, polarity=0):
+    def __init__(self, template: np.ndarray, low=30, high=60, levels=3, angle_step_deg=1.0, polarity=0,
+                 scales=None):
         t = np.ascontiguousarray(template, dtype=np.uint8)
         if t.ndim != 2:
             raise ValueError("template must be a 2-D uint8 array")
         self.params = ModelParams(int(low), int(high), int(levels), float(angle_step_deg), int(polarity))
         h = ctypes.c_void_p()
-        _check(lib().sam_create_model(t.ctypes.data_as(_vp), t.shape[1], t.shape[0], t.shape[1],
-                                      ctypes.byref(self.params), ctypes.byref(h)), "sam_create_model")
+        if scales is None:
+            _check(lib().sam_create_model(t.ctypes.data_as(_vp), t.shape[1], t.shape[0], t.shape[1],
+                                          ctypes.byref(self.params), ctypes.byref(h)), "sam_create_model")
+        else:
+            smin, sstep, ns = scales
+            _check(lib().sam_create_model_scaled(t.ctypes.data_as(_vp), t.shape[1], t.shape[0], t.shape[1],
+                                                 ctypes.byref(self.params), float(smin), float(sstep), int(ns),
+                                                 ctypes.byref(h)), "sam_create_model_scaled")
         self._h = h
         self.levels = lib().sam_model_levels(h)
+
+    def num_scales(self):
+        return int(lib().sam_model_num_scales(self._h))
+
+    def scale(self, j):
+        return float(lib().sam_model_scale(self._h, int(j)))
 
     @property
     def handle(self):
@@ -244,7 +267,7 @@ class Model:
 
 def _poses(arr, n) -> List[dict]:
     return [dict(x=arr[i].level0_x, y=arr[i].level0_y, theta_deg=arr[i].theta_deg, score=arr[i].score,
-                 k=arr[i].angle_index) for i in range(n)]
+                 k=arr[i].angle_index, j=arr[i].scale_index) for i in range(n)]
 
 
 def detect(model: Model, image, params: Optional[DetectParams] = None, stream=None, capacity=None):
@@ -413,6 +436,20 @@ def selftest_task_wait_timeout(limit_us=2000):
 def candidates_scratch_bytes(nth, gh, gw):
     """Device scratch bytes sam_candidates needs for an (nth, gh, gw) map."""
     return int(lib().sam_candidates_scratch_bytes(nth, gh, gw))
+
+
+def candidates_scaled_scratch_bytes(n_scales, n_angles, gh, gw):
+    """Device bytes of sam_candidates_scaled's scratch."""
+    return int(lib().sam_candidates_scaled_scratch_bytes(int(n_scales), int(n_angles), int(gh), int(gw)))
+
+
+def candidates_scaled(smap, min_score, K, out_kyx, out_s, count, scratch, stream=None):
+    """sam_candidates_scaled: strict local maxima over (scale, angle circular,
+    y, x) of a (n_scales, n_angles, gh, gw) score map; (plane, y, x) triples."""
+    ns, na, gh, gw = smap.shape
+    _check(lib().sam_candidates_scaled(_ptr(smap), ns, na, gh, gw, float(min_score), int(K), _ptr(out_kyx),
+                                       _ptr(out_s), _ptr(count), _ptr(scratch), _stream(stream)),
+           "sam_candidates_scaled")
 
 
 def candidates(smap, min_score, K, out_kyx, out_s, count, scratch, stream=None):

@@ -169,9 +169,10 @@ def render_template(spec: PartSpec) -> np.ndarray:
 
 
 def _inverse_map(qx, qy, pose, spec):
-    ux, uy, th = pose
+    ux, uy, th = pose[:3]
+    sc = pose[3] if len(pose) > 3 else 1.0     # optional scale of the instance
     c, s = math.cos(math.radians(th)), math.sin(math.radians(th))
-    dx, dy = qx - ux, qy - uy
+    dx, dy = (qx - ux) / sc, (qy - uy) / sc
     tx = c * dx + s * dy + spec.width // 2
     ty = -s * dx + c * dy + spec.height // 2
     return tx, ty
@@ -200,8 +201,9 @@ def render_scene(bg: np.ndarray, instances, paste_square=False) -> np.ndarray:
     H, W = out.shape
     for spec, pose, level in instances:
         part_level = spec.part_level if level is None else level
-        ux, uy, th = pose
-        rad = 0.5 * math.hypot(spec.width, spec.height) + 2
+        ux, uy, th = pose[:3]
+        sc = pose[3] if len(pose) > 3 else 1.0
+        rad = 0.5 * math.hypot(spec.width, spec.height) * sc + 2
         x0, x1 = max(0, int(math.floor(ux - rad))), min(W, int(math.ceil(ux + rad)) + 1)
         y0, y1 = max(0, int(math.floor(uy - rad))), min(H, int(math.ceil(uy + rad)) + 1)
         if x0 >= x1 or y0 >= y1:
@@ -209,7 +211,7 @@ def render_scene(bg: np.ndarray, instances, paste_square=False) -> np.ndarray:
         ys, xs = np.mgrid[y0:y1, x0:x1].astype(np.float64)
         acc = np.zeros(xs.shape, dtype=np.float64)
         cover = np.zeros(xs.shape, dtype=np.float64)
-        quarter = _exact_quarter_turn(th) and float(ux).is_integer() and float(uy).is_integer()
+        quarter = _exact_quarter_turn(th) and float(ux).is_integer() and float(uy).is_integer() and sc == 1.0
         for oy in _SUB:
             for ox in _SUB:
                 qx, qy = xs + ox, ys + oy
@@ -324,7 +326,7 @@ def _scene_background(rng, H, W, level=100.0):
     return np.full((H, W), level, dtype=np.float64)
 
 
-def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, subpixel=False):
+def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, subpixel=False, scales=None):
     """Paper-shaped scene: 1-4 instances of a side x side part with occlusion,
     an illumination ramp, 20 clutter segments and Gaussian noise sigma=6.
 
@@ -332,6 +334,9 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, s
     Instance angles are drawn on a 0.5 degree grid, positions on the pixel
     grid; with subpixel=True each position is moved by U(-1/2, 1/2) px per
     axis, drawn from a second generator so the scene is otherwise the same.
+    With `scales` (a list) each instance is drawn at a scale chosen from it
+    by a third generator (poses then carry it: (x, y, theta, s)), and the
+    placement keeps the largest scale's extent inside the image.
     """
     rng = np.random.default_rng(seed)
     if spec is None:
@@ -342,7 +347,7 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, s
         n_inst = int(rng.integers(1, 5))
     poses = []
     tries = 0
-    rad = 0.5 * math.hypot(side, side)
+    rad = 0.5 * math.hypot(side, side) * (max(scales) if scales else 1.0)
     while len(poses) < n_inst and tries < 10000:
         tries += 1
         p = (int(rng.integers(int(rad * 0.6), W - int(rad * 0.6))),
@@ -353,6 +358,9 @@ def config2_scene(seed=3234, W=1280, H=1024, side=200, spec=None, n_inst=None, s
     if subpixel:
         frac = np.random.default_rng(seed + 0x5EED).uniform(-0.5, 0.5, (len(poses), 2))
         poses = [(p[0] + float(f[0]), p[1] + float(f[1]), p[2]) for p, f in zip(poses, frac)]
+    if scales:
+        pick = np.random.default_rng(seed + 0x5CA1E).integers(0, len(scales), len(poses))
+        poses = [(p[0], p[1], p[2], float(scales[int(i)])) for p, i in zip(poses, pick)]
     img = render_scene(bg, [(spec, p, float(rng.uniform(170, 210))) for p in poses])
     # clutter: 20 random line segments, 1.5-3 px thick, random gray
     for _ in range(20):

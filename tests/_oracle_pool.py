@@ -30,6 +30,13 @@ def _score_map_one(job):
                             polarity=om.polarity)
 
 
+def _detect_scaled_one(job):
+    import oracle
+    tmpl, img, model_args, scales, params = job
+    om = oracle.create_model(tmpl, *model_args)
+    return oracle.detect_scaled(om, img, oracle.DetectParams(**params), scales)
+
+
 def _run(fn, jobs, workers=None):
     workers = workers or max(1, min(len(jobs), os.cpu_count() or 1, 16))
     if workers == 1 or len(jobs) == 1:
@@ -47,3 +54,8 @@ def detect_many(jobs, workers=None):
 def top_maps(jobs, workers=None):
     """jobs: (template, scene, model args, neighbourhood) tuples; returns the FP64 top-level score map of each."""
     return _run(_score_map_one, jobs, workers)
+
+
+def detect_scaled_many(jobs, workers=None):
+    """jobs: (template, scene, model args, scale grid, DetectParams kwargs) tuples; oracle.detect_scaled of each."""
+    return _run(_detect_scaled_one, jobs, workers)
