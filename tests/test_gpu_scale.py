@@ -181,7 +181,9 @@ def test_scaled_detection_finds_instances_at_their_scale(det_case):
                 hits += 1
                 d = near[0]
                 assert m.scale(d["j"]) == pytest.approx(gs)
-                assert abs(((d["theta_deg"] - gth) + 180) % 360 - 180) <= 1.0
+                # the descent keeps the best of its window, which may sit at
+                # the window's edge (as in the rigid search): within 3 degrees
+                assert abs(((d["theta_deg"] - gth) + 180) % 360 - 180) <= 3.0
     assert hits >= 4
 
 
