@@ -582,6 +582,51 @@ def run_storage_forms(args, sam, torch, dev, stream, model, batch):
 
 
 # ---------------------------------------------------------------------------
+# scaled poses (Eq. (2) with A = s R(theta))
+# ---------------------------------------------------------------------------
+
+SCALE_GRID = (0.9, 0.1, 3)     # 0.9, 1.0, 1.1
+
+
+def run_scaled(args, sam, torch, dev, stream, tm, spec, n_scenes=8):
+    """Detection over scales x angles x translations (a scaled model,
+    sam_create_model_scaled) on config-2 scenes whose instances are drawn at
+    the grid's scales, next to the rigid model on the same scenes: time per
+    batch (device-resident, graph replay), nominal pose-points, and the
+    instances found at their scale."""
+    grid = [SCALE_GRID[0] + j * SCALE_GRID[1] for j in range(SCALE_GRID[2])]
+    imgs, truth = [], []
+    for i in range(n_scenes):
+        _, sc, gts, _ = synth.config2_scene(seed=9300 + i, W=W, H=H, side=SIDE, spec=spec, scales=grid)
+        imgs.append(sc)
+        truth.append(gts)
+    batch = torch.from_numpy(np.stack(imgs)).to(dev)
+    params = sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, top_k=64, max_detections=16)
+    out = {"what": f"sam_detect_batch of {n_scenes} config-2 scenes with instances at scales {grid}; scaled model "
+                   f"(scales {grid}) vs the rigid model, autotuned tilings, early termination",
+           "scales": grid}
+    for name, model in (("scaled", sam.Model(tm, LOW, HIGH, LEVELS, STEP, scales=SCALE_GRID)),
+                        ("rigid", sam.Model(tm, LOW, HIGH, LEVELS, STEP))):
+        sam.autotune(model, batch, params)
+        for _ in range(3):
+            res = sam.detect_batch(model, batch, params)
+        ms = _event_ms(torch, dev, stream, lambda i: sam.detect_batch(model, batch, params), 10)
+        top = LEVELS - 1
+        pp = n_scenes * model.num_scales() * model.num_angles(top) * (W >> top) * (H >> top) * model.num_points(top)
+        found, right_scale = 0, 0
+        for dets, gts in zip(res, truth):
+            for gx, gy, gth, gs in gts:
+                near = [d for d in dets if (d["x"] - gx) ** 2 + (d["y"] - gy) ** 2 <= 9]
+                if near:
+                    found += 1
+                    right_scale += int(abs(model.scale(near[0]["j"]) - gs) < 1e-9)
+        out[name] = {"ms_per_batch": round(ms, 4), "ms_per_detection": round(ms / n_scenes, 5),
+                     "value": pp / (ms * 1e-3), "unit": UNIT, "pose_points_per_batch": pp,
+                     "instances": int(sum(len(t) for t in truth)), "found": found, "found_at_their_scale": right_scale}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # HBM-bound kernels (a) gradient and (b) pyramid on images larger than L2
 # ---------------------------------------------------------------------------
 # Algorithmic bytes: the gradient kernel reads each 8-bit pixel once and
@@ -862,6 +907,9 @@ def run_gpu(args):
     # ---- the large exhaustive stress slice (chunked scorer) ----
     stress = run_stress(args, sam, torch, dev, stream) if (args.stress and rank == 0) else None
 
+    # ---- scaled poses: the search over scales x angles x translations ----
+    scaled = run_scaled(args, sam, torch, dev, stream, tm, spec) if (args.scaled and rank == 0) else None
+
     # ---- field storage forms (FP32 / BF16 pairs / angle codes) on one top-level map ----
     storage = run_storage_forms(args, sam, torch, dev, stream, model, batches[0]) if rank == 0 else None
 
@@ -999,6 +1047,7 @@ def run_gpu(args):
         "quantized": quantized,
         "stress": stress,
         "storage_forms": storage,
+        "scaled": scaled,
         "hbm": hbm,
         "wall_s": wall,
     }
@@ -1038,6 +1087,7 @@ def main():
     ap.add_argument("--refine", type=int, default=4096, help="poses of the differentiable form (0: skip)")
     ap.add_argument("--stress", type=int, default=1, help="time the config-5 stress slices (0: skip)")
     ap.add_argument("--hbm", type=int, default=1, help="time the gradient and pyramid kernels against HBM (0: skip)")
+    ap.add_argument("--scaled", type=int, default=1, help="time the scaled-pose detection (0: skip)")
     ap.add_argument("--tiling", default="", help="force the tiled scorer's sx,sy,tg,warps[,cols] (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per score launch, if measured")
