@@ -92,16 +92,47 @@ __device__ __forceinline__ void push_candidate(const float *map, size_t idx, Can
 // Candidates (the best pose of Sec. II, generalised to every strict 3x3x3
 // local maximum at or above min_score) of `count` equal maps, image
 // blockIdx.y; appended to the image's list by atomic counter.
+// The map is read four entries at a time (one 16-byte load, four loads in
+// flight per thread); almost every entry is below min_score (or -inf where
+// early termination pruned it), and only the others are tested against
+// their neighbours.  vec: the map (and every image's map) is 16-byte aligned.
 __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
                                  float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt,
-                                 int ns) {
+                                 int ns, int vec) {
     const int img = blockIdx.y;
     map += (size_t)img * map_img;
+    cand += (size_t)img * cap;
+    cnt += img;
     const size_t total = (size_t)nth * gh * gw;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x)
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t idx0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t scalar_from = 0;
+    if (vec) {
+        const size_t total4 = total / 4;
+        const float4 *m4 = reinterpret_cast<const float4 *>(map);
+        for (size_t i4 = idx0; i4 < total4; i4 += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = i4 + u * stride < total4 ? __ldg(m4 + i4 + u * stride)
+                                                 : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (e[q] >= min_score) {
+                        const size_t idx = 4 * (i4 + u * stride) + q;
+                        if (is_candidate(map, nth, gh, gw, min_score, idx, ns))
+                            push_candidate(map, idx, cand, cap, cnt);
+                    }
+            }
+        }
+        scalar_from = 4 * total4;   // the last total % 4 entries
+    }
+    for (size_t idx = scalar_from + idx0; idx < total; idx += stride)
         if (is_candidate(map, nth, gh, gw, min_score, idx, ns))
-            push_candidate(map, idx, cand + (size_t)img * cap, cap, cnt + img);
+            push_candidate(map, idx, cand, cap, cnt);
 }
 
 // The same over a job list of maps of different sizes (job blockIdx.y).
@@ -525,9 +556,13 @@ cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh,
     if (e != cudaSuccess)
         return e;
     const size_t total = (size_t)nth * gh * gw;
-    int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const int vec = ((uintptr_t)map % 16 == 0) && (n_img == 1 || map_img % 4 == 0);
+    // about 8 CTAs of 256 threads per SM over all images, each thread a few
+    // 16-byte loads of 4 entries
+    const int per_img = std::max(1, 152 * 8 / std::max(1, n_img));
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total / 4 + 255) / 256, (size_t)per_img));
     dim3 grid((unsigned)blocks, (unsigned)n_img);
-    local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns);
+    local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns, vec);
     topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
     count_launches(2);
     return cudaGetLastError();

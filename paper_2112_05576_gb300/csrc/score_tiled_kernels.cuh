@@ -1010,6 +1010,14 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             // this lane's pose row in the bitmaps and its first pose's column
             const uint32_t *rbase = cbits + (size_t)(yrow - wy0) * dmw;
             const int xb = xseg - wx0;
+            // Early exit: after point i a pose still needs E_i >= need_i =
+            // emin - (n - i) edge hits (every remaining point adds at most
+            // one).  Every 32 points the lane checks, from its top count
+            // planes, whether all its poses are below 2^m <= need_i; once
+            // every lane of the warp is, no pose of the item can reach emin
+            // and the count stops (the poses are dead exactly as a complete
+            // count would find them).
+            bool all_dead = false;
             for (int i0 = 0; i0 < np8; i0 += 8) {
                 if ((i0 & 31) == 0) {
                     const int ii = i0 + lane;
@@ -1096,6 +1104,31 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     e1 = c1;
                     e2 = c2;
                 }
+                if (((i0 + 8) & 31) == 0) {
+                    const int need = a.emin - max(0, a.n - (i0 + 8));
+                    if (need > 0) {
+                        // every count < 2^m <= need when planes m .. 15 are clear
+                        const int m = 31 - __clz(need);
+                        uint32_t hi = 0u;
+#pragma unroll
+                        for (int pq = 0; pq < 16; ++pq) {
+                            if (pq < m)
+                                continue;
+                            if (pq == 0)
+                                hi |= ones0 | ones1 | ones2;
+                            else if (pq == 1)
+                                hi |= twos0 | twos1 | twos2;
+                            else if (pq == 2)
+                                hi |= fours0 | fours1 | fours2;
+                            else
+                                hi |= pl[pq][0] | pl[pq][1] | pl[pq][2];
+                        }
+                        if (__all_sync(0xffffffffu, hi == 0u)) {
+                            all_dead = true;
+                            break;
+                        }
+                    }
+                }
             }
             pl[0][0] = ones0;
             pl[0][1] = ones1;
@@ -1123,9 +1156,10 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     eq2 &= ~pl[pq][2];
                 }
             }
-            const uint32_t o0 = gt0 | eq0;
-            const uint32_t o1 = (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u));
-            const uint32_t o2 = BW > 64 ? ((gt2 | eq2) & ((1u << ((BW - 64) & 31)) - 1u)) : 0u;
+            const uint32_t o0 = all_dead ? 0u : gt0 | eq0;
+            const uint32_t o1 =
+                all_dead ? 0u : (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u));
+            const uint32_t o2 = (BW > 64 && !all_dead) ? ((gt2 | eq2) & ((1u << ((BW - 64) & 31)) - 1u)) : 0u;
             // this thread's 8 x TC block (rows ly*TR .., columns lx*TC ..) in
             // RD-row slices: a slice with no surviving pose is written -inf,
             // the others go to the queue
