@@ -853,19 +853,34 @@ __device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int
     }
 }
 
-// -inf into an R x TC pose block of the map, clipped to the map.
-template <int TC, int R>
-__device__ __forceinline__ void fill_neg(float *mk, int W, int H, int xl, int yl) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int y = yl + r;
-        if (y >= H)
-            break;
-        float *row = mk + (size_t)y * W;
-#pragma unroll
-        for (int c = 0; c < TC; ++c)
-            if (xl + c < W)
-                row[xl + c] = -INFINITY;
+// -inf over a WTX x WTY region of the map at (xl, yl), clipped to the map,
+// by the 32 lanes of a warp: rows in 16-byte chunks (one float4 store per
+// lane and chunk, a warp instruction covering 512 contiguous bytes of a row
+// where the region is as wide) when the region and the map rows are
+// 16-byte aligned, else element by element in row order.
+template <int WTX, int WTY>
+__device__ __forceinline__ void warp_fill_neg(float *mk, int W, int H, int xl, int yl, int lane) {
+    const int cols = min(WTX, W - xl), rows = min(WTY, H - yl);
+    if (cols <= 0 || rows <= 0)
+        return;
+    float *base = mk + (size_t)yl * W + xl;
+    if (((uintptr_t)base & 15) == 0 && (W & 3) == 0) {   // every row start 16-byte aligned
+        const int c4 = (cols + 3) >> 2;   // 16-byte chunks per row (the last may be partial)
+        for (int idx = lane; idx < rows * c4; idx += 32) {
+            const int r = idx / c4, c = (idx - r * c4) * 4;
+            float *p = base + (size_t)r * W + c;
+            if (c + 4 <= cols) {
+                *reinterpret_cast<float4 *>(p) = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            } else {
+                for (int e = 0; e < cols - c; ++e)
+                    p[e] = -INFINITY;
+            }
+        }
+    } else {
+        for (int idx = lane; idx < rows * cols; idx += 32) {
+            const int r = idx / cols;
+            base[(size_t)r * W + (idx - r * cols)] = -INFINITY;
+        }
     }
 }
 
@@ -1160,12 +1175,14 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             const uint32_t o1 =
                 all_dead ? 0u : (gt1 | eq1) & (BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u));
             const uint32_t o2 = (BW > 64 && !all_dead) ? ((gt2 | eq2) & ((1u << ((BW - 64) & 31)) - 1u)) : 0u;
-            // this thread's 8 x TC block (rows ly*TR .., columns lx*TC ..) in
-            // RD-row slices: a slice with no surviving pose is written -inf,
-            // the others go to the queue
+            // the item's whole warp tile is written -inf (coalesced); its
+            // surviving RD-row slices go to the queue and are overwritten
+            // when they are scored (after this write: the tasks are published
+            // behind a fence, the local drain behind a CTA barrier)
             const int seg = (lx * TC) / BW, c0 = lx * TC - seg * BW;
-            const int x0 = stx0 + (wt % a.sx) * WTX + lx * TC, y0 = sty0 + (wt / a.sx) * WTY + ly * TR;
             float *mk = a.map + (size_t)(k - a.k0) * a.H * a.W;
+            warp_fill_neg<WTX, WTY>(mk, a.W, a.H, stx0 + (wt % a.sx) * WTX - a.ox, sty0 + (wt / a.sx) * WTY - a.oy,
+                                    lane);
             uint32_t nib = 0u;   // surviving slices of this lane's block
 #pragma unroll
             for (int sp = 0; sp < SPLIT; ++sp) {
@@ -1180,8 +1197,6 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     const uint32_t hi = c0 < 32 ? v1 : (c0 < 64 ? v2 : 0u);
                     act |= __funnelshift_r(lo, hi, c0 & 31) & ((1u << TC) - 1u);
                 }
-                if (!act)
-                    fill_neg<TC, RD>(mk, a.W, a.H, x0 - a.ox, y0 + sp * RD - a.oy);
                 nib |= (act != 0u ? 1u : 0u) << sp;
             }
             // queue order (item, lane, slice): word q of the item's mask holds
