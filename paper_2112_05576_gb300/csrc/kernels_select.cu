@@ -116,16 +116,18 @@ __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, 
             for (int u = 0; u < 4; ++u)
                 v[u] = i4 + u * stride < total4 ? __ldg(m4 + i4 + u * stride)
                                                  : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            // the entries at or above min_score (rare), then one call site
+            uint32_t hit = 0u;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (e[q] >= min_score) {
-                        const size_t idx = 4 * (i4 + u * stride) + q;
-                        if (is_candidate(map, nth, gh, gw, min_score, idx, ns))
-                            push_candidate(map, idx, cand, cap, cnt);
-                    }
+            for (int u = 0; u < 4; ++u)
+                hit |= (v[u].x >= min_score ? 1u : 0u) << (4 * u) | (v[u].y >= min_score ? 2u : 0u) << (4 * u) |
+                       (v[u].z >= min_score ? 4u : 0u) << (4 * u) | (v[u].w >= min_score ? 8u : 0u) << (4 * u);
+            while (hit) {
+                const int b = __ffs(hit) - 1;
+                hit &= hit - 1u;
+                const size_t idx = 4 * (i4 + (size_t)(b >> 2) * stride) + (b & 3);
+                if (is_candidate(map, nth, gh, gw, min_score, idx, ns))
+                    push_candidate(map, idx, cand, cap, cnt);
             }
         }
         scalar_from = 4 * total4;   // the last total % 4 entries
@@ -557,9 +559,9 @@ cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh,
         return e;
     const size_t total = (size_t)nth * gh * gw;
     const int vec = ((uintptr_t)map % 16 == 0) && (n_img == 1 || map_img % 4 == 0);
-    // about 8 CTAs of 256 threads per SM over all images, each thread a few
-    // 16-byte loads of 4 entries
-    const int per_img = std::max(1, 152 * 8 / std::max(1, n_img));
+    // about 32 CTAs of 256 threads per SM over all images (several waves),
+    // each thread a few 16-byte loads of 4 entries
+    const int per_img = std::max(1, 152 * 32 / std::max(1, n_img));
     const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total / 4 + 255) / 256, (size_t)per_img));
     dim3 grid((unsigned)blocks, (unsigned)n_img);
     local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns, vec);
