@@ -298,12 +298,20 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
 #pragma unroll
             for (int q = 0; q < 27; ++q)
                 acc[q] = 0.f;
+            // the three angles' tables of this pass; per point the three
+            // projections are loaded together, then each angle's window
+            const RotPt *P3[3];
 #pragma unroll
-            for (int dk = 0; dk < 3; ++dk) {
-                const int kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
-                const RotPt *P = L.rot + (size_t)kk * L.n;
-                for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
-                    const RotPt p = P[i];
+            for (int dk = 0; dk < 3; ++dk)
+                P3[dk] = L.rot + (size_t)(js * nang + (2 * kp + dk - 1 + nang) % nang) * L.n;
+            for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
+                RotPt pt[3];
+#pragma unroll
+                for (int dk = 0; dk < 3; ++dk)
+                    pt[dk] = P3[dk][i];
+#pragma unroll
+                for (int dk = 0; dk < 3; ++dk) {
+                    const RotPt p = pt[dk];
                     const int bxp = cx + p.ox, byp = cy + p.oy;
                     constexpr int D = NB + 2;   // window of dot products
                     float d[D][D];
@@ -355,41 +363,57 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                 part[threadIdx.x] = v;
             }
             cluster.sync();   // every CTA's share is in its shared memory
-            if (rank == 0 && threadIdx.x == 0) {
-                float tot[27];
-                for (int q = 0; q < 27; ++q)
-                    tot[q] = 0.f;
-                for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r) {
-                    const float *pr = cluster.map_shared_rank(part, r);
-                    for (int q = 0; q < 27; ++q)
-                        tot[q] += pr[q];
+            if (rank == 0 && warp == 0) {
+                // lane q < 27: pose q's sum over the CTAs (in rank order) and
+                // its key; the best by the total order by a shuffle reduction
+                float M = -INFINITY;
+                unsigned long long key = ~0ull;
+                int X = 0, Y = 0, kk = 0;
+                bool valid = false;
+                if (lane < 27) {
+                    float tot = 0.f;
+                    for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r)
+                        tot += cluster.map_shared_rank(part, r)[lane];
+                    const int dk = lane / 9, ty = (lane / 3) % 3, tx = lane % 3;
+                    kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
+                    X = cx + tx - 1;
+                    Y = cy + ty - 1;
+                    valid = X >= 0 && Y >= 0 && X < W && Y < H;
+                    M = tot / (float)L.n;
+                    key = ((unsigned long long)kk * H + Y) * W + X;
                 }
-                for (int dk = 0; dk < 3; ++dk) {
-                    const int kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
-                    for (int ty = 0; ty < 3; ++ty) {
-                        for (int tx = 0; tx < 3; ++tx) {
-                            const int X = cx + tx - 1, Y = cy + ty - 1;
-                            if (X < 0 || Y < 0 || X >= W || Y >= H)
-                                continue;
-                            const float M = tot[dk * 9 + ty * 3 + tx] / (float)L.n;
-                            const unsigned long long key = ((unsigned long long)kk * H + Y) * W + X;
-                            if (!any || beats(M, key, bs, bk)) {
-                                any = true;
-                                bs = M;
-                                bk = key;
-                                bx = X;
-                                by = Y;
-                                bkk = kk;
-                            }
-                        }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float oM = __shfl_xor_sync(0xffffffffu, M, o);
+                    const unsigned long long okey = __shfl_xor_sync(0xffffffffu, key, o);
+                    const int oX = __shfl_xor_sync(0xffffffffu, X, o), oY = __shfl_xor_sync(0xffffffffu, Y, o);
+                    const int okk = __shfl_xor_sync(0xffffffffu, kk, o);
+                    const bool ovalid = __shfl_xor_sync(0xffffffffu, valid, o);
+                    if (ovalid && (!valid || beats(oM, okey, M, key))) {
+                        M = oM;
+                        key = okey;
+                        X = oX;
+                        Y = oY;
+                        kk = okk;
+                        valid = true;
                     }
                 }
-                if (ds == last_ds) {
-                    state[0] = bx;
-                    state[1] = by;
-                    state[2] = bkk;
-                    state[3] = any && bs >= j.min_score;
-                    sbest = bs;
+                if (lane == 0) {
+                    if (valid && (!any || beats(M, key, bs, bk))) {
+                        any = true;
+                        bs = M;
+                        bk = key;
+                        bx = X;
+                        by = Y;
+                        bkk = kk;
+                    }
+                    if (ds == last_ds) {
+                        state[0] = bx;
+                        state[1] = by;
+                        state[2] = bkk;
+                        state[3] = any && bs >= j.min_score;
+                        sbest = bs;
+                    }
                 }
             }
             cluster.sync();   // CTA 0 has read every share (and, after the last pass, chosen)
@@ -415,9 +439,10 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
 // Coarse-to-fine refinement (Sec. II: the search starts at the top pyramid
 // level; the size-3 neighbouring search in x, y and theta at each lower
 // level): a cluster of kRefineCluster CTAs per candidate of image
-// blockIdx.y, all levels down to 0 in one launch.
+// blockIdx.y, all levels down to 0 in one launch.  Three CTAs per SM (85
+// registers) measured faster than two with no register limit.
 template <int NB>
-__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
     refine_kernel(RefineLevels lv, RefineArgs a) {
     const int img = blockIdx.y;
     RefineJob j;
@@ -442,7 +467,7 @@ __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREAD
 
 // The same per job (pair blockIdx.y).
 template <int NB>
-__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS)
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
     refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
     const RefineJob &j = jobs[blockIdx.y];
     refine_body<NB>(j, j.L, blockIdx.x / kRefineCluster);

@@ -365,7 +365,10 @@ cudaError_t launch_score_pairs(const PairScore *pairs, int n_pairs, int total_it
 // Shared memory of the edge bitmaps the tiled scorers build over a window of
 // bxw x byw pixels (edge pixels and their 3x3 dilation, one bit per pixel,
 // rows padded by 3 words for the funnel shifts of the bound pass).
-__host__ __device__ inline int edge_bitmap_words(int bxw) { return (bxw + 31) / 32 + 3; }
+// Words per bitmap row: the window's pixels, 3 words of slack for the
+// four-word loads of a row segment, rounded to an odd count so that rows
+// read by consecutive lanes fall in distinct shared-memory banks.
+__host__ __device__ inline int edge_bitmap_words(int bxw) { return ((bxw + 31) / 32 + 3) | 1; }
 // 4 planes of edge pixels by the quadrants they can serve and their 4 dilated
 // copies (score_tiled_kernels.cuh, build_edge_bits).
 __host__ __device__ inline size_t edge_bitmap_bytes(int bxw, int byw) { return 8 * (size_t)byw * edge_bitmap_words(bxw) * 4; }

@@ -327,8 +327,13 @@ __device__ __forceinline__ void build_edge_bits(const typename Pairs<E>::Raw *wi
             e[b] = 0u;
         if (wi < nw) {
             const typename Pairs<E>::Raw *row = win + (size_t)r * pp;
+            // consecutive threads own consecutive words, 16 pixel pairs
+            // apart: each thread starts at its own pair of the word (lane
+            // rotation) so that one load instruction touches distinct banks
+            const int rot = threadIdx.x & 15;
 #pragma unroll 4
-            for (int q = 0; q < 16; ++q) {
+            for (int qq = 0; qq < 16; ++qq) {
+                const int q = (qq + rot) & 15;
                 const int pq = wi * 16 + q;
                 if (pq < pp) {
                     const float4 v = Pairs<E>::get(row, pq);   // {x0, x1, y0, y1}
