@@ -90,17 +90,27 @@ def block_candidates(k0: int, nk: int, nth: int, H: int, W: int, min_score: floa
     dropped, and K is raised until K maxima of the block's own planes are
     certain to be among those returned.
     """
-    ext = extended_angles(k0, nk, nth)
+    # The block and its halo planes, in increasing global angle index: a
+    # block that wraps around angle 0 ([nth-1, 0, 1, ..]) is stored as
+    # [0, 1, .., nth-1], so the extended map's circular plane order keeps every
+    # own plane next to its two global neighbours, and its plane order is the
+    # global one, so cand_fn breaks ties between planes as the single-rank
+    # search does (higher score, then the smaller global key).
+    ext = sorted(set(extended_angles(k0, nk, nth)))
     planes = []
     for _, ka, cnt in contiguous_runs(ext):
         planes.append(score_fn(ka, cnt))
     emap = planes[0] if len(planes) == 1 else _concat(planes)
-    halo = nk != nth
+    halo = len(ext) != nth
+
+    def is_own(g):
+        return (g - k0) % nth < nk
+
     k_ext = K if not halo else 4 * K
     while True:
         ks, ys, xs, ss = cand_fn(emap, min_score, k_ext)
         own = [(ext[int(k)], int(y), int(x), float(s)) for k, y, x, s in zip(ks, ys, xs, ss)
-               if not halo or 0 < int(k) < len(ext) - 1]
+               if not halo or is_own(ext[int(k)])]
         if len(own) >= K or len(ks) < k_ext:
             own.sort(key=lambda c: order_key(c, H, W))
             return own[:K]

@@ -121,3 +121,79 @@ def test_unit_ranges_and_halo():
     assert shard.contiguous_runs([35, 0, 1, 2, 3]) == [(0, 35, 1), (1, 0, 4)]
     with pytest.raises(ValueError):
         shard.angle_block(4, 5, 0)
+
+
+# ---------------------------------------------------------------------------
+# exact ties across block boundaries and across the angle wrap
+# ---------------------------------------------------------------------------
+
+TIE_NTH, TIE_H, TIE_W = 12, 6, 7
+
+
+def _tied_map():
+    # multiples of 1/8: many exact ties between neighbouring planes, and the
+    # first and last planes made equal so that ties straddle the wrap
+    rng = np.random.default_rng(77)
+    m = rng.integers(0, 9, (TIE_NTH, TIE_H, TIE_W)) / 8.0
+    m[-1] = m[0]
+    m[5] = m[6]
+    return m
+
+
+def _tied_fns():
+    full = _tied_map()
+
+    def score_fn(k_first, count):
+        return full[k_first:k_first + count]
+
+    def cand_fn(smap, min_score, k):
+        return oracle.candidates(smap, min_score, k)
+
+    return score_fn, cand_fn
+
+
+def _tie_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        score_fn, cand_fn = _tied_fns()
+        got = shard.sharded_candidates(TIE_NTH, TIE_H, TIE_W, 0.25, 40, score_fn, cand_fn)
+        lists = [None] * world
+        dist.all_gather_object(lists, got)
+        if rank == 0:
+            out.put(lists)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_sharded_candidates_break_ties_as_single_rank(world):
+    ks, ys, xs, ss = oracle.candidates(_tied_map(), 0.25, 40)
+    want = [(int(k), int(y), int(x), float(s)) for k, y, x, s in zip(ks, ys, xs, ss)]
+    assert len(want) >= 10
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_tie_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    lists = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for got in lists:
+        assert got == want
+
+
+def test_block_candidates_with_ties_without_processes():
+    # every block of every split, checked in one process against the single-rank search
+    score_fn, cand_fn = _tied_fns()
+    ks, ys, xs, ss = oracle.candidates(_tied_map(), 0.25, 40)
+    want = [(int(k), int(y), int(x), float(s)) for k, y, x, s in zip(ks, ys, xs, ss)]
+    for world in (2, 3, 4, 6, 12):
+        lists = []
+        for r in range(world):
+            k0, nk = shard.angle_block(TIE_NTH, world, r)
+            lists.append(shard.block_candidates(k0, nk, TIE_NTH, TIE_H, TIE_W, 0.25, 40, score_fn, cand_fn))
+        assert shard.merge_candidates(lists, 40, TIE_H, TIE_W) == want, world
