@@ -547,8 +547,11 @@ sam_status sam_score_bilinear_adjoint(sam_model *m, int level, const sam_field_r
  *   maps    device scratch of sam_response_maps_bytes(w, h, nbins) bytes
  *           (holds the response maps after the call).
  *   map     device float array of num_angles(level) * h * w.
- * Two launches, stream-ordered; the first call per (level, nbins) builds the
- * bin table (a synchronous upload).  Errors: SAM_ERR_ARG, SAM_ERR_NOMEM,
+ * Two launches, stream-ordered.  The first call per (level, nbins) builds
+ * the bin table on the host, allocates its device copy (cudaMalloc; held by
+ * the model until sam_free_model) and uploads it on `stream`: make that
+ * first call outside stream capture.  A scaled model's tables are binned per
+ * table (scale and angle).  Errors: SAM_ERR_ARG, SAM_ERR_NOMEM,
  * SAM_ERR_CUDA. */
 size_t sam_response_maps_bytes(int w, int h, int nbins);
 sam_status sam_score_map_quantized(sam_model *m, int level, const float *field, int w, int h, int nbins,

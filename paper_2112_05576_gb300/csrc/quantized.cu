@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "sam_internal.h"
@@ -93,7 +94,8 @@ std::vector<uint8_t> quant_bins(const LevelHost &L, int nbins, int polarity) {
     std::vector<uint8_t> out((size_t)L.ntheta * L.n);
     const double width = (polarity ? M_PI : 2.0 * M_PI) / nbins;
     for (int k = 0; k < L.ntheta; ++k) {
-        const double th = ((double)k * L.dtheta) * M_PI / 180.0;
+        // table k: scale k / nangles (directions do not depend on it), angle k mod nangles
+        const double th = ((double)(k % L.nangles) * L.dtheta) * M_PI / 180.0;
         const double c = cos(th), s = sin(th);
         for (int i = 0; i < L.n; ++i) {
             const double m = sqrt((double)L.gx[i] * L.gx[i] + (double)L.gy[i] * L.gy[i]);
@@ -111,7 +113,12 @@ std::vector<uint8_t> quant_bins(const LevelHost &L, int nbins, int polarity) {
     return out;
 }
 
-const uint8_t *bins_table(sam_model *m, int level, int nbins) {
+// The model's device bin table of (level, nbins), built and uploaded (on
+// `st`, behind the call's later launches) on first use; the model's table
+// list is guarded so that host threads sharing a model do not race on it.
+const uint8_t *bins_table(sam_model *m, int level, int nbins, cudaStream_t st) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     const int key = nbins * 2 + (m->p.polarity ? 1 : 0);
     for (const auto &q : m->qbins)
         if (q.level == level && q.nbins == key)
@@ -120,7 +127,8 @@ const uint8_t *bins_table(sam_model *m, int level, int nbins) {
     uint8_t *d = nullptr;
     if (cudaMalloc(&d, h.size()) != cudaSuccess)
         return nullptr;
-    if (cudaMemcpy(d, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    // pageable source: the copy is staged before the call returns
+    if (cudaMemcpyAsync(d, h.data(), h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaFree(d);
         return nullptr;
     }
@@ -149,7 +157,7 @@ extern "C" sam_status sam_score_map_quantized(sam_model *m, int level, const flo
     sam_status s = upload_model(m);
     if (s != SAM_OK)
         return s;
-    const uint8_t *bins = bins_table(m, level, nbins);
+    const uint8_t *bins = bins_table(m, level, nbins, (cudaStream_t)stream);
     if (!bins)
         return SAM_ERR_NOMEM;
     const int pol = m->p.polarity ? 1 : 0;
