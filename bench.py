@@ -555,12 +555,19 @@ def run_storage_forms(args, sam, torch, dev, stream, model, batch):
         fields[name] = (prec, fl, fl[0].numel() * fl[0].element_size())
     maps = [torch.empty((nth, th, tw), dtype=torch.float32, device=dev) for _ in imgs]
     out = {"what": f"sam_score_map of the {tw}x{th} top level, {nth} angles, {n} points, of {len(imgs)} config-2 "
-                   "scenes, one call per scene; error = max |M - M_fp32| over every pose (early termination off)",
+                   "scenes, one call per scene, each form with the tiling the autotuner picks for it (one image "
+                   "per call; angle codes take the FP32 tiling); error = max |M - M_fp32| over every pose (early "
+                   "termination off)",
            "pose_points_per_map": nth * th * tw * n}
     ref = None
+    one = batch[:1].contiguous()
     for early in (0, 1):
         key = "early_termination" if early else "every_pose"
         out[key] = {}
+        # the scorer's tiling for one image per call, per stored form and mode
+        for prec in (sam.FP32, sam.BF16):
+            sam.autotune(model, one, sam.default_detect_params(min_score=MIN_SCORE, neighbourhood=3, precision=prec,
+                                                               early_termination=early))
         for name, (prec, fl, fbytes) in fields.items():
             def call(i, prec=prec, fl=fl, early=early):
                 j = i % len(fl)
@@ -570,7 +577,8 @@ def run_storage_forms(args, sam, torch, dev, stream, model, batch):
                 call(i)
             ms = _event_ms(torch, dev, stream, call, 4 * len(imgs))
             res = {"ms_per_map": round(ms, 4), "value": out["pose_points_per_map"] / (ms * 1e-3), "unit": UNIT,
-                   "field_bytes": int(fbytes)}
+                   "field_bytes": int(fbytes),
+                   "tiling": list(sam.model_tiling(model, sam.FP32 if prec == sam.ANGLE16 else prec, 1))}
             if not early:
                 cur = torch.stack(maps).cpu().numpy()
                 if name == "fp32":
