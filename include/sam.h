@@ -409,7 +409,9 @@ sam_status sam_autotune(sam_model *m, const uint8_t *img, int count, size_t imag
                         const sam_detect_params *params, void *stream, int32_t *cfg_out, float *ms_out, int max_out,
                         int *n_out);
 /* The tiling the model's next calls with field `precision` over `count`
- * images will use (tuned, else the default; the paper has no counterpart).
+ * images will use (a process-wide selection set by sam_set_score_kernel
+ * overrides the model's tuning; tuned, else the default; the paper has no
+ * counterpart).
  * All outputs host ints.  Errors: SAM_ERR_ARG (NULL model or output,
  * precision out of range, count < 1). */
 sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_t *sx, int32_t *sy, int32_t *tg,

@@ -923,8 +923,10 @@ sam_status sam_model_tiling(const sam_model *m, int precision, int count, int32_
                             int32_t *warps, int32_t *cols) {
     if (!m || !sx || !sy || !tg || !warps || !cols || precision < SAM_FP32 || precision > SAM_FP16 || count < 1)
         return SAM_ERR_ARG;
-    const TileConfig *t = tuned_tiling(m, precision, count);
-    const TileConfig c = t ? *t : score_choice().cfg;
+    // a process-wide tiled selection overrides the model's tuning
+    const ScoreChoice &sc = score_choice();
+    const TileConfig *t = sc.kernel == 0 ? tuned_tiling(m, precision, count) : nullptr;
+    const TileConfig c = t ? *t : sc.cfg;
     *sx = c.sx;
     *sy = c.sy;
     *tg = c.tg;
