@@ -115,6 +115,7 @@ struct Plan {
     size_t off_rescore = 0;          // FP32 rescoring list (16-bit precisions)
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
     size_t off_queue = 0, queue_bytes = 0;   // persistent-form storage of the tiled scorer
+    size_t off_hot = 0, hot_cap = 0;         // the persistent scorer's hot list (entries of 8 bytes)
     size_t total = 0;
 };
 
@@ -184,6 +185,15 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
         P.off_queue = off;
         P.queue_bytes = drain_queue_bytes(count, P.gw, P.gh, P.nth);
         off += al(P.queue_bytes);
+        // hot list: every pose for a 16-bit map (the rescoring must see all
+        // of them), a sixteenth of the poses for FP32 (an overflow only
+        // sends candidate extraction back to the whole map)
+        const size_t poses = P.map_img * count;
+        P.hot_cap = p.precision == SAM_FP32 ? std::min(poses, std::max<size_t>(65536, poses / 16)) : poses;
+        if (P.hot_cap > 0xFFFFFFFFull)
+            P.hot_cap = 0;
+        P.off_hot = off;
+        off += al(P.hot_cap * 8);
     }
     P.total = off;
     return P;
@@ -274,6 +284,11 @@ ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_par
     sa.count = P.count;
     sa.queue = P.queue_bytes ? ws + P.off_queue : nullptr;
     sa.queue_bytes = P.queue_bytes;
+    if (P.hot_cap) {
+        sa.hot = (uint2 *)(ws + P.off_hot);
+        sa.hot_cap = (unsigned)P.hot_cap;
+        sa.hot_thr = p.precision == SAM_FP32 ? p.min_score : p.min_score - rescore_delta(p.precision);
+    }
     return sa;
 }
 
@@ -284,13 +299,24 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     const int count = P.count, top = P.L - 1;
     // (c) exhaustive top-level score map; a 16-bit map is rescored in FP32
     // wherever a pose can reach min_score
-    const ScoreArgs sa = top_score_args(m, P, p);
+    ScoreArgs sa = top_score_args(m, P, p);
+    bool hot_made = false;
+    sa.hot_made = &hot_made;
     prof_begin(2, st);
     SAM_CU(launch_score_map(m, top, sa, nullptr, st));
-    if (p.precision != SAM_FP32)
-        SAM_CU(launch_rescore(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
-                              P.h[top], p.step_x, p.step_y, count, p.neighbourhood, m->p.polarity, p.min_score,
-                              p.precision, sa.map, P.map_img, ws + P.off_rescore, P.map_img * count, st));
+    // the persistent scorer's hot list, when it made one: the poses that
+    // rescoring and candidate extraction have to look at
+    const unsigned *hot_cnt = hot_made ? (const unsigned *)(ws + P.off_queue) + kHotCounter : nullptr;
+    if (p.precision != SAM_FP32) {
+        if (hot_cnt)
+            SAM_CU(launch_rescore_hot(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
+                                      P.h[top], p.neighbourhood, m->p.polarity, sa.map, P.map_img, hot_cnt, sa.hot,
+                                      sa.hot_cap, st));
+        else
+            SAM_CU(launch_rescore(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
+                                  P.h[top], p.step_x, p.step_y, count, p.neighbourhood, m->p.polarity, p.min_score,
+                                  p.precision, sa.map, P.map_img, ws + P.off_rescore, P.map_img * count, st));
+    }
     prof_end(2, st);
     // (d) candidates, refinement, NMS
     const int K = p.top_k;
@@ -298,8 +324,12 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     float *cs = (float *)(ws + P.off_cs);
     int *ccount = (int *)(ws + P.off_ccount);
     prof_begin(3, st);
-    SAM_CU(launch_candidates(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
-                             ws + P.off_scratch, 0, count, st, m->nscales));
+    if (hot_cnt)
+        SAM_CU(launch_candidates_hot(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
+                                     ws + P.off_scratch, count, hot_cnt, sa.hot, sa.hot_cap, st, m->nscales));
+    else
+        SAM_CU(launch_candidates(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
+                                 ws + P.off_scratch, 0, count, st, m->nscales));
     prof_end(3, st);
     RefineArgs ra;
     memset(&ra, 0, sizeof(ra));
@@ -489,7 +519,11 @@ cudaError_t launch_fast_scorer(const sam_model *m, int level, const ScoreArgs &a
     if (cfg.tg == 0)
         return launch_score_chunked(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
                                     a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window);
-    const DrainQueue q{a.queue, a.queue_bytes};
+    DrainQueue q{a.queue, a.queue_bytes};
+    q.hot = a.hot;
+    q.hot_cap = a.hot_cap;
+    q.hot_thr = a.hot_thr;
+    q.hot_made = a.hot_made;
     return launch_score_tiled(m, level, a.field, a.precision, wp, a.field_img_px, a.w, a.h, a.count, a.nbhd,
                               a.polarity, a.min_score, a.early, a.map, a.map_img, cfg, st, window,
                               a.queue && !window ? &q : nullptr);

@@ -137,6 +137,36 @@ __global__ void local_max_kernel(const float *__restrict__ map, size_t map_img, 
             push_candidate(map, idx, cand, cap, cnt);
 }
 
+// Candidates of `n_img` equal maps from a scorer's hot list: every pose the
+// scorer stored at or above the list's threshold (at most min_score), so
+// every entry at or above min_score is listed and the test runs on the
+// listed poses only.  A list that overflowed (count above hot_cap) is
+// ignored and every map scanned instead.  Grid-stride over the entries.
+__global__ void local_max_hot_kernel(const float *__restrict__ map, size_t map_img, int nth, int gh, int gw,
+                                     float min_score, Cand *__restrict__ cand, size_t cap, int *__restrict__ cnt,
+                                     int ns, const unsigned *__restrict__ hot_cnt, const uint2 *__restrict__ hot,
+                                     unsigned hot_cap, int n_img) {
+    const unsigned total = *hot_cnt;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (total <= hot_cap) {
+        for (size_t e = tid; e < total; e += stride) {
+            const uint2 h = hot[e];
+            const float *mi = map + (size_t)h.x * map_img;
+            if (is_candidate(mi, nth, gh, gw, min_score, h.y, ns))
+                push_candidate(mi, h.y, cand + (size_t)h.x * cap, cap, cnt + h.x);
+        }
+        return;
+    }
+    const size_t per = (size_t)nth * gh * gw;
+    for (size_t g = tid; g < per * (size_t)n_img; g += stride) {
+        const size_t img = g / per, idx = g - img * per;
+        const float *mi = map + img * map_img;
+        if (is_candidate(mi, nth, gh, gw, min_score, idx, ns))
+            push_candidate(mi, idx, cand + img * cap, cap, cnt + img);
+    }
+}
+
 // The same over a job list of maps of different sizes (job blockIdx.y).
 __global__ void local_max_jobs_kernel(const CandJob *__restrict__ jobs, float min_score) {
     const CandJob j = jobs[blockIdx.y];
@@ -590,6 +620,25 @@ cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh,
     const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total / 4 + 255) / 256, (size_t)per_img));
     dim3 grid((unsigned)blocks, (unsigned)n_img);
     local_max_kernel<<<grid, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns, vec);
+    topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_candidates_hot(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
+                                  int32_t *out_kyx, float *out_s, int *count, void *scratch, int n_img,
+                                  const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap, cudaStream_t st,
+                                  int ns) {
+    const size_t cap = cand_cap(nth, gh, gw, ns);
+    int *cnt = reinterpret_cast<int *>(scratch);
+    Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n_img, st);
+    if (e != cudaSuccess)
+        return e;
+    // two CTAs per SM: a few thousand listed poses take one pass; the
+    // whole-map fallback strides over every map
+    local_max_hot_kernel<<<2 * 152, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns, hot_cnt,
+                                                  hot, hot_cap, n_img);
     topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
     count_launches(2);
     return cudaGetLastError();

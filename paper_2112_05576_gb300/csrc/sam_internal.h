@@ -209,6 +209,10 @@ struct ScoreArgs {
     int count;
     void *queue = nullptr;     // persistent-form storage of the tiled scorer (optional)
     size_t queue_bytes = 0;
+    uint2 *hot = nullptr;      // hot list of the persistent form (optional; see TiledArgs)
+    unsigned hot_cap = 0;
+    float hot_thr = 0.f;
+    bool *hot_made = nullptr;  // set true when the scorer fills the hot list
 };
 cudaError_t launch_score_map_generic(const LevelDev &L, const ScoreArgs &a, cudaStream_t st);
 
@@ -235,7 +239,13 @@ constexpr int kStageScoreBound = 6;   // the tiled scorer's launch (inside stage
 struct DrainQueue {
     void *base;    // 256-byte aligned
     size_t bytes;
+    uint2 *hot = nullptr;        // hot-list entries (optional; see TiledArgs)
+    unsigned hot_cap = 0;
+    float hot_thr = 0.f;
+    bool *hot_made = nullptr;    // set true when the launch fills the hot list
 };
+// Index of the hot-list counter among the persistent form's counters.
+constexpr int kHotCounter = 8;
 // Workspace bytes that cover the persistent form of every tiling the
 // autotuner tries for a gw x gh map with nth angles over `count` images.
 size_t drain_queue_bytes(int count, int gw, int gh, int nth);
@@ -275,6 +285,14 @@ struct TiledArgs {
     unsigned *qctr;             // [0] entries, [1] tasks, [2] next task, [3] next unit, [4] units done
     unsigned qcap, tcap;        // capacities (entries, tasks)
     int units;                  // work units (super-tile x angle group x image)
+    // Hot list (persistent form only; hot_cnt null: none): every pose the
+    // drain stores with a score >= hot_thr, as {image, map index}; the
+    // counter is qctr[8] (zeroed with the other counters).  A count above
+    // hot_cap means the list overflowed (entries past it are not written).
+    unsigned *hot_cnt;
+    uint2 *hot;
+    unsigned hot_cap;
+    float hot_thr;
 };
 
 
@@ -395,6 +413,13 @@ cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t fiel
                            int step_y, int count, int nbhd, int polarity, float min_score, int precision, float *map,
                            size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st,
                            const PoseWindow *window = nullptr);
+// FP32 rescoring of the poses of a 16-bit scorer's hot list (threshold
+// min_score - rescore_delta, capacity every pose of the maps, so it cannot
+// overflow); the other poses keep their 16-bit scores, which are below
+// min_score - delta and so below the FP32 score of any pose >= min_score.
+cudaError_t launch_rescore_hot(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h,
+                               int nbhd, int polarity, float *map, size_t map_img, const unsigned *hot_cnt,
+                               const uint2 *hot, unsigned hot_cap, cudaStream_t st);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {
@@ -409,6 +434,13 @@ size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img, int ns
 cudaError_t launch_candidates(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
                               int32_t *out_kyx, float *out_s, int *count, void *scratch, size_t scratch_img,
                               int n_img, cudaStream_t st, int ns = 1);
+// The same from a scorer's hot list (hot_cnt, hot, hot_cap; the list's
+// threshold at most min_score): the listed poses only, or every map if the
+// list overflowed.
+cudaError_t launch_candidates_hot(const float *map, size_t map_img, int nth, int gh, int gw, float min_score, int K,
+                                  int32_t *out_kyx, float *out_s, int *count, void *scratch, int n_img,
+                                  const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap, cudaStream_t st,
+                                  int ns = 1);
 
 // (d) refinement down the pyramid + NMS
 struct RefineArgs {

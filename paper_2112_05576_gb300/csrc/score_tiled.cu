@@ -245,6 +245,10 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
     a.qctr = nullptr;
     a.qcap = a.tcap = 0;
     a.units = (int)(grid.x * grid.y * grid.z);
+    a.hot_cnt = nullptr;
+    a.hot = nullptr;
+    a.hot_cap = 0;
+    a.hot_thr = 0.f;
     if (queue && queue->base && a.emin > 0 && L.n < 65536) {
         const size_t items = (size_t)cfg.tg * cfg.sx * cfg.sy;
         const size_t rounds = (items + 127) / 128;
@@ -264,6 +268,15 @@ cudaError_t launch_score_tiled(const sam_model *m, int level, const void *field,
             cudaError_t e = cudaMemsetAsync(b, 0, 256 + tcap * 16, st);
             if (e != cudaSuccess)
                 return e;
+            // the hot list (map indices must fit 32 bits)
+            if (queue->hot && queue->hot_cap && map_img <= 0xFFFFFFFFull) {
+                a.hot_cnt = a.qctr + kHotCounter;
+                a.hot = queue->hot;
+                a.hot_cap = queue->hot_cap;
+                a.hot_thr = queue->hot_thr;
+                if (queue->hot_made)
+                    *queue->hot_made = true;
+            }
         }
     }
     // the edge bitmaps follow the window; the persistent form reuses their

@@ -294,6 +294,12 @@ struct TileWork {
     unsigned *qctr;
     unsigned qcap, tcap;
     int unit;                   // this CTA's work unit
+    // hot list (hot_cnt null: none): see TiledArgs
+    unsigned *hot_cnt;
+    uint2 *hot;
+    unsigned hot_cap;
+    float hot_thr;
+    unsigned img;               // image (or pair) index of the hot entries
 };
 
 // Quadrant of a non-zero vector: 0 for angles in [0, 90) degrees, 1 for
@@ -544,6 +550,11 @@ __device__ __forceinline__ TileWork tile_work(const TiledArgs &a, int img) {
     t.qcap = a.qcap;
     t.tcap = a.tcap;
     t.unit = 0;
+    t.hot_cnt = a.hot_cnt;
+    t.hot = a.hot;
+    t.hot_cap = a.hot_cap;
+    t.hot_thr = a.hot_thr;
+    t.img = (unsigned)img;
     return t;
 }
 
@@ -858,6 +869,40 @@ __device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int
     }
 }
 
+// The poses of one lane's stored slice (map position xl, yl of angle k)
+// whose score, rounded exactly as block_store stores it, is at least
+// t.hot_thr, appended to the hot list as {image, map index}: one atomic per
+// lane that has such poses.  Entries past the capacity are counted, not
+// written (the readers then fall back to the whole map).
+template <int TC, int R>
+__device__ __forceinline__ void hot_append(const TileWork &t, int k, int xl, int yl, const float2 (&acc)[R][TC / 2]) {
+    static_assert(R * TC <= 32, "one bit per pose of the slice");
+    uint32_t m = 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < TC / 2; ++j) {
+            const bool row_in = yl + r < t.H;
+            const int x = xl + 2 * j;
+            if (row_in && x < t.W && acc[r][j].x * t.inv_n >= t.hot_thr)
+                m |= 1u << (r * TC + 2 * j);
+            if (row_in && x + 1 < t.W && acc[r][j].y * t.inv_n >= t.hot_thr)
+                m |= 1u << (r * TC + 2 * j + 1);
+        }
+    if (!m)
+        return;
+    unsigned pos = atomicAdd(t.hot_cnt, (unsigned)__popc(m));
+    const size_t plane = (size_t)(k - t.k0) * t.H * t.W;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        const int r = b / TC, c = b - r * TC;
+        if (pos < t.hot_cap)
+            t.hot[pos] = make_uint2(t.img, (unsigned)(plane + (size_t)(yl + r) * t.W + xl + c));
+        ++pos;
+    }
+}
+
 // -inf over a WTX x WTY region of the map at (xl, yl), clipped to the map,
 // by the 32 lanes of a warp: rows in 16-byte chunks (one float4 store per
 // lane and chunk, a warp instruction covering 512 contiguous bytes of a row
@@ -913,6 +958,8 @@ __device__ __forceinline__ void score_slice(const typename Pairs<E>::Raw *win, i
         executed += (unsigned long long)done * (vx * vy);
         block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n,
                             pruned);
+        if (a.hot_cnt && !pruned)
+            hot_append<TC, RD>(a, k, x0 - a.ox, y0 - a.oy, acc);
     }
 }
 
@@ -952,6 +999,8 @@ __device__ __forceinline__ void slice_store(int item, int src, int part, int stx
     const int x0 = stx0 + (wt % a.sx) * WTX + (src % LX) * TC;
     const int y0 = sty0 + (wt / a.sx) * WTY + (src / LX) * TR + part * RD;
     block_store<TC, RD>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n, false);
+    if (a.hot_cnt)
+        hot_append<TC, RD>(a, k, x0 - a.ox, y0 - a.oy, acc);
 }
 
 // The (angle, warp tile) items of one CTA work unit over its staged window
@@ -1440,6 +1489,11 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         t.qctr = nullptr;
         t.qcap = t.tcap = 0;
         t.unit = 0;
+        t.hot_cnt = nullptr;
+        t.hot = nullptr;
+        t.hot_cap = 0;
+        t.hot_thr = 0.f;
+        t.img = (unsigned)s_unit[1];
         score_items<E, NB, POL, WARPS, TC>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
                                        min(group * tg + tg, P.nth), t);
         __syncthreads();   // every warp is done with the window before the next copy
