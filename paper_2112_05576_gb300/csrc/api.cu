@@ -241,14 +241,15 @@ sam_status prepare_fields(sam_model *m, const Plan &P, const uint8_t *img0, int 
     lvl_bytes[0] = img0_bytes;
     // (b) pyramid
     prof_begin(0, st);
+    uint8_t *dsts[kMaxLevels] = {};
     for (int l = 1; l < P.L; ++l) {
-        uint8_t *dst = (uint8_t *)(ws + P.off_img[l]);
-        SAM_CU(launch_pyramid_down(lvl_img[l - 1], P.w[l - 1], P.h[l - 1], lvl_pitch[l - 1], lvl_bytes[l - 1], dst,
-                                   P.pitch[l], P.img_bytes[l], count, st));
-        lvl_img[l] = dst;
+        dsts[l] = (uint8_t *)(ws + P.off_img[l]);
+        lvl_img[l] = dsts[l];
         lvl_pitch[l] = P.pitch[l];
         lvl_bytes[l] = P.img_bytes[l];
     }
+    SAM_CU(launch_pyramid_levels(img0, P.w[0], P.h[0], pitch0, img0_bytes, P.L - 1, dsts, lvl_pitch, lvl_bytes, count,
+                                 st));
     prof_end(0, st);
     // (a) gradients: FP32 pixel-layout fields for the refinement levels, the
     // top level in the pairs layout and the detection precision
@@ -307,16 +308,12 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     // the persistent scorer's hot list, when it made one: the poses that
     // rescoring and candidate extraction have to look at
     const unsigned *hot_cnt = hot_made ? (const unsigned *)(ws + P.off_queue) + kHotCounter : nullptr;
-    if (p.precision != SAM_FP32) {
-        if (hot_cnt)
-            SAM_CU(launch_rescore_hot(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
-                                      P.h[top], p.neighbourhood, m->p.polarity, sa.map, P.map_img, hot_cnt, sa.hot,
-                                      sa.hot_cap, st));
-        else
-            SAM_CU(launch_rescore(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
-                                  P.h[top], p.step_x, p.step_y, count, p.neighbourhood, m->p.polarity, p.min_score,
-                                  p.precision, sa.map, P.map_img, ws + P.off_rescore, P.map_img * count, st));
-    }
+    // a 16-bit map without a hot list is rescored in FP32 wherever a pose
+    // can reach min_score; with one, candidate extraction decides in FP32
+    if (p.precision != SAM_FP32 && !hot_cnt)
+        SAM_CU(launch_rescore(m->dev[top], (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top],
+                              P.h[top], p.step_x, p.step_y, count, p.neighbourhood, m->p.polarity, p.min_score,
+                              p.precision, sa.map, P.map_img, ws + P.off_rescore, P.map_img * count, st));
     prof_end(2, st);
     // (d) candidates, refinement, NMS
     const int K = p.top_k;
@@ -324,7 +321,12 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
     float *cs = (float *)(ws + P.off_cs);
     int *ccount = (int *)(ws + P.off_ccount);
     prof_begin(3, st);
-    if (hot_cnt)
+    if (hot_cnt && p.precision != SAM_FP32)
+        SAM_CU(launch_candidates_hot16(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, rescore_delta(p.precision),
+                                       K, kyx, cs, ccount, ws + P.off_scratch, count, hot_cnt, sa.hot, sa.hot_cap,
+                                       (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top], P.h[top],
+                                       m->dev[top], p.neighbourhood, m->p.polarity, st, m->nscales));
+    else if (hot_cnt)
         SAM_CU(launch_candidates_hot(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
                                      ws + P.off_scratch, count, hot_cnt, sa.hot, sa.hot_cap, st, m->nscales));
     else
@@ -974,6 +976,25 @@ sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, ui
     if (!src || !dst || w < 0 || h < 0 || src_stride < w || dst_stride < w / 2)
         return SAM_ERR_ARG;
     return launch_pyramid_down(src, w, h, src_stride, 0, dst, dst_stride, 0, 1, (cudaStream_t)stream) == cudaSuccess
+               ? SAM_OK
+               : SAM_ERR_CUDA;
+}
+
+sam_status sam_pyramid_levels(const uint8_t *src, int w, int h, int src_stride, int levels, uint8_t *const *dst,
+                              const int *dst_stride, void *stream) {
+    if (!src || !dst || !dst_stride || w < 0 || h < 0 || src_stride < w || levels < 2 || levels > kMaxLevels)
+        return SAM_ERR_ARG;
+    uint8_t *d[kMaxLevels] = {};
+    int ds[kMaxLevels] = {};
+    size_t di[kMaxLevels] = {};
+    for (int l = 1; l < levels; ++l) {
+        if (!dst[l - 1] || dst_stride[l - 1] < (w >> l))
+            return SAM_ERR_ARG;
+        d[l] = dst[l - 1];
+        ds[l] = dst_stride[l - 1];
+    }
+    return launch_pyramid_levels(src, w, h, src_stride, 0, levels - 1, d, ds, di, 1, (cudaStream_t)stream) ==
+                   cudaSuccess
                ? SAM_OK
                : SAM_ERR_CUDA;
 }

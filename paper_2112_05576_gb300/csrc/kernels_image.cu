@@ -75,6 +75,79 @@ __global__ void pyramid_down_kernel(const uint8_t *__restrict__ src, int w, int 
                (blockIdx.x * blockDim.x + threadIdx.x) * 16);
 }
 
+// Every pyramid level below level 0 in one pass (levels 1 .. D, D <= 6):
+// one CTA per 128 x 64 block of level 0 (image blockIdx.z) computes its
+// 64 x 32 block of level 1 from 16-byte loads of level 0, then each further
+// level from the previous one held in shared memory.  A level-l pixel
+// depends only on the 2^l x 2^l level-0 pixels under it, so the blocks are
+// independent, and each level is the 2x2 rounded mean of the one above it
+// exactly as the one-step kernel computes it (floor of odd sizes
+// included).  Level l's image starts at dst[l] + image * dst_img[l], row
+// pitch dst_pitch[l] (a multiple of 16).
+constexpr int kPyrBW = 128, kPyrBH = 64;   // level-0 block
+struct PyramidLevels {
+    uint8_t *dst[kMaxLevels];
+    int pitch[kMaxLevels];
+    size_t img[kMaxLevels];
+};
+
+__global__ void __launch_bounds__(256) pyramid_levels_kernel(const uint8_t *__restrict__ src, int w, int h, int ss,
+                                                             size_t src_img, PyramidLevels out, int D, int vec) {
+    __shared__ __align__(16) uint8_t buf[2][(kPyrBW / 2) * (kPyrBH / 2)];
+    const int img = blockIdx.z, tid = threadIdx.x;
+    src += (size_t)img * src_img;
+    // level 1: 64 x 32 outputs, 8 per thread (row tid / 8, columns 8 (tid % 8) ..)
+    {
+        const int w1 = w >> 1, h1 = h >> 1;
+        const int r = tid >> 3, c = (tid & 7) * 8;
+        const int y = blockIdx.y * (kPyrBH / 2) + r, x0 = blockIdx.x * (kPyrBW / 2) + c;
+        uint32_t lo = 0u, hi = 0u;
+        if (y < h1 && x0 < w1) {
+            const uint8_t *r0 = src + (size_t)(2 * y) * ss + 2 * x0;
+            const uint8_t *r1 = r0 + ss;
+            uint8_t *o = out.dst[1] + (size_t)img * out.img[1] + (size_t)y * out.pitch[1] + x0;
+            if (vec && x0 + 8 <= w1) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4 *>(r0));
+                const uint4 b = __ldg(reinterpret_cast<const uint4 *>(r1));
+                lo = mean2x2_quad(a.x, a.y, b.x, b.y);
+                hi = mean2x2_quad(a.z, a.w, b.z, b.w);
+                *reinterpret_cast<uint2 *>(o) = make_uint2(lo, hi);
+            } else {
+                for (int j = 0; j < 8 && x0 + j < w1; ++j) {
+                    const uint32_t v = (r0[2 * j] + r0[2 * j + 1] + r1[2 * j] + r1[2 * j + 1] + 2) >> 2;
+                    o[j] = (uint8_t)v;
+                    if (j < 4)
+                        lo |= v << (8 * j);
+                    else
+                        hi |= v << (8 * (j - 4));
+                }
+            }
+        }
+        *reinterpret_cast<uint2 *>(&buf[0][r * (kPyrBW / 2) + c]) = make_uint2(lo, hi);
+    }
+    __syncthreads();
+    // levels 2 .. D from the previous level's block in shared memory
+    int lw = w >> 1, lh = h >> 1;
+    for (int l = 2; l <= D; ++l) {
+        const int pbw = kPyrBW >> (l - 1);          // previous block width
+        const int bw = pbw >> 1, bh = kPyrBH >> l;  // this block
+        lw >>= 1;
+        lh >>= 1;
+        const uint8_t *prev = buf[l & 1];
+        uint8_t *cur = buf[(l + 1) & 1];
+        for (int i = tid; i < bw * bh; i += 256) {
+            const int r = i / bw, c = i - r * bw;
+            const int y = blockIdx.y * bh + r, x = blockIdx.x * bw + c;
+            const uint8_t *p0 = prev + (2 * r) * pbw + 2 * c;
+            const uint8_t v = (uint8_t)((p0[0] + p0[1] + p0[pbw] + p0[pbw + 1] + 2) >> 2);
+            cur[i] = v;
+            if (y < lh && x < lw)
+                out.dst[l][(size_t)img * out.img[l] + (size_t)y * out.pitch[l] + x] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // One pyramid step of many images of different sizes: job blockIdx.z,
 // rows strided over gridDim.y.
 __global__ void pyramid_jobs_kernel(const ImageJob *__restrict__ jobs) {
@@ -536,6 +609,47 @@ cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride
     const int threads = 128;
     dim3 grid((unsigned)((w2 + 16 * threads - 1) / (16 * threads)), (unsigned)h2, (unsigned)count);
     pyramid_down_kernel<<<grid, threads, 0, st>>>(src, w, h, src_stride, src_img, dst, dst_stride, dst_img, vec);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid_levels(const uint8_t *src, int w, int h, int src_stride, size_t src_img, int D,
+                                  uint8_t *const *dst, const int *dst_stride, const size_t *dst_img, int count,
+                                  cudaStream_t st) {
+    if (D <= 0 || count <= 0)
+        return cudaSuccess;
+    if (D > 6 || (w >> 1) <= 0 || (h >> 1) <= 0) {
+        // deeper pyramids: one launch per level
+        const uint8_t *s = src;
+        int sw = w, sh = h, sp = src_stride;
+        size_t si = src_img;
+        for (int l = 1; l <= D; ++l) {
+            const cudaError_t e = launch_pyramid_down(s, sw, sh, sp, si, dst[l], dst_stride[l], dst_img[l], count, st);
+            if (e != cudaSuccess)
+                return e;
+            s = dst[l];
+            sw >>= 1;
+            sh >>= 1;
+            sp = dst_stride[l];
+            si = dst_img[l];
+        }
+        return cudaSuccess;
+    }
+    PyramidLevels out;
+    bool aligned = true;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        out.dst[l] = l >= 1 && l <= D ? dst[l] : nullptr;
+        out.pitch[l] = l >= 1 && l <= D ? dst_stride[l] : 0;
+        out.img[l] = l >= 1 && l <= D ? dst_img[l] : 0;
+        if (l >= 1 && l <= D)
+            aligned = aligned && ((uintptr_t)dst[l] % 16 == 0) && (dst_stride[l] % 16 == 0) &&
+                      (count == 1 || dst_img[l] % 16 == 0);
+    }
+    const int vec = aligned && ((uintptr_t)src % 16 == 0) && (src_stride % 16 == 0) &&
+                    (count == 1 || src_img % 16 == 0);
+    dim3 grid((unsigned)(((w >> 1) + kPyrBW / 2 - 1) / (kPyrBW / 2)), (unsigned)(((h >> 1) + kPyrBH / 2 - 1) / (kPyrBH / 2)),
+              (unsigned)count);
+    pyramid_levels_kernel<<<grid, 256, 0, st>>>(src, w, h, src_stride, src_img, out, D, vec);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -167,6 +167,219 @@ __global__ void local_max_hot_kernel(const float *__restrict__ map, size_t map_i
     }
 }
 
+// ---------------------------------------------------------------------------
+// candidates of a map scored from a 16-bit field, decided in FP32
+// ---------------------------------------------------------------------------
+//
+// The 16-bit map M16 is within delta (rescore_delta) of the FP32 score M32 at
+// every pose it did not prune, and the poses it pruned are below min_score in
+// FP32 too.  A pose p can be a strict local maximum of M32 at or above
+// min_score only if (i) M16(p) >= min_score - delta, so it is on the hot
+// list, and (ii) no neighbour q has M16(q) > M16(p) + 2 delta (else M32(q) >
+// M16(p) + delta >= M32(p)).  For each pose passing both, one CTA computes
+// M32 of the pose and of all its neighbours (per model point and angle one
+// (NB + 2)^2 window of field pixels serves the nine translations) and keeps
+// the pose if it beats every neighbour under the total order.  M32 of a pose
+// is the same function of the pose in every CTA (point i on thread i mod
+// 256, serial per thread, shuffle tree per warp, warps added in order), so
+// neighbouring CTAs agree.  The candidates are those of the FP32 map made of
+// these values.
+
+constexpr int kC16Threads = 256;
+
+struct Cand16Args {
+    const float *map;
+    size_t map_img;
+    int nth, gh, gw, ns;
+    float min_score, delta;
+    const unsigned *hot_cnt;
+    const uint2 *hot;
+    unsigned hot_cap;
+    const float2 *field;   // FP32 pixel-layout field of the scored level
+    size_t field_img_px;
+    int w, h;
+    const RotPt *rot;      // [nth][n]
+    int n, polarity;
+    Cand *cand;
+    size_t cap;
+    int *cnt;
+};
+
+// Whether no neighbour of map entry idx (the neighbourhood of is_candidate)
+// holds a value above `above`.
+__device__ __forceinline__ bool no_neighbour_above(const float *__restrict__ map, int nth, int gh, int gw, size_t idx,
+                                                   int ns, float above) {
+    const size_t plane = (size_t)gh * gw;
+    const int kk = (int)(idx / plane);
+    const int r = (int)(idx - (size_t)kk * plane);
+    const int y = r / gw, x = r - y * gw;
+    const int nang = nth / ns;
+    const int js = kk / nang, k = kk - js * nang;
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int j2 = js + dj;
+        if (j2 < 0 || j2 >= ns)
+            continue;
+        for (int dk = -1; dk <= 1; ++dk) {
+            if (dk != 0 && nang == 1)
+                continue;
+            const int k2 = j2 * nang + (k + dk + nang) % nang;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y2 = y + dy;
+                if (y2 < 0 || y2 >= gh)
+                    continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x2 = x + dx;
+                    if (x2 < 0 || x2 >= gw)
+                        continue;
+                    const size_t j = (size_t)k2 * plane + (size_t)y2 * gw + x2;
+                    if (j != idx && map[j] > above)
+                        return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a) {
+    __shared__ unsigned s_list[kC16Threads];        // hot entries of this round that pass the filter
+    __shared__ int s_n;
+    __shared__ float s_red[kC16Threads / 32][81];   // per-warp sums: plane d, translation q at 9 d + q
+    __shared__ float s_val[81];
+    const unsigned total = min(*a.hot_cnt, a.hot_cap);
+    const size_t G = gridDim.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const size_t plane = (size_t)a.gh * a.gw;
+    const int nang = a.nth / a.ns;
+    const float up = 2.f * a.delta;
+    // entry b + G (r0 + t) for thread t of CTA b: consecutive entries (often
+    // poses of one instance) go to different CTAs
+    for (size_t r0 = 0; blockIdx.x + G * r0 < total; r0 += kC16Threads) {
+        if (t == 0)
+            s_n = 0;
+        __syncthreads();
+        const size_t e = blockIdx.x + G * (r0 + t);
+        if (e < total) {
+            const uint2 hv = a.hot[e];
+            const float *m = a.map + (size_t)hv.x * a.map_img;
+            const float v = m[hv.y];
+            if (v >= a.min_score - a.delta && no_neighbour_above(m, a.nth, a.gh, a.gw, hv.y, a.ns, v + up))
+                s_list[atomicAdd(&s_n, 1)] = (unsigned)e;
+        }
+        __syncthreads();
+        const int np = s_n;
+        for (int ip = 0; ip < np; ++ip) {
+            const uint2 hv = a.hot[s_list[ip]];
+            const unsigned img = hv.x;
+            const size_t idx = hv.y;
+            const int kk = (int)(idx / plane);
+            const int rem = (int)(idx - (size_t)kk * plane);
+            const int y = rem / a.gw, x = rem - y * a.gw;
+            const int js = kk / nang, k = kk - js * nang;
+            // the neighbourhood's planes (scale j2, angle k2), the same list
+            // on every thread; dc is the pose's own plane
+            int kl[9];
+            int npl = 0, dc = 0;
+            for (int dj = -1; dj <= 1; ++dj) {
+                const int j2 = js + dj;
+                if (j2 < 0 || j2 >= a.ns)
+                    continue;
+                for (int dk = -1; dk <= 1; ++dk) {
+                    if (dk != 0 && nang == 1)
+                        continue;
+                    if (dj == 0 && dk == 0)
+                        dc = npl;
+                    kl[npl++] = j2 * nang + (k + dk + nang) % nang;
+                }
+            }
+            const float2 *F = a.field + (size_t)img * a.field_img_px;
+            for (int d = 0; d < npl; ++d) {
+                const RotPt *P = a.rot + (size_t)kl[d] * a.n;
+                float acc[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    acc[q] = 0.f;
+                for (int i = t; i < a.n; i += kC16Threads) {
+                    const RotPt p = P[i];
+                    const int bxp = x + p.ox, byp = y + p.oy;
+                    constexpr int D = NB + 2;
+                    float dd[D][D];
+#pragma unroll
+                    for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+                        for (int xx = 0; xx < D; ++xx) {
+                            const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
+                            float v = 0.f;
+                            if (X >= 0 && Y >= 0 && X < a.w && Y < a.h) {
+                                const float2 f = __ldg(F + (size_t)Y * a.w + X);
+                                v = fmaf(p.px, f.x, p.py * f.y);
+                                if (a.polarity)
+                                    v = fabsf(v);
+                            }
+                            dd[yy][xx] = v;
+                        }
+#pragma unroll
+                    for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+                        for (int tx = 0; tx < 3; ++tx) {
+                            float mx = -INFINITY;
+#pragma unroll
+                            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                                for (int aa = 0; aa < NB; ++aa)
+                                    mx = fmaxf(mx, dd[ty + b][tx + aa]);
+                            acc[ty * 3 + tx] += mx;
+                        }
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    float v = acc[q];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0)
+                        s_red[warp][d * 9 + q] = v;
+                }
+            }
+            __syncthreads();
+            if (t < npl * 9) {
+                float v = 0.f;
+                for (int wv = 0; wv < kC16Threads / 32; ++wv)
+                    v += s_red[wv][t];
+                s_val[t] = v / (float)a.n;
+            }
+            __syncthreads();
+            if (t == 0) {
+                const float sp = s_val[dc * 9 + 4];
+                bool ok = sp >= a.min_score;
+                for (int d = 0; d < npl && ok; ++d)
+                    for (int q = 0; q < 9; ++q) {
+                        const int X = x + q % 3 - 1, Y = y + q / 3 - 1;
+                        if (X < 0 || Y < 0 || X >= a.gw || Y >= a.gh)
+                            continue;
+                        const size_t key = (size_t)kl[d] * plane + (size_t)Y * a.gw + X;
+                        if (key != idx && !beats(sp, idx, s_val[d * 9 + q], key)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                if (ok) {
+                    const int pos = atomicAdd(a.cnt + img, 1);
+                    if ((size_t)pos < a.cap) {
+                        Cand c;
+                        c.s = sp;
+                        c.pad = 0;
+                        c.key = idx;
+                        a.cand[(size_t)img * a.cap + pos] = c;
+                    }
+                }
+            }
+            __syncthreads();   // s_red and s_val are reused by the next pose
+        }
+    }
+}
+
 // The same over a job list of maps of different sizes (job blockIdx.y).
 __global__ void local_max_jobs_kernel(const CandJob *__restrict__ jobs, float min_score) {
     const CandJob j = jobs[blockIdx.y];
@@ -639,6 +852,50 @@ cudaError_t launch_candidates_hot(const float *map, size_t map_img, int nth, int
     // whole-map fallback strides over every map
     local_max_hot_kernel<<<2 * 152, 256, 0, st>>>(map, map_img, nth, gh, gw, min_score, cand, cap, cnt, ns, hot_cnt,
                                                   hot, hot_cap, n_img);
+    topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, int gh, int gw, float min_score,
+                                    float delta, int K, int32_t *out_kyx, float *out_s, int *count, void *scratch,
+                                    int n_img, const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                    const float2 *field32, size_t field_img_px, int w, int h, const LevelDev &L,
+                                    int nbhd, int polarity, cudaStream_t st, int ns) {
+    const size_t cap = cand_cap(nth, gh, gw, ns);
+    int *cnt = reinterpret_cast<int *>(scratch);
+    Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)n_img, st);
+    if (e != cudaSuccess)
+        return e;
+    Cand16Args a;
+    a.map = map;
+    a.map_img = map_img;
+    a.nth = nth;
+    a.gh = gh;
+    a.gw = gw;
+    a.ns = ns;
+    a.min_score = min_score;
+    a.delta = delta;
+    a.hot_cnt = hot_cnt;
+    a.hot = hot;
+    a.hot_cap = hot_cap;
+    a.field = field32;
+    a.field_img_px = field_img_px;
+    a.w = w;
+    a.h = h;
+    a.rot = L.rot;
+    a.n = L.n;
+    a.polarity = polarity;
+    a.cand = cand;
+    a.cap = cap;
+    a.cnt = cnt;
+    // eight resident CTAs per SM: the few poses that pass the filter are
+    // spread one or two per CTA
+    if (nbhd == 3)
+        cand16_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(a);
+    else
+        cand16_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(a);
     topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
     count_launches(2);
     return cudaGetLastError();

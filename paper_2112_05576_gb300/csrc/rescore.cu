@@ -201,23 +201,6 @@ cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t fiel
     return cudaGetLastError();
 }
 
-// The listed poses of a hot list are {image, map index} pairs, the layout of
-// the rescoring list above, so the same kernel scores them.
-cudaError_t launch_rescore_hot(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h,
-                               int nbhd, int polarity, float *map, size_t map_img, const unsigned *hot_cnt,
-                               const uint2 *hot, unsigned hot_cap, cudaStream_t st) {
-    const unsigned *list = reinterpret_cast<const unsigned *>(hot);
-    const unsigned blocks = 152 * 8;
-    if (nbhd == 3)
-        rescore_kernel<3><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, w, h, 1, 1, 0, 0, 0, L.rot, L.n,
-                                                  polarity, map, map_img, list, hot_cnt, hot_cap);
-    else
-        rescore_kernel<1><<<blocks, 256, 0, st>>>(field32, field_img_px, w, h, w, h, 1, 1, 0, 0, 0, L.rot, L.n,
-                                                  polarity, map, map_img, list, hot_cnt, hot_cap);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 }  // namespace sam
 
 namespace sam {

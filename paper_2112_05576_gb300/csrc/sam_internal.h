@@ -172,6 +172,11 @@ cudaError_t launch_gradient_jobs(const ImageJob *jobs, int n_jobs, int max_w, in
 // (b) pyramid step; `count` images, image i at src + i*src_img / dst + i*dst_img
 cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
                                 int dst_stride, size_t dst_img, int count, cudaStream_t st);
+// Levels 1 .. D of `count` images in one launch (D <= 6; deeper pyramids take
+// one launch per level): dst[l], dst_stride[l], dst_img[l] for l = 1 .. D.
+cudaError_t launch_pyramid_levels(const uint8_t *src, int w, int h, int src_stride, size_t src_img, int D,
+                                  uint8_t *const *dst, const int *dst_stride, const size_t *dst_img, int count,
+                                  cudaStream_t st);
 // (a) gradient / threshold / normalise; field image i at field + i*field_img_px pixels
 cudaError_t launch_gradient(const uint8_t *img, int w, int h, int stride, size_t img_bytes, int low, int precision,
                             int layout, void *field, size_t field_img_px, int16_t *gx, int16_t *gy, int count,
@@ -413,13 +418,16 @@ cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t fiel
                            int step_y, int count, int nbhd, int polarity, float min_score, int precision, float *map,
                            size_t map_img, void *scratch, size_t poses_cap, cudaStream_t st,
                            const PoseWindow *window = nullptr);
-// FP32 rescoring of the poses of a 16-bit scorer's hot list (threshold
-// min_score - rescore_delta, capacity every pose of the maps, so it cannot
-// overflow); the other poses keep their 16-bit scores, which are below
-// min_score - delta and so below the FP32 score of any pose >= min_score.
-cudaError_t launch_rescore_hot(const LevelDev &L, const float2 *field32, size_t field_img_px, int w, int h,
-                               int nbhd, int polarity, float *map, size_t map_img, const unsigned *hot_cnt,
-                               const uint2 *hot, unsigned hot_cap, cudaStream_t st);
+// Candidates of a map scored from a 16-bit field, from its scorer's hot list
+// (threshold min_score - delta, capacity every pose): the poses whose 16-bit
+// score is within 2 delta of every neighbour's are rescored in FP32 with
+// their whole neighbourhood (field32: the level's FP32 pixel-layout field)
+// and kept if they are strict local maxima of the FP32 scores.
+cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, int gh, int gw, float min_score,
+                                    float delta, int K, int32_t *out_kyx, float *out_s, int *count, void *scratch,
+                                    int n_img, const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                    const float2 *field32, size_t field_img_px, int w, int h, const LevelDev &L,
+                                    int nbhd, int polarity, cudaStream_t st, int ns = 1);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {
