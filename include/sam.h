@@ -275,9 +275,10 @@ sam_status sam_multi_stats(const sam_multi *mp, long long *pose_points, long lon
 /* Copy of pair `pair`'s top-level score map, for inspection (the paper has
  * no counterpart).  The map is FP32 [nth][gh][gw], pose (x, y, theta_k) at
  * [k][y][x], and holds what the plan's last run (sam_multi_run or an
- * autotuning run) left in it: Eq. (1) scores, -inf for poses pruned by early
- * termination, and with a 16-bit field the FP32 rescores of the poses within
- * the storage bound of min_score (-inf for the others).
+ * autotuning run) left in it: Eq. (1) scores (with a 16-bit field, the
+ * scorer's 16-bit-field scores, within the storage bound 8e-4 (FP16) or 6e-3
+ * (BF16) of the FP32 ones; candidate extraction decides on FP32 rescores of
+ * its own), -inf for poses pruned by early termination.
  *   dst       device float array of `capacity` >= nth * gh * gw entries, or
  *             NULL to read the shape only.
  *   nth, gh, gw, level  optional host outputs: the map's shape and the
@@ -297,6 +298,16 @@ sam_status sam_multi_pair_map(const sam_multi *mp, int pair, float *dst, size_t 
  * x < w/2, y < h/2.  src, dst device; dst pitch dst_stride >= w/2. */
 sam_status sam_pyramid_down(const uint8_t *src, int w, int h, int src_stride, uint8_t *dst, int dst_stride,
                             void *stream);
+
+/* The whole image pyramid (Sec. II) in one launch: levels 1 .. levels-1 of
+ * a w x h device image, level l the pyramid step of level l - 1 (sizes
+ * floor(w / 2^l) x floor(h / 2^l)), written to dst[l - 1] with row pitch
+ * dst_stride[l - 1] (>= the level's width); dst and dst_stride are host
+ * arrays of levels - 1 entries, the buffers device memory.  Identical to
+ * levels - 1 calls of sam_pyramid_down; the detection pipeline uses it.
+ * 2 <= levels <= 8.  Errors: SAM_ERR_ARG, SAM_ERR_CUDA. */
+sam_status sam_pyramid_levels(const uint8_t *src, int w, int h, int src_stride, int levels, uint8_t *const *dst,
+                              const int *dst_stride, void *stream);
 
 /* Edge extraction (Sec. II) of a device image: 3x3 Sobel gx, gy (zero on the
  * 1-pixel border), edge iff gx^2+gy^2 >= 16 low^2, and the unit field

@@ -116,7 +116,20 @@ struct Plan {
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
     size_t off_queue = 0, queue_bytes = 0;   // persistent-form storage of the tiled scorer
     size_t off_hot = 0, hot_cap = 0;         // the persistent scorer's hot list (entries of 8 bytes)
+    // refinement-level gradient tiles computed on demand: one mask bit and
+    // one list entry per tile of levels 0 .. L - 2 of every image
+    int tiles_x[kMaxLevels] = {}, tiles_y[kMaxLevels] = {};
+    size_t tile_base[kMaxLevels] = {};
+    size_t tiles = 0, off_tmask = 0, tmask_bytes = 0, off_tlist = 0;
     size_t total = 0;
+};
+
+// Level images of one call: level 0 where the caller's (or the copied)
+// images are, the others in the workspace.
+struct LevelImgs {
+    const uint8_t *img[kMaxLevels];
+    int pitch[kMaxLevels];
+    size_t bytes[kMaxLevels];
 };
 
 sam_status check_detect_params(const sam_model *m, const sam_detect_params *p) {
@@ -195,6 +208,22 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
         P.off_hot = off;
         off += al(P.hot_cap * 8);
     }
+    {
+        const int TW = gradient_tile_w(), TH = gradient_tile_h();
+        size_t tiles = 0;
+        for (int l = 0; l < top; ++l) {
+            P.tiles_x[l] = (P.w[l] + TW - 1) / TW;
+            P.tiles_y[l] = (P.h[l] + TH - 1) / TH;
+            P.tile_base[l] = tiles;
+            tiles += (size_t)P.tiles_x[l] * P.tiles_y[l] * count;
+        }
+        P.tiles = tiles;
+        P.off_tmask = off;
+        P.tmask_bytes = (tiles + 31) / 32 * 4 + 4;   // the mask words, then the list counter
+        off += al(P.tmask_bytes);
+        P.off_tlist = off;
+        off += al(std::max<size_t>(1, tiles) * 8);
+    }
     P.total = off;
     return P;
 }
@@ -230,7 +259,7 @@ sam_status ensure_workspace(sam_model *m, size_t bytes) {
 // Pyramid and gradient fields for `count` images whose level-0 copies start
 // at img0 (row pitch pitch0, image i at img0 + i * img0_bytes).
 sam_status prepare_fields(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
-                          const sam_detect_params &p, cudaStream_t st) {
+                          const sam_detect_params &p, cudaStream_t st, LevelImgs *li = nullptr) {
     char *ws = (char *)m->ws.base;
     const int count = P.count, top = P.L - 1;
     const uint8_t *lvl_img[kMaxLevels];
@@ -251,17 +280,67 @@ sam_status prepare_fields(sam_model *m, const Plan &P, const uint8_t *img0, int 
     SAM_CU(launch_pyramid_levels(img0, P.w[0], P.h[0], pitch0, img0_bytes, P.L - 1, dsts, lvl_pitch, lvl_bytes, count,
                                  st));
     prof_end(0, st);
-    // (a) gradients: FP32 pixel-layout fields for the refinement levels, the
-    // top level in the pairs layout and the detection precision
+    // (a) gradients of the top level: the pairs layout in the detection
+    // precision, and for a 16-bit precision the FP32 pixel-layout field that
+    // candidate extraction rescores from.  The refinement levels' FP32
+    // fields are computed after candidate extraction, where the candidates
+    // can reach (run_search), or here in full when no level is refined
+    // from a candidate list.
     prof_begin(1, st);
-    const int nfp32 = p.precision == SAM_FP32 ? top : top + 1;
-    for (int l = 0; l < nfp32; ++l)
-        SAM_CU(launch_gradient(lvl_img[l], P.w[l], P.h[l], lvl_pitch[l], lvl_bytes[l], m->p.low, SAM_FP32,
-                               SAM_LAYOUT_PIXEL, ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
+    if (!li) {
+        for (int l = 0; l < top; ++l)
+            SAM_CU(launch_gradient(lvl_img[l], P.w[l], P.h[l], lvl_pitch[l], lvl_bytes[l], m->p.low, SAM_FP32,
+                                   SAM_LAYOUT_PIXEL, ws + P.off_field[l], P.field_px[l], nullptr, nullptr, count, st));
+    }
+    if (p.precision != SAM_FP32)
+        SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low, SAM_FP32,
+                               SAM_LAYOUT_PIXEL, ws + P.off_field[top], P.field_px[top], nullptr, nullptr, count, st));
     SAM_CU(launch_gradient(lvl_img[top], P.w[top], P.h[top], lvl_pitch[top], lvl_bytes[top], m->p.low, p.precision,
                            SAM_LAYOUT_PAIRS, ws + P.off_top, P.top_px, nullptr, nullptr, count, st));
     prof_end(1, st);
+    if (li)
+        for (int l = 0; l < P.L; ++l) {
+            li->img[l] = lvl_img[l];
+            li->pitch[l] = lvl_pitch[l];
+            li->bytes[l] = lvl_bytes[l];
+        }
     return SAM_OK;
+}
+
+// Level-l pixel reach of the coarse-to-fine refinement around 2^(top - l)
+// times a candidate's top-level position (refine_body): the search centre
+// at level l is 2 x + shift of the level-(l + 1) pose x, which is its own
+// centre +-1, so the centre's distance from the scaled candidate is at most
+// E(top - 1) = S(top) and E(l) = 2 E(l + 1) + 2 + S(l + 1) (S(l): the
+// largest child shift of level l's tables); the pixels read lie within the
+// rotated points' extent and 2 more pixels (a +-1 translation and the 3x3
+// window), plus one pixel of margin.
+void refine_reach(const sam_model *m, int top, int4 *reach) {
+    int ex = 0, ey = 0;
+    for (int l = top - 1; l >= 0; --l) {
+        int sx = 0, sy = 0;
+        for (const int2 &v : m->lv[l + 1].shift) {
+            sx = std::max(sx, std::abs(v.x));
+            sy = std::max(sy, std::abs(v.y));
+        }
+        if (l == top - 1) {
+            ex = sx;
+            ey = sy;
+        } else {
+            ex = 2 * ex + 2 + sx;
+            ey = 2 * ey + 2 + sy;
+        }
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        bool first = true;
+        for (const int4 &b : m->lv[l].bbox) {
+            x0 = first ? b.x : std::min(x0, b.x);
+            x1 = first ? b.y : std::max(x1, b.y);
+            y0 = first ? b.z : std::min(y0, b.z);
+            y1 = first ? b.w : std::max(y1, b.w);
+            first = false;
+        }
+        reach[l] = make_int4(-ex + x0 - 3, ex + x1 + 3, -ey + y0 - 3, ey + y1 + 3);
+    }
 }
 
 ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_params &p) {
@@ -295,7 +374,8 @@ ScoreArgs top_score_args(const sam_model *m, const Plan &P, const sam_detect_par
 
 // Exhaustive top-level search, candidates, refinement and NMS on the fields
 // prepared by prepare_fields.
-sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st) {
+sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, cudaStream_t st,
+                      const LevelImgs &li) {
     char *ws = (char *)m->ws.base;
     const int count = P.count, top = P.L - 1;
     // (c) exhaustive top-level score map; a 16-bit map is rescored in FP32
@@ -333,6 +413,52 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
         SAM_CU(launch_candidates(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
                                  ws + P.off_scratch, 0, count, st, m->nscales));
     prof_end(3, st);
+    // the refinement levels' FP32 fields where the candidates can reach
+    if (top > 0) {
+        prof_begin(1, st);
+        TileMarks tm;
+        memset(&tm, 0, sizeof(tm));
+        tm.kyx = kyx;
+        tm.count = ccount;
+        tm.K = K;
+        tm.count_images = count;
+        tm.top = top;
+        tm.step_x = p.step_x;
+        tm.step_y = p.step_y;
+        tm.nlev = top;
+        refine_reach(m, top, tm.reach);
+        GradTiles gt;
+        memset(&gt, 0, sizeof(gt));
+        bool vec = true;
+        for (int l = 0; l < top; ++l) {
+            tm.w[l] = P.w[l];
+            tm.h[l] = P.h[l];
+            tm.tiles_x[l] = P.tiles_x[l];
+            tm.tiles_y[l] = P.tiles_y[l];
+            tm.tile_base[l] = P.tile_base[l];
+            gt.img[l] = li.img[l];
+            gt.w[l] = P.w[l];
+            gt.h[l] = P.h[l];
+            gt.pitch[l] = li.pitch[l];
+            gt.img_bytes[l] = li.bytes[l];
+            gt.field[l] = (float2 *)(ws + P.off_field[l]);
+            gt.field_px[l] = P.field_px[l];
+            vec = vec && ((uintptr_t)li.img[l] % 16 == 0) && (li.pitch[l] % 16 == 0) &&
+                  (count == 1 || li.bytes[l] % 16 == 0) && ((uintptr_t)gt.field[l] % 16 == 0) &&
+                  (count == 1 || (P.field_px[l] * 8) % 16 == 0);
+        }
+        tm.mask = (uint32_t *)(ws + P.off_tmask);
+        tm.list_cnt = (unsigned *)(ws + P.off_tmask + P.tmask_bytes - 4);
+        tm.list = (uint2 *)(ws + P.off_tlist);
+        tm.list_cap = (unsigned)P.tiles;
+        gt.low = m->p.low;
+        gt.vec = vec ? 1 : 0;
+        gt.list_cnt = tm.list_cnt;
+        gt.list = tm.list;
+        gt.list_cap = tm.list_cap;
+        SAM_CU(launch_refine_fields(tm, gt, P.tmask_bytes, st));
+        prof_end(1, st);
+    }
     RefineArgs ra;
     memset(&ra, 0, sizeof(ra));
     for (int l = 0; l < P.L; ++l) {
@@ -378,8 +504,9 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
 
 sam_status run_pipeline(sam_model *m, const Plan &P, const uint8_t *img0, int pitch0, size_t img0_bytes,
                         const sam_detect_params &p, cudaStream_t st) {
-    const sam_status s = prepare_fields(m, P, img0, pitch0, img0_bytes, p, st);
-    return s != SAM_OK ? s : run_search(m, P, p, st);
+    LevelImgs li;
+    const sam_status s = prepare_fields(m, P, img0, pitch0, img0_bytes, p, st, &li);
+    return s != SAM_OK ? s : run_search(m, P, p, st, li);
 }
 
 // ---- graph mode ----

@@ -555,7 +555,68 @@ __global__ void __launch_bounds__(GTHREADS) gradient_jobs_kernel(const ImageJob 
         }
 }
 
+// Marked tiles of the refinement levels (FP32 pixel layout), each computed
+// exactly as gradient_kernel computes it: the persistent CTAs walk the list
+// that mark_tiles_kernel built.
+__global__ void __launch_bounds__(GTHREADS) gradient_tiles_kernel(const GradTiles g) {
+    const unsigned n = min(*g.list_cnt, g.list_cap);
+    for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint2 t = g.list[i];
+        const int l = (int)(t.x >> 24), im = (int)(t.x & 0xFFFFFFu);
+        const int ty = (int)(t.y >> 16), tx = (int)(t.y & 0xFFFFu);
+        gradient_tile<SAM_FP32, SAM_LAYOUT_PIXEL>(g.img[l] + (size_t)im * g.img_bytes[l], g.w[l], g.h[l], g.pitch[l],
+                                                 g.low, g.field[l], (size_t)im * g.field_px[l], nullptr, nullptr,
+                                                 g.vec, tx * GTX, ty * GTY);
+        __syncthreads();   // the tile buffers are reused by the next tile
+    }
+}
+
+// The gradient tiles of the refinement levels that the coarse-to-fine
+// refinement of candidate blockIdx.y of image blockIdx.x can read: at level
+// l the pixels within reach[l] of 2^(top - l) times the candidate's
+// position.  Each tile is listed once (the first CTA to set its bit in the
+// mask lists it).
+__global__ void mark_tiles_kernel(const TileMarks a) {
+    const int im = blockIdx.x, c = blockIdx.y;
+    if (c >= min(a.count[im], a.K))
+        return;
+    const int32_t *q = a.kyx + ((size_t)im * a.K + c) * 3;
+    const int xT = q[2] * a.step_x, yT = q[1] * a.step_y;
+    for (int l = 0; l < a.nlev; ++l) {
+        const int sc = 1 << (a.top - l);
+        const int x0 = max(0, sc * xT + a.reach[l].x), x1 = min(a.w[l] - 1, sc * xT + a.reach[l].y);
+        const int y0 = max(0, sc * yT + a.reach[l].z), y1 = min(a.h[l] - 1, sc * yT + a.reach[l].w);
+        if (x0 > x1 || y0 > y1)
+            continue;
+        const int tx0 = x0 / GTX, tx1 = x1 / GTX, ty0 = y0 / GTY, ty1 = y1 / GTY;
+        const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int ty = ty0 + i / ntx, tx = tx0 + i % ntx;
+            const size_t bit = a.tile_base[l] + ((size_t)im * a.tiles_y[l] + ty) * a.tiles_x[l] + tx;
+            const uint32_t mb = 1u << (bit & 31);
+            if (!(atomicOr(a.mask + (bit >> 5), mb) & mb)) {
+                const unsigned pos = atomicAdd(a.list_cnt, 1u);
+                if (pos < a.list_cap)
+                    a.list[pos] = make_uint2(((unsigned)l << 24) | (unsigned)im, ((unsigned)ty << 16) | (unsigned)tx);
+            }
+        }
+    }
+}
+
 }  // namespace
+
+int gradient_tile_w() { return GTX; }
+int gradient_tile_h() { return GTY; }
+
+cudaError_t launch_refine_fields(const TileMarks &marks, const GradTiles &g, size_t clear_bytes, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(marks.mask, 0, clear_bytes, st);
+    if (e != cudaSuccess)
+        return e;
+    mark_tiles_kernel<<<dim3((unsigned)marks.count_images, (unsigned)marks.K), 128, 0, st>>>(marks);
+    gradient_tiles_kernel<<<152 * 8, GTHREADS, 0, st>>>(g);
+    count_launches(2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pyramid_jobs(const ImageJob *jobs, int n_jobs, int max_w, int max_h, cudaStream_t st) {
     if (n_jobs <= 0)

@@ -187,6 +187,19 @@ __global__ void local_max_hot_kernel(const float *__restrict__ map, size_t map_i
 
 constexpr int kC16Threads = 256;
 
+// What the 16-bit candidate test needs of one image's (or pair's) map.
+struct C16View {
+    const float *map;      // [nth][gh][gw]
+    int nth, gh, gw, ns;
+    const float2 *field;   // FP32 pixel-layout field of the scored level (w x h, pitch w)
+    int w, h;
+    const RotPt *rot;      // [nth][n]
+    int n;
+    Cand *cand;            // the candidate list and its counter
+    size_t cap;
+    int *cnt;
+};
+
 struct Cand16Args {
     const float *map;
     size_t map_img;
@@ -241,18 +254,19 @@ __device__ __forceinline__ bool no_neighbour_above(const float *__restrict__ map
     return true;
 }
 
-template <int NB>
-__global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a) {
+// The test over the hot list (entries {view index, map index}); view(i)
+// describes map i.  All threads of the CTA call it.
+template <int NB, typename ViewAt>
+__device__ __forceinline__ void cand16_body(const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                            float min_score, float delta, int polarity, ViewAt view) {
     __shared__ unsigned s_list[kC16Threads];        // hot entries of this round that pass the filter
     __shared__ int s_n;
     __shared__ float s_red[kC16Threads / 32][81];   // per-warp sums: plane d, translation q at 9 d + q
     __shared__ float s_val[81];
-    const unsigned total = min(*a.hot_cnt, a.hot_cap);
+    const unsigned total = min(*hot_cnt, hot_cap);
     const size_t G = gridDim.x;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const size_t plane = (size_t)a.gh * a.gw;
-    const int nang = a.nth / a.ns;
-    const float up = 2.f * a.delta;
+    const float up = 2.f * delta;
     // entry b + G (r0 + t) for thread t of CTA b: consecutive entries (often
     // poses of one instance) go to different CTAs
     for (size_t r0 = 0; blockIdx.x + G * r0 < total; r0 += kC16Threads) {
@@ -261,21 +275,23 @@ __global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a)
         __syncthreads();
         const size_t e = blockIdx.x + G * (r0 + t);
         if (e < total) {
-            const uint2 hv = a.hot[e];
-            const float *m = a.map + (size_t)hv.x * a.map_img;
-            const float v = m[hv.y];
-            if (v >= a.min_score - a.delta && no_neighbour_above(m, a.nth, a.gh, a.gw, hv.y, a.ns, v + up))
+            const uint2 hv = hot[e];
+            const C16View V = view(hv.x);
+            const float v = V.map[hv.y];
+            if (v >= min_score - delta && no_neighbour_above(V.map, V.nth, V.gh, V.gw, hv.y, V.ns, v + up))
                 s_list[atomicAdd(&s_n, 1)] = (unsigned)e;
         }
         __syncthreads();
         const int np = s_n;
         for (int ip = 0; ip < np; ++ip) {
-            const uint2 hv = a.hot[s_list[ip]];
-            const unsigned img = hv.x;
+            const uint2 hv = hot[s_list[ip]];
+            const C16View V = view(hv.x);
+            const size_t plane = (size_t)V.gh * V.gw;
+            const int nang = V.nth / V.ns;
             const size_t idx = hv.y;
             const int kk = (int)(idx / plane);
             const int rem = (int)(idx - (size_t)kk * plane);
-            const int y = rem / a.gw, x = rem - y * a.gw;
+            const int y = rem / V.gw, x = rem - y * V.gw;
             const int js = kk / nang, k = kk - js * nang;
             // the neighbourhood's planes (scale j2, angle k2), the same list
             // on every thread; dc is the pose's own plane
@@ -283,7 +299,7 @@ __global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a)
             int npl = 0, dc = 0;
             for (int dj = -1; dj <= 1; ++dj) {
                 const int j2 = js + dj;
-                if (j2 < 0 || j2 >= a.ns)
+                if (j2 < 0 || j2 >= V.ns)
                     continue;
                 for (int dk = -1; dk <= 1; ++dk) {
                     if (dk != 0 && nang == 1)
@@ -293,14 +309,14 @@ __global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a)
                     kl[npl++] = j2 * nang + (k + dk + nang) % nang;
                 }
             }
-            const float2 *F = a.field + (size_t)img * a.field_img_px;
+            const float2 *F = V.field;
             for (int d = 0; d < npl; ++d) {
-                const RotPt *P = a.rot + (size_t)kl[d] * a.n;
+                const RotPt *P = V.rot + (size_t)kl[d] * V.n;
                 float acc[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q)
                     acc[q] = 0.f;
-                for (int i = t; i < a.n; i += kC16Threads) {
+                for (int i = t; i < V.n; i += kC16Threads) {
                     const RotPt p = P[i];
                     const int bxp = x + p.ox, byp = y + p.oy;
                     constexpr int D = NB + 2;
@@ -311,10 +327,10 @@ __global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a)
                         for (int xx = 0; xx < D; ++xx) {
                             const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
                             float v = 0.f;
-                            if (X >= 0 && Y >= 0 && X < a.w && Y < a.h) {
-                                const float2 f = __ldg(F + (size_t)Y * a.w + X);
+                            if (X >= 0 && Y >= 0 && X < V.w && Y < V.h) {
+                                const float2 f = __ldg(F + (size_t)Y * V.w + X);
                                 v = fmaf(p.px, f.x, p.py * f.y);
-                                if (a.polarity)
+                                if (polarity)
                                     v = fabsf(v);
                             }
                             dd[yy][xx] = v;
@@ -347,36 +363,113 @@ __global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a)
                 float v = 0.f;
                 for (int wv = 0; wv < kC16Threads / 32; ++wv)
                     v += s_red[wv][t];
-                s_val[t] = v / (float)a.n;
+                s_val[t] = v / (float)V.n;
             }
             __syncthreads();
             if (t == 0) {
                 const float sp = s_val[dc * 9 + 4];
-                bool ok = sp >= a.min_score;
+                bool ok = sp >= min_score;
                 for (int d = 0; d < npl && ok; ++d)
                     for (int q = 0; q < 9; ++q) {
                         const int X = x + q % 3 - 1, Y = y + q / 3 - 1;
-                        if (X < 0 || Y < 0 || X >= a.gw || Y >= a.gh)
+                        if (X < 0 || Y < 0 || X >= V.gw || Y >= V.gh)
                             continue;
-                        const size_t key = (size_t)kl[d] * plane + (size_t)Y * a.gw + X;
+                        const size_t key = (size_t)kl[d] * plane + (size_t)Y * V.gw + X;
                         if (key != idx && !beats(sp, idx, s_val[d * 9 + q], key)) {
                             ok = false;
                             break;
                         }
                     }
                 if (ok) {
-                    const int pos = atomicAdd(a.cnt + img, 1);
-                    if ((size_t)pos < a.cap) {
+                    const int pos = atomicAdd(V.cnt, 1);
+                    if ((size_t)pos < V.cap) {
                         Cand c;
                         c.s = sp;
                         c.pad = 0;
                         c.key = idx;
-                        a.cand[(size_t)img * a.cap + pos] = c;
+                        V.cand[pos] = c;
                     }
                 }
             }
             __syncthreads();   // s_red and s_val are reused by the next pose
         }
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a) {
+    cand16_body<NB>(a.hot_cnt, a.hot, a.hot_cap, a.min_score, a.delta, a.polarity, [&](unsigned img) {
+        C16View v;
+        v.map = a.map + (size_t)img * a.map_img;
+        v.nth = a.nth;
+        v.gh = a.gh;
+        v.gw = a.gw;
+        v.ns = a.ns;
+        v.field = a.field + (size_t)img * a.field_img_px;
+        v.w = a.w;
+        v.h = a.h;
+        v.rot = a.rot;
+        v.n = a.n;
+        v.cand = a.cand + (size_t)img * a.cap;
+        v.cap = a.cap;
+        v.cnt = a.cnt + img;
+        return v;
+    });
+}
+
+// The same over a job list: pair p's map and candidate list in cj[p], its
+// FP32 field and model points in rj[p].
+template <int NB>
+__global__ void __launch_bounds__(kC16Threads) cand16_jobs_kernel(const CandJob *__restrict__ cj,
+                                                                  const RescoreJob *__restrict__ rj,
+                                                                  const unsigned *hot_cnt, const uint2 *hot,
+                                                                  unsigned hot_cap, float min_score, float delta,
+                                                                  int polarity) {
+    cand16_body<NB>(hot_cnt, hot, hot_cap, min_score, delta, polarity, [&](unsigned p) {
+        const CandJob &c = cj[p];
+        const RescoreJob &r = rj[p];
+        C16View v;
+        v.map = c.map;
+        v.nth = c.nth;
+        v.gh = c.gh;
+        v.gw = c.gw;
+        v.ns = c.ns;
+        v.field = r.field;
+        v.w = r.w;
+        v.h = r.h;
+        v.rot = r.rot;
+        v.n = r.n;
+        v.cand = c.cand;
+        v.cap = c.cap;
+        v.cnt = c.cnt;
+        return v;
+    });
+}
+
+// Candidates of a job list's maps from the batch's hot list (entries {pair,
+// map index}; the list's threshold at most min_score); if the list
+// overflowed, every pair's map is scanned instead.
+__global__ void local_max_hot_jobs_kernel(const CandJob *__restrict__ jobs, int n_jobs, float min_score,
+                                          const unsigned *__restrict__ hot_cnt, const uint2 *__restrict__ hot,
+                                          unsigned hot_cap) {
+    const unsigned total = *hot_cnt;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (total <= hot_cap) {
+        for (size_t e = tid; e < total; e += stride) {
+            const uint2 h = hot[e];
+            const CandJob &j = jobs[h.x];
+            if (is_candidate(j.map, j.nth, j.gh, j.gw, min_score, h.y, j.ns))
+                push_candidate(j.map, h.y, j.cand, j.cap, j.cnt);
+        }
+        return;
+    }
+    for (int p = 0; p < n_jobs; ++p) {
+        const CandJob &j = jobs[p];
+        const size_t per = (size_t)j.nth * j.gh * j.gw;
+        for (size_t idx = tid; idx < per; idx += stride)
+            if (is_candidate(j.map, j.nth, j.gh, j.gw, min_score, idx, j.ns))
+                push_candidate(j.map, idx, j.cand, j.cap, j.cnt);
     }
 }
 
@@ -488,21 +581,26 @@ struct RefineLevels {
 };
 
 // One thread-block cluster of kRefineCluster CTAs per candidate: each CTA sums
-// its share of the model points for the 27 poses, CTA 0 adds the shares in
-// rank order through distributed shared memory, picks the level's best pose
-// and the other CTAs read it back.  Every branch that skips a cluster barrier
-// is taken by the whole cluster (same candidate, same state).
+// its share of the model points for the 27 poses and leaves the sums in its
+// shared memory; after one cluster barrier every CTA adds the shares of all
+// CTAs in rank order through distributed shared memory and picks the
+// level's best pose itself (the same sums in the same order, so the same
+// choice everywhere; no second barrier to broadcast it).  The share buffer
+// alternates between two slots per reduction: a CTA writes slot r & 1 only
+// after the barrier of reduction r - 1, which every CTA reaches after it has
+// read the shares of reduction r - 2.  Every branch that skips a cluster
+// barrier is taken by the whole cluster (same candidate, same state).
 template <int NB>
 __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    const unsigned rank = cluster.block_rank();
     __shared__ float red[RTHREADS / 32][27];
-    __shared__ float part[27];   // this CTA's sums of the 27 poses
-    __shared__ int state[4];     // x, y, k, alive
+    __shared__ float part[2][27];   // this CTA's sums of the 27 poses, slot = reduction parity
+    __shared__ int state[4];        // x, y, k, alive
     __shared__ float sbest;
     const int ncand = *j.count;
     float4 *outp = j.refined + c;
+    const unsigned rank = cluster.block_rank();
     if (c >= ncand) {
         if (rank == 0 && threadIdx.x == 0)
             *outp = make_float4(__int_as_float(0), __int_as_float(0), __int_as_float(0), -INFINITY);
@@ -519,6 +617,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = j.nscales;
+    int nred = 0;   // reductions so far (share slot parity)
     for (int l = j.top - 1; l >= 0; --l) {
         const LevelDev &L = lv[l];
         // parent table Kp = scale jp x angles + angle kp at level l + 1
@@ -529,7 +628,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
         const int W = j.w[l], H = j.h[l];
         const float2 *F = j.field[l];
         // the scales jp - 1 .. jp + 1 inside the grid, one pass of 27 poses
-        // each (a rigid model: one pass); CTA 0 keeps the best over the passes
+        // each (a rigid model: one pass); warp 0 keeps the best over the passes
         const int last_ds = min(1, ns - 1 - jp);
         float bs = -INFINITY;
         unsigned long long bk = ~0ull;
@@ -599,14 +698,15 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                     red[warp][q] = v;
             }
             __syncthreads();
+            float *share = part[nred & 1];
             if (threadIdx.x < 27) {
                 float v = 0.f;
                 for (int wv = 0; wv < RTHREADS / 32; ++wv)
                     v += red[wv][threadIdx.x];
-                part[threadIdx.x] = v;
+                share[threadIdx.x] = v;
             }
-            cluster.sync();   // every CTA's share is in its shared memory
-            if (rank == 0 && warp == 0) {
+            cluster.sync();   // every CTA's share of this reduction is in its shared memory
+            if (warp == 0) {
                 // lane q < 27: pose q's sum over the CTAs (in rank order) and
                 // its key; the best by the total order by a shuffle reduction
                 float M = -INFINITY;
@@ -616,7 +716,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                 if (lane < 27) {
                     float tot = 0.f;
                     for (unsigned r = 0; r < (unsigned)kRefineCluster; ++r)
-                        tot += cluster.map_shared_rank(part, r)[lane];
+                        tot += cluster.map_shared_rank(share, r)[lane];
                     const int dk = lane / 9, ty = (lane / 3) % 3, tx = lane % 3;
                     kk = js * nang + (2 * kp + dk - 1 + nang) % nang;
                     X = cx + tx - 1;
@@ -659,61 +759,83 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                     }
                 }
             }
-            cluster.sync();   // CTA 0 has read every share (and, after the last pass, chosen)
+            ++nred;
         }
-        if (rank != 0 && threadIdx.x == 0) {
-            const int *s0 = cluster.map_shared_rank(state, 0u);
-            state[0] = s0[0];
-            state[1] = s0[1];
-            state[2] = s0[2];
-            state[3] = s0[3];
-            sbest = *cluster.map_shared_rank(&sbest, 0u);
-        }
-        __syncthreads();
+        __syncthreads();   // warp 0's choice is visible to the CTA
         if (!state[3])
             break;
     }
-    cluster.sync();   // CTA 0 stays until every CTA has read its state
+    cluster.sync();   // no CTA leaves while another may still read its shares
     if (rank == 0 && threadIdx.x == 0)
         *outp = make_float4(__int_as_float(state[0]), __int_as_float(state[1]), __int_as_float(state[2]),
                             state[3] ? sbest : -INFINITY);
 }
 
+// Which candidate the cluster's turn cidx refines: the cidx-th of all
+// images' (or pairs') candidates in (image, slot) order; false past the last.
+template <typename CountAt>
+__device__ __forceinline__ bool locate_candidate(int cidx, int n, int K, CountAt count_at, int *img, int *slot) {
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        const int c = min(count_at(i), K);
+        if (cidx < acc + c) {
+            *img = i;
+            *slot = cidx - acc;
+            return true;
+        }
+        acc += c;
+    }
+    return false;
+}
+
 // Coarse-to-fine refinement (Sec. II: the search starts at the top pyramid
 // level; the size-3 neighbouring search in x, y and theta at each lower
-// level): a cluster of kRefineCluster CTAs per candidate of image
-// blockIdx.y, all levels down to 0 in one launch.  Three CTAs per SM (85
+// level), all levels down to 0 in one launch: persistent clusters of
+// kRefineCluster CTAs take the candidates of all images in turn (cluster c
+// the candidates c, c + clusters, ...), so only clusters with a candidate
+// run and empty candidate slots cost nothing.  Three CTAs per SM (85
 // registers) measured faster than two with no register limit.
 template <int NB>
 __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
     refine_kernel(RefineLevels lv, RefineArgs a) {
-    const int img = blockIdx.y;
-    RefineJob j;
-    j.L = nullptr;
-    for (int l = 0; l < kMaxLevels; ++l) {
-        j.field[l] = a.field[l] + (size_t)img * a.field_img_px[l];
-        j.w[l] = a.w[l];
-        j.h[l] = a.h[l];
+    const int clusters = gridDim.x / kRefineCluster;
+    for (int cidx = blockIdx.x / kRefineCluster;; cidx += clusters) {
+        int img = 0, slot = 0;
+        if (!locate_candidate(cidx, a.count, a.K, [&](int i) { return a.cand_count[i]; }, &img, &slot))
+            break;
+        RefineJob j;
+        j.L = nullptr;
+        for (int l = 0; l < kMaxLevels; ++l) {
+            j.field[l] = a.field[l] + (size_t)img * a.field_img_px[l];
+            j.w[l] = a.w[l];
+            j.h[l] = a.h[l];
+        }
+        j.top = a.top;
+        j.step_x = a.step_x;
+        j.step_y = a.step_y;
+        j.polarity = a.polarity;
+        j.min_score = a.min_score;
+        j.kyx = a.cand_kyx + (size_t)img * 3 * a.K;
+        j.cs = a.cand_s + (size_t)img * a.K;
+        j.count = a.cand_count + img;
+        j.refined = a.refined + (size_t)img * a.K;
+        j.nscales = a.nscales;
+        refine_body<NB>(j, lv.L, slot);
     }
-    j.top = a.top;
-    j.step_x = a.step_x;
-    j.step_y = a.step_y;
-    j.polarity = a.polarity;
-    j.min_score = a.min_score;
-    j.kyx = a.cand_kyx + (size_t)img * 3 * a.K;
-    j.cs = a.cand_s + (size_t)img * a.K;
-    j.count = a.cand_count + img;
-    j.refined = a.refined + (size_t)img * a.K;
-    j.nscales = a.nscales;
-    refine_body<NB>(j, lv.L, blockIdx.x / kRefineCluster);
 }
 
-// The same per job (pair blockIdx.y).
+// The same over a job list (pairs of different images and models).
 template <int NB>
 __global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
-    refine_jobs_kernel(const RefineJob *__restrict__ jobs) {
-    const RefineJob &j = jobs[blockIdx.y];
-    refine_body<NB>(j, j.L, blockIdx.x / kRefineCluster);
+    refine_jobs_kernel(const RefineJob *__restrict__ jobs, int n_jobs, int K) {
+    const int clusters = gridDim.x / kRefineCluster;
+    for (int cidx = blockIdx.x / kRefineCluster;; cidx += clusters) {
+        int job = 0, slot = 0;
+        if (!locate_candidate(cidx, n_jobs, K, [&](int i) { return *jobs[i].count; }, &job, &slot))
+            break;
+        const RefineJob &j = jobs[job];
+        refine_body<NB>(j, j.L, slot);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -901,6 +1023,33 @@ cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_candidates_hot_jobs(const CandJob *jobs, int n_jobs, float min_score, int K,
+                                       const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                       cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    local_max_hot_jobs_kernel<<<2 * 152, 256, 0, st>>>(jobs, n_jobs, min_score, hot_cnt, hot, hot_cap);
+    topk_jobs_kernel<<<n_jobs, 1024, 0, st>>>(jobs, K);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_candidates_hot16_jobs(const CandJob *cjobs, const RescoreJob *rjobs, int n_jobs, float min_score,
+                                         float delta, int K, int nbhd, int polarity, const unsigned *hot_cnt,
+                                         const uint2 *hot, unsigned hot_cap, cudaStream_t st) {
+    if (n_jobs <= 0)
+        return cudaSuccess;
+    if (nbhd == 3)
+        cand16_jobs_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot_cnt, hot, hot_cap, min_score, delta,
+                                                              polarity);
+    else
+        cand16_jobs_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot_cnt, hot, hot_cap, min_score, delta,
+                                                              polarity);
+    topk_jobs_kernel<<<n_jobs, 1024, 0, st>>>(cjobs, K);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 size_t candidates_scratch_bytes_batch(int nth, int gh, int gw, int n_img, int ns) {
     return 256 * ((n_img * sizeof(int) + 255) / 256) + (size_t)n_img * cand_cap(nth, gh, gw, ns) * sizeof(Cand);
 }
@@ -916,11 +1065,40 @@ cudaError_t launch_candidates_jobs(const CandJob *jobs, int n_jobs, size_t max_t
     return cudaGetLastError();
 }
 
+// Clusters of the persistent refinement that fit on the device at once (the
+// first query per device; 152 SMs x 3 CTAs if the query fails).
+int refine_clusters() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return 152 * 3 / kRefineCluster;
+    if (cached[dev] > 0)
+        return cached[dev];
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kRefineCluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kRefineCluster * 1024);
+    cfg.blockDim = dim3(RTHREADS);
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)refine_kernel<3>, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 152 * 3 / kRefineCluster;
+    }
+    cached[dev] = n;
+    return n;
+}
+
 cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t st) {
     RefineLevels lv;
     for (int l = 0; l < kMaxLevels; ++l)
         lv.L[l] = m->dev[l];
-    dim3 grid((unsigned)(a.K * kRefineCluster), (unsigned)a.count);
+    const int clusters = std::max(1, std::min(a.count * a.K, refine_clusters()));
+    dim3 grid((unsigned)(clusters * kRefineCluster));
     if (a.nbhd == 3)
         refine_kernel<3><<<grid, RTHREADS, 0, st>>>(lv, a);
     else
@@ -932,11 +1110,12 @@ cudaError_t launch_refine(const sam_model *m, const RefineArgs &a, cudaStream_t 
 cudaError_t launch_refine_jobs(const RefineJob *jobs, int n_jobs, int K, int nbhd, cudaStream_t st) {
     if (n_jobs <= 0)
         return cudaSuccess;
-    dim3 grid((unsigned)(K * kRefineCluster), (unsigned)n_jobs);
+    const int clusters = std::max(1, std::min(n_jobs * K, refine_clusters()));
+    dim3 grid((unsigned)(clusters * kRefineCluster));
     if (nbhd == 3)
-        refine_jobs_kernel<3><<<grid, RTHREADS, 0, st>>>(jobs);
+        refine_jobs_kernel<3><<<grid, RTHREADS, 0, st>>>(jobs, n_jobs, K);
     else
-        refine_jobs_kernel<1><<<grid, RTHREADS, 0, st>>>(jobs);
+        refine_jobs_kernel<1><<<grid, RTHREADS, 0, st>>>(jobs, n_jobs, K);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -71,6 +71,10 @@ struct sam_multi {
     size_t bitmap_bytes = 0;           // edge bitmaps of the largest window
     size_t max_map = 0;
     long long pose_points = 0;
+    // hot list of the pairs scorer (see TiledArgs): candidates (and, for a
+    // 16-bit field, their FP32 decision) from the listed poses only
+    bool hot = false;
+    size_t off_hot = 0, hot_cap = 0;
     bool dirty = true;                 // descriptors / graph must be rebuilt
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -196,6 +200,14 @@ sam_status upload_descriptors(sam_multi *mp) {
         s.emin = mp->p.early_termination ? edge_count_threshold(s.thresh, mp->p.precision) : 0;
         s.item_begin = item;
         item += q.items;
+        s.job = mp->order[r];
+        if (mp->hot) {
+            s.hot_cnt = (unsigned *)(base + mp->off_counters) + 1 + 3 * (size_t)np;
+            s.hot = (uint2 *)(base + mp->off_hot);
+            s.hot_cap = (unsigned)mp->hot_cap;
+            s.hot_thr = mp->p.precision == SAM_FP32 ? mp->p.min_score
+                                                     : mp->p.min_score - rescore_delta(mp->p.precision);
+        }
         put(mp->off_pairs + (size_t)r * sizeof(PairScore), &s, sizeof(s));
     }
     mp->total_items = item;
@@ -226,7 +238,7 @@ sam_status upload_descriptors(sam_multi *mp) {
         rs.field = (const float2 *)(base + I.off_field[q.top]);
         rs.rot = mp->models[q.model]->dev[q.top].rot;
         rs.map = (float *)(base + q.off_map);
-        rs.list = (unsigned *)(base + q.off_rescore + rescore_scratch_bytes(0));
+        rs.list = mp->hot ? nullptr : (unsigned *)(base + q.off_rescore + rescore_scratch_bytes(0));
         rs.count = (unsigned *)(cnt + 2 * np + i);
         rs.w = q.W;
         rs.h = q.H;
@@ -275,7 +287,7 @@ sam_status upload_descriptors(sam_multi *mp) {
 sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
     char *base = (char *)mp->base;
     const int np = (int)mp->pp.size();
-    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (1 + 3 * (size_t)np), st));
+    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (2 + 3 * (size_t)np), st));
     size_t o = mp->off_pyr;
     for (int l = 1; l < mp->Lmax; ++l) {
         const int n = mp->pyr_count[l];
@@ -294,11 +306,24 @@ sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
     MU_CU(launch_score_pairs((const PairScore *)(base + mp->off_pairs), np, mp->total_items, mp->p.precision,
                              mp->p.neighbourhood, mp->models[0]->p.polarity, mp->p.early_termination, mp->cfg,
                              mp->window_bytes, mp->bitmap_bytes, (unsigned *)(base + mp->off_counters), st));
-    if (mp->p.precision != SAM_FP32)
-        MU_CU(launch_rescore_jobs((const RescoreJob *)(base + mp->off_rsjobs), np, mp->max_map, mp->p.neighbourhood,
-                                  mp->models[0]->p.polarity, mp->p.min_score, mp->p.precision, st));
-    MU_CU(launch_candidates_jobs((const CandJob *)(base + mp->off_cjobs), np, mp->max_map, mp->p.min_score,
-                                 mp->p.top_k, st));
+    const unsigned *hot_cnt = (const unsigned *)(base + mp->off_counters) + 1 + 3 * (size_t)np;
+    const uint2 *hot = (const uint2 *)(base + mp->off_hot);
+    if (mp->hot && mp->p.precision != SAM_FP32) {
+        MU_CU(launch_candidates_hot16_jobs((const CandJob *)(base + mp->off_cjobs),
+                                           (const RescoreJob *)(base + mp->off_rsjobs), np, mp->p.min_score,
+                                           rescore_delta(mp->p.precision), mp->p.top_k, mp->p.neighbourhood,
+                                           mp->models[0]->p.polarity, hot_cnt, hot, (unsigned)mp->hot_cap, st));
+    } else if (mp->hot) {
+        MU_CU(launch_candidates_hot_jobs((const CandJob *)(base + mp->off_cjobs), np, mp->p.min_score, mp->p.top_k,
+                                         hot_cnt, hot, (unsigned)mp->hot_cap, st));
+    } else {
+        if (mp->p.precision != SAM_FP32)
+            MU_CU(launch_rescore_jobs((const RescoreJob *)(base + mp->off_rsjobs), np, mp->max_map,
+                                      mp->p.neighbourhood, mp->models[0]->p.polarity, mp->p.min_score,
+                                      mp->p.precision, st));
+        MU_CU(launch_candidates_jobs((const CandJob *)(base + mp->off_cjobs), np, mp->max_map, mp->p.min_score,
+                                     mp->p.top_k, st));
+    }
     MU_CU(launch_refine_jobs((const RefineJob *)(base + mp->off_rjobs), np, mp->p.top_k, mp->p.neighbourhood, st));
     MU_CU(launch_nms_jobs((const NmsJob *)(base + mp->off_njobs), np, mp->p.top_k, st));
     return SAM_OK;
@@ -478,13 +503,34 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
         off += al((size_t)params->max_detections * sizeof(sam_pose));
         q.off_nout = off;
         off += al(4);
-        q.off_rescore = off;
-        if (params->precision != SAM_FP32)
-            off += al(rescore_scratch_bytes(q.map_img));
         mp->pose_points += (long long)q.map_img * q.n;
     }
+    // hot list: every pose of every map for a 16-bit field (the FP32
+    // decision must see all poses within the storage bound of min_score),
+    // a sixteenth for FP32 (an overflow sends candidate extraction back to
+    // the whole maps); entries {pair, map index} of 32 bits each.  Plans
+    // too large for 32-bit counts rescore every map as before.
+    size_t poses = 0;
+    bool idx32 = true;
+    for (const PairPlan &q : mp->pp) {
+        poses += q.map_img;
+        idx32 = idx32 && q.map_img <= 0xFFFFFFFFull;
+    }
+    mp->hot_cap = params->precision == SAM_FP32 ? std::min(poses, std::max<size_t>(65536, poses / 16)) : poses;
+    mp->hot = idx32 && mp->hot_cap <= 0xFFFFFFFFull;
+    if (mp->hot) {
+        mp->off_hot = off;
+        off += al(mp->hot_cap * 8);
+    }
+    for (PairPlan &q : mp->pp) {
+        q.off_rescore = off;
+        if (params->precision != SAM_FP32 && !mp->hot)
+            off += al(rescore_scratch_bytes(q.map_img));
+    }
+    // counters: work counter, candidate counts, output counts, rescore
+    // counts (one per pair each), hot-list counter
     mp->off_counters = off;
-    off += al(sizeof(int) * (1 + 3 * (size_t)n_pairs));
+    off += al(sizeof(int) * (2 + 3 * (size_t)n_pairs));
     // descriptors
     mp->off_desc = off;
     mp->pyr_count.assign(mp->Lmax, 0);

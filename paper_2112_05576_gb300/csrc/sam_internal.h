@@ -172,6 +172,42 @@ cudaError_t launch_gradient_jobs(const ImageJob *jobs, int n_jobs, int max_w, in
 // (b) pyramid step; `count` images, image i at src + i*src_img / dst + i*dst_img
 cudaError_t launch_pyramid_down(const uint8_t *src, int w, int h, int src_stride, size_t src_img, uint8_t *dst,
                                 int dst_stride, size_t dst_img, int count, cudaStream_t st);
+// Refinement-level gradients on demand (kernels_image.cu): after candidate
+// extraction, the FP32 pixel-layout tiles (gradient_tile_w() x
+// gradient_tile_h() pixels) of levels 0 .. nlev - 1 that the refinement of
+// some candidate can read are marked and listed, then computed; the others
+// are left unwritten.  reach[l] = (xlo, xhi, ylo, yhi): level-l pixel
+// offsets, relative to 2^(top - l) times a candidate's top-level position,
+// that bound what its refinement reads.
+struct TileMarks {
+    const int32_t *kyx;        // candidates (k, y, x), K per image
+    const int *count;          // candidates per image
+    int K, count_images;
+    int top, step_x, step_y, nlev;
+    int w[kMaxLevels], h[kMaxLevels], tiles_x[kMaxLevels], tiles_y[kMaxLevels];
+    size_t tile_base[kMaxLevels];   // first mask bit of level l (image-major)
+    int4 reach[kMaxLevels];
+    uint32_t *mask;            // one bit per tile; mask, then the list counter, are cleared together
+    unsigned *list_cnt;
+    uint2 *list;               // {level << 24 | image, ty << 16 | tx}
+    unsigned list_cap;         // every tile of every level: cannot overflow
+};
+struct GradTiles {
+    const uint8_t *img[kMaxLevels];
+    int w[kMaxLevels], h[kMaxLevels], pitch[kMaxLevels];
+    size_t img_bytes[kMaxLevels];
+    float2 *field[kMaxLevels];
+    size_t field_px[kMaxLevels];
+    int low, vec;
+    const unsigned *list_cnt;
+    const uint2 *list;
+    unsigned list_cap;
+};
+int gradient_tile_w();
+int gradient_tile_h();
+// Clears clear_bytes at marks.mask (the mask and the counter after it),
+// marks, and computes the listed tiles.
+cudaError_t launch_refine_fields(const TileMarks &marks, const GradTiles &g, size_t clear_bytes, cudaStream_t st);
 // Levels 1 .. D of `count` images in one launch (D <= 6; deeper pyramids take
 // one launch per level): dst[l], dst_stride[l], dst_img[l] for l = 1 .. D.
 cudaError_t launch_pyramid_levels(const uint8_t *src, int w, int h, int src_stride, size_t src_img, int D,
@@ -379,6 +415,11 @@ struct PairScore {
     float inv_n, thresh;
     int item_begin;     // first work unit of this pair (units: tiles x angle groups)
     int emin;           // edge-presence bound (as TiledArgs::emin)
+    int job;            // the pair's index in caller order (its hot-list entries' first word)
+    unsigned *hot_cnt;  // the batch's hot list (null: none; see TiledArgs)
+    uint2 *hot;
+    unsigned hot_cap;
+    float hot_thr;
 };
 bool encode_pair_tmap(void *out, const void *field, int precision, int wp, int H, int bxw, int byw);
 int tiled_warp_tile(int precision, int tc, int *wty);
@@ -508,6 +549,17 @@ struct RescoreJob {
 };
 cudaError_t launch_rescore_jobs(const RescoreJob *jobs, int n_jobs, size_t max_map, int nbhd, int polarity,
                                 float min_score, int precision, cudaStream_t st);
+// Candidates of a job list from the pairs scorer's hot list (entries {pair,
+// map index}): FP32 maps (the list's threshold min_score; a list that
+// overflowed sends every map through the full scan), and 16-bit maps decided
+// in FP32 as launch_candidates_hot16 does (the list holds every pose at or
+// above min_score - delta; the pair's FP32 field and points from rjobs).
+cudaError_t launch_candidates_hot_jobs(const CandJob *jobs, int n_jobs, float min_score, int K,
+                                       const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                       cudaStream_t st);
+cudaError_t launch_candidates_hot16_jobs(const CandJob *cjobs, const RescoreJob *rjobs, int n_jobs, float min_score,
+                                         float delta, int K, int nbhd, int polarity, const unsigned *hot_cnt,
+                                         const uint2 *hot, unsigned hot_cap, cudaStream_t st);
 
 struct RefineJob {
     const LevelDev *L;                 // the model's level tables (device)

@@ -869,37 +869,38 @@ __device__ __forceinline__ void block_store(float *mk, int W, int H, int xl, int
     }
 }
 
-// The poses of one lane's stored slice (map position xl, yl of angle k)
-// whose score, rounded exactly as block_store stores it, is at least
-// t.hot_thr, appended to the hot list as {image, map index}: one atomic per
-// lane that has such poses.  Entries past the capacity are counted, not
-// written (the readers then fall back to the whole map).
+// The poses of one lane's stored block (R rows of TC poses at map position
+// xl, yl of angle k) whose score, rounded exactly as block_store stores it,
+// is at least t.hot_thr, appended to the hot list as {image, map index}: one
+// atomic per row that has such poses.  Entries past the capacity are
+// counted, not written (the readers then fall back to the whole map).
 template <int TC, int R>
 __device__ __forceinline__ void hot_append(const TileWork &t, int k, int xl, int yl, const float2 (&acc)[R][TC / 2]) {
-    static_assert(R * TC <= 32, "one bit per pose of the slice");
-    uint32_t m = 0u;
+    const size_t plane = (size_t)(k - t.k0) * t.H * t.W;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int r = 0; r < R; ++r) {
+        if (yl + r >= t.H)
+            break;
+        uint32_t m = 0u;
 #pragma unroll
         for (int j = 0; j < TC / 2; ++j) {
-            const bool row_in = yl + r < t.H;
             const int x = xl + 2 * j;
-            if (row_in && x < t.W && acc[r][j].x * t.inv_n >= t.hot_thr)
-                m |= 1u << (r * TC + 2 * j);
-            if (row_in && x + 1 < t.W && acc[r][j].y * t.inv_n >= t.hot_thr)
-                m |= 1u << (r * TC + 2 * j + 1);
+            if (x < t.W && acc[r][j].x * t.inv_n >= t.hot_thr)
+                m |= 1u << (2 * j);
+            if (x + 1 < t.W && acc[r][j].y * t.inv_n >= t.hot_thr)
+                m |= 1u << (2 * j + 1);
         }
-    if (!m)
-        return;
-    unsigned pos = atomicAdd(t.hot_cnt, (unsigned)__popc(m));
-    const size_t plane = (size_t)(k - t.k0) * t.H * t.W;
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1u;
-        const int r = b / TC, c = b - r * TC;
-        if (pos < t.hot_cap)
-            t.hot[pos] = make_uint2(t.img, (unsigned)(plane + (size_t)(yl + r) * t.W + xl + c));
-        ++pos;
+        if (!m)
+            continue;
+        unsigned pos = atomicAdd(t.hot_cnt, (unsigned)__popc(m));
+        const size_t row = plane + (size_t)(yl + r) * t.W + xl;
+        while (m) {
+            const int c = __ffs(m) - 1;
+            m &= m - 1u;
+            if (pos < t.hot_cap)
+                t.hot[pos] = make_uint2(t.img, (unsigned)(row + c));
+            ++pos;
+        }
     }
 }
 
@@ -1047,6 +1048,8 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             executed += (unsigned long long)done * (vx * vy);
             block_store<TC>(a.map + (size_t)(k - a.k0) * a.H * a.W, a.W, a.H, x0 - a.ox, y0 - a.oy, acc, a.inv_n,
                             pruned);
+            if (a.hot_cnt && !pruned)
+                hot_append<TC, TR>(a, k, x0 - a.ox, y0 - a.oy, acc);
         }
     }
     for (int r0 = 0; bound && r0 < items; r0 += kQueueItems) {
@@ -1489,11 +1492,11 @@ __global__ void __launch_bounds__(WARPS * 32) score_pairs_kernel(const PairScore
         t.qctr = nullptr;
         t.qcap = t.tcap = 0;
         t.unit = 0;
-        t.hot_cnt = nullptr;
-        t.hot = nullptr;
-        t.hot_cap = 0;
-        t.hot_thr = 0.f;
-        t.img = (unsigned)s_unit[1];
+        t.hot_cnt = P.hot_cnt;
+        t.hot = P.hot;
+        t.hot_cap = P.hot_cap;
+        t.hot_thr = P.hot_thr;
+        t.img = (unsigned)P.job;
         score_items<E, NB, POL, WARPS, TC>(win, P.bxw / 2, s_unit[4], s_unit[5], s_unit[2], s_unit[3], group * tg,
                                        min(group * tg + tg, P.nth), t);
         __syncthreads();   // every warp is done with the window before the next copy

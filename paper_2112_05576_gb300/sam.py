@@ -74,6 +74,7 @@ SIGNATURES = {
                                   ctypes.POINTER(DetectParams), _vp, ctypes.POINTER(Pose), _c_int,
                                   ctypes.POINTER(_c_int)]),
     "sam_pyramid_down": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
+    "sam_pyramid_levels": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp]),
     "sam_gradient": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _vp, _vp, _vp, _vp]),
     "sam_score_map": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_float,
                                _c_int, _vp, _vp]),
@@ -265,9 +266,26 @@ class Model:
         return sx.value, sy.value
 
 
+# sam_pose as a numpy record (the same 32 bytes), for reading whole result
+# arrays at once
+_POSE_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("theta_deg", "<f4"), ("score", "<f4"), ("angle_index", "<i4"),
+                        ("level0_x", "<i4"), ("level0_y", "<i4"), ("scale_index", "<i4")])
+assert _POSE_DTYPE.itemsize == ctypes.sizeof(Pose)
+
+
+def _pose_lists(out, cap, counts) -> List[List[dict]]:
+    """Pose dicts of consecutive result blocks of `cap` sam_pose each, the
+    first counts[i] of block i."""
+    rows = np.frombuffer(out, dtype=_POSE_DTYPE)
+    res = []
+    for i, n in enumerate(counts):
+        res.append([dict(x=r[5], y=r[6], theta_deg=r[2], score=r[3], k=r[4], j=r[7])
+                    for r in rows[i * cap:i * cap + n].tolist()])
+    return res
+
+
 def _poses(arr, n) -> List[dict]:
-    return [dict(x=arr[i].level0_x, y=arr[i].level0_y, theta_deg=arr[i].theta_deg, score=arr[i].score,
-                 k=arr[i].angle_index, j=arr[i].scale_index) for i in range(n)]
+    return _pose_lists(arr, n, [n])[0]
 
 
 def detect(model: Model, image, params: Optional[DetectParams] = None, stream=None, capacity=None):
@@ -328,7 +346,7 @@ def detect_batch(model: Model, images, params: Optional[DetectParams] = None, st
     _check(lib().sam_detect_batch(model.handle, ptr, N, strides[0], W, H, strides[1], on_dev, ctypes.byref(params),
                                   _stream(stream), out, cap, nout), "sam_detect_batch")
     del keep
-    return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(N)]
+    return _pose_lists(out, cap, nout)
 
 
 # ---- individual steps on torch CUDA tensors ----
@@ -339,6 +357,19 @@ def pyramid_down(src, dst, stream=None):
     h, w = src.shape
     _check(lib().sam_pyramid_down(_ptr(src), w, h, src.stride(0), _ptr(dst), dst.stride(0), _stream(stream)),
            "sam_pyramid_down")
+
+
+def pyramid_levels(src, dsts, stream=None):
+    """sam_pyramid_levels (Sec. II image pyramid): levels 1 .. len(dsts) of the
+    device uint8 image src in one launch, level l into dsts[l - 1] (device
+    uint8 tensors of at least floor(h / 2^l) x floor(w / 2^l), rows
+    contiguous)."""
+    h, w = src.shape
+    n = len(dsts)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(d) for d in dsts])
+    strides = (ctypes.c_int * n)(*[d.stride(0) for d in dsts])
+    _check(lib().sam_pyramid_levels(_ptr(src), w, h, src.stride(0), n + 1, ptrs, strides, _stream(stream)),
+           "sam_pyramid_levels")
 
 
 def field_pitch(w, layout, precision=FP32):
@@ -572,7 +603,7 @@ class MultiPlan:
         out = (Pose * (cap * self.n_pairs))()
         nout = (ctypes.c_int * self.n_pairs)()
         _check(lib().sam_multi_run(self._h, _stream(stream), out, cap, nout), "sam_multi_run")
-        return [_poses(out[i * cap:(i + 1) * cap], nout[i]) for i in range(self.n_pairs)]
+        return _pose_lists(out, cap, nout)
 
     def set_tiling(self, sx, sy, tg, warps, cols=6):
         _check(lib().sam_multi_set_tiling(self._h, sx, sy, tg, warps, cols), "sam_multi_set_tiling")

@@ -143,7 +143,10 @@ def test_plan_matches_oracle(plan_batch, prec):
         for p, (g, r) in enumerate(zip(got, ref)):
             assert_same_detections(g, r, what=(prec, rep, p, pairs[p]))
     # every pair's top-level map as the last run left it (a pair whose
-    # template is absent from its image may have every pose pruned)
+    # template is absent from its image may have every pose pruned); a
+    # 16-bit field's map holds its own scores, within the storage bound of
+    # the FP32 ones (candidate extraction rescored the poses it decided on)
+    tol = SCORE_TOL + {sam.FP32: 0.0, sam.FP16: 8e-4, sam.BF16: 6e-3}[prec]
     n_live = 0
     for p, om in enumerate(maps):
         gm, lvl = plan.pair_map(p)
@@ -154,7 +157,7 @@ def test_plan_matches_oracle(plan_batch, prec):
         live = ~pruned
         n_live += int(live.sum())
         if live.any():
-            assert np.max(np.abs(gm[live] - om[live])) < SCORE_TOL, (prec, p)
+            assert np.max(np.abs(gm[live] - om[live])) < tol, (prec, p)
     assert n_live > 0
     plan.close()
 

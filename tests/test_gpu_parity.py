@@ -61,6 +61,26 @@ def test_pyramid_strided_source():
     assert np.array_equal(dst.cpu().numpy(), oracle.pyramid_down(big[:, 10:171]))
 
 
+@pytest.mark.parametrize("h,w,levels", [(1024, 1280, 4), (77, 301, 4), (3, 2, 2), (5, 33, 3), (240, 320, 3),
+                                          (123, 4097, 7), (1944, 2592, 5), (1, 1, 3), (130, 129, 8)])
+def test_pyramid_levels_bit_exact(h, w, levels):
+    # all levels in one launch equal levels - 1 oracle steps (floors of odd
+    # sizes, block edges of the fused kernel, the per-level fallback at 8)
+    rng = np.random.default_rng(h * 31 + w * 7 + levels)
+    img = rng.integers(0, 256, (h, w)).astype(np.uint8)
+    src = _dev(img)
+    dsts = [torch.full((max(1, h >> l), max(1, w >> l) + 13), 77, dtype=torch.uint8, device="cuda")
+            for l in range(1, levels)]
+    sam.pyramid_levels(src, dsts)
+    torch.cuda.synchronize()
+    ref = img
+    for l, d in enumerate(dsts, start=1):
+        ref = oracle.pyramid_down(ref)
+        got = d.cpu().numpy()
+        assert np.array_equal(got[: h >> l, : w >> l], ref), l
+        assert (got[:, w >> l:] == 77).all()   # nothing written past the level's width
+
+
 # ---------------------------------------------------------------------------
 # (a) gradient / threshold / normalise
 # ---------------------------------------------------------------------------
