@@ -116,6 +116,7 @@ struct Plan {
     size_t off_kyx = 0, off_cs = 0, off_ccount = 0, off_refined = 0, off_out = 0, off_nout = 0;
     size_t off_queue = 0, queue_bytes = 0;   // persistent-form storage of the tiled scorer
     size_t off_hot = 0, hot_cap = 0;         // the persistent scorer's hot list (entries of 8 bytes)
+    size_t off_pass = 0;                     // 16-bit candidate filter's pass list (4 bytes per hot entry)
     // refinement-level gradient tiles computed on demand: one mask bit and
     // one list entry per tile of levels 0 .. L - 2 of every image
     int tiles_x[kMaxLevels] = {}, tiles_y[kMaxLevels] = {};
@@ -207,6 +208,10 @@ Plan make_plan(const sam_model *m, int w, int h, int count, bool copy_level0, co
             P.hot_cap = 0;
         P.off_hot = off;
         off += al(P.hot_cap * 8);
+        // the 16-bit candidate filter's pass list (room for every hot entry)
+        P.off_pass = off;
+        if (p.precision != SAM_FP32)
+            off += al(P.hot_cap * 4);
     }
     {
         const int TW = gradient_tile_w(), TH = gradient_tile_h();
@@ -405,7 +410,9 @@ sam_status run_search(sam_model *m, const Plan &P, const sam_detect_params &p, c
         SAM_CU(launch_candidates_hot16(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, rescore_delta(p.precision),
                                        K, kyx, cs, ccount, ws + P.off_scratch, count, hot_cnt, sa.hot, sa.hot_cap,
                                        (const float2 *)(ws + P.off_field[top]), P.field_px[top], P.w[top], P.h[top],
-                                       m->dev[top], p.neighbourhood, m->p.polarity, st, m->nscales));
+                                       m->dev[top], p.neighbourhood, m->p.polarity,
+                                       (unsigned *)(ws + P.off_queue) + kHotCounter + 1, (unsigned *)(ws + P.off_pass),
+                                       st, m->nscales));
     else if (hot_cnt)
         SAM_CU(launch_candidates_hot(sa.map, P.map_img, P.nth, P.gh, P.gw, p.min_score, K, kyx, cs, ccount,
                                      ws + P.off_scratch, count, hot_cnt, sa.hot, sa.hot_cap, st, m->nscales));

@@ -216,6 +216,8 @@ struct Cand16Args {
     Cand *cand;
     size_t cap;
     int *cnt;
+    unsigned *pass_cnt;    // poses passing the filter (zeroed before the launch) and their hot entries
+    unsigned *pass_list;
 };
 
 // Whether no neighbour of map entry idx (the neighbourhood of is_candidate)
@@ -254,196 +256,216 @@ __device__ __forceinline__ bool no_neighbour_above(const float *__restrict__ map
     return true;
 }
 
-// The test over the hot list (entries {view index, map index}); view(i)
-// describes map i.  All threads of the CTA call it.
-template <int NB, typename ViewAt>
-__device__ __forceinline__ void cand16_body(const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
-                                            float min_score, float delta, int polarity, ViewAt view) {
-    __shared__ unsigned s_list[kC16Threads];        // hot entries of this round that pass the filter
-    __shared__ int s_n;
-    __shared__ float s_red[kC16Threads / 32][81];   // per-warp sums: plane d, translation q at 9 d + q
-    __shared__ float s_val[81];
+// Filter: every hot entry (entries {view index, map index}; view(i)
+// describes map i) at or above min_score - delta whose score is within
+// 2 delta of every neighbour's goes to the pass list (grid-stride, one
+// thread per entry).
+template <typename ViewAt>
+__device__ __forceinline__ void cand16_filter(const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
+                                              float min_score, float delta, ViewAt view, unsigned *pass_cnt,
+                                              unsigned *pass_list) {
     const unsigned total = min(*hot_cnt, hot_cap);
-    const size_t G = gridDim.x;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float up = 2.f * delta;
-    // entry b + G (r0 + t) for thread t of CTA b: consecutive entries (often
-    // poses of one instance) go to different CTAs
-    for (size_t r0 = 0; blockIdx.x + G * r0 < total; r0 += kC16Threads) {
-        if (t == 0)
-            s_n = 0;
-        __syncthreads();
-        const size_t e = blockIdx.x + G * (r0 + t);
-        if (e < total) {
-            const uint2 hv = hot[e];
-            const C16View V = view(hv.x);
-            const float v = V.map[hv.y];
-            if (v >= min_score - delta && no_neighbour_above(V.map, V.nth, V.gh, V.gw, hv.y, V.ns, v + up))
-                s_list[atomicAdd(&s_n, 1)] = (unsigned)e;
-        }
-        __syncthreads();
-        const int np = s_n;
-        for (int ip = 0; ip < np; ++ip) {
-            const uint2 hv = hot[s_list[ip]];
-            const C16View V = view(hv.x);
-            const size_t plane = (size_t)V.gh * V.gw;
-            const int nang = V.nth / V.ns;
-            const size_t idx = hv.y;
-            const int kk = (int)(idx / plane);
-            const int rem = (int)(idx - (size_t)kk * plane);
-            const int y = rem / V.gw, x = rem - y * V.gw;
-            const int js = kk / nang, k = kk - js * nang;
-            // the neighbourhood's planes (scale j2, angle k2), the same list
-            // on every thread; dc is the pose's own plane
-            int kl[9];
-            int npl = 0, dc = 0;
-            for (int dj = -1; dj <= 1; ++dj) {
-                const int j2 = js + dj;
-                if (j2 < 0 || j2 >= V.ns)
-                    continue;
-                for (int dk = -1; dk <= 1; ++dk) {
-                    if (dk != 0 && nang == 1)
-                        continue;
-                    if (dj == 0 && dk == 0)
-                        dc = npl;
-                    kl[npl++] = j2 * nang + (k + dk + nang) % nang;
-                }
-            }
-            const float2 *F = V.field;
-            for (int d = 0; d < npl; ++d) {
-                const RotPt *P = V.rot + (size_t)kl[d] * V.n;
-                float acc[9];
-#pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    acc[q] = 0.f;
-                for (int i = t; i < V.n; i += kC16Threads) {
-                    const RotPt p = P[i];
-                    const int bxp = x + p.ox, byp = y + p.oy;
-                    constexpr int D = NB + 2;
-                    float dd[D][D];
-#pragma unroll
-                    for (int yy = 0; yy < D; ++yy)
-#pragma unroll
-                        for (int xx = 0; xx < D; ++xx) {
-                            const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
-                            float v = 0.f;
-                            if (X >= 0 && Y >= 0 && X < V.w && Y < V.h) {
-                                const float2 f = __ldg(F + (size_t)Y * V.w + X);
-                                v = fmaf(p.px, f.x, p.py * f.y);
-                                if (polarity)
-                                    v = fabsf(v);
-                            }
-                            dd[yy][xx] = v;
-                        }
-#pragma unroll
-                    for (int ty = 0; ty < 3; ++ty)
-#pragma unroll
-                        for (int tx = 0; tx < 3; ++tx) {
-                            float mx = -INFINITY;
-#pragma unroll
-                            for (int b = 0; b < NB; ++b)
-#pragma unroll
-                                for (int aa = 0; aa < NB; ++aa)
-                                    mx = fmaxf(mx, dd[ty + b][tx + aa]);
-                            acc[ty * 3 + tx] += mx;
-                        }
-                }
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    float v = acc[q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1)
-                        v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0)
-                        s_red[warp][d * 9 + q] = v;
-                }
-            }
-            __syncthreads();
-            if (t < npl * 9) {
-                float v = 0.f;
-                for (int wv = 0; wv < kC16Threads / 32; ++wv)
-                    v += s_red[wv][t];
-                s_val[t] = v / (float)V.n;
-            }
-            __syncthreads();
-            if (t == 0) {
-                const float sp = s_val[dc * 9 + 4];
-                bool ok = sp >= min_score;
-                for (int d = 0; d < npl && ok; ++d)
-                    for (int q = 0; q < 9; ++q) {
-                        const int X = x + q % 3 - 1, Y = y + q / 3 - 1;
-                        if (X < 0 || Y < 0 || X >= V.gw || Y >= V.gh)
-                            continue;
-                        const size_t key = (size_t)kl[d] * plane + (size_t)Y * V.gw + X;
-                        if (key != idx && !beats(sp, idx, s_val[d * 9 + q], key)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                if (ok) {
-                    const int pos = atomicAdd(V.cnt, 1);
-                    if ((size_t)pos < V.cap) {
-                        Cand c;
-                        c.s = sp;
-                        c.pad = 0;
-                        c.key = idx;
-                        V.cand[pos] = c;
-                    }
-                }
-            }
-            __syncthreads();   // s_red and s_val are reused by the next pose
-        }
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const uint2 hv = hot[e];
+        const C16View V = view(hv.x);
+        const float v = V.map[hv.y];
+        if (v >= min_score - delta && no_neighbour_above(V.map, V.nth, V.gh, V.gw, hv.y, V.ns, v + up))
+            pass_list[atomicAdd(pass_cnt, 1u)] = (unsigned)e;
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(kC16Threads) cand16_kernel(const Cand16Args a) {
-    cand16_body<NB>(a.hot_cnt, a.hot, a.hot_cap, a.min_score, a.delta, a.polarity, [&](unsigned img) {
-        C16View v;
-        v.map = a.map + (size_t)img * a.map_img;
-        v.nth = a.nth;
-        v.gh = a.gh;
-        v.gw = a.gw;
-        v.ns = a.ns;
-        v.field = a.field + (size_t)img * a.field_img_px;
-        v.w = a.w;
-        v.h = a.h;
-        v.rot = a.rot;
-        v.n = a.n;
-        v.cand = a.cand + (size_t)img * a.cap;
-        v.cap = a.cap;
-        v.cnt = a.cnt + img;
-        return v;
-    });
+// Decision: one CTA per listed pose (CTA b the entries b, b + grid, ...)
+// computes the FP32 scores of the pose and its neighbours and keeps the pose
+// if it beats all of them.  All threads of the CTA call it.
+template <int NB, typename ViewAt>
+__device__ __forceinline__ void cand16_eval(const uint2 *hot, const unsigned *pass_cnt, const unsigned *pass_list,
+                                            float min_score, int polarity, ViewAt view) {
+    __shared__ float s_red[kC16Threads / 32][81];   // per-warp sums: plane d, translation q at 9 d + q
+    __shared__ float s_val[81];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned np = *pass_cnt;
+    for (unsigned ip = blockIdx.x; ip < np; ip += gridDim.x) {
+        const uint2 hv = hot[pass_list[ip]];
+        const C16View V = view(hv.x);
+        const size_t plane = (size_t)V.gh * V.gw;
+        const int nang = V.nth / V.ns;
+        const size_t idx = hv.y;
+        const int kk = (int)(idx / plane);
+        const int rem = (int)(idx - (size_t)kk * plane);
+        const int y = rem / V.gw, x = rem - y * V.gw;
+        const int js = kk / nang, k = kk - js * nang;
+        // the neighbourhood's planes (scale j2, angle k2), the same list
+        // on every thread; dc is the pose's own plane
+        int kl[9];
+        int npl = 0, dc = 0;
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int j2 = js + dj;
+            if (j2 < 0 || j2 >= V.ns)
+                continue;
+            for (int dk = -1; dk <= 1; ++dk) {
+                if (dk != 0 && nang == 1)
+                    continue;
+                if (dj == 0 && dk == 0)
+                    dc = npl;
+                kl[npl++] = j2 * nang + (k + dk + nang) % nang;
+            }
+        }
+        const float2 *F = V.field;
+        for (int d = 0; d < npl; ++d) {
+            const RotPt *P = V.rot + (size_t)kl[d] * V.n;
+            float acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                acc[q] = 0.f;
+            for (int i = t; i < V.n; i += kC16Threads) {
+                const RotPt p = P[i];
+                const int bxp = x + p.ox, byp = y + p.oy;
+                constexpr int D = NB + 2;
+                float dd[D][D];
+#pragma unroll
+                for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+                    for (int xx = 0; xx < D; ++xx) {
+                        const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
+                        float v = 0.f;
+                        if (X >= 0 && Y >= 0 && X < V.w && Y < V.h) {
+                            const float2 f = __ldg(F + (size_t)Y * V.w + X);
+                            v = fmaf(p.px, f.x, p.py * f.y);
+                            if (polarity)
+                                v = fabsf(v);
+                        }
+                        dd[yy][xx] = v;
+                    }
+#pragma unroll
+                for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 3; ++tx) {
+                        float mx = -INFINITY;
+#pragma unroll
+                        for (int b = 0; b < NB; ++b)
+#pragma unroll
+                            for (int aa = 0; aa < NB; ++aa)
+                                mx = fmaxf(mx, dd[ty + b][tx + aa]);
+                        acc[ty * 3 + tx] += mx;
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                float v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0)
+                    s_red[warp][d * 9 + q] = v;
+            }
+        }
+        __syncthreads();
+        if (t < npl * 9) {
+            float v = 0.f;
+            for (int wv = 0; wv < kC16Threads / 32; ++wv)
+                v += s_red[wv][t];
+            s_val[t] = v / (float)V.n;
+        }
+        __syncthreads();
+        if (t == 0) {
+            const float sp = s_val[dc * 9 + 4];
+            bool ok = sp >= min_score;
+            for (int d = 0; d < npl && ok; ++d)
+                for (int q = 0; q < 9; ++q) {
+                    const int X = x + q % 3 - 1, Y = y + q / 3 - 1;
+                    if (X < 0 || Y < 0 || X >= V.gw || Y >= V.gh)
+                        continue;
+                    const size_t key = (size_t)kl[d] * plane + (size_t)Y * V.gw + X;
+                    if (key != idx && !beats(sp, idx, s_val[d * 9 + q], key)) {
+                        ok = false;
+                        break;
+                    }
+                }
+            if (ok) {
+                const int pos = atomicAdd(V.cnt, 1);
+                if ((size_t)pos < V.cap) {
+                    Cand c;
+                    c.s = sp;
+                    c.pad = 0;
+                    c.key = idx;
+                    V.cand[pos] = c;
+                }
+            }
+        }
+        __syncthreads();   // s_red and s_val are reused by the next pose
+    }
 }
 
-// The same over a job list: pair p's map and candidate list in cj[p], its
-// FP32 field and model points in rj[p].
+// A 16-bit map's candidates: the single-model form (image = view index).
+__device__ __forceinline__ C16View c16_view(const Cand16Args &a, unsigned img) {
+    C16View v;
+    v.map = a.map + (size_t)img * a.map_img;
+    v.nth = a.nth;
+    v.gh = a.gh;
+    v.gw = a.gw;
+    v.ns = a.ns;
+    v.field = a.field + (size_t)img * a.field_img_px;
+    v.w = a.w;
+    v.h = a.h;
+    v.rot = a.rot;
+    v.n = a.n;
+    v.cand = a.cand + (size_t)img * a.cap;
+    v.cap = a.cap;
+    v.cnt = a.cnt + img;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) cand16_filter_kernel(const Cand16Args a) {
+    cand16_filter(a.hot_cnt, a.hot, a.hot_cap, a.min_score, a.delta, [&](unsigned i) { return c16_view(a, i); },
+                  a.pass_cnt, a.pass_list);
+}
+
 template <int NB>
-__global__ void __launch_bounds__(kC16Threads) cand16_jobs_kernel(const CandJob *__restrict__ cj,
-                                                                  const RescoreJob *__restrict__ rj,
-                                                                  const unsigned *hot_cnt, const uint2 *hot,
-                                                                  unsigned hot_cap, float min_score, float delta,
-                                                                  int polarity) {
-    cand16_body<NB>(hot_cnt, hot, hot_cap, min_score, delta, polarity, [&](unsigned p) {
-        const CandJob &c = cj[p];
-        const RescoreJob &r = rj[p];
-        C16View v;
-        v.map = c.map;
-        v.nth = c.nth;
-        v.gh = c.gh;
-        v.gw = c.gw;
-        v.ns = c.ns;
-        v.field = r.field;
-        v.w = r.w;
-        v.h = r.h;
-        v.rot = r.rot;
-        v.n = r.n;
-        v.cand = c.cand;
-        v.cap = c.cap;
-        v.cnt = c.cnt;
-        return v;
-    });
+__global__ void __launch_bounds__(kC16Threads) cand16_eval_kernel(const Cand16Args a) {
+    cand16_eval<NB>(a.hot, a.pass_cnt, a.pass_list, a.min_score, a.polarity,
+                    [&](unsigned i) { return c16_view(a, i); });
+}
+
+// The job-list form: pair p's map and candidate list in cj[p], its FP32
+// field and model points in rj[p].
+__device__ __forceinline__ C16View c16_job_view(const CandJob *cj, const RescoreJob *rj, unsigned p) {
+    const CandJob &c = cj[p];
+    const RescoreJob &r = rj[p];
+    C16View v;
+    v.map = c.map;
+    v.nth = c.nth;
+    v.gh = c.gh;
+    v.gw = c.gw;
+    v.ns = c.ns;
+    v.field = r.field;
+    v.w = r.w;
+    v.h = r.h;
+    v.rot = r.rot;
+    v.n = r.n;
+    v.cand = c.cand;
+    v.cap = c.cap;
+    v.cnt = c.cnt;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) cand16_filter_jobs_kernel(const CandJob *__restrict__ cj,
+                                                                 const RescoreJob *__restrict__ rj,
+                                                                 const unsigned *hot_cnt, const uint2 *hot,
+                                                                 unsigned hot_cap, float min_score, float delta,
+                                                                 unsigned *pass_cnt, unsigned *pass_list) {
+    cand16_filter(hot_cnt, hot, hot_cap, min_score, delta, [&](unsigned p) { return c16_job_view(cj, rj, p); },
+                  pass_cnt, pass_list);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kC16Threads) cand16_eval_jobs_kernel(const CandJob *__restrict__ cj,
+                                                                       const RescoreJob *__restrict__ rj,
+                                                                       const uint2 *hot, const unsigned *pass_cnt,
+                                                                       const unsigned *pass_list, float min_score,
+                                                                       int polarity) {
+    cand16_eval<NB>(hot, pass_cnt, pass_list, min_score, polarity,
+                    [&](unsigned p) { return c16_job_view(cj, rj, p); });
 }
 
 // Candidates of a job list's maps from the batch's hot list (entries {pair,
@@ -983,7 +1005,8 @@ cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, i
                                     float delta, int K, int32_t *out_kyx, float *out_s, int *count, void *scratch,
                                     int n_img, const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
                                     const float2 *field32, size_t field_img_px, int w, int h, const LevelDev &L,
-                                    int nbhd, int polarity, cudaStream_t st, int ns) {
+                                    int nbhd, int polarity, unsigned *pass_cnt, unsigned *pass_list,
+                                    cudaStream_t st, int ns) {
     const size_t cap = cand_cap(nth, gh, gw, ns);
     int *cnt = reinterpret_cast<int *>(scratch);
     Cand *cand = reinterpret_cast<Cand *>(reinterpret_cast<char *>(scratch) + 256 * ((n_img * sizeof(int) + 255) / 256));
@@ -1012,14 +1035,17 @@ cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, i
     a.cand = cand;
     a.cap = cap;
     a.cnt = cnt;
-    // eight resident CTAs per SM: the few poses that pass the filter are
-    // spread one or two per CTA
+    a.pass_cnt = pass_cnt;
+    a.pass_list = pass_list;
+    // the filter, then the decision with eight resident CTAs per SM: the
+    // poses that pass (a few hundred to a few thousand) one or two per CTA
+    cand16_filter_kernel<<<2 * 152, 256, 0, st>>>(a);
     if (nbhd == 3)
-        cand16_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(a);
+        cand16_eval_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(a);
     else
-        cand16_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(a);
+        cand16_eval_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(a);
     topk_kernel<<<n_img, 1024, 0, st>>>(cand, cap, cnt, K, gh, gw, out_kyx, out_s, count);
-    count_launches(2);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -1036,17 +1062,20 @@ cudaError_t launch_candidates_hot_jobs(const CandJob *jobs, int n_jobs, float mi
 
 cudaError_t launch_candidates_hot16_jobs(const CandJob *cjobs, const RescoreJob *rjobs, int n_jobs, float min_score,
                                          float delta, int K, int nbhd, int polarity, const unsigned *hot_cnt,
-                                         const uint2 *hot, unsigned hot_cap, cudaStream_t st) {
+                                         const uint2 *hot, unsigned hot_cap, unsigned *pass_cnt,
+                                         unsigned *pass_list, cudaStream_t st) {
     if (n_jobs <= 0)
         return cudaSuccess;
+    cand16_filter_jobs_kernel<<<2 * 152, 256, 0, st>>>(cjobs, rjobs, hot_cnt, hot, hot_cap, min_score, delta, pass_cnt,
+                                                       pass_list);
     if (nbhd == 3)
-        cand16_jobs_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot_cnt, hot, hot_cap, min_score, delta,
-                                                              polarity);
+        cand16_eval_jobs_kernel<3><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot, pass_cnt, pass_list, min_score,
+                                                                   polarity);
     else
-        cand16_jobs_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot_cnt, hot, hot_cap, min_score, delta,
-                                                              polarity);
+        cand16_eval_jobs_kernel<1><<<8 * 152, kC16Threads, 0, st>>>(cjobs, rjobs, hot, pass_cnt, pass_list, min_score,
+                                                                   polarity);
     topk_jobs_kernel<<<n_jobs, 1024, 0, st>>>(cjobs, K);
-    count_launches(2);
+    count_launches(3);
     return cudaGetLastError();
 }
 

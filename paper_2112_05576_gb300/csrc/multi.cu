@@ -74,7 +74,7 @@ struct sam_multi {
     // hot list of the pairs scorer (see TiledArgs): candidates (and, for a
     // 16-bit field, their FP32 decision) from the listed poses only
     bool hot = false;
-    size_t off_hot = 0, hot_cap = 0;
+    size_t off_hot = 0, hot_cap = 0, off_pass = 0;
     bool dirty = true;                 // descriptors / graph must be rebuilt
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -287,7 +287,7 @@ sam_status upload_descriptors(sam_multi *mp) {
 sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
     char *base = (char *)mp->base;
     const int np = (int)mp->pp.size();
-    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (2 + 3 * (size_t)np), st));
+    MU_CU(cudaMemsetAsync(base + mp->off_counters, 0, sizeof(int) * (3 + 3 * (size_t)np), st));
     size_t o = mp->off_pyr;
     for (int l = 1; l < mp->Lmax; ++l) {
         const int n = mp->pyr_count[l];
@@ -312,7 +312,9 @@ sam_status enqueue_run(sam_multi *mp, cudaStream_t st) {
         MU_CU(launch_candidates_hot16_jobs((const CandJob *)(base + mp->off_cjobs),
                                            (const RescoreJob *)(base + mp->off_rsjobs), np, mp->p.min_score,
                                            rescore_delta(mp->p.precision), mp->p.top_k, mp->p.neighbourhood,
-                                           mp->models[0]->p.polarity, hot_cnt, hot, (unsigned)mp->hot_cap, st));
+                                           mp->models[0]->p.polarity, hot_cnt, hot, (unsigned)mp->hot_cap,
+                                           (unsigned *)(base + mp->off_counters) + 2 + 3 * (size_t)np,
+                                           (unsigned *)(base + mp->off_pass), st));
     } else if (mp->hot) {
         MU_CU(launch_candidates_hot_jobs((const CandJob *)(base + mp->off_cjobs), np, mp->p.min_score, mp->p.top_k,
                                          hot_cnt, hot, (unsigned)mp->hot_cap, st));
@@ -521,6 +523,9 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
     if (mp->hot) {
         mp->off_hot = off;
         off += al(mp->hot_cap * 8);
+        mp->off_pass = off;   // the 16-bit candidate filter's pass list
+        if (params->precision != SAM_FP32)
+            off += al(mp->hot_cap * 4);
     }
     for (PairPlan &q : mp->pp) {
         q.off_rescore = off;
@@ -528,9 +533,9 @@ sam_status sam_multi_create(sam_model *const *models, int n_models, const int32_
             off += al(rescore_scratch_bytes(q.map_img));
     }
     // counters: work counter, candidate counts, output counts, rescore
-    // counts (one per pair each), hot-list counter
+    // counts (one per pair each), hot-list counter, pass-list counter
     mp->off_counters = off;
-    off += al(sizeof(int) * (2 + 3 * (size_t)n_pairs));
+    off += al(sizeof(int) * (3 + 3 * (size_t)n_pairs));
     // descriptors
     mp->off_desc = off;
     mp->pyr_count.assign(mp->Lmax, 0);

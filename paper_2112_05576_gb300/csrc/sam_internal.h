@@ -285,7 +285,9 @@ struct DrainQueue {
     float hot_thr = 0.f;
     bool *hot_made = nullptr;    // set true when the launch fills the hot list
 };
-// Index of the hot-list counter among the persistent form's counters.
+// Index of the hot-list counter among the persistent form's counters (the
+// one after it counts the 16-bit candidate filter's pass list; both are
+// zeroed with the others before every launch).
 constexpr int kHotCounter = 8;
 // Workspace bytes that cover the persistent form of every tiling the
 // autotuner tries for a gw x gh map with nth angles over `count` images.
@@ -461,14 +463,17 @@ cudaError_t launch_rescore(const LevelDev &L, const float2 *field32, size_t fiel
                            const PoseWindow *window = nullptr);
 // Candidates of a map scored from a 16-bit field, from its scorer's hot list
 // (threshold min_score - delta, capacity every pose): the poses whose 16-bit
-// score is within 2 delta of every neighbour's are rescored in FP32 with
-// their whole neighbourhood (field32: the level's FP32 pixel-layout field)
-// and kept if they are strict local maxima of the FP32 scores.
+// score is within 2 delta of every neighbour's are listed (pass_cnt, zeroed
+// before the launch; pass_list, room for every hot entry), then rescored in
+// FP32 with their whole neighbourhood (field32: the level's FP32
+// pixel-layout field) and kept if they are strict local maxima of the FP32
+// scores.
 cudaError_t launch_candidates_hot16(const float *map, size_t map_img, int nth, int gh, int gw, float min_score,
                                     float delta, int K, int32_t *out_kyx, float *out_s, int *count, void *scratch,
                                     int n_img, const unsigned *hot_cnt, const uint2 *hot, unsigned hot_cap,
                                     const float2 *field32, size_t field_img_px, int w, int h, const LevelDev &L,
-                                    int nbhd, int polarity, cudaStream_t st, int ns = 1);
+                                    int nbhd, int polarity, unsigned *pass_cnt, unsigned *pass_list,
+                                    cudaStream_t st, int ns = 1);
 
 // (d) candidates: local maxima + top-K per image
 struct Cand {
@@ -559,7 +564,8 @@ cudaError_t launch_candidates_hot_jobs(const CandJob *jobs, int n_jobs, float mi
                                        cudaStream_t st);
 cudaError_t launch_candidates_hot16_jobs(const CandJob *cjobs, const RescoreJob *rjobs, int n_jobs, float min_score,
                                          float delta, int K, int nbhd, int polarity, const unsigned *hot_cnt,
-                                         const uint2 *hot, unsigned hot_cap, cudaStream_t st);
+                                         const uint2 *hot, unsigned hot_cap, unsigned *pass_cnt,
+                                         unsigned *pass_list, cudaStream_t st);
 
 struct RefineJob {
     const LevelDev *L;                 // the model's level tables (device)

@@ -1004,6 +1004,46 @@ __device__ __forceinline__ void slice_store(int item, int src, int part, int stx
         hot_append<TC, RD>(a, k, x0 - a.ox, y0 - a.oy, acc);
 }
 
+// One lane's edge-presence masks of 8 model points i0 .. i0 + 7 for its BW
+// poses (bit c: the window of the pose c columns right of the first holds an
+// edge pixel the point can take a positive vote from), from the dilated
+// plane row words.  qo holds, in lane i0 + j (mod 32), point i0 + j's word
+// offset and bit shift (UNI: one lane per pose row) or its column offset
+// and word offset.  Bits past BW are left as they come (the caller masks
+// them); CHECK: points past n give empty masks.
+template <bool UNI, bool CHECK, int BW>
+__device__ __forceinline__ void bound_masks8(const uint32_t *rbase, int xb, int2 qo, int i0, int n,
+                                             uint32_t (&mm0)[8], uint32_t (&mm1)[8], uint32_t (&mm2)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int q0 = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
+        const int q1 = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+        const uint32_t *row;
+        int sh;
+        if (UNI) {
+            row = rbase + q0;
+            sh = q1;
+        } else {
+            const int b = xb + q0;   // window column of the first pose's centre
+            row = rbase + q1 + (b >> 5);
+            sh = b & 31;
+        }
+        const uint32_t w0 = row[0], w1 = row[1], w2 = row[2];
+        uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh), m2 = 0u;
+        if (BW > 64)
+            m2 = __funnelshift_r(w2, row[3], sh);
+        if (CHECK) {
+            const bool in = i0 + j < n;
+            m0 = in ? m0 : 0u;
+            m1 = in ? m1 : 0u;
+            m2 = in ? m2 : 0u;
+        }
+        mm0[j] = m0;
+        mm1[j] = m1;
+        mm2[j] = m2;
+    }
+}
+
 // The (angle, warp tile) items of one CTA work unit over its staged window
 // (origin wx0, wy0; row pitch pp pixel pairs), written into t.map.
 //
@@ -1095,35 +1135,27 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     const int ii = i0 + lane;
                     qo = make_int2(0, 0);
                     if (ii < a.n) {
-                        // the column offset, and the word offset of the row
-                        // offset in the bitmap plane of the quadrant of the
-                        // point's rotated direction
+                        // the word offset of the row offset in the bitmap
+                        // plane of the quadrant of the point's rotated
+                        // direction, and the column offset; with one lane
+                        // per pose row every lane starts at column xb, and
+                        // the loading lane resolves the column into the
+                        // word offset and the bit shift once for the warp
                         const RotPt t = P[ii];
-                        qo = make_int2(t.ox, (POL ? 0 : quadrant(t.px, t.py)) * (int)plane + t.oy * dmw);
+                        const int qpo = (POL ? 0 : quadrant(t.px, t.py)) * (int)plane + t.oy * dmw;
+                        if (LPR == 1) {
+                            const int b = xb + t.ox;   // window column of the first pose's centre
+                            qo = make_int2(qpo + (b >> 5), b & 31);
+                        } else {
+                            qo = make_int2(t.ox, qpo);
+                        }
                     }
                 }
                 uint32_t mm0[8], mm1[8], mm2[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int qox = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
-                    const int qpo = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
-                    const int b = xb + qox;   // window column of the first pose's centre
-                    const uint32_t *row = rbase + qpo + (b >> 5);
-                    const int sh = b & 31;
-                    const uint32_t w0 = row[0], w1 = row[1], w2 = row[2], w3 = row[3];
-                    uint32_t m0 = __funnelshift_r(w0, w1, sh), m1 = __funnelshift_r(w1, w2, sh),
-                             m2 = __funnelshift_r(w2, w3, sh);
-                    if (BW <= 64) {
-                        m1 &= BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u);
-                        m2 = 0u;
-                    } else {
-                        m2 &= (1u << ((BW - 64) & 31)) - 1u;
-                    }
-                    const bool in = i0 + j < a.n;
-                    mm0[j] = in ? m0 : 0u;
-                    mm1[j] = in ? m1 : 0u;
-                    mm2[j] = in ? m2 : 0u;
-                }
+                if (i0 + 8 <= a.n)
+                    bound_masks8<LPR == 1, false, BW>(rbase, xb, qo, i0, a.n, mm0, mm1, mm2);
+                else
+                    bound_masks8<LPR == 1, true, BW>(rbase, xb, qo, i0, a.n, mm0, mm1, mm2);
                 // carry-save tree over the 8 masks
                 auto csa = [](uint32_t &h, uint32_t &l, uint32_t a_, uint32_t b_, uint32_t c_) {
                     const uint32_t u = a_ ^ b_;
@@ -1181,19 +1213,22 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                     if (need > 0) {
                         // every count < 2^m <= need when planes m .. 15 are clear
                         const int m = 31 - __clz(need);
+                        // (bits past the lane's BW poses hold no count)
+                        constexpr uint32_t M1 = BW >= 64 ? 0xffffffffu : ((1u << ((BW - 32) & 31)) - 1u);
+                        constexpr uint32_t M2 = BW > 64 ? ((1u << ((BW - 64) & 31)) - 1u) : 0u;
                         uint32_t hi = 0u;
 #pragma unroll
                         for (int pq = 0; pq < 16; ++pq) {
                             if (pq < m)
                                 continue;
                             if (pq == 0)
-                                hi |= ones0 | ones1 | ones2;
+                                hi |= ones0 | (ones1 & M1) | (ones2 & M2);
                             else if (pq == 1)
-                                hi |= twos0 | twos1 | twos2;
+                                hi |= twos0 | (twos1 & M1) | (twos2 & M2);
                             else if (pq == 2)
-                                hi |= fours0 | fours1 | fours2;
+                                hi |= fours0 | (fours1 & M1) | (fours2 & M2);
                             else
-                                hi |= pl[pq][0] | pl[pq][1] | pl[pq][2];
+                                hi |= pl[pq][0] | (pl[pq][1] & M1) | (pl[pq][2] & M2);
                         }
                         if (__all_sync(0xffffffffu, hi == 0u)) {
                             all_dead = true;

@@ -322,11 +322,14 @@ def _has_cuda():
         return False
 
 
-def detect_batch(model: Model, images, params: Optional[DetectParams] = None, stream=None, capacity=None):
+def detect_batch(model: Model, images, params: Optional[DetectParams] = None, stream=None, capacity=None,
+                 as_arrays=False):
     """sam_detect_batch (Sec. II, per image): detect in a (N, H, W) uint8 batch,
     a torch CUDA tensor or a host torch tensor / numpy array (copied by the
     library; pinned host memory makes the copy asynchronous); returns one pose
-    list per image."""
+    list per image, or with as_arrays the library's results as they are: an
+    (N, capacity) numpy record array of sam_pose (fields of Pose) and the
+    (N,) int32 array of poses per image."""
     params = params or default_detect_params()
     cap = capacity or params.max_detections
     if isinstance(images, np.ndarray):
@@ -346,6 +349,9 @@ def detect_batch(model: Model, images, params: Optional[DetectParams] = None, st
     _check(lib().sam_detect_batch(model.handle, ptr, N, strides[0], W, H, strides[1], on_dev, ctypes.byref(params),
                                   _stream(stream), out, cap, nout), "sam_detect_batch")
     del keep
+    if as_arrays:
+        return (np.frombuffer(out, dtype=_POSE_DTYPE).reshape(N, cap),
+                np.frombuffer(nout, dtype=np.int32))
     return _pose_lists(out, cap, nout)
 
 
