@@ -916,6 +916,7 @@ def run_gpu(args):
             forms[name] = {"value": top_pose_points(model, B) / (fms * 1e-3), "ms_per_step": round(fms, 4),
                            "ms_per_detection": round(fms / B, 5),
                            "score_map_ms": round(pf["score_map"][0] / max(1, pf["score_map"][1]), 4),
+                           "candidates_ms": round(pf["candidates"][0] / max(1, pf["candidates"][1]), 4),
                            "same_detections_as_fp32": bool(same), "steps": n_form,
                            "tiling": dict(zip(("sx", "sy", "tg", "warps", "cols"), sam.model_tiling(model, code, B)))}
 

@@ -1008,24 +1008,26 @@ __device__ __forceinline__ void slice_store(int item, int src, int part, int stx
 // poses (bit c: the window of the pose c columns right of the first holds an
 // edge pixel the point can take a positive vote from), from the dilated
 // plane row words.  qo holds, in lane i0 + j (mod 32), point i0 + j's word
-// offset and bit shift (UNI: one lane per pose row) or its column offset
-// and word offset.  Bits past BW are left as they come (the caller masks
-// them); CHECK: points past n give empty masks.
+// offset and bit shift (UNI: one lane per pose row), or 32 times the word
+// offset plus the shift for the first lane of a row, to which a lane adds
+// xoff, its own first pose's column less the first lane's.  Bits past BW
+// are left as they come (the caller masks them); CHECK: points past n give
+// empty masks.
 template <bool UNI, bool CHECK, int BW>
-__device__ __forceinline__ void bound_masks8(const uint32_t *rbase, int xb, int2 qo, int i0, int n,
+__device__ __forceinline__ void bound_masks8(const uint32_t *rbase, int xoff, int2 qo, int i0, int n,
                                              uint32_t (&mm0)[8], uint32_t (&mm1)[8], uint32_t (&mm2)[8]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int q0 = __shfl_sync(0xffffffffu, qo.x, (i0 + j) & 31);
-        const int q1 = __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31);
+        const int q1 = UNI ? __shfl_sync(0xffffffffu, qo.y, (i0 + j) & 31) : 0;
         const uint32_t *row;
         int sh;
         if (UNI) {
             row = rbase + q0;
             sh = q1;
         } else {
-            const int b = xb + q0;   // window column of the first pose's centre
-            row = rbase + q1 + (b >> 5);
+            const int b = q0 + xoff;   // 32 * word offset + shift of this lane's first pose
+            row = rbase + (b >> 5);
             sh = b & 31;
         }
         const uint32_t w0 = row[0], w1 = row[1], w2 = row[2];
@@ -1122,6 +1124,7 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             // this lane's pose row in the bitmaps and its first pose's column
             const uint32_t *rbase = cbits + (size_t)(yrow - wy0) * dmw;
             const int xb = xseg - wx0;
+            const int xb0 = xb - (lane % LPR) * BW;   // the first lane of the row's column
             // Early exit: after point i a pose still needs E_i >= need_i =
             // emin - (n - i) edge hits (every remaining point adds at most
             // one).  Every 32 points the lane checks, from its top count
@@ -1147,15 +1150,17 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                             const int b = xb + t.ox;   // window column of the first pose's centre
                             qo = make_int2(qpo + (b >> 5), b & 31);
                         } else {
-                            qo = make_int2(t.ox, qpo);
+                            // for the first lane of each pose row: word
+                            // offset * 32 + shift in one (all terms >= 0)
+                            qo = make_int2(32 * qpo + xb0 + t.ox, 0);
                         }
                     }
                 }
                 uint32_t mm0[8], mm1[8], mm2[8];
                 if (i0 + 8 <= a.n)
-                    bound_masks8<LPR == 1, false, BW>(rbase, xb, qo, i0, a.n, mm0, mm1, mm2);
+                    bound_masks8<LPR == 1, false, BW>(rbase, xb - xb0, qo, i0, a.n, mm0, mm1, mm2);
                 else
-                    bound_masks8<LPR == 1, true, BW>(rbase, xb, qo, i0, a.n, mm0, mm1, mm2);
+                    bound_masks8<LPR == 1, true, BW>(rbase, xb - xb0, qo, i0, a.n, mm0, mm1, mm2);
                 // carry-save tree over the 8 masks
                 auto csa = [](uint32_t &h, uint32_t &l, uint32_t a_, uint32_t b_, uint32_t c_) {
                     const uint32_t u = a_ ^ b_;
