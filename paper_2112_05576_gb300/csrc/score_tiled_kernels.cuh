@@ -758,8 +758,9 @@ __global__ void __launch_bounds__(WARPS * 32) score_fused_kernel(const __grid_co
         t.bits = bits;
         t.unit = s_job[1];
         if (kind == 1) {
+            // (with the bound on, score_items ends with a CTA barrier after
+            // thread 0 published the unit's last tasks)
             score_items<E, NB, POL, WARPS, TC>(win, pp, s_org[0], s_org[1], u.stx0, u.sty0, u.k_begin, u.k_end, t);
-            __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
                 atomicAdd(&a.qctr[4], 1u);   // this unit's tasks are all published
@@ -1308,6 +1309,9 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
                 s_mask[it][lane >> 3] = wq;
         }
         __syncthreads();
+        // one surviving slice per lane, in (item, slice, lane) order
+        constexpr int CH = WARPS * 32 < kTaskSlices ? WARPS * 32 : kTaskSlices;   // slices per task
+        __shared__ unsigned s_qb, s_tb, s_nt;
         if (warp == 0) {   // queue offsets: exclusive prefix sum of the surviving counts
             int carry = 0;
             for (int b0 = 0; b0 < ni; b0 += 32) {
@@ -1330,34 +1334,33 @@ __device__ __forceinline__ void score_items(const typename Pairs<E>::Raw *win, i
             }
             if (lane == 0)
                 s_off[ni] = carry;
-        }
-        __syncthreads();
-        const int total = s_off[ni];
-        // one surviving slice per lane, in (item, slice, lane) order
-        constexpr int CH = WARPS * 32 < kTaskSlices ? WARPS * 32 : kTaskSlices;   // slices per task
-        if (a.queue) {
-            // persistent form: the slices to the global queue and one task
-            // per CH of them (a CTA's worth), each published once written
-            __shared__ unsigned s_qb, s_tb, s_nt;
-            if (threadIdx.x == 0) {
-                const unsigned nt = (unsigned)((total + CH - 1) / CH);
+            // persistent form: the unit's queue run and its tasks, allocated
+            // by the same warp (one CTA barrier less)
+            if (a.queue && lane == 0) {
+                const int tot = carry;
+                const unsigned nt = (unsigned)((tot + CH - 1) / CH);
                 unsigned qb = ~0u, tb = 0;
-                if (total > 0) {
-                    qb = atomicAdd(&a.qctr[0], (unsigned)total);
+                if (tot > 0) {
+                    qb = atomicAdd(&a.qctr[0], (unsigned)tot);
                     tb = atomicAdd(&a.qctr[1], nt);
-                    if (qb + (unsigned)total > a.qcap || tb + nt > a.tcap) {
+                    if (qb + (unsigned)tot > a.qcap || tb + nt > a.tcap) {
                         atomicExch(a.err, 1);   // capacities cover every slice: cannot happen
                         qb = ~0u;
                     } else {
                         for (unsigned j = 0; j < nt; ++j)
-                            a.tasks[tb + j] = make_int4(a.unit, (int)(qb + j * CH), min(CH, total - (int)(j * CH)), 0);
+                            a.tasks[tb + j] = make_int4(a.unit, (int)(qb + j * CH), min(CH, tot - (int)(j * CH)), 0);
                     }
                 }
                 s_qb = qb;
                 s_tb = tb;
                 s_nt = qb == ~0u ? 0u : nt;
             }
-            __syncthreads();
+        }
+        __syncthreads();
+        const int total = s_off[ni];
+        if (a.queue) {
+            // persistent form: the slices to the global queue and one task
+            // per CH of them (a CTA's worth), each published once written
             const unsigned qb = s_qb;
             if (qb != ~0u) {
                 for (int it = warp; it < ni; it += WARPS) {
