@@ -869,6 +869,7 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
     __shared__ float s[kMaxTopK];
     __shared__ unsigned long long key[kMaxTopK];
     __shared__ int px[kMaxTopK], py[kMaxTopK], pk[kMaxTopK];
+    __shared__ int kx[kMaxTopK], ky[kMaxTopK];   // positions kept so far
     int n2 = 1;
     while (n2 < nc)
         n2 <<= 1;
@@ -905,7 +906,7 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
                 break;   // sorted: the rest are dead too
             bool ok = true;
             for (int q = 0; q < kept; ++q) {
-                const long long dx = px[i] - out[q].level0_x, dy = py[i] - out[q].level0_y;
+                const long long dx = px[i] - kx[q], dy = py[i] - ky[q];
                 if (4 * (dx * dx + dy * dy) < ms2) {
                     ok = false;
                     break;
@@ -924,6 +925,8 @@ __device__ void nms_body(const float4 *__restrict__ R, int nc, int w0, int h0, i
             p.level0_x = px[i];
             p.level0_y = py[i];
             p.scale_index = sj;
+            kx[kept] = px[i];
+            ky[kept] = py[i];
             out[kept++] = p;
         }
         *n_out = kept;

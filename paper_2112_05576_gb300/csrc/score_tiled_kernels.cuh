@@ -229,28 +229,59 @@ __device__ __forceinline__ void point_nb3(const typename Pairs<E>::Raw *win, int
                                           float2 pxx, float2 pyy, float2 (&acc)[R][TC / 2]) {
     constexpr int NP = ODD ? (TC + 4) / 2 : (TC + 2) / 2;   // pixel pairs per row
     constexpr int OFF = ODD ? 1 : 0;
-    float hp2[TC], hp1[TC];
+    if constexpr (R < TC) {
+        // fewer rows than columns (the 2-row slices of the drain, 8 x 10
+        // blocks): the 3-row maxima of the TC + 2 columns first, then the
+        // 3-column maxima, R (TC + 2) + R TC three-input maxima instead of
+        // (R + 2) TC + R TC (a maximum is exact in any order)
+        float dp2[TC + 2], dp1[TC + 2];
 #pragma unroll
-    for (int r = 0; r < R + 2; ++r) {
-        const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
-        float d[TC + 4];
-        dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
-        float h[TC];
+        for (int r = 0; r < R + 2; ++r) {
+            const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
+            float d[TC + 4];
+            dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
+            if (r >= 2) {
+                float v[TC + 2];
 #pragma unroll
-        for (int c = 0; c < TC; ++c)
-            h[c] = max3(d[OFF + c], d[OFF + c + 1], d[OFF + c + 2]);
-        if (r >= 2) {
+                for (int c = 0; c < TC + 2; ++c)
+                    v[c] = max3(dp2[c], dp1[c], d[OFF + c]);
 #pragma unroll
-            for (int j = 0; j < TC / 2; ++j) {
-                const float v0 = max3(hp2[2 * j], hp1[2 * j], h[2 * j]);
-                const float v1 = max3(hp2[2 * j + 1], hp1[2 * j + 1], h[2 * j + 1]);
-                acc[r - 2][j] = __fadd2_rn(acc[r - 2][j], make_float2(v0, v1));
+                for (int j = 0; j < TC / 2; ++j) {
+                    const float v0 = max3(v[2 * j], v[2 * j + 1], v[2 * j + 2]);
+                    const float v1 = max3(v[2 * j + 1], v[2 * j + 2], v[2 * j + 3]);
+                    acc[r - 2][j] = __fadd2_rn(acc[r - 2][j], make_float2(v0, v1));
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < TC + 2; ++c) {
+                dp2[c] = dp1[c];
+                dp1[c] = d[OFF + c];
             }
         }
+    } else {
+        float hp2[TC], hp1[TC];
 #pragma unroll
-        for (int c = 0; c < TC; ++c) {
-            hp2[c] = hp1[c];
-            hp1[c] = h[c];
+        for (int r = 0; r < R + 2; ++r) {
+            const typename Pairs<E>::Raw *row = win + (row0 + r) * pp;
+            float d[TC + 4];
+            dots_row<E, POL, TC>(row, pair0, d, NP, pxx, pyy);
+            float h[TC];
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+                h[c] = max3(d[OFF + c], d[OFF + c + 1], d[OFF + c + 2]);
+            if (r >= 2) {
+#pragma unroll
+                for (int j = 0; j < TC / 2; ++j) {
+                    const float v0 = max3(hp2[2 * j], hp1[2 * j], h[2 * j]);
+                    const float v1 = max3(hp2[2 * j + 1], hp1[2 * j + 1], h[2 * j + 1]);
+                    acc[r - 2][j] = __fadd2_rn(acc[r - 2][j], make_float2(v0, v1));
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < TC; ++c) {
+                hp2[c] = hp1[c];
+                hp1[c] = h[c];
+            }
         }
     }
 }
