@@ -207,3 +207,26 @@ def test_executed_pose_point_counter(cfg):
     _map(m, 3, top, 2, cfg, min_score=0.6, early=1)
     ex = sam.executed_pose_points(reset=True)
     assert 0 < ex < nominal
+
+
+def test_tiled_longest_single_window_sum_matches_oracle():
+    # the largest part whose rotated extent (with the edge bitmaps) still
+    # fits one staged window at the smallest tiling (one angle per CTA, 4
+    # warps): a 104-pixel part of 1077 points, every pose's vote sum taken
+    # serially over all its points in FP32, held to 1e-5 of the FP64 oracle
+    # (the worst-case rounding bound is 2^-25 n = 3.2e-5; the errors of
+    # random sign stay far below it)
+    rng = np.random.default_rng(77)
+    spec = synth.random_part(rng, 104, kind="part", margin=3.0)
+    tm = synth.render_template(spec)
+    img = synth.paste_scene(spec, (160, 128), [(80.0, 64.0, 30.0)])
+    img = np.clip(img.astype(np.int32) + rng.integers(-6, 7, img.shape), 0, 255).astype(np.uint8)
+    model = sam.Model(tm, 30, 60, 1, 45.0)
+    om = oracle.create_model(tm, 30, 60, 1, 45.0)
+    assert model.num_points(0) >= 1000
+    got = _map(model, 0, img, 2, cfg=(1, 1, 1, 4, 6))
+    generic = _map(model, 0, img, 1)
+    ref = _oracle_map(om, 0, img)
+    assert np.max(np.abs(got - ref)) < TOL
+    assert np.max(np.abs(generic - ref)) < TOL
+
