@@ -714,8 +714,21 @@ def run_hbm(args, sam, torch, dev, stream):
         res["pyramid"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(gbs / peak, 4), "traffic": NCU_HBM_TRAFFIC.get(("pyramid_down_kernel", W_, H_)),
                           "algorithmic_bytes": alg, "us_per_launch": round(ms * 1e3, 2)}
+        del dsts
+        # the detection pipeline's form: levels 1-3 in one launch (level 0
+        # read once, the later levels from shared memory)
+        lv = [[torch.empty((H_ >> l, W_ >> l), dtype=torch.uint8, device=dev) for l in (1, 2, 3)] for _ in range(n)]
+        call = lambda i: sam.pyramid_levels(srcs[i % n], lv[i % n])  # noqa: E731
+        for i in range(3):
+            call(i)
+        ms = _event_ms(torch, dev, stream, call, reps * 4)
+        alg = W_ * H_ + sum((W_ >> l) * (H_ >> l) for l in (1, 2, 3))
+        gbs = alg / (ms * 1e-3) / 1e9
+        res["pyramid_levels"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(gbs / peak, 4), "traffic": None, "algorithmic_bytes": alg,
+                                 "us_per_launch": round(ms * 1e3, 2)}
         out[label] = res
-        del srcs, dsts
+        del srcs, lv
         torch.cuda.empty_cache()
     return out
 
