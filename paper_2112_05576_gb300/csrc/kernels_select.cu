@@ -793,21 +793,58 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                             state[3] ? sbest : -INFINITY);
 }
 
-// Which candidate the cluster's turn cidx refines: the cidx-th of all
-// images' (or pairs') candidates in (image, slot) order; false past the last.
-template <typename CountAt>
-__device__ __forceinline__ bool locate_candidate(int cidx, int n, int K, CountAt count_at, int *img, int *slot) {
+// Which entry `item` is when entry counts weight(i) of n images (or
+// pairs) are laid end to end: *img = i and *rel = item less the entries of
+// the images before it; false past the last.  One warp (all lanes call it
+// with the same arguments): 32 images' counts are loaded at once and
+// scanned with shuffles, so the search costs one memory round trip per 32
+// images rather than one per image.
+template <typename Weight>
+__device__ __forceinline__ bool locate_item(int item, int n, Weight weight, int *img, int *rel) {
+    const int lane = threadIdx.x & 31;
     int acc = 0;
-    for (int i = 0; i < n; ++i) {
-        const int c = min(count_at(i), K);
-        if (cidx < acc + c) {
-            *img = i;
-            *slot = cidx - acc;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int w = i < n ? weight(i) : 0;
+        int v = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o)
+                v += t;
+        }
+        const int hi = acc + v, lo = hi - w;
+        const unsigned hit = __ballot_sync(0xffffffffu, i < n && item >= lo && item < hi);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            *img = base + L;
+            *rel = item - __shfl_sync(0xffffffffu, lo, L);
             return true;
         }
-        acc += c;
+        acc += __shfl_sync(0xffffffffu, v, 31);
     }
     return false;
+}
+
+// Which candidate the cluster's turn cidx refines: the cidx-th of all
+// images' (or pairs') candidates in (image, slot) order; false past the last.
+// Warp 0 searches, the CTA reads the answer from shared memory.
+template <typename CountAt>
+__device__ __forceinline__ bool locate_candidate(int cidx, int n, int K, CountAt count_at, int *img, int *slot) {
+    __shared__ int s_loc[2];
+    if (threadIdx.x < 32) {
+        int i = -1, r = 0;
+        const bool ok = locate_item(cidx, n, [&](int x) { return min(count_at(x), K); }, &i, &r);
+        if (threadIdx.x == 0) {
+            s_loc[0] = ok ? i : -1;
+            s_loc[1] = r;
+        }
+    }
+    __syncthreads();
+    *img = s_loc[0];
+    *slot = s_loc[1];
+    __syncthreads();   // s_loc is rewritten by the next search
+    return *img >= 0;
 }
 
 // Coarse-to-fine refinement (Sec. II: the search starts at the top pyramid
