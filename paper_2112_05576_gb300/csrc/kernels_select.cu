@@ -50,6 +50,29 @@ __device__ __forceinline__ bool is_candidate(const float *__restrict__ map, int 
     const int y = r / gw, x = r - y * gw;
     const int nang = nth / ns;
     const int js = kk / nang, k = kk - js * nang;
+    if (ns == 1) {
+        // one scale: the 26 neighbours' values are loaded together (one
+        // memory round trip), then compared
+        float v[27];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int dk = q / 9 - 1, dy = (q / 3) % 3 - 1, dx = q % 3 - 1;
+            const int y2 = y + dy, x2 = x + dx;
+            const bool in = q != 13 && (dk == 0 || nang > 1) && y2 >= 0 && y2 < gh && x2 >= 0 && x2 < gw;
+            const int k2 = (k + dk + nang) % nang;
+            v[q] = in ? __ldg(map + (size_t)k2 * plane + (size_t)y2 * gw + x2) : -INFINITY;
+        }
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int dk = q / 9 - 1, dy = (q / 3) % 3 - 1, dx = q % 3 - 1;
+            const int y2 = y + dy, x2 = x + dx;
+            const bool in = q != 13 && (dk == 0 || nang > 1) && y2 >= 0 && y2 < gh && x2 >= 0 && x2 < gw;
+            const size_t j = (size_t)((k + dk + nang) % nang) * plane + (size_t)y2 * gw + x2;
+            ok = ok && (!in || j == idx || beats(s, idx, v[q], j));
+        }
+        return ok;
+    }
     for (int dj = -1; dj <= 1; ++dj) {
         const int j2 = js + dj;
         if (j2 < 0 || j2 >= ns)
@@ -230,6 +253,20 @@ __device__ __forceinline__ bool no_neighbour_above(const float *__restrict__ map
     const int y = r / gw, x = r - y * gw;
     const int nang = nth / ns;
     const int js = kk / nang, k = kk - js * nang;
+    if (ns == 1) {
+        // one scale: the 26 neighbours loaded together, then compared
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            const int dk = q / 9 - 1, dy = (q / 3) % 3 - 1, dx = q % 3 - 1;
+            const int y2 = y + dy, x2 = x + dx;
+            const bool in = q != 13 && (dk == 0 || nang > 1) && y2 >= 0 && y2 < gh && x2 >= 0 && x2 < gw;
+            const int k2 = (k + dk + nang) % nang;
+            const float v = in ? __ldg(map + (size_t)k2 * plane + (size_t)y2 * gw + x2) : -INFINITY;
+            ok = ok && !(v > above);
+        }
+        return ok;
+    }
     for (int dj = -1; dj <= 1; ++dj) {
         const int j2 = js + dj;
         if (j2 < 0 || j2 >= ns)
