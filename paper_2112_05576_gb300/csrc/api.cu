@@ -596,11 +596,12 @@ sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p,
                         int capacity, int *n_out) {
     char *ws = (char *)m->ws.base;
     const int count = P.count;
-    std::vector<sam_pose> poses((size_t)p.max_detections * count);
-    std::vector<int> nout(count);
-    SAM_CU(cudaMemcpyAsync(poses.data(), ws + P.off_out, poses.size() * sizeof(sam_pose), cudaMemcpyDeviceToHost,
-                           st));
-    SAM_CU(cudaMemcpyAsync(nout.data(), ws + P.off_nout, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, st));
+    // the poses and the counts after them in one copy
+    const size_t span = P.off_nout + (size_t)count * sizeof(int) - P.off_out;
+    std::vector<char> host(span);
+    SAM_CU(cudaMemcpyAsync(host.data(), ws + P.off_out, span, cudaMemcpyDeviceToHost, st));
+    const sam_pose *poses = reinterpret_cast<const sam_pose *>(host.data());
+    const int *nout = reinterpret_cast<const int *>(host.data() + (P.off_nout - P.off_out));
     int dev_err = 0;
     SAM_CU(score_error_flag_async(&dev_err, st));
     SAM_CU(cudaStreamSynchronize(st));
@@ -611,7 +612,7 @@ sam_status read_results(sam_model *m, const Plan &P, const sam_detect_params &p,
     }
     for (int i = 0; i < count; ++i) {
         const int n = std::min(nout[i], capacity);
-        memcpy(out + (size_t)i * capacity, poses.data() + (size_t)i * p.max_detections, (size_t)n * sizeof(sam_pose));
+        memcpy(out + (size_t)i * capacity, poses + (size_t)i * p.max_detections, (size_t)n * sizeof(sam_pose));
         n_out[i] = n;
     }
     return SAM_OK;
