@@ -639,6 +639,44 @@ struct RefineLevels {
     LevelDev L[kMaxLevels];
 };
 
+__device__ __forceinline__ float rmax3(float a, float b, float c) {
+    float m;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    return m;
+}
+
+// The D x D dot products of one projected point's unit vector (px, py) with
+// the field pixels (x0 .. x0 + D - 1, y0 .. y0 + D - 1) of a W x H level;
+// pixels outside the level count 0.  CHECK = false: the caller has checked
+// that the whole window lies inside (no per-pixel tests).
+template <int D, bool CHECK>
+__device__ __forceinline__ void refine_window(const float2 *__restrict__ F, int W, int H, int x0, int y0, float px,
+                                              float py, float (&d)[D][D]) {
+    if constexpr (!CHECK) {
+        const float2 *q = F + (size_t)y0 * W + x0;
+#pragma unroll
+        for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+            for (int xx = 0; xx < D; ++xx) {
+                const float2 f = __ldg(q + (size_t)yy * W + xx);
+                d[yy][xx] = fmaf(px, f.x, py * f.y);
+            }
+    } else {
+#pragma unroll
+        for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+            for (int xx = 0; xx < D; ++xx) {
+                const int X = x0 + xx, Y = y0 + yy;
+                float v = 0.f;
+                if (X >= 0 && Y >= 0 && X < W && Y < H) {
+                    const float2 f = __ldg(F + (size_t)Y * W + X);
+                    v = fmaf(px, f.x, py * f.y);
+                }
+                d[yy][xx] = v;
+            }
+    }
+}
+
 // One thread-block cluster of kRefineCluster CTAs per candidate: each CTA sums
 // its share of the model points for the 27 poses and leaves the sums in its
 // shared memory; after one cluster barrier every CTA adds the shares of all
@@ -649,16 +687,16 @@ struct RefineLevels {
 // after the barrier of reduction r - 1, which every CTA reaches after it has
 // read the shares of reduction r - 2.  Every branch that skips a cluster
 // barrier is taken by the whole cluster (same candidate, same state).
-template <int NB>
-__device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
+template <int NB, typename View>
+__device__ void refine_body(const View &j, const LevelDev *lv, int c) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ float red[RTHREADS / 32][27];
     __shared__ float part[2][27];   // this CTA's sums of the 27 poses, slot = reduction parity
     __shared__ int state[4];        // x, y, k, alive
     __shared__ float sbest;
-    const int ncand = *j.count;
-    float4 *outp = j.refined + c;
+    const int ncand = *j.count();
+    float4 *outp = j.refined() + c;
     const unsigned rank = cluster.block_rank();
     if (c >= ncand) {
         if (rank == 0 && threadIdx.x == 0)
@@ -666,26 +704,26 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
         return;
     }
     if (threadIdx.x == 0) {
-        const int32_t *kyx = j.kyx + 3 * c;
-        state[0] = kyx[2] * j.step_x;
-        state[1] = kyx[1] * j.step_y;
+        const int32_t *kyx = j.kyx() + 3 * c;
+        state[0] = kyx[2] * j.step_x();
+        state[1] = kyx[1] * j.step_y();
         state[2] = kyx[0];
         state[3] = 1;
-        sbest = j.cs[c];
+        sbest = j.cs()[c];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ns = j.nscales;
+    const int ns = j.nscales();
     int nred = 0;   // reductions so far (share slot parity)
-    for (int l = j.top - 1; l >= 0; --l) {
+    for (int l = j.top() - 1; l >= 0; --l) {
         const LevelDev &L = lv[l];
         // parent table Kp = scale jp x angles + angle kp at level l + 1
         const int Kp = state[2];
         const int2 sh = lv[l + 1].shift[Kp];
         const int cx = 2 * state[0] + sh.x, cy = 2 * state[1] + sh.y;
         const int nang = L.nangles, jp = Kp / lv[l + 1].nangles, kp = Kp - jp * lv[l + 1].nangles;
-        const int W = j.w[l], H = j.h[l];
-        const float2 *F = j.field[l];
+        const int W = j.w(l), H = j.h(l);
+        const float2 *F = j.field(l);
         // the scales jp - 1 .. jp + 1 inside the grid, one pass of 27 poses
         // each (a rigid model: one pass); warp 0 keeps the best over the passes
         const int last_ds = min(1, ns - 1 - jp);
@@ -713,36 +751,39 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
 #pragma unroll
                 for (int dk = 0; dk < 3; ++dk) {
                     const RotPt p = pt[dk];
-                    const int bxp = cx + p.ox, byp = cy + p.oy;
                     constexpr int D = NB + 2;   // window of dot products
+                    const int x0 = cx + p.ox - D / 2, y0 = cy + p.oy - D / 2;
                     float d[D][D];
+                    if (x0 >= 0 && y0 >= 0 && x0 + D <= W && y0 + D <= H)
+                        refine_window<D, false>(F, W, H, x0, y0, p.px, p.py, d);
+                    else
+                        refine_window<D, true>(F, W, H, x0, y0, p.px, p.py, d);
+                    if (j.polarity()) {
 #pragma unroll
-                    for (int yy = 0; yy < D; ++yy) {
+                        for (int yy = 0; yy < D; ++yy)
 #pragma unroll
-                        for (int xx = 0; xx < D; ++xx) {
-                            const int X = bxp + xx - D / 2, Y = byp + yy - D / 2;
-                            float v = 0.f;
-                            if (X >= 0 && Y >= 0 && X < W && Y < H) {
-                                const float2 f = __ldg(F + (size_t)Y * W + X);
-                                v = fmaf(p.px, f.x, p.py * f.y);
-                                if (j.polarity)
-                                    v = fabsf(v);
-                            }
-                            d[yy][xx] = v;
-                        }
+                            for (int xx = 0; xx < D; ++xx)
+                                d[yy][xx] = fabsf(d[yy][xx]);
                     }
+                    if constexpr (NB == 3) {
+                        // 3x3 maxima: rows first, then columns
+                        float hm[D][3];
 #pragma unroll
-                    for (int ty = 0; ty < 3; ++ty) {
+                        for (int yy = 0; yy < D; ++yy)
 #pragma unroll
-                        for (int tx = 0; tx < 3; ++tx) {
-                            float m = -INFINITY;
+                            for (int tx = 0; tx < 3; ++tx)
+                                hm[yy][tx] = rmax3(d[yy][tx], d[yy][tx + 1], d[yy][tx + 2]);
 #pragma unroll
-                            for (int b = 0; b < NB; ++b)
+                        for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
-                                for (int aa = 0; aa < NB; ++aa)
-                                    m = fmaxf(m, d[ty + b][tx + aa]);
-                            acc[dk * 9 + ty * 3 + tx] += m;
-                        }
+                            for (int tx = 0; tx < 3; ++tx)
+                                acc[dk * 9 + ty * 3 + tx] += rmax3(hm[ty][tx], hm[ty + 1][tx], hm[ty + 2][tx]);
+                    } else {
+#pragma unroll
+                        for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+                            for (int tx = 0; tx < 3; ++tx)
+                                acc[dk * 9 + ty * 3 + tx] += d[ty][tx];
                     }
                 }
             }
@@ -813,7 +854,7 @@ __device__ void refine_body(const RefineJob &j, const LevelDev *lv, int c) {
                         state[0] = bx;
                         state[1] = by;
                         state[2] = bkk;
-                        state[3] = any && bs >= j.min_score;
+                        state[3] = any && bs >= j.min_score();
                         sbest = bs;
                     }
                 }
@@ -884,53 +925,75 @@ __device__ __forceinline__ bool locate_candidate(int cidx, int n, int K, CountAt
     return *img >= 0;
 }
 
+// A candidate's image seen through the kernel's arguments (image img of a
+// batch of equal-size images) or through a job of the job list; the
+// arguments are read in place (kernel parameter space or global memory),
+// never copied to a per-thread structure.
+struct ArgsView {
+    const RefineArgs *a;
+    int img;
+    __device__ const float2 *field(int l) const { return a->field[l] + (size_t)img * a->field_img_px[l]; }
+    __device__ int w(int l) const { return a->w[l]; }
+    __device__ int h(int l) const { return a->h[l]; }
+    __device__ int top() const { return a->top; }
+    __device__ int step_x() const { return a->step_x; }
+    __device__ int step_y() const { return a->step_y; }
+    __device__ int polarity() const { return a->polarity; }
+    __device__ float min_score() const { return a->min_score; }
+    __device__ int nscales() const { return a->nscales; }
+    __device__ const int32_t *kyx() const { return a->cand_kyx + (size_t)img * 3 * a->K; }
+    __device__ const float *cs() const { return a->cand_s + (size_t)img * a->K; }
+    __device__ const int *count() const { return a->cand_count + img; }
+    __device__ float4 *refined() const { return a->refined + (size_t)img * a->K; }
+};
+struct JobView {
+    const RefineJob *j;
+    __device__ const float2 *field(int l) const { return j->field[l]; }
+    __device__ int w(int l) const { return j->w[l]; }
+    __device__ int h(int l) const { return j->h[l]; }
+    __device__ int top() const { return j->top; }
+    __device__ int step_x() const { return j->step_x; }
+    __device__ int step_y() const { return j->step_y; }
+    __device__ int polarity() const { return j->polarity; }
+    __device__ float min_score() const { return j->min_score; }
+    __device__ int nscales() const { return j->nscales; }
+    __device__ const int32_t *kyx() const { return j->kyx; }
+    __device__ const float *cs() const { return j->cs; }
+    __device__ const int *count() const { return j->count; }
+    __device__ float4 *refined() const { return j->refined; }
+};
+
 // Coarse-to-fine refinement (Sec. II: the search starts at the top pyramid
 // level; the size-3 neighbouring search in x, y and theta at each lower
 // level), all levels down to 0 in one launch: persistent clusters of
 // kRefineCluster CTAs take the candidates of all images in turn (cluster c
 // the candidates c, c + clusters, ...), so only clusters with a candidate
-// run and empty candidate slots cost nothing.  Three CTAs per SM (85
-// registers) measured faster than two with no register limit.
+// run and empty candidate slots cost nothing.  Two CTAs per SM (128
+// registers, no spills) measured faster than three (80 registers, with
+// spills) and a prefetch of the next point's tables gained nothing.
 template <int NB>
-__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
-    refine_kernel(RefineLevels lv, RefineArgs a) {
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 2)
+    refine_kernel(const __grid_constant__ RefineLevels lv, const __grid_constant__ RefineArgs a) {
     const int clusters = gridDim.x / kRefineCluster;
     for (int cidx = blockIdx.x / kRefineCluster;; cidx += clusters) {
         int img = 0, slot = 0;
         if (!locate_candidate(cidx, a.count, a.K, [&](int i) { return a.cand_count[i]; }, &img, &slot))
             break;
-        RefineJob j;
-        j.L = nullptr;
-        for (int l = 0; l < kMaxLevels; ++l) {
-            j.field[l] = a.field[l] + (size_t)img * a.field_img_px[l];
-            j.w[l] = a.w[l];
-            j.h[l] = a.h[l];
-        }
-        j.top = a.top;
-        j.step_x = a.step_x;
-        j.step_y = a.step_y;
-        j.polarity = a.polarity;
-        j.min_score = a.min_score;
-        j.kyx = a.cand_kyx + (size_t)img * 3 * a.K;
-        j.cs = a.cand_s + (size_t)img * a.K;
-        j.count = a.cand_count + img;
-        j.refined = a.refined + (size_t)img * a.K;
-        j.nscales = a.nscales;
-        refine_body<NB>(j, lv.L, slot);
+        refine_body<NB>(ArgsView{&a, img}, lv.L, slot);
     }
 }
 
 // The same over a job list (pairs of different images and models).
 template <int NB>
-__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 3)
+__global__ void __cluster_dims__(kRefineCluster, 1, 1) __launch_bounds__(RTHREADS, 2)
     refine_jobs_kernel(const RefineJob *__restrict__ jobs, int n_jobs, int K) {
     const int clusters = gridDim.x / kRefineCluster;
     for (int cidx = blockIdx.x / kRefineCluster;; cidx += clusters) {
         int job = 0, slot = 0;
         if (!locate_candidate(cidx, n_jobs, K, [&](int i) { return *jobs[i].count; }, &job, &slot))
             break;
-        const RefineJob &j = jobs[job];
-        refine_body<NB>(j, j.L, slot);
+        const RefineJob *j = jobs + job;
+        refine_body<NB>(JobView{j}, j->L, slot);
     }
 }
 
