@@ -677,6 +677,49 @@ __device__ __forceinline__ void refine_window(const float2 *__restrict__ F, int 
     }
 }
 
+// The 9 scores' terms of one model point at one angle: for each pose
+// (x, y) of the 3 x 3 around (cx, cy), the maximum of the dot products over
+// the point's NB x NB window (Eq. (1)); the point's projection p at that
+// angle; pol: absolute dot products.
+template <int NB>
+__device__ __forceinline__ void refine_maxima(const float2 *__restrict__ F, int W, int H, int cx, int cy,
+                                              const RotPt &p, bool pol, float (&m)[9]) {
+    constexpr int D = NB + 2;   // window of dot products
+    const int x0 = cx + p.ox - D / 2, y0 = cy + p.oy - D / 2;
+    float d[D][D];
+    if (x0 >= 0 && y0 >= 0 && x0 + D <= W && y0 + D <= H)
+        refine_window<D, false>(F, W, H, x0, y0, p.px, p.py, d);
+    else
+        refine_window<D, true>(F, W, H, x0, y0, p.px, p.py, d);
+    if (pol) {
+#pragma unroll
+        for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+            for (int xx = 0; xx < D; ++xx)
+                d[yy][xx] = fabsf(d[yy][xx]);
+    }
+    if constexpr (NB == 3) {
+        // 3x3 maxima: rows first, then columns
+        float hm[D][3];
+#pragma unroll
+        for (int yy = 0; yy < D; ++yy)
+#pragma unroll
+            for (int tx = 0; tx < 3; ++tx)
+                hm[yy][tx] = rmax3(d[yy][tx], d[yy][tx + 1], d[yy][tx + 2]);
+#pragma unroll
+        for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+            for (int tx = 0; tx < 3; ++tx)
+                m[ty * 3 + tx] = rmax3(hm[ty][tx], hm[ty + 1][tx], hm[ty + 2][tx]);
+    } else {
+#pragma unroll
+        for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+            for (int tx = 0; tx < 3; ++tx)
+                m[ty * 3 + tx] = d[ty][tx];
+    }
+}
+
 // One thread-block cluster of kRefineCluster CTAs per candidate: each CTA sums
 // its share of the model points for the 27 poses and leaves the sums in its
 // shared memory; after one cluster barrier every CTA adds the shares of all
@@ -743,48 +786,42 @@ __device__ void refine_body(const View &j, const LevelDev *lv, int c) {
 #pragma unroll
             for (int dk = 0; dk < 3; ++dk)
                 P3[dk] = L.rot + (size_t)(js * nang + (2 * kp + dk - 1 + nang) % nang) * L.n;
-            for (int i = (int)rank * RTHREADS + threadIdx.x; i < L.n; i += kRefineCluster * RTHREADS) {
+            // whole rounds of kStride points, each thread a point at all three
+            // angles; the remaining points as (point, angle) items dealt
+            // round-robin over the cluster's threads, so that no thread
+            // carries a whole extra point while the others wait
+            constexpr int kStride = kRefineCluster * RTHREADS;
+            const int self = (int)rank * RTHREADS + threadIdx.x;
+            const int full = L.n - L.n % kStride, rest = L.n - full;
+            const bool pol = j.polarity() != 0;
+            for (int i = self; i < full; i += kStride) {
                 RotPt pt[3];
 #pragma unroll
                 for (int dk = 0; dk < 3; ++dk)
                     pt[dk] = P3[dk][i];
 #pragma unroll
                 for (int dk = 0; dk < 3; ++dk) {
-                    const RotPt p = pt[dk];
-                    constexpr int D = NB + 2;   // window of dot products
-                    const int x0 = cx + p.ox - D / 2, y0 = cy + p.oy - D / 2;
-                    float d[D][D];
-                    if (x0 >= 0 && y0 >= 0 && x0 + D <= W && y0 + D <= H)
-                        refine_window<D, false>(F, W, H, x0, y0, p.px, p.py, d);
-                    else
-                        refine_window<D, true>(F, W, H, x0, y0, p.px, p.py, d);
-                    if (j.polarity()) {
+                    float m[9];
+                    refine_maxima<NB>(F, W, H, cx, cy, pt[dk], pol, m);
 #pragma unroll
-                        for (int yy = 0; yy < D; ++yy)
+                    for (int q = 0; q < 9; ++q)
+                        acc[dk * 9 + q] += m[q];
+                }
+            }
+            // item dk * rest + r (point full + r at angle dk) goes to thread
+            // (dk * rest + r) mod kStride
 #pragma unroll
-                            for (int xx = 0; xx < D; ++xx)
-                                d[yy][xx] = fabsf(d[yy][xx]);
-                    }
-                    if constexpr (NB == 3) {
-                        // 3x3 maxima: rows first, then columns
-                        float hm[D][3];
+            for (int dk = 0; dk < 3; ++dk) {
+                int r = (self - dk * rest) % kStride;
+                if (r < 0)
+                    r += kStride;
+                for (; r < rest; r += kStride) {
+                    const RotPt pt = P3[dk][full + r];
+                    float m[9];
+                    refine_maxima<NB>(F, W, H, cx, cy, pt, pol, m);
 #pragma unroll
-                        for (int yy = 0; yy < D; ++yy)
-#pragma unroll
-                            for (int tx = 0; tx < 3; ++tx)
-                                hm[yy][tx] = rmax3(d[yy][tx], d[yy][tx + 1], d[yy][tx + 2]);
-#pragma unroll
-                        for (int ty = 0; ty < 3; ++ty)
-#pragma unroll
-                            for (int tx = 0; tx < 3; ++tx)
-                                acc[dk * 9 + ty * 3 + tx] += rmax3(hm[ty][tx], hm[ty + 1][tx], hm[ty + 2][tx]);
-                    } else {
-#pragma unroll
-                        for (int ty = 0; ty < 3; ++ty)
-#pragma unroll
-                            for (int tx = 0; tx < 3; ++tx)
-                                acc[dk * 9 + ty * 3 + tx] += d[ty][tx];
-                    }
+                    for (int q = 0; q < 9; ++q)
+                        acc[dk * 9 + q] += m[q];
                 }
             }
             // block reduction of the 27 sums into this CTA's share
