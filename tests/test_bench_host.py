@@ -1,6 +1,7 @@
 """Host logic of bench.py (no GPU): the roofline arithmetic, the algorithmic
-bytes of a scored slice, and the parsing of the clock samples the timing
-rules depend on (throttle reasons, median SM clock)."""
+bytes of a scored slice, the parsing of the clock samples the timing rules
+depend on (throttle reasons, median SM clock), and the reference arm's JSON
+line (the FP64 oracle timed on the host)."""
 
 import math
 import os
@@ -53,3 +54,28 @@ def test_clock_summary_without_samples(tmp_path):
     assert s.summary()["reasons"] == ["unsampled"]
     s = bench.ClockSampler(0)
     assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host and
+    prints one JSON line in the benchmark's format, with the oracle's own
+    host-only e2e figure (no copies)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
